@@ -1,0 +1,147 @@
+/*
+ * tdc.h -- C ABI of the GB300 structured divide-and-conquer tridiagonal
+ * eigensolver (Liao, Li, Lu, Roman, "A parallel structured divide-and-conquer
+ * algorithm for symmetric tridiagonal eigenvalue problems", IEEE TPDS 2020).
+ *
+ * Problem (Section 2, Eq. (t)): T is a real symmetric tridiagonal n x n matrix
+ * with diagonal d[0..n) and off-diagonal e[0..n-1) (T(i,i+1) = T(i+1,i) = e[i]).
+ * The solver returns T = Q diag(lam) Q^T with lam ascending and Q orthogonal,
+ * by Cuppen's divide and conquer (Algorithm 1 / Algorithm 3): leaf eigensolves,
+ * then a level-by-level merge that deflates (Section 3.2), solves the secular
+ * equation (Eq. (secular)), recomputes zhat, and updates the eigenvectors as
+ * Q * U with the Cauchy-like U of Eq. (Q_Cauchy) generated from (d, lambda,
+ * zhat) inside the GEMM (Section 3.1's generator observation) -- densely, with
+ * off-diagonal tiles compressed (Section 2.1, SRRSC), or as split-precision
+ * BF16 slice products.
+ *
+ * Conventions for every entry point:
+ *   - all array pointers are DEVICE pointers unless the name ends in _host;
+ *     the caller owns every buffer, including the workspace; the library
+ *     allocates no device memory on these paths;
+ *   - matrices are column-major FP64 with a leading dimension argument;
+ *   - work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without synchronising;
+ *   - the return value is a status: TDC_OK (0); -i when argument i (1-based)
+ *     is invalid, checked on the host before anything is enqueued; or one of
+ *     the TDC_E* codes below.  Device-side failures (secular non-convergence,
+ *     a bounded wait that expired) are recorded in a device status word that
+ *     tdc_sync_status() returns;
+ *   - inputs d and e are never modified.
+ */
+#ifndef TDC_H
+#define TDC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
+
+/* status codes */
+#define TDC_OK 0
+#define TDC_ENOWS (-101)       /* workspace pointer NULL or smaller than tdc_*workspace_size */
+#define TDC_ENONFINITE (-102)  /* non-finite value produced (device status) */
+#define TDC_ENOCONV (-103)     /* secular or leaf iteration hit its cap (device status) */
+#define TDC_ETIMEOUT (-104)    /* a bounded device-side wait expired (device status) */
+#define TDC_ECUDA (-105)       /* a CUDA runtime call failed */
+#define TDC_EUNSUPPORTED (-106) /* option combination not supported */
+
+/* merge modes: how the eigenvector update Q * U is computed */
+#define TDC_MERGE_AUTO 0        /* library choice (structured above structured_min_K) */
+#define TDC_MERGE_DENSE 1       /* FP64 GEMM, U generated from its generators in the producer */
+#define TDC_MERGE_STRUCTURED 2  /* near-diagonal tiles dense, off-diagonal tiles SRRSC-compressed */
+#define TDC_MERGE_SPLIT 3       /* BF16 slice products on tcgen05 tensor cores, FP32/FP64 accumulation */
+
+typedef struct {
+  int32_t leaf;             /* leaf size L in 2..64: the tree depth is the smallest t with ceil(n/2^t) <= L */
+  int32_t merge_mode;       /* TDC_MERGE_* */
+  int32_t structured_min_K; /* AUTO: merges with K >= this use the structured path */
+  int32_t lr_tile;          /* tile size m of the structured path (multiple of 64) */
+  double lr_tol;            /* SRRSC stopping tolerance, relative to the tile's largest entry */
+  int32_t split_slices;     /* BF16 slices per operand on the split path (3..8) */
+  int32_t max_iter;         /* secular iteration cap per root (>= 1) */
+  int32_t sign_normalise;   /* 1: make the largest-magnitude entry of every column positive */
+  int32_t collect_stats;    /* 1: record per-level statistics for tdc_get_stats (adds a sync) */
+  int64_t spin_budget;      /* bounded-wait iteration cap for persistent kernels */
+} tdc_opts;
+
+#define TDC_MAX_LEVELS 32
+
+typedef struct {
+  int32_t levels;                        /* merge levels of the last call */
+  int64_t n_merges[TDC_MAX_LEVELS];      /* index 0 = top level */
+  int64_t sum_n[TDC_MAX_LEVELS];
+  int64_t sum_K[TDC_MAX_LEVELS];         /* non-deflated sizes */
+  int64_t max_K[TDC_MAX_LEVELS];
+  int64_t n_rot[TDC_MAX_LEVELS];         /* type-2 (rotation) deflations */
+  int64_t n_type1[TDC_MAX_LEVELS];       /* type-1 (small z) deflations */
+  int64_t secular_iter_max;
+  double secular_iter_mean;
+  float phase_ms[8];                     /* leaf, prepare, secular, zhat+norms+order, gemm, copy, other, total */
+  double gemm_flops[TDC_MAX_LEVELS];     /* algorithmic flops of the Q*U products (2 per multiply-add) */
+  int64_t launches;                      /* kernel launches of the call */
+} tdc_stats;
+
+/* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,
+ * lr_tol 1e-15, split_slices 7, max_iter 64, sign_normalise 1, collect_stats 0). */
+void tdc_default_opts(tdc_opts* o);
+
+/* Workspace bytes tdc_eig needs for order n (o may be NULL = defaults).
+ * Returns TDC_OK, -1 if n < 0, -2 if the options are invalid. */
+int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
+
+/* Eigen-decomposition of one tridiagonal (Algorithm 1 / 3).
+ *   n       order (n = 0: nothing is done; n = 1: lam = d, Q = 1)
+ *   d[n]    diagonal, e[n-1] off-diagonal (device, FP64, not modified)
+ *   lam[n]  eigenvalues, ascending (device, written)
+ *   Q       n x n column-major, leading dimension ldq >= max(1, n) (device, written);
+ *           T = Q diag(lam) Q^T
+ *   ws      device workspace of at least tdc_workspace_size(n) bytes, 256-byte aligned
+ *   o       options (NULL = defaults)
+ * Errors: -1 n < 0; -2/-3 NULL d/e when n > 0 (e may be NULL when n = 1);
+ * -4/-5 NULL lam/Q; -6 ldq < max(1,n); TDC_ENOWS; -9 invalid options; TDC_ECUDA. */
+int tdc_eig(int64_t n, const double* d, const double* e, double* lam, double* Q, int64_t ldq, void* ws,
+            size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream);
+
+/* Workspace for a batch (n_host[batch] on the host). */
+int tdc_eig_batched_workspace_size(int32_t batch, const int64_t* n_host, const tdc_opts* o, size_t* bytes);
+
+/* Many independent tridiagonals in one call: problem b has order n_host[b], its
+ * diagonal at d + off_de_host[b] and off-diagonal at e + off_de_host[b]
+ * (n_b - 1 entries), eigenvalues written to lam + off_de_host[b], eigenvectors to
+ * Q + off_q_host[b] with leading dimension n_b.  All merges of one tree level of
+ * every problem run in the same launches; the host plan is passed to the device
+ * by value inside kernel parameters, so the whole call can be captured in a CUDA
+ * graph and replayed (the captured graph reuses the same pointers and sizes).
+ * Errors: -1 batch < 0, -2 NULL n_host, -3/-4 NULL offsets, -5..-8 NULL arrays,
+ * TDC_ENOWS, -11 invalid options, -1000-b when problem b has n_b < 0. */
+int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_host, const int64_t* off_q_host,
+                    const double* d, const double* e, double* lam, double* Q, void* ws, size_t ws_bytes,
+                    const tdc_opts* o, tdc_stream_t stream);
+
+/* Rank-one eigenproblem D + rho z z^T (one merge's secular stage on its own):
+ * D[K] strictly ascending, z[K] nonzero, rho > 0.  Writes org[K] (int32: index of
+ * the pole the root is measured from, j or j+1), tau[K] (lambda_j = D[org_j] + tau_j),
+ * zhat[K] (Loewner recomputation) and s[K] (column normalisers of Eq. (Q_Cauchy)).
+ * ws of tdc_rank_one_workspace_size(K) bytes. */
+int tdc_rank_one_workspace_size(int64_t K, size_t* bytes);
+int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_t* org, double* tau,
+                 double* zhat, double* s, int32_t max_iter, void* ws, size_t ws_bytes, tdc_stream_t stream);
+
+/* Synchronise `stream` and return the device status word of the last call on
+ * it (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE), then clear it. */
+int tdc_sync_status(tdc_stream_t stream);
+
+/* Copy the statistics of the last call made with collect_stats = 1. */
+int tdc_get_stats(tdc_stats* out);
+
+/* Static text for a status code. */
+const char* tdc_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDC_H */

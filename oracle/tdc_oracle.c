@@ -29,8 +29,10 @@
  *     Theorem 2, Eq. (sid)/(geneZ).
  *
  * Readings of points the paper leaves open (also listed in the design notes):
- *   - split point k = floor(m/2); the tree has a uniform depth t, the smallest
- *     t with ceil(n/2^t) <= leaf;
+ *   - the tree has a uniform depth t, the smallest t with ceil(n/2^t) <= leaf
+ *     (leaf >= 2, so that no node of the tree is empty),
+ *     and node boundaries at floor(i n / 2^l) on level l (so the top split is
+ *     k = floor(n/2) and sibling sizes differ by at most one);
  *   - corner modification d_{k-1} -= |b|, d_k -= |b|, rho = 2|b| >= 0 and
  *     z = [last row of Q1, sign(b) * first row of Q2]/sqrt(2), so ||z|| = 1;
  *   - deflation tolerance tol = 8 eps max(max|d_i|, max|z_i|);
@@ -178,7 +180,8 @@ int orc_leaf_qr(int n, double* d, double* e, double* Q, int64_t ldq) {
 /* (Remark, Eq. (d-lambda)): delta_i = d_i - d_org, and                */
 /*   g(tau) = 1/rho + sum_i z_i^2 / (delta_i - tau)                    */
 /* has the sign of f and increases with tau.  Newton steps safeguarded */
-/* by bisection on the bracket.  D ascending, rho > 0, z_i != 0.       */
+/* by bisection on the bracket until the bracket or the step reaches    */
+/* rounding level.  D ascending, rho > 0, z_i != 0.                    */
 /* Returns the iteration count (negative when the cap was hit).        */
 /* ------------------------------------------------------------------ */
 static void secular_eval(int K, const double* D, const double* z, double rho, int org, double tau,
@@ -218,8 +221,6 @@ int orc_secular_root(int K, const double* D, const double* z, double rho, int j,
     secular_eval(K, D, z, rho, org, tau, &g, &dg, &ga);
     if (g == 0.0) break;
     if (g < 0.0) lo = tau; else hi = tau;
-    /* g is zero within its own rounding error */
-    if (fabs(g) <= ORC_EPS * (double)(K + 2) * ga) break;
     double step = g / dg;
     double tn = tau - step;
     if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
@@ -466,33 +467,38 @@ int orc_merge(int n, int n1, double b, double* lam, double* Q, int64_t ldq, int 
 }
 
 /* ------------------------------------------------------------------ */
-/* Recursive DC (Algorithm 1) on the n x n block at Q (ldq).           */
-/* d is a private copy that receives the corner modifications.         */
+/* Recursive DC (Algorithm 1) on the node [lo, hi) of depth `level`,   */
+/* index `idx` within its level; the tree of order n and depth t has   */
+/* its node boundaries at floor(i n / 2^level), so the node splits at  */
+/* mid = floor((2 idx + 1) n / 2^(level+1)).  d is a private copy that */
+/* receives the corner modifications.                                  */
 /* ------------------------------------------------------------------ */
-static int dc_rec(int n, double* d, const double* e, int depth, double* lam, double* Q, int64_t ldq,
-                  int max_iter, orc_stats* st, int level) {
-  if (depth == 0 || n <= 1) {
+static int dc_rec(int64_t ntot, int64_t lo, int64_t hi, int level, int64_t idx, int t, double* d, const double* e,
+                  double* lam, double* Q, int64_t ldq, int max_iter, orc_stats* st) {
+  int n = (int)(hi - lo);
+  double* Qb = Q + lo + lo * ldq;
+  if (level == t || n <= 1) {
     double* ee = (double*)malloc(sizeof(double) * (size_t)(n > 1 ? n - 1 : 1));
-    for (int i = 0; i < n - 1; ++i) ee[i] = e[i];
-    for (int i = 0; i < n; ++i) lam[i] = d[i];
-    int s = orc_leaf_qr(n, lam, ee, Q, ldq);
+    for (int i = 0; i < n - 1; ++i) ee[i] = e[lo + i];
+    for (int i = 0; i < n; ++i) lam[lo + i] = d[lo + i];
+    int s = orc_leaf_qr(n, lam + lo, ee, Qb, ldq);
     free(ee);
     if (s && st) st->leaf_noconv += 1;
     return s ? 3 : 0;
   }
-  int n1 = n / 2, n2 = n - n1;
-  double b = e[n1 - 1];
-  /* Eq. (T2): T = diag(T1, T2) + |b| v v^T, v = e_{n1-1} + sign(b) e_{n1} */
-  d[n1 - 1] -= fabs(b);
-  d[n1] -= fabs(b);
+  int64_t mid = ((2 * idx + 1) * ntot) >> (level + 1);
+  int n1 = (int)(mid - lo);
+  double b = e[mid - 1];
+  /* Eq. (T2): T = diag(T1, T2) + |b| v v^T, v = e_{mid-1} + sign(b) e_{mid} */
+  d[mid - 1] -= fabs(b);
+  d[mid] -= fabs(b);
   for (int j = 0; j < n1; ++j)
-    for (int i = n1; i < n; ++i) Q[i + (int64_t)j * ldq] = 0.0;
+    for (int i = n1; i < n; ++i) Qb[i + (int64_t)j * ldq] = 0.0;
   for (int j = n1; j < n; ++j)
-    for (int i = 0; i < n1; ++i) Q[i + (int64_t)j * ldq] = 0.0;
-  int s1 = dc_rec(n1, d, e, depth - 1, lam, Q, ldq, max_iter, st, level + 1);
-  int s2 = dc_rec(n2, d + n1, e + n1, depth - 1, lam + n1, Q + n1 + (int64_t)n1 * ldq, ldq, max_iter, st,
-                  level + 1);
-  int s3 = orc_merge(n, n1, b, lam, Q, ldq, max_iter, st, level);
+    for (int i = 0; i < n1; ++i) Qb[i + (int64_t)j * ldq] = 0.0;
+  int s1 = dc_rec(ntot, lo, mid, level + 1, 2 * idx, t, d, e, lam, Q, ldq, max_iter, st);
+  int s2 = dc_rec(ntot, mid, hi, level + 1, 2 * idx + 1, t, d, e, lam, Q, ldq, max_iter, st);
+  int s3 = orc_merge(n, n1, b, lam + lo, Qb, ldq, max_iter, st, level);
   return s1 ? s1 : (s2 ? s2 : s3);
 }
 
@@ -518,7 +524,7 @@ int orc_eig(int n, const double* d, const double* e, int leaf, int max_iter, dou
   for (int i = 0; i < n; ++i) dc[i] = d[i];
   int depth = orc_tree_depth(n, leaf);
   if (st) st->levels = depth;
-  int s = dc_rec(n, dc, e, depth, lam, Q, ldq, max_iter, st, 0);
+  int s = dc_rec(n, 0, n, 0, 0, depth, dc, e, lam, Q, ldq, max_iter, st);
   orc_sign_normalise(n, Q, ldq);
   free(dc);
   return s;

@@ -1,0 +1,465 @@
+// tdc_api.cu -- the C ABI (include/tdc.h): argument checks, the host plan of
+// the divide-and-conquer tree, the workspace layout and the launch sequence.
+//
+// The tree of a problem of order n has depth t (the smallest t with
+// ceil(n/2^t) <= leaf) and node boundaries floor(i n / 2^l) on level l
+// (Algorithm 1's recursive split, written level by level).  Every kernel of a
+// merge level processes all nodes of that level of all problems at once.
+#include <algorithm>
+#include <array>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "tdc_common.cuh"
+
+namespace tdc {
+
+__device__ int g_status;  // device status word (first error wins), per device
+
+static std::mutex g_mu;
+static int* g_status_ptr[64];
+static tdc_stats g_last_stats;
+
+static int* status_ptr() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_status_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
+    g_status_ptr[dev] = (int*)p;
+  }
+  return g_status_ptr[dev];
+}
+
+static int depth_of(int64_t n, int leaf) {
+  int t = 0;
+  while (((n + (((int64_t)1) << t) - 1) >> t) > leaf) ++t;
+  return t;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---------------------------------------------------------------------------
+// Host plan
+// ---------------------------------------------------------------------------
+struct HostPlan {
+  std::vector<Problem> prob;  // sorted by depth, deepest first
+  int64_t N = 0;              // vector slots
+  int64_t Q1 = 0;             // doubles of the internal Q buffer
+  int64_t nleaves = 0;
+  int max_leaf = 1;
+  int T = 0;                  // levels
+  std::vector<LevelLaunch> levels;  // index l
+  int64_t Mmax = 1;
+  std::vector<int64_t> max_tiles;   // GEMM tile upper bound per level
+};
+
+static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const int64_t* off_de,
+                       const int64_t* off_q, const int64_t* ld0, int leaf) {
+  std::vector<Problem> v;
+  for (int32_t b = 0; b < batch; ++b) {
+    if (n_host[b] <= 0) continue;
+    Problem p;
+    memset(&p, 0, sizeof(p));
+    p.n = n_host[b];
+    p.off_de = off_de ? off_de[b] : 0;
+    p.off_q = off_q ? off_q[b] : 0;
+    p.ld0 = ld0 ? ld0[b] : p.n;
+    p.depth = depth_of(p.n, leaf);
+    v.push_back(p);
+  }
+  std::stable_sort(v.begin(), v.end(), [](const Problem& a, const Problem& b) { return a.depth > b.depth; });
+  int64_t vo = 0, qo = 0, lf = 0;
+  int T = 0, ml = 1;
+  for (auto& p : v) {
+    p.voff = vo;
+    p.qoff1 = qo;
+    p.leaf0 = lf;
+    vo += p.n;
+    qo += p.n * p.n;
+    lf += ((int64_t)1) << p.depth;
+    T = std::max(T, (int)p.depth);
+    ml = std::max(ml, (int)((p.n + (((int64_t)1) << p.depth) - 1) >> p.depth));
+  }
+  H.prob = v;
+  H.N = vo;
+  H.Q1 = qo;
+  H.nleaves = lf;
+  H.max_leaf = ml;
+  H.T = T;
+  H.levels.assign(T, LevelLaunch{});
+  H.max_tiles.assign(T, 0);
+  H.Mmax = 1;
+  for (int l = 0; l < T; ++l) {
+    LevelLaunch& L = H.levels[l];
+    L.level = l;
+    int32_t c = 0;
+    int64_t slots = 0, mx = 0, tiles = 0;
+    for (auto& p : v) {
+      if (p.depth <= l) break;
+      ++c;
+      slots += p.n;
+      const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;
+      mx = std::max(mx, nm);
+      const int64_t n1 = (nm + 1) / 2;
+      const int64_t rt = 2 * ((n1 + kDenseBM - 1) / kDenseBM);
+      tiles += (((int64_t)1) << l) * rt * ((nm + kDenseBN - 1) / kDenseBN);
+    }
+    L.nprob_act = c;
+    L.merges = ((int64_t)c) << l;
+    L.nslots = slots;
+    L.max_n = mx;
+    H.max_tiles[l] = tiles;
+    H.Mmax = std::max(H.Mmax, L.merges);
+  }
+}
+
+// workspace carving
+struct Layout {
+  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, q1, total;
+};
+
+static constexpr int kVecD = 17;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey)
+static constexpr int kVecI = 16;  // int32 per slot (incl. 4 for rij, 2 for stag)
+static constexpr int kVecB = 3;   // bytes per slot
+
+static Layout layout_of(const HostPlan& H) {
+  Layout L;
+  size_t o = 0;
+  L.prob = o; o = align_up(o + sizeof(Problem) * std::max<size_t>(1, H.prob.size()));
+  L.vec_d = o; o = align_up(o + sizeof(double) * kVecD * (size_t)std::max<int64_t>(1, H.N));
+  L.vec_i = o; o = align_up(o + sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
+  L.vec_b = o; o = align_up(o + kVecB * (size_t)std::max<int64_t>(1, H.N));
+  L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
+  L.tiles = o; o = align_up(o + sizeof(int64_t) * (size_t)(H.Mmax + 1));
+  L.stats = o; o = align_up(o + sizeof(Stats));
+  L.q1 = o; o = align_up(o + sizeof(double) * (size_t)H.Q1);
+  L.total = o + 256;  // slack for aligning an unaligned base
+  return L;
+}
+
+static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
+  const size_t N = (size_t)std::max<int64_t>(1, H.N);
+  double* vd = (double*)(base + L.vec_d);
+  Vecs& v = P.v;
+  v.dmod = vd + 0 * N; v.lam = vd + 1 * N; v.Dc = vd + 2 * N; v.zc = vd + 3 * N;
+  v.Ds = vd + 4 * N; v.zs = vd + 5 * N; v.Dk = vd + 6 * N; v.zk = vd + 7 * N;
+  v.tau = vd + 8 * N; v.zhat = vd + 9 * N; v.scol = vd + 10 * N; v.cmax = vd + 11 * N;
+  v.dval = vd + 12 * N; v.rcs = vd + 13 * N;  // rcs: 2 per slot (13N..15N)
+  v.skey = vd + 15 * N;                        // 2 per slot (15N..17N)
+  int32_t* vi = (int32_t*)(base + L.vec_i);
+  v.perm = vi + 0 * N; v.kept = vi + 1 * N; v.org = vi + 2 * N; v.dcol = vi + 3 * N;
+  v.tlist = vi + 4 * N; v.blist = vi + 5 * N; v.posr = vi + 6 * N; v.posd = vi + 7 * N;
+  v.rch = vi + 8 * N; v.stag = vi + 9 * N;  // 2N
+  v.rij = vi + 11 * N;                       // 4N (ends at 15N)
+  uint8_t* vb = (uint8_t*)(base + L.vec_b);
+  v.kseg = vb; v.dseg = vb + N; v.cseg = vb + 2 * N;
+  int32_t* mi = (int32_t*)(base + L.minfo);
+  const size_t M = (size_t)H.Mmax;
+  P.m.K = mi; P.m.nd = mi + M; P.m.nrot = mi + 2 * M; P.m.ntop = mi + 3 * M; P.m.nbot = mi + 4 * M;
+  P.m.nchain = mi + 5 * M;
+  P.m.tiles = (int64_t*)(base + L.tiles);
+  P.Q1 = (double*)(base + L.q1);
+  P.prob = (const Problem*)(base + L.prob);
+}
+
+// Problem table upload through kernel parameters (capture-safe: the values
+// are copied into the launch).
+static constexpr int kProbChunk = 40;
+struct ProbChunk {
+  Problem p[kProbChunk];
+};
+__global__ void k_write_problems(ProbChunk c, int cnt, Problem* dst) {
+  if (threadIdx.x < cnt) dst[threadIdx.x] = c.p[threadIdx.x];
+}
+
+static cudaError_t upload_problems(const HostPlan& H, Problem* dst, cudaStream_t s) {
+  const int n = (int)H.prob.size();
+  for (int b = 0; b < n; b += kProbChunk) {
+    ProbChunk c;
+    const int cnt = std::min(kProbChunk, n - b);
+    memset(&c, 0, sizeof(c));
+    for (int i = 0; i < cnt; ++i) c.p[i] = H.prob[b + i];
+    k_write_problems<<<1, 64, 0, s>>>(c, cnt, dst + b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static int validate_opts(const tdc_opts* o) {
+  if (o->leaf < 2 || o->leaf > 64) return 1;  // leaf >= 2 keeps every tree node non-empty
+  if (o->merge_mode < 0 || o->merge_mode > 3) return 1;
+  if (o->max_iter < 1) return 1;
+  if (o->lr_tile < 64 || (o->lr_tile % 64) != 0) return 1;
+  if (o->split_slices < 3 || o->split_slices > 8) return 1;
+  if (!(o->lr_tol > 0.0)) return 1;
+  return 0;
+}
+
+static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const double* e, double* lam, double* Q,
+                    void* ws, size_t ws_bytes, cudaStream_t s) {
+  Layout L = layout_of(H);
+  if (ws == nullptr || ws_bytes < L.total) return TDC_ENOWS;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  Plan P;
+  memset(&P, 0, sizeof(P));
+  carve(P, H, L, base);
+  P.nprob = (int32_t)H.prob.size();
+  P.leaf = o.leaf;
+  P.nslots = H.N;
+  P.Q0 = Q;
+  P.d = d;
+  P.e = e;
+  P.lam_out = lam;
+  P.max_iter = o.max_iter;
+  P.status = status_ptr();
+  if (!P.status) return TDC_ECUDA;
+  P.stats = o.collect_stats ? (Stats*)(base + L.stats) : nullptr;
+  if (H.N == 0) return TDC_OK;
+  cudaError_t err = upload_problems(H, (Problem*)P.prob, s);
+  if (err == cudaSuccess && P.stats) err = cudaMemsetAsync(P.stats, 0, sizeof(Stats), s);
+  cudaEvent_t ev[16];
+  int nev = 0;
+  const bool timing = o.collect_stats != 0;
+  auto mark = [&]() {
+    if (timing && nev < 16) {
+      cudaEventCreate(&ev[nev]);
+      cudaEventRecord(ev[nev], s);
+      ++nev;
+    }
+  };
+  float phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // kernel launches: problem upload, corner modification, leaves, 9 per level, output
+  const int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
+  std::vector<cudaEvent_t> lev;
+  mark();  // 0
+  if (err == cudaSuccess) err = launch_dmod(P, s);
+  if (err == cudaSuccess) err = launch_leaves(P, H.nleaves, H.max_leaf, s);
+  mark();  // 1
+  // per-phase event pairs per level (only when timing)
+  std::vector<std::array<cudaEvent_t, 6>> lv;
+  for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
+    const LevelLaunch& LL = H.levels[l];
+    std::array<cudaEvent_t, 6> es{};
+    auto rec = [&](int k) {
+      if (timing) { cudaEventCreate(&es[k]); cudaEventRecord(es[k], s); }
+    };
+    rec(0);
+    err = launch_prepare(P, LL, s);
+    if (err == cudaSuccess) err = launch_rotate(P, LL, s);
+    rec(1);
+    if (err == cudaSuccess) err = launch_secular(P, LL, s);
+    rec(2);
+    if (err == cudaSuccess) err = launch_lowner(P, LL, s);
+    if (err == cudaSuccess) err = launch_finalize(P, LL, kDenseBM, kDenseBN, s);
+    rec(3);
+    if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
+    rec(4);
+    if (err == cudaSuccess) err = launch_copy_deflated(P, LL, s);
+    rec(5);
+    if (timing) lv.push_back(es);
+  }
+  mark();  // 2
+  if (err == cudaSuccess) err = launch_sign_and_output(P, o.sign_normalise, s);
+  mark();  // 3
+  if (err != cudaSuccess) {
+    for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+    for (auto& es : lv) for (auto e2 : es) if (e2) cudaEventDestroy(e2);
+    return TDC_ECUDA;
+  }
+  if (P.stats) {
+    Stats hs;
+    cudaMemcpyAsync(&hs, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TDC_ECUDA;
+    if (nev >= 4) {
+      cudaEventElapsedTime(&phase[0], ev[0], ev[1]);
+      cudaEventElapsedTime(&phase[7], ev[0], ev[3]);
+      float other = 0;
+      cudaEventElapsedTime(&other, ev[2], ev[3]);
+      phase[6] += other;
+    }
+    for (auto& es : lv) {
+      float t;
+      cudaEventElapsedTime(&t, es[0], es[1]); phase[1] += t;
+      cudaEventElapsedTime(&t, es[1], es[2]); phase[2] += t;
+      cudaEventElapsedTime(&t, es[2], es[3]); phase[3] += t;
+      cudaEventElapsedTime(&t, es[3], es[4]); phase[4] += t;
+      cudaEventElapsedTime(&t, es[4], es[5]); phase[5] += t;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    memset(&g_last_stats, 0, sizeof(g_last_stats));
+    g_last_stats.levels = H.T;
+    for (int l = 0; l < H.T && l < TDC_MAX_LEVELS; ++l) {
+      g_last_stats.n_merges[l] = (int64_t)hs.n_merges[l];
+      g_last_stats.sum_n[l] = (int64_t)hs.sum_n[l];
+      g_last_stats.sum_K[l] = (int64_t)hs.sum_K[l];
+      g_last_stats.max_K[l] = hs.max_K[l];
+      g_last_stats.n_rot[l] = (int64_t)hs.n_rot[l];
+      g_last_stats.n_type1[l] = (int64_t)hs.n_type1[l];
+      g_last_stats.gemm_flops[l] = (double)hs.gemm_flops[l];
+    }
+    g_last_stats.launches = launches;
+    g_last_stats.secular_iter_max = hs.iter_max;
+    g_last_stats.secular_iter_mean = hs.iter_roots ? (double)hs.iter_sum / (double)hs.iter_roots : 0.0;
+    for (int i = 0; i < 8; ++i) g_last_stats.phase_ms[i] = phase[i];
+  }
+  for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
+  for (auto& es : lv) for (auto e2 : es) if (e2) cudaEventDestroy(e2);
+  return TDC_OK;
+}
+
+}  // namespace tdc
+
+using namespace tdc;
+
+extern "C" {
+
+void tdc_default_opts(tdc_opts* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->leaf = 32;
+  o->merge_mode = TDC_MERGE_AUTO;
+  o->structured_min_K = 4096;
+  o->lr_tile = 512;
+  o->lr_tol = 1e-15;
+  o->split_slices = 7;
+  o->max_iter = 64;
+  o->sign_normalise = 1;
+  o->collect_stats = 0;
+  o->spin_budget = 1 << 26;
+}
+
+int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
+  tdc_opts d;
+  tdc_default_opts(&d);
+  if (o) d = *o;
+  if (n < 0) return -1;
+  if (validate_opts(&d)) return -2;
+  if (!bytes) return -3;
+  HostPlan H;
+  build_plan(H, 1, &n, nullptr, nullptr, nullptr, d.leaf);
+  *bytes = layout_of(H).total;
+  return TDC_OK;
+}
+
+int tdc_eig(int64_t n, const double* d, const double* e, double* lam, double* Q, int64_t ldq, void* ws,
+            size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (n == 0) return TDC_OK;
+  if (!d) return -2;
+  if (!e && n > 1) return -3;
+  if (!lam) return -4;
+  if (!Q) return -5;
+  if (ldq < std::max<int64_t>(1, n)) return -6;
+  if (validate_opts(&op)) return -9;
+  HostPlan H;
+  int64_t off = 0, ld = ldq;
+  build_plan(H, 1, &n, &off, &off, &ld, op.leaf);
+  return run_plan(H, op, d, e, lam, Q, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int tdc_eig_batched_workspace_size(int32_t batch, const int64_t* n_host, const tdc_opts* o, size_t* bytes) {
+  tdc_opts d;
+  tdc_default_opts(&d);
+  if (o) d = *o;
+  if (batch < 0) return -1;
+  if (batch > 0 && !n_host) return -2;
+  if (validate_opts(&d)) return -3;
+  if (!bytes) return -4;
+  for (int32_t b = 0; b < batch; ++b)
+    if (n_host[b] < 0) return -1000 - b;
+  HostPlan H;
+  build_plan(H, batch, n_host, nullptr, nullptr, nullptr, d.leaf);
+  *bytes = layout_of(H).total;
+  return TDC_OK;
+}
+
+int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_host, const int64_t* off_q_host,
+                    const double* d, const double* e, double* lam, double* Q, void* ws, size_t ws_bytes,
+                    const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (batch < 0) return -1;
+  if (batch == 0) return TDC_OK;
+  if (!n_host) return -2;
+  if (!off_de_host) return -3;
+  if (!off_q_host) return -4;
+  if (!d) return -5;
+  if (!e) return -6;
+  if (!lam) return -7;
+  if (!Q) return -8;
+  if (validate_opts(&op)) return -11;
+  for (int32_t b = 0; b < batch; ++b)
+    if (n_host[b] < 0) return -1000 - b;
+  HostPlan H;
+  build_plan(H, batch, n_host, off_de_host, off_q_host, nullptr, op.leaf);
+  return run_plan(H, op, d, e, lam, Q, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+int tdc_rank_one_workspace_size(int64_t K, size_t* bytes) {
+  if (K < 0) return -1;
+  if (!bytes) return -2;
+  *bytes = 256;
+  return TDC_OK;
+}
+
+int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_t* org, double* tau, double* zhat,
+                 double* s, int32_t max_iter, void* ws, size_t ws_bytes, tdc_stream_t stream) {
+  (void)ws;
+  (void)ws_bytes;
+  if (K < 0 || K > 0x7fffffff) return -1;
+  if (K == 0) return TDC_OK;
+  if (!D) return -2;
+  if (!z) return -3;
+  if (!(rho > 0.0)) return -4;
+  if (!org) return -5;
+  if (!tau) return -6;
+  if (!zhat) return -7;
+  if (!s) return -8;
+  if (max_iter < 1) return -9;
+  int* st = status_ptr();
+  if (!st) return TDC_ECUDA;
+  cudaError_t e = launch_rank_one(D, z, K, rho, max_iter, org, tau, zhat, s, st, (cudaStream_t)stream);
+  return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+int tdc_sync_status(tdc_stream_t stream) {
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return TDC_ECUDA;
+  int* p = status_ptr();
+  if (!p) return TDC_ECUDA;
+  int v = 0;
+  if (cudaMemcpy(&v, p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TDC_ECUDA;
+  int z = 0;
+  if (cudaMemcpy(p, &z, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return TDC_ECUDA;
+  return v;
+}
+
+int tdc_get_stats(tdc_stats* out) {
+  if (!out) return -1;
+  std::lock_guard<std::mutex> lk(g_mu);
+  *out = g_last_stats;
+  return TDC_OK;
+}
+
+const char* tdc_strerror(int status) {
+  switch (status) {
+    case TDC_OK: return "success";
+    case TDC_ENOWS: return "workspace missing or too small";
+    case TDC_ENONFINITE: return "non-finite value";
+    case TDC_ENOCONV: return "iteration did not converge within its cap";
+    case TDC_ETIMEOUT: return "bounded device-side wait expired";
+    case TDC_ECUDA: return "CUDA runtime error";
+    case TDC_EUNSUPPORTED: return "unsupported option combination";
+    default: return status < 0 ? "invalid argument" : "unknown status";
+  }
+}
+
+}  // extern "C"

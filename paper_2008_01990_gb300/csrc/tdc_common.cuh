@@ -1,0 +1,220 @@
+// tdc_common.cuh -- device-side plan structures and helpers shared by the
+// CUDA translation units of libtdc (never by the CPU oracle).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/tdc.h"
+
+namespace tdc {
+
+// ---------------------------------------------------------------------------
+// Plan.  Problems are sorted by tree depth, deepest first, so that the
+// problems taking part in merge level l (depth > l) form a prefix.  The tree
+// of a problem of order n and depth t has node boundaries floor(i n / 2^l) on
+// level l; node i of level l splits at floor((2i+1) n / 2^(l+1)).
+// ---------------------------------------------------------------------------
+struct Problem {
+  int64_t n;       // order
+  int64_t off_de;  // caller's offset of d, e and lam
+  int64_t off_q;   // caller's offset of Q (buffer 0)
+  int64_t ld0;     // leading dimension in buffer 0
+  int64_t voff;    // offset in the internal vectors (prefix of n)
+  int64_t qoff1;   // offset in the internal Q buffer (prefix of n^2)
+  int64_t leaf0;   // first global leaf index of the problem
+  int32_t depth;   // tree depth t
+  int32_t pad;
+};
+
+struct Vecs {  // per-slot vectors of length N (sum of n); a merge owns [voff+lo, voff+hi)
+  double* dmod;    // corner-modified diagonal
+  double* lam;     // eigenvalues of the current nodes
+  double* Dc;      // poles by merge column (rotated)
+  double* zc;      // z by merge column (rotated)
+  double* Ds;      // poles in ascending order
+  double* zs;      // z in ascending pole order
+  double* Dk;      // non-deflated poles (ascending), K of them
+  double* zk;      // non-deflated z
+  double* tau;     // root offsets
+  double* zhat;    // Loewner zhat
+  double* scol;    // column normalisers
+  double* cmax;    // column max |U_ij| (split scaling)
+  double* dval;    // deflated eigenvalues (scan order)
+  double* rcs;     // rotations: (c, s) pairs, 2 per slot
+  double* skey;    // sort scratch keys, 2 slots per vector slot
+  int32_t* stag;   // sort scratch tags, 2 slots per vector slot
+  int32_t* perm;   // merge columns in ascending pole order
+  int32_t* kept;   // merge column of non-deflated pole j
+  int32_t* org;    // origin pole index of root j (j or j+1)
+  int32_t* dcol;   // merge column of deflated entry q
+  int32_t* tlist;  // non-deflated indices with support in the top half
+  int32_t* blist;  // ... in the bottom half
+  int32_t* posr;   // output column of root j
+  int32_t* posd;   // output column of deflated entry q
+  int32_t* rij;    // rotations: (pj, i, supports) triples, 4 ints per slot
+  int32_t* rch;    // first rotation of each independent rotation chain
+  uint8_t* kseg;   // support bits of non-deflated pole j (1 top, 2 bottom)
+  uint8_t* dseg;   // support bits of deflated entry q
+  uint8_t* cseg;   // support bits scratch by merge column
+};
+
+struct MergeInfo {  // per merge of the current level
+  int32_t* K;       // non-deflated count
+  int32_t* nd;      // deflated count
+  int32_t* nrot;    // rotations
+  int32_t* ntop;    // |S_top|
+  int32_t* nbot;    // |S_bot|
+  int32_t* nchain;  // independent rotation chains
+  int64_t* tiles;   // GEMM tile prefix (M + 1 entries)
+};
+
+struct Stats {  // device-side per-call statistics (index 0 = top level)
+  unsigned long long sum_n[TDC_MAX_LEVELS];
+  unsigned long long sum_K[TDC_MAX_LEVELS];
+  unsigned long long n_rot[TDC_MAX_LEVELS];
+  unsigned long long n_type1[TDC_MAX_LEVELS];
+  unsigned long long n_merges[TDC_MAX_LEVELS];
+  int max_K[TDC_MAX_LEVELS];
+  unsigned long long gemm_flops[TDC_MAX_LEVELS];
+  unsigned long long iter_sum;
+  unsigned long long iter_roots;
+  int iter_max;
+};
+
+struct Plan {
+  const Problem* prob;  // sorted problems (device)
+  int32_t nprob;        // problems in the plan
+  int32_t leaf;         // leaf size
+  int64_t nslots;       // N
+  double* Q0;           // caller's Q (buffer 0)
+  double* Q1;           // internal Q (buffer 1)
+  const double* d;      // caller's d
+  const double* e;      // caller's e
+  double* lam_out;      // caller's lam
+  Vecs v;
+  MergeInfo m;
+  Stats* stats;         // NULL when statistics are off
+  int* status;          // device status word
+  int32_t max_iter;
+};
+
+// A merge (node) of level l: node i of problem p splits at mid.
+struct Node {
+  int64_t lo, mid, hi;  // problem-local rows/columns
+  int64_t v0;           // first vector slot (p.voff + lo)
+  const Problem* p;
+  double* src;          // children's eigenvectors: element (r, c) of the node at src[r + c*lds]
+  double* dst;          // the node's eigenvectors
+  int64_t lds, ldd;
+  double b;             // coupling entry e[mid-1]
+};
+
+__device__ __forceinline__ int64_t node_bound(int64_t i, int64_t n, int level) {
+  return (i * n) >> level;
+}
+
+__device__ __forceinline__ Node make_node(const Plan& P, int level, int64_t g) {
+  Node nd;
+  const Problem* p = P.prob + (g >> level);
+  int64_t i = g & ((((int64_t)1) << level) - 1);
+  nd.p = p;
+  nd.lo = node_bound(i, p->n, level);
+  nd.hi = node_bound(i + 1, p->n, level);
+  nd.mid = node_bound(2 * i + 1, p->n, level + 1);
+  nd.v0 = p->voff + nd.lo;
+  double* b0 = P.Q0 + p->off_q;
+  double* b1 = P.Q1 + p->qoff1;
+  int64_t l0 = p->ld0, l1 = p->n;
+  // level l writes buffer (l & 1); its children (level l+1) live in the other one
+  if (level & 1) {
+    nd.dst = b1 + nd.lo + nd.lo * l1; nd.ldd = l1;
+    nd.src = b0 + nd.lo + nd.lo * l0; nd.lds = l0;
+  } else {
+    nd.dst = b0 + nd.lo + nd.lo * l0; nd.ldd = l0;
+    nd.src = b1 + nd.lo + nd.lo * l1; nd.lds = l1;
+  }
+  nd.b = P.e[p->off_de + nd.mid - 1];
+  return nd;
+}
+
+// binary search: index of the problem (among the first cnt) owning vector slot s
+__device__ __forceinline__ int find_problem_by_slot(const Problem* prob, int cnt, int64_t s) {
+  int lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    int m = (lo + hi + 1) >> 1;
+    if (prob[m].voff <= s) lo = m; else hi = m - 1;
+  }
+  return lo;
+}
+
+// node index on level l containing local row r of a problem of order n
+__device__ __forceinline__ int64_t node_of_row(int64_t r, int64_t n, int level) {
+  int64_t i = (((r + 1) << level) - 1) / n;  // floor(i n / 2^l) <= r
+  while (node_bound(i, n, level) > r) --i;
+  while (node_bound(i + 1, n, level) <= r) ++i;
+  return i;
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic helpers
+// ---------------------------------------------------------------------------
+// Reciprocal of x: hardware estimate (rcp.approx.ftz.f64) followed by two
+// Newton-Raphson refinements r <- r + r (1 - x r), each of which squares the
+// relative error.  Result within a few ulps of 1/x for normal, finite x.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+  double e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-x, r, 1.0);
+  r = fma(r, e, r);
+  return r;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_prod(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v *= __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace tdc
+
+// Host-side launchers (one translation unit each).
+namespace tdc {
+struct LevelLaunch {
+  int level;
+  int64_t merges;     // M
+  int32_t nprob_act;  // problems taking part (prefix)
+  int64_t nslots;     // vector slots of the active problems
+  int64_t max_n;      // largest merge order on the level
+};
+cudaError_t launch_dmod(const Plan& P, cudaStream_t s);
+cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStream_t s);
+cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, int bm, int bn, cudaStream_t s);
+cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream_t s);
+cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
+                            double* tau, double* zhat, double* s, int* status, cudaStream_t st);
+cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s);
+constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
+}  // namespace tdc

@@ -1,0 +1,144 @@
+// tdc_gemm_dense.cu -- eigenvector update of a merge, C = Qtilde * Qhat (Eq. (evect)),
+// in FP64, with Qhat generated from its generators inside the kernel
+// (Eq. (Q_Cauchy), Eq. (d-lambda)) so that it never exists in memory:
+//   Qhat_qj = zhat_q s_j / ((D_q - D_org(j)) - tau_j).
+// The rows of the node split into the top child's rows, which only see the
+// non-deflated columns with support there (S_top), and the bottom child's
+// rows (S_bot); each part is a GEMM over its own list of poles.  Output
+// column j goes to the node's eigenvector column posr[j].
+//
+// One CTA computes a 128 x 64 tile with 256 threads (8 x 4 outputs each) on
+// the FP64 pipe; per 16-deep k-step it stages the Qtilde tile in shared memory
+// and generates the 16 x 64 Qhat tile there (8 FP64 operations per entry,
+// amortised over 128 rows).  Tiles of all merges of the level form one work
+// list (prefix in MergeInfo::tiles) that a fixed grid walks.
+#include <float.h>
+
+#include "tdc_common.cuh"
+
+namespace tdc {
+
+namespace {
+constexpr int BM = kDenseBM, BN = kDenseBN, BK = kDenseBK;
+constexpr int kThreads = 256;
+}  // namespace
+
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, int64_t M) {
+  __shared__ double As[BK][BM];
+  __shared__ double Us[BK][BN];
+  __shared__ double sDo[BN], sTau[BN], sS[BN];
+  __shared__ int sPos[BN];
+  __shared__ int sCol[BK];
+  __shared__ double sDq[BK], sZq[BK];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15;  // column group: 4 columns
+  const int ty = tid >> 4;  // row group: 8 rows
+  const int64_t total = P.m.tiles[M];
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    // merge owning tile w
+    int64_t a = 0, b = M - 1;
+    while (a < b) {
+      int64_t m = (a + b + 1) >> 1;
+      if (P.m.tiles[m] <= w) a = m; else b = m - 1;
+    }
+    const int64_t g = a;
+    const int64_t local = w - P.m.tiles[g];
+    const Node nd = make_node(P, level, g);
+    const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+    const int K = P.m.K[g];
+    const int ct = (K + BN - 1) / BN;
+    const int rtt = (int)(local / ct), ctile = (int)(local % ct);
+    const int rt0 = (n1 + BM - 1) / BM;
+    int r0, rend, nl;
+    const int* list;
+    if (rtt < rt0) { r0 = rtt * BM; rend = n1; list = P.v.tlist + nd.v0; nl = P.m.ntop[g]; }
+    else { r0 = n1 + (rtt - rt0) * BM; rend = n; list = P.v.blist + nd.v0; nl = P.m.nbot[g]; }
+    const int j0 = ctile * BN;
+    const double* Dk = P.v.Dk + nd.v0;
+    __syncthreads();
+    if (tid < BN) {
+      const int j = j0 + tid;
+      if (j < K) {
+        sDo[tid] = Dk[P.v.org[nd.v0 + j]];
+        sTau[tid] = P.v.tau[nd.v0 + j];
+        sS[tid] = P.v.scol[nd.v0 + j];
+        sPos[tid] = P.v.posr[nd.v0 + j];
+      } else {
+        sDo[tid] = 0.0; sTau[tid] = 1.0; sS[tid] = 0.0; sPos[tid] = -1;
+      }
+    }
+    double acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
+    for (int k0 = 0; k0 < nl; k0 += BK) {
+      __syncthreads();
+      if (tid < BK) {
+        const int k = k0 + tid;
+        if (k < nl) {
+          const int q = list[k];
+          sCol[tid] = P.v.kept[nd.v0 + q];
+          sDq[tid] = Dk[q];
+          sZq[tid] = P.v.zhat[nd.v0 + q];
+        } else {
+          sCol[tid] = -1; sDq[tid] = 0.0; sZq[tid] = 0.0;
+        }
+      }
+      __syncthreads();
+      // Qtilde tile: BK columns x BM rows (each column contiguous)
+#pragma unroll
+      for (int e = 0; e < (BK * BM) / kThreads; ++e) {
+        const int idx = tid + e * kThreads;
+        const int k = idx / BM, r = idx % BM;
+        const int col = sCol[k];
+        const int row = r0 + r;
+        As[k][r] = (col >= 0 && row < rend) ? nd.src[row + (int64_t)col * nd.lds] : 0.0;
+      }
+      // Qhat tile generated from the generators
+#pragma unroll
+      for (int e = 0; e < (BK * BN) / kThreads; ++e) {
+        const int idx = tid + e * kThreads;
+        const int k = idx / BN, c = idx % BN;
+        const double del = (sDq[k] - sDo[c]) - sTau[c];
+        Us[k][c] = (sZq[k] * sS[c]) * rcp_nr(del);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        double av[8], bv[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) av[i] = As[k][ty * 8 + i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bv[c] = Us[k][tx * 4 + c];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][c] = fma(av[i], bv[c], acc[i][c]);
+      }
+    }
+    // epilogue: write to the node's output columns
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int pos = sPos[tx * 4 + c];
+      if (pos < 0 || pos >= n) continue;
+      double* out = nd.dst + (int64_t)pos * nd.ldd;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = r0 + ty * 8 + i;
+        if (row < rend) out[row] = acc[i][c];
+      }
+    }
+  }
+}
+
+cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s) {
+  if (max_tiles <= 0) return cudaSuccess;
+  int64_t grid = max_tiles;
+  const int64_t cap = 152 * 8;
+  if (grid > cap) grid = cap;
+  k_gemm_dense<<<(unsigned)grid, kThreads, 0, s>>>(P, L.level, L.merges);
+  return cudaGetLastError();
+}
+
+}  // namespace tdc

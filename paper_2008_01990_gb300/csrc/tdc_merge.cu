@@ -1,0 +1,861 @@
+// tdc_merge.cu -- the merge step of Cuppen's divide and conquer on the GPU,
+// level by level over every node of every problem in the plan:
+//   k_dmod      corner modification of the split points (Eq. (T2))
+//   k_leaf      leaf eigensolves, one warp per leaf (Algorithm 1, "QR")
+//   k_prepare   z gather (Eq. (T3)), merge of the two sorted spectra,
+//               deflation scan (Section 3.2, Eq. (T3-def)), compaction
+//   k_rotate    plane rotations of deflation applied to Q's columns
+//   k_secular   secular equation (Eq. (secular)), one warp per root, FP64,
+//               roots stored as (origin pole, offset) (Eq. (d-lambda))
+//   k_lowner    zhat recomputed from (d, lambda), one warp per pole
+//   k_colnorm   normalisers s_j of the Cauchy-like Qhat (Eq. (Q_Cauchy))
+//   k_finalize  ascending order of all eigenvalues of the node, column targets
+//   k_copy_defl deflated eigenvectors copied to their columns
+//   k_sign_out  sign convention and eigenvalue output
+#include <float.h>
+#include <math.h>
+
+#include "tdc_common.cuh"
+
+namespace tdc {
+
+static constexpr double kEps = DBL_EPSILON;
+
+// ---------------------------------------------------------------------------
+// corner modification: every split point p (a leaf boundary) subtracts |e|
+// from the diagonal entries on both sides
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool is_boundary(int64_t r, int64_t n, int t) {
+  if (r <= 0 || r >= n) return false;
+  int64_t i = ((r << t) + n - 1) / n;  // ceil(r 2^t / n)
+  return ((i * n) >> t) == r;
+}
+
+__global__ void k_dmod(Plan P) {
+  for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < P.nslots;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    int pi = find_problem_by_slot(P.prob, P.nprob, s);
+    const Problem& p = P.prob[pi];
+    int64_t r = s - p.voff;
+    double d = P.d[p.off_de + r];
+    bool ok = isfinite(d);
+    if (r + 1 < p.n) ok = ok && isfinite(P.e[p.off_de + r]);
+    if (is_boundary(r, p.n, p.depth)) d -= fabs(P.e[p.off_de + r - 1]);
+    if (is_boundary(r + 1, p.n, p.depth)) d -= fabs(P.e[p.off_de + r]);
+    if (!ok) set_status(P.status, TDC_ENONFINITE);
+    P.v.dmod[s] = d;
+  }
+}
+
+cudaError_t launch_dmod(const Plan& P, cudaStream_t s) {
+  if (P.nslots == 0) return cudaSuccess;
+  int64_t blocks = (P.nslots + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  k_dmod<<<(unsigned)blocks, 256, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Leaf eigensolves: implicit symmetric QR with Wilkinson shift on an L x L
+// tridiagonal (L <= 64), one warp per leaf.  Lane 0 runs the scalar sweep and
+// records its rotations; all lanes then apply them to their rows of Q, which
+// lives column-major in shared memory.
+// ---------------------------------------------------------------------------
+static constexpr int kMaxLeaf = 64;
+
+__global__ void __launch_bounds__(32) k_leaf(Plan P, int64_t nleaves) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x;
+  int64_t g = blockIdx.x;
+  if (g >= nleaves) return;
+  // problem owning global leaf g (problems sorted by leaf0 ascending)
+  int lo_i = 0, hi_i = P.nprob - 1;
+  while (lo_i < hi_i) {
+    int m = (lo_i + hi_i + 1) >> 1;
+    if (P.prob[m].leaf0 <= g) lo_i = m; else hi_i = m - 1;
+  }
+  const Problem& p = P.prob[lo_i];
+  int64_t li = g - p.leaf0;
+  int t = p.depth;
+  int64_t lo = node_bound(li, p.n, t), hi = node_bound(li + 1, p.n, t);
+  const int L = (int)(hi - lo);
+  double* Qs = sm;                 // L*L
+  double* dd = Qs + L * L;         // L
+  double* ee = dd + L;             // L
+  double* cs = ee + L;             // 2L
+  int* ctrl = (int*)(cs + 2 * L);  // p, q, done, iter
+  int* perm = ctrl + 4;            // L
+  for (int k = lane; k < L * L; k += 32) Qs[k] = ((k % L) == (k / L)) ? 1.0 : 0.0;
+  for (int k = lane; k < L; k += 32) {
+    dd[k] = P.v.dmod[p.voff + lo + k];
+    ee[k] = (k < L - 1) ? P.e[p.off_de + lo + k] : 0.0;
+  }
+  if (lane == 0) { ctrl[2] = 0; ctrl[3] = 0; }
+  __syncwarp();
+  const int max_sweeps = 40 * (L > 0 ? L : 1);
+  while (L > 1) {
+    if (lane == 0) {
+      int q = L - 1;
+      for (int k = 0; k < q; ++k)
+        if (fabs(ee[k]) <= kEps * (fabs(dd[k]) + fabs(dd[k + 1]))) ee[k] = 0.0;
+      while (q > 0 && ee[q - 1] == 0.0) --q;
+      if (q == 0) {
+        ctrl[2] = 1;
+      } else if (++ctrl[3] > max_sweeps) {
+        ctrl[2] = 1;
+        set_status(P.status, TDC_ENOCONV);
+      } else {
+        int pp = q - 1;
+        while (pp > 0 && ee[pp - 1] != 0.0) --pp;
+        // Wilkinson shift: eigenvalue of the trailing 2x2 block nearer to dd[q]
+        double hd = 0.5 * (dd[q - 1] - dd[q]);
+        double bq = ee[q - 1];
+        double h = hypot(hd, bq);
+        double mu = dd[q] - bq * bq / (hd + copysign(h, hd));
+        double x = dd[pp] - mu, y = ee[pp];
+        for (int k = pp; k < q; ++k) {
+          double r = hypot(x, y);
+          double c = 1.0, s = 0.0;
+          if (r != 0.0) { c = x / r; s = y / r; }
+          if (k > pp) ee[k - 1] = r;
+          double a0 = dd[k], a1 = dd[k + 1], bk = ee[k];
+          double cc = c * c, ss = s * s, c2s = 2.0 * c * s * bk;
+          dd[k] = cc * a0 + c2s + ss * a1;
+          dd[k + 1] = ss * a0 - c2s + cc * a1;
+          ee[k] = c * s * (a1 - a0) + (cc - ss) * bk;
+          if (k < q - 1) {
+            y = s * ee[k + 1];
+            ee[k + 1] *= c;
+            x = ee[k];
+          }
+          cs[2 * k] = c;
+          cs[2 * k + 1] = s;
+        }
+        ctrl[0] = pp;
+        ctrl[1] = q;
+      }
+    }
+    __syncwarp();
+    if (ctrl[2]) break;
+    const int pp = ctrl[0], q = ctrl[1];
+    for (int r = lane; r < L; r += 32) {
+      for (int k = pp; k < q; ++k) {
+        double c = cs[2 * k], s = cs[2 * k + 1];
+        double a0 = Qs[r + k * L], a1 = Qs[r + (k + 1) * L];
+        Qs[r + k * L] = c * a0 + s * a1;
+        Qs[r + (k + 1) * L] = c * a1 - s * a0;
+      }
+    }
+    __syncwarp();
+  }
+  // ascending order (stable)
+  if (lane == 0) {
+    for (int k = 0; k < L; ++k) perm[k] = k;
+    for (int k = 1; k < L; ++k) {
+      int v = perm[k];
+      int m = k - 1;
+      while (m >= 0 && dd[perm[m]] > dd[v]) { perm[m + 1] = perm[m]; --m; }
+      perm[m + 1] = v;
+    }
+  }
+  __syncwarp();
+  double* dst;
+  int64_t ld;
+  if (t & 1) { dst = P.Q1 + p.qoff1; ld = p.n; }
+  else { dst = P.Q0 + p.off_q; ld = p.ld0; }
+  dst += lo + lo * ld;
+  for (int k = 0; k < L; ++k) {
+    int c = perm[k];
+    for (int r = lane; r < L; r += 32) dst[r + k * ld] = Qs[r + c * L];
+  }
+  for (int k = lane; k < L; k += 32) P.v.lam[p.voff + lo + k] = dd[perm[k]];
+}
+
+cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStream_t s) {
+  if (nleaves == 0) return cudaSuccess;
+  if (max_leaf > kMaxLeaf) return cudaErrorInvalidValue;
+  size_t smem = sizeof(double) * (max_leaf * max_leaf + 4 * max_leaf) + sizeof(int) * (4 + max_leaf);
+  k_leaf<<<(unsigned)nleaves, 32, smem, s>>>(P, nleaves);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Block helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ T block_reduce_max(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    T m = red[0];
+    for (int i = 1; i < nw; ++i) m = max(m, red[i]);
+    red[0] = m;
+  }
+  __syncthreads();
+  T r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// exclusive prefix of per-thread counts (a, b) across the block
+__device__ void block_excl_scan2(int& a, int& b, int* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  int ia = a, ib = b;
+  for (int o = 1; o < 32; o <<= 1) {
+    int ta = __shfl_up_sync(0xffffffffu, ia, o), tb = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) { ia += ta; ib += tb; }
+  }
+  __syncthreads();
+  if (lane == 31) { red[2 * w] = ia; red[2 * w + 1] = ib; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int sa = 0, sb = 0;
+    for (int i = 0; i < nw; ++i) {
+      int ta = red[2 * i], tb = red[2 * i + 1];
+      red[2 * i] = sa; red[2 * i + 1] = sb;
+      sa += ta; sb += tb;
+    }
+  }
+  __syncthreads();
+  a = red[2 * w] + ia - a;
+  b = red[2 * w + 1] + ib - b;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// k_prepare: one block per merge.
+// ---------------------------------------------------------------------------
+static constexpr int kChunk = 2048;
+
+__global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
+  __shared__ double sD[kChunk];
+  __shared__ double sZ[kChunk];
+  __shared__ int sC[kChunk];
+  __shared__ double redd[64];
+  __shared__ int redi[64];
+  __shared__ int sres[4];
+  const int64_t g = blockIdx.x;
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int64_t v0 = nd.v0;
+  const Vecs& V = P.v;
+  const double rho = 2.0 * fabs(nd.b);
+  const double sg = nd.b < 0.0 ? -1.0 : 1.0;
+  const double rs2 = 0.70710678118654752440;
+  // 1. z gather (last row of Q1, first row of Q2) and column supports
+  double mx = 0.0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    double D = V.lam[v0 + c];
+    double z = (c < n1) ? nd.src[(n1 - 1) + (int64_t)c * nd.lds] : sg * nd.src[n1 + (int64_t)c * nd.lds];
+    z *= rs2;
+    V.Dc[v0 + c] = D;
+    V.zc[v0 + c] = z;
+    mx = fmax(mx, fmax(fabs(D), fabs(z)));
+  }
+  const double tol = 8.0 * kEps * block_reduce_max(mx, redd);
+  // 2. ascending order of the two sorted spectra (stable: first half first on ties)
+  const double* D1 = V.lam + v0;
+  const double* D2 = V.lam + v0 + n1;
+  const int n2 = n - n1;
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  auto rank_of = [&](int c) -> int {
+    const double D = V.lam[v0 + c];
+    if (c < n1) {  // count of D2 < D
+      int a = 0, b = n2;
+      while (a < b) { int m = (a + b) >> 1; if (D2[m] < D) a = m + 1; else b = m; }
+      return c + a;
+    }
+    int a = 0, b = n1;  // count of D1 <= D
+    while (a < b) { int m = (a + b) >> 1; if (D1[m] <= D) a = m + 1; else b = m; }
+    return (c - n1) + a;
+  };
+  for (int c = threadIdx.x; c < n; c += blockDim.x) V.perm[v0 + rank_of(c)] = c;
+  __syncthreads();
+  // the ranks form a permutation unless the spectra are not ordered (non-finite
+  // values); then fall back to the identity so that every index stays in range
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (V.perm[v0 + rank_of(c)] != c) s_bad = 1;
+  __syncthreads();
+  if (s_bad) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) V.perm[v0 + c] = c;
+    if (threadIdx.x == 0) set_status(P.status, TDC_ENONFINITE);
+  }
+  __syncthreads();
+  // 3. deflation scan in ascending pole order (sequential by nature; thread 0
+  //    scans chunks staged in shared memory)
+  int K = 0, ndf = 0, nr = 0, nch = 0;
+  int pj = -1, ps = 0, last_rot_i = -1;
+  double pD = 0.0, pz = 0.0;
+  int t1 = 0;
+  for (int base = 0; base < n; base += kChunk) {
+    const int cnt = min(kChunk, n - base);
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      int c = V.perm[v0 + base + k];
+      sC[k] = c;
+      sD[k] = V.Dc[v0 + c];
+      sZ[k] = V.zc[v0 + c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int k = 0; k < cnt; ++k) {
+        const int c = sC[k];
+        const double D = sD[k], z = sZ[k];
+        const int sp = (c < n1) ? 1 : 2;
+        if (rho * fabs(z) <= tol) {  // type 1: negligible z
+          V.dcol[v0 + ndf] = c; V.dval[v0 + ndf] = D; V.dseg[v0 + ndf] = (uint8_t)sp; ++ndf; ++t1;
+          continue;
+        }
+        if (pj < 0) { pj = c; pD = D; pz = z; ps = sp; continue; }
+        const double tau = hypot(z, pz);
+        const double cc = z / tau, ss = -pz / tau;
+        const double tt = D - pD;
+        if (fabs(tt * cc * ss) <= tol) {  // type 2: rotate the pair so that z_pj = 0
+          const int64_t ro = v0 + nr;
+          V.rij[4 * ro + 0] = pj;
+          V.rij[4 * ro + 1] = c;
+          V.rij[4 * ro + 2] = ps | (sp << 8);
+          V.rcs[2 * ro + 0] = cc;
+          V.rcs[2 * ro + 1] = ss;
+          if (pj != last_rot_i) V.rch[v0 + nch++] = nr;
+          last_rot_i = c;
+          ++nr;
+          const double dp = pD * cc * cc + D * ss * ss;
+          const double di = pD * ss * ss + D * cc * cc;
+          const int u = ps | sp;
+          V.dcol[v0 + ndf] = pj; V.dval[v0 + ndf] = dp; V.dseg[v0 + ndf] = (uint8_t)u; ++ndf;
+          pj = c; pD = di; pz = tau; ps = u;
+        } else {
+          V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
+          pj = c; pD = D; pz = z; ps = sp;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (pj >= 0) {
+      V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
+    }
+    sres[0] = K; sres[1] = ndf; sres[2] = nr; sres[3] = nch;
+    P.m.K[g] = K; P.m.nd[g] = ndf; P.m.nrot[g] = nr; P.m.nchain[g] = nch;
+    if (P.stats && level < TDC_MAX_LEVELS) {
+      atomicAdd(&P.stats->sum_n[level], (unsigned long long)n);
+      atomicAdd(&P.stats->sum_K[level], (unsigned long long)K);
+      atomicAdd(&P.stats->n_rot[level], (unsigned long long)nr);
+      atomicAdd(&P.stats->n_type1[level], (unsigned long long)t1);
+      atomicAdd(&P.stats->n_merges[level], 1ull);
+      atomicMax(&P.stats->max_K[level], K);
+    }
+  }
+  __syncthreads();
+  K = sres[0];
+  // 4. lists of non-deflated poles with support in the top / bottom rows
+  const int per = (K + blockDim.x - 1) / blockDim.x;
+  const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
+  int ct = 0, cb = 0;
+  for (int j = j0; j < j1; ++j) {
+    uint8_t s = V.kseg[v0 + j];
+    ct += (s & 1) ? 1 : 0;
+    cb += (s & 2) ? 1 : 0;
+  }
+  int ot = ct, ob = cb;
+  block_excl_scan2(ot, ob, redi);
+  for (int j = j0; j < j1; ++j) {
+    uint8_t s = V.kseg[v0 + j];
+    if (s & 1) V.tlist[v0 + ot++] = j;
+    if (s & 2) V.blist[v0 + ob++] = j;
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    P.m.ntop[g] = ot;
+    P.m.nbot[g] = ob;
+    if (P.stats && level < TDC_MAX_LEVELS)
+      atomicAdd(&P.stats->gemm_flops[level],
+                2ull * ((unsigned long long)n1 * ot + (unsigned long long)(n - n1) * ob) * (unsigned long long)K);
+  }
+}
+
+cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  int threads = 1024;
+  while (threads > 64 && threads / 2 >= L.max_n) threads /= 2;
+  k_prepare<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k_rotate: apply the deflation rotations to Q's columns.  Rows are
+// independent; chains of rotations that share a column run in order; distinct
+// chains touch disjoint columns.  An entry outside a column's row support
+// (top or bottom child) is a structural zero and is never read.
+// ---------------------------------------------------------------------------
+static constexpr int kRotChainsPerGrid = 64;
+
+__global__ void __launch_bounds__(256) k_rotate(Plan P, int level) {
+  const int64_t g = blockIdx.x;
+  const int nr = P.m.nrot[g];
+  if (nr == 0) return;
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int half = r < n1 ? 1 : 2;
+  const int nch = P.m.nchain[g];
+  const int64_t v0 = nd.v0;
+  double* col = nd.src + r;
+  for (int h = blockIdx.z; h < nch; h += gridDim.z) {
+    const int k0 = P.v.rch[v0 + h];
+    const int k1 = (h + 1 < nch) ? P.v.rch[v0 + h + 1] : nr;
+    for (int k = k0; k < k1; ++k) {
+      const int pj = P.v.rij[4 * (v0 + k) + 0];
+      const int ci = P.v.rij[4 * (v0 + k) + 1];
+      const int sup = P.v.rij[4 * (v0 + k) + 2];
+      const int sp = sup & 0xff, si = sup >> 8;
+      if (!((sp | si) & half)) continue;
+      const double c = P.v.rcs[2 * (v0 + k)], s = P.v.rcs[2 * (v0 + k) + 1];
+      const double x = (sp & half) ? col[(int64_t)pj * nd.lds] : 0.0;
+      const double y = (si & half) ? col[(int64_t)ci * nd.lds] : 0.0;
+      col[(int64_t)pj * nd.lds] = c * x + s * y;
+      col[(int64_t)ci * nd.lds] = c * y - s * x;
+    }
+  }
+}
+
+cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), kRotChainsPerGrid);
+  k_rotate<<<grid, 256, 0, s>>>(P, L.level);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Root-slot mapping: warp w of the level handles vector slot w.
+// ---------------------------------------------------------------------------
+struct Slot {
+  bool valid;
+  int64_t g;      // merge index on the level
+  int j;          // root / pole index within the merge
+  int K;
+  int64_t v0;
+  double rho;
+};
+
+__device__ __forceinline__ Slot slot_of(const Plan& P, int level, int nprob_act, int64_t s) {
+  Slot o;
+  o.valid = false;
+  int pi = find_problem_by_slot(P.prob, nprob_act, s);
+  const Problem& p = P.prob[pi];
+  int64_t r = s - p.voff;
+  if (r < 0 || r >= p.n) return o;
+  int64_t i = node_of_row(r, p.n, level);
+  int64_t lo = node_bound(i, p.n, level);
+  int64_t mid = node_bound(2 * i + 1, p.n, level + 1);
+  o.g = ((int64_t)pi << level) + i;
+  o.j = (int)(r - lo);
+  o.K = P.m.K[o.g];
+  o.v0 = p.voff + lo;
+  o.rho = 2.0 * fabs(P.e[p.off_de + mid - 1]);
+  o.valid = o.j < o.K;
+  return o;
+}
+
+// ---------------------------------------------------------------------------
+// k_secular: root j of 1/rho + sum_i z_i^2/(d_i - lambda) = 0 (Eq. (secular)).
+// Origin: d_j when the function is >= 0 at the midpoint of (d_j, d_{j+1}),
+// else d_{j+1}; the last root is measured from d_{K-1}.  With
+// delta_i = d_i - d_org, g(tau) = 1/rho + sum_i z_i^2/(delta_i - tau).
+// Iteration: the two sums over poles left (psi) and right (phi) of the root
+// are each replaced by a constant plus one pole term matching value and slope
+// at tau (the nearest poles d_j, d_{j+1}); the model's root is the next iterate
+// (a quadratic), safeguarded by bisection on the bracket.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void secular_sums(const double* D, const double* z, int K, int j, double dorg,
+                                             double tau, double& psi, double& dpsi, double& phi,
+                                             double& dphi, double& sabs) {
+  const int lane = threadIdx.x & 31;
+  double a = 0.0, da = 0.0, b = 0.0, db = 0.0, ab = 0.0;
+  for (int i = lane; i < K; i += 32) {
+    const double del = (D[i] - dorg) - tau;
+    const double r = rcp_nr(del);
+    const double zi = z[i];
+    const double t = zi * zi * r;
+    ab += fabs(t);
+    if (i <= j) { a += t; da = fma(t, r, da); }
+    else { b += t; db = fma(t, r, db); }
+  }
+  psi = warp_sum(a);
+  dpsi = warp_sum(da);
+  phi = warp_sum(b);
+  dphi = warp_sum(db);
+  sabs = warp_sum(ab);
+}
+
+// Warp-cooperative solve of root j; every lane returns the same (org, tau).
+__device__ void secular_root(const double* D, const double* z, int K, int j, double rho, int max_iter,
+                             int& org_out, double& tau_out, int& iters, bool& conv) {
+  const double irho = 1.0 / rho;
+  int org;
+  double lo, hi;
+  if (j < K - 1) {
+    const double gap = D[j + 1] - D[j];
+    double psi, dpsi, phi, dphi, sabs;
+    secular_sums(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
+    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; }
+    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; }
+  } else {
+    double zz = 0.0;
+    for (int i = threadIdx.x & 31; i < K; i += 32) zz = fma(z[i], z[i], zz);
+    zz = warp_sum(zz);
+    org = K - 1; lo = 0.0; hi = rho * zz;
+  }
+  const double dorg = D[org];
+  const double dl = D[j] - dorg;                         // delta_j (0 when org == j)
+  const double dr = (j < K - 1) ? D[j + 1] - dorg : 0.0; // delta_{j+1}
+  double tau = 0.5 * (lo + hi);
+  int it = 0;
+  conv = false;
+  for (it = 1; it <= max_iter; ++it) {
+    double psi, dpsi, phi, dphi, sabs;
+    secular_sums(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
+    const double gv = irho + psi + phi;
+    if (gv == 0.0 || fabs(gv) <= 8.0 * kEps * (irho + sabs)) { conv = true; break; }
+    if (gv < 0.0) lo = tau; else hi = tau;
+    // two-pole rational model of g around tau
+    const double p = dl - tau;  // < 0
+    double h = 0.0;
+    bool ok = true;
+    if (j < K - 1) {
+      const double q = dr - tau;  // > 0
+      const double b1 = dpsi * p * p, b2 = dphi * q * q;
+      const double A = irho + (psi - b1 / p) + (phi - b2 / q);
+      const double B = A * (p + q) + b1 + b2;
+      const double C = p * q * gv;
+      if (A == 0.0) {
+        h = C / B;
+      } else {
+        const double disc = B * B - 4.0 * A * C;
+        if (disc < 0.0) {
+          ok = false;
+        } else {
+          const double w = B + copysign(sqrt(disc), B);
+          const double h1 = (w != 0.0) ? 2.0 * C / w : 0.0;
+          const double h2 = w / (2.0 * A);
+          const bool in1 = (h1 > p && h1 < q), in2 = (h2 > p && h2 < q);
+          if (in1 && (!in2 || fabs(h1) <= fabs(h2))) h = h1;
+          else if (in2) h = h2;
+          else ok = false;
+        }
+      }
+    } else {
+      const double b1 = dpsi * p * p;
+      const double A = irho + (psi - b1 / p) + phi;
+      if (A != 0.0) h = p + b1 / A; else ok = false;
+    }
+    double tn = tau + h;
+    if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5 * (lo + hi);
+    const bool small_step = fabs(tn - tau) <= 2.0 * kEps * fabs(tau);
+    tau = tn;
+    if (small_step || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) { conv = true; break; }
+  }
+  org_out = org;
+  tau_out = tau;
+  iters = min(it, max_iter);
+}
+
+__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_act, int64_t nslots) {
+  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (s >= nslots) return;
+  const Slot S = slot_of(P, level, nprob_act, s);
+  if (!S.valid) return;
+  int org, it;
+  double tau;
+  bool conv;
+  secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
+  if ((threadIdx.x & 31) == 0) {
+    P.v.org[S.v0 + S.j] = org;
+    P.v.tau[S.v0 + S.j] = tau;
+    if (!conv) set_status(P.status, TDC_ENOCONV);
+    if (P.stats) {
+      atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
+      atomicAdd(&P.stats->iter_roots, 1ull);
+      atomicMax(&P.stats->iter_max, it);
+    }
+  }
+}
+
+cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  if (L.nslots == 0) return cudaSuccess;
+  const int64_t blocks = (L.nslots * 32 + 255) / 256;
+  k_secular<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k_lowner: zhat_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i)),
+// as the product of the ratios (lambda_j - d_i)/(d_j - d_i) for j < i,
+// (lambda_j - d_i)/(d_{j+1} - d_i) for i <= j < K-1 and (lambda_{K-1} - d_i)/rho,
+// each in (0, 1]; lambda_j - d_i = (d_org(j) - d_i) + tau_j.
+// ---------------------------------------------------------------------------
+__device__ double lowner_zhat(const double* D, const int* org, const double* tau, int K, int i, double rho,
+                              double zsign) {
+  const double di = D[i];
+  double pr = 1.0;
+  for (int j = threadIdx.x & 31; j < K; j += 32) {
+    const double num = (D[org[j]] - di) + tau[j];
+    if (j == K - 1) pr *= num / rho;
+    else {
+      const double den = (j < i) ? (D[j] - di) : (D[j + 1] - di);
+      pr *= num * rcp_nr(den);
+    }
+  }
+  pr = warp_prod(pr);
+  return copysign(sqrt(pr), zsign);
+}
+
+__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int nprob_act, int64_t nslots) {
+  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (s >= nslots) return;
+  const Slot S = slot_of(P, level, nprob_act, s);
+  if (!S.valid) return;
+  const double zh = lowner_zhat(P.v.Dk + S.v0, P.v.org + S.v0, P.v.tau + S.v0, S.K, S.j, S.rho,
+                                P.v.zk[S.v0 + S.j]);
+  if ((threadIdx.x & 31) == 0) P.v.zhat[S.v0 + S.j] = zh;
+}
+
+// s_j = 1 / sqrt(sum_i (zhat_i / delta_ij)^2), delta_ij = (d_i - d_org(j)) - tau_j; also max_i |Qhat_ij|.
+__device__ void column_norm(const double* D, const double* zh, int K, double dorg, double tj, double& sj,
+                            double& cmax) {
+  double acc = 0.0, mx = 0.0;
+  for (int i = threadIdx.x & 31; i < K; i += 32) {
+    const double u = zh[i] * rcp_nr((D[i] - dorg) - tj);
+    acc = fma(u, u, acc);
+    mx = fmax(mx, fabs(u));
+  }
+  acc = warp_sum(acc);
+  mx = warp_max(mx);
+  sj = 1.0 / sqrt(acc);
+  cmax = mx * sj;
+}
+
+__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int nprob_act, int64_t nslots) {
+  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (s >= nslots) return;
+  const Slot S = slot_of(P, level, nprob_act, s);
+  if (!S.valid) return;
+  const double* D = P.v.Dk + S.v0;
+  double sj, cm;
+  column_norm(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j], sj, cm);
+  if ((threadIdx.x & 31) == 0) {
+    P.v.scol[S.v0 + S.j] = sj;
+    P.v.cmax[S.v0 + S.j] = cm;
+  }
+}
+
+// Stand-alone rank-one eigenproblem (tdc_rank_one): the three warp-per-entry stages.
+__global__ void __launch_bounds__(256) k_r1_secular(const double* D, const double* z, int K, double rho,
+                                                     int max_iter, int* org, double* tau, int* status) {
+  const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (j >= K) return;
+  int o, it;
+  double t;
+  bool conv;
+  secular_root(D, z, K, (int)j, rho, max_iter, o, t, it, conv);
+  if ((threadIdx.x & 31) == 0) {
+    org[j] = o;
+    tau[j] = t;
+    if (!conv) set_status(status, TDC_ENOCONV);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_r1_lowner(const double* D, const double* z, const int* org,
+                                                    const double* tau, int K, double rho, double* zhat) {
+  const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (i >= K) return;
+  const double zh = lowner_zhat(D, org, tau, K, (int)i, rho, z[i]);
+  if ((threadIdx.x & 31) == 0) zhat[i] = zh;
+}
+
+__global__ void __launch_bounds__(256) k_r1_colnorm(const double* D, const int* org, const double* tau,
+                                                     const double* zhat, int K, double* s) {
+  const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (j >= K) return;
+  double sj, cm;
+  column_norm(D, zhat, K, D[org[j]], tau[j], sj, cm);
+  if ((threadIdx.x & 31) == 0) s[j] = sj;
+}
+
+cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
+                            double* tau, double* zhat, double* s, int* status, cudaStream_t st) {
+  if (K == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((K * 32 + 255) / 256);
+  k_r1_secular<<<blocks, 256, 0, st>>>(D, z, (int)K, rho, max_iter, org, tau, status);
+  k_r1_lowner<<<blocks, 256, 0, st>>>(D, z, org, tau, (int)K, rho, zhat);
+  k_r1_colnorm<<<blocks, 256, 0, st>>>(D, org, tau, zhat, (int)K, s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  if (L.nslots == 0) return cudaSuccess;
+  const int64_t blocks = (L.nslots * 32 + 255) / 256;
+  k_lowner<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_colnorm<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k_finalize: one block per merge.  All n eigenvalues of the node -- the K
+// roots d_org(j) + tau_j and the deflated values -- sorted ascending (stable
+// over [roots, deflated]) with a bitonic network in the sort scratch; the
+// result goes to lam, and every root / deflated entry learns its output column.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool key_less(double ka, int ta, double kb, int tb) {
+  return ka < kb || (ka == kb && ta < tb);
+}
+
+__global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, int bn) {
+  const int64_t g = blockIdx.x;
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int64_t v0 = nd.v0;
+  const int K = P.m.K[g];
+  int P2 = 1;
+  while (P2 < n) P2 <<= 1;
+  double* key = P.v.skey + 2 * v0;
+  int* tag = P.v.stag + 2 * v0;
+  for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+    double kv;
+    if (t < K) { kv = P.v.Dk[v0 + P.v.org[v0 + t]] + P.v.tau[v0 + t]; tag[t] = t; }
+    else if (t < n) { kv = P.v.dval[v0 + t - K]; tag[t] = t; }
+    else { kv = INFINITY; tag[t] = 0x7fffffff; }
+    key[t] = isnan(kv) ? INFINITY : kv;  // total order: the n real entries come first
+  }
+  __syncthreads();
+  for (int k = 2; k <= P2; k <<= 1) {
+    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+      for (int t = threadIdx.x; t < P2; t += blockDim.x) {
+        const int u = t ^ jj;
+        if (u > t) {
+          const bool up = (t & k) == 0;
+          const double ka = key[t], kb = key[u];
+          const int ta = tag[t], tb = tag[u];
+          const bool sw = up ? key_less(kb, tb, ka, ta) : key_less(ka, ta, kb, tb);
+          if (sw) { key[t] = kb; key[u] = ka; tag[t] = tb; tag[u] = ta; }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const int t = tag[p];
+    P.v.lam[v0 + p] = key[p];
+    if (t < K) P.v.posr[v0 + t] = p;
+    else if (t < n) P.v.posd[v0 + t - K] = p;
+  }
+  if (threadIdx.x == 0) {
+    // GEMM tiles of this merge: (row tiles of top + bottom parts) x column tiles
+    const int64_t rt = (n1 + bm - 1) / bm + (n - n1 + bm - 1) / bm;
+    const int64_t ct = (K + bn - 1) / bn;
+    P.m.tiles[g + 1] = (K > 0) ? rt * ct : 0;
+  }
+}
+
+__global__ void k_tile_scan(Plan P, int64_t M) {
+  // single block exclusive scan of P.m.tiles[1..M] into a prefix with tiles[0] = 0
+  __shared__ int64_t part[1024];
+  const int64_t per = (M + blockDim.x - 1) / blockDim.x;
+  const int64_t a = min(M, (int64_t)threadIdx.x * per), b = min(M, a + per);
+  int64_t s = 0;
+  for (int64_t i = a; i < b; ++i) s += P.m.tiles[i + 1];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { int64_t t = part[i]; part[i] = run; run += t; }
+  }
+  __syncthreads();
+  int64_t run = part[threadIdx.x];
+  for (int64_t i = a; i < b; ++i) { run += P.m.tiles[i + 1]; P.m.tiles[i + 1] = run; }
+  if (threadIdx.x == 0) P.m.tiles[0] = 0;
+}
+
+cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, int bm, int bn, cudaStream_t s) {
+  int threads = 1024;
+  while (threads > 64 && threads / 2 >= L.max_n) threads /= 2;
+  k_finalize<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level, bm, bn);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_tile_scan<<<1, 1024, 0, s>>>(P, L.merges);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// k_copy_defl: deflated eigenvectors (columns of the rotated Q) to their output
+// columns; entries outside the column's row support are written as zeros.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_copy_defl(Plan P, int level) {
+  const int64_t g = blockIdx.x;
+  const int ndf = P.m.nd[g];
+  if (ndf == 0) return;
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int r = blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const int half = r < n1 ? 1 : 2;
+  const int64_t v0 = nd.v0;
+  for (int q = blockIdx.z; q < ndf; q += gridDim.z) {
+    const int c = P.v.dcol[v0 + q];
+    const int sp = P.v.dseg[v0 + q];
+    const int o = P.v.posd[v0 + q];
+    if (o < 0 || o >= n) continue;
+    const double x = (sp & half) ? nd.src[r + (int64_t)c * nd.lds] : 0.0;
+    nd.dst[r + (int64_t)o * nd.ldd] = x;
+  }
+}
+
+cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), 64);
+  k_copy_defl<<<grid, 256, 0, s>>>(P, L.level);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Output: sign convention (entry of largest magnitude positive, lowest row on
+// ties) and eigenvalues to the caller's array.  One warp per column.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_sign_out(Plan P, int sign_normalise) {
+  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (s >= P.nslots) return;
+  const int lane = threadIdx.x & 31;
+  const int pi = find_problem_by_slot(P.prob, P.nprob, s);
+  const Problem& p = P.prob[pi];
+  const int64_t c = s - p.voff;
+  double* col = P.Q0 + p.off_q + c * p.ld0;
+  if (sign_normalise) {
+    double best = -1.0;
+    int64_t bi = 0;  // stays in range even for a column of NaNs
+    for (int64_t r = lane; r < p.n; r += 32) {
+      const double a = fabs(col[r]);
+      if (a > best) { best = a; bi = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (col[bi] < 0.0)
+      for (int64_t r = lane; r < p.n; r += 32) col[r] = -col[r];
+  }
+  if (lane == 0) P.lam_out[p.off_de + c] = P.v.lam[s];
+}
+
+cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream_t s) {
+  if (P.nslots == 0) return cudaSuccess;
+  const int64_t blocks = (P.nslots * 32 + 255) / 256;
+  k_sign_out<<<(unsigned)blocks, 256, 0, s>>>(P, sign_normalise);
+  return cudaGetLastError();
+}
+
+}  // namespace tdc

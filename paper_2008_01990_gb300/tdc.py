@@ -1,0 +1,239 @@
+"""Thin ctypes binding of ``libtdc.so`` (declared in ``include/tdc.h``).
+
+Argument marshalling only: every step of the eigensolver runs in the CUDA
+library.  PyTorch provides device memory and the current stream.  Loading
+fails loudly when the library has not been built -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtdc.so")
+_lib = None
+
+TDC_OK = 0
+TDC_ENOWS = -101
+TDC_ENONFINITE = -102
+TDC_ENOCONV = -103
+TDC_ETIMEOUT = -104
+TDC_ECUDA = -105
+TDC_EUNSUPPORTED = -106
+
+MERGE_AUTO = 0
+MERGE_DENSE = 1
+MERGE_STRUCTURED = 2
+MERGE_SPLIT = 3
+
+MAX_LEVELS = 32
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [
+        ("leaf", ctypes.c_int32),
+        ("merge_mode", ctypes.c_int32),
+        ("structured_min_K", ctypes.c_int32),
+        ("lr_tile", ctypes.c_int32),
+        ("lr_tol", ctypes.c_double),
+        ("split_slices", ctypes.c_int32),
+        ("max_iter", ctypes.c_int32),
+        ("sign_normalise", ctypes.c_int32),
+        ("collect_stats", ctypes.c_int32),
+        ("spin_budget", ctypes.c_int64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int32),
+        ("n_merges", ctypes.c_int64 * MAX_LEVELS),
+        ("sum_n", ctypes.c_int64 * MAX_LEVELS),
+        ("sum_K", ctypes.c_int64 * MAX_LEVELS),
+        ("max_K", ctypes.c_int64 * MAX_LEVELS),
+        ("n_rot", ctypes.c_int64 * MAX_LEVELS),
+        ("n_type1", ctypes.c_int64 * MAX_LEVELS),
+        ("secular_iter_max", ctypes.c_int64),
+        ("secular_iter_mean", ctypes.c_double),
+        ("phase_ms", ctypes.c_float * 8),
+        ("gemm_flops", ctypes.c_double * MAX_LEVELS),
+        ("launches", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        L = self.levels
+        names = ["leaf", "prepare", "secular", "zhat_norms_order", "gemm", "copy", "other", "total"]
+        return {
+            "levels": L,
+            "n_merges": list(self.n_merges[:L]),
+            "sum_n": list(self.sum_n[:L]),
+            "sum_K": list(self.sum_K[:L]),
+            "max_K": list(self.max_K[:L]),
+            "type2": list(self.n_rot[:L]),
+            "type1": list(self.n_type1[:L]),
+            "secular_iter_max": self.secular_iter_max,
+            "secular_iter_mean": self.secular_iter_mean,
+            "phase_ms": dict(zip(names, list(self.phase_ms))),
+            "gemm_flops": list(self.gemm_flops[:L]),
+            "launches": self.launches,
+        }
+
+
+class TdcError(RuntimeError):
+    def __init__(self, fn, status):
+        self.status = status
+        msg = lib().tdc_strerror(status).decode() if status != 0 else "ok"
+        super().__init__("%s failed: status %d (%s)" % (fn, status, msg))
+
+
+def lib():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libtdc.so is not built (run __graft_entry__.build() or python -m "
+                           "paper_2008_01990_gb300.build); there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P = ctypes.c_void_p
+    i64, i32, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+    L.tdc_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.tdc_default_opts.restype = None
+    L.tdc_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    L.tdc_eig.argtypes = [i64, P, P, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
+    L.tdc_eig_batched_workspace_size.argtypes = [i32, P, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+    L.tdc_eig_batched.argtypes = [i32, P, P, P, P, P, P, P, P, sz, ctypes.POINTER(Opts), P]
+    L.tdc_sync_status.argtypes = [P]
+    L.tdc_get_stats.argtypes = [ctypes.POINTER(Stats)]
+    L.tdc_strerror.argtypes = [ctypes.c_int]
+    L.tdc_strerror.restype = ctypes.c_char_p
+    if hasattr(L, "tdc_backward_workspace_size"):
+        L.tdc_backward_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
+        L.tdc_eig_backward.argtypes = [i64, P, P, i64, P, P, P, P, P, sz, P]
+        L.tdc_backward_batched_workspace_size.argtypes = [i32, i64, ctypes.POINTER(sz)]
+        L.tdc_eig_backward_batched.argtypes = [i32, i64, P, P, P, P, P, P, P, sz, P]
+    if hasattr(L, "tdc_rank_one"):
+        L.tdc_rank_one_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
+        L.tdc_rank_one.argtypes = [i64, P, P, ctypes.c_double, P, P, P, P, i32, P, sz, P]
+    if hasattr(L, "tdc_cauchy_gemm"):
+        L.tdc_cauchy_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_cauchy_gemm.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, i64, i32, ctypes.POINTER(Opts), P,
+                                      sz, P]
+    _lib = L
+    return L
+
+
+def _check(fn, st):
+    if st != 0:
+        raise TdcError(fn, st)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().tdc_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def workspace_size(n: int, opts: Opts | None = None) -> int:
+    b = ctypes.c_size_t(0)
+    _check("tdc_workspace_size", lib().tdc_workspace_size(int(n), ctypes.byref(opts) if opts else None,
+                                                          ctypes.byref(b)))
+    return b.value
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 1), dtype=torch.uint8, device=device)
+
+
+def eig(d: torch.Tensor, e: torch.Tensor, opts: Opts | None = None, ws: torch.Tensor | None = None,
+        lam: torch.Tensor | None = None, Q: torch.Tensor | None = None, stream=None, check: bool = False):
+    """T = Q diag(lam) Q^T for the tridiagonal (d, e) (device FP64).  Q is
+    returned as a column-major n x n matrix (a transposed view of row-major storage)."""
+    n = d.numel()
+    dev = d.device
+    if lam is None:
+        lam = torch.empty(n, dtype=torch.float64, device=dev)
+    if Q is None:
+        Q = torch.empty(n, n, dtype=torch.float64, device=dev).t()  # column-major storage
+    if ws is None:
+        ws = workspace(workspace_size(n, opts), dev)
+    ld = Q.stride(1) if n > 0 else 1
+    st = lib().tdc_eig(n, _ptr(d), _ptr(e), _ptr(lam), _ptr(Q), max(ld, 1), _ptr(ws), ws.numel(),
+                       ctypes.byref(opts) if opts else None, _stream(stream))
+    _check("tdc_eig", st)
+    if check:
+        _check("tdc_eig (device status)", sync_status(stream))
+    return lam, Q
+
+
+def batched_workspace_size(sizes, opts: Opts | None = None) -> int:
+    import numpy as np
+    nh = np.ascontiguousarray(sizes, dtype=np.int64)
+    b = ctypes.c_size_t(0)
+    _check("tdc_eig_batched_workspace_size",
+           lib().tdc_eig_batched_workspace_size(len(nh), nh.ctypes.data_as(ctypes.c_void_p),
+                                                ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    return b.value
+
+
+def eig_batched(sizes, d: torch.Tensor, e: torch.Tensor, off_de, off_q, lam: torch.Tensor, Q: torch.Tensor,
+                opts: Opts | None = None, ws: torch.Tensor | None = None, stream=None, check: bool = False):
+    import numpy as np
+    nh = np.ascontiguousarray(sizes, dtype=np.int64)
+    od = np.ascontiguousarray(off_de, dtype=np.int64)
+    oq = np.ascontiguousarray(off_q, dtype=np.int64)
+    if ws is None:
+        ws = workspace(batched_workspace_size(nh, opts), d.device)
+    st = lib().tdc_eig_batched(len(nh), nh.ctypes.data_as(ctypes.c_void_p), od.ctypes.data_as(ctypes.c_void_p),
+                               oq.ctypes.data_as(ctypes.c_void_p), _ptr(d), _ptr(e), _ptr(lam), _ptr(Q), _ptr(ws),
+                               ws.numel(), ctypes.byref(opts) if opts else None, _stream(stream))
+    _check("tdc_eig_batched", st)
+    if check:
+        _check("tdc_eig_batched (device status)", sync_status(stream))
+    return lam, Q
+
+
+def rank_one(D: torch.Tensor, z: torch.Tensor, rho: float, max_iter: int = 64, stream=None, check=False):
+    """Secular roots, Loewner zhat and column normalisers of D + rho z z^T (device FP64)."""
+    K = D.numel()
+    dev = D.device
+    org = torch.empty(K, dtype=torch.int32, device=dev)
+    tau = torch.empty(K, dtype=torch.float64, device=dev)
+    zhat = torch.empty(K, dtype=torch.float64, device=dev)
+    s = torch.empty(K, dtype=torch.float64, device=dev)
+    b = ctypes.c_size_t(0)
+    _check("tdc_rank_one_workspace_size", lib().tdc_rank_one_workspace_size(K, ctypes.byref(b)))
+    ws = workspace(b.value, dev)
+    _check("tdc_rank_one", lib().tdc_rank_one(K, _ptr(D), _ptr(z), float(rho), _ptr(org), _ptr(tau), _ptr(zhat),
+                                              _ptr(s), int(max_iter), _ptr(ws), ws.numel(), _stream(stream)))
+    if check:
+        _check("tdc_rank_one (device status)", sync_status(stream))
+    return org, tau, zhat, s
+
+
+def sync_status(stream=None) -> int:
+    return int(lib().tdc_sync_status(_stream(stream)))
+
+
+def get_stats() -> dict:
+    s = Stats()
+    _check("tdc_get_stats", lib().tdc_get_stats(ctypes.byref(s)))
+    return s.as_dict()
+
+
+def strerror(status: int) -> str:
+    return lib().tdc_strerror(int(status)).decode()

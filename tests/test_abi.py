@@ -1,0 +1,63 @@
+"""The C-ABI library builds, loads without a GPU, exports every entry point that
+include/tdc.h declares, and rejects invalid arguments on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2008_01990_gb300 import build, tdc
+    build.build()
+    return tdc.lib()
+
+
+def declared_functions():
+    hdr = open(os.path.join(ROOT, "include", "tdc.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(tdc_\w+)\s*\(", hdr, flags=re.M)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "tdc_eig" in names and "tdc_eig_batched" in names
+    for nm in names:
+        assert hasattr(lib, nm), nm
+
+
+def test_default_opts_and_workspace(lib):
+    from paper_2008_01990_gb300 import tdc
+    o = tdc.default_opts()
+    assert o.leaf == 32 and o.max_iter >= 1 and o.sign_normalise == 1
+    w1 = tdc.workspace_size(1024, o)
+    w2 = tdc.workspace_size(2048, o)
+    assert 2048 * 2048 * 8 < w2 and w1 < w2
+    assert tdc.workspace_size(0, o) > 0
+
+
+def test_host_argument_checks(lib):
+    from paper_2008_01990_gb300 import tdc
+    P = ctypes.c_void_p
+    bogus = P(0x1000)
+    assert lib.tdc_eig(-1, bogus, bogus, bogus, bogus, 1, bogus, 0, None, None) == -1
+    assert lib.tdc_eig(0, None, None, None, None, 1, None, 0, None, None) == 0
+    assert lib.tdc_eig(4, None, bogus, bogus, bogus, 4, bogus, 1 << 30, None, None) == -2
+    assert lib.tdc_eig(4, bogus, None, bogus, bogus, 4, bogus, 1 << 30, None, None) == -3
+    assert lib.tdc_eig(4, bogus, bogus, None, bogus, 4, bogus, 1 << 30, None, None) == -4
+    assert lib.tdc_eig(4, bogus, bogus, bogus, None, 4, bogus, 1 << 30, None, None) == -5
+    assert lib.tdc_eig(4, bogus, bogus, bogus, bogus, 3, bogus, 1 << 30, None, None) == -6
+    o = tdc.default_opts(leaf=1)
+    assert lib.tdc_eig(4, bogus, bogus, bogus, bogus, 4, bogus, 1 << 30, ctypes.byref(o), None) == -9
+    o = tdc.default_opts()
+    assert lib.tdc_eig(4, bogus, bogus, bogus, bogus, 4, bogus, 16, ctypes.byref(o), None) == tdc.TDC_ENOWS
+    assert lib.tdc_eig(4, bogus, bogus, bogus, bogus, 4, None, 1 << 30, ctypes.byref(o), None) == tdc.TDC_ENOWS
+    import numpy as np
+    nh = np.array([5, -2, 7], dtype=np.int64)
+    assert lib.tdc_eig_batched(3, nh.ctypes.data_as(P), nh.ctypes.data_as(P), nh.ctypes.data_as(P), bogus, bogus,
+                               bogus, bogus, bogus, 1 << 30, None, None) == -1001
+    assert lib.tdc_rank_one(4, bogus, bogus, -1.0, bogus, bogus, bogus, bogus, 8, bogus, 256, None) == -4
+    assert tdc.strerror(tdc.TDC_ENOWS).startswith("workspace")

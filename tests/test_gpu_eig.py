@@ -1,0 +1,206 @@
+"""GPU parity of the divide-and-conquer eigensolver (tdc_eig / tdc_eig_batched /
+tdc_rank_one through the C ABI) against the FP64 CPU oracle.
+
+Tolerances (from the accuracy targets of the method): |lam - lam_oracle| <=
+1e-12 ||T||_2, residual ||TQ - Q Lam||_1 / (n ||T|| eps) <= 50, orthogonality
+||Q^T Q - I||_1 / (n eps) <= 50, eigenvectors equal up to sign (subspaces for
+clusters)."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import EPS, compare_vectors, dense, ratios
+from paper_2008_01990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tdc():
+    from paper_2008_01990_gb300 import build, tdc as t
+    build.build()
+    t.lib()
+    return t
+
+
+DEV = "cuda:0"
+
+
+def run_gpu(tdc, d, e, **kw):
+    o = tdc.default_opts(**kw)
+    lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o, check=True)
+    return lam.cpu().numpy(), Q.cpu().numpy()
+
+
+def check_vs_oracle(orc, d, e, lam, Q, leaf, vec_tol=1e-9):
+    lam_o, Q_o = orc.eig(d, e, leaf=leaf)
+    nT = max(abs(lam_o[0]), abs(lam_o[-1]))
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * nT
+    assert np.all(np.diff(lam) >= 0)
+    if len(d) > 1:
+        res, orth = ratios(d, e, lam, Q)
+        assert res <= 50, res
+        assert orth <= 50, orth
+        compare_vectors(Q, Q_o, lam_o, 1e-8 * nT, vec_tol)
+    im = np.argmax(np.abs(Q), axis=0)
+    assert np.all(Q[im, np.arange(len(d))] > 0)
+    return lam_o, Q_o
+
+
+def test_c1_uniform_1024(tdc, orc):
+    n = 1024
+    d, e = inputs.uniform_tridiag(n, 1)
+    lam, Q = run_gpu(tdc, d, e, leaf=32, collect_stats=1)
+    check_vs_oracle(orc, d, e, lam, Q, 32)
+    st = tdc.get_stats()
+    _, _, sto = orc.eig(d, e, leaf=32, with_stats=True)
+    assert st["levels"] == sto["levels"] == 5
+    # deflation decisions agree level by level (both sides decide in FP64)
+    for a, b in zip(st["sum_K"], sto["sum_K"]):
+        assert abs(a - b) <= max(2, 0.01 * b)
+
+
+@pytest.mark.parametrize("n,leaf", [(1, 32), (2, 2), (3, 2), (5, 2), (9, 2), (31, 32), (33, 32), (64, 64), (65, 64),
+                                    (100, 7), (257, 32), (777, 13), (1000, 64)])
+def test_ragged_sizes(tdc, orc, n, leaf):
+    d, e = inputs.uniform_tridiag(n, 1000 + n)
+    lam, Q = run_gpu(tdc, d, e, leaf=leaf)
+    check_vs_oracle(orc, d, e, lam, Q, leaf)
+
+
+def test_toeplitz_2048_closed_form_and_deflation(tdc, orc):
+    n = 2048
+    d, e = inputs.toeplitz_tridiag(n)
+    lam, Q = run_gpu(tdc, d, e, leaf=64, collect_stats=1)
+    k = np.arange(1, n + 1)
+    ref = np.sort(2.0 + 2.0 * np.cos(k * np.pi / (n + 1)))
+    assert np.max(np.abs(lam - ref)) <= 1e-12 * 4
+    check_vs_oracle(orc, d, e, lam, Q, 64, vec_tol=1e-8)
+    st = tdc.get_stats()
+    assert st["sum_K"][0] == n // 2
+    assert st["type2"][0] == n // 2
+
+
+@pytest.mark.parametrize("fam,n,leaf", [("clement", 501, 16), ("hermite", 300, 32), ("sht", 700, 32),
+                                        ("c4", 1500, 64)])
+def test_families(tdc, orc, fam, n, leaf):
+    d, e = inputs.family(fam, n, 4)
+    lam, Q = run_gpu(tdc, d, e, leaf=leaf)
+    check_vs_oracle(orc, d, e, lam, Q, leaf, vec_tol=1e-7)
+
+
+def test_zero_coupling_deflates_everything(tdc, orc):
+    n = 256
+    d, e = inputs.uniform_tridiag(n, 77)
+    e[n // 2 - 1] = 0.0
+    e[n // 4 - 1] = 0.0
+    lam, Q = run_gpu(tdc, d, e, leaf=16, collect_stats=1)
+    check_vs_oracle(orc, d, e, lam, Q, 16)
+    assert tdc.get_stats()["sum_K"][0] == 0
+
+
+def test_leading_dimension_and_inputs_untouched(tdc, orc):
+    n, ld = 300, 311
+    d, e = inputs.uniform_tridiag(n, 5)
+    dt = torch.tensor(d, device=DEV)
+    et = torch.tensor(e, device=DEV)
+    store = torch.full((n, ld), 7.0, dtype=torch.float64, device=DEV)  # column-major n x n with ld 311
+    Qv = store.t()[:n, :]
+    assert Qv.stride(1) == ld
+    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=32), Q=Qv, check=True)
+    assert torch.equal(dt.cpu(), torch.tensor(d)) and torch.equal(et.cpu(), torch.tensor(e))
+    assert torch.all(store[:, n:] == 7.0)  # padding rows untouched
+    check_vs_oracle(orc, d, e, lam.cpu().numpy(), Q.cpu().numpy(), 32)
+
+
+def test_batched_uneven_sizes(tdc, orc):
+    sizes = np.array([1, 5, 33, 64, 100, 257, 2, 130])
+    d, e, offs = inputs.batched_uniform(sizes, 3)
+    qoffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
+    dt = torch.tensor(d, device=DEV)
+    et = torch.tensor(e, device=DEV)
+    lam = torch.zeros(int(offs[-1]), dtype=torch.float64, device=DEV)
+    Q = torch.zeros(int(qoffs[-1]), dtype=torch.float64, device=DEV)
+    tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, tdc.default_opts(leaf=16), check=True)
+    lam = lam.cpu().numpy()
+    Q = Q.cpu().numpy()
+    for b, nb in enumerate(sizes):
+        lb = lam[offs[b]:offs[b] + nb]
+        Qb = Q[qoffs[b]:qoffs[b] + nb * nb].reshape(nb, nb, order="F")
+        check_vs_oracle(orc, d[offs[b]:offs[b] + nb], e[offs[b]:offs[b] + nb - 1], lb, Qb, 16)
+
+
+def test_rank_one_vs_oracle(tdc, orc):
+    K = 3000
+    g = inputs.SplitMix64(17)
+    D = np.sort(g.uniform(K, -1.0, 1.0))
+    z = g.uniform(K, -1.0, 1.0)
+    z /= np.linalg.norm(z)
+    rho = 0.9
+    org, tau, zh, s = tdc.rank_one(torch.tensor(D, device=DEV), torch.tensor(z, device=DEV), rho, check=True)
+    org = org.cpu().numpy()
+    tau = tau.cpu().numpy()
+    zh = zh.cpu().numpy()
+    s = s.cpu().numpy()
+    org_o, tau_o, lam_o, _ = orc.secular(D, z, rho)
+    lam = D[org] + tau
+    # every root within a few ulps of the pole gap scale; interlacing
+    assert np.all(lam > D) and np.all(lam[:-1] < D[1:])
+    assert np.max(np.abs(lam - lam_o)) <= 64 * EPS * max(1.0, rho)
+    # offsets from the same pole agree to relative accuracy
+    same = org == org_o
+    assert np.mean(same) > 0.99
+    assert np.max(np.abs(tau[same] - tau_o[same]) / np.abs(tau_o[same])) <= 1e-11
+    zh_o = orc.lowner(D, z, rho, org_o, tau_o)
+    assert np.max(np.abs(zh - zh_o) / np.abs(zh_o)) <= 1e-10
+    s_o = orc.colnorm(D, org_o, tau_o, zh_o)
+    assert np.max(np.abs(s - s_o) / s_o) <= 1e-10
+
+
+def test_status_nonconvergence_then_recovery(tdc, orc):
+    n = 512
+    d, e = inputs.uniform_tridiag(n, 9)
+    o = tdc.default_opts(leaf=32, max_iter=1)
+    tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o)
+    assert tdc.sync_status() == tdc.TDC_ENOCONV
+    lam, Q = run_gpu(tdc, d, e, leaf=32)  # the next call is clean
+    check_vs_oracle(orc, d, e, lam, Q, 32)
+
+
+def test_status_nonfinite_input(tdc):
+    n = 100
+    d, e = inputs.uniform_tridiag(n, 9)
+    d[37] = np.nan
+    tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), tdc.default_opts(leaf=16))
+    assert tdc.sync_status() == tdc.TDC_ENONFINITE
+    assert tdc.sync_status() == 0
+
+
+def test_c2_toeplitz_16384_sampled(tdc):
+    """Full-size tridiag(1,2,1) at n=16384 (leaf 64): every eigenvalue against the
+    closed form; residual, orthogonality and sine vectors on sampled columns."""
+    n = 16384
+    d, e = inputs.toeplitz_tridiag(n)
+    dt = torch.tensor(d, device=DEV)
+    et = torch.tensor(e, device=DEV)
+    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=64), check=True)
+    k = torch.arange(1, n + 1, dtype=torch.float64, device=DEV)
+    ref = torch.sort(2.0 + 2.0 * torch.cos(k * np.pi / (n + 1))).values
+    assert torch.max(torch.abs(lam - ref)).item() <= 1e-12 * 4
+    g = np.random.default_rng(0)
+    cols = torch.tensor(np.sort(g.choice(n, 256, replace=False)), device=DEV)
+    Qs = Q[:, cols]
+    Tq = 2.0 * Qs
+    Tq[1:] += Qs[:-1]
+    Tq[:-1] += Qs[1:]
+    res = torch.abs(Tq - Qs * lam[cols]).sum(dim=0).max().item() / (n * 4.0 * EPS)
+    G = Qs.t() @ Q
+    G[torch.arange(256, device=DEV), cols] -= 1.0
+    orth = torch.abs(G).sum(dim=1).max().item() / (n * EPS)
+    assert res <= 50 and orth <= 50, (res, orth)
+    # eigenvalue lam_k (ascending) belongs to index m = n+1-k of 2+2cos(m pi/(n+1))
+    m = (n - cols).to(torch.float64)
+    j = torch.arange(1, n + 1, dtype=torch.float64, device=DEV)[:, None]
+    V = np.sqrt(2.0 / (n + 1)) * torch.sin(j * m[None, :] * np.pi / (n + 1))
+    dots = torch.abs(torch.sum(V * Qs, dim=0))
+    assert torch.max(torch.abs(dots - 1.0)).item() <= 1e-6

@@ -287,7 +287,7 @@ def test_dc_hermite_closed_form(orc):
     assert np.max(np.abs(lam - np.sort(ref))) <= 1e-12 * nT
 
 
-@pytest.mark.parametrize("n,leaf,seed", [(1, 32, 1), (2, 1, 1), (3, 1, 2), (17, 4, 3), (300, 32, 4), (1024, 32, 1)])
+@pytest.mark.parametrize("n,leaf,seed", [(1, 32, 1), (2, 2, 1), (3, 2, 2), (17, 2, 3), (19, 4, 3), (300, 32, 4), (1024, 32, 1)])
 def test_dc_uniform_sturm_and_invariants(orc, n, leaf, seed):
     d, e = inputs.uniform_tridiag(n, seed)
     lam, Q = orc.eig(d, e, leaf=leaf)
