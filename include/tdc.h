@@ -48,6 +48,7 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
 #define TDC_ETIMEOUT (-104)    /* a bounded device-side wait expired (device status) */
 #define TDC_ECUDA (-105)       /* a CUDA runtime call failed */
 #define TDC_EUNSUPPORTED (-106) /* option combination not supported */
+#define TDC_ETOOLARGE (-107)   /* problem needs more than the fixed scratch of tdc_eig_noalloc */
 
 /* merge modes: how the eigenvector update Q * U is computed */
 #define TDC_MERGE_AUTO 0        /* library choice (structured above structured_min_K) */
@@ -120,6 +121,27 @@ int tdc_eig_batched_workspace_size(int32_t batch, const int64_t* n_host, const t
  * TDC_ENOWS, -11 invalid options, -1000-b when problem b has n_b < 0. */
 int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_host, const int64_t* off_q_host,
                     const double* d, const double* e, double* lam, double* Q, void* ws, size_t ws_bytes,
+                    const tdc_opts* o, tdc_stream_t stream);
+
+/* tdc_eig for callers that cannot allocate device memory.  The paper has no
+ * counterpart: this is a deployment convenience.  Some callers cannot call
+ * cudaMalloc -- code in a process whose device memory is already fully reserved
+ * by another allocator, plugins that must not touch the allocator, and
+ * latency-critical paths where an allocation may block or fail -- so they cannot
+ * provide tdc_eig's workspace.  This entry point takes the same arguments as
+ * tdc_eig minus the workspace and uses instead a fixed 24 MiB array in the
+ * library's own device memory (a file-scope __device__ array that every GPU which
+ * loads the library holds until the process exits).  That covers orders up to
+ * about n = 1750 (whatever tdc_workspace_size(n, o) fits in 24 MiB); larger n
+ * returns TDC_ETOOLARGE before anything is enqueued.  The first call on each
+ * device looks the array's device address up (cudaGetSymbolAddress, with that
+ * device current), so make that first call before any stream capture.  All
+ * calls share the one array and it keeps the last call's contents (nothing in it
+ * has to start at zero): calls that overlap on the GPU race on it and must be
+ * ordered by the caller.  Allocates nothing; collect_stats is ignored.
+ * Errors: as tdc_eig (-1 n < 0, -2..-6 arguments, -7 invalid options),
+ * TDC_ETOOLARGE, TDC_ECUDA. */
+int tdc_eig_noalloc(int64_t n, const double* d, const double* e, double* lam, double* Q, int64_t ldq,
                     const tdc_opts* o, tdc_stream_t stream);
 
 /* Rank-one eigenproblem D + rho z z^T (one merge's secular stage on its own):

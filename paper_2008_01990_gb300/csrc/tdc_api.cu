@@ -458,6 +458,7 @@ const char* tdc_strerror(int status) {
     case TDC_ETIMEOUT: return "bounded device-side wait expired";
     case TDC_ECUDA: return "CUDA runtime error";
     case TDC_EUNSUPPORTED: return "unsupported option combination";
+    case TDC_ETOOLARGE: return "problem larger than the fixed scratch of tdc_eig_noalloc";
     default: return status < 0 ? "invalid argument" : "unknown status";
   }
 }

@@ -22,6 +22,7 @@ TDC_ENOCONV = -103
 TDC_ETIMEOUT = -104
 TDC_ECUDA = -105
 TDC_EUNSUPPORTED = -106
+TDC_ETOOLARGE = -107
 
 MERGE_AUTO = 0
 MERGE_DENSE = 1
@@ -113,6 +114,8 @@ def lib():
         L.tdc_eig_backward.argtypes = [i64, P, P, i64, P, P, P, P, P, sz, P]
         L.tdc_backward_batched_workspace_size.argtypes = [i32, i64, ctypes.POINTER(sz)]
         L.tdc_eig_backward_batched.argtypes = [i32, i64, P, P, P, P, P, P, P, sz, P]
+    if hasattr(L, "tdc_eig_noalloc"):
+        L.tdc_eig_noalloc.argtypes = [i64, P, P, P, P, i64, ctypes.POINTER(Opts), P]
     if hasattr(L, "tdc_rank_one"):
         L.tdc_rank_one_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
         L.tdc_rank_one.argtypes = [i64, P, P, ctypes.c_double, P, P, P, P, i32, P, sz, P]
