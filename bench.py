@@ -113,6 +113,9 @@ def workload(name: str):
     if name == "toeplitz16384":
         d, e = inputs.toeplitz_tridiag(16384)
         return d, e, 64, "tridiag(1,2,1) n=16384 leaf 64"
+    if name == "toeplitz4096":
+        d, e = inputs.toeplitz_tridiag(4096)
+        return d, e, 64, "tridiag(1,2,1) n=4096 leaf 64"
     if name == "uniform1024":
         d, e = inputs.uniform_tridiag(1024, 1)
         return d, e, 32, "uniform(-1,1) n=1024 leaf 32 seed 1"
@@ -134,7 +137,7 @@ def cpu_baseline(wl: str, budget_s: float = 20.0):
     d_full, e_full, leaf, desc = workload(wl)
     n_full = d_full.size
     n = min(n_full, 2048)
-    fam = {"toeplitz16384": "toeplitz", "uniform1024": "uniform", "c4_32768": "c4"}[wl]
+    fam = {"toeplitz16384": "toeplitz", "toeplitz4096": "toeplitz", "uniform1024": "uniform", "c4_32768": "c4"}[wl]
     while True:
         d, e = inputs.family(fam, n, 4 if fam == "c4" else 1)
         t0 = time.perf_counter()
@@ -249,9 +252,43 @@ def run_ours(args):
         tdc.eig(d, e, opts_st, ws=wsb, lam=lam, Q=Q, stream=stream)
         phases.append(tdc.get_stats())
     stats = phases[-1]
-    gemm_ms = float(np.median([p["phase_ms"]["gemm"] for p in phases]))
-    flops = float(sum(stats["gemm_flops"]))
-    achieved = flops / (gemm_ms * 1e-3) / 1e12
+    S = opts.split_slices
+    products = S * (S + 1) // 2
+    split_ms = float(np.median([p["phase_ms"]["split_mma"] for p in phases]))
+    digits_ms = float(np.median([p["phase_ms"]["split_digits"] for p in phases]))
+    dense_ms = float(np.median([p["phase_ms"]["gemm_fp64"] for p in phases]))
+    split_flops = float(stats["split_flops"])
+    dense_flops = float(sum(stats["gemm_flops"])) - split_flops
+    pk, pk_kind = peaks()
+    if split_flops > 0 and split_ms > 0:
+        achieved = split_flops * products / (split_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "k_gemm_split (BF16 digit products, tcgen05, TMEM FP32 levels)",
+                "achieved": achieved, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
+                "frac": achieved / pk["bf16_tflops_sustained"], "traffic": None,
+                "peak_kind": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % pk_kind,
+                "fp64_equivalent_tflops": split_flops / (split_ms * 1e-3) / 1e12,
+                "bf16_products_per_fp64_product": products}
+        qu_tflops = (split_flops + dense_flops) / ((split_ms + digits_ms + dense_ms) * 1e-3) / 1e12
+    else:
+        achieved = dense_flops / (dense_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_gemm_dense (FP64 Q*U with generated U)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
+        qu_tflops = achieved
+    # the plain dense FP64 merge on the same input, for the structured/split comparison
+    compare = {args.merge: ms / 1e3}
+    if args.merge != "dense" and not args.no_compare:
+        od = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_DENSE)
+        tdc.eig(d, e, od, ws=wsb, lam=lam, Q=Q, stream=stream)
+        c0 = torch.cuda.Event(enable_timing=True)
+        c1 = torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        tdc.eig(d, e, od, ws=wsb, lam=lam, Q=Q, stream=stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        compare["dense"] = c0.elapsed_time(c1) / 1e3
+        tdc.eig(d, e, opts, ws=wsb, lam=lam, Q=Q, stream=stream)  # leave the timed configuration's result
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     d_h = torch.tensor(d_np).pin_memory()
     e_h = torch.tensor(e_np).pin_memory()
@@ -276,7 +313,7 @@ def run_ours(args):
     # accuracy of the timed configuration (outside the timed region)
     res, orth, nT = sampled_ratios(lam, Q, d, e)
     lam_err = None
-    if args.workload == "toeplitz16384":
+    if args.workload.startswith("toeplitz"):
         k = torch.arange(1, n + 1, dtype=torch.float64, device=dev)
         ref = torch.sort(2.0 + 2.0 * torch.cos(k * np.pi / (n + 1))).values
         lam_err = torch.max(torch.abs(lam - ref)).item() / 4.0
@@ -284,7 +321,6 @@ def run_ours(args):
         if ws_n > 1:
             dist.destroy_process_group()
         return 0
-    pk, pk_kind = peaks()
     line = {
         "metric": METRIC,
         "value": ms / 1e3 / ws_n,
@@ -296,16 +332,13 @@ def run_ours(args):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64",
+        "dtype": "f64" if args.merge == "dense" else "f64 (Q*U as bf16 digit products, fp32 accumulate)",
         "data": "synthetic",
         "config": {"workload": desc, "merge": args.merge, "l2": "no flush: Q and workspace (4 GiB) exceed L2",
                    "parallelism": "replicas" if ws_n > 1 else "single"},
-        "roofline": {"bound": "alu", "kernel": "k_gemm_dense (FP64 Q*U with generated U)",
-                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"},
-        "qu_tflops": achieved,
-        "gemm_ms": gemm_ms,
+        "roofline": roof,
+        "qu_tflops_fp64_equivalent": qu_tflops,
+        "merge_compare_s": compare,
         "phase_ms": stats["phase_ms"],
         "K_per_level": stats["sum_K"],
         "test_ratios": {"lam_err_over_normT": lam_err, "residual": res, "orthogonality": orth,
@@ -329,8 +362,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "uniform1024", "c4_32768"])
-    ap.add_argument("--merge", default="dense", choices=["dense", "auto", "structured", "split"])
+    ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768"])
+    ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
+    ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

@@ -62,7 +62,8 @@ typedef struct {
   int32_t structured_min_K; /* AUTO: merges with K >= this use the structured path */
   int32_t lr_tile;          /* tile size m of the structured path (multiple of 64) */
   double lr_tol;            /* SRRSC stopping tolerance, relative to the tile's largest entry */
-  int32_t split_slices;     /* BF16 slices per operand on the split path (3..8) */
+  int32_t split_slices;     /* base-256 BF16 digits per operand on the split path (3..7) */
+  int32_t split_min_K;      /* SPLIT/AUTO: merges with K >= this use the split path, smaller ones FP64 */
   int32_t max_iter;         /* secular iteration cap per root (>= 1) */
   int32_t sign_normalise;   /* 1: make the largest-magnitude entry of every column positive */
   int32_t collect_stats;    /* 1: record per-level statistics for tdc_get_stats (adds a sync) */
@@ -81,13 +82,18 @@ typedef struct {
   int64_t n_type1[TDC_MAX_LEVELS];       /* type-1 (small z) deflations */
   int64_t secular_iter_max;
   double secular_iter_mean;
-  float phase_ms[8];                     /* leaf, prepare, secular, zhat+norms+order, gemm, copy, other, total */
+  /* CUDA-event times on the call's stream: 0 leaf, 1 prepare+rotate, 2 secular,
+   * 3 zhat+norms+order, 4 FP64 GEMM, 5 split digit images, 6 split tensor-core GEMM,
+   * 7 deflated copies, 8 output, 9 total */
+  float phase_ms[12];
   double gemm_flops[TDC_MAX_LEVELS];     /* algorithmic flops of the Q*U products (2 per multiply-add) */
+  double split_flops;                    /* part of gemm_flops computed on the split path */
   int64_t launches;                      /* kernel launches of the call */
 } tdc_stats;
 
 /* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,
- * lr_tol 1e-15, split_slices 7, max_iter 64, sign_normalise 1, collect_stats 0). */
+ * lr_tol 1e-15, split_slices 7, split_min_K 256, max_iter 64, sign_normalise 1,
+ * collect_stats 0, spin_budget 2^24). */
 void tdc_default_opts(tdc_opts* o);
 
 /* Workspace bytes tdc_eig needs for order n (o may be NULL = defaults).
@@ -132,8 +138,10 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
  * tdc_eig minus the workspace and uses instead a fixed 24 MiB array in the
  * library's own device memory (a file-scope __device__ array that every GPU which
  * loads the library holds until the process exits).  That covers orders up to
- * about n = 1750 (whatever tdc_workspace_size(n, o) fits in 24 MiB); larger n
- * returns TDC_ETOOLARGE before anything is enqueued.  The first call on each
+ * about n = 1750 with the FP64 merge (whatever tdc_workspace_size(n, o) fits in
+ * 24 MiB); with merge_mode AUTO the FP64 merge is used whenever the split path's
+ * digit images would not fit, and larger n returns TDC_ETOOLARGE before
+ * anything is enqueued.  The first call on each
  * device looks the array's device address up (cudaGetSymbolAddress, with that
  * device current), so make that first call before any stream capture.  All
  * calls share the one array and it keeps the last call's contents (nothing in it
@@ -152,6 +160,19 @@ int tdc_eig_noalloc(int64_t n, const double* d, const double* e, double* lam, do
 int tdc_rank_one_workspace_size(int64_t K, size_t* bytes);
 int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_t* org, double* tau,
                  double* zhat, double* s, int32_t max_iter, void* ws, size_t ws_bytes, tdc_stream_t stream);
+
+/* Structured product C = A * Qhat with Qhat the K x K Cauchy-like matrix
+ * Qhat_ij = zhat_i s_j / ((D_i - D_org_j) - tau_j) given by its generators
+ * (Eq. (Q_Cauchy) with Eq. (d-lambda)); A is m x K (lda), C is m x K (ldc).
+ * mode: TDC_MERGE_DENSE (FP64) or TDC_MERGE_SPLIT (base-256 BF16 digit products
+ * on the tensor cores; requires |A_ij| <= 1, which holds for the orthogonal
+ * factors the merge multiplies, and uses o->split_slices digits);
+ * TDC_MERGE_STRUCTURED returns TDC_EUNSUPPORTED here.
+ * ws of tdc_cauchy_gemm_workspace_size(m, K, mode, o) bytes. */
+int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc_opts* o, size_t* bytes);
+int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const double* D, const int32_t* org,
+                    const double* tau, const double* zhat, const double* s, double* C, int64_t ldc, int32_t mode,
+                    const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream);
 
 /* Synchronise `stream` and return the device status word of the last call on
  * it (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE), then clear it. */

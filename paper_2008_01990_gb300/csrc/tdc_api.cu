@@ -55,7 +55,31 @@ struct HostPlan {
   std::vector<LevelLaunch> levels;  // index l
   int64_t Mmax = 1;
   std::vector<int64_t> max_tiles;   // GEMM tile upper bound per level
+  int64_t img_elems = 0;            // digit images of the split path (bf16 elements)
+  int split_S = 0;                  // 0: split path off
 };
+
+// the split path is used for merge_mode SPLIT and AUTO
+static bool split_enabled(const tdc_opts& o) {
+  return o.merge_mode == TDC_MERGE_SPLIT || o.merge_mode == TDC_MERGE_AUTO;
+}
+
+static void plan_split(HostPlan& H, const tdc_opts& o) {
+  H.img_elems = 0;
+  H.split_S = split_enabled(o) ? o.split_slices : 0;
+  if (!H.split_S) return;
+  for (int l = 0; l < H.T; ++l) {
+    int64_t tot = 0;
+    for (auto& p : H.prob) {
+      if (p.depth <= l) break;
+      const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;  // largest node of the level
+      if (nm < o.split_min_K) continue;                          // K <= nm < split_min_K
+      const int64_t n1 = (nm + 1) / 2;
+      tot += (((int64_t)1) << l) * split_img_elems(n1, n1, nm, nm, H.split_S);
+    }
+    H.img_elems = std::max(H.img_elems, tot);
+  }
+}
 
 static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const int64_t* off_de,
                        const int64_t* off_q, const int64_t* ld0, int leaf) {
@@ -119,7 +143,7 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
 
 // workspace carving
 struct Layout {
-  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, q1, total;
+  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, q1, total;
 };
 
 static constexpr int kVecD = 17;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey)
@@ -136,6 +160,8 @@ static Layout layout_of(const HostPlan& H) {
   L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
   L.tiles = o; o = align_up(o + sizeof(int64_t) * (size_t)(H.Mmax + 1));
   L.stats = o; o = align_up(o + sizeof(Stats));
+  L.segs = o; o = align_up(o + (H.split_S ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
+  L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
   L.q1 = o; o = align_up(o + sizeof(double) * (size_t)H.Q1);
   L.total = o + 256;  // slack for aligning an unaligned base
   return L;
@@ -164,6 +190,9 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   P.m.tiles = (int64_t*)(base + L.tiles);
   P.Q1 = (double*)(base + L.q1);
   P.prob = (const Problem*)(base + L.prob);
+  P.segs = H.split_S ? (GemmSeg*)(base + L.segs) : nullptr;
+  P.img = (__nv_bfloat16*)(base + L.img);
+  P.img_cap = H.img_elems;
 }
 
 // Problem table upload through kernel parameters (capture-safe: the values
@@ -195,7 +224,9 @@ static int validate_opts(const tdc_opts* o) {
   if (o->merge_mode < 0 || o->merge_mode > 3) return 1;
   if (o->max_iter < 1) return 1;
   if (o->lr_tile < 64 || (o->lr_tile % 64) != 0) return 1;
-  if (o->split_slices < 3 || o->split_slices > 8) return 1;
+  if (o->split_slices < 3 || o->split_slices > 7) return 1;
+  if (o->split_min_K < 1) return 1;
+  if (o->spin_budget < 1) return 1;
   if (!(o->lr_tol > 0.0)) return 1;
   return 0;
 }
@@ -216,79 +247,91 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   P.e = e;
   P.lam_out = lam;
   P.max_iter = o.max_iter;
+  P.split_min_K = H.split_S ? o.split_min_K : 0;
+  P.split_slices = H.split_S ? H.split_S : 7;
+  P.spin_budget = o.spin_budget;
   P.status = status_ptr();
   if (!P.status) return TDC_ECUDA;
   P.stats = o.collect_stats ? (Stats*)(base + L.stats) : nullptr;
   if (H.N == 0) return TDC_OK;
   cudaError_t err = upload_problems(H, (Problem*)P.prob, s);
   if (err == cudaSuccess && P.stats) err = cudaMemsetAsync(P.stats, 0, sizeof(Stats), s);
-  cudaEvent_t ev[16];
-  int nev = 0;
+  // Phase timing (statistics only): events recorded on the call's stream.
   const bool timing = o.collect_stats != 0;
-  auto mark = [&]() {
-    if (timing && nev < 16) {
-      cudaEventCreate(&ev[nev]);
-      cudaEventRecord(ev[nev], s);
-      ++nev;
-    }
+  std::vector<cudaEvent_t> evs;
+  std::vector<std::pair<int, std::pair<size_t, size_t>>> spans;  // (phase, (from, to))
+  auto mark = [&]() -> size_t {
+    if (!timing) return 0;
+    cudaEvent_t ev;
+    cudaEventCreate(&ev);
+    cudaEventRecord(ev, s);
+    evs.push_back(ev);
+    return evs.size() - 1;
   };
-  float phase[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  auto span = [&](int phase, size_t a0, size_t a1) {
+    if (timing) spans.push_back({phase, {a0, a1}});
+  };
   // kernel launches: problem upload, corner modification, leaves, 9 per level, output
-  const int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
-  std::vector<cudaEvent_t> lev;
-  mark();  // 0
+  int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
+  for (int l = 0; l < H.T; ++l)
+    if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4;
+  const size_t t0 = mark();
   if (err == cudaSuccess) err = launch_dmod(P, s);
   if (err == cudaSuccess) err = launch_leaves(P, H.nleaves, H.max_leaf, s);
-  mark();  // 1
-  // per-phase event pairs per level (only when timing)
-  std::vector<std::array<cudaEvent_t, 6>> lv;
+  span(0, t0, mark());
   for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
     const LevelLaunch& LL = H.levels[l];
-    std::array<cudaEvent_t, 6> es{};
-    auto rec = [&](int k) {
-      if (timing) { cudaEventCreate(&es[k]); cudaEventRecord(es[k], s); }
-    };
-    rec(0);
+    const size_t a0 = mark();
     err = launch_prepare(P, LL, s);
     if (err == cudaSuccess) err = launch_rotate(P, LL, s);
-    rec(1);
+    const size_t a1 = mark();
     if (err == cudaSuccess) err = launch_secular(P, LL, s);
-    rec(2);
+    const size_t a2 = mark();
     if (err == cudaSuccess) err = launch_lowner(P, LL, s);
     if (err == cudaSuccess) err = launch_finalize(P, LL, kDenseBM, kDenseBN, s);
-    rec(3);
+    const size_t a3 = mark();
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
-    rec(4);
+    const size_t a4 = mark();
+    span(1, a0, a1);
+    span(2, a1, a2);
+    span(3, a2, a3);
+    span(4, a3, a4);
+    size_t a6 = a4;
+    if (err == cudaSuccess && P.split_min_K > 0 && LL.max_n >= P.split_min_K) {
+      cudaEvent_t mid = nullptr;
+      if (timing) {
+        cudaEventCreate(&mid);
+        evs.push_back(mid);
+      }
+      const size_t a5 = timing ? evs.size() - 1 : 0;
+      err = launch_gemm_split(P, LL, s, mid);
+      a6 = mark();
+      span(5, a4, a5);
+      span(6, a5, a6);
+    }
     if (err == cudaSuccess) err = launch_copy_deflated(P, LL, s);
-    rec(5);
-    if (timing) lv.push_back(es);
+    span(7, a6, mark());
   }
-  mark();  // 2
+  const size_t t8 = mark();
   if (err == cudaSuccess) err = launch_sign_and_output(P, o.sign_normalise, s);
-  mark();  // 3
+  const size_t t9 = mark();
+  span(8, t8, t9);
+  span(9, t0, t9);
   if (err != cudaSuccess) {
-    for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
-    for (auto& es : lv) for (auto e2 : es) if (e2) cudaEventDestroy(e2);
+    for (auto e2 : evs) cudaEventDestroy(e2);
     return TDC_ECUDA;
   }
   if (P.stats) {
     Stats hs;
     cudaMemcpyAsync(&hs, P.stats, sizeof(Stats), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TDC_ECUDA;
-    if (nev >= 4) {
-      cudaEventElapsedTime(&phase[0], ev[0], ev[1]);
-      cudaEventElapsedTime(&phase[7], ev[0], ev[3]);
-      float other = 0;
-      cudaEventElapsedTime(&other, ev[2], ev[3]);
-      phase[6] += other;
+    if (cudaStreamSynchronize(s) != cudaSuccess) {
+      for (auto e2 : evs) cudaEventDestroy(e2);
+      return TDC_ECUDA;
     }
-    for (auto& es : lv) {
-      float t;
-      cudaEventElapsedTime(&t, es[0], es[1]); phase[1] += t;
-      cudaEventElapsedTime(&t, es[1], es[2]); phase[2] += t;
-      cudaEventElapsedTime(&t, es[2], es[3]); phase[3] += t;
-      cudaEventElapsedTime(&t, es[3], es[4]); phase[4] += t;
-      cudaEventElapsedTime(&t, es[4], es[5]); phase[5] += t;
+    float phase[12] = {0};
+    for (auto& sp : spans) {
+      float t = 0;
+      if (cudaEventElapsedTime(&t, evs[sp.second.first], evs[sp.second.second]) == cudaSuccess) phase[sp.first] += t;
     }
     std::lock_guard<std::mutex> lk(g_mu);
     memset(&g_last_stats, 0, sizeof(g_last_stats));
@@ -302,13 +345,13 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       g_last_stats.n_type1[l] = (int64_t)hs.n_type1[l];
       g_last_stats.gemm_flops[l] = (double)hs.gemm_flops[l];
     }
+    g_last_stats.split_flops = (double)hs.split_flops;
     g_last_stats.launches = launches;
     g_last_stats.secular_iter_max = hs.iter_max;
     g_last_stats.secular_iter_mean = hs.iter_roots ? (double)hs.iter_sum / (double)hs.iter_roots : 0.0;
-    for (int i = 0; i < 8; ++i) g_last_stats.phase_ms[i] = phase[i];
+    for (int i = 0; i < 12; ++i) g_last_stats.phase_ms[i] = phase[i];
   }
-  for (int i = 0; i < nev; ++i) cudaEventDestroy(ev[i]);
-  for (auto& es : lv) for (auto e2 : es) if (e2) cudaEventDestroy(e2);
+  for (auto e2 : evs) cudaEventDestroy(e2);
   return TDC_OK;
 }
 
@@ -327,10 +370,11 @@ void tdc_default_opts(tdc_opts* o) {
   o->lr_tile = 512;
   o->lr_tol = 1e-15;
   o->split_slices = 7;
+  o->split_min_K = 256;
   o->max_iter = 64;
   o->sign_normalise = 1;
   o->collect_stats = 0;
-  o->spin_budget = 1 << 26;
+  o->spin_budget = 1 << 24;
 }
 
 int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
@@ -342,6 +386,7 @@ int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
   if (!bytes) return -3;
   HostPlan H;
   build_plan(H, 1, &n, nullptr, nullptr, nullptr, d.leaf);
+  plan_split(H, d);
   *bytes = layout_of(H).total;
   return TDC_OK;
 }
@@ -362,6 +407,7 @@ int tdc_eig(int64_t n, const double* d, const double* e, double* lam, double* Q,
   HostPlan H;
   int64_t off = 0, ld = ldq;
   build_plan(H, 1, &n, &off, &off, &ld, op.leaf);
+  plan_split(H, op);
   return run_plan(H, op, d, e, lam, Q, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -377,6 +423,7 @@ int tdc_eig_batched_workspace_size(int32_t batch, const int64_t* n_host, const t
     if (n_host[b] < 0) return -1000 - b;
   HostPlan H;
   build_plan(H, batch, n_host, nullptr, nullptr, nullptr, d.leaf);
+  plan_split(H, d);
   *bytes = layout_of(H).total;
   return TDC_OK;
 }
@@ -401,6 +448,7 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
     if (n_host[b] < 0) return -1000 - b;
   HostPlan H;
   build_plan(H, batch, n_host, off_de_host, off_q_host, nullptr, op.leaf);
+  plan_split(H, op);
   return run_plan(H, op, d, e, lam, Q, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -429,6 +477,94 @@ int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_
   if (!st) return TDC_ECUDA;
   cudaError_t e = launch_rank_one(D, z, K, rho, max_iter, org, tau, zhat, s, st, (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+static int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+static int64_t cauchy_split_elems(int64_t m, int64_t K, int S, int64_t* a_elems) {
+  const int64_t KB = cdiv64(K, kSplitBK);
+  const int64_t a = cdiv64(m, kSplitBM) * KB * S * kSplitBM * kSplitBK;
+  const int64_t b = cdiv64(K, kSplitBN) * KB * S * kSplitBN * kSplitBK;
+  if (a_elems) *a_elems = a;
+  return a + b;
+}
+
+__global__ void k_write_segs(GemmSeg s0, GemmSeg s1, GemmSeg* dst) {
+  if (threadIdx.x == 0) { dst[0] = s0; dst[1] = s1; }
+}
+
+int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc_opts* o, size_t* bytes) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0) return -1;
+  if (K < 0) return -2;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -3;
+  if (validate_opts(&op)) return -4;
+  if (!bytes) return -5;
+  if (mode == TDC_MERGE_DENSE) {
+    *bytes = 256;
+    return TDC_OK;
+  }
+  *bytes = 256 + align_up(2 * sizeof(GemmSeg)) + sizeof(__nv_bfloat16) * (size_t)cauchy_split_elems(m, K, op.split_slices, nullptr);
+  return TDC_OK;
+}
+
+int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const double* D, const int32_t* org,
+                    const double* tau, const double* zhat, const double* s, double* C, int64_t ldc, int32_t mode,
+                    const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0 || m > 0x7fffffff) return -1;
+  if (K < 0 || K > 0x7fffffff) return -2;
+  if (m == 0 || K == 0) return TDC_OK;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (!D) return -5;
+  if (!org) return -6;
+  if (!tau) return -7;
+  if (!zhat) return -8;
+  if (!s) return -9;
+  if (!C) return -10;
+  if (ldc < m) return -11;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return mode == TDC_MERGE_STRUCTURED ? TDC_EUNSUPPORTED : -12;
+  if (validate_opts(&op)) return -13;
+  size_t need = 0;
+  tdc_cauchy_gemm_workspace_size(m, K, mode, &op, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  int* st = status_ptr();
+  if (!st) return TDC_ECUDA;
+  GemmSeg sg;
+  memset(&sg, 0, sizeof(sg));
+  sg.A = A; sg.lda = lda; sg.rows = (int32_t)m; sg.kk = (int32_t)K; sg.K = (int32_t)K;
+  sg.D = D; sg.org = org; sg.tau = tau; sg.zhat = zhat; sg.scol = s;
+  sg.C = C; sg.ldc = ldc;
+  cudaStream_t cs = (cudaStream_t)stream;
+  cudaError_t err;
+  if (mode == TDC_MERGE_DENSE) {
+    err = launch_seg_dense(sg, cs);
+  } else {
+    const int S = op.split_slices;
+    int64_t a_el = 0;
+    const int64_t tot = cauchy_split_elems(m, K, S, &a_el);
+    char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    GemmSeg* segs = (GemmSeg*)base;
+    __nv_bfloat16* img = (__nv_bfloat16*)(base + align_up(2 * sizeof(GemmSeg)));
+    const int64_t RT = cdiv64(m, kSplitBM), KB = cdiv64(K, kSplitBK), CT = cdiv64(K, kSplitBN);
+    sg.a_img = 0;
+    sg.b_img = a_el;
+    GemmSeg last;
+    memset(&last, 0, sizeof(last));
+    last.it_a = RT * KB;
+    last.it_b = CT * KB;
+    last.it_t = RT * CT;
+    last.a_img = tot;
+    k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, cs);
+  }
+  return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
 int tdc_sync_status(tdc_stream_t stream) {

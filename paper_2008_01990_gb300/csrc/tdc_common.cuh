@@ -1,6 +1,7 @@
 // tdc_common.cuh -- device-side plan structures and helpers shared by the
 // CUDA translation units of libtdc (never by the CPU oracle).
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -76,9 +77,34 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   unsigned long long n_merges[TDC_MAX_LEVELS];
   int max_K[TDC_MAX_LEVELS];
   unsigned long long gemm_flops[TDC_MAX_LEVELS];
+  unsigned long long split_flops;
   unsigned long long iter_sum;
   unsigned long long iter_roots;
   int iter_max;
+};
+
+// One GEMM segment C(rows x K) = A(rows x kk) * Qhat(list, :) of the merge
+// update: list position q names pole p = plist[q] (identity when NULL), whose
+// column of A is acol[p] (identity when NULL); Qhat_pj = zhat_p scol_j /
+// ((D_p - D_org(j)) - tau_j); output column of root j is cpos[j] (identity when
+// NULL).  a_img / b_img / it_* place the segment in the split path's digit
+// images and work lists.
+struct GemmSeg {
+  const double* A;
+  int64_t lda;
+  const int32_t* acol;
+  const int32_t* plist;
+  int32_t rows, kk, K, pad;
+  const double* D;
+  const int32_t* org;
+  const double* tau;
+  const double* zhat;
+  const double* scol;
+  double* C;
+  int64_t ldc;
+  const int32_t* cpos;
+  int64_t a_img, b_img;    // element offsets (bf16) of the digit images
+  int64_t it_a, it_b, it_t;  // first item in the digit-A, digit-B and tile work lists
 };
 
 struct Plan {
@@ -96,6 +122,12 @@ struct Plan {
   Stats* stats;         // NULL when statistics are off
   int* status;          // device status word
   int32_t max_iter;
+  int32_t split_min_K;  // merges with K >= this use the split path (0: never)
+  int32_t split_slices; // BF16 digit slices per operand
+  GemmSeg* segs;        // 2 M + 1 segments of the current level (split path)
+  __nv_bfloat16* img;   // digit images (split path)
+  int64_t img_cap;      // capacity of img in elements
+  long long spin_budget;
 };
 
 // A merge (node) of level l: node i of problem p splits at mid.
@@ -216,5 +248,11 @@ cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
                             double* tau, double* zhat, double* s, int* status, cudaStream_t st);
 cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s);
+cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, cudaStream_t s, cudaEvent_t mid);
+cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
+                             __nv_bfloat16* img, cudaStream_t s);
+cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
+int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
+constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 32;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
 }  // namespace tdc

@@ -132,6 +132,91 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
   }
 }
 
+// The same FP64 product for one stand-alone segment (tdc_cauchy_gemm).
+__global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
+  __shared__ double As[BK][BM];
+  __shared__ double Us[BK][BN];
+  __shared__ double sDo[BN], sTau[BN], sS[BN];
+  __shared__ int sCol[BK];
+  __shared__ double sDq[BK], sZq[BK];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int rtiles = (sg.rows + BM - 1) / BM, ctiles = (sg.K + BN - 1) / BN;
+  for (int64_t w = blockIdx.x; w < (int64_t)rtiles * ctiles; w += gridDim.x) {
+    const int r0 = (int)(w / ctiles) * BM, j0 = (int)(w % ctiles) * BN;
+    __syncthreads();
+    if (tid < BN) {
+      const int j = j0 + tid;
+      if (j < sg.K) { sDo[tid] = sg.D[sg.org[j]]; sTau[tid] = sg.tau[j]; sS[tid] = sg.scol[j]; }
+      else { sDo[tid] = 0.0; sTau[tid] = 1.0; sS[tid] = 0.0; }
+    }
+    double acc[8][4];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
+    for (int k0 = 0; k0 < sg.kk; k0 += BK) {
+      __syncthreads();
+      if (tid < BK) {
+        const int k = k0 + tid;
+        if (k < sg.kk) {
+          const int p = sg.plist ? sg.plist[k] : k;
+          sCol[tid] = sg.acol ? sg.acol[p] : p;
+          sDq[tid] = sg.D[p];
+          sZq[tid] = sg.zhat[p];
+        } else {
+          sCol[tid] = -1; sDq[tid] = 0.0; sZq[tid] = 0.0;
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < (BK * BM) / kThreads; ++e) {
+        const int idx = tid + e * kThreads;
+        const int k = idx / BM, r = idx % BM;
+        const int col = sCol[k], row = r0 + r;
+        As[k][r] = (col >= 0 && row < sg.rows) ? sg.A[row + (int64_t)col * sg.lda] : 0.0;
+      }
+#pragma unroll
+      for (int e = 0; e < (BK * BN) / kThreads; ++e) {
+        const int idx = tid + e * kThreads;
+        const int k = idx / BN, c = idx % BN;
+        Us[k][c] = (sZq[k] * sS[c]) * rcp_nr((sDq[k] - sDo[c]) - sTau[c]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < BK; ++k) {
+        double av[8], bv[4];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) av[i] = As[k][ty * 8 + i];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) bv[c] = Us[k][tx * 4 + c];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[i][c] = fma(av[i], bv[c], acc[i][c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx * 4 + c;
+      if (j >= sg.K) continue;
+      const int pos = sg.cpos ? sg.cpos[j] : j;
+      double* out = sg.C + (int64_t)pos * sg.ldc;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int row = r0 + ty * 8 + i;
+        if (row < sg.rows) out[row] = acc[i][c];
+      }
+    }
+  }
+}
+
+cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s) {
+  const int64_t tiles = (int64_t)((seg.rows + BM - 1) / BM) * ((seg.K + BN - 1) / BN);
+  if (tiles == 0) return cudaSuccess;
+  k_gemm_dense_seg<<<(unsigned)(tiles < 152 * 8 ? tiles : 152 * 8), kThreads, 0, s>>>(seg);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s) {
   if (max_tiles <= 0) return cudaSuccess;
   int64_t grid = max_tiles;

@@ -1,0 +1,410 @@
+// tdc_gemm_split.cu -- split-precision eigenvector update C = A * Qhat on the
+// BF16 tensor cores (tcgen05, FP32 accumulators in TMEM), FP64 result.
+//
+// Both operands are written as fixed-point numbers with scale 1 (every entry of
+// an orthogonal matrix and of the orthonormal Cauchy-like Qhat has |x| <= 1) and
+// cut into S balanced base-256 digits:  x = sum_s 2^(-8(s+1)) a_s with integer
+// digits |a_0| <= 256 and a_s in [-128, 127] (x 2^56 rounded to an integer),
+// each exact in BF16.  Then
+//     C = sum_{s+t <= S-1} 2^(-8(s+t+2)) (a_s . u_t),
+// and every product of digits is an integer of magnitude at most 2^16.  All
+// products of one level m = s+t accumulate in their own FP32 TMEM accumulator
+// over the whole reduction: by Cauchy-Schwarz on the unit-norm rows of A and
+// columns of Qhat the partial sums of levels 0 and 1 stay below 2^24 (exact in
+// FP32); the digits below the top one are zero-mean, so the partial sums of the
+// higher levels are random walks of about 2^12.4 sqrt((m+1) kk), far below 2^24
+// (signed-magnitude digits would not do: their mean follows sign(A U), which is
+// coherent for smooth eigenvectors).  The S level accumulators (S x 64 TMEM
+// columns) are combined in FP64 once per tile.  Dropped levels (m >= S) and the
+// rounded digits cost about 2^-8S absolute per entry.
+//
+// Data flow per merge part: k_split_a writes the digits of the gathered A
+// columns, k_split_b generates Qhat from its generators in FP64 (once per entry)
+// and writes its digits; both images are laid out tile by tile in exactly the
+// shared-memory form the tensor core reads (K-major 8 x 16-byte core matrices),
+// so k_gemm_split only streams 16-byte vectors into shared memory, issues
+// S(S+1)/2 MMAs (M=128, N=64, K=16) per 16-deep step from one thread, and
+// double-buffers the stages against the MMAs with mbarriers.
+#include <float.h>
+
+#include "tdc_common.cuh"
+#include "tdc_umma.cuh"
+
+namespace tdc {
+
+namespace {
+constexpr int BM = kSplitBM, BN = kSplitBN, BK = kSplitBK;
+constexpr int kATileElems = BM * BK;  // 4096 per slice
+constexpr int kBTileElems = BN * BK;  // 2048 per slice
+constexpr int kMaxS = 7;
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// element offset of (row, k) inside one K-major core-matrix tile (8 rows x 8 k per core
+// matrix, core matrices along K 64 elements apart, 8-row groups BK*8 elements apart)
+__device__ __forceinline__ int core_off(int r, int k) { return (r >> 3) * (BK * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
+
+// The S leading balanced base-256 digits of x (|x| <= 1 + O(eps)), as floats:
+// F = round(x 2^56) as a two's-complement integer, then digits taken from the
+// least significant end in [-128, 127] (the top digit carries the rest, |d_0| <=
+// 256).  Below the top digit the digits are zero-mean whatever the sign of x, so
+// sums of their products behave like random walks.
+__device__ __forceinline__ void digits_of(double x, int S, float (&dg)[kMaxS]) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const bool neg = (b >> 63) != 0;
+  int e = (int)((b >> 52) & 0x7FF);
+  unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  if (e) m |= 1ull << 52; else e = 1;
+  const int sh = e - 1019;  // |x| 2^56 = m * 2^(e - 1075 + 56)
+  unsigned long long mag;
+  if (sh >= 0) mag = (sh < 8) ? (m << sh) : 0ull;
+  else if (sh > -63) mag = ((m >> (-sh - 1)) + 1ull) >> 1;  // round half up
+  else mag = 0ull;
+  long long F = neg ? -(long long)mag : (long long)mag;
+  int d[kMaxS];
+#pragma unroll
+  for (int s = kMaxS - 1; s >= 1; --s) {
+    d[s] = (int)((F + 128) & 255) - 128;
+    F = (F - d[s]) >> 8;
+  }
+  d[0] = (int)F;
+#pragma unroll
+  for (int s = 0; s < kMaxS; ++s) dg[s] = (s < S) ? (float)d[s] : 0.0f;
+}
+
+__device__ __forceinline__ int find_seg(const GemmSeg* segs, int nseg, int64_t w, int which) {
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int m = (lo + hi + 1) >> 1;
+    const int64_t v = which == 0 ? segs[m].it_a : (which == 1 ? segs[m].it_b : segs[m].it_t);
+    if (v <= w) lo = m; else hi = m - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint4 pack8(const float* v) {
+  uint4 o;
+  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
+  __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
+  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
+  __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
+  o.x = *reinterpret_cast<uint32_t*>(&p0);
+  o.y = *reinterpret_cast<uint32_t*>(&p1);
+  o.z = *reinterpret_cast<uint32_t*>(&p2);
+  o.w = *reinterpret_cast<uint32_t*>(&p3);
+  return o;
+}
+}  // namespace
+
+int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S) {
+  const int64_t KB = cdiv(kk_bound, BK), CT = cdiv(K_bound, BN);
+  const int64_t a = (cdiv(rows_top, BM) + cdiv(rows_bot, BM)) * KB * S * kATileElems;
+  const int64_t b = 2 * CT * KB * S * kBTileElems;
+  return a + b;
+}
+
+// ---------------------------------------------------------------------------
+// Segments of a tree level: one per (merge, top/bottom part).
+// ---------------------------------------------------------------------------
+__global__ void k_split_segs(Plan P, int level, int64_t M) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int S = P.split_slices;
+  int64_t ia = 0, ib = 0, it = 0, e = 0;
+  for (int64_t g = 0; g < M; ++g) {
+    const Node nd = make_node(P, level, g);
+    const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+    const int K = P.m.K[g];
+    const bool use = P.split_min_K > 0 && K >= P.split_min_K;
+    for (int p = 0; p < 2; ++p) {
+      GemmSeg sg;
+      sg.rows = p ? n - n1 : n1;
+      sg.kk = p ? P.m.nbot[g] : P.m.ntop[g];
+      sg.K = K;
+      sg.pad = 0;
+      sg.A = nd.src + (p ? n1 : 0);
+      sg.lda = nd.lds;
+      sg.acol = P.v.kept + nd.v0;
+      sg.plist = (p ? P.v.blist : P.v.tlist) + nd.v0;
+      sg.D = P.v.Dk + nd.v0;
+      sg.org = P.v.org + nd.v0;
+      sg.tau = P.v.tau + nd.v0;
+      sg.zhat = P.v.zhat + nd.v0;
+      sg.scol = P.v.scol + nd.v0;
+      sg.C = nd.dst + (p ? n1 : 0);
+      sg.ldc = nd.ldd;
+      sg.cpos = P.v.posr + nd.v0;
+      sg.it_a = ia;
+      sg.it_b = ib;
+      sg.it_t = it;
+      sg.a_img = e;
+      sg.b_img = e;
+      if (use) {
+        const int64_t RT = cdiv(sg.rows, BM), KB = cdiv(sg.kk, BK), CT = cdiv(K, BN);
+        sg.b_img = e + RT * KB * S * kATileElems;
+        e = sg.b_img + CT * KB * S * kBTileElems;
+        ia += RT * KB;
+        ib += CT * KB;
+        it += RT * CT;
+        if (P.stats) atomicAdd(&P.stats->split_flops, 2ull * (unsigned long long)sg.rows * sg.kk * (unsigned long long)K);
+      }
+      P.segs[2 * g + p] = sg;
+    }
+  }
+  GemmSeg last;
+  memset(&last, 0, sizeof(last));
+  last.it_a = ia;
+  last.it_b = ib;
+  last.it_t = it;
+  last.a_img = e;
+  if (e > P.img_cap) {  // cannot happen with the host's bound; never write past the images
+    last.it_a = last.it_b = last.it_t = 0;
+    set_status(P.status, TDC_EUNSUPPORTED);
+  }
+  P.segs[2 * M] = last;
+}
+
+// ---------------------------------------------------------------------------
+// Digit images
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img) {
+  const int64_t total = segs[nseg].it_a;
+  const int tid = threadIdx.x;
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int si = find_seg(segs, nseg, w, 0);
+    const GemmSeg& sg = segs[si];
+    const int64_t local = w - sg.it_a;
+    const int KB = (int)cdiv(sg.kk, BK);
+    const int rt = (int)(local / KB), kb = (int)(local % KB);
+    __nv_bfloat16* tile = img + sg.a_img + ((int64_t)rt * KB + kb) * S * kATileElems;
+    for (int u = tid; u < BM * (BK / 8); u += blockDim.x) {
+      const int r = u % BM, kg = u / BM;
+      const int row = rt * BM + r;
+      float dig[8][kMaxS];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int q = kb * BK + kg * 8 + i;
+        double x = 0.0;
+        if (q < sg.kk && row < sg.rows) {
+          const int p = sg.plist ? sg.plist[q] : q;
+          const int col = sg.acol ? sg.acol[p] : p;
+          x = sg.A[row + (int64_t)col * sg.lda];
+        }
+        digits_of(x, S, dig[i]);
+      }
+      const int off = core_off(r, kg * 8);
+#pragma unroll
+      for (int s = 0; s < kMaxS; ++s) {
+        if (s >= S) break;
+        float v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = dig[i][s];
+        *reinterpret_cast<uint4*>(tile + (int64_t)s * kATileElems + off) = pack8(v);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img) {
+  const int64_t total = segs[nseg].it_b;
+  const int tid = threadIdx.x;
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    const int si = find_seg(segs, nseg, w, 1);
+    const GemmSeg& sg = segs[si];
+    const int64_t local = w - sg.it_b;
+    const int KB = (int)cdiv(sg.kk, BK);
+    const int ct = (int)(local / KB), kb = (int)(local % KB);
+    __nv_bfloat16* tile = img + sg.b_img + ((int64_t)ct * KB + kb) * S * kBTileElems;
+    const int j = tid % BN, kg = tid / BN;  // 64 columns x 4 groups of 8 poles
+    const int jj = ct * BN + j;
+    double dorg = 0.0, tj = 1.0, sj = 0.0;
+    if (jj < sg.K) {
+      dorg = sg.D[sg.org[jj]];
+      tj = sg.tau[jj];
+      sj = sg.scol[jj];
+    }
+    float dig[8][kMaxS];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int q = kb * BK + kg * 8 + i;
+      double u = 0.0;
+      if (q < sg.kk && jj < sg.K) {
+        const int p = sg.plist ? sg.plist[q] : q;
+        u = (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
+      }
+      digits_of(u, S, dig[i]);
+    }
+    const int off = core_off(j, kg * 8);
+#pragma unroll
+    for (int s = 0; s < kMaxS; ++s) {
+      if (s >= S) break;
+      float v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = dig[i][s];
+      *reinterpret_cast<uint4*>(tile + (int64_t)s * kBTileElems + off) = pack8(v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The tensor-core GEMM over the digit images.  128 threads, one CTA per SM,
+// persistent over the tile list.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int nseg, int S,
+                                                       const __nv_bfloat16* img, int* status, long long budget) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t total = segs[nseg].it_t;
+  if ((int64_t)blockIdx.x >= total) return;
+  const int stage_bytes = S * (kATileElems + kBTileElems) * 2;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * stage_bytes + 16);
+  __shared__ int s_fail;
+  if (tid == 0) {
+    umma::mbar_init(&mbar[0], 1);
+    umma::mbar_init(&mbar[1], 1);
+    umma::fence_mbar_init();
+    s_fail = 0;
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(tmem_slot, 512);
+    umma::tmem_relinquish();
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  umma::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t idesc = umma::idesc_bf16(BM, BN);
+  const uint32_t sbase = umma::smem_u32(smem);
+  long long it = 0;  // k-blocks issued by this CTA so far (stage = it & 1)
+  bool failed = false;
+  for (int64_t w = blockIdx.x; w < total && !failed; w += gridDim.x) {
+    const int si = find_seg(segs, nseg, w, 2);
+    const GemmSeg& sg = segs[si];
+    const int64_t local = w - sg.it_t;
+    const int CT = (int)cdiv(sg.K, BN);
+    const int KB = (int)cdiv(sg.kk, BK);
+    const int rt = (int)(local / CT), ct = (int)(local % CT);
+    const __nv_bfloat16* aimg = img + sg.a_img + (int64_t)rt * KB * S * kATileElems;
+    const __nv_bfloat16* bimg = img + sg.b_img + (int64_t)ct * KB * S * kBTileElems;
+    uint32_t touched = 0;
+    for (int kb = 0; kb < KB; ++kb, ++it) {
+      const int st = (int)(it & 1);
+      if (it >= 2) {  // the MMAs that last read this stage must be complete
+        const bool ok = umma::mbar_wait(&mbar[st], (uint32_t)(((it - 2) >> 1) & 1), budget);
+        if (__syncthreads_or(!ok)) { failed = true; break; }
+      }
+      // stream the stage: S A-slices (8 KB each) and S B-slices (4 KB each)
+      uint8_t* sA = smem + st * stage_bytes;
+      uint8_t* sB = sA + S * kATileElems * 2;
+      const uint4* gA = reinterpret_cast<const uint4*>(aimg + (int64_t)kb * S * kATileElems);
+      const uint4* gB = reinterpret_cast<const uint4*>(bimg + (int64_t)kb * S * kBTileElems);
+      const int nA = S * kATileElems / 8, nB = S * kBTileElems / 8;
+      for (int i = tid; i < nA; i += 128) reinterpret_cast<uint4*>(sA)[i] = __ldg(gA + i);
+      for (int i = tid; i < nB; i += 128) reinterpret_cast<uint4*>(sB)[i] = __ldg(gB + i);
+      umma::fence_proxy_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        umma::tc_fence_after();
+        const uint32_t a0 = sbase + st * stage_bytes;
+        const uint32_t b0 = a0 + S * kATileElems * 2;
+#pragma unroll
+        for (int h = 0; h < BK / 16; ++h) {
+          for (int s = 0; s < S; ++s) {
+            const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2 + h * 256, 128, BK * 16);
+            for (int t = 0; s + t < S; ++t) {
+              const uint64_t bd = umma::sdesc(b0 + t * kBTileElems * 2 + h * 256, 128, BK * 16);
+              const int m = s + t;
+              umma::mma_bf16(tmem + m * BN, ad, bd, idesc, (touched >> m) & 1u);
+              touched |= 1u << m;
+            }
+          }
+        }
+        umma::mma_commit(&mbar[st]);
+      }
+    }
+    if (failed) break;
+    // epilogue: wait for the last MMAs, combine the S levels in FP64, store
+    if (KB > 0) {
+      const long long last = it - 1;
+      const bool ok = umma::mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1), budget);
+      if (__syncthreads_or(!ok)) { failed = true; break; }
+      umma::tc_fence_after();
+    }
+    const int row = rt * BM + warp * 32 + lane;
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      double acc[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+      if (KB > 0) {
+        for (int m = S - 1; m >= 0; --m) {
+          float v[32];
+          umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * BN + c0), v);
+          const double sc = ldexp(1.0, -8 * (m + 2));
+#pragma unroll
+          for (int i = 0; i < 32; ++i) acc[i] = fma((double)v[i], sc, acc[i]);
+        }
+      }
+      if (row < sg.rows) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int j = ct * BN + c0 + i;
+          if (j < sg.K) {
+            const int pos = sg.cpos ? sg.cpos[j] : j;
+            sg.C[row + (int64_t)pos * sg.ldc] = acc[i];
+          }
+        }
+      }
+    }
+    umma::tc_fence_before();
+    __syncthreads();
+  }
+  if (failed) {
+    if (tid == 0) set_status(status, TDC_ETIMEOUT);
+    // give in-flight MMAs a bounded chance to drain before the accumulators are freed
+    if (it > 0) umma::mbar_wait(&mbar[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1), budget);
+  }
+  umma::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, 512);
+}
+
+static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img, cudaStream_t s) {
+  k_split_a<<<152 * 8, 256, 0, s>>>(segs, nseg, S, img);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_split_b<<<152 * 8, 256, 0, s>>>(segs, nseg, S, img);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, int S, int* status, long long budget,
+                                    const __nv_bfloat16* img, cudaStream_t s) {
+  cudaError_t e;
+  const int smem = 2 * S * (kATileElems + kBTileElems) * 2 + 64;
+  e = cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_gemm_split<<<sms, 128, smem, s>>>(segs, nseg, S, img, status, budget);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, cudaStream_t s, cudaEvent_t mid) {
+  if (P.split_min_K <= 0 || P.segs == nullptr) return cudaSuccess;
+  k_split_segs<<<1, 32, 0, s>>>(P, L.level, L.merges);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_split_digits(P.segs, (int)(2 * L.merges), P.split_slices, P.img, s);
+  if (e != cudaSuccess) return e;
+  if (mid) cudaEventRecord(mid, s);
+  return launch_split_mma(P.segs, (int)(2 * L.merges), P.split_slices, P.status, P.spin_budget, P.img, s);
+}
+
+cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
+                             __nv_bfloat16* img, cudaStream_t s) {
+  cudaError_t e = launch_split_digits(segs_dev, nseg, S, img, s);
+  if (e != cudaSuccess) return e;
+  return launch_split_mma(segs_dev, nseg, S, status, spin_budget, img, s);
+}
+
+}  // namespace tdc

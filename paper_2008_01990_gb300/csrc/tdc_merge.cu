@@ -758,7 +758,8 @@ __global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, in
     // GEMM tiles of this merge: (row tiles of top + bottom parts) x column tiles
     const int64_t rt = (n1 + bm - 1) / bm + (n - n1 + bm - 1) / bm;
     const int64_t ct = (K + bn - 1) / bn;
-    P.m.tiles[g + 1] = (K > 0) ? rt * ct : 0;
+    const bool split = P.split_min_K > 0 && K >= P.split_min_K;
+    P.m.tiles[g + 1] = (K > 0 && !split) ? rt * ct : 0;
   }
 }
 

@@ -57,8 +57,14 @@ extern "C" int tdc_eig_noalloc(int64_t n, const double* d, const double* e, doub
   if (n < 0) return -1;
   if (n == 0) return TDC_OK;
   size_t need = 0;
-  const int ws_status = tdc_workspace_size(n, &op, &need);
+  int ws_status = tdc_workspace_size(n, &op, &need);
   if (ws_status != TDC_OK) return ws_status == -1 ? -1 : -7;
+  if (need > kNoAllocScratchBytes && op.merge_mode == TDC_MERGE_AUTO) {
+    // the library's choice: without room for the split path's digit images, the FP64 merge
+    op.merge_mode = TDC_MERGE_DENSE;
+    ws_status = tdc_workspace_size(n, &op, &need);
+    if (ws_status != TDC_OK) return -7;
+  }
   if (need > kNoAllocScratchBytes) return TDC_ETOOLARGE;
   void* ws = noalloc_scratch();
   if (!ws) return TDC_ECUDA;

@@ -40,6 +40,7 @@ class Opts(ctypes.Structure):
         ("lr_tile", ctypes.c_int32),
         ("lr_tol", ctypes.c_double),
         ("split_slices", ctypes.c_int32),
+        ("split_min_K", ctypes.c_int32),
         ("max_iter", ctypes.c_int32),
         ("sign_normalise", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32),
@@ -58,14 +59,16 @@ class Stats(ctypes.Structure):
         ("n_type1", ctypes.c_int64 * MAX_LEVELS),
         ("secular_iter_max", ctypes.c_int64),
         ("secular_iter_mean", ctypes.c_double),
-        ("phase_ms", ctypes.c_float * 8),
+        ("phase_ms", ctypes.c_float * 12),
         ("gemm_flops", ctypes.c_double * MAX_LEVELS),
+        ("split_flops", ctypes.c_double),
         ("launches", ctypes.c_int64),
     ]
 
     def as_dict(self):
         L = self.levels
-        names = ["leaf", "prepare", "secular", "zhat_norms_order", "gemm", "copy", "other", "total"]
+        names = ["leaf", "prepare", "secular", "zhat_norms_order", "gemm_fp64", "split_digits", "split_mma",
+                 "copy", "output", "total"]
         return {
             "levels": L,
             "n_merges": list(self.n_merges[:L]),
@@ -78,6 +81,7 @@ class Stats(ctypes.Structure):
             "secular_iter_mean": self.secular_iter_mean,
             "phase_ms": dict(zip(names, list(self.phase_ms))),
             "gemm_flops": list(self.gemm_flops[:L]),
+            "split_flops": self.split_flops,
             "launches": self.launches,
         }
 
@@ -226,6 +230,25 @@ def rank_one(D: torch.Tensor, z: torch.Tensor, rho: float, max_iter: int = 64, s
     if check:
         _check("tdc_rank_one (device status)", sync_status(stream))
     return org, tau, zhat, s
+
+
+def cauchy_gemm(A: torch.Tensor, D: torch.Tensor, org: torch.Tensor, tau: torch.Tensor, zhat: torch.Tensor,
+                s: torch.Tensor, mode: int = MERGE_DENSE, opts: Opts | None = None, stream=None, check=False):
+    """C = A * Qhat with Qhat_ij = zhat_i s_j / ((D_i - D_org_j) - tau_j); A is a column-major m x K view."""
+    m, K = A.shape
+    lda = A.stride(1) if K > 0 else max(m, 1)
+    C = torch.empty(K, m, dtype=torch.float64, device=A.device).t()
+    b = ctypes.c_size_t(0)
+    _check("tdc_cauchy_gemm_workspace_size",
+           lib().tdc_cauchy_gemm_workspace_size(m, K, mode, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    ws = workspace(b.value, A.device)
+    _check("tdc_cauchy_gemm", lib().tdc_cauchy_gemm(m, K, _ptr(A), max(lda, 1), _ptr(D), _ptr(org), _ptr(tau),
+                                                    _ptr(zhat), _ptr(s), _ptr(C), max(m, 1), mode,
+                                                    ctypes.byref(opts) if opts else None, _ptr(ws), ws.numel(),
+                                                    _stream(stream)))
+    if check:
+        _check("tdc_cauchy_gemm (device status)", sync_status(stream))
+    return C
 
 
 def sync_status(stream=None) -> int:

@@ -1,0 +1,99 @@
+"""Split-precision (tcgen05 BF16 digit) and FP64 eigenvector-update products
+against the oracle's plain FP64 product, element by element, and the
+eigensolver with the split merge against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import EPS, compare_vectors, ratios
+from paper_2008_01990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def tdc():
+    from paper_2008_01990_gb300 import build, tdc as t
+    build.build()
+    t.lib()
+    return t
+
+
+def generators(orc, K, seed):
+    g = inputs.SplitMix64(seed)
+    D = np.sort(g.uniform(K, -1.0, 1.0))
+    z = g.uniform(K, -1.0, 1.0)
+    z /= np.linalg.norm(z)
+    org, tau, _, _ = orc.secular(D, z, 0.8)
+    zh = orc.lowner(D, z, 0.8, org, tau)
+    s = orc.colnorm(D, org, tau, zh)
+    return D, org, tau, zh, s
+
+
+def orthogonal_rows(orc, m, K, seed):
+    # rows of an orthogonal matrix (the oracle's eigenvectors of a random tridiagonal)
+    n = max(m, K)
+    d, e = inputs.uniform_tridiag(n, seed)
+    _, Q = orc.eig(d, e, leaf=32)
+    return np.asfortranarray(Q[:m, :K])
+
+
+def run_cauchy(tdc, A, D, org, tau, zh, s, mode, **kw):
+    t = lambda x: torch.tensor(x, device=DEV)
+    At = torch.tensor(np.ascontiguousarray(A.T), device=DEV).t()  # column-major
+    C = tdc.cauchy_gemm(At, t(D), torch.tensor(org, dtype=torch.int32, device=DEV), t(tau), t(zh), t(s), mode,
+                        tdc.default_opts(**kw), check=True)
+    return C.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,K", [(1, 1), (37, 5), (300, 200), (129, 65), (256, 512)])
+def test_cauchy_dense_vs_oracle(tdc, orc, m, K):
+    D, org, tau, zh, s = generators(orc, K, 40 + K)
+    A = orthogonal_rows(orc, m, K, 7 + m)
+    U = orc.qhat(D, org, tau, zh, s)
+    Co = orc.gemm(A, U)
+    C = run_cauchy(tdc, A, D, org, tau, zh, s, tdc.MERGE_DENSE)
+    assert np.max(np.abs(C - Co)) <= 1e-14 * max(1.0, np.sqrt(K))
+
+
+@pytest.mark.parametrize("m,K", [(1, 1), (37, 5), (300, 200), (129, 65), (256, 512), (700, 1111)])
+def test_cauchy_split_vs_oracle(tdc, orc, m, K):
+    D, org, tau, zh, s = generators(orc, K, 40 + K)
+    A = orthogonal_rows(orc, m, K, 7 + m)
+    U = orc.qhat(D, org, tau, zh, s)
+    Co = orc.gemm(A, U)
+    C = run_cauchy(tdc, A, D, org, tau, zh, s, tdc.MERGE_SPLIT, split_slices=7)
+    # 7 digits: truncation and dropped digit levels cost ~2^-56 sqrt(K) per entry
+    assert np.max(np.abs(C - Co)) <= 2e-15 * max(1.0, np.sqrt(K))
+
+
+def test_cauchy_split_error_follows_digit_count(tdc, orc):
+    m, K = 256, 384
+    D, org, tau, zh, s = generators(orc, K, 99)
+    A = orthogonal_rows(orc, m, K, 5)
+    Co = orc.gemm(A, orc.qhat(D, org, tau, zh, s))
+    errs = {}
+    for S in (3, 4, 5, 6, 7):
+        C = run_cauchy(tdc, A, D, org, tau, zh, s, tdc.MERGE_SPLIT, split_slices=S)
+        errs[S] = float(np.max(np.abs(C - Co)))
+    for S in (3, 4, 5, 6):
+        # each digit adds 8 bits: the error bound 2^-8S sqrt(K) and a real decrease
+        assert errs[S] <= 2.0 ** (-8 * S) * 4 * np.sqrt(K)
+        assert errs[S + 1] < errs[S] / 16
+    assert errs[3] > 1e-9  # the digits really are the only precision (no FP64 shortcut)
+
+
+@pytest.mark.parametrize("n,leaf,fam", [(1024, 32, "uniform"), (777, 13, "uniform"), (2048, 64, "toeplitz"),
+                                        (1500, 64, "c4"), (501, 16, "clement")])
+def test_eig_split_merge_vs_oracle(tdc, orc, n, leaf, fam):
+    d, e = inputs.family(fam, n, 1)
+    o = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_SPLIT, split_min_K=64)
+    lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o, check=True)
+    lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
+    lam_o, Q_o = orc.eig(d, e, leaf=leaf)
+    nT = max(abs(lam_o[0]), abs(lam_o[-1]))
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * nT
+    res, orth = ratios(d, e, lam, Q)
+    assert res <= 50 and orth <= 50, (res, orth)
+    compare_vectors(Q, Q_o, lam_o, 1e-8 * nT, 1e-7)
