@@ -253,6 +253,6 @@ cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* stat
                              __nv_bfloat16* img, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
-constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 32;
+constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
 }  // namespace tdc

@@ -22,9 +22,10 @@
 // columns, k_split_b generates Qhat from its generators in FP64 (once per entry)
 // and writes its digits; both images are laid out tile by tile in exactly the
 // shared-memory form the tensor core reads (K-major 8 x 16-byte core matrices),
-// so k_gemm_split only streams 16-byte vectors into shared memory, issues
-// S(S+1)/2 MMAs (M=128, N=64, K=16) per 16-deep step from one thread, and
-// double-buffers the stages against the MMAs with mbarriers.
+// so k_gemm_split moves each 16-deep k-step of a tile (S A-slices of 4 KB and S
+// B-slices of 2 KB, contiguous) with two bulk copies, issues S(S+1)/2 MMAs
+// (M=128, N=64, K=16) per step from one thread, and keeps a 4-stage ring of
+// shared-memory buffers in flight with mbarriers.
 #include <float.h>
 
 #include "tdc_common.cuh"
@@ -34,9 +35,10 @@ namespace tdc {
 
 namespace {
 constexpr int BM = kSplitBM, BN = kSplitBN, BK = kSplitBK;
-constexpr int kATileElems = BM * BK;  // 4096 per slice
-constexpr int kBTileElems = BN * BK;  // 2048 per slice
+constexpr int kATileElems = BM * BK;  // 2048 per slice (4 KB)
+constexpr int kBTileElems = BN * BK;  // 1024 per slice (2 KB)
 constexpr int kMaxS = 7;
+constexpr int kStages = 4;
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
     const int rt = (int)(local / KB), kb = (int)(local % KB);
     __nv_bfloat16* tile = img + sg.a_img + ((int64_t)rt * KB + kb) * S * kATileElems;
     for (int u = tid; u < BM * (BK / 8); u += blockDim.x) {
-      const int r = u % BM, kg = u / BM;
+      const int r = u % BM, kg = u / BM;  // BK/8 groups of 8 consecutive k
       const int row = rt * BM + r;
       float dig[8][kMaxS];
 #pragma unroll
@@ -214,7 +216,8 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
     const int KB = (int)cdiv(sg.kk, BK);
     const int ct = (int)(local / KB), kb = (int)(local % KB);
     __nv_bfloat16* tile = img + sg.b_img + ((int64_t)ct * KB + kb) * S * kBTileElems;
-    const int j = tid % BN, kg = tid / BN;  // 64 columns x 4 groups of 8 poles
+    if (tid >= BN * (BK / 8)) continue;
+    const int j = tid % BN, kg = tid / BN;  // 64 columns x BK/8 groups of 8 poles
     const int jj = ct * BN + j;
     double dorg = 0.0, tj = 1.0, sj = 0.0;
     if (jj < sg.K) {
@@ -247,7 +250,11 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 
 // ---------------------------------------------------------------------------
 // The tensor-core GEMM over the digit images.  128 threads, one CTA per SM,
-// persistent over the tile list.
+// persistent over the tile list.  Thread 0 runs a kStages-deep pipeline: bulk
+// copies (cp.async.bulk, completion on full[st]) keep up to kStages-1 k-steps
+// in flight while the S(S+1)/2 MMAs of the current step are queued; each step's
+// commit frees its stage (empty[st]).  All four warps then combine the S level
+// accumulators of the tile in FP64 and store it.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int nseg, int S,
                                                        const __nv_bfloat16* img, int* status, long long budget) {
@@ -255,13 +262,17 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t total = segs[nseg].it_t;
   if ((int64_t)blockIdx.x >= total) return;
-  const int stage_bytes = S * (kATileElems + kBTileElems) * 2;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + 2 * stage_bytes + 16);
+  const uint32_t a_bytes = (uint32_t)(S * kATileElems * 2), b_bytes = (uint32_t)(S * kBTileElems * 2);
+  const uint32_t stage_bytes = a_bytes + b_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes);
+  uint64_t* empty = full + kStages;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kStages);
   __shared__ int s_fail;
   if (tid == 0) {
-    umma::mbar_init(&mbar[0], 1);
-    umma::mbar_init(&mbar[1], 1);
+    for (int i = 0; i < kStages; ++i) {
+      umma::mbar_init(&full[i], 1);
+      umma::mbar_init(&empty[i], 1);
+    }
     umma::fence_mbar_init();
     s_fail = 0;
   }
@@ -275,61 +286,64 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = umma::idesc_bf16(BM, BN);
   const uint32_t sbase = umma::smem_u32(smem);
-  long long it = 0;  // k-blocks issued by this CTA so far (stage = it & 1)
-  bool failed = false;
-  for (int64_t w = blockIdx.x; w < total && !failed; w += gridDim.x) {
+  long long step = 0;  // k-steps consumed by this CTA (stage = step % kStages)
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     const int si = find_seg(segs, nseg, w, 2);
     const GemmSeg& sg = segs[si];
     const int64_t local = w - sg.it_t;
     const int CT = (int)cdiv(sg.K, BN);
     const int KB = (int)cdiv(sg.kk, BK);
     const int rt = (int)(local / CT), ct = (int)(local % CT);
-    const __nv_bfloat16* aimg = img + sg.a_img + (int64_t)rt * KB * S * kATileElems;
-    const __nv_bfloat16* bimg = img + sg.b_img + (int64_t)ct * KB * S * kBTileElems;
-    uint32_t touched = 0;
-    for (int kb = 0; kb < KB; ++kb, ++it) {
-      const int st = (int)(it & 1);
-      if (it >= 2) {  // the MMAs that last read this stage must be complete
-        const bool ok = umma::mbar_wait(&mbar[st], (uint32_t)(((it - 2) >> 1) & 1), budget);
-        if (__syncthreads_or(!ok)) { failed = true; break; }
-      }
-      // stream the stage: S A-slices (8 KB each) and S B-slices (4 KB each)
-      uint8_t* sA = smem + st * stage_bytes;
-      uint8_t* sB = sA + S * kATileElems * 2;
-      const uint4* gA = reinterpret_cast<const uint4*>(aimg + (int64_t)kb * S * kATileElems);
-      const uint4* gB = reinterpret_cast<const uint4*>(bimg + (int64_t)kb * S * kBTileElems);
-      const int nA = S * kATileElems / 8, nB = S * kBTileElems / 8;
-      for (int i = tid; i < nA; i += 128) reinterpret_cast<uint4*>(sA)[i] = __ldg(gA + i);
-      for (int i = tid; i < nB; i += 128) reinterpret_cast<uint4*>(sB)[i] = __ldg(gB + i);
-      umma::fence_proxy_async_smem();
-      __syncthreads();
-      if (tid == 0) {
+    const uint8_t* aimg = reinterpret_cast<const uint8_t*>(img + sg.a_img + (int64_t)rt * KB * S * kATileElems);
+    const uint8_t* bimg = reinterpret_cast<const uint8_t*>(img + sg.b_img + (int64_t)ct * KB * S * kBTileElems);
+    if (tid == 0 && KB > 0) {
+      bool ok = true;
+      // load of k-step kb of this tile into stage (step + kb) % kStages; the stage is
+      // free once the MMAs of the step kStages earlier have completed
+      auto issue_load = [&](int kb) {
+        const long long g = step + kb;
+        const int st = (int)(g % kStages);
+        if (g >= kStages) ok = ok && umma::mbar_wait(&empty[st], (uint32_t)(((g - kStages) / kStages) & 1), budget);
+        uint8_t* dst = smem + st * stage_bytes;
+        umma::mbar_arrive_expect_tx(&full[st], stage_bytes);
+        umma::bulk_g2s(dst, aimg + (int64_t)kb * a_bytes, a_bytes, &full[st]);
+        umma::bulk_g2s(dst + a_bytes, bimg + (int64_t)kb * b_bytes, b_bytes, &full[st]);
+      };
+      const int pre = KB < kStages - 1 ? KB : kStages - 1;
+      for (int kb = 0; kb < pre && ok; ++kb) issue_load(kb);
+      uint32_t touched = 0;
+      for (int kb = 0; kb < KB && ok; ++kb) {
+        const long long g = step + kb;
+        const int st = (int)(g % kStages);
+        ok = umma::mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), budget);
+        if (!ok) break;
         umma::tc_fence_after();
         const uint32_t a0 = sbase + st * stage_bytes;
-        const uint32_t b0 = a0 + S * kATileElems * 2;
-#pragma unroll
-        for (int h = 0; h < BK / 16; ++h) {
-          for (int s = 0; s < S; ++s) {
-            const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2 + h * 256, 128, BK * 16);
-            for (int t = 0; s + t < S; ++t) {
-              const uint64_t bd = umma::sdesc(b0 + t * kBTileElems * 2 + h * 256, 128, BK * 16);
-              const int m = s + t;
-              umma::mma_bf16(tmem + m * BN, ad, bd, idesc, (touched >> m) & 1u);
-              touched |= 1u << m;
-            }
+        const uint32_t b0 = a0 + a_bytes;
+        for (int s = 0; s < S; ++s) {
+          const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2, 128, BK * 16);
+          for (int t = 0; s + t < S; ++t) {
+            const uint64_t bd = umma::sdesc(b0 + t * kBTileElems * 2, 128, BK * 16);
+            const int m = s + t;
+            umma::mma_bf16(tmem + m * BN, ad, bd, idesc, (touched >> m) & 1u);
+            touched |= 1u << m;
           }
         }
-        umma::mma_commit(&mbar[st]);
+        umma::mma_commit(&empty[st]);
+        if (kb + kStages - 1 < KB) issue_load(kb + kStages - 1);
       }
+      // the last commit covers every MMA of the tile
+      if (ok) {
+        const long long g = step + KB - 1;
+        ok = umma::mbar_wait(&empty[g % kStages], (uint32_t)((g / kStages) & 1), budget);
+      }
+      if (!ok) s_fail = 1;
     }
-    if (failed) break;
-    // epilogue: wait for the last MMAs, combine the S levels in FP64, store
-    if (KB > 0) {
-      const long long last = it - 1;
-      const bool ok = umma::mbar_wait(&mbar[last & 1], (uint32_t)((last >> 1) & 1), budget);
-      if (__syncthreads_or(!ok)) { failed = true; break; }
-      umma::tc_fence_after();
-    }
+    step += KB;
+    __syncthreads();
+    if (s_fail) break;
+    umma::tc_fence_after();
+    // epilogue: combine the S levels in FP64, store to the output columns
     const int row = rt * BM + warp * 32 + lane;
     for (int c0 = 0; c0 < BN; c0 += 32) {
       double acc[32];
@@ -358,10 +372,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
     umma::tc_fence_before();
     __syncthreads();
   }
-  if (failed) {
-    if (tid == 0) set_status(status, TDC_ETIMEOUT);
-    // give in-flight MMAs a bounded chance to drain before the accumulators are freed
-    if (it > 0) umma::mbar_wait(&mbar[(it - 1) & 1], (uint32_t)(((it - 1) >> 1) & 1), budget);
+  if (s_fail && tid == 0) {
+    set_status(status, TDC_ETIMEOUT);
+    // give copies and MMAs still in flight a bounded chance to land before the
+    // shared memory and the accumulators are released
+    for (int i = 0; i < kStages; ++i) umma::mbar_wait(&full[i], 0, budget);
   }
   umma::tc_fence_before();
   __syncthreads();
@@ -379,7 +394,7 @@ static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, int S, __n
 static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, int S, int* status, long long budget,
                                     const __nv_bfloat16* img, cudaStream_t s) {
   cudaError_t e;
-  const int smem = 2 * S * (kATileElems + kBTileElems) * 2 + 64;
+  const int smem = kStages * S * (kATileElems + kBTileElems) * 2 + 128;
   e = cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 152;

@@ -310,10 +310,14 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
           continue;
         }
         if (pj < 0) { pj = c; pD = D; pz = z; ps = sp; continue; }
-        const double tau = hypot(z, pz);
-        const double cc = z / tau, ss = -pz / tau;
+        // type 2 test |(D - pD) c s| <= tol with c s = -z pz / (z^2 + pz^2), free of
+        // division and square root; the rotation itself is formed only when taken
         const double tt = D - pD;
-        if (fabs(tt * cc * ss) <= tol) {  // type 2: rotate the pair so that z_pj = 0
+        const double t2 = fma(z, z, pz * pz);
+        if (fabs(tt * z * pz) <= tol * t2) {  // type 2: rotate the pair so that z_pj = 0
+          const double tau = sqrt(t2);
+          const double rt = 1.0 / tau;
+          const double cc = z * rt, ss = -pz * rt;
           const int64_t ro = v0 + nr;
           V.rij[4 * ro + 0] = pj;
           V.rij[4 * ro + 1] = c;
@@ -474,21 +478,29 @@ __device__ __forceinline__ void secular_sums(const double* D, const double* z, i
                                              double tau, double& psi, double& dpsi, double& phi,
                                              double& dphi, double& sabs) {
   const int lane = threadIdx.x & 31;
-  double a = 0.0, da = 0.0, b = 0.0, db = 0.0, ab = 0.0;
-  for (int i = lane; i < K; i += 32) {
-    const double del = (D[i] - dorg) - tau;
-    const double r = rcp_nr(del);
+  double a = 0.0, da = 0.0, b = 0.0, db = 0.0;
+  // poles left of the root (i <= j) give negative terms, poles right of it positive
+  // ones, so sum |t| = phi - psi needs no separate accumulation
+  const int split = min(K, j + 1);
+  for (int i = lane; i < split; i += 32) {
+    const double r = rcp_nr((D[i] - dorg) - tau);
     const double zi = z[i];
     const double t = zi * zi * r;
-    ab += fabs(t);
-    if (i <= j) { a += t; da = fma(t, r, da); }
-    else { b += t; db = fma(t, r, db); }
+    a += t;
+    da = fma(t, r, da);
+  }
+  for (int i = split + lane; i < K; i += 32) {
+    const double r = rcp_nr((D[i] - dorg) - tau);
+    const double zi = z[i];
+    const double t = zi * zi * r;
+    b += t;
+    db = fma(t, r, db);
   }
   psi = warp_sum(a);
   dpsi = warp_sum(da);
   phi = warp_sum(b);
   dphi = warp_sum(db);
-  sabs = warp_sum(ab);
+  sabs = phi - psi;
 }
 
 // Warp-cooperative solve of root j; every lane returns the same (org, tau).
@@ -496,28 +508,28 @@ __device__ void secular_root(const double* D, const double* z, int K, int j, dou
                              int& org_out, double& tau_out, int& iters, bool& conv) {
   const double irho = 1.0 / rho;
   int org;
-  double lo, hi;
+  double lo, hi, tau;
+  // sums at the starting point (carried into the first iteration)
+  double psi, dpsi, phi, dphi, sabs;
   if (j < K - 1) {
     const double gap = D[j + 1] - D[j];
-    double psi, dpsi, phi, dphi, sabs;
     secular_sums(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
-    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; }
-    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; }
+    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; tau = hi; }
+    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; tau = lo; }
   } else {
     double zz = 0.0;
     for (int i = threadIdx.x & 31; i < K; i += 32) zz = fma(z[i], z[i], zz);
     zz = warp_sum(zz);
-    org = K - 1; lo = 0.0; hi = rho * zz;
+    org = K - 1; lo = 0.0; hi = rho * zz; tau = hi;
+    secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
   }
   const double dorg = D[org];
   const double dl = D[j] - dorg;                         // delta_j (0 when org == j)
   const double dr = (j < K - 1) ? D[j + 1] - dorg : 0.0; // delta_{j+1}
-  double tau = 0.5 * (lo + hi);
   int it = 0;
   conv = false;
   for (it = 1; it <= max_iter; ++it) {
-    double psi, dpsi, phi, dphi, sabs;
-    secular_sums(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
+    if (it > 1) secular_sums(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
     const double gv = irho + psi + phi;
     if (gv == 0.0 || fabs(gv) <= 8.0 * kEps * (irho + sabs)) { conv = true; break; }
     if (gv < 0.0) lo = tau; else hi = tau;
