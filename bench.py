@@ -196,6 +196,40 @@ def sampled_ratios(tdc_lam, Q, d, e, nsample=256):
     return res, orth, nT
 
 
+def run_qhat(args):
+    """Stand-alone eigenvector-update product C = A * Qhat (tdc_cauchy_gemm) at the size of
+    the top merge of the n=16384 workload: A 8192 x 8192 with |A_ij| <= 1, Qhat the 8192 x 8192
+    Cauchy-like eigenvector matrix of a rank-one problem (generators from tdc_rank_one)."""
+    import torch
+    from paper_2008_01990_gb300 import inputs, tdc
+    dev = torch.device("cuda", 0)
+    m = K = 8192
+    g = inputs.SplitMix64(11)
+    D = np.sort(g.uniform(K, -1.0, 1.0))
+    z = g.uniform(K, -1.0, 1.0)
+    z /= np.linalg.norm(z)
+    A = torch.tensor(g.uniform(m * K, -1.0, 1.0).reshape(K, m), device=dev).t() / np.sqrt(K)
+    Dt, zt = torch.tensor(D, device=dev), torch.tensor(z, device=dev)
+    org, tau, zh, s = tdc.rank_one(Dt, zt, 0.9, check=True)
+    mode = tdc.MERGE_SPLIT if args.merge in ("split", "auto") else tdc.MERGE_DENSE
+    opts = tdc.default_opts()
+    for _ in range(args.warmup):
+        C = tdc.cauchy_gemm(A, Dt, org, tau, zh, s, mode, opts)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        C = tdc.cauchy_gemm(A, Dt, org, tau, zh, s, mode, opts)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    flops = 2.0 * m * K * K
+    print(json.dumps({"workload": "qhat8192", "merge": args.merge, "ms": ms,
+                      "fp64_equivalent_tflops": flops / (ms * 1e-3) / 1e12}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -362,7 +396,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768"])
+    ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -370,6 +404,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "qhat8192":
+        return run_qhat(args)
     return run_ours(args)
 
 

@@ -23,9 +23,11 @@
 // and writes its digits; both images are laid out tile by tile in exactly the
 // shared-memory form the tensor core reads (K-major 8 x 16-byte core matrices),
 // so k_gemm_split moves each 16-deep k-step of a tile (S A-slices of 4 KB and S
-// B-slices of 2 KB, contiguous) with two bulk copies, issues S(S+1)/2 MMAs
-// (M=128, N=64, K=16) per step from one thread, and keeps a 4-stage ring of
-// shared-memory buffers in flight with mbarriers.
+// B-slices of 2 KB, contiguous) with two bulk copies and keeps a 4-stage ring of
+// shared-memory buffers in flight with mbarriers.  A tcgen05 MMA with M = 128
+// costs about the same issue time for any N up to 128, so the S(S+1)/2 digit
+// products of a step are issued as S wide MMAs (A_s against the stacked B slices,
+// N = 64 (S - s), split at 256): 10 MMAs per step for S = 7 instead of 28.
 #include <float.h>
 
 #include "tdc_common.cuh"
@@ -284,7 +286,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
   __syncthreads();
   umma::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = umma::idesc_bf16(BM, BN);
   const uint32_t sbase = umma::smem_u32(smem);
   long long step = 0;  // k-steps consumed by this CTA (stage = step % kStages)
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
@@ -311,7 +312,6 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
       };
       const int pre = KB < kStages - 1 ? KB : kStages - 1;
       for (int kb = 0; kb < pre && ok; ++kb) issue_load(kb);
-      uint32_t touched = 0;
       for (int kb = 0; kb < KB && ok; ++kb) {
         const long long g = step + kb;
         const int st = (int)(g % kStages);
@@ -320,13 +320,17 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
         umma::tc_fence_after();
         const uint32_t a0 = sbase + st * stage_bytes;
         const uint32_t b0 = a0 + a_bytes;
+        // The S B-slices are stacked along N in shared memory and level m's
+        // accumulator starts at TMEM column m*BN, so A_s against the stacked slices
+        // B_0..B_{S-1-s} (N = BN (S - s)) drops every product A_s B_t into level s+t:
+        // one wide MMA per A-slice (split at N = 256) instead of one per digit pair.
         for (int s = 0; s < S; ++s) {
           const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2, 128, BK * 16);
-          for (int t = 0; s + t < S; ++t) {
-            const uint64_t bd = umma::sdesc(b0 + t * kBTileElems * 2, 128, BK * 16);
-            const int m = s + t;
-            umma::mma_bf16(tmem + m * BN, ad, bd, idesc, (touched >> m) & 1u);
-            touched |= 1u << m;
+          const int ncols = BN * (S - s);
+          for (int off = 0; off < ncols; off += 256) {
+            const int nn = ncols - off < 256 ? ncols - off : 256;
+            const uint64_t bd = umma::sdesc(b0 + (off / BN) * kBTileElems * 2, 128, BK * 16);
+            umma::mma_bf16(tmem + s * BN + off, ad, bd, umma::idesc_bf16(BM, nn), (kb > 0 || s > 0) ? 1u : 0u);
           }
         }
         umma::mma_commit(&empty[st]);
@@ -343,19 +347,31 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
     __syncthreads();
     if (s_fail) break;
     umma::tc_fence_after();
-    // epilogue: combine the S levels in FP64, store to the output columns
+    // epilogue: combine the S levels (exact FP32 integers P_m) and store.
+    // C = 2^-16 sum_m 2^-8m P_m = 2^-48 ((((P0 2^8 + P1) 2^8 + P2) 2^8 + P3) 2^8 + P4)
+    //   + 2^-56 (P5 + 2^-8 P6): the first five levels combine exactly in a 64-bit
+    // integer, the last two in FP32 (rounding about 2^-59 absolute), leaving four
+    // FP64 operations per entry.
     const int row = rt * BM + warp * 32 + lane;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     for (int c0 = 0; c0 < BN; c0 += 32) {
-      double acc[32];
+      long long hi[32];
+      float lo[32];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) acc[i] = 0.0;
+      for (int i = 0; i < 32; ++i) { hi[i] = 0; lo[i] = 0.0f; }
       if (KB > 0) {
-        for (int m = S - 1; m >= 0; --m) {
+        for (int m = 0; m < 5; ++m) {
           float v[32];
-          umma::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(m * BN + c0), v);
-          const double sc = ldexp(1.0, -8 * (m + 2));
+          if (m < S) umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) acc[i] = fma((double)v[i], sc, acc[i]);
+          for (int i = 0; i < 32; ++i) hi[i] = hi[i] * 256 + (m < S ? (long long)__float2int_rn(v[i]) : 0ll);
+        }
+        for (int m = 6; m >= 5; --m) {
+          if (m >= S) continue;
+          float v[32];
+          umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) lo[i] = fmaf(lo[i], 0.00390625f, v[i]);
         }
       }
       if (row < sg.rows) {
@@ -364,7 +380,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
           const int j = ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            sg.C[row + (int64_t)pos * sg.ldc] = acc[i];
+            const double val = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+            sg.C[row + (int64_t)pos * sg.ldc] = val;
           }
         }
       }
