@@ -375,6 +375,7 @@ def run_ours(args):
         "merge_compare_s": compare,
         "phase_ms": stats["phase_ms"],
         "K_per_level": stats["sum_K"],
+        "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"]},
         "test_ratios": {"lam_err_over_normT": lam_err, "residual": res, "orthogonality": orth,
                         "sampled_columns": 256},
         "gpu_launches": int(stats["launches"]) * args.steps,

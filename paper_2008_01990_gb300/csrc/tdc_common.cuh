@@ -203,6 +203,17 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return r;
 }
 
+// 1/sqrt(x): hardware estimate (rsqrt.approx.ftz.f64) followed by two Newton-Raphson
+// refinements y <- y (3 - x y^2) / 2, each of which squares the relative error.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double h = 0.5 * x;
+  y = y * fma(-h * y, y, 1.5);
+  y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -41,6 +41,7 @@ constexpr int kATileElems = BM * BK;  // 2048 per slice (4 KB)
 constexpr int kBTileElems = BN * BK;  // 1024 per slice (2 KB)
 constexpr int kMaxS = 7;
 constexpr int kStages = 4;
+constexpr int kGroupRows = 8;
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
@@ -294,7 +295,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
     const int64_t local = w - sg.it_t;
     const int CT = (int)cdiv(sg.K, BN);
     const int KB = (int)cdiv(sg.kk, BK);
-    const int rt = (int)(local / CT), ct = (int)(local % CT);
+    // tiles in groups of kGroupRows row tiles, column tile by column tile, so that
+    // the CTAs running together share A row tiles and B column tiles in L2
+    const int RT = (int)cdiv(sg.rows, BM);
+    const int grp = (int)(local / ((int64_t)kGroupRows * CT));
+    const int within = (int)(local % ((int64_t)kGroupRows * CT));
+    const int gr = min(kGroupRows, RT - grp * kGroupRows);
+    const int rt = grp * kGroupRows + within % gr, ct = within / gr;
     const uint8_t* aimg = reinterpret_cast<const uint8_t*>(img + sg.a_img + (int64_t)rt * KB * S * kATileElems);
     const uint8_t* bimg = reinterpret_cast<const uint8_t*>(img + sg.b_img + (int64_t)ct * KB * S * kBTileElems);
     if (tid == 0 && KB > 0) {

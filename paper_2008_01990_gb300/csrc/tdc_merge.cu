@@ -114,9 +114,17 @@ __global__ void __launch_bounds__(32) k_leaf(Plan P, int64_t nleaves) {
         double mu = dd[q] - bq * bq / (hd + copysign(h, hd));
         double x = dd[pp] - mu, y = ee[pp];
         for (int k = pp; k < q; ++k) {
-          double r = hypot(x, y);
-          double c = 1.0, s = 0.0;
-          if (r != 0.0) { c = x / r; s = y / r; }
+          // Givens rotation from (x, y) through a refined reciprocal square root
+          // (no division on the sequential path); hypot only where squares leave range
+          const double t2 = fma(x, x, y * y);
+          double r, c = 1.0, s = 0.0;
+          if (t2 > 1e-290 && t2 < 1e290) {
+            const double ri = rsqrt_nr(t2);
+            c = x * ri; s = y * ri; r = t2 * ri;
+          } else {
+            r = hypot(x, y);
+            if (r != 0.0) { c = x / r; s = y / r; }
+          }
           if (k > pp) ee[k - 1] = r;
           double a0 = dd[k], a1 = dd[k + 1], bk = ee[k];
           double cc = c * c, ss = s * s, c2s = 2.0 * c * s * bk;
@@ -228,12 +236,8 @@ __device__ void block_excl_scan2(int& a, int& b, int* red) {
 // ---------------------------------------------------------------------------
 // k_prepare: one block per merge.
 // ---------------------------------------------------------------------------
-static constexpr int kChunk = 2048;
 
 __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
-  __shared__ double sD[kChunk];
-  __shared__ double sZ[kChunk];
-  __shared__ int sC[kChunk];
   __shared__ double redd[64];
   __shared__ int redi[64];
   __shared__ int sres[4];
@@ -285,62 +289,113 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     if (threadIdx.x == 0) set_status(P.status, TDC_ENONFINITE);
   }
   __syncthreads();
-  // 3. deflation scan in ascending pole order (sequential by nature; thread 0
-  //    scans chunks staged in shared memory)
-  int K = 0, ndf = 0, nr = 0, nch = 0;
-  int pj = -1, ps = 0, last_rot_i = -1;
-  double pD = 0.0, pz = 0.0;
-  int t1 = 0;
-  for (int base = 0; base < n; base += kChunk) {
-    const int cnt = min(kChunk, n - base);
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-      int c = V.perm[v0 + base + k];
-      sC[k] = c;
-      sD[k] = V.Dc[v0 + c];
-      sZ[k] = V.zc[v0 + c];
+  // 3. deflation (Section 3.2).  Type 1 is a per-pole test; type 2 compares each
+  //    remaining pole with the last kept one, which is sequential only through
+  //    chains of rotations.  3a/3b run in parallel: the compacted list L of the
+  //    poles that survive type 1, and for each consecutive pair of L the type-2 test
+  //    and rotation evaluated on the original values (valid whenever the previous
+  //    pair did not rotate).  3c resolves the sequence in one thread and does FP64
+  //    work only right after a rotation.
+  int* Lpos = P.v.stag + 2 * v0;    // sorted positions of the poles surviving type 1
+  uint8_t* flag = P.v.cseg + v0;    // speculative type-2 outcome for pair (q-1, q)
+  double* spc = P.v.skey + 2 * v0;  // speculative c (q) and s (n + q)
+  double* sdp = P.v.Ds + v0;        // speculative deflated value of the predecessor
+  double* sdi = P.v.zs + v0;        // speculative new value of the survivor
+  double* stau = P.v.tau + v0;      // speculative new z of the survivor
+  // 3a. type-1 entries go straight to the deflated list (sorted order), the rest to L
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int p0 = min(n, (int)threadIdx.x * per), p1 = min(n, p0 + per);
+  int c_keep = 0, c_t1 = 0;
+  for (int p = p0; p < p1; ++p) {
+    const int c = V.perm[v0 + p];
+    if (rho * fabs(V.zc[v0 + c]) <= tol) ++c_t1; else ++c_keep;
+  }
+  int o_keep = c_keep, o_t1 = c_t1;
+  block_excl_scan2(o_keep, o_t1, redi);
+  for (int p = p0; p < p1; ++p) {
+    const int c = V.perm[v0 + p];
+    if (rho * fabs(V.zc[v0 + c]) <= tol) {
+      V.dcol[v0 + o_t1] = c;
+      V.dval[v0 + o_t1] = V.Dc[v0 + c];
+      V.dseg[v0 + o_t1] = (uint8_t)((c < n1) ? 1 : 2);
+      ++o_t1;
+    } else {
+      Lpos[o_keep++] = p;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int k = 0; k < cnt; ++k) {
-        const int c = sC[k];
-        const double D = sD[k], z = sZ[k];
-        const int sp = (c < n1) ? 1 : 2;
-        if (rho * fabs(z) <= tol) {  // type 1: negligible z
-          V.dcol[v0 + ndf] = c; V.dval[v0 + ndf] = D; V.dseg[v0 + ndf] = (uint8_t)sp; ++ndf; ++t1;
-          continue;
-        }
-        if (pj < 0) { pj = c; pD = D; pz = z; ps = sp; continue; }
-        // type 2 test |(D - pD) c s| <= tol with c s = -z pz / (z^2 + pz^2), free of
-        // division and square root; the rotation itself is formed only when taken
-        const double tt = D - pD;
+  }
+  if (threadIdx.x == blockDim.x - 1) { sres[0] = o_keep; sres[1] = o_t1; }
+  __syncthreads();
+  const int nL = sres[0], t1 = sres[1];
+  __syncthreads();
+  // 3b. speculative type-2 test and rotation for each consecutive pair of L
+  for (int q = 1 + threadIdx.x; q < nL; q += blockDim.x) {
+    const int a = V.perm[v0 + Lpos[q - 1]], b = V.perm[v0 + Lpos[q]];
+    const double pD = V.Dc[v0 + a], pz = V.zc[v0 + a];
+    const double D = V.Dc[v0 + b], z = V.zc[v0 + b];
+    // |(D - pD) c s| <= tol with c s = -z pz / (z^2 + pz^2): no division, no root
+    const double t2 = fma(z, z, pz * pz);
+    const bool f = fabs((D - pD) * z * pz) <= tol * t2;
+    flag[q] = f ? 1 : 0;
+    if (f) {
+      const double r = rsqrt_nr(t2);
+      const double cc = z * r, ss = -pz * r;
+      spc[q] = cc;
+      spc[n + q] = ss;
+      stau[q] = t2 * r;
+      sdp[q] = pD * cc * cc + D * ss * ss;
+      sdi[q] = pD * ss * ss + D * cc * cc;
+    }
+  }
+  __syncthreads();
+  // 3c. sequential resolution
+  if (threadIdx.x == 0) {
+    int K = 0, ndf = t1, nr = 0, nch = 0, last_rot_i = -1;
+    int pj = -1, ps = 0;
+    double pD = 0.0, pz = 0.0;
+    bool prev_rot = false;
+    for (int q = 0; q < nL; ++q) {
+      const int c = V.perm[v0 + Lpos[q]];
+      const int sp = (c < n1) ? 1 : 2;
+      if (q == 0) {
+        pj = c; pD = V.Dc[v0 + c]; pz = V.zc[v0 + c]; ps = sp; prev_rot = false;
+        continue;
+      }
+      bool rot;
+      double cc = 0.0, ss = 0.0, tau = 0.0, dp = 0.0, di = 0.0;
+      if (!prev_rot) {
+        rot = flag[q] != 0;
+        if (rot) { cc = spc[q]; ss = spc[n + q]; tau = stau[q]; dp = sdp[q]; di = sdi[q]; }
+      } else {  // the last kept pole was rotated: test with its current values
+        const double D = V.Dc[v0 + c], z = V.zc[v0 + c];
         const double t2 = fma(z, z, pz * pz);
-        if (fabs(tt * z * pz) <= tol * t2) {  // type 2: rotate the pair so that z_pj = 0
-          const double tau = sqrt(t2);
-          const double rt = 1.0 / tau;
-          const double cc = z * rt, ss = -pz * rt;
-          const int64_t ro = v0 + nr;
-          V.rij[4 * ro + 0] = pj;
-          V.rij[4 * ro + 1] = c;
-          V.rij[4 * ro + 2] = ps | (sp << 8);
-          V.rcs[2 * ro + 0] = cc;
-          V.rcs[2 * ro + 1] = ss;
-          if (pj != last_rot_i) V.rch[v0 + nch++] = nr;
-          last_rot_i = c;
-          ++nr;
-          const double dp = pD * cc * cc + D * ss * ss;
-          const double di = pD * ss * ss + D * cc * cc;
-          const int u = ps | sp;
-          V.dcol[v0 + ndf] = pj; V.dval[v0 + ndf] = dp; V.dseg[v0 + ndf] = (uint8_t)u; ++ndf;
-          pj = c; pD = di; pz = tau; ps = u;
-        } else {
-          V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
-          pj = c; pD = D; pz = z; ps = sp;
+        rot = fabs((D - pD) * z * pz) <= tol * t2;
+        if (rot) {
+          const double r = rsqrt_nr(t2);
+          cc = z * r; ss = -pz * r; tau = t2 * r;
+          dp = pD * cc * cc + D * ss * ss;
+          di = pD * ss * ss + D * cc * cc;
         }
       }
+      if (rot) {  // type 2: rotate (pj, c) so that z_pj = 0; pj is deflated
+        const int64_t ro = v0 + nr;
+        V.rij[4 * ro + 0] = pj;
+        V.rij[4 * ro + 1] = c;
+        V.rij[4 * ro + 2] = ps | (sp << 8);
+        V.rcs[2 * ro + 0] = cc;
+        V.rcs[2 * ro + 1] = ss;
+        if (pj != last_rot_i) V.rch[v0 + nch++] = nr;
+        last_rot_i = c;
+        ++nr;
+        const int u = ps | sp;
+        V.dcol[v0 + ndf] = pj; V.dval[v0 + ndf] = dp; V.dseg[v0 + ndf] = (uint8_t)u; ++ndf;
+        pj = c; pD = di; pz = tau; ps = u;
+        prev_rot = true;
+      } else {
+        V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
+        pj = c; pD = V.Dc[v0 + c]; pz = V.zc[v0 + c]; ps = sp;
+        prev_rot = false;
+      }
     }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
     if (pj >= 0) {
       V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
     }
@@ -356,10 +411,10 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     }
   }
   __syncthreads();
-  K = sres[0];
+  const int K = sres[0];
   // 4. lists of non-deflated poles with support in the top / bottom rows
-  const int per = (K + blockDim.x - 1) / blockDim.x;
-  const int j0 = min(K, (int)threadIdx.x * per), j1 = min(K, j0 + per);
+  const int perk = (K + blockDim.x - 1) / blockDim.x;
+  const int j0 = min(K, (int)threadIdx.x * perk), j1 = min(K, j0 + perk);
   int ct = 0, cb = 0;
   for (int j = j0; j < j1; ++j) {
     uint8_t s = V.kseg[v0 + j];
