@@ -164,10 +164,14 @@ int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_
 /* Structured product C = A * Qhat with Qhat the K x K Cauchy-like matrix
  * Qhat_ij = zhat_i s_j / ((D_i - D_org_j) - tau_j) given by its generators
  * (Eq. (Q_Cauchy) with Eq. (d-lambda)); A is m x K (lda), C is m x K (ldc).
- * mode: TDC_MERGE_DENSE (FP64) or TDC_MERGE_SPLIT (base-256 BF16 digit products
- * on the tensor cores; requires |A_ij| <= 1, which holds for the orthogonal
- * factors the merge multiplies, and uses o->split_slices digits);
- * TDC_MERGE_STRUCTURED returns TDC_EUNSUPPORTED here.
+ * mode: TDC_MERGE_DENSE (FP64); TDC_MERGE_STRUCTURED (Section 2.1: Qhat cut into
+ * o->lr_tile square tiles, the tiles on and next to the diagonal multiplied densely
+ * in FP64, every other tile replaced by its SRRSC skeleton Qhat(I,T) [I Z] at
+ * tolerance o->lr_tol and applied as two thin FP64 products, Z generated from its
+ * generators; tiles whose rank would exceed 64 stay dense); or TDC_MERGE_SPLIT
+ * (base-256 BF16 digit products on the tensor cores; requires |A_ij| <= 1, which
+ * holds for the orthogonal factors the merge multiplies, and uses
+ * o->split_slices digits).
  * ws of tdc_cauchy_gemm_workspace_size(m, K, mode, o) bytes. */
 int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc_opts* o, size_t* bytes);
 int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const double* D, const int32_t* org,

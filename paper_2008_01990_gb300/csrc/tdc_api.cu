@@ -57,7 +57,34 @@ struct HostPlan {
   std::vector<int64_t> max_tiles;   // GEMM tile upper bound per level
   int64_t img_elems = 0;            // digit images of the split path (bf16 elements)
   int split_S = 0;                  // 0: split path off
+  int struct_m = 0;                 // 0: structured path off
+  int64_t struct_slots = 0;         // SRRSC slots (segments x Tmax^2)
+  int64_t struct_w = 0;             // W doubles
+  int64_t struct_segs = 0;          // segments
 };
+
+static bool struct_enabled(const tdc_opts& o) { return o.merge_mode == TDC_MERGE_STRUCTURED; }
+
+static void level_struct_dims(const LevelLaunch& L, int m, int64_t& Tmax, int64_t& ldw) {
+  Tmax = (L.max_n + m - 1) / m;
+  ldw = (L.max_n + 1) / 2;
+}
+
+static void plan_struct(HostPlan& H, const tdc_opts& o) {
+  H.struct_m = struct_enabled(o) ? o.lr_tile : 0;
+  H.struct_slots = H.struct_w = H.struct_segs = 0;
+  if (!H.struct_m) return;
+  for (int l = 0; l < H.T; ++l) {
+    const LevelLaunch& L = H.levels[l];
+    if (L.max_n < o.structured_min_K) continue;
+    int64_t Tmax, ldw;
+    level_struct_dims(L, H.struct_m, Tmax, ldw);
+    const int64_t nseg = 2 * L.merges;
+    H.struct_slots = std::max(H.struct_slots, nseg * Tmax * Tmax);
+    H.struct_w = std::max(H.struct_w, nseg * Tmax * kStructRmax * ldw);
+    H.struct_segs = std::max(H.struct_segs, nseg + 1);
+  }
+}
 
 // the split path is used for merge_mode SPLIT and AUTO
 static bool split_enabled(const tdc_opts& o) {
@@ -143,7 +170,7 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
 
 // workspace carving
 struct Layout {
-  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, q1, total;
+  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
 };
 
 static constexpr int kVecD = 17;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey)
@@ -160,8 +187,15 @@ static Layout layout_of(const HostPlan& H) {
   L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
   L.tiles = o; o = align_up(o + sizeof(int64_t) * (size_t)(H.Mmax + 1));
   L.stats = o; o = align_up(o + sizeof(Stats));
-  L.segs = o; o = align_up(o + (H.split_S ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
+  L.segs = o; o = align_up(o + ((H.split_S || H.struct_m) ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
+  const size_t ns = (size_t)H.struct_slots, mm = (size_t)H.struct_m;
+  L.srank = o; o = align_up(o + sizeof(int) * ns);
+  L.spiv = o; o = align_up(o + sizeof(int) * ns * kStructRmax);
+  L.sy = o; o = align_up(o + sizeof(double) * ns * kStructRmax);
+  L.svr = o; o = align_up(o + sizeof(double) * ns * mm);
+  L.scolpiv = o; o = align_up(o + sizeof(int) * ns * mm);
+  L.sw = o; o = align_up(o + sizeof(double) * (size_t)H.struct_w);
   L.q1 = o; o = align_up(o + sizeof(double) * (size_t)H.Q1);
   L.total = o + 256;  // slack for aligning an unaligned base
   return L;
@@ -190,7 +224,7 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   P.m.tiles = (int64_t*)(base + L.tiles);
   P.Q1 = (double*)(base + L.q1);
   P.prob = (const Problem*)(base + L.prob);
-  P.segs = H.split_S ? (GemmSeg*)(base + L.segs) : nullptr;
+  P.segs = (H.split_S || H.struct_m) ? (GemmSeg*)(base + L.segs) : nullptr;
   P.img = (__nv_bfloat16*)(base + L.img);
   P.img_cap = H.img_elems;
 }
@@ -250,6 +284,19 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   P.split_min_K = H.split_S ? o.split_min_K : 0;
   P.split_slices = H.split_S ? H.split_S : 7;
   P.spin_budget = o.spin_budget;
+  P.struct_min_K = H.struct_m ? o.structured_min_K : 0;
+  P.struct_m = H.struct_m;
+  StructArgs SA;
+  memset(&SA, 0, sizeof(SA));
+  SA.m = H.struct_m;
+  SA.rmax = kStructRmax;
+  SA.tol = o.lr_tol;
+  SA.srank = (int*)(base + L.srank);
+  SA.spiv = (int*)(base + L.spiv);
+  SA.sy = (double*)(base + L.sy);
+  SA.svr = (double*)(base + L.svr);
+  SA.scolpiv = (int*)(base + L.scolpiv);
+  SA.W = (double*)(base + L.sw);
   P.status = status_ptr();
   if (!P.status) return TDC_ECUDA;
   P.stats = o.collect_stats ? (Stats*)(base + L.stats) : nullptr;
@@ -273,8 +320,11 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   };
   // kernel launches: problem upload, corner modification, leaves, 9 per level, output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
-  for (int l = 0; l < H.T; ++l)
+  for (int l = 0; l < H.T; ++l) {
     if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4;
+    if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
+      launches += 2 + 2 * ((H.levels[l].max_n + H.struct_m - 1) / H.struct_m);
+  }
   const size_t t0 = mark();
   if (err == cudaSuccess) err = launch_dmod(P, s);
   if (err == cudaSuccess) err = launch_leaves(P, H.nleaves, H.max_leaf, s);
@@ -291,6 +341,15 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     if (err == cudaSuccess) err = launch_finalize(P, LL, kDenseBM, kDenseBN, s);
     const size_t a3 = mark();
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
+    if (err == cudaSuccess && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
+      int64_t Tmax, ldw;
+      level_struct_dims(LL, H.struct_m, Tmax, ldw);
+      SA.Tmax = (int)Tmax;
+      SA.ldw = ldw;
+      SA.status = P.status;
+      err = launch_struct_segs(P, LL, s);
+      if (err == cudaSuccess) err = launch_struct(P.segs, (int)(2 * LL.merges), SA, s);
+    }
     const size_t a4 = mark();
     span(1, a0, a1);
     span(2, a1, a2);
@@ -387,6 +446,7 @@ int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
   HostPlan H;
   build_plan(H, 1, &n, nullptr, nullptr, nullptr, d.leaf);
   plan_split(H, d);
+  plan_struct(H, d);
   *bytes = layout_of(H).total;
   return TDC_OK;
 }
@@ -408,6 +468,7 @@ int tdc_eig(int64_t n, const double* d, const double* e, double* lam, double* Q,
   int64_t off = 0, ld = ldq;
   build_plan(H, 1, &n, &off, &off, &ld, op.leaf);
   plan_split(H, op);
+  plan_struct(H, op);
   return run_plan(H, op, d, e, lam, Q, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -424,6 +485,7 @@ int tdc_eig_batched_workspace_size(int32_t batch, const int64_t* n_host, const t
   HostPlan H;
   build_plan(H, batch, n_host, nullptr, nullptr, nullptr, d.leaf);
   plan_split(H, d);
+  plan_struct(H, d);
   *bytes = layout_of(H).total;
   return TDC_OK;
 }
@@ -449,6 +511,7 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
   HostPlan H;
   build_plan(H, batch, n_host, off_de_host, off_q_host, nullptr, op.leaf);
   plan_split(H, op);
+  plan_struct(H, op);
   return run_plan(H, op, d, e, lam, Q, ws, ws_bytes, (cudaStream_t)stream);
 }
 
@@ -499,11 +562,19 @@ int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc
   if (o) op = *o;
   if (m < 0) return -1;
   if (K < 0) return -2;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -3;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED) return -3;
   if (validate_opts(&op)) return -4;
   if (!bytes) return -5;
   if (mode == TDC_MERGE_DENSE) {
     *bytes = 256;
+    return TDC_OK;
+  }
+  if (mode == TDC_MERGE_STRUCTURED) {
+    const int64_t mm = op.lr_tile, T = (K + mm - 1) / mm, ns = T * T;
+    *bytes = 256 + align_up(2 * sizeof(GemmSeg)) + align_up(sizeof(int) * ns) +
+             align_up(sizeof(int) * ns * kStructRmax) + align_up(sizeof(double) * ns * kStructRmax) +
+             align_up(sizeof(double) * ns * mm) + align_up(sizeof(int) * ns * mm) +
+             align_up(sizeof(double) * T * kStructRmax * std::max<int64_t>(m, 1));
     return TDC_OK;
   }
   *bytes = 256 + align_up(2 * sizeof(GemmSeg)) + sizeof(__nv_bfloat16) * (size_t)cauchy_split_elems(m, K, op.split_slices, nullptr);
@@ -528,7 +599,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   if (!s) return -9;
   if (!C) return -10;
   if (ldc < m) return -11;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return mode == TDC_MERGE_STRUCTURED ? TDC_EUNSUPPORTED : -12;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED) return -12;
   if (validate_opts(&op)) return -13;
   size_t need = 0;
   tdc_cauchy_gemm_workspace_size(m, K, mode, &op, &need);
@@ -544,6 +615,31 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   cudaError_t err;
   if (mode == TDC_MERGE_DENSE) {
     err = launch_seg_dense(sg, cs);
+  } else if (mode == TDC_MERGE_STRUCTURED) {
+    const int64_t mm = op.lr_tile, T = (K + mm - 1) / mm, ns = T * T;
+    char* p = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+    GemmSeg* segs = (GemmSeg*)p; p += align_up(2 * sizeof(GemmSeg));
+    StructArgs SA;
+    memset(&SA, 0, sizeof(SA));
+    SA.m = (int)mm;
+    SA.rmax = kStructRmax;
+    SA.Tmax = (int)T;
+    SA.tol = op.lr_tol;
+    SA.srank = (int*)p; p += align_up(sizeof(int) * ns);
+    SA.spiv = (int*)p; p += align_up(sizeof(int) * ns * kStructRmax);
+    SA.sy = (double*)p; p += align_up(sizeof(double) * ns * kStructRmax);
+    SA.svr = (double*)p; p += align_up(sizeof(double) * ns * mm);
+    SA.scolpiv = (int*)p; p += align_up(sizeof(int) * ns * mm);
+    SA.W = (double*)p;
+    SA.ldw = m;
+    SA.status = st;
+    sg.near_m = (int32_t)mm;
+    GemmSeg last;
+    memset(&last, 0, sizeof(last));
+    k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) err = launch_seg_dense(sg, cs);  // near-diagonal tiles (written)
+    if (err == cudaSuccess) err = launch_struct(segs, 1, SA, cs);  // low-rank tiles (accumulated)
   } else {
     const int S = op.split_slices;
     int64_t a_el = 0;

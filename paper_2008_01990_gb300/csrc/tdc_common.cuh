@@ -87,14 +87,16 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
 // update: list position q names pole p = plist[q] (identity when NULL), whose
 // column of A is acol[p] (identity when NULL); Qhat_pj = zhat_p scol_j /
 // ((D_p - D_org(j)) - tau_j); output column of root j is cpos[j] (identity when
-// NULL).  a_img / b_img / it_* place the segment in the split path's digit
+// NULL).  near_m > 0 marks a structured segment: its dense product only covers
+// the poles within one tile of size near_m of each output column (the rest is
+// low rank).  a_img / b_img / it_* place the segment in the split path's digit
 // images and work lists.
 struct GemmSeg {
   const double* A;
   int64_t lda;
   const int32_t* acol;
   const int32_t* plist;
-  int32_t rows, kk, K, pad;
+  int32_t rows, kk, K, near_m;
   const double* D;
   const int32_t* org;
   const double* tau;
@@ -124,10 +126,28 @@ struct Plan {
   int32_t max_iter;
   int32_t split_min_K;  // merges with K >= this use the split path (0: never)
   int32_t split_slices; // BF16 digit slices per operand
-  GemmSeg* segs;        // 2 M + 1 segments of the current level (split path)
+  GemmSeg* segs;        // 2 M + 1 segments of the current level (split and structured paths)
   __nv_bfloat16* img;   // digit images (split path)
   int64_t img_cap;      // capacity of img in elements
   long long spin_budget;
+  int32_t struct_min_K; // merges with K >= this use the structured path (0: never)
+  int32_t struct_m;     // tile size of the structured path
+};
+
+// Scratch of the structured path: one slot per (segment, row tile I, column tile J).
+struct StructArgs {
+  int m;          // tile size
+  int rmax;       // largest rank kept in low-rank form (larger: dense tile)
+  int Tmax;       // tiles per dimension allotted per segment
+  double tol;     // SRRSC stopping tolerance relative to the tile's largest entry
+  int* srank;     // per slot: rank r, -1 = dense fallback, 0 = empty
+  int* spiv;      // per slot x rmax: root index of pivot column a
+  double* sy;     // per slot x rmax: Theorem-2 generator y_a
+  double* svr;    // per slot x m: column generator v^(r) of the tile's columns
+  int* scolpiv;   // per slot x m: pivot position of the column, -1 if not a pivot
+  double* W;      // per (segment, I) x rmax columns of ldw rows: Qtilde(:, I) Qhat(I, pivots)
+  int64_t ldw;
+  int* status;
 };
 
 // A merge (node) of level l: node i of problem p splits at mid.
@@ -263,6 +283,9 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, cudaStream_t 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
+cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
+cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+constexpr int kStructRmax = 64;
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;

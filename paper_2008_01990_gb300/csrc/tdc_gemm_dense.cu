@@ -21,6 +21,30 @@ namespace tdc {
 namespace {
 constexpr int BM = kDenseBM, BN = kDenseBN, BK = kDenseBK;
 constexpr int kThreads = 256;
+
+__device__ __forceinline__ int lower_bound_i(const int* a, int n, int x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// List positions [qlo, qhi) of the poles within one structured tile (size m) of
+// the tile holding output column j0 (pole indices in [(J-1) m, (J+2) m)).
+__device__ __forceinline__ void near_range(const int* list, int nl, int j0, int m, int K, int& qlo, int& qhi) {
+  const int J = j0 / m;
+  const int plo = J >= 1 ? (J - 1) * m : 0;
+  const int phi = min(K, (J + 2) * m);
+  if (list) {
+    qlo = lower_bound_i(list, nl, plo);
+    qhi = lower_bound_i(list, nl, phi);
+  } else {
+    qlo = min(plo, nl);
+    qhi = min(phi, nl);
+  }
+}
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, int64_t M) {
@@ -55,6 +79,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
     else { r0 = n1 + (rtt - rt0) * BM; rend = n; list = P.v.blist + nd.v0; nl = P.m.nbot[g]; }
     const int j0 = ctile * BN;
     const double* Dk = P.v.Dk + nd.v0;
+    // structured merge: only the poles within one tile of the output columns here
+    int qlo = 0, qhi = nl;
+    if (P.struct_min_K > 0 && K >= P.struct_min_K) near_range(list, nl, j0, P.struct_m, K, qlo, qhi);
     __syncthreads();
     if (tid < BN) {
       const int j = j0 + tid;
@@ -72,11 +99,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
-    for (int k0 = 0; k0 < nl; k0 += BK) {
+    for (int k0 = qlo; k0 < qhi; k0 += BK) {
       __syncthreads();
       if (tid < BK) {
         const int k = k0 + tid;
-        if (k < nl) {
+        if (k < qhi) {
           const int q = list[k];
           sCol[tid] = P.v.kept[nd.v0 + q];
           sDq[tid] = Dk[q];
@@ -154,11 +181,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
     for (int i = 0; i < 8; ++i)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
-    for (int k0 = 0; k0 < sg.kk; k0 += BK) {
+    int qlo = 0, qhi = sg.kk;
+    if (sg.near_m > 0) near_range(sg.plist, sg.kk, j0, sg.near_m, sg.K, qlo, qhi);
+    for (int k0 = qlo; k0 < qhi; k0 += BK) {
       __syncthreads();
       if (tid < BK) {
         const int k = k0 + tid;
-        if (k < sg.kk) {
+        if (k < qhi) {
           const int p = sg.plist ? sg.plist[k] : k;
           sCol[tid] = sg.acol ? sg.acol[p] : p;
           sDq[tid] = sg.D[p];

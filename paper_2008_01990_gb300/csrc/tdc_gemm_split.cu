@@ -125,7 +125,7 @@ __global__ void k_split_segs(Plan P, int level, int64_t M) {
       sg.rows = p ? n - n1 : n1;
       sg.kk = p ? P.m.nbot[g] : P.m.ntop[g];
       sg.K = K;
-      sg.pad = 0;
+      sg.near_m = 0;
       sg.A = nd.src + (p ? n1 : 0);
       sg.lda = nd.lds;
       sg.acol = P.v.kept + nd.v0;

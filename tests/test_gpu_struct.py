@@ -1,0 +1,87 @@
+"""Structured (SRRSC low-rank) eigenvector update on the GPU against the oracle's
+plain FP64 product, element by element, and the eigensolver with the structured
+merge against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import compare_vectors, ratios
+from paper_2008_01990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def tdc():
+    from paper_2008_01990_gb300 import build, tdc as t
+    build.build()
+    t.lib()
+    return t
+
+
+def generators(orc, K, seed):
+    g = inputs.SplitMix64(seed)
+    D = np.sort(g.uniform(K, -1.0, 1.0))
+    z = g.uniform(K, -1.0, 1.0)
+    z /= np.linalg.norm(z)
+    org, tau, _, _ = orc.secular(D, z, 0.8)
+    zh = orc.lowner(D, z, 0.8, org, tau)
+    s = orc.colnorm(D, org, tau, zh)
+    return D, org, tau, zh, s
+
+
+def run(tdc, A, D, org, tau, zh, s, mode, **kw):
+    t = lambda x: torch.tensor(x, device=DEV)
+    At = torch.tensor(np.ascontiguousarray(A.T), device=DEV).t()
+    C = tdc.cauchy_gemm(At, t(D), torch.tensor(org, dtype=torch.int32, device=DEV), t(tau), t(zh), t(s), mode,
+                        tdc.default_opts(**kw), check=True)
+    return C.cpu().numpy()
+
+
+@pytest.mark.parametrize("m,K,tile", [(300, 1000, 128), (513, 700, 64), (256, 2048, 256), (1, 640, 64)])
+def test_cauchy_structured_vs_oracle(tdc, orc, m, K, tile):
+    D, org, tau, zh, s = generators(orc, K, 50 + K)
+    g = inputs.SplitMix64(m)
+    A = g.uniform(m * K, -1.0, 1.0).reshape(m, K) / np.sqrt(K)
+    Co = orc.gemm(A, orc.qhat(D, org, tau, zh, s))
+    C = run(tdc, A, D, org, tau, zh, s, tdc.MERGE_STRUCTURED, lr_tile=tile, lr_tol=1e-15)
+    assert np.max(np.abs(C - Co)) <= 1e-14 * np.sqrt(K)
+
+
+def test_cauchy_structured_error_follows_tolerance(tdc, orc):
+    m, K = 256, 1536
+    D, org, tau, zh, s = generators(orc, K, 77)
+    g = inputs.SplitMix64(9)
+    A = g.uniform(m * K, -1.0, 1.0).reshape(m, K) / np.sqrt(K)
+    Co = orc.gemm(A, orc.qhat(D, org, tau, zh, s))
+    e6 = np.max(np.abs(run(tdc, A, D, org, tau, zh, s, tdc.MERGE_STRUCTURED, lr_tile=128, lr_tol=1e-6) - Co))
+    e12 = np.max(np.abs(run(tdc, A, D, org, tau, zh, s, tdc.MERGE_STRUCTURED, lr_tile=128, lr_tol=1e-12) - Co))
+    assert 1e-12 < e6 <= 1e-5       # the low-rank form is really used
+    assert e12 <= 1e-10 and e12 < e6 / 100
+
+
+def test_cauchy_structured_dense_fallback(tdc, orc):
+    # a tolerance no pivot can meet: every far tile exceeds the rank cap and stays dense
+    m, K = 200, 1024
+    D, org, tau, zh, s = generators(orc, K, 78)
+    g = inputs.SplitMix64(10)
+    A = g.uniform(m * K, -1.0, 1.0).reshape(m, K) / np.sqrt(K)
+    Co = orc.gemm(A, orc.qhat(D, org, tau, zh, s))
+    C = run(tdc, A, D, org, tau, zh, s, tdc.MERGE_STRUCTURED, lr_tile=128, lr_tol=1e-300)
+    assert np.max(np.abs(C - Co)) <= 1e-14 * np.sqrt(K)
+
+
+@pytest.mark.parametrize("n,leaf,fam", [(2048, 64, "toeplitz"), (1500, 32, "c4"), (1024, 32, "uniform"),
+                                        (901, 16, "clement")])
+def test_eig_structured_merge_vs_oracle(tdc, orc, n, leaf, fam):
+    d, e = inputs.family(fam, n, 1)
+    o = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_STRUCTURED, structured_min_K=256, lr_tile=128)
+    lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o, check=True)
+    lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
+    lam_o, Q_o = orc.eig(d, e, leaf=leaf)
+    nT = max(abs(lam_o[0]), abs(lam_o[-1]))
+    assert np.max(np.abs(lam - lam_o)) <= 1e-12 * nT
+    res, orth = ratios(d, e, lam, Q)
+    assert res <= 50 and orth <= 50, (res, orth)
+    compare_vectors(Q, Q_o, lam_o, 1e-8 * nT, 1e-7)
