@@ -303,6 +303,18 @@ def run_ours(args):
                 "fp64_equivalent_tflops": split_flops / (split_ms * 1e-3) / 1e12,
                 "bf16_products_per_fp64_product": products}
         qu_tflops = (split_flops + dense_flops) / ((split_ms + digits_ms + dense_ms) * 1e-3) / 1e12
+    elif stats["struct_flops"] > 0:
+        # structured path: the executed flops (dense near-diagonal tiles and the two thin
+        # products of the low-rank tiles), not the dense flops it avoids
+        sflops = float(stats["struct_flops"])
+        achieved = sflops / (dense_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_gemm_dense (near-diagonal) + k_struct_w + k_struct_apply (FP64)",
+                "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                "executed_flops": sflops, "dense_equivalent_flops": dense_flops,
+                "note": "the phase also holds the FP32 SRRSC pivot searches"}
+        qu_tflops = dense_flops / (dense_ms * 1e-3) / 1e12
     else:
         achieved = dense_flops / (dense_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_gemm_dense (FP64 Q*U with generated U)",

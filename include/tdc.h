@@ -88,6 +88,8 @@ typedef struct {
   float phase_ms[12];
   double gemm_flops[TDC_MAX_LEVELS];     /* algorithmic flops of the Q*U products (2 per multiply-add) */
   double split_flops;                    /* part of gemm_flops computed on the split path */
+  double struct_flops;                   /* flops executed by the structured path (dense near-diagonal
+                                            tiles + the two thin products of the low-rank tiles) */
   int64_t launches;                      /* kernel launches of the call */
 } tdc_stats;
 
@@ -151,6 +153,24 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
  * TDC_ETOOLARGE, TDC_ECUDA. */
 int tdc_eig_noalloc(int64_t n, const double* d, const double* e, double* lam, double* Q, int64_t ldq,
                     const tdc_opts* o, tdc_stream_t stream);
+
+/* Adjoint of the eigen-decomposition (reverse mode): given lam[n], Q (n x n, ldq)
+ * from tdc_eig and the cotangents lam_bar[n] and Q_bar (n x n, ldq; either may be
+ * NULL = zero), writes the cotangents of the tridiagonal entries
+ *   M = diag(lam_bar) + F o skew(Q^T Q_bar),  F_ij = 1/(lam_j - lam_i) (i != j), F_ii = 0,
+ *   d_bar[i] = (Q M Q^T)_{ii},  e_bar[i] = 2 (Q M Q^T)_{i,i+1}.
+ * Requires distinct eigenvalues.  ws of tdc_backward_workspace_size(n) bytes. */
+int tdc_backward_workspace_size(int64_t n, size_t* bytes);
+int tdc_eig_backward(int64_t n, const double* lam, const double* Q, int64_t ldq, const double* lam_bar,
+                     const double* Q_bar, double* d_bar, double* e_bar, void* ws, size_t ws_bytes,
+                     tdc_stream_t stream);
+
+/* Batched adjoint over `batch` problems of the same order n stored back to back
+ * (lam: batch*n, Q and Q_bar: batch*n*n with ld n, d_bar: batch*n, e_bar: batch*(n-1)). */
+int tdc_backward_batched_workspace_size(int32_t batch, int64_t n, size_t* bytes);
+int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const double* Q,
+                             const double* lam_bar, const double* Q_bar, double* d_bar, double* e_bar,
+                             void* ws, size_t ws_bytes, tdc_stream_t stream);
 
 /* Rank-one eigenproblem D + rho z z^T (one merge's secular stage on its own):
  * D[K] strictly ascending, z[K] nonzero, rho > 0.  Writes org[K] (int32: index of

@@ -347,6 +347,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       SA.Tmax = (int)Tmax;
       SA.ldw = ldw;
       SA.status = P.status;
+      SA.flops = P.stats ? &P.stats->struct_flops : nullptr;
       err = launch_struct_segs(P, LL, s);
       if (err == cudaSuccess) err = launch_struct(P.segs, (int)(2 * LL.merges), SA, s);
     }
@@ -405,6 +406,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       g_last_stats.gemm_flops[l] = (double)hs.gemm_flops[l];
     }
     g_last_stats.split_flops = (double)hs.split_flops;
+    g_last_stats.struct_flops = (double)hs.struct_flops;
     g_last_stats.launches = launches;
     g_last_stats.secular_iter_max = hs.iter_max;
     g_last_stats.secular_iter_mean = hs.iter_roots ? (double)hs.iter_sum / (double)hs.iter_roots : 0.0;
@@ -661,6 +663,60 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
     if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, cs);
   }
   return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+int tdc_backward_workspace_size(int64_t n, size_t* bytes) {
+  if (n < 0) return -1;
+  if (!bytes) return -2;
+  *bytes = 256 + sizeof(double) * 2 * (size_t)n * (size_t)n;
+  return TDC_OK;
+}
+
+int tdc_eig_backward(int64_t n, const double* lam, const double* Q, int64_t ldq, const double* lam_bar,
+                     const double* Q_bar, double* d_bar, double* e_bar, void* ws, size_t ws_bytes,
+                     tdc_stream_t stream) {
+  if (n < 0 || n > 0x7fffffff) return -1;
+  if (n == 0) return TDC_OK;
+  if (!lam) return -2;
+  if (!Q) return -3;
+  if (ldq < n) return -4;
+  if (!d_bar) return -7;
+  if (!e_bar && n > 1) return -8;
+  size_t need = 0;
+  tdc_backward_workspace_size(n, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  double* w = (double*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  cudaError_t e = launch_adjoint(1, (int)n, lam, Q, ldq, 0, lam_bar, Q_bar, 0, d_bar, e_bar, w,
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+int tdc_backward_batched_workspace_size(int32_t batch, int64_t n, size_t* bytes) {
+  if (batch < 0) return -1;
+  if (n < 0) return -2;
+  if (!bytes) return -3;
+  *bytes = 256 + sizeof(double) * 2 * (size_t)batch * (size_t)n * (size_t)n;
+  return TDC_OK;
+}
+
+int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const double* Q, const double* lam_bar,
+                             const double* Q_bar, double* d_bar, double* e_bar, void* ws, size_t ws_bytes,
+                             tdc_stream_t stream) {
+  if (batch < 0) return -1;
+  if (n < 0 || n > 0x7fffffff) return -2;
+  if (batch == 0 || n == 0) return TDC_OK;
+  if (!lam) return -3;
+  if (!Q) return -4;
+  if (!d_bar) return -7;
+  if (!e_bar && n > 1) return -8;
+  size_t need = 0;
+  tdc_backward_batched_workspace_size(batch, n, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  double* w = (double*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  const int64_t nn = n * n;
+  cudaError_t e = launch_adjoint(batch, (int)n, lam, Q, n, nn, lam_bar, Q_bar, nn, d_bar, e_bar, w,
+                                 (cudaStream_t)stream);
+  return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
 int tdc_sync_status(tdc_stream_t stream) {

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/tdc.h"
 
 namespace tdc {
@@ -78,6 +80,7 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   int max_K[TDC_MAX_LEVELS];
   unsigned long long gemm_flops[TDC_MAX_LEVELS];
   unsigned long long split_flops;
+  unsigned long long struct_flops;
   unsigned long long iter_sum;
   unsigned long long iter_roots;
   int iter_max;
@@ -148,6 +151,7 @@ struct StructArgs {
   double* W;      // per (segment, I) x rmax columns of ldw rows: Qtilde(:, I) Qhat(I, pivots)
   int64_t ldw;
   int* status;
+  unsigned long long* flops;  // executed multiply-add flops (statistics; NULL when off)
 };
 
 // A merge (node) of level l: node i of problem p splits at mid.
@@ -286,6 +290,9 @@ cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 constexpr int kStructRmax = 64;
+cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q, int64_t ldq, int64_t sQ,
+                           const double* lam_bar, const double* Q_bar, int64_t sQb, double* d_bar,
+                           double* e_bar, double* ws, cudaStream_t s);
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;

@@ -81,7 +81,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
     const double* Dk = P.v.Dk + nd.v0;
     // structured merge: only the poles within one tile of the output columns here
     int qlo = 0, qhi = nl;
-    if (P.struct_min_K > 0 && K >= P.struct_min_K) near_range(list, nl, j0, P.struct_m, K, qlo, qhi);
+    const bool structured = P.struct_min_K > 0 && K >= P.struct_min_K;
+    if (structured) {
+      near_range(list, nl, j0, P.struct_m, K, qlo, qhi);
+      if (P.stats && tid == 0)
+        atomicAdd(&P.stats->struct_flops, 2ull * (unsigned long long)min(BM, rend - r0) *
+                                               (unsigned long long)(qhi - qlo) * (unsigned long long)min(BN, K - j0));
+    }
     __syncthreads();
     if (tid < BN) {
       const int j = j0 + tid;

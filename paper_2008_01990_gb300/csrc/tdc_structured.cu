@@ -276,6 +276,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_struct_w(const GemmSeg* segs, S
         for (int c = 0; c < 4; ++c) acc[i][c] = fma(av[i], bv[c], acc[i][c]);
     }
   }
+  if (S.flops && tid == 0)
+    atomicAdd(S.flops, 2ull * (unsigned long long)min(kBM, sg.rows - r0) * (unsigned long long)(qb - qa) * r);
   double* Wt = S.W + (((int64_t)s * S.Tmax + I) * S.rmax) * S.ldw;
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
@@ -338,6 +340,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_struct_apply(const GemmSeg* seg
     int qa = 0, qb = 0;
     if (r < 0) row_range(sg, I, m, qa, qb);
     const int kn = r > 0 ? r : qb - qa;
+    if (S.flops && tid == 0)
+      atomicAdd(S.flops, 2ull * (unsigned long long)min(kBM, sg.rows - r0) * (unsigned long long)kn *
+                             (unsigned long long)min(kBN, min(sg.K - j0, m - (int)blockIdx.y * kBN)));
     const double* Wt = S.W + (((int64_t)s * S.Tmax + I) * S.rmax) * S.ldw;
     for (int k0 = 0; k0 < kn; k0 += kBK) {
       __syncthreads();

@@ -62,6 +62,7 @@ class Stats(ctypes.Structure):
         ("phase_ms", ctypes.c_float * 12),
         ("gemm_flops", ctypes.c_double * MAX_LEVELS),
         ("split_flops", ctypes.c_double),
+        ("struct_flops", ctypes.c_double),
         ("launches", ctypes.c_int64),
     ]
 
@@ -82,6 +83,7 @@ class Stats(ctypes.Structure):
             "phase_ms": dict(zip(names, list(self.phase_ms))),
             "gemm_flops": list(self.gemm_flops[:L]),
             "split_flops": self.split_flops,
+            "struct_flops": self.struct_flops,
             "launches": self.launches,
         }
 
@@ -249,6 +251,87 @@ def cauchy_gemm(A: torch.Tensor, D: torch.Tensor, org: torch.Tensor, tau: torch.
     if check:
         _check("tdc_cauchy_gemm (device status)", sync_status(stream))
     return C
+
+
+def eig_backward(lam: torch.Tensor, Q: torch.Tensor, lam_bar=None, Q_bar=None, stream=None):
+    """Cotangents (d_bar, e_bar) of the tridiagonal entries (tdc_eig_backward).  Q is the
+    column-major n x n eigenvector matrix; Q_bar any n x n tensor (copied column-major)."""
+    n = lam.numel()
+    dev = lam.device
+    Qc = Q if (Q.stride(0) == 1 and Q.stride(1) >= max(n, 1)) else Q.t().contiguous().t()
+    Qb = None if Q_bar is None else Q_bar.t().contiguous().t()
+    if Qb is not None and Qb.stride(1) != Qc.stride(1):
+        Qc = Q.t().contiguous().t()
+    lb = None if lam_bar is None else lam_bar.contiguous().to(torch.float64)
+    d_bar = torch.empty(n, dtype=torch.float64, device=dev)
+    e_bar = torch.empty(max(n - 1, 0), dtype=torch.float64, device=dev)
+    b = ctypes.c_size_t(0)
+    _check("tdc_backward_workspace_size", lib().tdc_backward_workspace_size(n, ctypes.byref(b)))
+    ws = workspace(b.value, dev)
+    _check("tdc_eig_backward", lib().tdc_eig_backward(n, _ptr(lam), _ptr(Qc), max(Qc.stride(1), 1), _ptr(lb),
+                                                      _ptr(Qb), _ptr(d_bar), _ptr(e_bar), _ptr(ws), ws.numel(),
+                                                      _stream(stream)))
+    return d_bar, e_bar
+
+
+def eig_backward_batched(lam: torch.Tensor, Qs: torch.Tensor, lam_bar=None, Qs_bar=None, stream=None):
+    """Batched adjoint: lam (B, n); Qs the (B, n, n) storage whose [b] is Q_b column-major
+    (i.e. Q_b = Qs[b].t()); Qs_bar likewise."""
+    B, n = lam.shape
+    dev = lam.device
+    d_bar = torch.empty(B, n, dtype=torch.float64, device=dev)
+    e_bar = torch.empty(B, max(n - 1, 0), dtype=torch.float64, device=dev)
+    b = ctypes.c_size_t(0)
+    _check("tdc_backward_batched_workspace_size", lib().tdc_backward_batched_workspace_size(B, n, ctypes.byref(b)))
+    ws = workspace(b.value, dev)
+    lb = None if lam_bar is None else lam_bar.contiguous()
+    qb = None if Qs_bar is None else Qs_bar.contiguous()
+    _check("tdc_eig_backward_batched",
+           lib().tdc_eig_backward_batched(B, n, _ptr(lam.contiguous()), _ptr(Qs.contiguous()), _ptr(lb), _ptr(qb),
+                                          _ptr(d_bar), _ptr(e_bar), _ptr(ws), ws.numel(), _stream(stream)))
+    return d_bar, e_bar
+
+
+class _EighTridiagonal(torch.autograd.Function):
+    """(lam, Q) = eig(T(d, e)) with the backward of tdc_eig_backward; d, e of shape
+    (n,) / (n-1,) or batched (B, n) / (B, n-1)."""
+
+    @staticmethod
+    def forward(ctx, d, e, opts):
+        if d.dim() == 1:
+            lam, Q = eig(d.contiguous(), e.contiguous(), opts)
+            ctx.save_for_backward(lam, Q)
+            ctx.batched = False
+            return lam, Q
+        import numpy as np
+        B, n = d.shape
+        dev = d.device
+        dd = d.contiguous().reshape(-1)
+        ee = torch.zeros(B, n, dtype=torch.float64, device=dev)
+        ee[:, : n - 1] = e
+        lam = torch.empty(B, n, dtype=torch.float64, device=dev)
+        Qs = torch.empty(B, n, n, dtype=torch.float64, device=dev)
+        sizes = np.full(B, n, dtype=np.int64)
+        eig_batched(sizes, dd, ee.reshape(-1), np.arange(B, dtype=np.int64) * n,
+                    np.arange(B, dtype=np.int64) * n * n, lam.reshape(-1), Qs.reshape(-1), opts)
+        ctx.save_for_backward(lam, Qs)
+        ctx.batched = True
+        return lam, Qs.transpose(1, 2)
+
+    @staticmethod
+    def backward(ctx, lam_bar, Q_bar):
+        lam, Qx = ctx.saved_tensors
+        if not ctx.batched:
+            d_bar, e_bar = eig_backward(lam, Qx, lam_bar, Q_bar)
+        else:
+            qsb = None if Q_bar is None else Q_bar.transpose(1, 2).contiguous()
+            d_bar, e_bar = eig_backward_batched(lam, Qx, lam_bar, qsb)
+        return d_bar, e_bar, None
+
+
+def eigh_tridiagonal(d: torch.Tensor, e: torch.Tensor, opts: Opts | None = None):
+    """Differentiable eigen-decomposition of the symmetric tridiagonal (d, e)."""
+    return _EighTridiagonal.apply(d, e, opts)
 
 
 def sync_status(stream=None) -> int:
