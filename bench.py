@@ -230,6 +230,46 @@ def run_qhat(args):
     return 0
 
 
+def run_batched(args):
+    """The batched workload: 4096 tridiagonals, n_b uniform in [64, 2048] (seed 3), entries
+    uniform(-1,1) (seed 3 + b), solved by one tdc_eig_batched call replayed from a CUDA
+    graph, options chosen by the autotuner (outside the timed region)."""
+    import torch
+    from paper_2008_01990_gb300 import autotune, inputs, tdc
+    dev = torch.device("cuda", 0)
+    sizes = inputs.batched_sizes(4096, 64, 2048, 3)
+    d, e, offs = inputs.batched_uniform(sizes, 3)
+    qoffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
+    dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+    opts = autotune.tune_batched(sizes, dt, et, offs[:-1], cache_path=None)
+    lam = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
+    Q = torch.empty(int(qoffs[-1]), dtype=torch.float64, device=dev)
+    ws = tdc.workspace(tdc.batched_workspace_size(sizes, opts), dev)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, opts, ws=ws, stream=s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, opts, ws=ws, stream=s)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = tdc.sync_status()
+    print(json.dumps({"workload": "batched4096", "ms_per_batch": ms, "problems_per_s": 4096 / (ms * 1e-3),
+                      "leaf": opts.leaf, "split_min_K": opts.split_min_K, "status": st,
+                      "sum_n": int(sizes.sum()), "q_bytes": int(qoffs[-1]) * 8}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -409,7 +449,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192"])
+    ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
+                                                          "batched4096"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -419,6 +460,8 @@ def main():
         return run_reference(args)
     if args.workload == "qhat8192":
         return run_qhat(args)
+    if args.workload == "batched4096":
+        return run_batched(args)
     return run_ours(args)
 
 

@@ -57,6 +57,7 @@ struct HostPlan {
   std::vector<int64_t> max_tiles;   // GEMM tile upper bound per level
   int64_t img_elems = 0;            // digit images of the split path (bf16 elements)
   int split_S = 0;                  // 0: split path off
+  std::vector<std::vector<std::pair<int64_t, int64_t>>> split_chunks;  // per level: merge ranges
   int struct_m = 0;                 // 0: structured path off
   int64_t struct_slots = 0;         // SRRSC slots (segments x Tmax^2)
   int64_t struct_w = 0;             // W doubles
@@ -91,20 +92,52 @@ static bool split_enabled(const tdc_opts& o) {
   return o.merge_mode == TDC_MERGE_SPLIT || o.merge_mode == TDC_MERGE_AUTO;
 }
 
+// Digit images of a merge of order nm on the split path (upper bound: kk, K <= nm).
+static int64_t merge_img_bound(int64_t nm, int S) {
+  const int64_t n1 = (nm + 1) / 2;
+  return split_img_elems(n1, n1, nm, nm, S);
+}
+
+// The split path materialises digit images for the merges of a level; many-problem
+// levels are processed in chunks of consecutive merges whose images fit a cap
+// (at least the largest single merge).
+static constexpr int64_t kSplitImgCap = (int64_t)4 << 30;  // bf16 elements (8 GiB)
+
 static void plan_split(HostPlan& H, const tdc_opts& o) {
   H.img_elems = 0;
   H.split_S = split_enabled(o) ? o.split_slices : 0;
+  H.split_chunks.assign(H.T, {});
   if (!H.split_S) return;
-  for (int l = 0; l < H.T; ++l) {
-    int64_t tot = 0;
+  int64_t biggest = 0;
+  for (int l = 0; l < H.T; ++l)
     for (auto& p : H.prob) {
       if (p.depth <= l) break;
-      const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;  // largest node of the level
-      if (nm < o.split_min_K) continue;                          // K <= nm < split_min_K
-      const int64_t n1 = (nm + 1) / 2;
-      tot += (((int64_t)1) << l) * split_img_elems(n1, n1, nm, nm, H.split_S);
+      const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;
+      if (nm >= o.split_min_K) biggest = std::max(biggest, merge_img_bound(nm, H.split_S));
     }
-    H.img_elems = std::max(H.img_elems, tot);
+  const int64_t cap = std::max(kSplitImgCap, biggest);
+  for (int l = 0; l < H.T; ++l) {
+    const LevelLaunch& L = H.levels[l];
+    if (L.max_n < o.split_min_K) continue;
+    int64_t g = 0, start = 0, acc = 0;
+    for (int pi = 0; pi < L.nprob_act; ++pi) {
+      const Problem& p = H.prob[pi];
+      const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;
+      const int64_t per = nm >= o.split_min_K ? merge_img_bound(nm, H.split_S) : 0;
+      for (int64_t i = 0; i < (((int64_t)1) << l); ++i, ++g) {
+        if (acc + per > cap && g > start) {
+          H.split_chunks[l].push_back({start, g});
+          H.img_elems = std::max(H.img_elems, acc);
+          start = g;
+          acc = 0;
+        }
+        acc += per;
+      }
+    }
+    if (g > start) {
+      H.split_chunks[l].push_back({start, g});
+      H.img_elems = std::max(H.img_elems, acc);
+    }
   }
 }
 
@@ -321,7 +354,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   // kernel launches: problem upload, corner modification, leaves, 9 per level, output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
-    if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4;
+    if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4 * (int64_t)H.split_chunks[l].size();
     if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
       launches += 2 + 2 * ((H.levels[l].max_n + H.struct_m - 1) / H.struct_m);
   }
@@ -358,16 +391,19 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     span(4, a3, a4);
     size_t a6 = a4;
     if (err == cudaSuccess && P.split_min_K > 0 && LL.max_n >= P.split_min_K) {
-      cudaEvent_t mid = nullptr;
-      if (timing) {
-        cudaEventCreate(&mid);
-        evs.push_back(mid);
+      for (auto& ch : H.split_chunks[l]) {
+        cudaEvent_t mid = nullptr;
+        if (timing) {
+          cudaEventCreate(&mid);
+          evs.push_back(mid);
+        }
+        const size_t b5 = timing ? evs.size() - 1 : 0;
+        const size_t b4 = a6;
+        if (err == cudaSuccess) err = launch_gemm_split(P, LL, ch.first, ch.second, s, mid);
+        a6 = mark();
+        span(5, b4, b5);
+        span(6, b5, a6);
       }
-      const size_t a5 = timing ? evs.size() - 1 : 0;
-      err = launch_gemm_split(P, LL, s, mid);
-      a6 = mark();
-      span(5, a4, a5);
-      span(6, a5, a6);
     }
     if (err == cudaSuccess) err = launch_copy_deflated(P, LL, s);
     span(7, a6, mark());

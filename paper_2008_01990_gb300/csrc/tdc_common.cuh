@@ -283,7 +283,8 @@ cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
                             double* tau, double* zhat, double* s, int* status, cudaStream_t st);
 cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s);
-cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, cudaStream_t s, cudaEvent_t mid);
+cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, cudaStream_t s,
+                              cudaEvent_t mid);
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);

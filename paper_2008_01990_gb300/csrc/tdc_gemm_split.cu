@@ -111,11 +111,12 @@ int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, in
 // ---------------------------------------------------------------------------
 // Segments of a tree level: one per (merge, top/bottom part).
 // ---------------------------------------------------------------------------
-__global__ void k_split_segs(Plan P, int level, int64_t M) {
+__global__ void k_split_segs(Plan P, int level, int64_t g0, int64_t g1) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int S = P.split_slices;
+  const int64_t M = g1 - g0;
   int64_t ia = 0, ib = 0, it = 0, e = 0;
-  for (int64_t g = 0; g < M; ++g) {
+  for (int64_t g = g0; g < g1; ++g) {
     const Node nd = make_node(P, level, g);
     const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
     const int K = P.m.K[g];
@@ -152,7 +153,7 @@ __global__ void k_split_segs(Plan P, int level, int64_t M) {
         it += RT * CT;
         if (P.stats) atomicAdd(&P.stats->split_flops, 2ull * (unsigned long long)sg.rows * sg.kk * (unsigned long long)K);
       }
-      P.segs[2 * g + p] = sg;
+      P.segs[2 * (g - g0) + p] = sg;
     }
   }
   GemmSeg last;
@@ -428,15 +429,17 @@ static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, int S, int* s
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, cudaStream_t s, cudaEvent_t mid) {
-  if (P.split_min_K <= 0 || P.segs == nullptr) return cudaSuccess;
-  k_split_segs<<<1, 32, 0, s>>>(P, L.level, L.merges);
+cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, cudaStream_t s,
+                              cudaEvent_t mid) {
+  if (P.split_min_K <= 0 || P.segs == nullptr || g1 <= g0) return cudaSuccess;
+  k_split_segs<<<1, 32, 0, s>>>(P, L.level, g0, g1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_split_digits(P.segs, (int)(2 * L.merges), P.split_slices, P.img, s);
+  const int nseg = (int)(2 * (g1 - g0));
+  e = launch_split_digits(P.segs, nseg, P.split_slices, P.img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
-  return launch_split_mma(P.segs, (int)(2 * L.merges), P.split_slices, P.status, P.spin_budget, P.img, s);
+  return launch_split_mma(P.segs, nseg, P.split_slices, P.status, P.spin_budget, P.img, s);
 }
 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,

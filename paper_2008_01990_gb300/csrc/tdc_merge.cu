@@ -483,7 +483,9 @@ __global__ void __launch_bounds__(256) k_rotate(Plan P, int level) {
 }
 
 cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
-  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), kRotChainsPerGrid);
+  // chains are spread over grid.z; small merges (many per level) need few
+  const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRotChainsPerGrid, L.max_n / 256));
+  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), gz);
   k_rotate<<<grid, 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
 }
@@ -884,7 +886,8 @@ __global__ void __launch_bounds__(256) k_copy_defl(Plan P, int level) {
 }
 
 cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
-  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), 64);
+  const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, L.max_n / 256));
+  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), gz);
   k_copy_defl<<<grid, 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
 }

@@ -1,0 +1,98 @@
+"""Batched eigensolves (tdc_eig_batched): replay under a CUDA graph, the autotuner,
+and the full-size batched workload (4096 tridiagonals of orders uniform in
+[64, 2048]) checked problem by problem on a sample against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import compare_vectors, ratios
+from paper_2008_01990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def tdc():
+    from paper_2008_01990_gb300 import build, tdc as t
+    build.build()
+    t.lib()
+    return t
+
+
+def batch(sizes, seed):
+    d, e, offs = inputs.batched_uniform(sizes, seed)
+    qoffs = np.concatenate([[0], np.cumsum(np.asarray(sizes, dtype=np.int64) ** 2)])
+    return d, e, offs, qoffs
+
+
+def test_graph_replay_matches_direct_call(tdc):
+    sizes = inputs.batched_sizes(64, 64, 700, 31)
+    d, e, offs, qoffs = batch(sizes, 31)
+    d2, e2, _, _ = batch(sizes, 32)
+    o = tdc.default_opts(leaf=32)
+    dt = torch.tensor(d, device=DEV)
+    et = torch.tensor(e, device=DEV)
+    lam = torch.zeros(int(offs[-1]), dtype=torch.float64, device=DEV)
+    Q = torch.zeros(int(qoffs[-1]), dtype=torch.float64, device=DEV)
+    ws = tdc.workspace(tdc.batched_workspace_size(sizes, o), DEV)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, o, ws=ws, stream=s)  # warm-up
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, o, ws=ws, stream=s)
+    for dd, ee in ((d, e), (d2, e2)):
+        dt.copy_(torch.tensor(dd))
+        et.copy_(torch.tensor(ee))
+        g.replay()
+        torch.cuda.synchronize()
+        lam_g, Q_g = lam.cpu().numpy(), Q.cpu().numpy()
+        lam_r, Q_r = tdc.eig_batched(sizes, torch.tensor(dd, device=DEV), torch.tensor(ee, device=DEV),
+                                     offs[:-1], qoffs[:-1], torch.zeros_like(lam), torch.zeros_like(Q), o,
+                                     check=True)
+        assert np.array_equal(lam_g, lam_r.cpu().numpy())
+        assert np.array_equal(Q_g, Q_r.cpu().numpy())
+    assert tdc.sync_status() == 0
+
+
+def test_autotuner_picks_and_caches(tdc, tmp_path):
+    from paper_2008_01990_gb300 import autotune
+    sizes = inputs.batched_sizes(48, 64, 600, 41)
+    d, e, offs, qoffs = batch(sizes, 41)
+    cache = str(tmp_path / "tune.json")
+    o = autotune.tune_batched(sizes, torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), offs[:-1],
+                              sample=16, cache_path=cache)
+    assert o.leaf in autotune.LEAVES and o.split_min_K in autotune.SPLIT_MIN_K
+    o2 = autotune.tune_batched(sizes, None, None, None, cache_path=cache)  # served from the cache
+    assert (o2.leaf, o2.split_min_K) == (o.leaf, o.split_min_K)
+
+
+def test_c3_full_batch_sampled(tdc, orc):
+    """4096 problems, n_b uniform in [64, 2048] (seed 3), d, e uniform(-1,1) (seed 3+b),
+    one call; every eigenvalue sorted and finite, sampled problems against the oracle."""
+    sizes = inputs.batched_sizes(4096, 64, 2048, 3)
+    d, e, offs, qoffs = batch(sizes, 3)
+    o = tdc.default_opts(leaf=32)
+    lam = torch.empty(int(offs[-1]), dtype=torch.float64, device=DEV)
+    Q = torch.empty(int(qoffs[-1]), dtype=torch.float64, device=DEV)
+    tdc.eig_batched(sizes, torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), offs[:-1], qoffs[:-1],
+                    lam, Q, o, check=True)
+    lam_h = lam.cpu().numpy()
+    assert np.all(np.isfinite(lam_h))
+    for b in range(len(sizes)):
+        lb = lam_h[offs[b]:offs[b] + sizes[b]]
+        assert np.all(np.diff(lb) >= 0)
+    pick = [int(np.argmin(sizes)), int(np.argmax(sizes)), 0, 1000, 2047, 4095]
+    for b in pick:
+        nb = int(sizes[b])
+        db, eb = d[offs[b]:offs[b] + nb], e[offs[b]:offs[b] + nb - 1]
+        lb = lam_h[offs[b]:offs[b] + nb]
+        Qb = Q[int(qoffs[b]):int(qoffs[b]) + nb * nb].cpu().numpy().reshape(nb, nb, order="F")
+        lo, Qo = orc.eig(db, eb, leaf=32)
+        nT = max(abs(lo[0]), abs(lo[-1]))
+        assert np.max(np.abs(lb - lo)) <= 1e-12 * nT
+        res, orth = ratios(db, eb, lb, Qb)
+        assert res <= 50 and orth <= 50
+        compare_vectors(Qb, Qo, lo, 1e-8 * nT, 1e-7)
