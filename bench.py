@@ -270,6 +270,61 @@ def run_batched(args):
     return 0
 
 
+def run_backward(args):
+    """The backward workload: 256 tridiagonals of order 512 (d, e uniform(-1,1), seed 5,
+    redrawn until the smallest eigen-gap is >= 1e-5 ||T||), loss sum w_j lam_j + sum G_ij Q_ij
+    with w, G ~ N(0,1); one step = batched forward solve + batched adjoint."""
+    import torch
+    from paper_2008_01990_gb300 import inputs, tdc
+    dev = torch.device("cuda", 0)
+    B, n = 256, 512
+    ds, es, ws_, Gs, gaps, draws = inputs.backward_problems(B, n, 5)
+    d = torch.tensor(ds, device=dev)
+    e = torch.tensor(es, device=dev)
+    w = torch.tensor(ws_, device=dev)
+    G = torch.tensor(Gs, device=dev)
+    opts = tdc.default_opts(leaf=32)
+
+    def step():
+        dd = d.clone().requires_grad_(True)
+        ee = e.clone().requires_grad_(True)
+        lam, Q = tdc.eigh_tridiagonal(dd, ee, opts)
+        loss = (w * lam).sum() + (G * Q).sum()
+        loss.backward()
+        return dd.grad, ee.grad
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # adjoint alone (the two n^3 products per problem)
+    lam, Q = tdc.eigh_tridiagonal(d, e, opts)
+    Qs = Q.transpose(1, 2).contiguous()
+    Gs_t = G.transpose(1, 2).contiguous()
+    tdc.eig_backward_batched(lam, Qs, w, Gs_t)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    for _ in range(args.steps):
+        tdc.eig_backward_batched(lam, Qs, w, Gs_t)
+    a1.record()
+    torch.cuda.synchronize()
+    ams = a0.elapsed_time(a1) / args.steps
+    flops = B * 4.0 * n ** 3
+    print(json.dumps({"workload": "backward256x512", "ms_forward_backward": ms, "ms_adjoint": ams,
+                      "adjoint_tflops_fp64": flops / (ams * 1e-3) / 1e12, "min_gap_rel": float(gaps.min()),
+                      "draws": int(draws)}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -420,7 +475,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if args.merge == "dense" else "f64 (Q*U as bf16 digit products, fp32 accumulate)",
         "data": "synthetic",
-        "config": {"workload": desc, "merge": args.merge, "l2": "no flush: Q and workspace (4 GiB) exceed L2",
+        "config": {"workload": desc, "merge": args.merge, "l2": "no flush: Q and workspace (%.1f GiB) exceed the 129 MB L2" % ((8 * n * n + wsb.numel()) / 2**30),
                    "parallelism": "replicas" if ws_n > 1 else "single"},
         "roofline": roof,
         "qu_tflops_fp64_equivalent": qu_tflops,
@@ -450,7 +505,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
-                                                          "batched4096"])
+                                                          "batched4096", "backward256"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -462,6 +517,8 @@ def main():
         return run_qhat(args)
     if args.workload == "batched4096":
         return run_batched(args)
+    if args.workload == "backward256":
+        return run_backward(args)
     return run_ours(args)
 
 

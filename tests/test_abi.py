@@ -61,3 +61,18 @@ def test_host_argument_checks(lib):
                                bogus, bogus, bogus, 1 << 30, None, None) == -1001
     assert lib.tdc_rank_one(4, bogus, bogus, -1.0, bogus, bogus, bogus, bogus, 8, bogus, 256, None) == -4
     assert tdc.strerror(tdc.TDC_ENOWS).startswith("workspace")
+
+
+@pytest.mark.parametrize("bad", [dict(leaf=1), dict(leaf=65), dict(merge_mode=4), dict(max_iter=0),
+                                 dict(lr_tile=100), dict(split_slices=2), dict(split_slices=8),
+                                 dict(split_min_K=0), dict(spin_budget=0), dict(lr_tol=0.0)])
+def test_invalid_options_rejected_on_host(lib, bad):
+    """Every option outside its documented range is refused before anything is
+    enqueued (the workspace query validates the same way)."""
+    from paper_2008_01990_gb300 import tdc
+    o = tdc.default_opts(**bad)
+    P = ctypes.c_void_p
+    bogus = P(0x1000)
+    assert lib.tdc_eig(4, bogus, bogus, bogus, bogus, 4, bogus, 1 << 30, ctypes.byref(o), None) == -9
+    nb = ctypes.c_size_t(0)
+    assert lib.tdc_workspace_size(4, ctypes.byref(o), ctypes.byref(nb)) == -2

@@ -97,3 +97,45 @@ def test_eig_split_merge_vs_oracle(tdc, orc, n, leaf, fam):
     res, orth = ratios(d, e, lam, Q)
     assert res <= 50 and orth <= 50, (res, orth)
     compare_vectors(Q, Q_o, lam_o, 1e-8 * nT, 1e-7)
+
+
+def sturm_count(d, e, x):
+    x = np.atleast_1d(np.asarray(x, dtype=float))
+    cnt = np.zeros(x.shape, dtype=np.int64)
+    q = d[0] - x
+    q = np.where(q == 0, -1e-300, q)
+    cnt += q < 0
+    for i in range(1, len(d)):
+        q = (d[i] - x) - e[i - 1] ** 2 / q
+        q = np.where(q == 0, -1e-300, q)
+        cnt += q < 0
+    return cnt
+
+
+def test_c4_split_32768_sampled(tdc):
+    """n = 32768, d uniform(0,1), e = 1 (seed 4), split merge: sampled eigenvalues
+    pinned by Sturm counts, trace invariant, residual and orthogonality on sampled
+    columns (the oracle is too slow at this order; these properties hold at any size)."""
+    n = 32768
+    d, e = inputs.c4_tridiag(n, 4)
+    dt, et = torch.tensor(d, device=DEV), torch.tensor(e, device=DEV)
+    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_SPLIT), check=True)
+    lh = lam.cpu().numpy()
+    nT = max(abs(lh[0]), abs(lh[-1]))
+    assert np.all(np.diff(lh) >= 0)
+    assert abs(lh.sum() - d.sum()) <= 1e-12 * n * nT
+    g = np.random.default_rng(1)
+    ks = np.sort(g.choice(n, 64, replace=False))
+    tol = 1e-12 * nT
+    assert np.all(sturm_count(d, e, lh[ks] - tol) <= ks)
+    assert np.all(sturm_count(d, e, lh[ks] + tol) >= ks + 1)
+    cols = torch.tensor(np.sort(g.choice(n, 256, replace=False)), device=DEV)
+    Qs = Q[:, cols]
+    Tq = dt[:, None] * Qs
+    Tq[1:] += et[:, None] * Qs[:-1]
+    Tq[:-1] += et[:, None] * Qs[1:]
+    res = torch.abs(Tq - Qs * lam[cols]).sum(dim=0).max().item() / (n * nT * EPS)
+    Gm = Qs.t() @ Q
+    Gm[torch.arange(256, device=DEV), cols] -= 1.0
+    orth = torch.abs(Gm).sum(dim=1).max().item() / (n * EPS)
+    assert res <= 50 and orth <= 50, (res, orth)
