@@ -339,7 +339,9 @@ def run_ours(args):
     n = d_np.size
     mode = {"dense": tdc.MERGE_DENSE, "auto": tdc.MERGE_AUTO, "structured": tdc.MERGE_STRUCTURED,
             "split": tdc.MERGE_SPLIT}[args.merge]
-    opts = tdc.default_opts(leaf=leaf, merge_mode=mode)
+    # statistics on: the library records CUDA events around its phases on the call's
+    # stream, so the per-kernel times below come from the timed steps themselves
+    opts = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1)
     d = torch.tensor(d_np, device=dev)
     e = torch.tensor(e_np, device=dev)
     lam = torch.empty(n, dtype=torch.float64, device=dev)
@@ -362,9 +364,11 @@ def run_ours(args):
     sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    phases = []
     e0.record(stream)
     for _ in range(args.steps):
         step()
+        phases.append(tdc.get_stats())
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -374,12 +378,7 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = t.item()
         dist.barrier()
-    # per-phase CUDA-event times inside the library (same stream) and algorithmic flops
-    opts_st = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1)
-    phases = []
-    for _ in range(max(1, min(3, args.steps))):
-        tdc.eig(d, e, opts_st, ws=wsb, lam=lam, Q=Q, stream=stream)
-        phases.append(tdc.get_stats())
+    # per-phase CUDA-event times of the timed steps (same stream) and algorithmic flops
     stats = phases[-1]
     S = opts.split_slices
     products = S * (S + 1) // 2
@@ -392,9 +391,11 @@ def run_ours(args):
     if split_flops > 0 and split_ms > 0:
         achieved = split_flops * products / (split_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": "k_gemm_split (BF16 digit products, tcgen05, TMEM FP32 levels)",
-                "achieved": achieved, "peak": pk["bf16_tflops_sustained"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_tflops_sustained"], "traffic": None,
-                "peak_kind": "bf16_tflops_sustained of %s (kernel timed inside a long step)" % pk_kind,
+                "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                "peak_kind": "bf16_tflops (burst) of %s: the kernel runs in bursts of tens of ms and the SM "
+                             "clock stays at its maximum (see clocks)" % pk_kind,
+                "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],
                 "fp64_equivalent_tflops": split_flops / (split_ms * 1e-3) / 1e12,
                 "bf16_products_per_fp64_product": products}
         qu_tflops = (split_flops + dense_flops) / ((split_ms + digits_ms + dense_ms) * 1e-3) / 1e12

@@ -253,30 +253,91 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 }
 
 // ---------------------------------------------------------------------------
-// The tensor-core GEMM over the digit images.  128 threads, one CTA per SM,
-// persistent over the tile list.  Thread 0 runs a kStages-deep pipeline: bulk
-// copies (cp.async.bulk, completion on full[st]) keep up to kStages-1 k-steps
-// in flight while the S(S+1)/2 MMAs of the current step are queued; each step's
-// commit frees its stage (empty[st]).  All four warps then combine the S level
-// accumulators of the tile in FP64 and store it.
+// The tensor-core GEMM over the digit images: one CTA per SM, persistent over
+// the tile list, three roles in separate warps so that no role waits on another
+// one's bookkeeping:
+//   warp 5 (one thread)  producer: bulk copies of one k-step (S A-slices + S
+//                        B-slices, contiguous) into a kStages ring, completion
+//                        on full[st]; a stage is reused once empty[st] fires;
+//   warp 4 (one thread)  MMA issuer: waits full[st], issues the S wide MMAs of the
+//                        step, commits them to empty[st]; after a tile's last
+//                        step commits to tfull, and starts the next tile only
+//                        after the epilogue has released the accumulators
+//                        (tempty);
+//   warps 0-3            epilogue: TMEM lane quarter w of the tile, the S level
+//                        accumulators combined in FP64, released, then stored.
+// The producer runs ahead into the next tile while the epilogue drains, and S is
+// a compile-time constant so that the issue loop is straight-line code (every
+// descriptor a constant offset of the stage base).  Every wait is bounded; a
+// role that gives up raises s_fail, which the other roles poll, and the CTA
+// reports TDC_ETIMEOUT after its copies and MMAs in flight have landed.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int nseg, int S,
-                                                       const __nv_bfloat16* img, int* status, long long budget) {
+namespace {
+constexpr int kMmaWarp = 4, kLoadWarp = 5, kSplitThreads = 192;
+
+__device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, long long budget,
+                                             volatile int* fail) {
+  for (long long i = 0; i < budget; ++i) {
+    if (umma::mbar_try_wait(bar, parity)) return true;
+    if ((i & 255) == 255 && *fail) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(bar)) : "memory");
+}
+
+struct TileRef {
+  const GemmSeg* sg;
+  int rt, ct, KB;
+};
+
+// tile w of the level: tiles in groups of kGroupRows row tiles, column tile by
+// column tile, so that the CTAs running together share A row tiles and B column
+// tiles in L2
+__device__ __forceinline__ TileRef tile_ref(const GemmSeg* segs, int nseg, int64_t w) {
+  TileRef t;
+  t.sg = &segs[find_seg(segs, nseg, w, 2)];
+  const int64_t local = w - t.sg->it_t;
+  const int CT = (int)cdiv(t.sg->K, BN);
+  const int RT = (int)cdiv(t.sg->rows, BM);
+  t.KB = (int)cdiv(t.sg->kk, BK);
+  const int grp = (int)(local / ((int64_t)kGroupRows * CT));
+  const int within = (int)(local % ((int64_t)kGroupRows * CT));
+  const int gr = min(kGroupRows, RT - grp * kGroupRows);
+  t.rt = grp * kGroupRows + within % gr;
+  t.ct = within / gr;
+  return t;
+}
+}  // namespace
+
+template <int S>
+__global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* segs, int nseg,
+                                                                 const __nv_bfloat16* img, int* status,
+                                                                 long long budget) {
   extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr uint32_t a_bytes = S * kATileElems * 2, b_bytes = S * kBTileElems * 2;
+  constexpr uint32_t stage_bytes = a_bytes + b_bytes;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t total = segs[nseg].it_t;
   if ((int64_t)blockIdx.x >= total) return;
-  const uint32_t a_bytes = (uint32_t)(S * kATileElems * 2), b_bytes = (uint32_t)(S * kBTileElems * 2);
-  const uint32_t stage_bytes = a_bytes + b_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * stage_bytes);
   uint64_t* empty = full + kStages;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(empty + kStages);
+  uint64_t* tfull = empty + kStages;
+  uint64_t* tempty = tfull + 1;
+  uint64_t* done = tempty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int s_fail;
+  volatile int* vfail = &s_fail;
   if (tid == 0) {
     for (int i = 0; i < kStages; ++i) {
       umma::mbar_init(&full[i], 1);
       umma::mbar_init(&empty[i], 1);
     }
+    umma::mbar_init(tfull, 1);
+    umma::mbar_init(tempty, 4);
+    umma::mbar_init(done, 1);
     umma::fence_mbar_init();
     s_fail = 0;
   }
@@ -289,122 +350,152 @@ __global__ void __launch_bounds__(128, 1) k_gemm_split(const GemmSeg* segs, int 
   umma::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t sbase = umma::smem_u32(smem);
-  long long step = 0;  // k-steps consumed by this CTA (stage = step % kStages)
-  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
-    const int si = find_seg(segs, nseg, w, 2);
-    const GemmSeg& sg = segs[si];
-    const int64_t local = w - sg.it_t;
-    const int CT = (int)cdiv(sg.K, BN);
-    const int KB = (int)cdiv(sg.kk, BK);
-    // tiles in groups of kGroupRows row tiles, column tile by column tile, so that
-    // the CTAs running together share A row tiles and B column tiles in L2
-    const int RT = (int)cdiv(sg.rows, BM);
-    const int grp = (int)(local / ((int64_t)kGroupRows * CT));
-    const int within = (int)(local % ((int64_t)kGroupRows * CT));
-    const int gr = min(kGroupRows, RT - grp * kGroupRows);
-    const int rt = grp * kGroupRows + within % gr, ct = within / gr;
-    const uint8_t* aimg = reinterpret_cast<const uint8_t*>(img + sg.a_img + (int64_t)rt * KB * S * kATileElems);
-    const uint8_t* bimg = reinterpret_cast<const uint8_t*>(img + sg.b_img + (int64_t)ct * KB * S * kBTileElems);
-    if (tid == 0 && KB > 0) {
+
+  if (warp == kLoadWarp) {
+    if (lane == 0) {
+      long long g = 0;  // k-steps loaded by this CTA (stage g % kStages, use g / kStages)
       bool ok = true;
-      // load of k-step kb of this tile into stage (step + kb) % kStages; the stage is
-      // free once the MMAs of the step kStages earlier have completed
-      auto issue_load = [&](int kb) {
-        const long long g = step + kb;
-        const int st = (int)(g % kStages);
-        if (g >= kStages) ok = ok && umma::mbar_wait(&empty[st], (uint32_t)(((g - kStages) / kStages) & 1), budget);
-        uint8_t* dst = smem + st * stage_bytes;
-        umma::mbar_arrive_expect_tx(&full[st], stage_bytes);
-        umma::bulk_g2s(dst, aimg + (int64_t)kb * a_bytes, a_bytes, &full[st]);
-        umma::bulk_g2s(dst + a_bytes, bimg + (int64_t)kb * b_bytes, b_bytes, &full[st]);
-      };
-      const int pre = KB < kStages - 1 ? KB : kStages - 1;
-      for (int kb = 0; kb < pre && ok; ++kb) issue_load(kb);
-      for (int kb = 0; kb < KB && ok; ++kb) {
-        const long long g = step + kb;
-        const int st = (int)(g % kStages);
-        ok = umma::mbar_wait(&full[st], (uint32_t)((g / kStages) & 1), budget);
-        if (!ok) break;
-        umma::tc_fence_after();
-        const uint32_t a0 = sbase + st * stage_bytes;
-        const uint32_t b0 = a0 + a_bytes;
-        // The S B-slices are stacked along N in shared memory and level m's
-        // accumulator starts at TMEM column m*BN, so A_s against the stacked slices
-        // B_0..B_{S-1-s} (N = BN (S - s)) drops every product A_s B_t into level s+t:
-        // one wide MMA per A-slice (split at N = 256) instead of one per digit pair.
-        for (int s = 0; s < S; ++s) {
-          const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2, 128, BK * 16);
-          const int ncols = BN * (S - s);
-          for (int off = 0; off < ncols; off += 256) {
-            const int nn = ncols - off < 256 ? ncols - off : 256;
-            const uint64_t bd = umma::sdesc(b0 + (off / BN) * kBTileElems * 2, 128, BK * 16);
-            umma::mma_bf16(tmem + s * BN + off, ad, bd, umma::idesc_bf16(BM, nn), (kb > 0 || s > 0) ? 1u : 0u);
+      for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
+        const TileRef t = tile_ref(segs, nseg, w);
+        const uint8_t* ai = reinterpret_cast<const uint8_t*>(img + t.sg->a_img + (int64_t)t.rt * t.KB * S * kATileElems);
+        const uint8_t* bi = reinterpret_cast<const uint8_t*>(img + t.sg->b_img + (int64_t)t.ct * t.KB * S * kBTileElems);
+        for (int kb = 0; kb < t.KB; ++kb, ++g) {
+          const int st = (int)(g % kStages);
+          if (g >= kStages && !wait_or_fail(&empty[st], (uint32_t)(((g - kStages) / kStages) & 1), budget, vfail)) {
+            ok = false;
+            break;
           }
+          uint8_t* dst = smem + st * stage_bytes;
+          umma::mbar_arrive_expect_tx(&full[st], stage_bytes);
+          umma::bulk_g2s(dst, ai + (int64_t)kb * a_bytes, a_bytes, &full[st]);
+          umma::bulk_g2s(dst + a_bytes, bi + (int64_t)kb * b_bytes, b_bytes, &full[st]);
         }
-        umma::mma_commit(&empty[st]);
-        if (kb + kStages - 1 < KB) issue_load(kb + kStages - 1);
       }
-      // the last commit covers every MMA of the tile
-      if (ok) {
-        const long long g = step + KB - 1;
-        ok = umma::mbar_wait(&empty[g % kStages], (uint32_t)((g / kStages) & 1), budget);
-      }
-      if (!ok) s_fail = 1;
+      if (!ok) *vfail = 1;
+      // copies issued but not consumed (only after a failure) land before the CTA exits
+      for (long long q = g > kStages ? g - kStages : 0; q < g; ++q)
+        umma::mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1), budget);
     }
-    step += KB;
-    __syncthreads();
-    if (s_fail) break;
-    umma::tc_fence_after();
-    // epilogue: combine the S levels (exact FP32 integers P_m) and store.
-    // C = 2^-16 sum_m 2^-8m P_m = 2^-48 ((((P0 2^8 + P1) 2^8 + P2) 2^8 + P3) 2^8 + P4)
-    //   + 2^-56 (P5 + 2^-8 P6): the first five levels combine exactly in a 64-bit
-    // integer, the last two in FP32 (rounding about 2^-59 absolute), leaving four
-    // FP64 operations per entry.
-    const int row = rt * BM + warp * 32 + lane;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      long long hi[32];
-      float lo[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) { hi[i] = 0; lo[i] = 0.0f; }
-      if (KB > 0) {
-        for (int m = 0; m < 5; ++m) {
-          float v[32];
-          if (m < S) umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) hi[i] = hi[i] * 256 + (m < S ? (long long)__float2int_rn(v[i]) : 0ll);
+  } else if (warp == kMmaWarp) {
+    if (lane == 0) {
+      long long g = 0;
+      int it = 0;
+      bool ok = true, issued = false;
+      for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++it) {
+        const TileRef t = tile_ref(segs, nseg, w);
+        if (it > 0 && !wait_or_fail(tempty, (uint32_t)((it - 1) & 1), budget, vfail)) {
+          ok = false;
+          break;
         }
-        for (int m = 6; m >= 5; --m) {
-          if (m >= S) continue;
-          float v[32];
-          umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
+        umma::tc_fence_after();
+        for (int kb = 0; kb < t.KB; ++kb, ++g) {
+          const int st = (int)(g % kStages);
+          if (!wait_or_fail(&full[st], (uint32_t)((g / kStages) & 1), budget, vfail)) {
+            ok = false;
+            break;
+          }
+          umma::tc_fence_after();
+          const uint32_t a0 = sbase + st * stage_bytes;
+          const uint32_t b0 = a0 + a_bytes;
+          // The S B-slices are stacked along N in shared memory and level m's
+          // accumulator starts at TMEM column m*BN, so A_s against the stacked slices
+          // B_0..B_{S-1-s} (N = BN (S - s)) drops every product A_s B_t into level
+          // s+t: one wide MMA per A-slice (split at N = 256) instead of one per pair.
 #pragma unroll
-          for (int i = 0; i < 32; ++i) lo[i] = fmaf(lo[i], 0.00390625f, v[i]);
+          for (int s = 0; s < S; ++s) {
+            const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2, 128, BK * 16);
+#pragma unroll
+            for (int off = 0; off < BN * (S - s); off += 256) {
+              const int nn = BN * (S - s) - off < 256 ? BN * (S - s) - off : 256;
+              const uint64_t bd = umma::sdesc(b0 + (off / BN) * kBTileElems * 2, 128, BK * 16);
+              umma::mma_bf16(tmem + s * BN + off, ad, bd, umma::idesc_bf16(BM, nn), (kb > 0 || s > 0) ? 1u : 0u);
+            }
+          }
+          umma::mma_commit(&empty[st]);
+          issued = true;
         }
+        if (!ok) break;
+        if (t.KB > 0) umma::mma_commit(tfull);
+        else mbar_arrive(tfull);
       }
-      if (row < sg.rows) {
+      if (!ok) *vfail = 1;
+      // every MMA issued has completed before the accumulators are released
+      if (issued) {
+        umma::mma_commit(done);
+        umma::mbar_wait(done, 0, budget);
+      }
+    }
+  } else {
+    // epilogue: C = 2^-16 sum_m 2^-8m P_m with P_m the exact FP32 integer sums of
+    // level m.  The first five levels combine exactly in a 64-bit integer
+    // 2^-48 ((((P0 2^8 + P1) 2^8 + P2) 2^8 + P3) 2^8 + P4), the last two in FP32
+    // as 2^-56 (P5 + 2^-8 P6) (rounding about 2^-59 absolute).
+    int it = 0;
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++it) {
+      const TileRef t = tile_ref(segs, nseg, w);
+      const bool okw = __all_sync(0xffffffffu, wait_or_fail(tfull, (uint32_t)(it & 1), budget, vfail));
+      if (!okw) {
+        if (lane == 0) *vfail = 1;
+        break;
+      }
+      umma::tc_fence_after();
+      double val[BN];
+#pragma unroll
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        long long hi[32];
+        float lo[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int j = ct * BN + c0 + i;
+          hi[i] = 0;
+          lo[i] = 0.0f;
+        }
+        if (t.KB > 0) {
+#pragma unroll
+          for (int m = 0; m < 5; ++m) {
+            if (m < S) {
+              float v[32];
+              umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) hi[i] = hi[i] * 256 + (long long)__float2int_rn(v[i]);
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) hi[i] *= 256;
+            }
+          }
+#pragma unroll
+          for (int m = 6; m >= 5; --m) {
+            if (m < S) {
+              float v[32];
+              umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
+#pragma unroll
+              for (int i = 0; i < 32; ++i) lo[i] = fmaf(lo[i], 0.00390625f, v[i]);
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) val[c0 + i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+      }
+      umma::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty);
+      const GemmSeg& sg = *t.sg;
+      const int row = t.rt * BM + warp * 32 + lane;
+      if (row < sg.rows) {
+#pragma unroll
+        for (int i = 0; i < BN; ++i) {
+          const int j = t.ct * BN + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            const double val = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
-            sg.C[row + (int64_t)pos * sg.ldc] = val;
+            sg.C[row + (int64_t)pos * sg.ldc] = val[i];
           }
         }
       }
     }
-    umma::tc_fence_before();
-    __syncthreads();
-  }
-  if (s_fail && tid == 0) {
-    set_status(status, TDC_ETIMEOUT);
-    // give copies and MMAs still in flight a bounded chance to land before the
-    // shared memory and the accumulators are released
-    for (int i = 0; i < kStages; ++i) umma::mbar_wait(&full[i], 0, budget);
   }
   umma::tc_fence_before();
   __syncthreads();
+  if (tid == 0 && s_fail) set_status(status, TDC_ETIMEOUT);
   if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
@@ -416,17 +507,29 @@ static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, int S, __n
   return cudaGetLastError();
 }
 
+template <int S>
+static cudaError_t launch_split_mma_s(const GemmSeg* segs, int nseg, int* status, long long budget,
+                                      const __nv_bfloat16* img, int sms, cudaStream_t s) {
+  const int smem = kStages * S * (kATileElems + kBTileElems) * 2 + 128;
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_gemm_split<S><<<sms, kSplitThreads, smem, s>>>(segs, nseg, img, status, budget);
+  return cudaGetLastError();
+}
+
 static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, int S, int* status, long long budget,
                                     const __nv_bfloat16* img, cudaStream_t s) {
-  cudaError_t e;
-  const int smem = kStages * S * (kATileElems + kBTileElems) * 2 + 128;
-  e = cudaFuncSetAttribute(k_gemm_split, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_gemm_split<<<sms, 128, smem, s>>>(segs, nseg, S, img, status, budget);
-  return cudaGetLastError();
+  switch (S) {
+    case 3: return launch_split_mma_s<3>(segs, nseg, status, budget, img, sms, s);
+    case 4: return launch_split_mma_s<4>(segs, nseg, status, budget, img, sms, s);
+    case 5: return launch_split_mma_s<5>(segs, nseg, status, budget, img, sms, s);
+    case 6: return launch_split_mma_s<6>(segs, nseg, status, budget, img, sms, s);
+    case 7: return launch_split_mma_s<7>(segs, nseg, status, budget, img, sms, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, cudaStream_t s,
