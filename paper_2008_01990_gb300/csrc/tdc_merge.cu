@@ -63,9 +63,16 @@ cudaError_t launch_dmod(const Plan& P, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 static constexpr int kMaxLeaf = 64;
 
-__global__ void __launch_bounds__(32) k_leaf(Plan P, int64_t nleaves) {
+// One leaf per block of two warps.  Implicit symmetric QR with Wilkinson shift:
+// warp 0 tests every off-diagonal for negligibility in parallel (one ballot finds
+// the active block [pp, q]) and lane 0 chases the bulge through it, carrying the
+// running diagonal / off-diagonal entries in registers; warp 1 meanwhile applies
+// the previous sweep's rotations to the eigenvector block (two rows per lane,
+// the running column in a register).  The rotations of consecutive sweeps are
+// double-buffered, so the sequential chase and the parallel update overlap.
+__global__ void __launch_bounds__(64) k_leaf(Plan P, int64_t nleaves) {
   extern __shared__ double sm[];
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int64_t g = blockIdx.x;
   if (g >= nleaves) return;
   // problem owning global leaf g (problems sorted by leaf0 ascending)
@@ -79,94 +86,149 @@ __global__ void __launch_bounds__(32) k_leaf(Plan P, int64_t nleaves) {
   int t = p.depth;
   int64_t lo = node_bound(li, p.n, t), hi = node_bound(li + 1, p.n, t);
   const int L = (int)(hi - lo);
-  double* Qs = sm;                 // L*L
+  double* Qs = sm;                 // L*L, column-major
   double* dd = Qs + L * L;         // L
   double* ee = dd + L;             // L
-  double* cs = ee + L;             // 2L
-  int* ctrl = (int*)(cs + 2 * L);  // p, q, done, iter
-  int* perm = ctrl + 4;            // L
-  for (int k = lane; k < L * L; k += 32) Qs[k] = ((k % L) == (k / L)) ? 1.0 : 0.0;
-  for (int k = lane; k < L; k += 32) {
+  double* cs = ee + L;             // 2 buffers x 2L (c, s of each rotation)
+  int* ctrl = (int*)(cs + 4 * L);  // [b][0..1] = pp, q of the sweep in buffer b; [4] = done
+  int* perm = ctrl + 6;            // L
+  for (int k = tid; k < L * L; k += blockDim.x) Qs[k] = ((k % L) == (k / L)) ? 1.0 : 0.0;
+  for (int k = tid; k < L; k += blockDim.x) {
     dd[k] = P.v.dmod[p.voff + lo + k];
     ee[k] = (k < L - 1) ? P.e[p.off_de + lo + k] : 0.0;
   }
-  if (lane == 0) { ctrl[2] = 0; ctrl[3] = 0; }
-  __syncwarp();
+  if (tid == 0) ctrl[4] = (L <= 1) ? 1 : 0;
+  __syncthreads();
   const int max_sweeps = 40 * (L > 0 ? L : 1);
-  while (L > 1) {
-    if (lane == 0) {
-      int q = L - 1;
-      for (int k = 0; k < q; ++k)
-        if (fabs(ee[k]) <= kEps * (fabs(dd[k]) + fabs(dd[k + 1]))) ee[k] = 0.0;
-      while (q > 0 && ee[q - 1] == 0.0) --q;
-      if (q == 0) {
-        ctrl[2] = 1;
-      } else if (++ctrl[3] > max_sweeps) {
-        ctrl[2] = 1;
-        set_status(P.status, TDC_ENOCONV);
-      } else {
-        int pp = q - 1;
-        while (pp > 0 && ee[pp - 1] != 0.0) --pp;
-        // Wilkinson shift: eigenvalue of the trailing 2x2 block nearer to dd[q]
-        double hd = 0.5 * (dd[q - 1] - dd[q]);
-        double bq = ee[q - 1];
-        double h = hypot(hd, bq);
-        double mu = dd[q] - bq * bq / (hd + copysign(h, hd));
-        double x = dd[pp] - mu, y = ee[pp];
-        for (int k = pp; k < q; ++k) {
-          // Givens rotation from (x, y) through a refined reciprocal square root
-          // (no division on the sequential path); hypot only where squares leave range
-          const double t2 = fma(x, x, y * y);
-          double r, c = 1.0, s = 0.0;
-          if (t2 > 1e-290 && t2 < 1e290) {
-            const double ri = rsqrt_nr(t2);
-            c = x * ri; s = y * ri; r = t2 * ri;
-          } else {
-            r = hypot(x, y);
-            if (r != 0.0) { c = x / r; s = y / r; }
-          }
-          if (k > pp) ee[k - 1] = r;
-          double a0 = dd[k], a1 = dd[k + 1], bk = ee[k];
-          double cc = c * c, ss = s * s, c2s = 2.0 * c * s * bk;
-          dd[k] = cc * a0 + c2s + ss * a1;
-          dd[k + 1] = ss * a0 - c2s + cc * a1;
-          ee[k] = c * s * (a1 - a0) + (cc - ss) * bk;
-          if (k < q - 1) {
-            y = s * ee[k + 1];
-            ee[k + 1] *= c;
-            x = ee[k];
-          }
-          cs[2 * k] = c;
-          cs[2 * k + 1] = s;
+  int sweep = 0;
+  while (!ctrl[4]) {
+    const int b = sweep & 1;
+    if (warp == 0) {
+      // negligible off-diagonals (all lanes), then the trailing unreduced block
+      unsigned long long nz = 0ull;
+      for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        bool keep = false;
+        if (k < L - 1) {
+          const double ek = ee[k];
+          if (fabs(ek) <= kEps * (fabs(dd[k]) + fabs(dd[k + 1]))) ee[k] = 0.0;
+          else keep = ek != 0.0;
         }
-        ctrl[0] = pp;
-        ctrl[1] = q;
+        nz |= (unsigned long long)__ballot_sync(0xffffffffu, keep) << (32 * h);
+      }
+      __syncwarp();
+      if (lane == 0) {
+        if (nz == 0ull) {
+          ctrl[4] = 1;
+          ctrl[2 * b] = 0;
+          ctrl[2 * b + 1] = 0;
+        } else if (sweep >= max_sweeps) {
+          ctrl[4] = 1;
+          ctrl[2 * b] = 0;
+          ctrl[2 * b + 1] = 0;
+          set_status(P.status, TDC_ENOCONV);
+        } else {
+          const int q = 64 - __clzll((long long)nz);  // ee[q-1] != 0, ee[q..] == 0
+          const unsigned long long below = (q - 1 > 0) ? (~nz & ((1ull << (q - 1)) - 1ull)) : 0ull;
+          const int pp = below ? 64 - __clzll((long long)below) : 0;
+          // Wilkinson shift: eigenvalue of the trailing 2x2 block nearer to dd[q]
+          const double hd = 0.5 * (dd[q - 1] - dd[q]);
+          const double bq = ee[q - 1];
+          const double hh = hypot(hd, bq);
+          const double mu = dd[q] - bq * bq / (hd + copysign(hh, hd));
+          double a0 = dd[pp], bk = ee[pp];
+          double x = a0 - mu, y = bk;
+          double* cb = cs + 2 * L * b;
+          for (int k = pp; k < q; ++k) {
+            const double a1 = dd[k + 1];
+            const double en = (k < q - 1) ? ee[k + 1] : 0.0;
+            // Givens rotation from (x, y) through a refined reciprocal square root
+            // (no division on the sequential path); hypot only where squares leave range
+            const double t2 = fma(x, x, y * y);
+            double r, c = 1.0, sn = 0.0;
+            if (t2 > 1e-290 && t2 < 1e290) {
+              const double ri = rsqrt_nr(t2);
+              c = x * ri; sn = y * ri; r = t2 * ri;
+            } else {
+              r = hypot(x, y);
+              if (r != 0.0) { c = x / r; sn = y / r; }
+            }
+            if (k > pp) ee[k - 1] = r;
+            const double cc = c * c, ss = sn * sn, c2s = 2.0 * c * sn * bk;
+            dd[k] = cc * a0 + c2s + ss * a1;
+            const double a0n = ss * a0 - c2s + cc * a1;
+            const double ek = c * sn * (a1 - a0) + (cc - ss) * bk;
+            if (k < q - 1) {
+              y = sn * en;
+              bk = c * en;
+              x = ek;
+            } else {
+              ee[k] = ek;
+            }
+            a0 = a0n;
+            cb[2 * k] = c;
+            cb[2 * k + 1] = sn;
+          }
+          dd[q] = a0;
+          ctrl[2 * b] = pp;
+          ctrl[2 * b + 1] = q;
+        }
+      }
+    } else if (sweep > 0) {
+      // rotations of the previous sweep, rows lane and lane + 32
+      const int pb = b ^ 1;
+      const int pp = ctrl[2 * pb], q = ctrl[2 * pb + 1];
+      const double* cb = cs + 2 * L * pb;
+      const int r0 = lane, r1 = lane + 32;
+      if (r0 < L && q > pp) {
+        const bool two = r1 < L;
+        double v0 = Qs[r0 + pp * L], v1 = two ? Qs[r1 + pp * L] : 0.0;
+        for (int k = pp; k < q; ++k) {
+          const double c = cb[2 * k], sn = cb[2 * k + 1];
+          const double w0 = Qs[r0 + (k + 1) * L];
+          Qs[r0 + k * L] = c * v0 + sn * w0;
+          v0 = c * w0 - sn * v0;
+          if (two) {
+            const double w1 = Qs[r1 + (k + 1) * L];
+            Qs[r1 + k * L] = c * v1 + sn * w1;
+            v1 = c * w1 - sn * v1;
+          }
+        }
+        Qs[r0 + q * L] = v0;
+        if (two) Qs[r1 + q * L] = v1;
       }
     }
-    __syncwarp();
-    if (ctrl[2]) break;
-    const int pp = ctrl[0], q = ctrl[1];
-    for (int r = lane; r < L; r += 32) {
+    __syncthreads();
+    ++sweep;
+  }
+  // the sweep in the last buffer (if any) is still to be applied
+  if (warp == 1 && sweep > 0) {
+    const int pb = (sweep - 1) & 1;
+    const int pp = ctrl[2 * pb], q = ctrl[2 * pb + 1];
+    const double* cb = cs + 2 * L * pb;
+    for (int r = lane; r < L && q > pp; r += 32) {
+      double v = Qs[r + pp * L];
       for (int k = pp; k < q; ++k) {
-        double c = cs[2 * k], s = cs[2 * k + 1];
-        double a0 = Qs[r + k * L], a1 = Qs[r + (k + 1) * L];
-        Qs[r + k * L] = c * a0 + s * a1;
-        Qs[r + (k + 1) * L] = c * a1 - s * a0;
+        const double c = cb[2 * k], sn = cb[2 * k + 1];
+        const double w = Qs[r + (k + 1) * L];
+        Qs[r + k * L] = c * v + sn * w;
+        v = c * w - sn * v;
       }
-    }
-    __syncwarp();
-  }
-  // ascending order (stable)
-  if (lane == 0) {
-    for (int k = 0; k < L; ++k) perm[k] = k;
-    for (int k = 1; k < L; ++k) {
-      int v = perm[k];
-      int m = k - 1;
-      while (m >= 0 && dd[perm[m]] > dd[v]) { perm[m + 1] = perm[m]; --m; }
-      perm[m + 1] = v;
+      Qs[r + q * L] = v;
     }
   }
-  __syncwarp();
+  __syncthreads();
+  // ascending order (stable): rank of each eigenvalue
+  for (int k = tid; k < L; k += blockDim.x) {
+    const double v = dd[k];
+    int rk = 0;
+    for (int m = 0; m < L; ++m) {
+      const double w = dd[m];
+      rk += (w < v || (w == v && m < k)) ? 1 : 0;
+    }
+    perm[rk] = k;
+  }
+  __syncthreads();
   double* dst;
   int64_t ld;
   if (t & 1) { dst = P.Q1 + p.qoff1; ld = p.n; }
@@ -174,16 +236,16 @@ __global__ void __launch_bounds__(32) k_leaf(Plan P, int64_t nleaves) {
   dst += lo + lo * ld;
   for (int k = 0; k < L; ++k) {
     int c = perm[k];
-    for (int r = lane; r < L; r += 32) dst[r + k * ld] = Qs[r + c * L];
+    for (int r = tid; r < L; r += blockDim.x) dst[r + k * ld] = Qs[r + c * L];
   }
-  for (int k = lane; k < L; k += 32) P.v.lam[p.voff + lo + k] = dd[perm[k]];
+  for (int k = tid; k < L; k += blockDim.x) P.v.lam[p.voff + lo + k] = dd[perm[k]];
 }
 
 cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStream_t s) {
   if (nleaves == 0) return cudaSuccess;
   if (max_leaf > kMaxLeaf) return cudaErrorInvalidValue;
-  size_t smem = sizeof(double) * (max_leaf * max_leaf + 4 * max_leaf) + sizeof(int) * (4 + max_leaf);
-  k_leaf<<<(unsigned)nleaves, 32, smem, s>>>(P, nleaves);
+  size_t smem = sizeof(double) * (max_leaf * max_leaf + 6 * max_leaf) + sizeof(int) * (6 + max_leaf);
+  k_leaf<<<(unsigned)nleaves, 64, smem, s>>>(P, nleaves);
   return cudaGetLastError();
 }
 
@@ -236,6 +298,29 @@ __device__ void block_excl_scan2(int& a, int& b, int* red) {
 // ---------------------------------------------------------------------------
 // k_prepare: one block per merge.
 // ---------------------------------------------------------------------------
+
+// Type-2 deflation test of pole (D, z) against the last kept pole (pD, pz):
+// |(D - pD) c s| <= tol with c s = -z pz / (z^2 + pz^2), i.e. without division or
+// root.  Every rounding is explicit so that the speculative (parallel) and the
+// sequential evaluation of the same pair give the same answer.
+__device__ __forceinline__ bool type2_test(double D, double z, double pD, double pz, double tol) {
+  const double t2 = __fma_rn(z, z, __dmul_rn(pz, pz));
+  return fabs(__dmul_rn(__dmul_rn(__dsub_rn(D, pD), z), pz)) <= __dmul_rn(tol, t2);
+}
+
+// The rotation that moves all of z onto the new pole: c = z/tau, s = -pz/tau,
+// tau = hypot(z, pz); the deflated value dp and the survivor's new value di.
+__device__ __forceinline__ void type2_rot(double D, double z, double pD, double pz, double& cc, double& ss,
+                                          double& tau, double& dp, double& di) {
+  const double t2 = __fma_rn(z, z, __dmul_rn(pz, pz));
+  const double r = rsqrt_nr(t2);
+  cc = __dmul_rn(z, r);
+  ss = __dmul_rn(-pz, r);
+  tau = __dmul_rn(t2, r);
+  const double c2 = __dmul_rn(cc, cc), s2 = __dmul_rn(ss, ss);
+  dp = __fma_rn(pD, c2, __dmul_rn(D, s2));
+  di = __fma_rn(pD, s2, __dmul_rn(D, c2));
+}
 
 __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   __shared__ double redd[64];
@@ -328,74 +413,107 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   const int nL = sres[0], t1 = sres[1];
   __syncthreads();
   // 3b. speculative type-2 test and rotation for each consecutive pair of L
+  //     (bit 0 of flag[q]), and for the pole after a speculative rotation the test
+  //     against the rotated survivor (bit 1), which covers isolated pairs of
+  //     equal poles without sequential FP64 work
   for (int q = 1 + threadIdx.x; q < nL; q += blockDim.x) {
     const int a = V.perm[v0 + Lpos[q - 1]], b = V.perm[v0 + Lpos[q]];
     const double pD = V.Dc[v0 + a], pz = V.zc[v0 + a];
     const double D = V.Dc[v0 + b], z = V.zc[v0 + b];
-    // |(D - pD) c s| <= tol with c s = -z pz / (z^2 + pz^2): no division, no root
-    const double t2 = fma(z, z, pz * pz);
-    const bool f = fabs((D - pD) * z * pz) <= tol * t2;
+    const bool f = type2_test(D, z, pD, pz, tol);
     flag[q] = f ? 1 : 0;
-    if (f) {
-      const double r = rsqrt_nr(t2);
-      const double cc = z * r, ss = -pz * r;
-      spc[q] = cc;
-      spc[n + q] = ss;
-      stau[q] = t2 * r;
-      sdp[q] = pD * cc * cc + D * ss * ss;
-      sdi[q] = pD * ss * ss + D * cc * cc;
-    }
+    if (f) type2_rot(D, z, pD, pz, spc[q], spc[n + q], stau[q], sdp[q], sdi[q]);
   }
   __syncthreads();
-  // 3c. sequential resolution
-  if (threadIdx.x == 0) {
-    int K = 0, ndf = t1, nr = 0, nch = 0, last_rot_i = -1;
-    int pj = -1, ps = 0;
-    double pD = 0.0, pz = 0.0;
-    bool prev_rot = false;
-    for (int q = 0; q < nL; ++q) {
+  for (int q = 2 + threadIdx.x; q < nL; q += blockDim.x) {
+    if (!(flag[q - 1] & 1)) continue;
+    const int b = V.perm[v0 + Lpos[q]];
+    if (type2_test(V.Dc[v0 + b], V.zc[v0 + b], sdi[q - 1], stau[q - 1], tol)) flag[q] |= 2;
+  }
+  __syncthreads();
+  // 3c. sequential resolution.  The per-pair inputs are staged through shared
+  //     memory in chunks (loaded by warps 1.. while thread 0 resolves the previous
+  //     chunk), so the sequential loop never waits on a global-memory gather.
+  constexpr int kCh = 256;
+  __shared__ int sc_c[2][kCh];
+  __shared__ uint8_t sc_f[2][kCh];
+  __shared__ double sc_D[2][kCh], sc_z[2][kCh], sc_cs[2][kCh], sc_sn[2][kCh], sc_tau[2][kCh], sc_dp[2][kCh],
+      sc_di[2][kCh];
+  auto stage = [&](int b, int q0, int t0, int nt) {
+    for (int i = t0; i < kCh; i += nt) {
+      const int q = q0 + i;
+      if (q >= nL) break;
       const int c = V.perm[v0 + Lpos[q]];
-      const int sp = (c < n1) ? 1 : 2;
-      if (q == 0) {
-        pj = c; pD = V.Dc[v0 + c]; pz = V.zc[v0 + c]; ps = sp; prev_rot = false;
-        continue;
-      }
-      bool rot;
-      double cc = 0.0, ss = 0.0, tau = 0.0, dp = 0.0, di = 0.0;
-      if (!prev_rot) {
-        rot = flag[q] != 0;
-        if (rot) { cc = spc[q]; ss = spc[n + q]; tau = stau[q]; dp = sdp[q]; di = sdi[q]; }
-      } else {  // the last kept pole was rotated: test with its current values
-        const double D = V.Dc[v0 + c], z = V.zc[v0 + c];
-        const double t2 = fma(z, z, pz * pz);
-        rot = fabs((D - pD) * z * pz) <= tol * t2;
-        if (rot) {
-          const double r = rsqrt_nr(t2);
-          cc = z * r; ss = -pz * r; tau = t2 * r;
-          dp = pD * cc * cc + D * ss * ss;
-          di = pD * ss * ss + D * cc * cc;
-        }
-      }
-      if (rot) {  // type 2: rotate (pj, c) so that z_pj = 0; pj is deflated
-        const int64_t ro = v0 + nr;
-        V.rij[4 * ro + 0] = pj;
-        V.rij[4 * ro + 1] = c;
-        V.rij[4 * ro + 2] = ps | (sp << 8);
-        V.rcs[2 * ro + 0] = cc;
-        V.rcs[2 * ro + 1] = ss;
-        if (pj != last_rot_i) V.rch[v0 + nch++] = nr;
-        last_rot_i = c;
-        ++nr;
-        const int u = ps | sp;
-        V.dcol[v0 + ndf] = pj; V.dval[v0 + ndf] = dp; V.dseg[v0 + ndf] = (uint8_t)u; ++ndf;
-        pj = c; pD = di; pz = tau; ps = u;
-        prev_rot = true;
-      } else {
-        V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
-        pj = c; pD = V.Dc[v0 + c]; pz = V.zc[v0 + c]; ps = sp;
-        prev_rot = false;
+      sc_c[b][i] = c;
+      sc_D[b][i] = V.Dc[v0 + c];
+      sc_z[b][i] = V.zc[v0 + c];
+      const uint8_t f = q > 0 ? flag[q] : 0;
+      sc_f[b][i] = f;
+      if (f & 1) {
+        sc_cs[b][i] = spc[q];
+        sc_sn[b][i] = spc[n + q];
+        sc_tau[b][i] = stau[q];
+        sc_dp[b][i] = sdp[q];
+        sc_di[b][i] = sdi[q];
       }
     }
+  };
+  stage(0, 0, threadIdx.x, blockDim.x);
+  __syncthreads();
+  int K = 0, ndf = t1, nr = 0, nch = 0, last_rot_i = -1;
+  int pj = -1, ps = 0;
+  double pD = 0.0, pz = 0.0;
+  bool prev_rot = false, prev_simple = false;
+  for (int ch = 0; ch * kCh < nL; ++ch) {
+    const int b = ch & 1;
+    if (threadIdx.x >= 32) stage(b ^ 1, (ch + 1) * kCh, threadIdx.x - 32, blockDim.x - 32);
+    if (threadIdx.x == 0) {
+      const int qend = min(kCh, nL - ch * kCh);
+      for (int i = 0; i < qend; ++i) {
+        const int q = ch * kCh + i;
+        const int c = sc_c[b][i];
+        const int sp = (c < n1) ? 1 : 2;
+        if (q == 0) {
+          pj = c; pD = sc_D[b][i]; pz = sc_z[b][i]; ps = sp; prev_rot = false;
+          continue;
+        }
+        bool rot;
+        double cc = 0.0, ss = 0.0, tau = 0.0, dp = 0.0, di = 0.0;
+        const uint8_t f = sc_f[b][i];
+        if (!prev_rot) {
+          rot = (f & 1) != 0;
+          if (rot) { cc = sc_cs[b][i]; ss = sc_sn[b][i]; tau = sc_tau[b][i]; dp = sc_dp[b][i]; di = sc_di[b][i]; }
+          prev_simple = rot;
+        } else {  // the last kept pole was rotated: test against its current values
+          const double D = sc_D[b][i], z = sc_z[b][i];
+          rot = prev_simple ? (f & 2) != 0 : type2_test(D, z, pD, pz, tol);
+          if (rot) type2_rot(D, z, pD, pz, cc, ss, tau, dp, di);
+          prev_simple = false;
+        }
+        if (rot) {  // type 2: rotate (pj, c) so that z_pj = 0; pj is deflated
+          const int64_t ro = v0 + nr;
+          V.rij[4 * ro + 0] = pj;
+          V.rij[4 * ro + 1] = c;
+          V.rij[4 * ro + 2] = ps | (sp << 8);
+          V.rcs[2 * ro + 0] = cc;
+          V.rcs[2 * ro + 1] = ss;
+          if (pj != last_rot_i) V.rch[v0 + nch++] = nr;
+          last_rot_i = c;
+          ++nr;
+          const int u = ps | sp;
+          V.dcol[v0 + ndf] = pj; V.dval[v0 + ndf] = dp; V.dseg[v0 + ndf] = (uint8_t)u; ++ndf;
+          pj = c; pD = di; pz = tau; ps = u;
+          prev_rot = true;
+        } else {
+          V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
+          pj = c; pD = sc_D[b][i]; pz = sc_z[b][i]; ps = sp;
+          prev_rot = false;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
     if (pj >= 0) {
       V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
     }
@@ -411,10 +529,10 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     }
   }
   __syncthreads();
-  const int K = sres[0];
+  const int Kf = sres[0];
   // 4. lists of non-deflated poles with support in the top / bottom rows
-  const int perk = (K + blockDim.x - 1) / blockDim.x;
-  const int j0 = min(K, (int)threadIdx.x * perk), j1 = min(K, j0 + perk);
+  const int perk = (Kf + blockDim.x - 1) / blockDim.x;
+  const int j0 = min(Kf, (int)threadIdx.x * perk), j1 = min(Kf, j0 + perk);
   int ct = 0, cb = 0;
   for (int j = j0; j < j1; ++j) {
     uint8_t s = V.kseg[v0 + j];
@@ -433,7 +551,7 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     P.m.nbot[g] = ob;
     if (P.stats && level < TDC_MAX_LEVELS)
       atomicAdd(&P.stats->gemm_flops[level],
-                2ull * ((unsigned long long)n1 * ot + (unsigned long long)(n - n1) * ob) * (unsigned long long)K);
+                2ull * ((unsigned long long)n1 * ot + (unsigned long long)(n - n1) * ob) * (unsigned long long)Kf);
   }
 }
 
