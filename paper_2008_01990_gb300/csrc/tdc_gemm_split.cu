@@ -381,6 +381,11 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       long long g = 0;
       int it = 0;
       bool ok = true, issued = false;
+      // shared-memory descriptor of slice 0 of stage 0 (K-major core matrices:
+      // 128 bytes between the two core matrices along K, 256 between 8-row groups);
+      // the start-address field (bits 0-13, address / 16) absorbs every offset below
+      // without carrying, as all of shared memory lies below 2^18 bytes
+      const uint64_t desc0 = umma::sdesc(sbase, 128, BK * 16);
       for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++it) {
         const TileRef t = tile_ref(segs, nseg, w);
         if (it > 0 && !wait_or_fail(tempty, (uint32_t)((it - 1) & 1), budget, vfail)) {
@@ -395,19 +400,20 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
             break;
           }
           umma::tc_fence_after();
-          const uint32_t a0 = sbase + st * stage_bytes;
-          const uint32_t b0 = a0 + a_bytes;
           // The S B-slices are stacked along N in shared memory and level m's
           // accumulator starts at TMEM column m*BN, so A_s against the stacked slices
           // B_0..B_{S-1-s} (N = BN (S - s)) drops every product A_s B_t into level
           // s+t: one wide MMA per A-slice (split at N = 256) instead of one per pair.
+          // Every operand descriptor is the stage-0 descriptor plus a constant, so
+          // the issue loop is a handful of integer adds per MMA.
+          const uint64_t dst = desc0 + (uint64_t)((st * stage_bytes) >> 4);
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const uint64_t ad = umma::sdesc(a0 + s * kATileElems * 2, 128, BK * 16);
+            const uint64_t ad = dst + (uint64_t)((s * kATileElems * 2) >> 4);
 #pragma unroll
             for (int off = 0; off < BN * (S - s); off += 256) {
               const int nn = BN * (S - s) - off < 256 ? BN * (S - s) - off : 256;
-              const uint64_t bd = umma::sdesc(b0 + (off / BN) * kBTileElems * 2, 128, BK * 16);
+              const uint64_t bd = dst + (uint64_t)((a_bytes + (off / BN) * kBTileElems * 2) >> 4);
               umma::mma_bf16(tmem + s * BN + off, ad, bd, umma::idesc_bf16(BM, nn), (kb > 0 || s > 0) ? 1u : 0u);
             }
           }
