@@ -240,7 +240,7 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   Vecs& v = P.v;
   v.dmod = vd + 0 * N; v.lam = vd + 1 * N; v.Dc = vd + 2 * N; v.zc = vd + 3 * N;
   v.Ds = vd + 4 * N; v.zs = vd + 5 * N; v.Dk = vd + 6 * N; v.zk = vd + 7 * N;
-  v.tau = vd + 8 * N; v.zhat = vd + 9 * N; v.scol = vd + 10 * N; v.cmax = vd + 11 * N;
+  v.tau = vd + 8 * N; v.zhat = vd + 9 * N; v.scol = vd + 10 * N; v.xz = (float2*)(vd + 11 * N);
   v.dval = vd + 12 * N; v.rcs = vd + 13 * N;  // rcs: 2 per slot (13N..15N)
   v.skey = vd + 15 * N;                        // 2 per slot (15N..17N)
   int32_t* vi = (int32_t*)(base + L.vec_i);

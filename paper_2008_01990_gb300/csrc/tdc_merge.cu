@@ -546,6 +546,15 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     if (s & 1) V.tlist[v0 + ot++] = j;
     if (s & 2) V.blist[v0 + ob++] = j;
   }
+  // FP32 copies for the secular pre-iteration: coordinate relative to a centre pole
+  // and the squared weight
+  if (Kf > 0) {
+    const double dc = V.Dk[v0 + (Kf >> 1)];
+    for (int j = threadIdx.x; j < Kf; j += blockDim.x) {
+      const double zj = V.zk[v0 + j];
+      V.xz[v0 + j] = make_float2((float)(V.Dk[v0 + j] - dc), (float)(zj * zj));
+    }
+  }
   if (threadIdx.x == blockDim.x - 1) {
     P.m.ntop[g] = ot;
     P.m.nbot[g] = ob;
@@ -678,37 +687,27 @@ __device__ __forceinline__ void secular_sums(const double* D, const double* z, i
   sabs = phi - psi;
 }
 
-// Warp-cooperative solve of root j; every lane returns the same (org, tau).
-__device__ void secular_root(const double* D, const double* z, int K, int j, double rho, int max_iter,
-                             int& org_out, double& tau_out, int& iters, bool& conv) {
-  const double irho = 1.0 / rho;
-  int org;
-  double lo, hi, tau;
-  // sums at the starting point (carried into the first iteration)
-  double psi, dpsi, phi, dphi, sabs;
-  if (j < K - 1) {
-    const double gap = D[j + 1] - D[j];
-    secular_sums(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
-    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; tau = hi; }
-    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; tau = lo; }
-  } else {
-    double zz = 0.0;
-    for (int i = threadIdx.x & 31; i < K; i += 32) zz = fma(z[i], z[i], zz);
-    zz = warp_sum(zz);
-    org = K - 1; lo = 0.0; hi = rho * zz; tau = hi;
-    secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
-  }
+// FP64 iteration for root j from origin org, starting at tau inside [lo, hi] with
+// the sums at tau already known.  Two-pole rational model of g around tau (the
+// nearest poles exact), safeguarded by bisection; stops when |g| is at rounding
+// level of 1/rho + sum |t| or the step is below rounding level of tau.  Returns
+// the number of passes over the poles (sum evaluations) made.
+__device__ int secular_fp64(const double* D, const double* z, int K, int j, double irho, int org, double& tau,
+                            double& lo, double& hi, double psi, double dpsi, double phi, double dphi, double sabs,
+                            int max_iter, bool& conv) {
   const double dorg = D[org];
   const double dl = D[j] - dorg;                         // delta_j (0 when org == j)
   const double dr = (j < K - 1) ? D[j + 1] - dorg : 0.0; // delta_{j+1}
-  int it = 0;
+  int passes = 0;
   conv = false;
-  for (it = 1; it <= max_iter; ++it) {
-    if (it > 1) secular_sums(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
+  for (int it = 1; it <= max_iter; ++it) {
+    if (it > 1) {
+      secular_sums(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
+      ++passes;
+    }
     const double gv = irho + psi + phi;
     if (gv == 0.0 || fabs(gv) <= 8.0 * kEps * (irho + sabs)) { conv = true; break; }
     if (gv < 0.0) lo = tau; else hi = tau;
-    // two-pole rational model of g around tau
     const double p = dl - tau;  // < 0
     double h = 0.0;
     bool ok = true;
@@ -745,9 +744,128 @@ __device__ void secular_root(const double* D, const double* z, int K, int j, dou
     tau = tn;
     if (small_step || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) { conv = true; break; }
   }
+  return passes;
+}
+
+// FP32 pre-iteration for root j < K-1 in the frame of pole j: tau in (0, gap).
+// Far poles use FP32 coordinates xz[i].x = d_i - d_c (one centre per merge) and
+// xz[i].y = z_i^2; the 32 poles nearest to j (one per lane) use their FP64
+// differences, so close neighbours keep their relative accuracy.  The same
+// two-pole model as in FP64.  Returns false if no usable estimate was found.
+__device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, float irho, float gap, float& tau_out) {
+  const int lane = threadIdx.x & 31;
+  // the window pole of this lane: the i = lane (mod 32) in [j - 15, j + 16]
+  const int iw = j - 15 + ((lane - (j - 15)) & 31);
+  const float dw = (iw >= 0 && iw < K) ? (float)(D[iw] - D[j]) : 0.0f;
+  const float xj = xz[j].x;
+  float lo = 0.0f, hi = gap, tau = 0.5f * gap;
+  for (int it = 0; it < 12; ++it) {
+    float a = 0.0f, da = 0.0f, b = 0.0f, db = 0.0f;
+    for (int i = lane; i < K; i += 32) {
+      const float2 v = xz[i];
+      const float del = (i == iw) ? dw : v.x - xj;
+      float r;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tau));
+      const float t = v.y * r;
+      if (i <= j) { a += t; da = fmaf(t, r, da); }
+      else { b += t; db = fmaf(t, r, db); }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      da += __shfl_xor_sync(0xffffffffu, da, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+      db += __shfl_xor_sync(0xffffffffu, db, o);
+    }
+    const float gv = irho + a + b;
+    if (!isfinite(gv)) return false;
+    if (gv == 0.0f) break;
+    if (gv < 0.0f) lo = tau; else hi = tau;
+    const float p = -tau, q = gap - tau;
+    const float b1 = da * p * p, b2 = db * q * q;
+    const float A = irho + (a - b1 / p) + (b - b2 / q);
+    const float B = A * (p + q) + b1 + b2;
+    const float C = p * q * gv;
+    float h = 0.0f;
+    bool ok = true;
+    if (A == 0.0f) {
+      h = C / B;
+    } else {
+      const float disc = B * B - 4.0f * A * C;
+      if (disc < 0.0f) {
+        ok = false;
+      } else {
+        const float w = B + copysignf(sqrtf(disc), B);
+        const float h1 = (w != 0.0f) ? 2.0f * C / w : 0.0f;
+        const float h2 = w / (2.0f * A);
+        const bool in1 = (h1 > p && h1 < q), in2 = (h2 > p && h2 < q);
+        if (in1 && (!in2 || fabsf(h1) <= fabsf(h2))) h = h1;
+        else if (in2) h = h2;
+        else ok = false;
+      }
+    }
+    float tn = tau + h;
+    if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5f * (lo + hi);
+    const bool small = fabsf(tn - tau) <= 2e-7f * fabsf(tau);
+    tau = tn;
+    if (small || (hi - lo) <= 4e-7f * hi) break;
+  }
+  if (!(tau > 0.0f && tau < gap)) return false;
+  tau_out = tau;
+  return true;
+}
+
+// Warp-cooperative solve of root j; every lane returns the same (org, tau).
+// With xz (FP32 copies of the poles and weights) the root is first located in
+// FP32; its position picks the origin (the nearer pole) and the FP64 iteration
+// starts there, with the whole interval as bracket.  A root that converges in
+// the half of the far pole is re-solved from that pole.  Without xz, or when the
+// FP32 estimate is unusable, the origin comes from the sign of g at the midpoint.
+__device__ void secular_root(const double* D, const double* z, const float2* xz, int K, int j, double rho,
+                             int max_iter, int& org_out, double& tau_out, int& iters, bool& conv) {
+  const double irho = 1.0 / rho;
+  int org;
+  double lo, hi, tau;
+  double psi, dpsi, phi, dphi, sabs;
+  int passes = 1;
+  if (j < K - 1) {
+    const double gap = D[j + 1] - D[j];
+    float t32 = 0.0f;
+    const bool have32 = xz != nullptr && gap > 0.0 && secular_fp32(D, xz, K, j, (float)irho, (float)gap, t32);
+    if (have32) {
+      if (t32 <= 0.5f * (float)gap) { org = j; lo = 0.0; hi = gap; tau = (double)t32; }
+      else { org = j + 1; lo = -gap; hi = 0.0; tau = (double)t32 - gap; }
+      if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+      secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+      passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+      // converged nearer the other pole: continue from that pole
+      const bool far = conv && ((org == j) ? (tau > 0.5 * gap) : (tau < -0.5 * gap));
+      if (far) {
+        if (org == j) { org = j + 1; tau -= gap; lo -= gap; hi -= gap; }
+        else { org = j; tau += gap; lo += gap; hi += gap; }
+        secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+        ++passes;
+        passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+      }
+      org_out = org;
+      tau_out = tau;
+      iters = min(passes, max_iter);
+      return;
+    }
+    secular_sums(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
+    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; tau = hi; }
+    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; tau = lo; }
+  } else {
+    double zz = 0.0;
+    for (int i = threadIdx.x & 31; i < K; i += 32) zz = fma(z[i], z[i], zz);
+    zz = warp_sum(zz);
+    org = K - 1; lo = 0.0; hi = rho * zz; tau = hi;
+    secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+  }
+  passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
   org_out = org;
   tau_out = tau;
-  iters = min(it, max_iter);
+  iters = min(passes, max_iter);
 }
 
 __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_act, int64_t nslots) {
@@ -758,7 +876,7 @@ __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_ac
   int org, it;
   double tau;
   bool conv;
-  secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
+  secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
   if ((threadIdx.x & 31) == 0) {
     P.v.org[S.v0 + S.j] = org;
     P.v.tau[S.v0 + S.j] = tau;
@@ -810,19 +928,15 @@ __global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int nprob_act
   if ((threadIdx.x & 31) == 0) P.v.zhat[S.v0 + S.j] = zh;
 }
 
-// s_j = 1 / sqrt(sum_i (zhat_i / delta_ij)^2), delta_ij = (d_i - d_org(j)) - tau_j; also max_i |Qhat_ij|.
-__device__ void column_norm(const double* D, const double* zh, int K, double dorg, double tj, double& sj,
-                            double& cmax) {
-  double acc = 0.0, mx = 0.0;
+// s_j = 1 / sqrt(sum_i (zhat_i / delta_ij)^2), delta_ij = (d_i - d_org(j)) - tau_j.
+__device__ double column_norm(const double* D, const double* zh, int K, double dorg, double tj) {
+  double acc = 0.0;
   for (int i = threadIdx.x & 31; i < K; i += 32) {
     const double u = zh[i] * rcp_nr((D[i] - dorg) - tj);
     acc = fma(u, u, acc);
-    mx = fmax(mx, fabs(u));
   }
   acc = warp_sum(acc);
-  mx = warp_max(mx);
-  sj = 1.0 / sqrt(acc);
-  cmax = mx * sj;
+  return 1.0 / sqrt(acc);
 }
 
 __global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int nprob_act, int64_t nslots) {
@@ -831,12 +945,8 @@ __global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int nprob_ac
   const Slot S = slot_of(P, level, nprob_act, s);
   if (!S.valid) return;
   const double* D = P.v.Dk + S.v0;
-  double sj, cm;
-  column_norm(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j], sj, cm);
-  if ((threadIdx.x & 31) == 0) {
-    P.v.scol[S.v0 + S.j] = sj;
-    P.v.cmax[S.v0 + S.j] = cm;
-  }
+  const double sj = column_norm(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j]);
+  if ((threadIdx.x & 31) == 0) P.v.scol[S.v0 + S.j] = sj;
 }
 
 // Stand-alone rank-one eigenproblem (tdc_rank_one): the three warp-per-entry stages.
@@ -847,7 +957,7 @@ __global__ void __launch_bounds__(256) k_r1_secular(const double* D, const doubl
   int o, it;
   double t;
   bool conv;
-  secular_root(D, z, K, (int)j, rho, max_iter, o, t, it, conv);
+  secular_root(D, z, nullptr, K, (int)j, rho, max_iter, o, t, it, conv);
   if ((threadIdx.x & 31) == 0) {
     org[j] = o;
     tau[j] = t;
@@ -867,8 +977,7 @@ __global__ void __launch_bounds__(256) k_r1_colnorm(const double* D, const int* 
                                                      const double* zhat, int K, double* s) {
   const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (j >= K) return;
-  double sj, cm;
-  column_norm(D, zhat, K, D[org[j]], tau[j], sj, cm);
+  const double sj = column_norm(D, zhat, K, D[org[j]], tau[j]);
   if ((threadIdx.x & 31) == 0) s[j] = sj;
 }
 
