@@ -210,17 +210,19 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
   }
 }
 
+// Two B tiles per block iteration: threads 0-127 and 128-255 each take one
+// (64 columns x BK/8 groups of 8 poles).
+static_assert(BN * (BK / 8) == 128, "k_split_b maps 128 threads onto one B tile");
 __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img) {
   const int64_t total = segs[nseg].it_b;
-  const int tid = threadIdx.x;
-  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+  const int tid = threadIdx.x & 127;
+  for (int64_t w = 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7); w < total; w += 2 * (int64_t)gridDim.x) {
     const int si = find_seg(segs, nseg, w, 1);
     const GemmSeg& sg = segs[si];
     const int64_t local = w - sg.it_b;
     const int KB = (int)cdiv(sg.kk, BK);
     const int ct = (int)(local / KB), kb = (int)(local % KB);
     __nv_bfloat16* tile = img + sg.b_img + ((int64_t)ct * KB + kb) * S * kBTileElems;
-    if (tid >= BN * (BK / 8)) continue;
     const int j = tid % BN, kg = tid / BN;  // 64 columns x BK/8 groups of 8 poles
     const int jj = ct * BN + j;
     double dorg = 0.0, tj = 1.0, sj = 0.0;

@@ -431,14 +431,17 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     if (type2_test(V.Dc[v0 + b], V.zc[v0 + b], sdi[q - 1], stau[q - 1], tol)) flag[q] |= 2;
   }
   __syncthreads();
-  // 3c. sequential resolution.  The per-pair inputs are staged through shared
-  //     memory in chunks (loaded by warps 1.. while thread 0 resolves the previous
-  //     chunk), so the sequential loop never waits on a global-memory gather.
-  constexpr int kCh = 256;
-  __shared__ int sc_c[2][kCh];
-  __shared__ uint8_t sc_f[2][kCh];
-  __shared__ double sc_D[2][kCh], sc_z[2][kCh], sc_cs[2][kCh], sc_sn[2][kCh], sc_tau[2][kCh], sc_dp[2][kCh],
-      sc_di[2][kCh];
+  // 3c. sequential resolution, pipelined over chunks of kCh poles in three
+  //     shared-memory buffers: while thread 0 decides chunk ch (rotate or keep,
+  //     FP64 work only after a rotation that the speculation did not cover), the
+  //     other warps write the records of chunk ch-1 (whose output positions thread
+  //     0 has already assigned) and stage the inputs of chunk ch+1.
+  constexpr int kCh = 128;
+  __shared__ int sc_c[3][kCh];
+  __shared__ uint8_t sc_f[3][kCh], o_code[3][kCh];
+  __shared__ int o_idx[3][kCh], o_cidx[3][kCh], o_pj[3][kCh], o_sup[3][kCh];
+  __shared__ double sc_D[3][kCh], sc_z[3][kCh], sc_cs[3][kCh], sc_sn[3][kCh], sc_tau[3][kCh], sc_dp[3][kCh],
+      sc_di[3][kCh];
   auto stage = [&](int b, int q0, int t0, int nt) {
     for (int i = t0; i < kCh; i += nt) {
       const int q = q0 + i;
@@ -458,23 +461,58 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
       }
     }
   };
+  // records of a decided chunk: code bit 0 = rotation (else the previous survivor
+  // is kept), bit 1 = first rotation of a chain; values in sc_cs/sc_sn/sc_dp
+  // (rotation: c, s, deflated value) or sc_cs/sc_sn (kept: pole, weight)
+  auto emit = [&](int b, int q0, int t0, int nt) {
+    for (int i = t0; i < kCh; i += nt) {
+      const int q = q0 + i;
+      if (q >= nL) break;
+      if (q == 0) continue;
+      const uint8_t code = o_code[b][i];
+      const int idx = o_idx[b][i], pjq = o_pj[b][i], sup = o_sup[b][i];
+      if (code & 1) {
+        const int64_t ro = v0 + idx;
+        V.rij[4 * ro + 0] = pjq;
+        V.rij[4 * ro + 1] = sc_c[b][i];
+        V.rij[4 * ro + 2] = sup;
+        V.rcs[2 * ro + 0] = sc_cs[b][i];
+        V.rcs[2 * ro + 1] = sc_sn[b][i];
+        if (code & 2) V.rch[v0 + o_cidx[b][i]] = idx;
+        const int d = t1 + idx;
+        V.dcol[v0 + d] = pjq;
+        V.dval[v0 + d] = sc_dp[b][i];
+        V.dseg[v0 + d] = (uint8_t)((sup & 0xff) | (sup >> 8));
+      } else {
+        V.kept[v0 + idx] = pjq;
+        V.Dk[v0 + idx] = sc_cs[b][i];
+        V.zk[v0 + idx] = sc_sn[b][i];
+        V.kseg[v0 + idx] = (uint8_t)sup;
+      }
+    }
+  };
+  const int nch_chunks = (nL + kCh - 1) / kCh;
   stage(0, 0, threadIdx.x, blockDim.x);
   __syncthreads();
-  int K = 0, ndf = t1, nr = 0, nch = 0, last_rot_i = -1;
+  int K = 0, nr = 0, nch = 0;
   int pj = -1, ps = 0;
   double pD = 0.0, pz = 0.0;
   bool prev_rot = false, prev_simple = false;
-  for (int ch = 0; ch * kCh < nL; ++ch) {
-    const int b = ch & 1;
-    if (threadIdx.x >= 32) stage(b ^ 1, (ch + 1) * kCh, threadIdx.x - 32, blockDim.x - 32);
+  for (int ch = 0; ch < nch_chunks; ++ch) {
+    const int b = ch % 3;
+    if (threadIdx.x >= 32) {
+      if (ch > 0) emit((ch + 2) % 3, (ch - 1) * kCh, threadIdx.x - 32, blockDim.x - 32);
+      stage((ch + 1) % 3, (ch + 1) * kCh, threadIdx.x - 32, blockDim.x - 32);
+    }
     if (threadIdx.x == 0) {
       const int qend = min(kCh, nL - ch * kCh);
       for (int i = 0; i < qend; ++i) {
         const int q = ch * kCh + i;
         const int c = sc_c[b][i];
         const int sp = (c < n1) ? 1 : 2;
+        const double Dq = sc_D[b][i], zq = sc_z[b][i];
         if (q == 0) {
-          pj = c; pD = sc_D[b][i]; pz = sc_z[b][i]; ps = sp; prev_rot = false;
+          pj = c; pD = Dq; pz = zq; ps = sp; prev_rot = false;
           continue;
         }
         bool rot;
@@ -482,37 +520,41 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
         const uint8_t f = sc_f[b][i];
         if (!prev_rot) {
           rot = (f & 1) != 0;
-          if (rot) { cc = sc_cs[b][i]; ss = sc_sn[b][i]; tau = sc_tau[b][i]; dp = sc_dp[b][i]; di = sc_di[b][i]; }
+          if (rot) { tau = sc_tau[b][i]; di = sc_di[b][i]; }
           prev_simple = rot;
-        } else {  // the last kept pole was rotated: test against its current values
-          const double D = sc_D[b][i], z = sc_z[b][i];
-          rot = prev_simple ? (f & 2) != 0 : type2_test(D, z, pD, pz, tol);
-          if (rot) type2_rot(D, z, pD, pz, cc, ss, tau, dp, di);
+        } else {  // the survivor was rotated: test against its current values
+          rot = prev_simple ? (f & 2) != 0 : type2_test(Dq, zq, pD, pz, tol);
+          if (rot) {
+            type2_rot(Dq, zq, pD, pz, cc, ss, tau, dp, di);
+            sc_cs[b][i] = cc;
+            sc_sn[b][i] = ss;
+            sc_dp[b][i] = dp;
+          }
           prev_simple = false;
         }
+        o_pj[b][i] = pj;
         if (rot) {  // type 2: rotate (pj, c) so that z_pj = 0; pj is deflated
-          const int64_t ro = v0 + nr;
-          V.rij[4 * ro + 0] = pj;
-          V.rij[4 * ro + 1] = c;
-          V.rij[4 * ro + 2] = ps | (sp << 8);
-          V.rcs[2 * ro + 0] = cc;
-          V.rcs[2 * ro + 1] = ss;
-          if (pj != last_rot_i) V.rch[v0 + nch++] = nr;
-          last_rot_i = c;
-          ++nr;
-          const int u = ps | sp;
-          V.dcol[v0 + ndf] = pj; V.dval[v0 + ndf] = dp; V.dseg[v0 + ndf] = (uint8_t)u; ++ndf;
-          pj = c; pD = di; pz = tau; ps = u;
+          o_code[b][i] = prev_rot ? 1 : 3;
+          o_idx[b][i] = nr++;
+          if (!prev_rot) o_cidx[b][i] = nch++;
+          o_sup[b][i] = ps | (sp << 8);
+          pj = c; pD = di; pz = tau; ps |= sp;
           prev_rot = true;
         } else {
-          V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
-          pj = c; pD = sc_D[b][i]; pz = sc_z[b][i]; ps = sp;
+          o_code[b][i] = 0;
+          o_idx[b][i] = K++;
+          o_sup[b][i] = ps;
+          sc_cs[b][i] = pD;
+          sc_sn[b][i] = pz;
+          pj = c; pD = Dq; pz = zq; ps = sp;
           prev_rot = false;
         }
       }
     }
     __syncthreads();
   }
+  if (nch_chunks > 0) emit((nch_chunks - 1) % 3, (nch_chunks - 1) * kCh, threadIdx.x, blockDim.x);
+  const int ndf = t1 + nr;
   if (threadIdx.x == 0) {
     if (pj >= 0) {
       V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
@@ -687,6 +729,48 @@ __device__ __forceinline__ void secular_sums(const double* D, const double* z, i
   sabs = phi - psi;
 }
 
+// Next iterate from the two-pole rational model of g at tau: psi and phi are
+// each replaced by a constant plus the term of the nearest pole on their side
+// (d_j at dl, d_{j+1} at dr, in the origin's frame), matching value and slope;
+// the model's root in the bracket (lo, hi), else the bracket's midpoint.
+__device__ __forceinline__ double model_step(int j, int K, double irho, double dl, double dr, double tau, double gv,
+                                             double psi, double dpsi, double phi, double dphi, double lo,
+                                             double hi) {
+  const double p = dl - tau;  // < 0
+  double h = 0.0;
+  bool ok = true;
+  if (j < K - 1) {
+    const double q = dr - tau;  // > 0
+    const double b1 = dpsi * p * p, b2 = dphi * q * q;
+    const double A = irho + (psi - b1 / p) + (phi - b2 / q);
+    const double B = A * (p + q) + b1 + b2;
+    const double C = p * q * gv;
+    if (A == 0.0) {
+      h = C / B;
+    } else {
+      const double disc = B * B - 4.0 * A * C;
+      if (disc < 0.0) {
+        ok = false;
+      } else {
+        const double w = B + copysign(sqrt(disc), B);
+        const double h1 = (w != 0.0) ? 2.0 * C / w : 0.0;
+        const double h2 = w / (2.0 * A);
+        const bool in1 = (h1 > p && h1 < q), in2 = (h2 > p && h2 < q);
+        if (in1 && (!in2 || fabs(h1) <= fabs(h2))) h = h1;
+        else if (in2) h = h2;
+        else ok = false;
+      }
+    }
+  } else {
+    const double b1 = dpsi * p * p;
+    const double A = irho + (psi - b1 / p) + phi;
+    if (A != 0.0) h = p + b1 / A; else ok = false;
+  }
+  double tn = tau + h;
+  if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5 * (lo + hi);
+  return tn;
+}
+
 // FP64 iteration for root j from origin org, starting at tau inside [lo, hi] with
 // the sums at tau already known.  Two-pole rational model of g around tau (the
 // nearest poles exact), safeguarded by bisection; stops when |g| is at rounding
@@ -708,43 +792,84 @@ __device__ int secular_fp64(const double* D, const double* z, int K, int j, doub
     const double gv = irho + psi + phi;
     if (gv == 0.0 || fabs(gv) <= 8.0 * kEps * (irho + sabs)) { conv = true; break; }
     if (gv < 0.0) lo = tau; else hi = tau;
-    const double p = dl - tau;  // < 0
-    double h = 0.0;
-    bool ok = true;
-    if (j < K - 1) {
-      const double q = dr - tau;  // > 0
-      const double b1 = dpsi * p * p, b2 = dphi * q * q;
-      const double A = irho + (psi - b1 / p) + (phi - b2 / q);
-      const double B = A * (p + q) + b1 + b2;
-      const double C = p * q * gv;
-      if (A == 0.0) {
-        h = C / B;
-      } else {
-        const double disc = B * B - 4.0 * A * C;
-        if (disc < 0.0) {
-          ok = false;
-        } else {
-          const double w = B + copysign(sqrt(disc), B);
-          const double h1 = (w != 0.0) ? 2.0 * C / w : 0.0;
-          const double h2 = w / (2.0 * A);
-          const bool in1 = (h1 > p && h1 < q), in2 = (h2 > p && h2 < q);
-          if (in1 && (!in2 || fabs(h1) <= fabs(h2))) h = h1;
-          else if (in2) h = h2;
-          else ok = false;
-        }
-      }
-    } else {
-      const double b1 = dpsi * p * p;
-      const double A = irho + (psi - b1 / p) + phi;
-      if (A != 0.0) h = p + b1 / A; else ok = false;
-    }
-    double tn = tau + h;
-    if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5 * (lo + hi);
+    const double tn = model_step(j, K, irho, dl, dr, tau, gv, psi, dpsi, phi, dphi, lo, hi);
     const bool small_step = fabs(tn - tau) <= 2.0 * kEps * fabs(tau);
     tau = tn;
     if (small_step || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) { conv = true; break; }
   }
   return passes;
+}
+
+// First FP64 step for root j < K-1 from a close starting point (the FP32
+// estimate), arranged so that the next iterate can be checked without another
+// pass over all poles.  In the one full pass, the term of each lane's pole in the
+// window [j-15, j+16] (the 32 poles nearest the root) is kept apart from the far
+// terms, whose sums of t, t r and t r^2 (r = 1/(delta_i - tau)) are kept per side.
+// After the model step h, the far sums at tau + h follow from
+//   t_i(tau + h) = t_i / (1 - h r_i) = t_i (1 + h r_i + (h r_i)^2) + rest,
+//   |sum of rests| <= (sum of far |t_i|) q^3 / (1 - q),  q = |h| / (distance from
+//   tau to the nearest far pole),
+// and only the window terms are evaluated afresh.  If g at tau + h passes the
+// convergence test with that bound added to |g|, the root is accepted there.
+// Returns true when accepted (tau updated, conv set); otherwise tau is the next
+// iterate, lo / hi hold the bracket, and the caller continues with full passes.
+__device__ bool secular_certified(const double* D, const double* z, int K, int j, double irho, int org,
+                                  double& tau, double& lo, double& hi, bool& conv) {
+  const int lane = threadIdx.x & 31;
+  const double dorg = D[org];
+  const double dl = D[j] - dorg, dr = D[j + 1] - dorg;
+  const int wlo = j - 15, whi = j + 16;
+  const int iw = wlo + ((lane - wlo) & 31);  // this lane's window pole
+  const bool wv = iw >= 0 && iw < K, wleft = iw <= j;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, wt = 0.0, wd = 0.0;
+  for (int i = lane; i < K; i += 32) {
+    const double r = rcp_nr((D[i] - dorg) - tau);
+    const double zi = z[i];
+    const double t = zi * zi * r;
+    const double tr = t * r;
+    if (i == iw) { wt = t; wd = tr; }
+    else if (i <= j) { a0 += t; a1 += tr; a2 = fma(tr, r, a2); }
+    else { b0 += t; b1 += tr; b2 = fma(tr, r, b2); }
+  }
+  const double wtl = (wv && wleft) ? wt : 0.0, wtr = (wv && !wleft) ? wt : 0.0;
+  const double wdl = (wv && wleft) ? wd : 0.0, wdr = (wv && !wleft) ? wd : 0.0;
+  a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
+  b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2);
+  const double psi = a0 + warp_sum(wtl), dpsi = a1 + warp_sum(wdl);
+  const double phi = b0 + warp_sum(wtr), dphi = b1 + warp_sum(wdr);
+  const double gv = irho + psi + phi;
+  conv = false;
+  if (gv == 0.0 || fabs(gv) <= 8.0 * kEps * (irho + (phi - psi))) { conv = true; return true; }
+  if (gv < 0.0) lo = tau; else hi = tau;
+  const double tn = model_step(j, K, irho, dl, dr, tau, gv, psi, dpsi, phi, dphi, lo, hi);
+  const double h = tn - tau;
+  if (fabs(h) <= 2.0 * kEps * fabs(tau) || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) {
+    tau = tn;
+    conv = true;
+    return true;
+  }
+  // distance from tau to the nearest far pole (poles are sorted)
+  double dmin = HUGE_VAL;
+  if (wlo - 1 >= 0) dmin = fmin(dmin, fabs((D[wlo - 1] - dorg) - tau));
+  if (whi + 1 < K) dmin = fmin(dmin, fabs((D[whi + 1] - dorg) - tau));
+  const double q = fabs(h) / dmin;
+  tau = tn;
+  if (!(q < 1e-3)) return false;
+  const double rest = (b0 - a0) * (q * q * q) / (1.0 - q);
+  const double fl = a0 + h * (a1 + h * a2), fr = b0 + h * (b1 + h * b2);
+  double ut = 0.0;
+  if (wv) ut = z[iw] * z[iw] * rcp_nr((D[iw] - dorg) - tn);
+  const double ul = warp_sum(wleft ? ut : 0.0), ur = warp_sum(wleft ? 0.0 : ut);
+  const double g2 = irho + (fl + ul) + (fr + ur);
+  const double sabs2 = (fr + ur) - (fl + ul);
+  if (fabs(g2) + rest <= 8.0 * kEps * (irho + sabs2)) {
+    conv = true;
+    return true;
+  }
+  if (fabs(g2) > rest) {
+    if (g2 < 0.0) lo = tau; else hi = tau;
+  }
+  return false;
 }
 
 // FP32 pre-iteration for root j < K-1 in the frame of pole j: tau in (0, gap).
@@ -836,8 +961,12 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
       if (t32 <= 0.5f * (float)gap) { org = j; lo = 0.0; hi = gap; tau = (double)t32; }
       else { org = j + 1; lo = -gap; hi = 0.0; tau = (double)t32 - gap; }
       if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
-      secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
-      passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+      const bool tried = max_iter >= 2;
+      if (!tried || !secular_certified(D, z, K, j, irho, org, tau, lo, hi, conv)) {
+        secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+        if (tried) ++passes;
+        passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+      }
       // converged nearer the other pole: continue from that pole
       const bool far = conv && ((org == j) ? (tau > 0.5 * gap) : (tau < -0.5 * gap));
       if (far) {
@@ -898,24 +1027,66 @@ cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) 
 
 // ---------------------------------------------------------------------------
 // k_lowner: zhat_i^2 = prod_j (lambda_j - d_i) / (rho prod_{j != i} (d_j - d_i)),
-// as the product of the ratios (lambda_j - d_i)/(d_j - d_i) for j < i,
-// (lambda_j - d_i)/(d_{j+1} - d_i) for i <= j < K-1 and (lambda_{K-1} - d_i)/rho,
-// each in (0, 1]; lambda_j - d_i = (d_org(j) - d_i) + tau_j.
+// with the factors paired as (lambda_j - d_i)/(d_j - d_i) for j < i,
+// (lambda_j - d_i)/(d_{j+1} - d_i) for i <= j < K-1 and (lambda_{K-1} - d_i)/rho
+// (each ratio in (0, 1]); lambda_j - d_i = (d_org(j) - d_i) + tau_j.
 // ---------------------------------------------------------------------------
+// Exponent field of x, and x scaled by 2^(1023 - e) (into [1, 2) when e is the
+// exponent field of a normal x): integer work plus one multiplication.
+__device__ __forceinline__ int dexp_field(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+__device__ __forceinline__ double dscale(double x, int e) { return x * __hiloint2double((2046 - e) << 20, 0); }
+
+// (x, ex) -> mantissa in [1, 2) and exponent, for normal x (zero, subnormal and
+// non-finite values are left as they are)
+__device__ __forceinline__ void dnorm(double& x, int& ex) {
+  const int f = dexp_field(x);
+  if (f > 0 && f < 2047) {
+    x = dscale(x, f);
+    ex += f - 1023;
+  }
+}
+
+// The numerator prod_j (lambda_j - d_i) and the denominator prod of the paired
+// pole differences are accumulated as two separate products with their exponents
+// kept apart (one division per pole instead of one per term): both stay within
+// [2^-600, 2^600] and are renormalised when they leave it.
 __device__ double lowner_zhat(const double* D, const int* org, const double* tau, int K, int i, double rho,
                               double zsign) {
   const double di = D[i];
-  double pr = 1.0;
+  double pn = 1.0, pd = 1.0;
+  int en = 0, ed = 0;  // pn 2^en, pd 2^ed
   for (int j = threadIdx.x & 31; j < K; j += 32) {
     const double num = (D[org[j]] - di) + tau[j];
-    if (j == K - 1) pr *= num / rho;
-    else {
-      const double den = (j < i) ? (D[j] - di) : (D[j + 1] - di);
-      pr *= num * rcp_nr(den);
+    const double den = (j == K - 1) ? rho : ((j < i) ? D[j] - di : D[j + 1] - di);
+    pn *= num;
+    pd *= den;
+    const int fn = dexp_field(pn), fd = dexp_field(pd);
+    if (fn < 423 || fn > 1623 || fd < 423 || fd > 1623) {
+      dnorm(pn, en);
+      dnorm(pd, ed);
     }
   }
-  pr = warp_prod(pr);
-  return copysign(sqrt(pr), zsign);
+  dnorm(pn, en);
+  dnorm(pd, ed);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double qn = __shfl_xor_sync(0xffffffffu, pn, o), qd = __shfl_xor_sync(0xffffffffu, pd, o);
+    const int gn = __shfl_xor_sync(0xffffffffu, en, o), gd = __shfl_xor_sync(0xffffffffu, ed, o);
+    pn *= qn;
+    pd *= qd;
+    en += gn;
+    ed += gd;
+    dnorm(pn, en);
+    dnorm(pd, ed);
+  }
+  // zhat_i^2 = (pn / pd) 2^(en - ed), with an even exponent for the root
+  double r = pn / pd;
+  int E = en - ed;
+  if (E & 1) {
+    r *= 2.0;
+    E -= 1;
+  }
+  return copysign(ldexp(sqrt(r), E / 2), zsign);
 }
 
 __global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int nprob_act, int64_t nslots) {
@@ -1092,29 +1263,42 @@ cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, int bm, int bn,
 // k_copy_defl: deflated eigenvectors (columns of the rotated Q) to their output
 // columns; entries outside the column's row support are written as zeros.
 // ---------------------------------------------------------------------------
+// Warp w of block (g, y, z) copies rows [y*kCopyRows, (y+1)*kCopyRows) of the
+// deflated columns z*8+w, z*8+w + 8*gridDim.z, ... of merge g: rows and columns
+// are both spread over the grid, so a few long columns and many short ones both
+// fill the machine.
+static constexpr int kCopyRows = 2048;
+
 __global__ void __launch_bounds__(256) k_copy_defl(Plan P, int level) {
   const int64_t g = blockIdx.x;
   const int ndf = P.m.nd[g];
   if (ndf == 0) return;
   const Node nd = make_node(P, level, g);
   const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
-  const int r = blockIdx.y * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const int half = r < n1 ? 1 : 2;
+  const int r0 = blockIdx.y * kCopyRows;
+  if (r0 >= n) return;
+  const int r1 = min(n, r0 + kCopyRows);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int64_t v0 = nd.v0;
-  for (int q = blockIdx.z; q < ndf; q += gridDim.z) {
+  for (int q = blockIdx.z * nw + (threadIdx.x >> 5); q < ndf; q += gridDim.z * nw) {
     const int c = P.v.dcol[v0 + q];
     const int sp = P.v.dseg[v0 + q];
     const int o = P.v.posd[v0 + q];
     if (o < 0 || o >= n) continue;
-    const double x = (sp & half) ? nd.src[r + (int64_t)c * nd.lds] : 0.0;
-    nd.dst[r + (int64_t)o * nd.ldd] = x;
+    const double* src = nd.src + (int64_t)c * nd.lds;
+    double* dst = nd.dst + (int64_t)o * nd.ldd;
+#pragma unroll 8
+    for (int r = r0 + lane; r < r1; r += 32) {
+      const int half = r < n1 ? 1 : 2;
+      dst[r] = (sp & half) ? src[r] : 0.0;
+    }
   }
 }
 
 cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
-  const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(64, L.max_n / 256));
-  dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), gz);
+  const unsigned gy = (unsigned)((L.max_n + kCopyRows - 1) / kCopyRows);
+  const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(256, L.max_n / 64));
+  dim3 grid((unsigned)L.merges, gy, gz);
   k_copy_defl<<<grid, 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
 }
@@ -1132,19 +1316,40 @@ __global__ void __launch_bounds__(256) k_sign_out(Plan P, int sign_normalise) {
   const int64_t c = s - p.voff;
   double* col = P.Q0 + p.off_q + c * p.ld0;
   if (sign_normalise) {
+    // eight independent loads per lane in flight
     double best = -1.0;
     int64_t bi = 0;  // stays in range even for a column of NaNs
-    for (int64_t r = lane; r < p.n; r += 32) {
-      const double a = fabs(col[r]);
-      if (a > best) { best = a; bi = r; }
+    for (int64_t r0 = 0; r0 < p.n; r0 += 256) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int64_t r = r0 + k * 32 + lane;
+        v[k] = r < p.n ? fabs(col[r]) : -1.0;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (v[k] > best) { best = v[k]; bi = r0 + k * 32 + lane; }
     }
     for (int o = 16; o > 0; o >>= 1) {
       const double ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
       if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
     }
-    if (col[bi] < 0.0)
-      for (int64_t r = lane; r < p.n; r += 32) col[r] = -col[r];
+    if (col[bi] < 0.0) {
+      for (int64_t r0 = 0; r0 < p.n; r0 += 256) {
+        double v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int64_t r = r0 + k * 32 + lane;
+          v[k] = r < p.n ? col[r] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int64_t r = r0 + k * 32 + lane;
+          if (r < p.n) col[r] = -v[k];
+        }
+      }
+    }
   }
   if (lane == 0) P.lam_out[p.off_de + c] = P.v.lam[s];
 }
