@@ -800,7 +800,7 @@ __device__ int secular_fp64(const double* D, const double* z, int K, int j, doub
   return passes;
 }
 
-// First FP64 step for root j < K-1 from a close starting point (the FP32
+// First FP64 step for root j from a close starting point (the FP32
 // estimate), arranged so that the next iterate can be checked without another
 // pass over all poles.  In the one full pass, the term of each lane's pole in the
 // window [j-15, j+16] (the 32 poles nearest the root) is kept apart from the far
@@ -817,7 +817,7 @@ __device__ bool secular_certified(const double* D, const double* z, int K, int j
                                   double& tau, double& lo, double& hi, bool& conv) {
   const int lane = threadIdx.x & 31;
   const double dorg = D[org];
-  const double dl = D[j] - dorg, dr = D[j + 1] - dorg;
+  const double dl = D[j] - dorg, dr = (j < K - 1) ? D[j + 1] - dorg : 0.0;
   const int wlo = j - 15, whi = j + 16;
   const int iw = wlo + ((lane - wlo) & 31);  // this lane's window pole
   const bool wv = iw >= 0 && iw < K, wleft = iw <= j;
@@ -872,25 +872,33 @@ __device__ bool secular_certified(const double* D, const double* z, int K, int j
   return false;
 }
 
-// FP32 pre-iteration for root j < K-1 in the frame of pole j: tau in (0, gap).
-// Far poles use FP32 coordinates xz[i].x = d_i - d_c (one centre per merge) and
-// xz[i].y = z_i^2; the 32 poles nearest to j (one per lane) use their FP64
-// differences, so close neighbours keep their relative accuracy.  The same
-// two-pole model as in FP64.  Returns false if no usable estimate was found.
-__device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, float irho, float gap, float& tau_out) {
+// FP32 pre-iteration for root j in the frame of pole j: tau in (0, width) with
+// width = d_{j+1} - d_j, or for the last root width = rho |z|^2.  Far poles use
+// FP32 coordinates xz[i].x = d_i - d_c (one centre per merge) and xz[i].y = z_i^2;
+// the 32 poles nearest to j (one per lane) use their FP64 differences, so close
+// neighbours keep their relative accuracy.  Interior roots start at the midpoint
+// with the two-pole model; the last root starts from the root of g with every
+// other pole frozen at tau = 0 (it often lies far below the interval's middle)
+// and iterates the one-pole model.  Returns false if no usable estimate was found.
+__device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, float irho, float width,
+                             float& tau_out) {
   const int lane = threadIdx.x & 31;
+  const bool last = j == K - 1;
   // the window pole of this lane: the i = lane (mod 32) in [j - 15, j + 16]
   const int iw = j - 15 + ((lane - (j - 15)) & 31);
   const float dw = (iw >= 0 && iw < K) ? (float)(D[iw] - D[j]) : 0.0f;
   const float xj = xz[j].x;
-  float lo = 0.0f, hi = gap, tau = 0.5f * gap;
+  float lo = 0.0f, hi = width, tau = 0.5f * width;
   for (int it = 0; it < 12; ++it) {
+    // it == 0 for the last root: the sum of the other poles' terms at tau = 0
+    const float tv = (last && it == 0) ? 0.0f : tau;
     float a = 0.0f, da = 0.0f, b = 0.0f, db = 0.0f;
     for (int i = lane; i < K; i += 32) {
       const float2 v = xz[i];
       const float del = (i == iw) ? dw : v.x - xj;
+      if (last && it == 0 && i == j) continue;
       float r;
-      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tau));
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tv));
       const float t = v.y * r;
       if (i <= j) { a += t; da = fmaf(t, r, da); }
       else { b += t; db = fmaf(t, r, db); }
@@ -902,31 +910,44 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
       b += __shfl_xor_sync(0xffffffffu, b, o);
       db += __shfl_xor_sync(0xffffffffu, db, o);
     }
+    if (last && it == 0) {
+      const float den = irho + a;
+      const float t0 = den > 0.0f ? xz[j].y / den : -1.0f;
+      if (t0 > 0.0f && t0 < width) tau = t0;
+      continue;
+    }
     const float gv = irho + a + b;
     if (!isfinite(gv)) return false;
     if (gv == 0.0f) break;
     if (gv < 0.0f) lo = tau; else hi = tau;
-    const float p = -tau, q = gap - tau;
-    const float b1 = da * p * p, b2 = db * q * q;
-    const float A = irho + (a - b1 / p) + (b - b2 / q);
-    const float B = A * (p + q) + b1 + b2;
-    const float C = p * q * gv;
+    const float p = -tau;
     float h = 0.0f;
     bool ok = true;
-    if (A == 0.0f) {
-      h = C / B;
+    if (last) {
+      const float b1 = da * p * p;
+      const float A = irho + (a - b1 / p) + b;
+      if (A != 0.0f) h = p + b1 / A; else ok = false;
     } else {
-      const float disc = B * B - 4.0f * A * C;
-      if (disc < 0.0f) {
-        ok = false;
+      const float q = width - tau;
+      const float b1 = da * p * p, b2 = db * q * q;
+      const float A = irho + (a - b1 / p) + (b - b2 / q);
+      const float B = A * (p + q) + b1 + b2;
+      const float C = p * q * gv;
+      if (A == 0.0f) {
+        h = C / B;
       } else {
-        const float w = B + copysignf(sqrtf(disc), B);
-        const float h1 = (w != 0.0f) ? 2.0f * C / w : 0.0f;
-        const float h2 = w / (2.0f * A);
-        const bool in1 = (h1 > p && h1 < q), in2 = (h2 > p && h2 < q);
-        if (in1 && (!in2 || fabsf(h1) <= fabsf(h2))) h = h1;
-        else if (in2) h = h2;
-        else ok = false;
+        const float disc = B * B - 4.0f * A * C;
+        if (disc < 0.0f) {
+          ok = false;
+        } else {
+          const float w = B + copysignf(sqrtf(disc), B);
+          const float h1 = (w != 0.0f) ? 2.0f * C / w : 0.0f;
+          const float h2 = w / (2.0f * A);
+          const bool in1 = (h1 > p && h1 < q), in2 = (h2 > p && h2 < q);
+          if (in1 && (!in2 || fabsf(h1) <= fabsf(h2))) h = h1;
+          else if (in2) h = h2;
+          else ok = false;
+        }
       }
     }
     float tn = tau + h;
@@ -935,7 +956,7 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
     tau = tn;
     if (small || (hi - lo) <= 4e-7f * hi) break;
   }
-  if (!(tau > 0.0f && tau < gap)) return false;
+  if (!(tau > 0.0f && tau < width)) return false;
   tau_out = tau;
   return true;
 }
@@ -953,42 +974,46 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
   double lo, hi, tau;
   double psi, dpsi, phi, dphi, sabs;
   int passes = 1;
-  if (j < K - 1) {
-    const double gap = D[j + 1] - D[j];
-    float t32 = 0.0f;
-    const bool have32 = xz != nullptr && gap > 0.0 && secular_fp32(D, xz, K, j, (float)irho, (float)gap, t32);
-    if (have32) {
-      if (t32 <= 0.5f * (float)gap) { org = j; lo = 0.0; hi = gap; tau = (double)t32; }
-      else { org = j + 1; lo = -gap; hi = 0.0; tau = (double)t32 - gap; }
-      if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
-      const bool tried = max_iter >= 2;
-      if (!tried || !secular_certified(D, z, K, j, irho, org, tau, lo, hi, conv)) {
-        secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
-        if (tried) ++passes;
-        passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
-      }
-      // converged nearer the other pole: continue from that pole
-      const bool far = conv && ((org == j) ? (tau > 0.5 * gap) : (tau < -0.5 * gap));
-      if (far) {
-        if (org == j) { org = j + 1; tau -= gap; lo -= gap; hi -= gap; }
-        else { org = j; tau += gap; lo += gap; hi += gap; }
-        secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
-        ++passes;
-        passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
-      }
-      org_out = org;
-      tau_out = tau;
-      iters = min(passes, max_iter);
-      return;
-    }
-    secular_sums(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
-    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; tau = hi; }
-    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; tau = lo; }
+  const bool last = j == K - 1;
+  double width;
+  if (!last) {
+    width = D[j + 1] - D[j];
   } else {
     double zz = 0.0;
     for (int i = threadIdx.x & 31; i < K; i += 32) zz = fma(z[i], z[i], zz);
-    zz = warp_sum(zz);
-    org = K - 1; lo = 0.0; hi = rho * zz; tau = hi;
+    width = rho * warp_sum(zz);
+  }
+  float t32 = 0.0f;
+  if (xz != nullptr && width > 0.0 && secular_fp32(D, xz, K, j, (float)irho, (float)width, t32)) {
+    if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
+    else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
+    if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+    const bool tried = max_iter >= 2;
+    if (!tried || !secular_certified(D, z, K, j, irho, org, tau, lo, hi, conv)) {
+      secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+      if (tried) ++passes;
+      passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+    }
+    // an interior root that converged nearer the other pole: continue from that pole
+    const bool far = !last && conv && ((org == j) ? (tau > 0.5 * width) : (tau < -0.5 * width));
+    if (far) {
+      if (org == j) { org = j + 1; tau -= width; lo -= width; hi -= width; }
+      else { org = j; tau += width; lo += width; hi += width; }
+      secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+      ++passes;
+      passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+    }
+    org_out = org;
+    tau_out = tau;
+    iters = min(passes, max_iter);
+    return;
+  }
+  if (!last) {
+    secular_sums(D, z, K, j, D[j], 0.5 * width, psi, dpsi, phi, dphi, sabs);
+    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * width; tau = hi; }
+    else { org = j + 1; lo = -0.5 * width; hi = 0.0; tau = lo; }
+  } else {
+    org = K - 1; lo = 0.0; hi = width; tau = hi;
     secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
   }
   passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
@@ -1005,10 +1030,13 @@ __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_ac
   int org, it;
   double tau;
   bool conv;
-  secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
+  // the merge's first slot takes its last root, usually the slowest to converge,
+  // so that it starts with the first wave of warps instead of ending the kernel
+  const int j = S.j == 0 ? S.K - 1 : S.j - 1;
+  secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, S.K, j, S.rho, P.max_iter, org, tau, it, conv);
   if ((threadIdx.x & 31) == 0) {
-    P.v.org[S.v0 + S.j] = org;
-    P.v.tau[S.v0 + S.j] = tau;
+    P.v.org[S.v0 + j] = org;
+    P.v.tau[S.v0 + j] = tau;
     if (!conv) set_status(P.status, TDC_ENOCONV);
     if (P.stats) {
       atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
