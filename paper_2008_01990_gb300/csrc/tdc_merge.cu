@@ -800,19 +800,19 @@ __device__ int secular_fp64(const double* D, const double* z, int K, int j, doub
   return passes;
 }
 
-// First FP64 step for root j from a close starting point (the FP32
-// estimate), arranged so that the next iterate can be checked without another
-// pass over all poles.  In the one full pass, the term of each lane's pole in the
-// window [j-15, j+16] (the 32 poles nearest the root) is kept apart from the far
-// terms, whose sums of t, t r and t r^2 (r = 1/(delta_i - tau)) are kept per side.
-// After the model step h, the far sums at tau + h follow from
-//   t_i(tau + h) = t_i / (1 - h r_i) = t_i (1 + h r_i + (h r_i)^2) + rest,
-//   |sum of rests| <= (sum of far |t_i|) q^3 / (1 - q),  q = |h| / (distance from
-//   tau to the nearest far pole),
-// and only the window terms are evaluated afresh.  If g at tau + h passes the
-// convergence test with that bound added to |g|, the root is accepted there.
-// Returns true when accepted (tau updated, conv set); otherwise tau is the next
-// iterate, lo / hi hold the bracket, and the caller continues with full passes.
+// FP64 iteration for root j from a close starting point (the FP32 estimate)
+// with a single pass over all poles.  In that pass, at tau1, the term of each
+// lane's pole in the window [j-15, j+16] (the 32 poles nearest the root) is kept
+// apart from the far terms, whose sums of t, t r and t r^2 (r = 1/(delta_i - tau1))
+// are kept per side.  The following iterates tau = tau1 + e re-evaluate only the
+// window terms; the far sums follow from
+//   t_i(tau1 + e) = t_i / (1 - e r_i) = t_i (1 + e r_i + (e r_i)^2) + rest_i,
+//   |sum of rest_i| <= (sum of far |t_i|) q^3 / (1 - q),  q = |e| / (distance from
+//   tau1 to the nearest far pole),
+// (their slopes likewise, to first order, for the model only).  A root is
+// accepted when |g| plus that bound passes the convergence test.  Returns true
+// when accepted (tau updated, conv set); otherwise tau is the last iterate,
+// lo / hi hold the bracket, and the caller continues with full passes.
 __device__ bool secular_certified(const double* D, const double* z, int K, int j, double irho, int org,
                                   double& tau, double& lo, double& hi, bool& conv) {
   const int lane = threadIdx.x & 31;
@@ -821,9 +821,11 @@ __device__ bool secular_certified(const double* D, const double* z, int K, int j
   const int wlo = j - 15, whi = j + 16;
   const int iw = wlo + ((lane - wlo) & 31);  // this lane's window pole
   const bool wv = iw >= 0 && iw < K, wleft = iw <= j;
+  const double zw2 = wv ? z[iw] * z[iw] : 0.0, dw = wv ? D[iw] - dorg : 0.0;
+  const double tau1 = tau;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, wt = 0.0, wd = 0.0;
   for (int i = lane; i < K; i += 32) {
-    const double r = rcp_nr((D[i] - dorg) - tau);
+    const double r = rcp_nr((D[i] - dorg) - tau1);
     const double zi = z[i];
     const double t = zi * zi * r;
     const double tr = t * r;
@@ -831,44 +833,53 @@ __device__ bool secular_certified(const double* D, const double* z, int K, int j
     else if (i <= j) { a0 += t; a1 += tr; a2 = fma(tr, r, a2); }
     else { b0 += t; b1 += tr; b2 = fma(tr, r, b2); }
   }
-  const double wtl = (wv && wleft) ? wt : 0.0, wtr = (wv && !wleft) ? wt : 0.0;
-  const double wdl = (wv && wleft) ? wd : 0.0, wdr = (wv && !wleft) ? wd : 0.0;
   a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
   b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2);
-  const double psi = a0 + warp_sum(wtl), dpsi = a1 + warp_sum(wdl);
-  const double phi = b0 + warp_sum(wtr), dphi = b1 + warp_sum(wdr);
-  const double gv = irho + psi + phi;
-  conv = false;
-  if (gv == 0.0 || fabs(gv) <= 8.0 * kEps * (irho + (phi - psi))) { conv = true; return true; }
-  if (gv < 0.0) lo = tau; else hi = tau;
-  const double tn = model_step(j, K, irho, dl, dr, tau, gv, psi, dpsi, phi, dphi, lo, hi);
-  const double h = tn - tau;
-  if (fabs(h) <= 2.0 * kEps * fabs(tau) || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi))) {
-    tau = tn;
-    conv = true;
-    return true;
-  }
-  // distance from tau to the nearest far pole (poles are sorted)
+  // distance from tau1 to the nearest far pole (poles are sorted)
   double dmin = HUGE_VAL;
-  if (wlo - 1 >= 0) dmin = fmin(dmin, fabs((D[wlo - 1] - dorg) - tau));
-  if (whi + 1 < K) dmin = fmin(dmin, fabs((D[whi + 1] - dorg) - tau));
-  const double q = fabs(h) / dmin;
-  tau = tn;
-  if (!(q < 1e-3)) return false;
-  const double rest = (b0 - a0) * (q * q * q) / (1.0 - q);
-  const double fl = a0 + h * (a1 + h * a2), fr = b0 + h * (b1 + h * b2);
-  double ut = 0.0;
-  if (wv) ut = z[iw] * z[iw] * rcp_nr((D[iw] - dorg) - tn);
-  const double ul = warp_sum(wleft ? ut : 0.0), ur = warp_sum(wleft ? 0.0 : ut);
-  const double g2 = irho + (fl + ul) + (fr + ur);
-  const double sabs2 = (fr + ur) - (fl + ul);
-  if (fabs(g2) + rest <= 8.0 * kEps * (irho + sabs2)) {
-    conv = true;
-    return true;
+  if (wlo - 1 >= 0) dmin = fmin(dmin, fabs((D[wlo - 1] - dorg) - tau1));
+  if (whi + 1 < K) dmin = fmin(dmin, fabs((D[whi + 1] - dorg) - tau1));
+  conv = false;
+  double tc = tau1;
+  for (int k = 0; k < 8; ++k) {
+    const double e = tc - tau1;
+    const double q = fabs(e) / dmin;
+    // beyond q ~ eps^(1/3) the expansion is no better than a full evaluation
+    if (!(q < 4e-6)) break;
+    if (k > 0) {  // window terms at tc
+      wt = 0.0;
+      wd = 0.0;
+      if (wv) {
+        const double r = rcp_nr(dw - tc);
+        wt = zw2 * r;
+        wd = wt * r;
+      }
+    }
+    const double wtl = warp_sum((wv && wleft) ? wt : 0.0), wtr = warp_sum((wv && !wleft) ? wt : 0.0);
+    const double wdl = warp_sum((wv && wleft) ? wd : 0.0), wdr = warp_sum((wv && !wleft) ? wd : 0.0);
+    const double rest = k > 0 ? (b0 - a0) * (q * q * q) / (1.0 - q) : 0.0;
+    const double psi = a0 + e * (a1 + e * a2) + wtl, dpsi = a1 + 2.0 * e * a2 + wdl;
+    const double phi = b0 + e * (b1 + e * b2) + wtr, dphi = b1 + 2.0 * e * b2 + wdr;
+    const double gv = irho + psi + phi;
+    if (gv == 0.0 || fabs(gv) + rest <= 8.0 * kEps * (irho + (phi - psi))) {
+      tau = tc;
+      conv = true;
+      return true;
+    }
+    if (fabs(gv) > rest) {
+      if (gv < 0.0) lo = tc; else hi = tc;
+    }
+    const double tn = model_step(j, K, irho, dl, dr, tc, gv, psi, dpsi, phi, dphi, lo, hi);
+    // a vanishing step counts only where g is known to rounding level
+    const bool exact_g = rest <= kEps * (irho + (phi - psi));
+    if (exact_g && (fabs(tn - tc) <= 2.0 * kEps * fabs(tc) || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)))) {
+      tau = tn;
+      conv = true;
+      return true;
+    }
+    tc = tn;
   }
-  if (fabs(g2) > rest) {
-    if (g2 < 0.0) lo = tau; else hi = tau;
-  }
+  tau = tc;
   return false;
 }
 
