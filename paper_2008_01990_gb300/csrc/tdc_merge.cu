@@ -1217,11 +1217,29 @@ cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
 // over [roots, deflated]) with a bitonic network in the sort scratch; the
 // result goes to lam, and every root / deflated entry learns its output column.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool key_less(double ka, int ta, double kb, int tb) {
+// Doubles as unsigned integers in the same order (negative values with all bits
+// flipped, others with the sign bit set), so that the sort compares on the
+// integer pipes; NaN is mapped to +infinity first.
+__device__ __forceinline__ unsigned long long sort_key(double x) {
+  if (isnan(x)) x = INFINITY;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double key_value(unsigned long long k) {
+  return __longlong_as_double((long long)((k >> 63) ? (k & 0x7fffffffffffffffull) : ~k));
+}
+__device__ __forceinline__ bool key_less(unsigned long long ka, int ta, unsigned long long kb, int tb) {
   return ka < kb || (ka == kb && ta < tb);
 }
 
+// Ascending order of the node's eigenvalues: bitonic sort of (value, tag) pairs,
+// tags breaking ties (a total order).  Stages whose partners lie within a chunk
+// of kSortChunk entries run in shared memory, the wider ones in global memory.
+static constexpr int kSortChunk = 2048;
+
 __global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, int bn) {
+  __shared__ unsigned long long sk[kSortChunk];
+  __shared__ int stg[kSortChunk];
   const int64_t g = blockIdx.x;
   const Node nd = make_node(P, level, g);
   const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
@@ -1229,23 +1247,55 @@ __global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, in
   const int K = P.m.K[g];
   int P2 = 1;
   while (P2 < n) P2 <<= 1;
-  double* key = P.v.skey + 2 * v0;
+  unsigned long long* key = reinterpret_cast<unsigned long long*>(P.v.skey + 2 * v0);
   int* tag = P.v.stag + 2 * v0;
   for (int t = threadIdx.x; t < P2; t += blockDim.x) {
     double kv;
     if (t < K) { kv = P.v.Dk[v0 + P.v.org[v0 + t]] + P.v.tau[v0 + t]; tag[t] = t; }
     else if (t < n) { kv = P.v.dval[v0 + t - K]; tag[t] = t; }
     else { kv = INFINITY; tag[t] = 0x7fffffff; }
-    key[t] = isnan(kv) ? INFINITY : kv;  // total order: the n real entries come first
+    key[t] = sort_key(kv);  // the n real entries come first
   }
   __syncthreads();
-  for (int k = 2; k <= P2; k <<= 1) {
-    for (int jj = k >> 1; jj > 0; jj >>= 1) {
+  const int len = min(P2, kSortChunk);
+  // stages k0..k1 (jj from jtop down to 1) of every chunk in shared memory
+  auto chunk_stages = [&](int k0, int k1, int jtop) {
+    for (int c0 = 0; c0 < P2; c0 += len) {
+      for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        sk[t] = key[c0 + t];
+        stg[t] = tag[c0 + t];
+      }
+      __syncthreads();
+      for (int k = k0; k <= k1; k <<= 1) {
+        for (int jj = (k == k0 ? jtop : k >> 1); jj > 0; jj >>= 1) {
+          for (int t = threadIdx.x; t < len; t += blockDim.x) {
+            const int u = t ^ jj;
+            if (u > t) {
+              const bool up = ((c0 + t) & k) == 0;
+              const unsigned long long ka = sk[t], kb = sk[u];
+              const int ta = stg[t], tb = stg[u];
+              const bool sw = up ? key_less(kb, tb, ka, ta) : key_less(ka, ta, kb, tb);
+              if (sw) { sk[t] = kb; sk[u] = ka; stg[t] = tb; stg[u] = ta; }
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int t = threadIdx.x; t < len; t += blockDim.x) {
+        key[c0 + t] = sk[t];
+        tag[c0 + t] = stg[t];
+      }
+      __syncthreads();
+    }
+  };
+  if (P2 > 1) chunk_stages(2, len, 1);
+  for (int k = 2 * len; k <= P2; k <<= 1) {
+    for (int jj = k >> 1; jj >= len; jj >>= 1) {
       for (int t = threadIdx.x; t < P2; t += blockDim.x) {
         const int u = t ^ jj;
         if (u > t) {
           const bool up = (t & k) == 0;
-          const double ka = key[t], kb = key[u];
+          const unsigned long long ka = key[t], kb = key[u];
           const int ta = tag[t], tb = tag[u];
           const bool sw = up ? key_less(kb, tb, ka, ta) : key_less(ka, ta, kb, tb);
           if (sw) { key[t] = kb; key[u] = ka; tag[t] = tb; tag[u] = ta; }
@@ -1253,10 +1303,11 @@ __global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, in
       }
       __syncthreads();
     }
+    chunk_stages(k, k, len >> 1);
   }
   for (int p = threadIdx.x; p < n; p += blockDim.x) {
     const int t = tag[p];
-    P.v.lam[v0 + p] = key[p];
+    P.v.lam[v0 + p] = key_value(key[p]);
     if (t < K) P.v.posr[v0 + t] = p;
     else if (t < n) P.v.posd[v0 + t - K] = p;
   }
@@ -1355,37 +1406,44 @@ __global__ void __launch_bounds__(256) k_sign_out(Plan P, int sign_normalise) {
   const int64_t c = s - p.voff;
   double* col = P.Q0 + p.off_q + c * p.ld0;
   if (sign_normalise) {
-    // eight independent loads per lane in flight
-    double best = -1.0;
-    int64_t bi = 0;  // stays in range even for a column of NaNs
+    // |x| compared as the integer of its bits (same order for finite values, on the
+    // integer pipes); eight independent loads per lane in flight
+    const unsigned long long* cb = reinterpret_cast<const unsigned long long*>(col);
+    unsigned long long best = 0ull;
+    int64_t bi = 0;
+    bool any = false;
     for (int64_t r0 = 0; r0 < p.n; r0 += 256) {
-      double v[8];
+      unsigned long long v[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
         const int64_t r = r0 + k * 32 + lane;
-        v[k] = r < p.n ? fabs(col[r]) : -1.0;
+        v[k] = r < p.n ? (cb[r] & 0x7fffffffffffffffull) : 0ull;
       }
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (v[k] > best) { best = v[k]; bi = r0 + k * 32 + lane; }
+      for (int k = 0; k < 8; ++k) {
+        const int64_t r = r0 + k * 32 + lane;
+        if (r < p.n && v[k] <= 0x7ff0000000000000ull && (!any || v[k] > best)) { best = v[k]; bi = r; any = true; }
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      const bool oa = __shfl_xor_sync(0xffffffffu, any, o);
+      if (oa && (!any || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; any = true; }
     }
-    if (col[bi] < 0.0) {
+    if ((long long)cb[bi] < 0) {  // sign bit of the largest entry
+      unsigned long long* cw = reinterpret_cast<unsigned long long*>(col);
       for (int64_t r0 = 0; r0 < p.n; r0 += 256) {
-        double v[8];
+        unsigned long long v[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int64_t r = r0 + k * 32 + lane;
-          v[k] = r < p.n ? col[r] : 0.0;
+          v[k] = r < p.n ? cw[r] : 0ull;
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int64_t r = r0 + k * 32 + lane;
-          if (r < p.n) col[r] = -v[k];
+          if (r < p.n) cw[r] = v[k] ^ 0x8000000000000000ull;
         }
       }
     }
