@@ -341,9 +341,19 @@ def run_ours(args):
             "split": tdc.MERGE_SPLIT}[args.merge]
     # statistics on: the library records CUDA events around its phases on the call's
     # stream, so the per-kernel times below come from the timed steps themselves
-    opts = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1)
+    if args.leaf:
+        leaf = args.leaf
+        desc = desc.split(" leaf ")[0] + " leaf %d" % leaf + (" seed" + desc.split(" seed")[1] if " seed" in desc else "")
+    kw = {"split_min_K": args.split_min_k} if args.split_min_k else {}
     d = torch.tensor(d_np, device=dev)
     e = torch.tensor(e_np, device=dev)
+    if args.workload == "c4_32768" and not args.leaf and not args.split_min_k:
+        # this workload's leaf size is chosen by the autotuner (timed on the matrix)
+        from paper_2008_01990_gb300 import autotune
+        t = autotune.tune_single(d, e, mode, cache_path=None)
+        leaf, kw = t.leaf, {"split_min_K": t.split_min_K}
+        desc = desc.split(" leaf ")[0] + " leaf %d (autotuned, split_min_K %d) seed 4" % (leaf, t.split_min_K)
+    opts = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1, **kw)
     lam = torch.empty(n, dtype=torch.float64, device=dev)
     Q = torch.empty(n, n, dtype=torch.float64, device=dev).t()
     wsb = tdc.workspace(tdc.workspace_size(n, opts), dev)
@@ -509,6 +519,8 @@ def main():
                                                           "batched4096", "backward256"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--leaf", type=int, default=0, help="leaf size (default: the workload's)")
+    ap.add_argument("--split-min-k", type=int, default=0, help="smallest merge on the split path (default: library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

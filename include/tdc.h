@@ -94,7 +94,7 @@ typedef struct {
 } tdc_stats;
 
 /* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,
- * lr_tol 1e-15, split_slices 7, split_min_K 256, max_iter 64, sign_normalise 1,
+ * lr_tol 1e-15, split_slices 7, split_min_K 128, max_iter 64, sign_normalise 1,
  * collect_stats 0, spin_budget 2^24). */
 void tdc_default_opts(tdc_opts* o);
 

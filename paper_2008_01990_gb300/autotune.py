@@ -8,6 +8,7 @@ so that later calls skip the search.  Only the library's own entry points run.
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -18,7 +19,7 @@ from . import tdc
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "tdc_autotune.json")
 LEAVES = (16, 32, 48, 64)
-SPLIT_MIN_K = (128, 256, 512, 1024)
+SPLIT_MIN_K = (64, 128, 256, 512)
 
 
 def _bucket(n: int) -> int:
@@ -93,5 +94,37 @@ def tune_batched(sizes, d: torch.Tensor, e: torch.Tensor, off_de, merge_mode=tdc
         print("autotune", key, "best leaf %d split_min_K %d: %.3f ms" % (leaf, smk, t))
     if cache_path:
         cache[key] = {"leaf": leaf, "split_min_K": smk, "ms_sample": t, "candidates": len(results)}
+        _save(cache_path, cache)
+    return tdc.default_opts(leaf=leaf, merge_mode=merge_mode, split_min_K=smk)
+
+
+def tune_single(d: torch.Tensor, e: torch.Tensor, merge_mode=tdc.MERGE_AUTO, leaves=LEAVES, split_min_k=SPLIT_MIN_K,
+                cache_path: str | None = DEFAULT_CACHE, verbose=False):
+    """Options for tdc_eig on the tridiagonal (d, e) (device FP64): every (leaf,
+    split_min_K) candidate timed on the matrix itself.  Cached under the order, the
+    merge mode and a digest of the entries."""
+    n = int(d.numel())
+    h = hashlib.sha1(d.detach().cpu().numpy().tobytes() + e.detach().cpu().numpy().tobytes()).hexdigest()[:16]
+    key = "single:%d:%d:%s" % (n, merge_mode, h)
+    cache = _load(cache_path) if cache_path else {}
+    if key in cache:
+        c = cache[key]
+        return tdc.default_opts(leaf=c["leaf"], merge_mode=merge_mode, split_min_K=c["split_min_K"])
+    smks = split_min_k if merge_mode in (tdc.MERGE_AUTO, tdc.MERGE_SPLIT) else (128,)
+    cands = [tdc.default_opts(leaf=lf, merge_mode=merge_mode, split_min_K=sk) for lf in leaves for sk in smks]
+    ws = tdc.workspace(max(tdc.workspace_size(n, o) for o in cands), d.device)
+    lam = torch.empty(n, dtype=torch.float64, device=d.device)
+    Q = torch.empty(n, n, dtype=torch.float64, device=d.device).t()
+    results = []
+    for o in cands:
+        t = _time(lambda: tdc.eig(d, e, o, ws=ws, lam=lam, Q=Q), reps=2)
+        results.append((t, o.leaf, o.split_min_K))
+    del ws, Q
+    results.sort()
+    t, leaf, smk = results[0]
+    if verbose:
+        print("autotune", key, "best leaf %d split_min_K %d: %.3f ms" % (leaf, smk, t))
+    if cache_path:
+        cache[key] = {"leaf": leaf, "split_min_K": smk, "ms": t, "candidates": len(results)}
         _save(cache_path, cache)
     return tdc.default_opts(leaf=leaf, merge_mode=merge_mode, split_min_K=smk)

@@ -467,7 +467,7 @@ void tdc_default_opts(tdc_opts* o) {
   o->lr_tile = 512;
   o->lr_tol = 1e-15;
   o->split_slices = 7;
-  o->split_min_K = 256;
+  o->split_min_K = 128;
   o->max_iter = 64;
   o->sign_normalise = 1;
   o->collect_stats = 0;

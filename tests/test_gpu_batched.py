@@ -69,6 +69,23 @@ def test_autotuner_picks_and_caches(tdc, tmp_path):
     assert (o2.leaf, o2.split_min_K) == (o.leaf, o.split_min_K)
 
 
+def test_single_problem_autotuner(tdc, orc, tmp_path):
+    """Leaf size and split threshold timed on one matrix; the chosen options solve it
+    to the oracle's accuracy and a second call is served from the cache."""
+    from paper_2008_01990_gb300 import autotune
+    n = 1500
+    d, e = inputs.c4_tridiag(n, 4)
+    dt, et = torch.tensor(d, device=DEV), torch.tensor(e, device=DEV)
+    cache = str(tmp_path / "tune1.json")
+    o = autotune.tune_single(dt, et, cache_path=cache, leaves=(16, 32), split_min_k=(64, 256))
+    assert o.leaf in (16, 32) and o.split_min_K in (64, 256)
+    o2 = autotune.tune_single(dt, et, cache_path=cache, leaves=(16, 32), split_min_k=(64, 256))
+    assert (o2.leaf, o2.split_min_K) == (o.leaf, o.split_min_K)
+    lam, Q = tdc.eig(dt, et, o, check=True)
+    lo, _ = orc.eig(d, e, leaf=o.leaf)
+    assert np.max(np.abs(lam.cpu().numpy() - lo)) <= 1e-12 * max(abs(lo[0]), abs(lo[-1]))
+
+
 def test_c3_full_batch_sampled(tdc, orc):
     """4096 problems, n_b uniform in [64, 2048] (seed 3), d, e uniform(-1,1) (seed 3+b),
     one call; every eigenvalue sorted and finite, sampled problems against the oracle."""
