@@ -5,78 +5,15 @@
 // (M symmetric, so Q M Q^T is symmetric and e_bar doubles its off-diagonal).
 // Only the tridiagonal of Q M Q^T is formed; nothing of the merge tree is needed.
 // Batched over problems of the same order stored back to back.
+//
+// The two n^3 products run on the split-precision tensor-core GEMM of the merge
+// (base-256 BF16 digits, exact FP32 level sums, FP64 result): the left operand
+// is Q^T or Q, whose rows have unit norm; the right operand (Q_bar or M, any
+// magnitude) enters column by column scaled by a power of two that brings its
+// largest entry below 1, and the product's column is scaled back exactly.
 #include "tdc_common.cuh"
 
 namespace tdc {
-
-namespace {
-constexpr int BM = 128, BN = 64, BK = 16, kThreads = 256;
-}
-
-// C[b] = op(A[b]) * B[b] for square n x n FP64 matrices (column-major), op = A^T
-// when TA.  128 x 64 tiles, 256 threads with 8 x 4 outputs each.
-template <bool TA>
-__global__ void __launch_bounds__(kThreads, 2) k_gemm64(int n, const double* A, int64_t lda, int64_t sA,
-                                                        const double* B, int64_t ldb, int64_t sB, double* C,
-                                                        int64_t ldc, int64_t sC) {
-  __shared__ double As[BK][BM];
-  __shared__ double Bs[BK][BN];
-  const int b = blockIdx.z;
-  A += b * sA;
-  B += b * sB;
-  C += b * sC;
-  const int r0 = blockIdx.x * BM, c0 = blockIdx.y * BN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  double acc[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
-  for (int k0 = 0; k0 < n; k0 += BK) {
-    __syncthreads();
-#pragma unroll
-    for (int e = 0; e < (BK * BM) / kThreads; ++e) {
-      const int idx = tid + e * kThreads;
-      int k, r;
-      if (TA) { k = idx % BK; r = idx / BK; }  // A^T(r, k) = A(k, r): k contiguous
-      else { r = idx % BM; k = idx / BM; }
-      const int row = r0 + r, kk = k0 + k;
-      double x = 0.0;
-      if (row < n && kk < n) x = TA ? A[kk + (int64_t)row * lda] : A[row + (int64_t)kk * lda];
-      As[k][r] = x;
-    }
-#pragma unroll
-    for (int e = 0; e < (BK * BN) / kThreads; ++e) {
-      const int idx = tid + e * kThreads;
-      const int k = idx % BK, c = idx / BK;
-      const int kk = k0 + k, col = c0 + c;
-      Bs[k][c] = (kk < n && col < n) ? B[kk + (int64_t)col * ldb] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < BK; ++k) {
-      double av[8], bv[4];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) av[i] = As[k][ty * 8 + i];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) bv[c] = Bs[k][tx * 4 + c];
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[i][c] = fma(av[i], bv[c], acc[i][c]);
-    }
-  }
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const int col = c0 + tx * 4 + c;
-    if (col >= n) continue;
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int row = r0 + ty * 8 + i;
-      if (row < n) C[row + (int64_t)col * ldc] = acc[i][c];
-    }
-  }
-}
 
 // M = diag(lam_bar) + F o skew(W), in place over W (each thread owns a pair (i,j), (j,i)).
 __global__ void k_adj_m(int n, double* W, int64_t sW, const double* lam, int64_t sL, const double* lam_bar,
@@ -126,23 +63,107 @@ __global__ void k_adj_dots(int n, const double* R, int64_t sR, const double* Q, 
   }
 }
 
+// cexp[b n + j]: exponent e of the largest |X_ij| of column j (= m 2^e, m in
+// [0.5, 1)), clamped to [-1022, 1022]; magnitudes compared as integers.
+__global__ void k_col_exp(int n, const double* X, int64_t ld, int64_t sX, int32_t* cexp) {
+  const int b = blockIdx.y;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  if (w >= n) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long* col = reinterpret_cast<const unsigned long long*>(X + b * sX + w * ld);
+  unsigned long long mx = 0ull;
+  for (int i = lane; i < n; i += 32) {
+    const unsigned long long v = col[i] & 0x7fffffffffffffffull;
+    if (v <= 0x7ff0000000000000ull && v > mx) mx = v;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ov = __shfl_xor_sync(0xffffffffu, mx, o);
+    if (ov > mx) mx = ov;
+  }
+  if (lane == 0) {
+    const int f = (int)(mx >> 52);
+    int e = f == 0 ? -1022 : f - 1022;
+    cexp[(int64_t)b * n + w] = e < -1022 ? -1022 : (e > 1022 ? 1022 : e);
+  }
+}
+
+// Segment b of a batched product C_b = op(A_b) B_b (n x n each) for the split GEMM.
+__global__ void k_adj_segs(int batch, int n, int S, const double* A, int64_t ars, int64_t lda, int64_t sA,
+                           const double* B, int64_t ldb, int64_t sB, const int32_t* cexp, double* C, int64_t sC,
+                           GemmSeg* segs) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b > batch) return;
+  const int64_t RT = (n + kSplitBM - 1) / kSplitBM, KB = (n + kSplitBK - 1) / kSplitBK,
+                CT = (n + kSplitBN - 1) / kSplitBN;
+  const int64_t ta = RT * KB, tb = CT * KB, tt = RT * CT;
+  const int64_t ael = ta * S * kSplitBM * kSplitBK, bel = tb * S * kSplitBN * kSplitBK;
+  GemmSeg sg;
+  memset(&sg, 0, sizeof(sg));
+  sg.it_a = b * ta;
+  sg.it_b = b * tb;
+  sg.it_t = b * tt;
+  sg.a_img = b * (ael + bel);
+  sg.b_img = sg.a_img + ael;
+  if (b < batch) {
+    sg.A = A + b * sA;
+    sg.ars = ars;
+    sg.lda = lda;
+    sg.rows = sg.kk = sg.K = n;
+    sg.Bd = B + b * sB;
+    sg.ldb = ldb;
+    sg.cexp = cexp + (int64_t)b * n;
+    sg.C = C + b * sC;
+    sg.ldc = n;
+  }
+  segs[b] = sg;
+}
+
+int64_t adjoint_split_img_elems(int batch, int64_t n) {
+  const int64_t RT = (n + kSplitBM - 1) / kSplitBM, KB = (n + kSplitBK - 1) / kSplitBK,
+                CT = (n + kSplitBN - 1) / kSplitBN;
+  return (int64_t)batch * (RT * KB * kAdjSlices * kSplitBM * kSplitBK + CT * KB * kAdjSlices * kSplitBN * kSplitBK);
+}
+
+// ws: W, R (batch n^2 doubles each), then the column exponents (batch n int32),
+// the segments (batch + 1) and the digit images (adjoint_split_img_elems).
 cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q, int64_t ldq, int64_t sQ,
                            const double* lam_bar, const double* Q_bar, int64_t sQb, double* d_bar,
-                           double* e_bar, double* ws, cudaStream_t s) {
+                           double* e_bar, double* ws, int* status, long long spin_budget, cudaStream_t s) {
   if (batch <= 0 || n <= 0) return cudaSuccess;
   const int64_t nn = (int64_t)n * n;
   double* W = ws;                // batch x n x n
   double* R = ws + batch * nn;   // batch x n x n
-  const dim3 grid((n + BM - 1) / BM, (n + BN - 1) / BN, batch);
+  int32_t* cexp = reinterpret_cast<int32_t*>(R + batch * nn);
+  uintptr_t sp = reinterpret_cast<uintptr_t>(cexp + (int64_t)batch * n);
+  sp = (sp + 255) & ~(uintptr_t)255;
+  GemmSeg* segs = reinterpret_cast<GemmSeg*>(sp);
+  sp = reinterpret_cast<uintptr_t>(segs + batch + 1);
+  sp = (sp + 255) & ~(uintptr_t)255;
+  __nv_bfloat16* img = reinterpret_cast<__nv_bfloat16*>(sp);
+  const dim3 cg((unsigned)((n * 32 + 255) / 256), batch);
+  const unsigned sgrid = (unsigned)((batch + 1 + 127) / 128);
+  cudaError_t e;
   if (Q_bar) {
-    k_gemm64<true><<<grid, kThreads, 0, s>>>(n, Q, ldq, sQ, Q_bar, ldq, sQb, W, n, nn);
+    // W = Q^T Q_bar: A(i, k) = Q(k, i)
+    k_col_exp<<<cg, 256, 0, s>>>(n, Q_bar, ldq, sQb, cexp);
+    k_adj_segs<<<sgrid, 128, 0, s>>>(batch, n, kAdjSlices, Q, ldq, 1, sQ, Q_bar, ldq, sQb, cexp, W, nn, segs);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = launch_seg_split(segs, batch, kAdjSlices, status, spin_budget, img, s);
+    if (e != cudaSuccess) return e;
   } else {
-    cudaError_t e = cudaMemsetAsync(W, 0, sizeof(double) * batch * nn, s);
+    e = cudaMemsetAsync(W, 0, sizeof(double) * batch * nn, s);
     if (e != cudaSuccess) return e;
   }
   const unsigned mb = (unsigned)std::min<int64_t>((nn + 255) / 256, 1024);
   k_adj_m<<<dim3(mb, batch), 256, 0, s>>>(n, W, nn, lam, n, lam_bar, Q_bar != nullptr);
-  k_gemm64<false><<<grid, kThreads, 0, s>>>(n, Q, ldq, sQ, W, n, nn, R, n, nn);
+  // R = Q M: A(i, k) = Q(i, k)
+  k_col_exp<<<cg, 256, 0, s>>>(n, W, n, nn, cexp);
+  k_adj_segs<<<sgrid, 128, 0, s>>>(batch, n, kAdjSlices, Q, 1, ldq, sQ, W, n, nn, cexp, R, nn, segs);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = launch_seg_split(segs, batch, kAdjSlices, status, spin_budget, img, s);
+  if (e != cudaSuccess) return e;
   k_adj_dots<<<dim3((unsigned)((n * 32 + 255) / 256), batch), 256, 0, s>>>(n, R, nn, Q, ldq, sQ, d_bar, n, e_bar,
                                                                           n > 1 ? n - 1 : 1);
   return cudaGetLastError();

@@ -646,6 +646,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   if (!st) return TDC_ECUDA;
   GemmSeg sg;
   memset(&sg, 0, sizeof(sg));
+  sg.ars = 1;
   sg.A = A; sg.lda = lda; sg.rows = (int32_t)m; sg.kk = (int32_t)K; sg.K = (int32_t)K;
   sg.D = D; sg.org = org; sg.tau = tau; sg.zhat = zhat; sg.scol = s;
   sg.C = C; sg.ldc = ldc;
@@ -701,10 +702,18 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
+// W and R (n^2 doubles each per problem), column exponents, segments and the
+// digit images of the split products
+static size_t adjoint_ws_bytes(int32_t batch, int64_t n) {
+  return 256 + align_up(sizeof(double) * 2 * (size_t)batch * (size_t)n * (size_t)n) +
+         align_up(sizeof(int32_t) * (size_t)batch * (size_t)n) + align_up(sizeof(GemmSeg) * ((size_t)batch + 1)) +
+         256 + sizeof(__nv_bfloat16) * (size_t)adjoint_split_img_elems(batch, n);
+}
+
 int tdc_backward_workspace_size(int64_t n, size_t* bytes) {
   if (n < 0) return -1;
   if (!bytes) return -2;
-  *bytes = 256 + sizeof(double) * 2 * (size_t)n * (size_t)n;
+  *bytes = adjoint_ws_bytes(1, n);
   return TDC_OK;
 }
 
@@ -722,8 +731,8 @@ int tdc_eig_backward(int64_t n, const double* lam, const double* Q, int64_t ldq,
   tdc_backward_workspace_size(n, &need);
   if (!ws || ws_bytes < need) return TDC_ENOWS;
   double* w = (double*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  cudaError_t e = launch_adjoint(1, (int)n, lam, Q, ldq, 0, lam_bar, Q_bar, 0, d_bar, e_bar, w,
-                                 (cudaStream_t)stream);
+  cudaError_t e = launch_adjoint(1, (int)n, lam, Q, ldq, 0, lam_bar, Q_bar, 0, d_bar, e_bar, w, status_ptr(),
+                                 1ll << 24, (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
@@ -731,7 +740,7 @@ int tdc_backward_batched_workspace_size(int32_t batch, int64_t n, size_t* bytes)
   if (batch < 0) return -1;
   if (n < 0) return -2;
   if (!bytes) return -3;
-  *bytes = 256 + sizeof(double) * 2 * (size_t)batch * (size_t)n * (size_t)n;
+  *bytes = adjoint_ws_bytes(batch, n);
   return TDC_OK;
 }
 
@@ -750,8 +759,8 @@ int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const 
   if (!ws || ws_bytes < need) return TDC_ENOWS;
   double* w = (double*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   const int64_t nn = n * n;
-  cudaError_t e = launch_adjoint(batch, (int)n, lam, Q, n, nn, lam_bar, Q_bar, nn, d_bar, e_bar, w,
-                                 (cudaStream_t)stream);
+  cudaError_t e = launch_adjoint(batch, (int)n, lam, Q, n, nn, lam_bar, Q_bar, nn, d_bar, e_bar, w, status_ptr(),
+                                 1ll << 24, (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 

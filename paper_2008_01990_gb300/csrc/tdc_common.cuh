@@ -110,6 +110,14 @@ struct GemmSeg {
   const int32_t* cpos;
   int64_t a_img, b_img;    // element offsets (bf16) of the digit images
   int64_t it_a, it_b, it_t;  // first item in the digit-A, digit-B and tile work lists
+  // split path with plain dense operands (the adjoint's products): A(row, col) =
+  // A[row * ars + col * lda] (ars = 1 on the merge path); when Bd is set, B(k, j) =
+  // Bd[k + j * ldb] 2^-cexp[j] replaces the generated Cauchy-like entries, and the
+  // product's column j is scaled back by 2^cexp[j]
+  int64_t ars;
+  const double* Bd;
+  int64_t ldb;
+  const int32_t* cexp;
 };
 
 struct Plan {
@@ -291,9 +299,12 @@ cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 constexpr int kStructRmax = 64;
+// digits of the adjoint's split products and their image size for a batch
+constexpr int kAdjSlices = 7;
+int64_t adjoint_split_img_elems(int batch, int64_t n);
 cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q, int64_t ldq, int64_t sQ,
                            const double* lam_bar, const double* Q_bar, int64_t sQb, double* d_bar,
-                           double* e_bar, double* ws, cudaStream_t s);
+                           double* e_bar, double* ws, int* status, long long spin_budget, cudaStream_t s);
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;

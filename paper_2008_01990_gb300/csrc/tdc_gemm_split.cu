@@ -49,6 +49,9 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 // matrix, core matrices along K 64 elements apart, 8-row groups BK*8 elements apart)
 __device__ __forceinline__ int core_off(int r, int k) { return (r >> 3) * (BK * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
 
+// 2^e for e in [-1022, 1023], built from its bits
+__device__ __forceinline__ double pow2(int e) { return __hiloint2double((1023 + e) << 20, 0); }
+
 // The S leading balanced base-256 digits of x (|x| <= 1 + O(eps)), as floats:
 // F = round(x 2^56) as a two's-complement integer, then digits taken from the
 // least significant end in [-128, 127] (the top digit carries the rest, |d_0| <=
@@ -123,6 +126,8 @@ __global__ void k_split_segs(Plan P, int level, int64_t g0, int64_t g1) {
     const bool use = P.split_min_K > 0 && K >= P.split_min_K;
     for (int p = 0; p < 2; ++p) {
       GemmSeg sg;
+      memset(&sg, 0, sizeof(sg));
+      sg.ars = 1;
       sg.rows = p ? n - n1 : n1;
       sg.kk = p ? P.m.nbot[g] : P.m.ntop[g];
       sg.K = K;
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
         if (q < sg.kk && row < sg.rows) {
           const int p = sg.plist ? sg.plist[q] : q;
           const int col = sg.acol ? sg.acol[p] : p;
-          x = sg.A[row + (int64_t)col * sg.lda];
+          x = sg.A[(int64_t)row * sg.ars + (int64_t)col * sg.lda];
         }
         digits_of(x, S, dig[i]);
       }
@@ -227,9 +232,13 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
     const int jj = ct * BN + j;
     double dorg = 0.0, tj = 1.0, sj = 0.0;
     if (jj < sg.K) {
-      dorg = sg.D[sg.org[jj]];
-      tj = sg.tau[jj];
-      sj = sg.scol[jj];
+      if (sg.Bd) {
+        sj = sg.cexp ? pow2(-sg.cexp[jj]) : 1.0;
+      } else {
+        dorg = sg.D[sg.org[jj]];
+        tj = sg.tau[jj];
+        sj = sg.scol[jj];
+      }
     }
     float dig[8][kMaxS];
 #pragma unroll
@@ -238,7 +247,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
       double u = 0.0;
       if (q < sg.kk && jj < sg.K) {
         const int p = sg.plist ? sg.plist[q] : q;
-        u = (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
+        u = sg.Bd ? sg.Bd[p + (int64_t)jj * sg.ldb] * sj : (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
       }
       digits_of(u, S, dig[i]);
     }
@@ -495,7 +504,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           const int j = t.ct * BN + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            sg.C[row + (int64_t)pos * sg.ldc] = val[i];
+            sg.C[row + (int64_t)pos * sg.ldc] = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
           }
         }
       }

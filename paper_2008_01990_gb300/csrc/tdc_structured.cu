@@ -434,6 +434,7 @@ __global__ void k_struct_segs(Plan P, int level, int64_t M) {
   for (int p = 0; p < 2; ++p) {
     GemmSeg sg;
     memset(&sg, 0, sizeof(sg));
+    sg.ars = 1;
     sg.rows = p ? n - n1 : n1;
     sg.kk = p ? P.m.nbot[g] : P.m.ntop[g];
     sg.K = use ? K : 0;
