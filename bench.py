@@ -141,7 +141,9 @@ def cpu_baseline(wl: str, budget_s: float = 20.0):
     while True:
         d, e = inputs.family(fam, n, 4 if fam == "c4" else 1)
         t0 = time.perf_counter()
-        oracle.eig(d, e, leaf=leaf)
+        # the iteration cap only guards against a runaway root: bisection alone may need
+        # a few hundred halvings on these spectra before the bracket reaches rounding level
+        oracle.eig(d, e, leaf=leaf, max_iter=2000)
         dt = time.perf_counter() - t0
         if n >= n_full or dt * 8 > budget_s:
             break
