@@ -405,7 +405,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
         span(6, b5, a6);
       }
     }
-    if (err == cudaSuccess) err = launch_copy_deflated(P, LL, s);
+    if (err == cudaSuccess) err = launch_copy_deflated(P, LL, o.sign_normalise, s);
     span(7, a6, mark());
   }
   const size_t t8 = mark();

@@ -286,7 +286,7 @@ cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, int bm, int bn, cudaStream_t s);
-cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, int sign_normalise, cudaStream_t s);
 cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream_t s);
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
                             double* tau, double* zhat, double* s, int* status, cudaStream_t st);

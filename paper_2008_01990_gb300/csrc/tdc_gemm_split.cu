@@ -114,64 +114,122 @@ int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, in
 // ---------------------------------------------------------------------------
 // Segments of a tree level: one per (merge, top/bottom part).
 // ---------------------------------------------------------------------------
-__global__ void k_split_segs(Plan P, int level, int64_t g0, int64_t g1) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// One block: each thread counts the digit tiles, output tiles and image elements
+// of a contiguous range of merges, a block scan gives every range its offsets,
+// then the threads write their segments.
+__device__ __forceinline__ void split_seg_counts(const Plan& P, int level, int64_t g, int S, int p, int64_t& ta,
+                                                 int64_t& tb, int64_t& tt, int64_t& el) {
+  ta = tb = tt = el = 0;
+  const int K = P.m.K[g];
+  if (!(P.split_min_K > 0 && K >= P.split_min_K)) return;
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int64_t rows = p ? n - n1 : n1, kk = p ? P.m.nbot[g] : P.m.ntop[g];
+  const int64_t RT = cdiv(rows, BM), KB = cdiv(kk, BK), CT = cdiv(K, BN);
+  ta = RT * KB;
+  tb = CT * KB;
+  tt = RT * CT;
+  el = ta * S * kATileElems + tb * S * kBTileElems;
+}
+
+// Exclusive scan of four int64 values over the block (warp shuffles, then the
+// warp totals scanned by warp 0); blockDim.x a multiple of 32, at most 1024.
+__device__ __forceinline__ void block_excl_scan4(int64_t (&v)[4], int64_t (&sc)[4][32]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t inc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    inc[q] = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, inc[q], o);
+      if (lane >= o) inc[q] += t;
+    }
+    if (lane == 31) sc[q][w] = inc[q];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int64_t x = lane < nw ? sc[q][lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      if (lane < nw) sc[q][lane] = x;  // inclusive over warps
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = inc[q] - v[q] + (w > 0 ? sc[q][w - 1] : 0);
+}
+
+__global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t g0, int64_t g1) {
+  __shared__ int64_t sc[4][32];
   const int S = P.split_slices;
-  const int64_t M = g1 - g0;
-  int64_t ia = 0, ib = 0, it = 0, e = 0;
-  for (int64_t g = g0; g < g1; ++g) {
+  const int64_t M = g1 - g0, items = 2 * M;
+  const int64_t per = (items + blockDim.x - 1) / blockDim.x;
+  const int64_t w0 = min(items, (int64_t)threadIdx.x * per), w1 = min(items, w0 + per);
+  int64_t cta = 0, ctb = 0, ctt = 0, cel = 0;
+  for (int64_t w = w0; w < w1; ++w) {
+    int64_t ta, tb, tt, el;
+    split_seg_counts(P, level, g0 + w / 2, S, (int)(w & 1), ta, tb, tt, el);
+    cta += ta; ctb += tb; ctt += tt; cel += el;
+  }
+  int64_t v[4] = {cta, ctb, ctt, cel};
+  block_excl_scan4(v, sc);
+  int64_t ia = v[0], ib = v[1], it = v[2], e = v[3];
+  for (int64_t w = w0; w < w1; ++w) {
+    const int64_t g = g0 + w / 2;
+    const int p = (int)(w & 1);
     const Node nd = make_node(P, level, g);
     const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
     const int K = P.m.K[g];
-    const bool use = P.split_min_K > 0 && K >= P.split_min_K;
-    for (int p = 0; p < 2; ++p) {
-      GemmSeg sg;
-      memset(&sg, 0, sizeof(sg));
-      sg.ars = 1;
-      sg.rows = p ? n - n1 : n1;
-      sg.kk = p ? P.m.nbot[g] : P.m.ntop[g];
-      sg.K = K;
-      sg.near_m = 0;
-      sg.A = nd.src + (p ? n1 : 0);
-      sg.lda = nd.lds;
-      sg.acol = P.v.kept + nd.v0;
-      sg.plist = (p ? P.v.blist : P.v.tlist) + nd.v0;
-      sg.D = P.v.Dk + nd.v0;
-      sg.org = P.v.org + nd.v0;
-      sg.tau = P.v.tau + nd.v0;
-      sg.zhat = P.v.zhat + nd.v0;
-      sg.scol = P.v.scol + nd.v0;
-      sg.C = nd.dst + (p ? n1 : 0);
-      sg.ldc = nd.ldd;
-      sg.cpos = P.v.posr + nd.v0;
-      sg.it_a = ia;
-      sg.it_b = ib;
-      sg.it_t = it;
-      sg.a_img = e;
-      sg.b_img = e;
-      if (use) {
-        const int64_t RT = cdiv(sg.rows, BM), KB = cdiv(sg.kk, BK), CT = cdiv(K, BN);
-        sg.b_img = e + RT * KB * S * kATileElems;
-        e = sg.b_img + CT * KB * S * kBTileElems;
-        ia += RT * KB;
-        ib += CT * KB;
-        it += RT * CT;
-        if (P.stats) atomicAdd(&P.stats->split_flops, 2ull * (unsigned long long)sg.rows * sg.kk * (unsigned long long)K);
-      }
-      P.segs[2 * (g - g0) + p] = sg;
+    GemmSeg sg;
+    memset(&sg, 0, sizeof(sg));
+    sg.ars = 1;
+    sg.rows = p ? n - n1 : n1;
+    sg.kk = p ? P.m.nbot[g] : P.m.ntop[g];
+    sg.K = K;
+    sg.near_m = 0;
+    sg.A = nd.src + (p ? n1 : 0);
+    sg.lda = nd.lds;
+    sg.acol = P.v.kept + nd.v0;
+    sg.plist = (p ? P.v.blist : P.v.tlist) + nd.v0;
+    sg.D = P.v.Dk + nd.v0;
+    sg.org = P.v.org + nd.v0;
+    sg.tau = P.v.tau + nd.v0;
+    sg.zhat = P.v.zhat + nd.v0;
+    sg.scol = P.v.scol + nd.v0;
+    sg.C = nd.dst + (p ? n1 : 0);
+    sg.ldc = nd.ldd;
+    sg.cpos = P.v.posr + nd.v0;
+    sg.it_a = ia;
+    sg.it_b = ib;
+    sg.it_t = it;
+    int64_t ta, tb, tt, el;
+    split_seg_counts(P, level, g, S, p, ta, tb, tt, el);
+    sg.a_img = e;
+    sg.b_img = e + ta * S * kATileElems;
+    if (el > 0 && P.stats)
+      atomicAdd(&P.stats->split_flops, 2ull * (unsigned long long)sg.rows * sg.kk * (unsigned long long)K);
+    ia += ta; ib += tb; it += tt; e += el;
+    P.segs[w] = sg;
+  }
+  if (threadIdx.x == blockDim.x - 1) {
+    GemmSeg last;
+    memset(&last, 0, sizeof(last));
+    last.it_a = ia;
+    last.it_b = ib;
+    last.it_t = it;
+    last.a_img = e;
+    if (e > P.img_cap) {  // cannot happen with the host's bound; never write past the images
+      last.it_a = last.it_b = last.it_t = 0;
+      set_status(P.status, TDC_EUNSUPPORTED);
     }
+    P.segs[items] = last;
   }
-  GemmSeg last;
-  memset(&last, 0, sizeof(last));
-  last.it_a = ia;
-  last.it_b = ib;
-  last.it_t = it;
-  last.a_img = e;
-  if (e > P.img_cap) {  // cannot happen with the host's bound; never write past the images
-    last.it_a = last.it_b = last.it_t = 0;
-    set_status(P.status, TDC_EUNSUPPORTED);
-  }
-  P.segs[2 * M] = last;
 }
 
 // ---------------------------------------------------------------------------
@@ -552,7 +610,7 @@ static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, int S, int* s
 cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, cudaStream_t s,
                               cudaEvent_t mid) {
   if (P.split_min_K <= 0 || P.segs == nullptr || g1 <= g0) return cudaSuccess;
-  k_split_segs<<<1, 32, 0, s>>>(P, L.level, g0, g1);
+  k_split_segs<<<1, 1024, 0, s>>>(P, L.level, g0, g1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nseg = (int)(2 * (g1 - g0));

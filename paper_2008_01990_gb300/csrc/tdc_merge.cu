@@ -619,7 +619,7 @@ cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s) 
 // chains touch disjoint columns.  An entry outside a column's row support
 // (top or bottom child) is a structural zero and is never read.
 // ---------------------------------------------------------------------------
-static constexpr int kRotChainsPerGrid = 64;
+static constexpr int kRotChainsPerGrid = 512;
 
 __global__ void __launch_bounds__(256) k_rotate(Plan P, int level) {
   const int64_t g = blockIdx.x;
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(256) k_rotate(Plan P, int level) {
 
 cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   // chains are spread over grid.z; small merges (many per level) need few
-  const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRotChainsPerGrid, L.max_n / 256));
+  const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(kRotChainsPerGrid, L.max_n / 32));
   dim3 grid((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256), gz);
   k_rotate<<<grid, 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
@@ -1385,7 +1385,72 @@ __global__ void __launch_bounds__(256) k_copy_defl(Plan P, int level) {
   }
 }
 
-cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+// The top merge of each problem (level 0) writes the caller's Q: there a warp owns
+// a whole deflated column, finds its entry of largest magnitude within the
+// column's row support (lowest row on ties, as the output pass does) and writes
+// the column with the sign convention already applied, so that the output pass
+// can skip it.  Magnitudes compare as integers of their bits.
+__global__ void __launch_bounds__(256) k_copy_defl_sign(Plan P) {
+  const int64_t g = blockIdx.x;
+  const int ndf = P.m.nd[g];
+  if (ndf == 0) return;
+  const Node nd = make_node(P, 0, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int64_t v0 = nd.v0;
+  for (int q = blockIdx.y * nw + (threadIdx.x >> 5); q < ndf; q += gridDim.y * nw) {
+    const int c = P.v.dcol[v0 + q];
+    const int sp = P.v.dseg[v0 + q];
+    const int o = P.v.posd[v0 + q];
+    if (o < 0 || o >= n) continue;
+    const int ra = (sp & 1) ? 0 : n1, rb = (sp & 2) ? n : n1;  // row support [ra, rb)
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(nd.src + (int64_t)c * nd.lds);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(nd.dst + (int64_t)o * nd.ldd);
+    unsigned long long best = 0ull;
+    int bi = ra;
+    bool any = false;
+    for (int r0 = ra; r0 < rb; r0 += 256) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = r0 + k * 32 + lane;
+        v[k] = r < rb ? (src[r] & 0x7fffffffffffffffull) : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = r0 + k * 32 + lane;
+        if (r < rb && v[k] <= 0x7ff0000000000000ull && (!any || v[k] > best)) { best = v[k]; bi = r; any = true; }
+      }
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, off);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+      const bool oa = __shfl_xor_sync(0xffffffffu, any, off);
+      if (oa && (!any || ob > best || (ob == best && oi < bi))) { best = ob; bi = oi; any = true; }
+    }
+    const unsigned long long flip = (rb > ra && (long long)src[bi] < 0) ? 0x8000000000000000ull : 0ull;
+    for (int r0 = 0; r0 < n; r0 += 256) {
+      unsigned long long v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = r0 + k * 32 + lane;
+        v[k] = (r >= ra && r < rb) ? src[r] ^ flip : 0ull;
+      }
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int r = r0 + k * 32 + lane;
+        if (r < n) dst[r] = v[k];
+      }
+    }
+  }
+}
+
+cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, int sign_normalise, cudaStream_t s) {
+  if (L.level == 0 && sign_normalise) {
+    const unsigned gy = (unsigned)std::max<int64_t>(1, std::min<int64_t>(1024, L.max_n / 64));
+    k_copy_defl_sign<<<dim3((unsigned)L.merges, gy), 256, 0, s>>>(P);
+    return cudaGetLastError();
+  }
   const unsigned gy = (unsigned)((L.max_n + kCopyRows - 1) / kCopyRows);
   const unsigned gz = (unsigned)std::max<int64_t>(1, std::min<int64_t>(256, L.max_n / 64));
   dim3 grid((unsigned)L.merges, gy, gz);
@@ -1405,7 +1470,9 @@ __global__ void __launch_bounds__(256) k_sign_out(Plan P, int sign_normalise) {
   const Problem& p = P.prob[pi];
   const int64_t c = s - p.voff;
   double* col = P.Q0 + p.off_q + c * p.ld0;
-  if (sign_normalise) {
+  // columns of the top merge that came from deflation were normalised by the copy
+  const bool done = p.depth > 0 && P.v.stag[2 * p.voff + c] >= P.m.K[pi];
+  if (sign_normalise && !done) {
     // |x| compared as the integer of its bits (same order for finite values, on the
     // integer pipes); eight independent loads per lane in flight
     const unsigned long long* cb = reinterpret_cast<const unsigned long long*>(col);
