@@ -412,11 +412,18 @@ def run_ours(args):
     split_flops = float(stats["split_flops"])
     dense_flops = float(sum(stats["gemm_flops"])) - split_flops
     pk, pk_kind = peaks()
+    # DRAM bytes of k_gemm_split over one eigensolve, summed over its launches, from
+    # single-pass ncu captures of this kernel; keyed by the exact configuration,
+    # absent (null) for any other
+    traffic_table = {("toeplitz16384", 64, 128): 52.25e9, ("c4_32768", 16, 64): 15.83e9}
+    traffic = traffic_table.get((args.workload, opts.leaf, opts.split_min_K))
     if split_flops > 0 and split_ms > 0:
         achieved = split_flops * products / (split_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": "k_gemm_split (BF16 digit products, tcgen05, TMEM FP32 levels)",
                 "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_tflops"], "traffic": None,
+                "frac": achieved / pk["bf16_tflops"], "traffic": traffic,
+                "traffic_scope": "DRAM bytes of all k_gemm_split launches of one eigensolve (ncu)",
+                "algorithmic_bytes": stats.get("split_bytes"),
                 "peak_kind": "bf16_tflops (burst) of %s: the kernel runs in bursts of tens of ms and the SM "
                              "clock stays at its maximum (see clocks)" % pk_kind,
                 "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],

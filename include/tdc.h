@@ -88,6 +88,9 @@ typedef struct {
   float phase_ms[12];
   double gemm_flops[TDC_MAX_LEVELS];     /* algorithmic flops of the Q*U products (2 per multiply-add) */
   double split_flops;                    /* part of gemm_flops computed on the split path */
+  double split_bytes;                    /* algorithmic HBM bytes of the split products: digit images
+                                            read once (2 B per slice per entry of each operand) and
+                                            the FP64 result written once */
   double struct_flops;                   /* flops executed by the structured path (dense near-diagonal
                                             tiles + the two thin products of the low-rank tiles) */
   int64_t launches;                      /* kernel launches of the call */

@@ -442,6 +442,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       g_last_stats.gemm_flops[l] = (double)hs.gemm_flops[l];
     }
     g_last_stats.split_flops = (double)hs.split_flops;
+    g_last_stats.split_bytes = (double)hs.split_bytes;
     g_last_stats.struct_flops = (double)hs.struct_flops;
     g_last_stats.launches = launches;
     g_last_stats.secular_iter_max = hs.iter_max;

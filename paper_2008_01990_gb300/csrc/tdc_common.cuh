@@ -80,6 +80,7 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   int max_K[TDC_MAX_LEVELS];
   unsigned long long gemm_flops[TDC_MAX_LEVELS];
   unsigned long long split_flops;
+  unsigned long long split_bytes;
   unsigned long long struct_flops;
   unsigned long long iter_sum;
   unsigned long long iter_roots;

@@ -212,8 +212,12 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
     split_seg_counts(P, level, g, S, p, ta, tb, tt, el);
     sg.a_img = e;
     sg.b_img = e + ta * S * kATileElems;
-    if (el > 0 && P.stats)
-      atomicAdd(&P.stats->split_flops, 2ull * (unsigned long long)sg.rows * sg.kk * (unsigned long long)K);
+    if (el > 0 && P.stats) {
+      const unsigned long long r = (unsigned long long)sg.rows, kq = (unsigned long long)sg.kk,
+                               kc = (unsigned long long)K;
+      atomicAdd(&P.stats->split_flops, 2ull * r * kq * kc);
+      atomicAdd(&P.stats->split_bytes, 2ull * S * (r * kq + kq * kc) + 8ull * r * kc);
+    }
     ia += ta; ib += tb; it += tt; e += el;
     P.segs[w] = sg;
   }

@@ -62,6 +62,7 @@ class Stats(ctypes.Structure):
         ("phase_ms", ctypes.c_float * 12),
         ("gemm_flops", ctypes.c_double * MAX_LEVELS),
         ("split_flops", ctypes.c_double),
+        ("split_bytes", ctypes.c_double),
         ("struct_flops", ctypes.c_double),
         ("launches", ctypes.c_int64),
     ]
@@ -83,6 +84,7 @@ class Stats(ctypes.Structure):
             "phase_ms": dict(zip(names, list(self.phase_ms))),
             "gemm_flops": list(self.gemm_flops[:L]),
             "split_flops": self.split_flops,
+            "split_bytes": self.split_bytes,
             "struct_flops": self.struct_flops,
             "launches": self.launches,
         }
