@@ -257,7 +257,10 @@ def run_batched(args):
     d, e, offs = inputs.batched_uniform(sizes, 3)
     qoffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
     dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
-    opts = autotune.tune_batched(sizes, dt, et, offs[:-1], cache_path=None)
+    if args.leaf or args.split_min_k:
+        opts = tdc.default_opts(leaf=args.leaf or 32, split_min_K=args.split_min_k or 128)
+    else:
+        opts = autotune.tune_batched(sizes, dt, et, offs[:-1], cache_path=None)
     lam = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
     Q = torch.empty(int(qoffs[-1]), dtype=torch.float64, device=dev)
     ws = tdc.workspace(tdc.batched_workspace_size(sizes, opts), dev)
@@ -280,9 +283,14 @@ def run_batched(args):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
     st = tdc.sync_status()
+    # one more solve with statistics (outside the timed region): launches and phases
+    ost = tdc.default_opts(leaf=opts.leaf, split_min_K=opts.split_min_K, collect_stats=1)
+    tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, ost, ws=ws)
+    stats = tdc.get_stats()
     print(json.dumps({"workload": "batched4096", "ms_per_batch": ms, "problems_per_s": 4096 / (ms * 1e-3),
                       "leaf": opts.leaf, "split_min_K": opts.split_min_K, "status": st,
-                      "sum_n": int(sizes.sum()), "q_bytes": int(qoffs[-1]) * 8}), flush=True)
+                      "sum_n": int(sizes.sum()), "q_bytes": int(qoffs[-1]) * 8,
+                      "launches_per_solve": int(stats["launches"]), "phase_ms": stats["phase_ms"]}), flush=True)
     return 0
 
 
