@@ -241,9 +241,204 @@ __global__ void __launch_bounds__(64) k_leaf(Plan P, int64_t nleaves) {
   for (int k = tid; k < L; k += blockDim.x) P.v.lam[p.voff + lo + k] = dd[perm[k]];
 }
 
+// Many small leaves per block.  The sequential bulge chase costs one warp
+// instruction per FP64 operation whether one lane or 32 are active, so here lane l
+// of warp 0 runs the whole QR iteration of leaf l (its own deflation scan, shift
+// and chase) and the G leaves of the block advance together; warps 1.. apply each
+// round's rotations to the leaves' eigenvector blocks (one row per lane, the
+// rotations of consecutive rounds double-buffered).  Used when leaves have at
+// most 32 rows; every leaf gets the same arithmetic as in k_leaf.
+__global__ void __launch_bounds__(1024) k_leaf_multi(Plan P, int64_t nleaves, int Lm, int G) {
+  extern __shared__ double sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int slot = Lm * Lm + 6 * Lm;  // doubles per leaf: Q block, d, e, 2 x (c, s) buffers
+  int* ib = reinterpret_cast<int*>(sm + (size_t)G * slot);
+  int* ctrl = ib;                  // [G][4]: pp, q of buffers 0 and 1
+  int* perm = ctrl + 4 * G;        // [G][Lm]
+  int* sL = perm + G * Lm;         // [G] leaf order (0: no leaf)
+  int* sprob = sL + G;             // [G] problem index
+  long long* slo = reinterpret_cast<long long*>(sprob + G + ((6 * G + G * Lm) & 1));  // [G] first row
+  const int64_t g0 = (int64_t)blockIdx.x * G;
+  if (tid < G) {
+    const int64_t g = g0 + tid;
+    int L = 0, pi = 0;
+    long long lo = 0;
+    if (g < nleaves) {
+      int a = 0, b = P.nprob - 1;
+      while (a < b) {
+        const int m = (a + b + 1) >> 1;
+        if (P.prob[m].leaf0 <= g) a = m; else b = m - 1;
+      }
+      const Problem& pr = P.prob[a];
+      const int64_t li = g - pr.leaf0;
+      lo = node_bound(li, pr.n, pr.depth);
+      L = (int)(node_bound(li + 1, pr.n, pr.depth) - lo);
+      pi = a;
+    }
+    sL[tid] = L;
+    sprob[tid] = pi;
+    slo[tid] = lo;
+  }
+  __syncthreads();
+  for (int x = tid; x < G * Lm * Lm; x += blockDim.x) {
+    const int l = x / (Lm * Lm), k = x % (Lm * Lm);
+    sm[(size_t)l * slot + k] = ((k % Lm) == (k / Lm)) ? 1.0 : 0.0;
+  }
+  for (int x = tid; x < G * Lm; x += blockDim.x) {
+    const int l = x / Lm, k = x % Lm, L = sL[l];
+    double* dd = sm + (size_t)l * slot + Lm * Lm;
+    double* ee = dd + Lm;
+    if (k < L) {
+      const Problem& pr = P.prob[sprob[l]];
+      dd[k] = P.v.dmod[pr.voff + slo[l] + k];
+      ee[k] = (k < L - 1) ? P.e[pr.off_de + slo[l] + k] : 0.0;
+    }
+  }
+  __syncthreads();
+  const int lpw = 32 / Lm;                 // leaves per apply warp
+  const int max_sweeps = 40 * (Lm > 0 ? Lm : 1);
+  int sweeps = 0;
+  bool done = !(warp == 0 && lane < G && sL[lane] > 1);
+  for (int round = 0;; ++round) {
+    const int b = round & 1;
+    bool nonempty = false;
+    if (warp == 0) {
+      if (lane < G) {
+        const int L = sL[lane];
+        double* dd = sm + (size_t)lane * slot + Lm * Lm;
+        double* ee = dd + Lm;
+        double* cb = ee + Lm + 2 * Lm * b;
+        int pp = 0, q = 0;
+        if (!done) {
+          q = L - 1;
+          for (int k = 0; k < q; ++k)
+            if (fabs(ee[k]) <= kEps * (fabs(dd[k]) + fabs(dd[k + 1]))) ee[k] = 0.0;
+          while (q > 0 && ee[q - 1] == 0.0) --q;
+          if (q == 0) {
+            done = true;
+          } else if (sweeps >= max_sweeps) {
+            done = true;
+            q = 0;
+            set_status(P.status, TDC_ENOCONV);
+          } else {
+            ++sweeps;
+            pp = q - 1;
+            while (pp > 0 && ee[pp - 1] != 0.0) --pp;
+            const double hd = 0.5 * (dd[q - 1] - dd[q]);
+            const double bq = ee[q - 1];
+            const double hh = hypot(hd, bq);
+            const double mu = dd[q] - bq * bq / (hd + copysign(hh, hd));
+            double a0 = dd[pp], bk = ee[pp];
+            double x = a0 - mu, y = bk;
+            for (int k = pp; k < q; ++k) {
+              const double a1 = dd[k + 1];
+              const double en = (k < q - 1) ? ee[k + 1] : 0.0;
+              const double t2 = fma(x, x, y * y);
+              double r, c = 1.0, sn = 0.0;
+              if (t2 > 1e-290 && t2 < 1e290) {
+                const double ri = rsqrt_nr(t2);
+                c = x * ri; sn = y * ri; r = t2 * ri;
+              } else {
+                r = hypot(x, y);
+                if (r != 0.0) { c = x / r; sn = y / r; }
+              }
+              if (k > pp) ee[k - 1] = r;
+              const double cc = c * c, ss = sn * sn, c2s = 2.0 * c * sn * bk;
+              dd[k] = cc * a0 + c2s + ss * a1;
+              const double a0n = ss * a0 - c2s + cc * a1;
+              const double ek = c * sn * (a1 - a0) + (cc - ss) * bk;
+              if (k < q - 1) {
+                y = sn * en;
+                bk = c * en;
+                x = ek;
+              } else {
+                ee[k] = ek;
+              }
+              a0 = a0n;
+              cb[2 * k] = c;
+              cb[2 * k + 1] = sn;
+            }
+            dd[q] = a0;
+            nonempty = true;
+          }
+        }
+        ctrl[4 * lane + 2 * b] = nonempty ? pp : 0;
+        ctrl[4 * lane + 2 * b + 1] = nonempty ? q : 0;
+      }
+    } else if (round > 0) {
+      // rotations of the previous round: apply warp w takes leaves (w-1)*lpw .. + lpw - 1
+      const int l = (warp - 1) * lpw + lane / Lm, r = lane % Lm;
+      if (lane < lpw * Lm && l < G && r < sL[l]) {
+        const int pb = b ^ 1;
+        const int pp = ctrl[4 * l + 2 * pb], q = ctrl[4 * l + 2 * pb + 1];
+        if (q > pp) {
+          double* Qs = sm + (size_t)l * slot;
+          const double* cb = Qs + Lm * Lm + 2 * Lm + 2 * Lm * pb;
+          double v = Qs[r + pp * Lm];
+          for (int k = pp; k < q; ++k) {
+            const double c = cb[2 * k], sn = cb[2 * k + 1];
+            const double w = Qs[r + (k + 1) * Lm];
+            Qs[r + k * Lm] = c * v + sn * w;
+            v = c * w - sn * v;
+          }
+          Qs[r + q * Lm] = v;
+        }
+      }
+    }
+    if (!__syncthreads_or(nonempty ? 1 : 0)) break;
+  }
+  // ascending order (stable) per leaf, then the blocks and eigenvalues out
+  for (int x = tid; x < G * Lm; x += blockDim.x) {
+    const int l = x / Lm, k = x % Lm, L = sL[l];
+    if (k >= L) continue;
+    const double* dd = sm + (size_t)l * slot + Lm * Lm;
+    const double v = dd[k];
+    int rk = 0;
+    for (int m = 0; m < L; ++m) {
+      const double w = dd[m];
+      rk += (w < v || (w == v && m < k)) ? 1 : 0;
+    }
+    perm[l * Lm + rk] = k;
+  }
+  __syncthreads();
+  for (int x = tid; x < G * Lm * Lm; x += blockDim.x) {
+    const int l = x / (Lm * Lm), rem = x % (Lm * Lm), k = rem / Lm, r = rem % Lm, L = sL[l];
+    if (k >= L || r >= L) continue;
+    const Problem& pr = P.prob[sprob[l]];
+    double* dst;
+    int64_t ld;
+    if (pr.depth & 1) { dst = P.Q1 + pr.qoff1; ld = pr.n; }
+    else { dst = P.Q0 + pr.off_q; ld = pr.ld0; }
+    const int64_t lo = slo[l];
+    dst[(lo + r) + (lo + k) * ld] = sm[(size_t)l * slot + r + perm[l * Lm + k] * Lm];
+  }
+  for (int x = tid; x < G * Lm; x += blockDim.x) {
+    const int l = x / Lm, k = x % Lm, L = sL[l];
+    if (k >= L) continue;
+    const Problem& pr = P.prob[sprob[l]];
+    P.v.lam[pr.voff + slo[l] + k] = sm[(size_t)l * slot + Lm * Lm + perm[l * Lm + k]];
+  }
+}
+
 cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStream_t s) {
   if (nleaves == 0) return cudaSuccess;
   if (max_leaf > kMaxLeaf) return cudaErrorInvalidValue;
+  if (max_leaf <= 32 && nleaves >= 64) {
+    // G leaves per block within a shared-memory budget, one apply warp per 32 rows
+    const int Lm = max_leaf;
+    // per leaf: Q block, d, e and two rotation buffers; pp/q of both buffers, the
+    // permutation, order, problem and first row
+    const size_t per = sizeof(double) * (size_t)(Lm * Lm + 6 * Lm) + sizeof(int) * (size_t)(6 + Lm) + 8;
+    const int lpw = 32 / Lm;
+    int G = (int)std::min<size_t>(32, (size_t)(96 * 1024) / per);
+    G = std::max(1, std::min(G, 31 * lpw));
+    const int warps = 1 + (G + lpw - 1) / lpw;
+    const size_t smem = per * G + 64;
+    cudaError_t e = cudaFuncSetAttribute(k_leaf_multi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_leaf_multi<<<(unsigned)((nleaves + G - 1) / G), 32 * warps, smem, s>>>(P, nleaves, Lm, G);
+    return cudaGetLastError();
+  }
   size_t smem = sizeof(double) * (max_leaf * max_leaf + 6 * max_leaf) + sizeof(int) * (6 + max_leaf);
   k_leaf<<<(unsigned)nleaves, 64, smem, s>>>(P, nleaves);
   return cudaGetLastError();

@@ -68,6 +68,14 @@ def test_ragged_sizes(tdc, orc, n, leaf):
     check_vs_oracle(orc, d, e, lam, Q, leaf)
 
 
+@pytest.mark.parametrize("n,leaf,fam", [(3000, 16, "uniform"), (2500, 31, "c4"), (4100, 8, "sht"), (2049, 32, "clement")])
+def test_many_small_leaves(tdc, orc, n, leaf, fam):
+    """Problems with many leaves of at most 32 rows take the many-leaves-per-block QR."""
+    d, e = inputs.family(fam, n, 7)
+    lam, Q = run_gpu(tdc, d, e, leaf=leaf)
+    check_vs_oracle(orc, d, e, lam, Q, leaf, vec_tol=1e-7)
+
+
 def test_toeplitz_2048_closed_form_and_deflation(tdc, orc):
     n = 2048
     d, e = inputs.toeplitz_tridiag(n)
