@@ -351,9 +351,11 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   auto span = [&](int phase, size_t a0, size_t a1) {
     if (timing) spans.push_back({phase, {a0, a1}});
   };
-  // kernel launches: problem upload, corner modification, leaves, 9 per level, output
+  // kernel launches: problem upload, corner modification, leaves, 9 per level (12
+  // on levels that also run the thread-per-root variants), output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
+    if (H.levels[l].nslots >= kSmallMinSlots) launches += 3;
     if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4 * (int64_t)H.split_chunks[l].size();
     if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
       launches += 2 + 2 * ((H.levels[l].max_n + H.struct_m - 1) / H.struct_m);

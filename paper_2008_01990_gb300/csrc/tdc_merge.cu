@@ -895,32 +895,41 @@ __device__ __forceinline__ Slot slot_of(const Plan& P, int level, int nprob_act,
 // at tau (the nearest poles d_j, d_{j+1}); the model's root is the next iterate
 // (a quadratic), safeguarded by bisection on the bracket.
 // ---------------------------------------------------------------------------
+// W = 32: the warp's lanes share the poles and the sums are reduced over the
+// warp; W = 1: one thread takes every pole (small merges, a root per thread).
+template <int W = 32>
 __device__ __forceinline__ void secular_sums(const double* D, const double* z, int K, int j, double dorg,
                                              double tau, double& psi, double& dpsi, double& phi,
                                              double& dphi, double& sabs) {
-  const int lane = threadIdx.x & 31;
+  const int lane = W == 32 ? (threadIdx.x & 31) : 0;
   double a = 0.0, da = 0.0, b = 0.0, db = 0.0;
   // poles left of the root (i <= j) give negative terms, poles right of it positive
   // ones, so sum |t| = phi - psi needs no separate accumulation
   const int split = min(K, j + 1);
-  for (int i = lane; i < split; i += 32) {
+  for (int i = lane; i < split; i += W) {
     const double r = rcp_nr((D[i] - dorg) - tau);
     const double zi = z[i];
     const double t = zi * zi * r;
     a += t;
     da = fma(t, r, da);
   }
-  for (int i = split + lane; i < K; i += 32) {
+  for (int i = split + lane; i < K; i += W) {
     const double r = rcp_nr((D[i] - dorg) - tau);
     const double zi = z[i];
     const double t = zi * zi * r;
     b += t;
     db = fma(t, r, db);
   }
-  psi = warp_sum(a);
-  dpsi = warp_sum(da);
-  phi = warp_sum(b);
-  dphi = warp_sum(db);
+  if (W == 32) {
+    a = warp_sum(a);
+    da = warp_sum(da);
+    b = warp_sum(b);
+    db = warp_sum(db);
+  }
+  psi = a;
+  dpsi = da;
+  phi = b;
+  dphi = db;
   sabs = phi - psi;
 }
 
@@ -971,6 +980,7 @@ __device__ __forceinline__ double model_step(int j, int K, double irho, double d
 // nearest poles exact), safeguarded by bisection; stops when |g| is at rounding
 // level of 1/rho + sum |t| or the step is below rounding level of tau.  Returns
 // the number of passes over the poles (sum evaluations) made.
+template <int W = 32>
 __device__ int secular_fp64(const double* D, const double* z, int K, int j, double irho, int org, double& tau,
                             double& lo, double& hi, double psi, double dpsi, double phi, double dphi, double sabs,
                             int max_iter, bool& conv) {
@@ -981,7 +991,7 @@ __device__ int secular_fp64(const double* D, const double* z, int K, int j, doub
   conv = false;
   for (int it = 1; it <= max_iter; ++it) {
     if (it > 1) {
-      secular_sums(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
+      secular_sums<W>(D, z, K, j, dorg, tau, psi, dpsi, phi, dphi, sabs);
       ++passes;
     }
     const double gv = irho + psi + phi;
@@ -1228,11 +1238,71 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
   iters = min(passes, max_iter);
 }
 
-__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_act, int64_t nslots) {
+// Root j of a small merge by one thread (all poles in its loop): origin from the
+// sign of g at the midpoint; for the last root the start is the root of g with
+// every other pole frozen at tau = 0.  Same model, bracket and stopping rules as
+// the warp version.
+__device__ void secular_root_thread(const double* D, const double* z, int K, int j, double rho, int max_iter,
+                                    int& org_out, double& tau_out, int& iters, bool& conv) {
+  const double irho = 1.0 / rho;
+  int org;
+  double lo, hi, tau, psi, dpsi, phi, dphi, sabs;
+  if (j < K - 1) {
+    const double gap = D[j + 1] - D[j];
+    secular_sums<1>(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
+    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; tau = hi; }
+    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; tau = lo; }
+  } else {
+    double zz = 0.0, s0 = 0.0;
+    for (int i = 0; i < K; ++i) {
+      zz = fma(z[i], z[i], zz);
+      if (i < j) s0 += z[i] * z[i] * rcp_nr(D[i] - D[j]);
+    }
+    org = K - 1; lo = 0.0; hi = rho * zz; tau = hi;
+    const double den = irho + s0;
+    if (den > 0.0) {
+      const double t0 = z[j] * z[j] / den;
+      if (t0 > lo && t0 < hi) tau = t0;
+    }
+    secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+  }
+  const int passes = 1 + secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+  org_out = org;
+  tau_out = tau;
+  iters = min(passes, max_iter);
+}
+
+// Levels with at least kSmallMinSlots slots (many merges, e.g. batches) take
+// merges with K <= kSmallK a thread per root: that fills the machine with
+// independent work.  Levels with fewer slots keep a warp per root, which finishes
+// each root sooner.  small_k is the threshold a launch uses (0: none).
+static constexpr int kSmallK = 128;
+
+
+__global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nslots) return;
+  const Slot S = slot_of(P, level, nprob_act, s);
+  if (!S.valid || S.K > small_k) return;
+  int org, it;
+  double tau;
+  bool conv;
+  secular_root_thread(P.v.Dk + S.v0, P.v.zk + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
+  P.v.org[S.v0 + S.j] = org;
+  P.v.tau[S.v0 + S.j] = tau;
+  if (!conv) set_status(P.status, TDC_ENOCONV);
+  if (P.stats) {
+    atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
+    atomicAdd(&P.stats->iter_roots, 1ull);
+    atomicMax(&P.stats->iter_max, it);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
   const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (s >= nslots) return;
   const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid) return;
+  if (!S.valid || S.K <= small_k) return;
   int org, it;
   double tau;
   bool conv;
@@ -1255,7 +1325,11 @@ __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_ac
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.nslots == 0) return cudaSuccess;
   const int64_t blocks = (L.nslots * 32 + 255) / 256;
-  k_secular<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots);
+  const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
+  k_secular<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || small_k == 0) return e;
+  k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
   return cudaGetLastError();
 }
 
@@ -1284,12 +1358,13 @@ __device__ __forceinline__ void dnorm(double& x, int& ex) {
 // pole differences are accumulated as two separate products with their exponents
 // kept apart (one division per pole instead of one per term): both stay within
 // [2^-600, 2^600] and are renormalised when they leave it.
+template <int W = 32>
 __device__ double lowner_zhat(const double* D, const int* org, const double* tau, int K, int i, double rho,
                               double zsign) {
   const double di = D[i];
   double pn = 1.0, pd = 1.0;
   int en = 0, ed = 0;  // pn 2^en, pd 2^ed
-  for (int j = threadIdx.x & 31; j < K; j += 32) {
+  for (int j = W == 32 ? (threadIdx.x & 31) : 0; j < K; j += W) {
     const double num = (D[org[j]] - di) + tau[j];
     const double den = (j == K - 1) ? rho : ((j < i) ? D[j] - di : D[j + 1] - di);
     pn *= num;
@@ -1303,7 +1378,7 @@ __device__ double lowner_zhat(const double* D, const int* org, const double* tau
   dnorm(pn, en);
   dnorm(pd, ed);
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
+  for (int o = 16; o > 0 && W == 32; o >>= 1) {
     const double qn = __shfl_xor_sync(0xffffffffu, pn, o), qd = __shfl_xor_sync(0xffffffffu, pd, o);
     const int gn = __shfl_xor_sync(0xffffffffu, en, o), gd = __shfl_xor_sync(0xffffffffu, ed, o);
     pn *= qn;
@@ -1323,32 +1398,53 @@ __device__ double lowner_zhat(const double* D, const int* org, const double* tau
   return copysign(ldexp(sqrt(r), E / 2), zsign);
 }
 
-__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int nprob_act, int64_t nslots) {
+__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
   const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (s >= nslots) return;
   const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid) return;
+  if (!S.valid || S.K <= small_k) return;
   const double zh = lowner_zhat(P.v.Dk + S.v0, P.v.org + S.v0, P.v.tau + S.v0, S.K, S.j, S.rho,
                                 P.v.zk[S.v0 + S.j]);
   if ((threadIdx.x & 31) == 0) P.v.zhat[S.v0 + S.j] = zh;
 }
 
+// Merges with K <= kSmallK: a thread per pole (k_colnorm_small: per column).
+__global__ void __launch_bounds__(256) k_lowner_small(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nslots) return;
+  const Slot S = slot_of(P, level, nprob_act, s);
+  if (!S.valid || S.K > small_k) return;
+  P.v.zhat[S.v0 + S.j] = lowner_zhat<1>(P.v.Dk + S.v0, P.v.org + S.v0, P.v.tau + S.v0, S.K, S.j, S.rho,
+                                        P.v.zk[S.v0 + S.j]);
+}
+
+
 // s_j = 1 / sqrt(sum_i (zhat_i / delta_ij)^2), delta_ij = (d_i - d_org(j)) - tau_j.
+template <int W = 32>
 __device__ double column_norm(const double* D, const double* zh, int K, double dorg, double tj) {
   double acc = 0.0;
-  for (int i = threadIdx.x & 31; i < K; i += 32) {
+  for (int i = W == 32 ? (threadIdx.x & 31) : 0; i < K; i += W) {
     const double u = zh[i] * rcp_nr((D[i] - dorg) - tj);
     acc = fma(u, u, acc);
   }
-  acc = warp_sum(acc);
+  if (W == 32) acc = warp_sum(acc);
   return 1.0 / sqrt(acc);
 }
 
-__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int nprob_act, int64_t nslots) {
+__global__ void __launch_bounds__(256) k_colnorm_small(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= nslots) return;
+  const Slot S = slot_of(P, level, nprob_act, s);
+  if (!S.valid || S.K > small_k) return;
+  const double* D = P.v.Dk + S.v0;
+  P.v.scol[S.v0 + S.j] = column_norm<1>(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j]);
+}
+
+__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
   const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (s >= nslots) return;
   const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid) return;
+  if (!S.valid || S.K <= small_k) return;
   const double* D = P.v.Dk + S.v0;
   const double sj = column_norm(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j]);
   if ((threadIdx.x & 31) == 0) P.v.scol[S.v0 + S.j] = sj;
@@ -1399,10 +1495,14 @@ cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double 
 cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.nslots == 0) return cudaSuccess;
   const int64_t blocks = (L.nslots * 32 + 255) / 256;
-  k_lowner<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots);
+  const unsigned tblocks = (unsigned)((L.nslots + 255) / 256);
+  const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
+  k_lowner<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  if (small_k) k_lowner_small<<<tblocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_colnorm<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots);
+  k_colnorm<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  if (small_k) k_colnorm_small<<<tblocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
   return cudaGetLastError();
 }
 
