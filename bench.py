@@ -253,7 +253,7 @@ def run_batched(args):
     import torch
     from paper_2008_01990_gb300 import autotune, inputs, tdc
     dev = torch.device("cuda", 0)
-    sizes = inputs.batched_sizes(4096, 64, 2048, 3)
+    sizes = inputs.batched_sizes(args.batch, 64, 2048, 3)
     d, e, offs = inputs.batched_uniform(sizes, 3)
     qoffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
     dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
@@ -287,7 +287,8 @@ def run_batched(args):
     ost = tdc.default_opts(leaf=opts.leaf, split_min_K=opts.split_min_K, collect_stats=1)
     tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, ost, ws=ws)
     stats = tdc.get_stats()
-    print(json.dumps({"workload": "batched4096", "ms_per_batch": ms, "problems_per_s": 4096 / (ms * 1e-3),
+    print(json.dumps({"workload": "batched4096" if args.batch == 4096 else "batched%d" % args.batch,
+                      "ms_per_batch": ms, "problems_per_s": args.batch / (ms * 1e-3),
                       "leaf": opts.leaf, "split_min_K": opts.split_min_K, "status": st,
                       "sum_n": int(sizes.sum()), "q_bytes": int(qoffs[-1]) * 8,
                       "launches_per_solve": int(stats["launches"]), "phase_ms": stats["phase_ms"]}), flush=True)
@@ -551,6 +552,7 @@ def main():
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (default: the workload's)")
+    ap.add_argument("--batch", type=int, default=4096, help="problems of the batched workload (first ones of its sequence)")
     ap.add_argument("--split-min-k", type=int, default=0, help="smallest merge on the split path (default: library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

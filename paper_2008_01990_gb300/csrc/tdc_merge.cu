@@ -1298,21 +1298,26 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int np
   }
 }
 
-__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
-  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (s >= nslots) return;
-  const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid || S.K <= small_k) return;
+// Warp per root, merge-major: block (g, y) holds the roots 8y .. 8y+7 of merge g
+// (no slot search; blocks past K or of small merges leave at once).
+__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int small_k) {
+  const int64_t g = blockIdx.x;
+  const int K = P.m.K[g];
+  const int jw = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (K <= small_k || jw >= K) return;
+  const Node nd = make_node(P, level, g);
+  const int64_t v0 = nd.v0;
+  const double rho = 2.0 * fabs(nd.b);
   int org, it;
   double tau;
   bool conv;
-  // the merge's first slot takes its last root, usually the slowest to converge,
+  // the merge's first warp takes its last root, usually the slowest to converge,
   // so that it starts with the first wave of warps instead of ending the kernel
-  const int j = S.j == 0 ? S.K - 1 : S.j - 1;
-  secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, S.K, j, S.rho, P.max_iter, org, tau, it, conv);
+  const int j = jw == 0 ? K - 1 : jw - 1;
+  secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, rho, P.max_iter, org, tau, it, conv);
   if ((threadIdx.x & 31) == 0) {
-    P.v.org[S.v0 + j] = org;
-    P.v.tau[S.v0 + j] = tau;
+    P.v.org[v0 + j] = org;
+    P.v.tau[v0 + j] = tau;
     if (!conv) set_status(P.status, TDC_ENOCONV);
     if (P.stats) {
       atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
@@ -1324,9 +1329,9 @@ __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int nprob_ac
 
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.nslots == 0) return cudaSuccess;
-  const int64_t blocks = (L.nslots * 32 + 255) / 256;
   const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
-  k_secular<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  const dim3 wgrid((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
+  k_secular<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || small_k == 0) return e;
   k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
@@ -1398,14 +1403,15 @@ __device__ double lowner_zhat(const double* D, const int* org, const double* tau
   return copysign(ldexp(sqrt(r), E / 2), zsign);
 }
 
-__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
-  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (s >= nslots) return;
-  const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid || S.K <= small_k) return;
-  const double zh = lowner_zhat(P.v.Dk + S.v0, P.v.org + S.v0, P.v.tau + S.v0, S.K, S.j, S.rho,
-                                P.v.zk[S.v0 + S.j]);
-  if ((threadIdx.x & 31) == 0) P.v.zhat[S.v0 + S.j] = zh;
+__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int small_k) {
+  const int64_t g = blockIdx.x;
+  const int K = P.m.K[g];
+  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (K <= small_k || j >= K) return;
+  const Node nd = make_node(P, level, g);
+  const int64_t v0 = nd.v0;
+  const double zh = lowner_zhat(P.v.Dk + v0, P.v.org + v0, P.v.tau + v0, K, j, 2.0 * fabs(nd.b), P.v.zk[v0 + j]);
+  if ((threadIdx.x & 31) == 0) P.v.zhat[v0 + j] = zh;
 }
 
 // Merges with K <= kSmallK: a thread per pole (k_colnorm_small: per column).
@@ -1440,14 +1446,15 @@ __global__ void __launch_bounds__(256) k_colnorm_small(Plan P, int level, int np
   P.v.scol[S.v0 + S.j] = column_norm<1>(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j]);
 }
 
-__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
-  const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  if (s >= nslots) return;
-  const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid || S.K <= small_k) return;
-  const double* D = P.v.Dk + S.v0;
-  const double sj = column_norm(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j]);
-  if ((threadIdx.x & 31) == 0) P.v.scol[S.v0 + S.j] = sj;
+__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int small_k) {
+  const int64_t g = blockIdx.x;
+  const int K = P.m.K[g];
+  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+  if (K <= small_k || j >= K) return;
+  const int64_t v0 = make_node(P, level, g).v0;
+  const double* D = P.v.Dk + v0;
+  const double sj = column_norm(D, P.v.zhat + v0, K, D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
+  if ((threadIdx.x & 31) == 0) P.v.scol[v0 + j] = sj;
 }
 
 // Stand-alone rank-one eigenproblem (tdc_rank_one): the three warp-per-entry stages.
@@ -1494,14 +1501,14 @@ cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double 
 
 cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.nslots == 0) return cudaSuccess;
-  const int64_t blocks = (L.nslots * 32 + 255) / 256;
   const unsigned tblocks = (unsigned)((L.nslots + 255) / 256);
   const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
-  k_lowner<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  const dim3 wgrid((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
+  k_lowner<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
   if (small_k) k_lowner_small<<<tblocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_colnorm<<<(unsigned)blocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  k_colnorm<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
   if (small_k) k_colnorm_small<<<tblocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
   return cudaGetLastError();
 }
