@@ -218,7 +218,7 @@ static Layout layout_of(const HostPlan& H) {
   L.vec_i = o; o = align_up(o + sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
   L.vec_b = o; o = align_up(o + kVecB * (size_t)std::max<int64_t>(1, H.N));
   L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
-  L.tiles = o; o = align_up(o + sizeof(int64_t) * (size_t)(H.Mmax + 1));
+  L.tiles = o; o = align_up(o + sizeof(int64_t) * 2 * (size_t)(H.Mmax + 1));
   L.stats = o; o = align_up(o + sizeof(Stats));
   L.segs = o; o = align_up(o + ((H.split_S || H.struct_m) ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
@@ -255,6 +255,7 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   P.m.K = mi; P.m.nd = mi + M; P.m.nrot = mi + 2 * M; P.m.ntop = mi + 3 * M; P.m.nbot = mi + 4 * M;
   P.m.nchain = mi + 5 * M;
   P.m.tiles = (int64_t*)(base + L.tiles);
+  P.m.roff = P.m.tiles + (H.Mmax + 1);
   P.Q1 = (double*)(base + L.q1);
   P.prob = (const Problem*)(base + L.prob);
   P.segs = (H.split_S || H.struct_m) ? (GemmSeg*)(base + L.segs) : nullptr;
@@ -351,11 +352,11 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   auto span = [&](int phase, size_t a0, size_t a1) {
     if (timing) spans.push_back({phase, {a0, a1}});
   };
-  // kernel launches: problem upload, corner modification, leaves, 9 per level (12
+  // kernel launches: problem upload, corner modification, leaves, 9 per level (13
   // on levels that also run the thread-per-root variants), output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
-    if (H.levels[l].nslots >= kSmallMinSlots) launches += 3;
+    if (H.levels[l].nslots >= kSmallMinSlots) launches += 4;
     if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4 * (int64_t)H.split_chunks[l].size();
     if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
       launches += 2 + 2 * ((H.levels[l].max_n + H.struct_m - 1) / H.struct_m);

@@ -1238,35 +1238,141 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
   iters = min(passes, max_iter);
 }
 
-// Root j of a small merge by one thread (all poles in its loop): origin from the
-// sign of g at the midpoint; for the last root the start is the root of g with
-// every other pole frozen at tau = 0.  Same model, bracket and stopping rules as
-// the warp version.
-__device__ void secular_root_thread(const double* D, const double* z, int K, int j, double rho, int max_iter,
-                                    int& org_out, double& tau_out, int& iters, bool& conv) {
-  const double irho = 1.0 / rho;
-  int org;
-  double lo, hi, tau, psi, dpsi, phi, dphi, sabs;
-  if (j < K - 1) {
-    const double gap = D[j + 1] - D[j];
-    secular_sums<1>(D, z, K, j, D[j], 0.5 * gap, psi, dpsi, phi, dphi, sabs);
-    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * gap; tau = hi; }
-    else { org = j + 1; lo = -0.5 * gap; hi = 0.0; tau = lo; }
-  } else {
-    double zz = 0.0, s0 = 0.0;
+// FP32 pre-iteration of one thread for root j of a small merge, in the frame of
+// pole j: tau in (0, width).  The six poles j-2 .. j+3 use their FP64 differences,
+// the others the merge's FP32 coordinates; the model steps are those of the warp
+// version (two-pole for interior roots from the midpoint; one-pole for the last
+// root from its frozen-poles start).  Returns false if no usable estimate.
+__device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, int j, float irho, float width,
+                                    float& tau_out) {
+  const bool last = j == K - 1;
+  float w6[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int i = j - 2 + q;
+    w6[q] = (i >= 0 && i < K) ? (float)(D[i] - D[j]) : 0.0f;
+  }
+  const float xj = xz[j].x;
+  float lo = 0.0f, hi = width, tau = 0.5f * width;
+  for (int it = 0; it < 12; ++it) {
+    const float tv = (last && it == 0) ? 0.0f : tau;
+    float a = 0.0f, da = 0.0f, b = 0.0f, db = 0.0f;
     for (int i = 0; i < K; ++i) {
-      zz = fma(z[i], z[i], zz);
-      if (i < j) s0 += z[i] * z[i] * rcp_nr(D[i] - D[j]);
+      if (last && it == 0 && i == j) continue;
+      const float2 v = xz[i];
+      float del = v.x - xj;
+      const int q = i - (j - 2);
+#pragma unroll
+      for (int u = 0; u < 6; ++u)
+        if (q == u) del = w6[u];
+      float r;
+      asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tv));
+      const float t = v.y * r;
+      if (i <= j) { a += t; da = fmaf(t, r, da); }
+      else { b += t; db = fmaf(t, r, db); }
     }
-    org = K - 1; lo = 0.0; hi = rho * zz; tau = hi;
+    if (last && it == 0) {
+      const float den = irho + a;
+      const float t0 = den > 0.0f ? xz[j].y / den : -1.0f;
+      if (t0 > 0.0f && t0 < width) tau = t0;
+      continue;
+    }
+    const float gv = irho + a + b;
+    if (!isfinite(gv)) return false;
+    if (gv == 0.0f) break;
+    if (gv < 0.0f) lo = tau; else hi = tau;
+    const float p = -tau;
+    float h = 0.0f;
+    bool ok = true;
+    if (last) {
+      const float b1 = da * p * p;
+      const float A = irho + (a - b1 / p) + b;
+      if (A != 0.0f) h = p + b1 / A; else ok = false;
+    } else {
+      const float q2 = width - tau;
+      const float b1 = da * p * p, b2 = db * q2 * q2;
+      const float A = irho + (a - b1 / p) + (b - b2 / q2);
+      const float B = A * (p + q2) + b1 + b2;
+      const float C = p * q2 * gv;
+      if (A == 0.0f) {
+        h = C / B;
+      } else {
+        const float disc = B * B - 4.0f * A * C;
+        if (disc < 0.0f) {
+          ok = false;
+        } else {
+          const float w = B + copysignf(sqrtf(disc), B);
+          const float h1 = (w != 0.0f) ? 2.0f * C / w : 0.0f;
+          const float h2 = w / (2.0f * A);
+          const bool in1 = (h1 > p && h1 < q2), in2 = (h2 > p && h2 < q2);
+          if (in1 && (!in2 || fabsf(h1) <= fabsf(h2))) h = h1;
+          else if (in2) h = h2;
+          else ok = false;
+        }
+      }
+    }
+    float tn = tau + h;
+    if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5f * (lo + hi);
+    const bool small = fabsf(tn - tau) <= 2e-7f * fabsf(tau);
+    tau = tn;
+    if (small || (hi - lo) <= 4e-7f * hi) break;
+  }
+  if (!(tau > 0.0f && tau < width)) return false;
+  tau_out = tau;
+  return true;
+}
+
+// Root j of a small merge by one thread (all poles in its loop): the FP32
+// estimate picks the origin and starts the FP64 iteration (whole interval as
+// bracket; re-solved from the other pole if it converges in that pole's half);
+// without a usable estimate, the origin comes from the sign of g at the midpoint
+// and the last root starts from the root of g with the other poles frozen.
+__device__ void secular_root_thread(const double* D, const double* z, const float2* xz, int K, int j, double rho,
+                                    int max_iter, int& org_out, double& tau_out, int& iters, bool& conv) {
+  const double irho = 1.0 / rho;
+  const bool last = j == K - 1;
+  int org;
+  double lo, hi, tau, psi, dpsi, phi, dphi, sabs, width;
+  if (!last) {
+    width = D[j + 1] - D[j];
+  } else {
+    double zz = 0.0;
+    for (int i = 0; i < K; ++i) zz = fma(z[i], z[i], zz);
+    width = rho * zz;
+  }
+  float t32 = 0.0f;
+  int passes = 1;
+  if (xz != nullptr && width > 0.0 && secular_fp32_thread(D, xz, K, j, (float)irho, (float)width, t32)) {
+    if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
+    else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
+    if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+    secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+    passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+    const bool far = !last && conv && ((org == j) ? (tau > 0.5 * width) : (tau < -0.5 * width));
+    if (far) {
+      if (org == j) { org = j + 1; tau -= width; lo -= width; hi -= width; }
+      else { org = j; tau += width; lo += width; hi += width; }
+      secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+      ++passes;
+      passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+    }
+  } else if (!last) {
+    secular_sums<1>(D, z, K, j, D[j], 0.5 * width, psi, dpsi, phi, dphi, sabs);
+    if (irho + psi + phi >= 0.0) { org = j; lo = 0.0; hi = 0.5 * width; tau = hi; }
+    else { org = j + 1; lo = -0.5 * width; hi = 0.0; tau = lo; }
+    passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+  } else {
+    double s0 = 0.0;
+    for (int i = 0; i < j; ++i) s0 += z[i] * z[i] * rcp_nr(D[i] - D[j]);
+    org = K - 1; lo = 0.0; hi = width; tau = hi;
     const double den = irho + s0;
     if (den > 0.0) {
       const double t0 = z[j] * z[j] / den;
       if (t0 > lo && t0 < hi) tau = t0;
     }
     secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+    passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
   }
-  const int passes = 1 + secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
   org_out = org;
   tau_out = tau;
   iters = min(passes, max_iter);
@@ -1279,17 +1385,61 @@ __device__ void secular_root_thread(const double* D, const double* z, int K, int
 static constexpr int kSmallK = 128;
 
 
-__global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= nslots) return;
-  const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid || S.K > small_k) return;
+// Roots of the merges with 0 < K <= small_k, numbered merge by merge: roff[g] is
+// the first number of merge g, roff[M] the total (one block, two-level scan).
+__global__ void __launch_bounds__(1024) k_root_scan(Plan P, int64_t M, int small_k) {
+  __shared__ int64_t part[1024];
+  const int64_t per = (M + blockDim.x - 1) / blockDim.x;
+  const int64_t a = min(M, (int64_t)threadIdx.x * per), b = min(M, a + per);
+  int64_t s = 0;
+  for (int64_t g = a; g < b; ++g) {
+    const int K = P.m.K[g];
+    s += (K > 0 && K <= small_k) ? K : 0;
+  }
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t t = part[i]; part[i] = run; run += t; }
+    P.m.roff[M] = run;
+  }
+  __syncthreads();
+  int64_t run = part[threadIdx.x];
+  for (int64_t g = a; g < b; ++g) {
+    P.m.roff[g] = run;
+    const int K = P.m.K[g];
+    run += (K > 0 && K <= small_k) ? K : 0;
+  }
+}
+
+// Thread t -> (merge g, root j) of the small merges: the last g with roff[g] <= t.
+__device__ __forceinline__ bool small_root(const Plan& P, int64_t M, int64_t t, int64_t& g, int& j) {
+  if (t >= P.m.roff[M]) return false;
+  int64_t lo = 0, hi = M - 1;
+  while (lo < hi) {
+    const int64_t m = (lo + hi + 1) >> 1;
+    if (P.m.roff[m] <= t) lo = m; else hi = m - 1;
+  }
+  g = lo;
+  j = (int)(t - P.m.roff[lo]);
+  return true;
+}
+
+__global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_t M) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t g;
+  int j;
+  if (!small_root(P, M, t, g, j)) return;
+  const Node nd = make_node(P, level, g);
+  const int64_t v0 = nd.v0;
+  const int K = P.m.K[g];
   int org, it;
   double tau;
   bool conv;
-  secular_root_thread(P.v.Dk + S.v0, P.v.zk + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
-  P.v.org[S.v0 + S.j] = org;
-  P.v.tau[S.v0 + S.j] = tau;
+  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, 2.0 * fabs(nd.b), P.max_iter, org, tau, it,
+                      conv);
+  P.v.org[v0 + j] = org;
+  P.v.tau[v0 + j] = tau;
   if (!conv) set_status(P.status, TDC_ENOCONV);
   if (P.stats) {
     atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
@@ -1334,7 +1484,8 @@ cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) 
   k_secular<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || small_k == 0) return e;
-  k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  k_root_scan<<<1, 1024, 0, s>>>(P, L.merges, small_k);
+  k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.merges);
   return cudaGetLastError();
 }
 
@@ -1415,13 +1566,15 @@ __global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int small_k) 
 }
 
 // Merges with K <= kSmallK: a thread per pole (k_colnorm_small: per column).
-__global__ void __launch_bounds__(256) k_lowner_small(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= nslots) return;
-  const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid || S.K > small_k) return;
-  P.v.zhat[S.v0 + S.j] = lowner_zhat<1>(P.v.Dk + S.v0, P.v.org + S.v0, P.v.tau + S.v0, S.K, S.j, S.rho,
-                                        P.v.zk[S.v0 + S.j]);
+__global__ void __launch_bounds__(256) k_lowner_small(Plan P, int level, int64_t M) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t g;
+  int j;
+  if (!small_root(P, M, t, g, j)) return;
+  const Node nd = make_node(P, level, g);
+  const int64_t v0 = nd.v0;
+  P.v.zhat[v0 + j] = lowner_zhat<1>(P.v.Dk + v0, P.v.org + v0, P.v.tau + v0, P.m.K[g], j, 2.0 * fabs(nd.b),
+                                    P.v.zk[v0 + j]);
 }
 
 
@@ -1437,13 +1590,14 @@ __device__ double column_norm(const double* D, const double* zh, int K, double d
   return 1.0 / sqrt(acc);
 }
 
-__global__ void __launch_bounds__(256) k_colnorm_small(Plan P, int level, int nprob_act, int64_t nslots, int small_k) {
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= nslots) return;
-  const Slot S = slot_of(P, level, nprob_act, s);
-  if (!S.valid || S.K > small_k) return;
-  const double* D = P.v.Dk + S.v0;
-  P.v.scol[S.v0 + S.j] = column_norm<1>(D, P.v.zhat + S.v0, S.K, D[P.v.org[S.v0 + S.j]], P.v.tau[S.v0 + S.j]);
+__global__ void __launch_bounds__(256) k_colnorm_small(Plan P, int level, int64_t M) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t g;
+  int j;
+  if (!small_root(P, M, t, g, j)) return;
+  const int64_t v0 = make_node(P, level, g).v0;
+  const double* D = P.v.Dk + v0;
+  P.v.scol[v0 + j] = column_norm<1>(D, P.v.zhat + v0, P.m.K[g], D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
 }
 
 __global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int small_k) {
@@ -1505,11 +1659,11 @@ cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
   const dim3 wgrid((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
   k_lowner<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
-  if (small_k) k_lowner_small<<<tblocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  if (small_k) k_lowner_small<<<tblocks, 256, 0, s>>>(P, L.level, L.merges);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_colnorm<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
-  if (small_k) k_colnorm_small<<<tblocks, 256, 0, s>>>(P, L.level, L.nprob_act, L.nslots, small_k);
+  if (small_k) k_colnorm_small<<<tblocks, 256, 0, s>>>(P, L.level, L.merges);
   return cudaGetLastError();
 }
 
