@@ -218,7 +218,7 @@ static Layout layout_of(const HostPlan& H) {
   L.vec_i = o; o = align_up(o + sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
   L.vec_b = o; o = align_up(o + kVecB * (size_t)std::max<int64_t>(1, H.N));
   L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
-  L.tiles = o; o = align_up(o + sizeof(int64_t) * 2 * (size_t)(H.Mmax + 1));
+  L.tiles = o; o = align_up(o + sizeof(int64_t) * (2 * (size_t)H.Mmax + 3));
   L.stats = o; o = align_up(o + sizeof(Stats));
   L.segs = o; o = align_up(o + ((H.split_S || H.struct_m) ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
@@ -352,11 +352,11 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   auto span = [&](int phase, size_t a0, size_t a1) {
     if (timing) spans.push_back({phase, {a0, a1}});
   };
-  // kernel launches: problem upload, corner modification, leaves, 9 per level (13
+  // kernel launches: problem upload, corner modification, leaves, 9 per level (14
   // on levels that also run the thread-per-root variants), output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
-    if (H.levels[l].nslots >= kSmallMinSlots) launches += 4;
+    if (H.levels[l].nslots >= kSmallMinSlots) launches += 5;
     if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4 * (int64_t)H.split_chunks[l].size();
     if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
       launches += 2 + 2 * ((H.levels[l].max_n + H.struct_m - 1) / H.struct_m);

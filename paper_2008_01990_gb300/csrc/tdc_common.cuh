@@ -69,7 +69,8 @@ struct MergeInfo {  // per merge of the current level
   int32_t* nbot;    // |S_bot|
   int32_t* nchain;  // independent rotation chains
   int64_t* tiles;   // GEMM tile prefix (M + 1 entries)
-  int64_t* roff;    // prefix of the roots of small merges (thread-per-root kernels), M + 1 entries
+  int64_t* roff;    // prefix of the roots of small merges (thread-per-root kernels), M + 1 entries,
+                    // then the count of roots handed to the warp-per-root fix-up
 };
 
 struct Stats {  // device-side per-call statistics (index 0 = top level)

@@ -1402,6 +1402,7 @@ __global__ void __launch_bounds__(1024) k_root_scan(Plan P, int64_t M, int small
     int64_t run = 0;
     for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t t = part[i]; part[i] = run; run += t; }
     P.m.roff[M] = run;
+    P.m.roff[M + 1] = 0;  // roots passed on to k_secular_fixup
   }
   __syncthreads();
   int64_t run = part[threadIdx.x];
@@ -1425,6 +1426,12 @@ __device__ __forceinline__ bool small_root(const Plan& P, int64_t M, int64_t t, 
   return true;
 }
 
+// A thread per root, at most kSmallPasses FP64 passes: a warp waits for its slowest
+// lane, so the few roots that need more are listed (slot numbers, in the sort tag
+// scratch, free between deflation and the final ordering) and finished by a warp
+// each in k_secular_fixup.
+static constexpr int kSmallPasses = 6;
+
 __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_t M) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t g;
@@ -1433,11 +1440,17 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
   const Node nd = make_node(P, level, g);
   const int64_t v0 = nd.v0;
   const int K = P.m.K[g];
+  const bool capped = P.max_iter > kSmallPasses;
   int org, it;
   double tau;
   bool conv;
-  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, 2.0 * fabs(nd.b), P.max_iter, org, tau, it,
-                      conv);
+  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, 2.0 * fabs(nd.b),
+                      capped ? kSmallPasses : P.max_iter, org, tau, it, conv);
+  if (!conv && capped) {
+    const unsigned long long q = atomicAdd(reinterpret_cast<unsigned long long*>(P.m.roff + M + 1), 1ull);
+    P.v.stag[q] = (int)(v0 + j);
+    return;
+  }
   P.v.org[v0 + j] = org;
   P.v.tau[v0 + j] = tau;
   if (!conv) set_status(P.status, TDC_ENOCONV);
@@ -1445,6 +1458,30 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
     atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
     atomicAdd(&P.stats->iter_roots, 1ull);
     atomicMax(&P.stats->iter_max, it);
+  }
+}
+
+// The listed roots, a warp each (the warp-per-root solver with its full budget).
+__global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int nprob_act, int64_t M) {
+  const int64_t cnt = P.m.roff[M + 1];
+  for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < cnt;
+       w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const Slot S = slot_of(P, level, nprob_act, P.v.stag[w]);
+    if (!S.valid) continue;
+    int org, it;
+    double tau;
+    bool conv;
+    secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
+    if ((threadIdx.x & 31) == 0) {
+      P.v.org[S.v0 + S.j] = org;
+      P.v.tau[S.v0 + S.j] = tau;
+      if (!conv) set_status(P.status, TDC_ENOCONV);
+      if (P.stats) {
+        atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
+        atomicAdd(&P.stats->iter_roots, 1ull);
+        atomicMax(&P.stats->iter_max, it);
+      }
+    }
   }
 }
 
@@ -1486,6 +1523,7 @@ cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) 
   if (e != cudaSuccess || small_k == 0) return e;
   k_root_scan<<<1, 1024, 0, s>>>(P, L.merges, small_k);
   k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.merges);
+  k_secular_fixup<<<152 * 8, 256, 0, s>>>(P, L.level, L.nprob_act, L.merges);
   return cudaGetLastError();
 }
 
