@@ -1257,8 +1257,9 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
   for (int it = 0; it < 12; ++it) {
     const float tv = (last && it == 0) ? 0.0f : tau;
     float a = 0.0f, da = 0.0f, b = 0.0f, db = 0.0f;
-    for (int i = 0; i < K; ++i) {
-      if (last && it == 0 && i == j) continue;
+    // poles left of the root and right of it in two loops (each lane its own j):
+    // no divergent branch inside the loop
+    auto term = [&](int i, float& acc, float& dacc) {
       const float2 v = xz[i];
       float del = v.x - xj;
       const int q = i - (j - 2);
@@ -1268,9 +1269,12 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
       float r;
       asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tv));
       const float t = v.y * r;
-      if (i <= j) { a += t; da = fmaf(t, r, da); }
-      else { b += t; db = fmaf(t, r, db); }
-    }
+      acc += t;
+      dacc = fmaf(t, r, dacc);
+    };
+    const int jl = (last && it == 0) ? j : j + 1;  // the last root's first pass leaves out pole j
+    for (int i = 0; i < jl; ++i) term(i, a, da);
+    for (int i = j + 1; i < K; ++i) term(i, b, db);
     if (last && it == 0) {
       const float den = irho + a;
       const float t0 = den > 0.0f ? xz[j].y / den : -1.0f;
@@ -1322,6 +1326,68 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
   return true;
 }
 
+// The certified FP64 iteration of secular_certified for one thread: one full pass
+// at tau1 keeps the six poles j-2 .. j+3 apart from the far sums (t, t r, t r^2 per
+// side), the following iterates re-evaluate only those six; same remainder bound
+// and acceptance test.
+__device__ bool secular_certified_thread(const double* D, const double* z, int K, int j, double irho, int org,
+                                         double& tau, double& lo, double& hi, bool& conv) {
+  const double dorg = D[org];
+  const double dl = D[j] - dorg, dr = (j < K - 1) ? D[j + 1] - dorg : 0.0;
+  const int wlo = max(0, j - 2), whi = min(K - 1, j + 3);
+  const double tau1 = tau;
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
+  for (int i = 0; i < wlo; ++i) {
+    const double r = rcp_nr((D[i] - dorg) - tau1);
+    const double t = z[i] * z[i] * r, tr = t * r;
+    a0 += t; a1 += tr; a2 = fma(tr, r, a2);
+  }
+  for (int i = whi + 1; i < K; ++i) {
+    const double r = rcp_nr((D[i] - dorg) - tau1);
+    const double t = z[i] * z[i] * r, tr = t * r;
+    b0 += t; b1 += tr; b2 = fma(tr, r, b2);
+  }
+  double dmin = HUGE_VAL;
+  if (wlo - 1 >= 0) dmin = fmin(dmin, fabs((D[wlo - 1] - dorg) - tau1));
+  if (whi + 1 < K) dmin = fmin(dmin, fabs((D[whi + 1] - dorg) - tau1));
+  conv = false;
+  double tc = tau1;
+  for (int k = 0; k < 8; ++k) {
+    const double e = tc - tau1;
+    const double q = fabs(e) / dmin;
+    if (!(q < 4e-6)) break;
+    double wl = 0.0, wr = 0.0, wdl = 0.0, wdr = 0.0;
+    for (int i = wlo; i <= whi; ++i) {
+      const double r = rcp_nr((D[i] - dorg) - tc);
+      const double t = z[i] * z[i] * r;
+      if (i <= j) { wl += t; wdl = fma(t, r, wdl); }
+      else { wr += t; wdr = fma(t, r, wdr); }
+    }
+    const double rest = k > 0 ? (b0 - a0) * (q * q * q) / (1.0 - q) : 0.0;
+    const double psi = a0 + e * (a1 + e * a2) + wl, dpsi = a1 + 2.0 * e * a2 + wdl;
+    const double phi = b0 + e * (b1 + e * b2) + wr, dphi = b1 + 2.0 * e * b2 + wdr;
+    const double gv = irho + psi + phi;
+    if (gv == 0.0 || fabs(gv) + rest <= 8.0 * kEps * (irho + (phi - psi))) {
+      tau = tc;
+      conv = true;
+      return true;
+    }
+    if (fabs(gv) > rest) {
+      if (gv < 0.0) lo = tc; else hi = tc;
+    }
+    const double tn = model_step(j, K, irho, dl, dr, tc, gv, psi, dpsi, phi, dphi, lo, hi);
+    const bool exact_g = rest <= kEps * (irho + (phi - psi));
+    if (exact_g && (fabs(tn - tc) <= 2.0 * kEps * fabs(tc) || (hi - lo) <= 2.0 * kEps * fmax(fabs(lo), fabs(hi)))) {
+      tau = tn;
+      conv = true;
+      return true;
+    }
+    tc = tn;
+  }
+  tau = tc;
+  return false;
+}
+
 // Root j of a small merge by one thread (all poles in its loop): the FP32
 // estimate picks the origin and starts the FP64 iteration (whole interval as
 // bracket; re-solved from the other pole if it converges in that pole's half);
@@ -1346,8 +1412,12 @@ __device__ void secular_root_thread(const double* D, const double* z, const floa
     if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
     else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
-    secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
-    passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+    const bool tried = max_iter >= 2;
+    if (!tried || !secular_certified_thread(D, z, K, j, irho, org, tau, lo, hi, conv)) {
+      secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
+      if (tried) ++passes;
+      passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
+    }
     const bool far = !last && conv && ((org == j) ? (tau > 0.5 * width) : (tau < -0.5 * width));
     if (far) {
       if (org == j) { org = j + 1; tau -= width; lo -= width; hi -= width; }
