@@ -292,7 +292,8 @@ def run_batched(args):
                       "leaf": opts.leaf, "split_min_K": opts.split_min_K, "status": st,
                       "sum_n": int(sizes.sum()), "q_bytes": int(qoffs[-1]) * 8,
                       "launches_per_solve": int(stats["launches"]), "phase_ms": stats["phase_ms"],
-                      "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"]},
+                      "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"],
+                                             "handoffs": stats.get("secular_handoffs")},
                       "K_per_level": stats["sum_K"], "n_per_level": stats["sum_n"]}), flush=True)
     return 0
 

@@ -94,6 +94,8 @@ typedef struct {
   double struct_flops;                   /* flops executed by the structured path (dense near-diagonal
                                             tiles + the two thin products of the low-rank tiles) */
   int64_t launches;                      /* kernel launches of the call */
+  int64_t secular_handoffs;              /* roots of small merges whose thread-per-root solve was not
+                                            certified in one pass and went to a warp-per-root solve */
 } tdc_stats;
 
 /* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,

@@ -189,8 +189,10 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
       const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;
       mx = std::max(mx, nm);
       const int64_t n1 = (nm + 1) / 2;
-      const int64_t rt = 2 * ((n1 + kDenseBM - 1) / kDenseBM);
-      tiles += (((int64_t)1) << l) * rt * ((nm + kDenseBN - 1) / kDenseBN);
+      int bm, bn;
+      dense_tile_dims(nm, bm, bn);
+      const int64_t rt = 2 * ((n1 + bm - 1) / bm);
+      tiles += (((int64_t)1) << l) * rt * ((nm + bn - 1) / bn);
     }
     L.nprob_act = c;
     L.merges = ((int64_t)c) << l;
@@ -218,7 +220,7 @@ static Layout layout_of(const HostPlan& H) {
   L.vec_i = o; o = align_up(o + sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
   L.vec_b = o; o = align_up(o + kVecB * (size_t)std::max<int64_t>(1, H.N));
   L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
-  L.tiles = o; o = align_up(o + sizeof(int64_t) * (2 * (size_t)H.Mmax + 3));
+  L.tiles = o; o = align_up(o + sizeof(int64_t) * (3 * (size_t)H.Mmax + 4));
   L.stats = o; o = align_up(o + sizeof(Stats));
   L.segs = o; o = align_up(o + ((H.split_S || H.struct_m) ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
@@ -256,6 +258,7 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   P.m.nchain = mi + 5 * M;
   P.m.tiles = (int64_t*)(base + L.tiles);
   P.m.roff = P.m.tiles + (H.Mmax + 1);
+  P.m.boff = P.m.roff + (H.Mmax + 2);
   P.Q1 = (double*)(base + L.q1);
   P.prob = (const Problem*)(base + L.prob);
   P.segs = (H.split_S || H.struct_m) ? (GemmSeg*)(base + L.segs) : nullptr;
@@ -374,7 +377,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     if (err == cudaSuccess) err = launch_secular(P, LL, s);
     const size_t a2 = mark();
     if (err == cudaSuccess) err = launch_lowner(P, LL, s);
-    if (err == cudaSuccess) err = launch_finalize(P, LL, kDenseBM, kDenseBN, s);
+    if (err == cudaSuccess) err = launch_finalize(P, LL, s);
     const size_t a3 = mark();
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
     if (err == cudaSuccess && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
@@ -448,6 +451,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     g_last_stats.split_bytes = (double)hs.split_bytes;
     g_last_stats.struct_flops = (double)hs.struct_flops;
     g_last_stats.launches = launches;
+    g_last_stats.secular_handoffs = (int64_t)hs.handoffs;
     g_last_stats.secular_iter_max = hs.iter_max;
     g_last_stats.secular_iter_mean = hs.iter_roots ? (double)hs.iter_sum / (double)hs.iter_roots : 0.0;
     for (int i = 0; i < 12; ++i) g_last_stats.phase_ms[i] = phase[i];

@@ -71,6 +71,7 @@ struct MergeInfo {  // per merge of the current level
   int64_t* tiles;   // GEMM tile prefix (M + 1 entries)
   int64_t* roff;    // prefix of the roots of small merges (thread-per-root kernels), M + 1 entries,
                     // then the count of roots handed to the warp-per-root fix-up
+  int64_t* boff;    // prefix of the 8-root blocks of the other merges (warp per root), M + 1 entries
 };
 
 struct Stats {  // device-side per-call statistics (index 0 = top level)
@@ -87,6 +88,7 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   unsigned long long iter_sum;
   unsigned long long iter_roots;
   int iter_max;
+  unsigned long long handoffs;
 };
 
 // One GEMM segment C(rows x K) = A(rows x kk) * Qhat(list, :) of the merge
@@ -290,7 +292,7 @@ cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s);
-cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, int bm, int bn, cudaStream_t s);
+cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, int sign_normalise, cudaStream_t s);
 cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream_t s);
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
@@ -313,4 +315,11 @@ cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q,
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
+// merges of order n <= kDenseSmallN take 32 x 32 tiles: their halves are at most 64 rows,
+// so a 128-row tile would leave most of its FP64 multiply-adds on padding
+constexpr int kDenseSmallN = 128, kDenseSmallBM = 32, kDenseSmallBN = 32;
+__host__ __device__ inline void dense_tile_dims(int64_t n, int& bm, int& bn) {
+  bm = n <= kDenseSmallN ? kDenseSmallBM : kDenseBM;
+  bn = n <= kDenseSmallN ? kDenseSmallBN : kDenseBN;
+}
 }  // namespace tdc

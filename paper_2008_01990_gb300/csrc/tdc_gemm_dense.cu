@@ -45,18 +45,128 @@ __device__ __forceinline__ void near_range(const int* list, int nl, int j0, int 
     qhi = min(phi, nl);
   }
 }
+
+// Per-column and per-pole values of the tile being computed.
+struct DenseCols {
+  double Do[BN], Tau[BN], S[BN];
+  int Pos[BN];
+  int Col[BK];
+  double Dq[BK], Zq[BK];
+};
+
+// One TBM x TBN output tile (tile number `local` of merge g) on 256 threads,
+// TM x TN outputs each.  kRowFast puts consecutive threads on consecutive row
+// groups, so that a warp's stores of one column are contiguous.
+template <int TBM, int TBN, bool kRowFast>
+__device__ __forceinline__ void dense_tile(const Plan& P, const Node& nd, int64_t g, int64_t local, double* As,
+                                           double* Us, DenseCols& sc) {
+  constexpr int TM = TBM / 16, TN = TBN / 16;
+  static_assert(TBM % 16 == 0 && TBN % 16 == 0 && TBN <= BN && TBM * BK <= BM * BK, "tile shape");
+  const int tid = threadIdx.x;
+  const int ty = kRowFast ? (tid & 15) : (tid >> 4);  // row group: TM rows
+  const int tx = kRowFast ? (tid >> 4) : (tid & 15);  // column group: TN columns
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int K = P.m.K[g];
+  const int ct = (K + TBN - 1) / TBN;
+  const int rtt = (int)(local / ct), ctile = (int)(local % ct);
+  const int rt0 = (n1 + TBM - 1) / TBM;
+  int r0, rend, nl;
+  const int* list;
+  if (rtt < rt0) { r0 = rtt * TBM; rend = n1; list = P.v.tlist + nd.v0; nl = P.m.ntop[g]; }
+  else { r0 = n1 + (rtt - rt0) * TBM; rend = n; list = P.v.blist + nd.v0; nl = P.m.nbot[g]; }
+  const int j0 = ctile * TBN;
+  const double* Dk = P.v.Dk + nd.v0;
+  // structured merge: only the poles within one tile of the output columns here
+  // (TBN divides the structured tile size, a multiple of 64)
+  int qlo = 0, qhi = nl;
+  const bool structured = P.struct_min_K > 0 && K >= P.struct_min_K;
+  if (structured) {
+    near_range(list, nl, j0, P.struct_m, K, qlo, qhi);
+    if (P.stats && tid == 0)
+      atomicAdd(&P.stats->struct_flops, 2ull * (unsigned long long)min(TBM, rend - r0) *
+                                             (unsigned long long)(qhi - qlo) * (unsigned long long)min(TBN, K - j0));
+  }
+  __syncthreads();
+  if (tid < TBN) {
+    const int j = j0 + tid;
+    if (j < K) {
+      sc.Do[tid] = Dk[P.v.org[nd.v0 + j]];
+      sc.Tau[tid] = P.v.tau[nd.v0 + j];
+      sc.S[tid] = P.v.scol[nd.v0 + j];
+      sc.Pos[tid] = P.v.posr[nd.v0 + j];
+    } else {
+      sc.Do[tid] = 0.0; sc.Tau[tid] = 1.0; sc.S[tid] = 0.0; sc.Pos[tid] = -1;
+    }
+  }
+  double acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int c = 0; c < TN; ++c) acc[i][c] = 0.0;
+  for (int k0 = qlo; k0 < qhi; k0 += BK) {
+    __syncthreads();
+    if (tid < BK) {
+      const int k = k0 + tid;
+      if (k < qhi) {
+        const int q = list[k];
+        sc.Col[tid] = P.v.kept[nd.v0 + q];
+        sc.Dq[tid] = Dk[q];
+        sc.Zq[tid] = P.v.zhat[nd.v0 + q];
+      } else {
+        sc.Col[tid] = -1; sc.Dq[tid] = 0.0; sc.Zq[tid] = 0.0;
+      }
+    }
+    __syncthreads();
+    // Qtilde tile: BK columns x TBM rows (each column contiguous)
+#pragma unroll
+    for (int e = 0; e < (BK * TBM) / kThreads; ++e) {
+      const int idx = tid + e * kThreads;
+      const int k = idx / TBM, r = idx % TBM;
+      const int col = sc.Col[k];
+      const int row = r0 + r;
+      As[k * TBM + r] = (col >= 0 && row < rend) ? nd.src[row + (int64_t)col * nd.lds] : 0.0;
+    }
+    // Qhat tile generated from the generators
+#pragma unroll
+    for (int e = 0; e < (BK * TBN) / kThreads; ++e) {
+      const int idx = tid + e * kThreads;
+      const int k = idx / TBN, c = idx % TBN;
+      const double del = (sc.Dq[k] - sc.Do[c]) - sc.Tau[c];
+      Us[k * TBN + c] = (sc.Zq[k] * sc.S[c]) * rcp_nr(del);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      double av[TM], bv[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) av[i] = As[k * TBM + ty * TM + i];
+#pragma unroll
+      for (int c = 0; c < TN; ++c) bv[c] = Us[k * TBN + tx * TN + c];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int c = 0; c < TN; ++c) acc[i][c] = fma(av[i], bv[c], acc[i][c]);
+    }
+  }
+  // epilogue: write to the node's output columns
+#pragma unroll
+  for (int c = 0; c < TN; ++c) {
+    const int pos = sc.Pos[tx * TN + c];
+    if (pos < 0 || pos >= n) continue;
+    double* out = nd.dst + (int64_t)pos * nd.ldd;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int row = r0 + ty * TM + i;
+      if (row < rend) out[row] = acc[i][c];
+    }
+  }
+}
 }  // namespace
 
 __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, int64_t M) {
-  __shared__ double As[BK][BM];
-  __shared__ double Us[BK][BN];
-  __shared__ double sDo[BN], sTau[BN], sS[BN];
-  __shared__ int sPos[BN];
-  __shared__ int sCol[BK];
-  __shared__ double sDq[BK], sZq[BK];
-  const int tid = threadIdx.x;
-  const int tx = tid & 15;  // column group: 4 columns
-  const int ty = tid >> 4;  // row group: 8 rows
+  __shared__ double As[BK * BM];
+  __shared__ double Us[BK * BN];
+  __shared__ DenseCols sc;
   const int64_t total = P.m.tiles[M];
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
     // merge owning tile w
@@ -66,102 +176,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
       if (P.m.tiles[m] <= w) a = m; else b = m - 1;
     }
     const int64_t g = a;
-    const int64_t local = w - P.m.tiles[g];
     const Node nd = make_node(P, level, g);
-    const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
-    const int K = P.m.K[g];
-    const int ct = (K + BN - 1) / BN;
-    const int rtt = (int)(local / ct), ctile = (int)(local % ct);
-    const int rt0 = (n1 + BM - 1) / BM;
-    int r0, rend, nl;
-    const int* list;
-    if (rtt < rt0) { r0 = rtt * BM; rend = n1; list = P.v.tlist + nd.v0; nl = P.m.ntop[g]; }
-    else { r0 = n1 + (rtt - rt0) * BM; rend = n; list = P.v.blist + nd.v0; nl = P.m.nbot[g]; }
-    const int j0 = ctile * BN;
-    const double* Dk = P.v.Dk + nd.v0;
-    // structured merge: only the poles within one tile of the output columns here
-    int qlo = 0, qhi = nl;
-    const bool structured = P.struct_min_K > 0 && K >= P.struct_min_K;
-    if (structured) {
-      near_range(list, nl, j0, P.struct_m, K, qlo, qhi);
-      if (P.stats && tid == 0)
-        atomicAdd(&P.stats->struct_flops, 2ull * (unsigned long long)min(BM, rend - r0) *
-                                               (unsigned long long)(qhi - qlo) * (unsigned long long)min(BN, K - j0));
-    }
-    __syncthreads();
-    if (tid < BN) {
-      const int j = j0 + tid;
-      if (j < K) {
-        sDo[tid] = Dk[P.v.org[nd.v0 + j]];
-        sTau[tid] = P.v.tau[nd.v0 + j];
-        sS[tid] = P.v.scol[nd.v0 + j];
-        sPos[tid] = P.v.posr[nd.v0 + j];
-      } else {
-        sDo[tid] = 0.0; sTau[tid] = 1.0; sS[tid] = 0.0; sPos[tid] = -1;
-      }
-    }
-    double acc[8][4];
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-#pragma unroll
-      for (int c = 0; c < 4; ++c) acc[i][c] = 0.0;
-    for (int k0 = qlo; k0 < qhi; k0 += BK) {
-      __syncthreads();
-      if (tid < BK) {
-        const int k = k0 + tid;
-        if (k < qhi) {
-          const int q = list[k];
-          sCol[tid] = P.v.kept[nd.v0 + q];
-          sDq[tid] = Dk[q];
-          sZq[tid] = P.v.zhat[nd.v0 + q];
-        } else {
-          sCol[tid] = -1; sDq[tid] = 0.0; sZq[tid] = 0.0;
-        }
-      }
-      __syncthreads();
-      // Qtilde tile: BK columns x BM rows (each column contiguous)
-#pragma unroll
-      for (int e = 0; e < (BK * BM) / kThreads; ++e) {
-        const int idx = tid + e * kThreads;
-        const int k = idx / BM, r = idx % BM;
-        const int col = sCol[k];
-        const int row = r0 + r;
-        As[k][r] = (col >= 0 && row < rend) ? nd.src[row + (int64_t)col * nd.lds] : 0.0;
-      }
-      // Qhat tile generated from the generators
-#pragma unroll
-      for (int e = 0; e < (BK * BN) / kThreads; ++e) {
-        const int idx = tid + e * kThreads;
-        const int k = idx / BN, c = idx % BN;
-        const double del = (sDq[k] - sDo[c]) - sTau[c];
-        Us[k][c] = (sZq[k] * sS[c]) * rcp_nr(del);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int k = 0; k < BK; ++k) {
-        double av[8], bv[4];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) av[i] = As[k][ty * 8 + i];
-#pragma unroll
-        for (int c = 0; c < 4; ++c) bv[c] = Us[k][tx * 4 + c];
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-          for (int c = 0; c < 4; ++c) acc[i][c] = fma(av[i], bv[c], acc[i][c]);
-      }
-    }
-    // epilogue: write to the node's output columns
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int pos = sPos[tx * 4 + c];
-      if (pos < 0 || pos >= n) continue;
-      double* out = nd.dst + (int64_t)pos * nd.ldd;
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int row = r0 + ty * 8 + i;
-        if (row < rend) out[row] = acc[i][c];
-      }
-    }
+    int bm, bn;
+    dense_tile_dims(nd.hi - nd.lo, bm, bn);
+    if (bm == kDenseSmallBM)
+      dense_tile<kDenseSmallBM, kDenseSmallBN, true>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
+    else
+      dense_tile<BM, BN, false>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
   }
 }
 

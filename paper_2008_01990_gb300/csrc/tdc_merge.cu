@@ -1393,8 +1393,12 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
 // bracket; re-solved from the other pole if it converges in that pole's half);
 // without a usable estimate, the origin comes from the sign of g at the midpoint
 // and the last root starts from the root of g with the other poles frozen.
+// single: only the FP32 estimate and the certified pass; a root that needs more
+// (no usable estimate, no certificate, or a root in the other pole's half) comes
+// back with conv == false for the warp-per-root solver.
 __device__ void secular_root_thread(const double* D, const double* z, const float2* xz, int K, int j, double rho,
-                                    int max_iter, int& org_out, double& tau_out, int& iters, bool& conv) {
+                                    int max_iter, bool single, int& org_out, double& tau_out, int& iters,
+                                    bool& conv) {
   const double irho = 1.0 / rho;
   const bool last = j == K - 1;
   int org;
@@ -1408,7 +1412,26 @@ __device__ void secular_root_thread(const double* D, const double* z, const floa
   }
   float t32 = 0.0f;
   int passes = 1;
-  if (xz != nullptr && width > 0.0 && secular_fp32_thread(D, xz, K, j, (float)irho, (float)width, t32)) {
+  conv = false;
+  org_out = j;
+  tau_out = 0.0;
+  iters = 1;
+  const bool est = xz != nullptr && width > 0.0 && secular_fp32_thread(D, xz, K, j, (float)irho, (float)width, t32);
+  if (single) {
+    if (!est) return;
+    if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
+    else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
+    if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
+    if (!secular_certified_thread(D, z, K, j, irho, org, tau, lo, hi, conv)) return;
+    if (!last && ((org == j) ? (tau > 0.5 * width) : (tau < -0.5 * width))) {
+      conv = false;
+      return;
+    }
+    org_out = org;
+    tau_out = tau;
+    return;
+  }
+  if (est) {
     if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
     else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
@@ -1457,30 +1480,77 @@ static constexpr int kSmallK = 128;
 
 // Roots of the merges with 0 < K <= small_k, numbered merge by merge: roff[g] is
 // the first number of merge g, roff[M] the total (one block, two-level scan).
+// Two prefixes over the merges of a level: roff counts the roots of the merges
+// with K <= small_k (a thread each), boff the 8-root blocks of the others (a warp
+// per root), so that neither kind of kernel visits the other kind's merges.
 __global__ void __launch_bounds__(1024) k_root_scan(Plan P, int64_t M, int small_k) {
-  __shared__ int64_t part[1024];
+  __shared__ int64_t part[2][1024];
   const int64_t per = (M + blockDim.x - 1) / blockDim.x;
   const int64_t a = min(M, (int64_t)threadIdx.x * per), b = min(M, a + per);
-  int64_t s = 0;
+  int64_t s = 0, sb = 0;
   for (int64_t g = a; g < b; ++g) {
     const int K = P.m.K[g];
     s += (K > 0 && K <= small_k) ? K : 0;
+    sb += K > small_k ? (K + 7) / 8 : 0;
   }
-  part[threadIdx.x] = s;
+  part[0][threadIdx.x] = s;
+  part[1][threadIdx.x] = sb;
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 2) {
     int64_t run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) { const int64_t t = part[i]; part[i] = run; run += t; }
-    P.m.roff[M] = run;
-    P.m.roff[M + 1] = 0;  // roots passed on to k_secular_fixup
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      const int64_t t = part[threadIdx.x][i];
+      part[threadIdx.x][i] = run;
+      run += t;
+    }
+    if (threadIdx.x == 0) {
+      P.m.roff[M] = run;
+      P.m.roff[M + 1] = 0;  // roots passed on to k_secular_fixup
+    } else {
+      P.m.boff[M] = run;
+    }
   }
   __syncthreads();
-  int64_t run = part[threadIdx.x];
+  int64_t run = part[0][threadIdx.x], runb = part[1][threadIdx.x];
   for (int64_t g = a; g < b; ++g) {
     P.m.roff[g] = run;
+    P.m.boff[g] = runb;
     const int K = P.m.K[g];
     run += (K > 0 && K <= small_k) ? K : 0;
+    runb += K > small_k ? (K + 7) / 8 : 0;
   }
+}
+
+// The warp-per-root work of a level, as f(g, K, j) for every root j of the merges
+// with K > small_k, a warp each.  Merge-major (listed == false): block (g, y) holds
+// the roots 8y .. 8y+7 of merge g, and blocks past K or of small merges leave at
+// once.  Listed: a fixed grid walks the compacted block list of k_root_scan (on
+// levels with many merges, most of the merge-major blocks would be empty).
+template <typename F>
+__device__ __forceinline__ void for_warp_roots(const Plan& P, int64_t M, int small_k, bool listed, F&& f) {
+  const int wid = threadIdx.x >> 5;
+  if (!listed) {
+    const int64_t g = blockIdx.x;
+    const int K = P.m.K[g];
+    const int j = blockIdx.y * 8 + wid;
+    if (K > small_k && j < K) f(g, K, j);
+    return;
+  }
+  const int64_t total = P.m.boff[M];
+  for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
+    int64_t lo = 0, hi = M - 1;
+    while (lo < hi) {
+      const int64_t m = (lo + hi + 1) >> 1;
+      if (P.m.boff[m] <= w) lo = m; else hi = m - 1;
+    }
+    const int K = P.m.K[lo];
+    const int j = (int)(w - P.m.boff[lo]) * 8 + wid;
+    if (j < K) f(lo, K, j);
+  }
+}
+
+static dim3 warp_root_grid(const LevelLaunch& L, bool listed) {
+  return listed ? dim3(152 * 8) : dim3((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
 }
 
 // Thread t -> (merge g, root j) of the small merges: the last g with roff[g] <= t.
@@ -1496,11 +1566,11 @@ __device__ __forceinline__ bool small_root(const Plan& P, int64_t M, int64_t t, 
   return true;
 }
 
-// A thread per root, at most kSmallPasses FP64 passes: a warp waits for its slowest
-// lane, so the few roots that need more are listed (slot numbers, in the sort tag
-// scratch, free between deflation and the final ordering) and finished by a warp
-// each in k_secular_fixup.
-static constexpr int kSmallPasses = 6;
+// A thread per root, the FP32 estimate and one certified FP64 pass: a warp waits
+// for its slowest lane, so every root that needs more is listed (slot numbers, in
+// the sort tag scratch, free between deflation and the final ordering) and
+// finished by a warp each in k_secular_fixup.  With an iteration limit below two
+// passes the thread runs the whole iteration itself.
 
 __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_t M) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1510,13 +1580,13 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
   const Node nd = make_node(P, level, g);
   const int64_t v0 = nd.v0;
   const int K = P.m.K[g];
-  const bool capped = P.max_iter > kSmallPasses;
+  const bool single = P.max_iter >= 2;
   int org, it;
   double tau;
   bool conv;
-  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, 2.0 * fabs(nd.b),
-                      capped ? kSmallPasses : P.max_iter, org, tau, it, conv);
-  if (!conv && capped) {
+  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, 2.0 * fabs(nd.b), P.max_iter, single, org,
+                      tau, it, conv);
+  if (!conv && single) {
     const unsigned long long q = atomicAdd(reinterpret_cast<unsigned long long*>(P.m.roff + M + 1), 1ull);
     P.v.stag[q] = (int)(v0 + j);
     return;
@@ -1534,6 +1604,7 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
 // The listed roots, a warp each (the warp-per-root solver with its full budget).
 __global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int nprob_act, int64_t M) {
   const int64_t cnt = P.m.roff[M + 1];
+  if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.stats->handoffs, (unsigned long long)cnt);
   for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < cnt;
        w += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const Slot S = slot_of(P, level, nprob_act, P.v.stag[w]);
@@ -1555,43 +1626,40 @@ __global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int np
   }
 }
 
-// Warp per root, merge-major: block (g, y) holds the roots 8y .. 8y+7 of merge g
-// (no slot search; blocks past K or of small merges leave at once).
-__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int small_k) {
-  const int64_t g = blockIdx.x;
-  const int K = P.m.K[g];
-  const int jw = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (K <= small_k || jw >= K) return;
-  const Node nd = make_node(P, level, g);
-  const int64_t v0 = nd.v0;
-  const double rho = 2.0 * fabs(nd.b);
-  int org, it;
-  double tau;
-  bool conv;
-  // the merge's first warp takes its last root, usually the slowest to converge,
-  // so that it starts with the first wave of warps instead of ending the kernel
-  const int j = jw == 0 ? K - 1 : jw - 1;
-  secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, rho, P.max_iter, org, tau, it, conv);
-  if ((threadIdx.x & 31) == 0) {
-    P.v.org[v0 + j] = org;
-    P.v.tau[v0 + j] = tau;
-    if (!conv) set_status(P.status, TDC_ENOCONV);
-    if (P.stats) {
-      atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
-      atomicAdd(&P.stats->iter_roots, 1ull);
-      atomicMax(&P.stats->iter_max, it);
+// Warp per root over the merges with K > small_k (for_warp_roots).
+__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int64_t M, int small_k, bool listed) {
+  for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int jw) {
+    const Node nd = make_node(P, level, g);
+    const int64_t v0 = nd.v0;
+    const double rho = 2.0 * fabs(nd.b);
+    int org, it;
+    double tau;
+    bool conv;
+    // the merge's first warp takes its last root, usually the slowest to converge,
+    // so that it starts with the first wave of warps instead of ending the kernel
+    const int j = jw == 0 ? K - 1 : jw - 1;
+    secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, rho, P.max_iter, org, tau, it, conv);
+    if ((threadIdx.x & 31) == 0) {
+      P.v.org[v0 + j] = org;
+      P.v.tau[v0 + j] = tau;
+      if (!conv) set_status(P.status, TDC_ENOCONV);
+      if (P.stats) {
+        atomicAdd(&P.stats->iter_sum, (unsigned long long)it);
+        atomicAdd(&P.stats->iter_roots, 1ull);
+        atomicMax(&P.stats->iter_max, it);
+      }
     }
-  }
+  });
 }
 
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.nslots == 0) return cudaSuccess;
   const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
-  const dim3 wgrid((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
-  k_secular<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
+  const bool listed = small_k > 0;
+  if (listed) k_root_scan<<<1, 1024, 0, s>>>(P, L.merges, small_k);
+  k_secular<<<warp_root_grid(L, listed), 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || small_k == 0) return e;
-  k_root_scan<<<1, 1024, 0, s>>>(P, L.merges, small_k);
   k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.merges);
   k_secular_fixup<<<152 * 8, 256, 0, s>>>(P, L.level, L.nprob_act, L.merges);
   return cudaGetLastError();
@@ -1662,15 +1730,14 @@ __device__ double lowner_zhat(const double* D, const int* org, const double* tau
   return copysign(ldexp(sqrt(r), E / 2), zsign);
 }
 
-__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int small_k) {
-  const int64_t g = blockIdx.x;
-  const int K = P.m.K[g];
-  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (K <= small_k || j >= K) return;
-  const Node nd = make_node(P, level, g);
-  const int64_t v0 = nd.v0;
-  const double zh = lowner_zhat(P.v.Dk + v0, P.v.org + v0, P.v.tau + v0, K, j, 2.0 * fabs(nd.b), P.v.zk[v0 + j]);
-  if ((threadIdx.x & 31) == 0) P.v.zhat[v0 + j] = zh;
+__global__ void __launch_bounds__(256) k_lowner(Plan P, int level, int64_t M, int small_k, bool listed) {
+  for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int j) {
+    const Node nd = make_node(P, level, g);
+    const int64_t v0 = nd.v0;
+    const double zh =
+        lowner_zhat(P.v.Dk + v0, P.v.org + v0, P.v.tau + v0, K, j, 2.0 * fabs(nd.b), P.v.zk[v0 + j]);
+    if ((threadIdx.x & 31) == 0) P.v.zhat[v0 + j] = zh;
+  });
 }
 
 // Merges with K <= kSmallK: a thread per pole (k_colnorm_small: per column).
@@ -1708,15 +1775,13 @@ __global__ void __launch_bounds__(256) k_colnorm_small(Plan P, int level, int64_
   P.v.scol[v0 + j] = column_norm<1>(D, P.v.zhat + v0, P.m.K[g], D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
 }
 
-__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int small_k) {
-  const int64_t g = blockIdx.x;
-  const int K = P.m.K[g];
-  const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
-  if (K <= small_k || j >= K) return;
-  const int64_t v0 = make_node(P, level, g).v0;
-  const double* D = P.v.Dk + v0;
-  const double sj = column_norm(D, P.v.zhat + v0, K, D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
-  if ((threadIdx.x & 31) == 0) P.v.scol[v0 + j] = sj;
+__global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int64_t M, int small_k, bool listed) {
+  for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int j) {
+    const int64_t v0 = make_node(P, level, g).v0;
+    const double* D = P.v.Dk + v0;
+    const double sj = column_norm(D, P.v.zhat + v0, K, D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
+    if ((threadIdx.x & 31) == 0) P.v.scol[v0 + j] = sj;
+  });
 }
 
 // Stand-alone rank-one eigenproblem (tdc_rank_one): the three warp-per-entry stages.
@@ -1765,12 +1830,13 @@ cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.nslots == 0) return cudaSuccess;
   const unsigned tblocks = (unsigned)((L.nslots + 255) / 256);
   const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
-  const dim3 wgrid((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
-  k_lowner<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
+  const bool listed = small_k > 0;  // block list left by launch_secular's k_root_scan
+  const dim3 wgrid = warp_root_grid(L, listed);
+  k_lowner<<<wgrid, 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
   if (small_k) k_lowner_small<<<tblocks, 256, 0, s>>>(P, L.level, L.merges);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_colnorm<<<wgrid, 256, 0, s>>>(P, L.level, small_k);
+  k_colnorm<<<wgrid, 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
   if (small_k) k_colnorm_small<<<tblocks, 256, 0, s>>>(P, L.level, L.merges);
   return cudaGetLastError();
 }
@@ -1801,7 +1867,7 @@ __device__ __forceinline__ bool key_less(unsigned long long ka, int ta, unsigned
 // of kSortChunk entries run in shared memory, the wider ones in global memory.
 static constexpr int kSortChunk = 2048;
 
-__global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, int bn) {
+__global__ void __launch_bounds__(1024) k_finalize(Plan P, int level) {
   __shared__ unsigned long long sk[kSortChunk];
   __shared__ int stg[kSortChunk];
   const int64_t g = blockIdx.x;
@@ -1877,6 +1943,8 @@ __global__ void __launch_bounds__(1024) k_finalize(Plan P, int level, int bm, in
   }
   if (threadIdx.x == 0) {
     // GEMM tiles of this merge: (row tiles of top + bottom parts) x column tiles
+    int bm, bn;
+    dense_tile_dims(n, bm, bn);
     const int64_t rt = (n1 + bm - 1) / bm + (n - n1 + bm - 1) / bm;
     const int64_t ct = (K + bn - 1) / bn;
     const bool split = P.split_min_K > 0 && K >= P.split_min_K;
@@ -1903,10 +1971,10 @@ __global__ void k_tile_scan(Plan P, int64_t M) {
   if (threadIdx.x == 0) P.m.tiles[0] = 0;
 }
 
-cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, int bm, int bn, cudaStream_t s) {
+cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   int threads = 1024;
   while (threads > 64 && threads / 2 >= L.max_n) threads /= 2;
-  k_finalize<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level, bm, bn);
+  k_finalize<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_tile_scan<<<1, 1024, 0, s>>>(P, L.merges);

@@ -65,6 +65,7 @@ class Stats(ctypes.Structure):
         ("split_bytes", ctypes.c_double),
         ("struct_flops", ctypes.c_double),
         ("launches", ctypes.c_int64),
+        ("secular_handoffs", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -87,6 +88,7 @@ class Stats(ctypes.Structure):
             "split_bytes": self.split_bytes,
             "struct_flops": self.struct_flops,
             "launches": self.launches,
+            "secular_handoffs": self.secular_handoffs,
         }
 
 
