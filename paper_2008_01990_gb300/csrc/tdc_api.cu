@@ -56,6 +56,7 @@ struct HostPlan {
   int64_t Mmax = 1;
   std::vector<int64_t> max_tiles;   // GEMM tile upper bound per level
   int64_t img_elems = 0;            // digit images of the split path (bf16 elements)
+  int64_t max_passes = 0;           // most split passes of a level
   int split_S = 0;                  // 0: split path off
   std::vector<std::vector<std::pair<int64_t, int64_t>>> split_chunks;  // per level: merge ranges
   int struct_m = 0;                 // 0: structured path off
@@ -105,6 +106,7 @@ static constexpr int64_t kSplitImgCap = (int64_t)4 << 30;  // bf16 elements (8 G
 
 static void plan_split(HostPlan& H, const tdc_opts& o) {
   H.img_elems = 0;
+  H.max_passes = 0;
   H.split_S = split_enabled(o) ? o.split_slices : 0;
   H.split_chunks.assign(H.T, {});
   if (!H.split_S) return;
@@ -138,6 +140,7 @@ static void plan_split(HostPlan& H, const tdc_opts& o) {
       H.split_chunks[l].push_back({start, g});
       H.img_elems = std::max(H.img_elems, acc);
     }
+    H.max_passes = std::max(H.max_passes, (int64_t)H.split_chunks[l].size());
   }
 }
 
@@ -220,7 +223,7 @@ static Layout layout_of(const HostPlan& H) {
   L.vec_i = o; o = align_up(o + sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
   L.vec_b = o; o = align_up(o + kVecB * (size_t)std::max<int64_t>(1, H.N));
   L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
-  L.tiles = o; o = align_up(o + sizeof(int64_t) * (3 * (size_t)H.Mmax + 4));
+  L.tiles = o; o = align_up(o + sizeof(int64_t) * (4 * (size_t)H.Mmax + 5 + 2 * (size_t)H.max_passes + 2));
   L.stats = o; o = align_up(o + sizeof(Stats));
   L.segs = o; o = align_up(o + ((H.split_S || H.struct_m) ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
@@ -259,6 +262,9 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   P.m.tiles = (int64_t*)(base + L.tiles);
   P.m.roff = P.m.tiles + (H.Mmax + 1);
   P.m.boff = P.m.roff + (H.Mmax + 2);
+  P.m.ioff = P.m.boff + (H.Mmax + 1);
+  P.m.spass = P.m.ioff + (H.Mmax + 1);
+  P.m.sseg = P.m.spass + (2 * H.max_passes + 1);
   P.Q1 = (double*)(base + L.q1);
   P.prob = (const Problem*)(base + L.prob);
   P.segs = (H.split_S || H.struct_m) ? (GemmSeg*)(base + L.segs) : nullptr;
@@ -360,7 +366,8 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
     if (H.levels[l].nslots >= kSmallMinSlots) launches += 5;
-    if (H.split_S && H.levels[l].max_n >= o.split_min_K) launches += 4 * (int64_t)H.split_chunks[l].size();
+    if (H.split_S && H.levels[l].max_n >= o.split_min_K)
+      launches += 4 * (int64_t)H.split_chunks[l].size() + (H.split_chunks[l].size() > 1 ? 1 : 0);
     if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
       launches += 2 + 2 * ((H.levels[l].max_n + H.struct_m - 1) / H.struct_m);
   }
@@ -397,6 +404,10 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     span(4, a3, a4);
     size_t a6 = a4;
     if (err == cudaSuccess && P.split_min_K > 0 && LL.max_n >= P.split_min_K) {
+      // several passes on the host's bound: packed again on the device from the actual sizes
+      const int npass = (int)H.split_chunks[l].size();
+      if (npass > 1) err = launch_split_pack(P, LL, npass, s);
+      int pass = 0;
       for (auto& ch : H.split_chunks[l]) {
         cudaEvent_t mid = nullptr;
         if (timing) {
@@ -405,7 +416,8 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
         }
         const size_t b5 = timing ? evs.size() - 1 : 0;
         const size_t b4 = a6;
-        if (err == cudaSuccess) err = launch_gemm_split(P, LL, ch.first, ch.second, s, mid);
+        if (err == cudaSuccess) err = launch_gemm_split(P, LL, ch.first, ch.second, npass > 1 ? pass : -1, s, mid);
+        ++pass;
         a6 = mark();
         span(5, b4, b5);
         span(6, b5, a6);

@@ -72,6 +72,9 @@ struct MergeInfo {  // per merge of the current level
   int64_t* roff;    // prefix of the roots of small merges (thread-per-root kernels), M + 1 entries,
                     // then the count of roots handed to the warp-per-root fix-up
   int64_t* boff;    // prefix of the 8-root blocks of the other merges (warp per root), M + 1 entries
+  int64_t* ioff;    // split path, levels cut into passes: prefix of the merges' digit-image elements
+  int64_t* spass;   // split path: pass count, then the merge range [g0, g1) of each pass
+  int64_t* sseg;    // split path: segments of the pass being processed
 };
 
 struct Stats {  // device-side per-call statistics (index 0 = top level)
@@ -298,7 +301,8 @@ cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
                             double* tau, double* zhat, double* s, int* status, cudaStream_t st);
 cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s);
-cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, cudaStream_t s,
+cudaError_t launch_split_pack(const Plan& P, const LevelLaunch& L, int max_pass, cudaStream_t s);
+cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, int pass, cudaStream_t s,
                               cudaEvent_t mid);
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, cudaStream_t s);

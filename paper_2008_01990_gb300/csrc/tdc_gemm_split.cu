@@ -165,9 +165,17 @@ __device__ __forceinline__ void block_excl_scan4(int64_t (&v)[4], int64_t (&sc)[
   for (int q = 0; q < 4; ++q) v[q] = inc[q] - v[q] + (w > 0 ? sc[q][w - 1] : 0);
 }
 
-__global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t g0, int64_t g1) {
+// Merges [g0, g1), or (pass >= 0) the merge range of that pass from k_split_pack
+// (none past the pass count); the segment count goes to P.m.sseg in that case.
+__global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t g0, int64_t g1, int pass) {
   __shared__ int64_t sc[4][32];
   const int S = P.split_slices;
+  if (pass >= 0) {
+    const bool live = pass < P.m.spass[0];
+    g0 = live ? P.m.spass[1 + 2 * pass] : 0;
+    g1 = live ? P.m.spass[2 + 2 * pass] : 0;
+    if (threadIdx.x == 0) *P.m.sseg = 2 * (g1 - g0);
+  }
   const int64_t M = g1 - g0, items = 2 * M;
   const int64_t per = (items + blockDim.x - 1) / blockDim.x;
   const int64_t w0 = min(items, (int64_t)threadIdx.x * per), w1 = min(items, w0 + per);
@@ -236,10 +244,63 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
   }
 }
 
+// Levels the host cut into passes on a bound of every merge's digit images (its
+// order): after deflation the actual images are known, usually far smaller, so
+// the merges are packed again, greedily in order, into as few passes as fit the
+// image buffer.  Greedy packing of smaller items never needs more passes than
+// the host's packing of the bounds; passes beyond the count find no merges.
+__global__ void __launch_bounds__(1024) k_split_pack(Plan P, int level, int64_t M, int max_pass) {
+  __shared__ int64_t sc[4][32];
+  const int S = P.split_slices;
+  const int64_t per = (M + blockDim.x - 1) / blockDim.x;
+  const int64_t a = min(M, (int64_t)threadIdx.x * per), b = min(M, a + per);
+  int64_t cel = 0;
+  for (int64_t g = a; g < b; ++g)
+    for (int p = 0; p < 2; ++p) {
+      int64_t ta, tb, tt, el;
+      split_seg_counts(P, level, g, S, p, ta, tb, tt, el);
+      cel += el;
+    }
+  int64_t v[4] = {cel, 0, 0, 0};
+  block_excl_scan4(v, sc);
+  int64_t run = v[0];
+  for (int64_t g = a; g < b; ++g) {
+    P.m.ioff[g] = run;
+    for (int p = 0; p < 2; ++p) {
+      int64_t ta, tb, tt, el;
+      split_seg_counts(P, level, g, S, p, ta, tb, tt, el);
+      run += el;
+    }
+  }
+  if (threadIdx.x == blockDim.x - 1) P.m.ioff[M] = run;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const int64_t* io = P.m.ioff;
+  const int64_t cap = P.img_cap;
+  int64_t g = 0;
+  int c = 0;
+  while (g < M && c < max_pass) {
+    // last e in (g, M] with io[e] - io[g] <= cap (at least g + 1)
+    int64_t lo = g + 1, hi = M;
+    while (lo < hi) {
+      const int64_t m = (lo + hi + 1) >> 1;
+      if (io[m] - io[g] <= cap) lo = m; else hi = m - 1;
+    }
+    P.m.spass[1 + 2 * c] = g;
+    P.m.spass[2 + 2 * c] = lo;
+    ++c;
+    g = lo;
+  }
+  if (g < M) set_status(P.status, TDC_EUNSUPPORTED);  // cannot happen (see above)
+  P.m.spass[0] = c;
+}
+
 // ---------------------------------------------------------------------------
 // Digit images
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img) {
+__global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
+                                                 __nv_bfloat16* img) {
+  if (dnseg) nseg = (int)*dnseg;
   const int64_t total = segs[nseg].it_a;
   const int tid = threadIdx.x;
   for (int64_t w = blockIdx.x; w < total; w += gridDim.x) {
@@ -280,7 +341,9 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
 // Two B tiles per block iteration: threads 0-127 and 128-255 each take one
 // (64 columns x BK/8 groups of 8 poles).
 static_assert(BN * (BK / 8) == 128, "k_split_b maps 128 threads onto one B tile");
-__global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img) {
+__global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
+                                                 __nv_bfloat16* img) {
+  if (dnseg) nseg = (int)*dnseg;
   const int64_t total = segs[nseg].it_b;
   const int tid = threadIdx.x & 127;
   for (int64_t w = 2 * (int64_t)blockIdx.x + (threadIdx.x >> 7); w < total; w += 2 * (int64_t)gridDim.x) {
@@ -386,9 +449,10 @@ __device__ __forceinline__ TileRef tile_ref(const GemmSeg* segs, int nseg, int64
 }  // namespace
 
 template <int S>
-__global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* segs, int nseg,
+__global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* segs, int nseg, const int64_t* dnseg,
                                                                  const __nv_bfloat16* img, int* status,
                                                                  long long budget) {
+  if (dnseg) nseg = (int)*dnseg;
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t a_bytes = S * kATileElems * 2, b_bytes = S * kBTileElems * 2;
   constexpr uint32_t stage_bytes = a_bytes + b_bytes;
@@ -578,57 +642,66 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
   if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
-static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, int S, __nv_bfloat16* img, cudaStream_t s) {
-  k_split_a<<<152 * 8, 256, 0, s>>>(segs, nseg, S, img);
+static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
+                                       __nv_bfloat16* img, cudaStream_t s) {
+  k_split_a<<<152 * 8, 256, 0, s>>>(segs, nseg, dnseg, S, img);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_split_b<<<152 * 8, 256, 0, s>>>(segs, nseg, S, img);
+  k_split_b<<<152 * 8, 256, 0, s>>>(segs, nseg, dnseg, S, img);
   return cudaGetLastError();
 }
 
 template <int S>
-static cudaError_t launch_split_mma_s(const GemmSeg* segs, int nseg, int* status, long long budget,
-                                      const __nv_bfloat16* img, int sms, cudaStream_t s) {
+static cudaError_t launch_split_mma_s(const GemmSeg* segs, int nseg, const int64_t* dnseg, int* status,
+                                      long long budget, const __nv_bfloat16* img, int sms, cudaStream_t s) {
   const int smem = kStages * S * (kATileElems + kBTileElems) * 2 + 128;
   cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_gemm_split<S><<<sms, kSplitThreads, smem, s>>>(segs, nseg, img, status, budget);
+  k_gemm_split<S><<<sms, kSplitThreads, smem, s>>>(segs, nseg, dnseg, img, status, budget);
   return cudaGetLastError();
 }
 
-static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, int S, int* status, long long budget,
-                                    const __nv_bfloat16* img, cudaStream_t s) {
+static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S, int* status,
+                                    long long budget, const __nv_bfloat16* img, cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   switch (S) {
-    case 3: return launch_split_mma_s<3>(segs, nseg, status, budget, img, sms, s);
-    case 4: return launch_split_mma_s<4>(segs, nseg, status, budget, img, sms, s);
-    case 5: return launch_split_mma_s<5>(segs, nseg, status, budget, img, sms, s);
-    case 6: return launch_split_mma_s<6>(segs, nseg, status, budget, img, sms, s);
-    case 7: return launch_split_mma_s<7>(segs, nseg, status, budget, img, sms, s);
+    case 3: return launch_split_mma_s<3>(segs, nseg, dnseg, status, budget, img, sms, s);
+    case 4: return launch_split_mma_s<4>(segs, nseg, dnseg, status, budget, img, sms, s);
+    case 5: return launch_split_mma_s<5>(segs, nseg, dnseg, status, budget, img, sms, s);
+    case 6: return launch_split_mma_s<6>(segs, nseg, dnseg, status, budget, img, sms, s);
+    case 7: return launch_split_mma_s<7>(segs, nseg, dnseg, status, budget, img, sms, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, cudaStream_t s,
+cudaError_t launch_split_pack(const Plan& P, const LevelLaunch& L, int max_pass, cudaStream_t s) {
+  if (P.split_min_K <= 0 || P.segs == nullptr || L.merges == 0) return cudaSuccess;
+  k_split_pack<<<1, 1024, 0, s>>>(P, L.level, L.merges, max_pass);
+  return cudaGetLastError();
+}
+
+// Merges [g0, g1) of the level, or (pass >= 0) the device-packed pass of that number.
+cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, int pass, cudaStream_t s,
                               cudaEvent_t mid) {
   if (P.split_min_K <= 0 || P.segs == nullptr || g1 <= g0) return cudaSuccess;
-  k_split_segs<<<1, 1024, 0, s>>>(P, L.level, g0, g1);
+  k_split_segs<<<1, 1024, 0, s>>>(P, L.level, g0, g1, pass);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int nseg = (int)(2 * (g1 - g0));
-  e = launch_split_digits(P.segs, nseg, P.split_slices, P.img, s);
+  const int64_t* dn = pass >= 0 ? P.m.sseg : nullptr;
+  e = launch_split_digits(P.segs, nseg, dn, P.split_slices, P.img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
-  return launch_split_mma(P.segs, nseg, P.split_slices, P.status, P.spin_budget, P.img, s);
+  return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, s);
 }
 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, cudaStream_t s) {
-  cudaError_t e = launch_split_digits(segs_dev, nseg, S, img, s);
+  cudaError_t e = launch_split_digits(segs_dev, nseg, nullptr, S, img, s);
   if (e != cudaSuccess) return e;
-  return launch_split_mma(segs_dev, nseg, S, status, spin_budget, img, s);
+  return launch_split_mma(segs_dev, nseg, nullptr, S, status, spin_budget, img, s);
 }
 
 }  // namespace tdc

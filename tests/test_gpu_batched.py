@@ -113,3 +113,30 @@ def test_c3_full_batch_sampled(tdc, orc):
         res, orth = ratios(db, eb, lb, Qb)
         assert res <= 50 and orth <= 50
         compare_vectors(Qb, Qo, lo, 1e-8 * nT, 1e-7)
+
+
+@pytest.mark.parametrize("leaf,split_min_k", [(8, 16), (16, 32)])
+def test_batched_tiny_merges_on_split_path(tdc, orc, leaf, split_min_k):
+    """Merges down to K = 16 on the split path (a 128-row tile holding 8 or 16 rows)
+    and small leaves: sampled problems against the oracle, test ratios on all of them."""
+    sizes = inputs.batched_sizes(160, 64, 700, 53)
+    d, e, offs, qoffs = batch(sizes, 53)
+    o = tdc.default_opts(leaf=leaf)
+    o.split_min_K = split_min_k
+    lam = torch.empty(int(offs[-1]), dtype=torch.float64, device=DEV)
+    Q = torch.empty(int(qoffs[-1]), dtype=torch.float64, device=DEV)
+    tdc.eig_batched(sizes, torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), offs[:-1], qoffs[:-1],
+                    lam, Q, o, check=True)
+    lam_h, Q_h = lam.cpu().numpy(), Q.cpu().numpy()
+    for b in range(len(sizes)):
+        nb = int(sizes[b])
+        db, eb = d[offs[b]:offs[b] + nb], e[offs[b]:offs[b] + nb - 1]
+        lb = lam_h[offs[b]:offs[b] + nb]
+        Qb = Q_h[int(qoffs[b]):int(qoffs[b]) + nb * nb].reshape(nb, nb, order="F")
+        res, orth = ratios(db, eb, lb, Qb)
+        assert res <= 50 and orth <= 50, (b, res, orth)
+        if b % 40 == 0:
+            lo, Qo = orc.eig(db, eb, leaf=leaf)
+            nT = max(abs(lo[0]), abs(lo[-1]))
+            assert np.max(np.abs(lb - lo)) <= 1e-12 * nT
+            compare_vectors(Qb, Qo, lo, 1e-8 * nT, 1e-7)
