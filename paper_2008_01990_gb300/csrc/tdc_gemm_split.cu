@@ -571,8 +571,14 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
   } else {
     // epilogue: C = 2^-16 sum_m 2^-8m P_m with P_m the exact FP32 integer sums of
     // level m.  The first five levels combine exactly in a 64-bit integer
-    // 2^-48 ((((P0 2^8 + P1) 2^8 + P2) 2^8 + P3) 2^8 + P4), the last two in FP32
-    // as 2^-56 (P5 + 2^-8 P6) (rounding about 2^-59 absolute).
+    // hi = (((P0 2^8 + P1) 2^8 + P2) 2^8 + P3) 2^8 + P4, the last two in FP32 as
+    // lo = P5 + 2^-8 P6 (rounding near 2^-60 absolute), C = 2^-48 hi + 2^-56 lo.
+    // The FP64 pipe retires 2 operations per clock per SM, which shallow tiles feel:
+    // where |hi| < 2^52 (merge products: unit rows times unit columns give
+    // |hi| <= 2^48) C is formed as I = 2^10 hi + round(4 lo) (error <= 2^-59),
+    // one conversion to double, and the factor 2^-58 applied to the exponent
+    // field (I != 0 gives |I| >= 1, so the result stays normal); otherwise, e.g.
+    // for the adjoint's column-scaled products, in FP64 as written.
     int it = 0;
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++it) {
@@ -616,8 +622,20 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
             }
           }
         }
+        bool fits = true;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) val[c0 + i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+        for (int i = 0; i < 32; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
+        if (__all_sync(0xffffffffu, fits)) {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const long long I = hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]);
+            const long long b = __double_as_longlong(__ll2double_rn(I)) - (58ll << 52);
+            val[c0 + i] = I == 0 ? 0.0 : __longlong_as_double(b);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) val[c0 + i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+        }
       }
       umma::tc_fence_before();
       __syncwarp();
