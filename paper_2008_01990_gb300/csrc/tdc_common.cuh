@@ -41,7 +41,8 @@ struct Vecs {  // per-slot vectors of length N (sum of n); a merge owns [voff+lo
   double* tau;     // root offsets
   double* zhat;    // Loewner zhat
   double* scol;    // column normalisers
-  float2* xz;      // FP32 pole coordinate (d_i - d_centre) and z_i^2 (secular pre-iteration)
+  float2* xz;      // FP32 pole coordinate d_i - d_centre (high part) and z_i^2 (secular pre-iteration)
+  float* xlo;      // low part of that coordinate (xz.x + xlo = d_i - d_centre to about 2^-48)
   double* dval;    // deflated eigenvalues (scan order)
   double* rcs;     // rotations: (c, s) pairs, 2 per slot
   double* skey;    // sort scratch keys, 2 slots per vector slot

@@ -784,12 +784,15 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     if (s & 2) V.blist[v0 + ob++] = j;
   }
   // FP32 copies for the secular pre-iteration: coordinate relative to a centre pole
-  // and the squared weight
+  // (as an unevaluated sum of two floats, xz.x + xlo) and the squared weight
   if (Kf > 0) {
     const double dc = V.Dk[v0 + (Kf >> 1)];
     for (int j = threadIdx.x; j < Kf; j += blockDim.x) {
       const double zj = V.zk[v0 + j];
-      V.xz[v0 + j] = make_float2((float)(V.Dk[v0 + j] - dc), (float)(zj * zj));
+      const double x = V.Dk[v0 + j] - dc;
+      const float xh = (float)x;
+      V.xz[v0 + j] = make_float2(xh, (float)(zj * zj));
+      V.xlo[v0 + j] = (float)(x - (double)xh);
     }
   }
   if (threadIdx.x == blockDim.x - 1) {
@@ -1238,21 +1241,20 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
   iters = min(passes, max_iter);
 }
 
-// FP32 pre-iteration of one thread for root j of a small merge, in the frame of
-// pole j: tau in (0, width).  The six poles j-2 .. j+3 use their FP64 differences,
-// the others the merge's FP32 coordinates; the model steps are those of the warp
-// version (two-pole for interior roots from the midpoint; one-pole for the last
-// root from its frozen-poles start).  Returns false if no usable estimate.
-__device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, int j, float irho, float width,
-                                    float& tau_out) {
+// FP32 pre-iteration of one thread for root j of a small merge.  Pole differences
+// come from the two-float coordinates, (x_i - x_o) + (xlo_i - xlo_o), accurate to
+// a few FP32 roundings of d_i - d_o itself however far the poles lie from the
+// merge's centre.  The first evaluation, at the middle of (d_j, d_j+1), picks the
+// frame: tau is kept relative to the nearer pole o (j, or j+1 with tau < 0), so a
+// root close to d_j+1 keeps its relative precision instead of rounding onto
+// width.  The model steps are those of the warp version (two-pole for interior
+// roots from the midpoint; one-pole for the last root from its frozen-poles
+// start).  Returns false if no usable estimate; otherwise org_out and tau_out.
+__device__ bool secular_fp32_thread(const float2* xz, const float* xlo, int K, int j, float irho, float width,
+                                    int& org_out, float& tau_out) {
   const bool last = j == K - 1;
-  float w6[6];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const int i = j - 2 + q;
-    w6[q] = (i >= 0 && i < K) ? (float)(D[i] - D[j]) : 0.0f;
-  }
-  const float xj = xz[j].x;
+  int o = j;
+  float xo = xz[j].x, xlo_o = xlo[j];
   float lo = 0.0f, hi = width, tau = 0.5f * width;
   for (int it = 0; it < 12; ++it) {
     const float tv = (last && it == 0) ? 0.0f : tau;
@@ -1261,11 +1263,7 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
     // no divergent branch inside the loop
     auto term = [&](int i, float& acc, float& dacc) {
       const float2 v = xz[i];
-      float del = v.x - xj;
-      const int q = i - (j - 2);
-#pragma unroll
-      for (int u = 0; u < 6; ++u)
-        if (q == u) del = w6[u];
+      const float del = (v.x - xo) + (xlo[i] - xlo_o);
       float r;
       asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tv));
       const float t = v.y * r;
@@ -1284,8 +1282,18 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
     const float gv = irho + a + b;
     if (!isfinite(gv)) return false;
     if (gv == 0.0f) break;
+    if (it == 0 && !last && gv < 0.0f) {
+      // root in the upper half: continue in the frame of pole j+1 (same point)
+      o = j + 1;
+      xo = xz[j + 1].x;
+      xlo_o = xlo[j + 1];
+      tau = -0.5f * width;
+      lo = -width;
+      hi = 0.0f;
+    }
     if (gv < 0.0f) lo = tau; else hi = tau;
-    const float p = -tau;
+    // p = d_j - lambda, q2 = d_j+1 - lambda in the current frame
+    const float p = o == j ? -tau : -(width + tau);
     float h = 0.0f;
     bool ok = true;
     if (last) {
@@ -1293,7 +1301,7 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
       const float A = irho + (a - b1 / p) + b;
       if (A != 0.0f) h = p + b1 / A; else ok = false;
     } else {
-      const float q2 = width - tau;
+      const float q2 = o == j ? width - tau : -tau;
       const float b1 = da * p * p, b2 = db * q2 * q2;
       const float A = irho + (a - b1 / p) + (b - b2 / q2);
       const float B = A * (p + q2) + b1 + b2;
@@ -1319,9 +1327,10 @@ __device__ bool secular_fp32_thread(const double* D, const float2* xz, int K, in
     if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5f * (lo + hi);
     const bool small = fabsf(tn - tau) <= 2e-7f * fabsf(tau);
     tau = tn;
-    if (small || (hi - lo) <= 4e-7f * hi) break;
+    if (small || (hi - lo) <= 4e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
   }
-  if (!(tau > 0.0f && tau < width)) return false;
+  if (o == j ? !(tau > 0.0f && tau < width) : !(tau > -width && tau < 0.0f)) return false;
+  org_out = o;
   tau_out = tau;
   return true;
 }
@@ -1350,6 +1359,10 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
   double dmin = HUGE_VAL;
   if (wlo - 1 >= 0) dmin = fmin(dmin, fabs((D[wlo - 1] - dorg) - tau1));
   if (whi + 1 < K) dmin = fmin(dmin, fabs((D[whi + 1] - dorg) - tau1));
+  // rounding bound of the two recursive far sums (terms of one sign each: at most
+  // one unit roundoff of the sum per addition), added to the acceptance threshold
+  // so that a root whose |g| is below what this pass can resolve is not rejected
+  const double sum_err = kEps * ((double)wlo * fabs(a0) + (double)(K - 1 - whi) * fabs(b0));
   conv = false;
   double tc = tau1;
   for (int k = 0; k < 8; ++k) {
@@ -1367,12 +1380,12 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
     const double psi = a0 + e * (a1 + e * a2) + wl, dpsi = a1 + 2.0 * e * a2 + wdl;
     const double phi = b0 + e * (b1 + e * b2) + wr, dphi = b1 + 2.0 * e * b2 + wdr;
     const double gv = irho + psi + phi;
-    if (gv == 0.0 || fabs(gv) + rest <= 8.0 * kEps * (irho + (phi - psi))) {
+    if (gv == 0.0 || fabs(gv) + rest <= 8.0 * kEps * (irho + (phi - psi)) + sum_err) {
       tau = tc;
       conv = true;
       return true;
     }
-    if (fabs(gv) > rest) {
+    if (fabs(gv) > rest + sum_err) {
       if (gv < 0.0) lo = tc; else hi = tc;
     }
     const double tn = model_step(j, K, irho, dl, dr, tc, gv, psi, dpsi, phi, dphi, lo, hi);
@@ -1396,9 +1409,9 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
 // single: only the FP32 estimate and the certified pass; a root that needs more
 // (no usable estimate, no certificate, or a root in the other pole's half) comes
 // back with conv == false for the warp-per-root solver.
-__device__ void secular_root_thread(const double* D, const double* z, const float2* xz, int K, int j, double rho,
-                                    int max_iter, bool single, int& org_out, double& tau_out, int& iters,
-                                    bool& conv) {
+__device__ void secular_root_thread(const double* D, const double* z, const float2* xz, const float* xlo, int K,
+                                    int j, double rho, int max_iter, bool single, int& org_out, double& tau_out,
+                                    int& iters, bool& conv) {
   const double irho = 1.0 / rho;
   const bool last = j == K - 1;
   int org;
@@ -1411,16 +1424,19 @@ __device__ void secular_root_thread(const double* D, const double* z, const floa
     width = rho * zz;
   }
   float t32 = 0.0f;
+  int o32 = j;
   int passes = 1;
   conv = false;
   org_out = j;
   tau_out = 0.0;
   iters = 1;
-  const bool est = xz != nullptr && width > 0.0 && secular_fp32_thread(D, xz, K, j, (float)irho, (float)width, t32);
+  const bool est =
+      xz != nullptr && width > 0.0 && secular_fp32_thread(xz, xlo, K, j, (float)irho, (float)width, o32, t32);
   if (single) {
     if (!est) return;
-    if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
-    else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
+    org = o32;
+    tau = (double)t32;
+    if (org == j) { lo = 0.0; hi = width; } else { lo = -width; hi = 0.0; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
     if (!secular_certified_thread(D, z, K, j, irho, org, tau, lo, hi, conv)) return;
     if (!last && ((org == j) ? (tau > 0.5 * width) : (tau < -0.5 * width))) {
@@ -1432,8 +1448,9 @@ __device__ void secular_root_thread(const double* D, const double* z, const floa
     return;
   }
   if (est) {
-    if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
-    else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
+    org = o32;
+    tau = (double)t32;
+    if (org == j) { lo = 0.0; hi = width; } else { lo = -width; hi = 0.0; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
     const bool tried = max_iter >= 2;
     if (!tried || !secular_certified_thread(D, z, K, j, irho, org, tau, lo, hi, conv)) {
@@ -1584,7 +1601,7 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
   int org, it;
   double tau;
   bool conv;
-  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, 2.0 * fabs(nd.b), P.max_iter, single, org,
+  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, P.v.xlo + v0, K, j, 2.0 * fabs(nd.b), P.max_iter, single, org,
                       tau, it, conv);
   if (!conv && single) {
     const unsigned long long q = atomicAdd(reinterpret_cast<unsigned long long*>(P.m.roff + M + 1), 1ull);
