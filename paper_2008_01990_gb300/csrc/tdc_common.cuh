@@ -231,17 +231,16 @@ __device__ __forceinline__ int64_t node_of_row(int64_t r, int64_t n, int level) 
 // ---------------------------------------------------------------------------
 // Arithmetic helpers
 // ---------------------------------------------------------------------------
-// Reciprocal of x: hardware estimate (rcp.approx.ftz.f64) followed by two
-// Newton-Raphson refinements r <- r + r (1 - x r), each of which squares the
-// relative error.  Result within a few ulps of 1/x for normal, finite x.
+// Reciprocal of x: hardware estimate r (rcp.approx.ftz.f64, relative error e of
+// about 2^-20) followed by one third-order refinement r <- r + r (e + e^2) with
+// e = 1 - x r, which leaves a relative error e^3 (about 2^-60) before the final
+// rounding: within an ulp of 1/x for normal, finite x, in three FP64 operations
+// instead of the four of two Newton-Raphson steps.
 __device__ __forceinline__ double rcp_nr(double x) {
   double r;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
-  double e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-x, r, 1.0);
-  r = fma(r, e, r);
-  return r;
+  const double e = fma(-x, r, 1.0);
+  return fma(r, fma(e, e, e), r);
 }
 
 // 1/sqrt(x): hardware estimate (rsqrt.approx.ftz.f64) followed by two Newton-Raphson

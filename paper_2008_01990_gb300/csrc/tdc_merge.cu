@@ -1091,22 +1091,26 @@ __device__ bool secular_certified(const double* D, const double* z, int K, int j
   return false;
 }
 
-// FP32 pre-iteration for root j in the frame of pole j: tau in (0, width) with
-// width = d_{j+1} - d_j, or for the last root width = rho |z|^2.  Far poles use
-// FP32 coordinates xz[i].x = d_i - d_c (one centre per merge) and xz[i].y = z_i^2;
-// the 32 poles nearest to j (one per lane) use their FP64 differences, so close
-// neighbours keep their relative accuracy.  Interior roots start at the midpoint
-// with the two-pole model; the last root starts from the root of g with every
-// other pole frozen at tau = 0 (it often lies far below the interval's middle)
-// and iterates the one-pole model.  Returns false if no usable estimate was found.
-__device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, float irho, float width,
-                             float& tau_out) {
+// FP32 pre-iteration for root j: width = d_{j+1} - d_j, or for the last root
+// width = rho |z|^2.  Far poles use the two-float coordinates (xz[i].x + xlo[i] =
+// d_i - d_c, one centre per merge) and xz[i].y = z_i^2; the 32 poles nearest to j
+// (one per lane) use their FP64 differences.  The first evaluation, at the middle
+// of the interval, picks the frame: tau is kept relative to the nearer pole o (j,
+// or j+1 with tau < 0), so a root close to d_j+1 keeps its relative precision.
+// Interior roots start at the midpoint with the two-pole model; the last root
+// starts from the root of g with every other pole frozen at tau = 0 (it often
+// lies far below the interval's middle) and iterates the one-pole model.
+// Returns false if no usable estimate; otherwise org_out and tau_out.
+__device__ bool secular_fp32(const double* D, const float2* xz, const float* xlo, int K, int j, float irho,
+                             float width, int& org_out, float& tau_out) {
   const int lane = threadIdx.x & 31;
   const bool last = j == K - 1;
   // the window pole of this lane: the i = lane (mod 32) in [j - 15, j + 16]
   const int iw = j - 15 + ((lane - (j - 15)) & 31);
-  const float dw = (iw >= 0 && iw < K) ? (float)(D[iw] - D[j]) : 0.0f;
-  const float xj = xz[j].x;
+  const bool wv = iw >= 0 && iw < K;
+  float dw = wv ? (float)(D[iw] - D[j]) : 0.0f;
+  int o = j;
+  float xo = xz[j].x, xlo_o = xlo[j];
   float lo = 0.0f, hi = width, tau = 0.5f * width;
   for (int it = 0; it < 12; ++it) {
     // it == 0 for the last root: the sum of the other poles' terms at tau = 0
@@ -1114,7 +1118,7 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
     float a = 0.0f, da = 0.0f, b = 0.0f, db = 0.0f;
     for (int i = lane; i < K; i += 32) {
       const float2 v = xz[i];
-      const float del = (i == iw) ? dw : v.x - xj;
+      const float del = (i == iw) ? dw : (v.x - xo) + (xlo[i] - xlo_o);
       if (last && it == 0 && i == j) continue;
       float r;
       asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(del - tv));
@@ -1123,11 +1127,11 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
       else { b += t; db = fmaf(t, r, db); }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      da += __shfl_xor_sync(0xffffffffu, da, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-      db += __shfl_xor_sync(0xffffffffu, db, o);
+    for (int s = 16; s > 0; s >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, s);
+      da += __shfl_xor_sync(0xffffffffu, da, s);
+      b += __shfl_xor_sync(0xffffffffu, b, s);
+      db += __shfl_xor_sync(0xffffffffu, db, s);
     }
     if (last && it == 0) {
       const float den = irho + a;
@@ -1138,8 +1142,19 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
     const float gv = irho + a + b;
     if (!isfinite(gv)) return false;
     if (gv == 0.0f) break;
+    if (it == 0 && !last && gv < 0.0f) {
+      // root in the upper half: continue in the frame of pole j+1 (same point)
+      o = j + 1;
+      xo = xz[j + 1].x;
+      xlo_o = xlo[j + 1];
+      dw = wv ? (float)(D[iw] - D[j + 1]) : 0.0f;
+      tau = -0.5f * width;
+      lo = -width;
+      hi = 0.0f;
+    }
     if (gv < 0.0f) lo = tau; else hi = tau;
-    const float p = -tau;
+    // p = d_j - lambda, q = d_j+1 - lambda in the current frame
+    const float p = o == j ? -tau : -(width + tau);
     float h = 0.0f;
     bool ok = true;
     if (last) {
@@ -1147,7 +1162,7 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
       const float A = irho + (a - b1 / p) + b;
       if (A != 0.0f) h = p + b1 / A; else ok = false;
     } else {
-      const float q = width - tau;
+      const float q = o == j ? width - tau : -tau;
       const float b1 = da * p * p, b2 = db * q * q;
       const float A = irho + (a - b1 / p) + (b - b2 / q);
       const float B = A * (p + q) + b1 + b2;
@@ -1173,9 +1188,10 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
     if (!ok || !(tn > lo && tn < hi) || !isfinite(tn)) tn = 0.5f * (lo + hi);
     const bool small = fabsf(tn - tau) <= 2e-7f * fabsf(tau);
     tau = tn;
-    if (small || (hi - lo) <= 4e-7f * hi) break;
+    if (small || (hi - lo) <= 4e-7f * fmaxf(fabsf(lo), fabsf(hi))) break;
   }
-  if (!(tau > 0.0f && tau < width)) return false;
+  if (o == j ? !(tau > 0.0f && tau < width) : !(tau > -width && tau < 0.0f)) return false;
+  org_out = o;
   tau_out = tau;
   return true;
 }
@@ -1186,8 +1202,8 @@ __device__ bool secular_fp32(const double* D, const float2* xz, int K, int j, fl
 // starts there, with the whole interval as bracket.  A root that converges in
 // the half of the far pole is re-solved from that pole.  Without xz, or when the
 // FP32 estimate is unusable, the origin comes from the sign of g at the midpoint.
-__device__ void secular_root(const double* D, const double* z, const float2* xz, int K, int j, double rho,
-                             int max_iter, int& org_out, double& tau_out, int& iters, bool& conv) {
+__device__ void secular_root(const double* D, const double* z, const float2* xz, const float* xlo, int K, int j,
+                             double rho, int max_iter, int& org_out, double& tau_out, int& iters, bool& conv) {
   const double irho = 1.0 / rho;
   int org;
   double lo, hi, tau;
@@ -1203,9 +1219,11 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
     width = rho * warp_sum(zz);
   }
   float t32 = 0.0f;
-  if (xz != nullptr && width > 0.0 && secular_fp32(D, xz, K, j, (float)irho, (float)width, t32)) {
-    if (last || t32 <= 0.5f * (float)width) { org = j; lo = 0.0; hi = width; tau = (double)t32; }
-    else { org = j + 1; lo = -width; hi = 0.0; tau = (double)t32 - width; }
+  int o32 = j;
+  if (xz != nullptr && width > 0.0 && secular_fp32(D, xz, xlo, K, j, (float)irho, (float)width, o32, t32)) {
+    org = o32;
+    tau = (double)t32;
+    if (org == j) { lo = 0.0; hi = width; } else { lo = -width; hi = 0.0; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
     const bool tried = max_iter >= 2;
     if (!tried || !secular_certified(D, z, K, j, irho, org, tau, lo, hi, conv)) {
@@ -1629,7 +1647,8 @@ __global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int np
     int org, it;
     double tau;
     bool conv;
-    secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, S.K, S.j, S.rho, P.max_iter, org, tau, it, conv);
+    secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, P.v.xlo + S.v0, S.K, S.j, S.rho, P.max_iter, org,
+                 tau, it, conv);
     if ((threadIdx.x & 31) == 0) {
       P.v.org[S.v0 + S.j] = org;
       P.v.tau[S.v0 + S.j] = tau;
@@ -1655,7 +1674,7 @@ __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int64_t M, i
     // the merge's first warp takes its last root, usually the slowest to converge,
     // so that it starts with the first wave of warps instead of ending the kernel
     const int j = jw == 0 ? K - 1 : jw - 1;
-    secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, K, j, rho, P.max_iter, org, tau, it, conv);
+    secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, P.v.xlo + v0, K, j, rho, P.max_iter, org, tau, it, conv);
     if ((threadIdx.x & 31) == 0) {
       P.v.org[v0 + j] = org;
       P.v.tau[v0 + j] = tau;
@@ -1809,7 +1828,7 @@ __global__ void __launch_bounds__(256) k_r1_secular(const double* D, const doubl
   int o, it;
   double t;
   bool conv;
-  secular_root(D, z, nullptr, K, (int)j, rho, max_iter, o, t, it, conv);
+  secular_root(D, z, nullptr, nullptr, K, (int)j, rho, max_iter, o, t, it, conv);
   if ((threadIdx.x & 31) == 0) {
     org[j] = o;
     tau[j] = t;
