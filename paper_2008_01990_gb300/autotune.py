@@ -18,7 +18,7 @@ import torch
 from . import tdc
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "tdc_autotune.json")
-LEAVES = (16, 32, 48, 64)
+LEAVES = (8, 16, 32, 48, 64)
 SPLIT_MIN_K = (64, 128, 256, 512)
 
 

@@ -319,11 +319,14 @@ cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q,
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
-// merges of order n <= kDenseSmallN take 32 x 32 tiles: their halves are at most 64 rows,
-// so a 128-row tile would leave most of its FP64 multiply-adds on padding
+// merges of order n <= kDenseSmallN take 32 x 32 tiles, of order n <= kDenseTinyN
+// 16 x 16: their halves have at most 64 (8) rows, so a 128-row tile would leave
+// most of its FP64 multiply-adds on padding (16 x 16 tiles, one output per thread,
+// were measured slower than 32 x 32 ones for merges of order 32)
 constexpr int kDenseSmallN = 128, kDenseSmallBM = 32, kDenseSmallBN = 32;
+constexpr int kDenseTinyN = 16, kDenseTinyBM = 16, kDenseTinyBN = 16;
 __host__ __device__ inline void dense_tile_dims(int64_t n, int& bm, int& bn) {
-  bm = n <= kDenseSmallN ? kDenseSmallBM : kDenseBM;
-  bn = n <= kDenseSmallN ? kDenseSmallBN : kDenseBN;
+  bm = n <= kDenseTinyN ? kDenseTinyBM : (n <= kDenseSmallN ? kDenseSmallBM : kDenseBM);
+  bn = n <= kDenseTinyN ? kDenseTinyBN : (n <= kDenseSmallN ? kDenseSmallBN : kDenseBN);
 }
 }  // namespace tdc

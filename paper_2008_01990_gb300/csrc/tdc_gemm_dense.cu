@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
     const Node nd = make_node(P, level, g);
     int bm, bn;
     dense_tile_dims(nd.hi - nd.lo, bm, bn);
-    if (bm == kDenseSmallBM)
+    if (bm == kDenseTinyBM)
+      dense_tile<kDenseTinyBM, kDenseTinyBN, true>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
+    else if (bm == kDenseSmallBM)
       dense_tile<kDenseSmallBM, kDenseSmallBN, true>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
     else
       dense_tile<BM, BN, false>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
