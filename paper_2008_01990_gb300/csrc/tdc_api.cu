@@ -184,13 +184,14 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
     LevelLaunch& L = H.levels[l];
     L.level = l;
     int32_t c = 0;
-    int64_t slots = 0, mx = 0, tiles = 0;
+    int64_t slots = 0, mx = 0, mn = INT64_MAX, tiles = 0;
     for (auto& p : v) {
       if (p.depth <= l) break;
       ++c;
       slots += p.n;
       const int64_t nm = (p.n + (((int64_t)1) << l) - 1) >> l;
       mx = std::max(mx, nm);
+      mn = std::min(mn, p.n >> l);
       const int64_t n1 = (nm + 1) / 2;
       int bm, bn;
       dense_tile_dims(nm, bm, bn);
@@ -201,6 +202,7 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
     L.merges = ((int64_t)c) << l;
     L.nslots = slots;
     L.max_n = mx;
+    L.min_n = c > 0 ? mn : 0;
     H.max_tiles[l] = tiles;
     H.Mmax = std::max(H.Mmax, L.merges);
   }
@@ -367,6 +369,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
     if (H.levels[l].nslots >= kSmallMinSlots) launches += 5;
+    if (H.levels[l].merges > 0 && H.levels[l].min_n <= kTinyN) launches += 1;
     if (H.split_S && H.levels[l].max_n >= o.split_min_K)
       launches += 4 * (int64_t)H.split_chunks[l].size() + (H.split_chunks[l].size() > 1 ? 1 : 0);
     if (H.struct_m && H.levels[l].max_n >= o.structured_min_K)
@@ -388,6 +391,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     if (err == cudaSuccess) err = launch_finalize(P, LL, s);
     const size_t a3 = mark();
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
+    if (err == cudaSuccess) err = launch_gemm_tiny(P, LL, s);
     if (err == cudaSuccess && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
       int64_t Tmax, ldw;
       level_struct_dims(LL, H.struct_m, Tmax, ldw);

@@ -286,6 +286,7 @@ struct LevelLaunch {
   int32_t nprob_act;  // problems taking part (prefix)
   int64_t nslots;     // vector slots of the active problems
   int64_t max_n;      // largest merge order on the level
+  int64_t min_n;      // smallest merge order on the level
 };
 cudaError_t launch_dmod(const Plan& P, cudaStream_t s);
 cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStream_t s);
@@ -301,6 +302,7 @@ cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
                             double* tau, double* zhat, double* s, int* status, cudaStream_t st);
 cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s);
+cudaError_t launch_gemm_tiny(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_split_pack(const Plan& P, const LevelLaunch& L, int max_pass, cudaStream_t s);
 cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, int pass, cudaStream_t s,
                               cudaEvent_t mid);
@@ -319,14 +321,19 @@ cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q,
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
-// merges of order n <= kDenseSmallN take 32 x 32 tiles, of order n <= kDenseTinyN
-// 16 x 16: their halves have at most 64 (8) rows, so a 128-row tile would leave
-// most of its FP64 multiply-adds on padding (16 x 16 tiles, one output per thread,
-// were measured slower than 32 x 32 ones for merges of order 32)
+// merges of order n <= kDenseSmallN take 32 x 32 tiles: their halves have at most 64
+// rows, so a 128-row tile would leave most of its FP64 multiply-adds on padding
 constexpr int kDenseSmallN = 128, kDenseSmallBM = 32, kDenseSmallBN = 32;
-constexpr int kDenseTinyN = 16, kDenseTinyBM = 16, kDenseTinyBN = 16;
 __host__ __device__ inline void dense_tile_dims(int64_t n, int& bm, int& bn) {
-  bm = n <= kDenseTinyN ? kDenseTinyBM : (n <= kDenseSmallN ? kDenseSmallBM : kDenseBM);
-  bn = n <= kDenseTinyN ? kDenseTinyBN : (n <= kDenseSmallN ? kDenseSmallBN : kDenseBN);
+  bm = n <= kDenseSmallN ? kDenseSmallBM : kDenseBM;
+  bn = n <= kDenseSmallN ? kDenseSmallBN : kDenseBN;
+}
+// merges of order n <= kTinyN (halves of at most 16 rows and poles, K <= 32) off the
+// split and structured paths take a warp each (k_gemm_tiny) instead of tiles
+constexpr int kTinyN = 32;
+__host__ __device__ inline bool tiny_merge(int64_t n, int K, int ntop, int nbot, int split_min_K,
+                                           int struct_min_K) {
+  return n <= kTinyN && K > 0 && ntop <= kTinyN / 2 && nbot <= kTinyN / 2 &&
+         !(split_min_K > 0 && K >= split_min_K) && !(struct_min_K > 0 && K >= struct_min_K);
 }
 }  // namespace tdc

@@ -179,12 +179,71 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense(Plan P, int level, i
     const Node nd = make_node(P, level, g);
     int bm, bn;
     dense_tile_dims(nd.hi - nd.lo, bm, bn);
-    if (bm == kDenseTinyBM)
-      dense_tile<kDenseTinyBM, kDenseTinyBN, true>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
-    else if (bm == kDenseSmallBM)
+    if (bm == kDenseSmallBM)
       dense_tile<kDenseSmallBM, kDenseSmallBN, true>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
     else
       dense_tile<BM, BN, false>(P, nd, g, w - P.m.tiles[g], As, Us, sc);
+  }
+}
+
+// Merges of order <= kTinyN: a warp per merge, lane c computing output column c
+// (K <= 32) for every row of a half, its Qhat entries generated in registers and
+// the half's Qtilde block (at most 16 x 16) staged in shared memory.  Same
+// products in the same order as the tiled kernel; no tile search, no block
+// barriers.
+constexpr int kTinyWarps = 4, kTinyRows = kTinyN / 2;
+__global__ void __launch_bounds__(32 * kTinyWarps) k_gemm_tiny(Plan P, int level, int64_t M) {
+  __shared__ double sA[kTinyWarps][kTinyRows * kTinyRows];
+  __shared__ double sDq[kTinyWarps][kTinyRows], sZq[kTinyWarps][kTinyRows];
+  __shared__ int sCol[kTinyWarps][kTinyRows];
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t g = (int64_t)blockIdx.x * kTinyWarps + wid;
+  if (g >= M) return;
+  const int K = P.m.K[g];
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  if (!tiny_merge(n, K, P.m.ntop[g], P.m.nbot[g], P.split_min_K, P.struct_min_K)) return;
+  const double* Dk = P.v.Dk + nd.v0;
+  double Do = 0.0, Tau = 1.0, S = 0.0;
+  int pos = -1;
+  if (lane < K) {
+    Do = Dk[P.v.org[nd.v0 + lane]];
+    Tau = P.v.tau[nd.v0 + lane];
+    S = P.v.scol[nd.v0 + lane];
+    pos = P.v.posr[nd.v0 + lane];
+  }
+  double* A = sA[wid];
+  for (int h = 0; h < 2; ++h) {
+    const int r0 = h ? n1 : 0, rows = h ? n - n1 : n1;
+    const int* list = (h ? P.v.blist : P.v.tlist) + nd.v0;
+    const int nl = h ? P.m.nbot[g] : P.m.ntop[g];  // poles with support in this half (<= rows)
+    __syncwarp();
+    if (lane < nl) {
+      const int q = list[lane];
+      sCol[wid][lane] = P.v.kept[nd.v0 + q];
+      sDq[wid][lane] = Dk[q];
+      sZq[wid][lane] = P.v.zhat[nd.v0 + q];
+    }
+    __syncwarp();
+    for (int e = lane; e < kTinyRows * nl; e += 32) {
+      const int k = e / kTinyRows, r = e % kTinyRows;
+      A[e] = r < rows ? nd.src[(r0 + r) + (int64_t)sCol[wid][k] * nd.lds] : 0.0;
+    }
+    __syncwarp();
+    double acc[kTinyRows];
+#pragma unroll
+    for (int r = 0; r < kTinyRows; ++r) acc[r] = 0.0;
+    for (int k = 0; k < nl; ++k) {
+      const double u = (sZq[wid][k] * S) * rcp_nr((sDq[wid][k] - Do) - Tau);
+#pragma unroll
+      for (int r = 0; r < kTinyRows; ++r) acc[r] = fma(A[k * kTinyRows + r], u, acc[r]);
+    }
+    if (lane < K && pos >= 0 && pos < n) {
+      double* out = nd.dst + (int64_t)pos * nd.ldd + r0;
+#pragma unroll
+      for (int r = 0; r < kTinyRows; ++r)
+        if (r < rows) out[r] = acc[r];
+    }
   }
 }
 
@@ -272,6 +331,12 @@ cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s) {
   const int64_t tiles = (int64_t)((seg.rows + BM - 1) / BM) * ((seg.K + BN - 1) / BN);
   if (tiles == 0) return cudaSuccess;
   k_gemm_dense_seg<<<(unsigned)(tiles < 152 * 8 ? tiles : 152 * 8), kThreads, 0, s>>>(seg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_tiny(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  if (L.merges == 0 || L.min_n > kTinyN) return cudaSuccess;
+  k_gemm_tiny<<<(unsigned)((L.merges + kTinyWarps - 1) / kTinyWarps), 32 * kTinyWarps, 0, s>>>(P, L.level, L.merges);
   return cudaGetLastError();
 }
 

@@ -1984,7 +1984,8 @@ __global__ void __launch_bounds__(1024) k_finalize(Plan P, int level) {
     const int64_t rt = (n1 + bm - 1) / bm + (n - n1 + bm - 1) / bm;
     const int64_t ct = (K + bn - 1) / bn;
     const bool split = P.split_min_K > 0 && K >= P.split_min_K;
-    P.m.tiles[g + 1] = (K > 0 && !split) ? rt * ct : 0;
+    const bool tiny = tiny_merge(n, K, P.m.ntop[g], P.m.nbot[g], P.split_min_K, P.struct_min_K);
+    P.m.tiles[g + 1] = (K > 0 && !split && !tiny) ? rt * ct : 0;
   }
 }
 
