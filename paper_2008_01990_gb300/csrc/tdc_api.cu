@@ -213,7 +213,7 @@ struct Layout {
   size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
 };
 
-static constexpr int kVecD = 18;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, 1 for xlo)
+static constexpr int kVecD = 19;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz)
 static constexpr int kVecI = 16;  // int32 per slot (incl. 4 for rij, 2 for stag)
 static constexpr int kVecB = 3;   // bytes per slot
 
@@ -251,6 +251,7 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   v.dval = vd + 12 * N; v.rcs = vd + 13 * N;  // rcs: 2 per slot (13N..15N)
   v.skey = vd + 15 * N;                        // 2 per slot (15N..17N)
   v.xlo = (float*)(vd + 17 * N);
+  v.zz = vd + 18 * N;
   int32_t* vi = (int32_t*)(base + L.vec_i);
   v.perm = vi + 0 * N; v.kept = vi + 1 * N; v.org = vi + 2 * N; v.dcol = vi + 3 * N;
   v.tlist = vi + 4 * N; v.blist = vi + 5 * N; v.posr = vi + 6 * N; v.posd = vi + 7 * N;

@@ -43,6 +43,7 @@ struct Vecs {  // per-slot vectors of length N (sum of n); a merge owns [voff+lo
   double* scol;    // column normalisers
   float2* xz;      // FP32 pole coordinate d_i - d_centre (high part) and z_i^2 (secular pre-iteration)
   float* xlo;      // low part of that coordinate (xz.x + xlo = d_i - d_centre to about 2^-48)
+  double* zz;      // z_i^2 of the non-deflated poles
   double* dval;    // deflated eigenvalues (scan order)
   double* rcs;     // rotations: (c, s) pairs, 2 per slot
   double* skey;    // sort scratch keys, 2 slots per vector slot

@@ -792,6 +792,7 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
       const double x = V.Dk[v0 + j] - dc;
       const float xh = (float)x;
       V.xz[v0 + j] = make_float2(xh, (float)(zj * zj));
+      V.zz[v0 + j] = zj * zj;
       V.xlo[v0 + j] = (float)(x - (double)xh);
     }
   }
@@ -1021,25 +1022,34 @@ __device__ int secular_fp64(const double* D, const double* z, int K, int j, doub
 // accepted when |g| plus that bound passes the convergence test.  Returns true
 // when accepted (tau updated, conv set); otherwise tau is the last iterate,
 // lo / hi hold the bracket, and the caller continues with full passes.
-__device__ bool secular_certified(const double* D, const double* z, int K, int j, double irho, int org,
-                                  double& tau, double& lo, double& hi, bool& conv) {
+__device__ bool secular_certified(const double* D, const double* z, const double* zz, int K, int j, double irho,
+                                  int org, double& tau, double& lo, double& hi, bool& conv) {
   const int lane = threadIdx.x & 31;
   const double dorg = D[org];
   const double dl = D[j] - dorg, dr = (j < K - 1) ? D[j + 1] - dorg : 0.0;
   const int wlo = j - 15, whi = j + 16;
   const int iw = wlo + ((lane - wlo) & 31);  // this lane's window pole
   const bool wv = iw >= 0 && iw < K, wleft = iw <= j;
-  const double zw2 = wv ? z[iw] * z[iw] : 0.0, dw = wv ? D[iw] - dorg : 0.0;
+  const double zw2 = wv ? zz[iw] : 0.0, dw = wv ? D[iw] - dorg : 0.0;
   const double tau1 = tau;
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0, wt = 0.0, wd = 0.0;
-  for (int i = lane; i < K; i += 32) {
+  // this lane's poles are i = lane (mod 32): those below the window lie left of the
+  // root, its one window pole iw is kept apart, those above the window lie right
+  // of it -- three branch-free ranges
+  for (int i = lane; i < wlo; i += 32) {
     const double r = rcp_nr((D[i] - dorg) - tau1);
-    const double zi = z[i];
-    const double t = zi * zi * r;
-    const double tr = t * r;
-    if (i == iw) { wt = t; wd = tr; }
-    else if (i <= j) { a0 += t; a1 += tr; a2 = fma(tr, r, a2); }
-    else { b0 += t; b1 += tr; b2 = fma(tr, r, b2); }
+    const double t = zz[i] * r, tr = t * r;
+    a0 += t; a1 += tr; a2 = fma(tr, r, a2);
+  }
+  if (wv) {
+    const double r = rcp_nr(dw - tau1);
+    wt = zw2 * r;
+    wd = wt * r;
+  }
+  for (int i = iw + 32; i < K; i += 32) {
+    const double r = rcp_nr((D[i] - dorg) - tau1);
+    const double t = zz[i] * r, tr = t * r;
+    b0 += t; b1 += tr; b2 = fma(tr, r, b2);
   }
   a0 = warp_sum(a0); a1 = warp_sum(a1); a2 = warp_sum(a2);
   b0 = warp_sum(b0); b1 = warp_sum(b1); b2 = warp_sum(b2);
@@ -1202,7 +1212,8 @@ __device__ bool secular_fp32(const double* D, const float2* xz, const float* xlo
 // starts there, with the whole interval as bracket.  A root that converges in
 // the half of the far pole is re-solved from that pole.  Without xz, or when the
 // FP32 estimate is unusable, the origin comes from the sign of g at the midpoint.
-__device__ void secular_root(const double* D, const double* z, const float2* xz, const float* xlo, int K, int j,
+__device__ void secular_root(const double* D, const double* z, const double* zz, const float2* xz, const float* xlo,
+                             int K, int j,
                              double rho, int max_iter, int& org_out, double& tau_out, int& iters, bool& conv) {
   const double irho = 1.0 / rho;
   int org;
@@ -1226,7 +1237,7 @@ __device__ void secular_root(const double* D, const double* z, const float2* xz,
     if (org == j) { lo = 0.0; hi = width; } else { lo = -width; hi = 0.0; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
     const bool tried = max_iter >= 2;
-    if (!tried || !secular_certified(D, z, K, j, irho, org, tau, lo, hi, conv)) {
+    if (!tried || !secular_certified(D, z, zz, K, j, irho, org, tau, lo, hi, conv)) {
       secular_sums(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
       if (tried) ++passes;
       passes += secular_fp64(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
@@ -1357,7 +1368,7 @@ __device__ bool secular_fp32_thread(const float2* xz, const float* xlo, int K, i
 // at tau1 keeps the six poles j-2 .. j+3 apart from the far sums (t, t r, t r^2 per
 // side), the following iterates re-evaluate only those six; same remainder bound
 // and acceptance test.
-__device__ bool secular_certified_thread(const double* D, const double* z, int K, int j, double irho, int org,
+__device__ bool secular_certified_thread(const double* D, const double* zz, int K, int j, double irho, int org,
                                          double& tau, double& lo, double& hi, bool& conv) {
   const double dorg = D[org];
   const double dl = D[j] - dorg, dr = (j < K - 1) ? D[j + 1] - dorg : 0.0;
@@ -1366,12 +1377,12 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
   double a0 = 0.0, a1 = 0.0, a2 = 0.0, b0 = 0.0, b1 = 0.0, b2 = 0.0;
   for (int i = 0; i < wlo; ++i) {
     const double r = rcp_nr((D[i] - dorg) - tau1);
-    const double t = z[i] * z[i] * r, tr = t * r;
+    const double t = zz[i] * r, tr = t * r;
     a0 += t; a1 += tr; a2 = fma(tr, r, a2);
   }
   for (int i = whi + 1; i < K; ++i) {
     const double r = rcp_nr((D[i] - dorg) - tau1);
-    const double t = z[i] * z[i] * r, tr = t * r;
+    const double t = zz[i] * r, tr = t * r;
     b0 += t; b1 += tr; b2 = fma(tr, r, b2);
   }
   double dmin = HUGE_VAL;
@@ -1390,7 +1401,7 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
     double wl = 0.0, wr = 0.0, wdl = 0.0, wdr = 0.0;
     for (int i = wlo; i <= whi; ++i) {
       const double r = rcp_nr((D[i] - dorg) - tc);
-      const double t = z[i] * z[i] * r;
+      const double t = zz[i] * r;
       if (i <= j) { wl += t; wdl = fma(t, r, wdl); }
       else { wr += t; wdr = fma(t, r, wdr); }
     }
@@ -1427,7 +1438,8 @@ __device__ bool secular_certified_thread(const double* D, const double* z, int K
 // single: only the FP32 estimate and the certified pass; a root that needs more
 // (no usable estimate, no certificate, or a root in the other pole's half) comes
 // back with conv == false for the warp-per-root solver.
-__device__ void secular_root_thread(const double* D, const double* z, const float2* xz, const float* xlo, int K,
+__device__ void secular_root_thread(const double* D, const double* z, const double* zz, const float2* xz,
+                                    const float* xlo, int K,
                                     int j, double rho, int max_iter, bool single, int& org_out, double& tau_out,
                                     int& iters, bool& conv) {
   const double irho = 1.0 / rho;
@@ -1456,7 +1468,7 @@ __device__ void secular_root_thread(const double* D, const double* z, const floa
     tau = (double)t32;
     if (org == j) { lo = 0.0; hi = width; } else { lo = -width; hi = 0.0; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
-    if (!secular_certified_thread(D, z, K, j, irho, org, tau, lo, hi, conv)) return;
+    if (!secular_certified_thread(D, zz, K, j, irho, org, tau, lo, hi, conv)) return;
     if (!last && ((org == j) ? (tau > 0.5 * width) : (tau < -0.5 * width))) {
       conv = false;
       return;
@@ -1471,7 +1483,7 @@ __device__ void secular_root_thread(const double* D, const double* z, const floa
     if (org == j) { lo = 0.0; hi = width; } else { lo = -width; hi = 0.0; }
     if (!(tau > lo && tau < hi)) tau = 0.5 * (lo + hi);
     const bool tried = max_iter >= 2;
-    if (!tried || !secular_certified_thread(D, z, K, j, irho, org, tau, lo, hi, conv)) {
+    if (!tried || !secular_certified_thread(D, zz, K, j, irho, org, tau, lo, hi, conv)) {
       secular_sums<1>(D, z, K, j, D[org], tau, psi, dpsi, phi, dphi, sabs);
       if (tried) ++passes;
       passes += secular_fp64<1>(D, z, K, j, irho, org, tau, lo, hi, psi, dpsi, phi, dphi, sabs, max_iter, conv);
@@ -1619,7 +1631,8 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
   int org, it;
   double tau;
   bool conv;
-  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, P.v.xlo + v0, K, j, 2.0 * fabs(nd.b), P.max_iter, single, org,
+  secular_root_thread(P.v.Dk + v0, P.v.zk + v0, P.v.zz + v0, P.v.xz + v0, P.v.xlo + v0, K, j, 2.0 * fabs(nd.b),
+                      P.max_iter, single, org,
                       tau, it, conv);
   if (!conv && single) {
     const unsigned long long q = atomicAdd(reinterpret_cast<unsigned long long*>(P.m.roff + M + 1), 1ull);
@@ -1647,7 +1660,8 @@ __global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int np
     int org, it;
     double tau;
     bool conv;
-    secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.xz + S.v0, P.v.xlo + S.v0, S.K, S.j, S.rho, P.max_iter, org,
+    secular_root(P.v.Dk + S.v0, P.v.zk + S.v0, P.v.zz + S.v0, P.v.xz + S.v0, P.v.xlo + S.v0, S.K, S.j, S.rho,
+                 P.max_iter, org,
                  tau, it, conv);
     if ((threadIdx.x & 31) == 0) {
       P.v.org[S.v0 + S.j] = org;
@@ -1674,7 +1688,8 @@ __global__ void __launch_bounds__(256) k_secular(Plan P, int level, int64_t M, i
     // the merge's first warp takes its last root, usually the slowest to converge,
     // so that it starts with the first wave of warps instead of ending the kernel
     const int j = jw == 0 ? K - 1 : jw - 1;
-    secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.xz + v0, P.v.xlo + v0, K, j, rho, P.max_iter, org, tau, it, conv);
+    secular_root(P.v.Dk + v0, P.v.zk + v0, P.v.zz + v0, P.v.xz + v0, P.v.xlo + v0, K, j, rho, P.max_iter, org, tau,
+                 it, conv);
     if ((threadIdx.x & 31) == 0) {
       P.v.org[v0 + j] = org;
       P.v.tau[v0 + j] = tau;
@@ -1828,7 +1843,7 @@ __global__ void __launch_bounds__(256) k_r1_secular(const double* D, const doubl
   int o, it;
   double t;
   bool conv;
-  secular_root(D, z, nullptr, nullptr, K, (int)j, rho, max_iter, o, t, it, conv);
+  secular_root(D, z, nullptr, nullptr, nullptr, K, (int)j, rho, max_iter, o, t, it, conv);
   if ((threadIdx.x & 31) == 0) {
     org[j] = o;
     tau[j] = t;
