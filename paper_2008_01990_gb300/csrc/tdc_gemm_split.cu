@@ -52,12 +52,16 @@ __device__ __forceinline__ int core_off(int r, int k) { return (r >> 3) * (BK * 
 // 2^e for e in [-1022, 1023], built from its bits
 __device__ __forceinline__ double pow2(int e) { return __hiloint2double((1023 + e) << 20, 0); }
 
-// The S leading balanced base-256 digits of x (|x| <= 1 + O(eps)), as floats:
-// F = round(x 2^56) as a two's-complement integer, then digits taken from the
-// least significant end in [-128, 127] (the top digit carries the rest, |d_0| <=
-// 256).  Below the top digit the digits are zero-mean whatever the sign of x, so
-// sums of their products behave like random walks.
-__device__ __forceinline__ void digits_of(double x, int S, float (&dg)[kMaxS]) {
+// The S leading balanced base-256 digits of x (|x| <= 1 + O(eps)), as BF16 bit
+// patterns: F = round(x 2^56) as a two's-complement integer, written as
+// F = sum_s d_s 256^(6-s) with d_s in [-128, 127] for s >= 1 (the top digit carries
+// the rest, |d_0| <= 256).  Below the top digit the digits are zero-mean whatever
+// the sign of x, so sums of their products behave like random walks.  With
+// G = F + 128 (1 + 256 + ... + 256^5) the bytes of G below bit 48 are d_s + 128 and
+// G >> 48 is d_0, so the digits come out of 32-bit field extractions; a small
+// integer d becomes a float as (2^23 + 2^22 + d) - (2^23 + 2^22) on the FP32 pipe,
+// and its BF16 pattern is the float's upper half (exact: |d| <= 256).
+__device__ __forceinline__ void digits_bf16(double x, int S, uint32_t (&dg)[kMaxS]) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const bool neg = (b >> 63) != 0;
   int e = (int)((b >> 52) & 0x7FF);
@@ -68,16 +72,33 @@ __device__ __forceinline__ void digits_of(double x, int S, float (&dg)[kMaxS]) {
   if (sh >= 0) mag = (sh < 8) ? (m << sh) : 0ull;
   else if (sh > -63) mag = ((m >> (-sh - 1)) + 1ull) >> 1;  // round half up
   else mag = 0ull;
-  long long F = neg ? -(long long)mag : (long long)mag;
+  const long long F = neg ? -(long long)mag : (long long)mag;
+  const long long G = F + 0x808080808080ll;
+  const uint32_t lo = (uint32_t)G;
+  const int hi = (int)(G >> 32);
   int d[kMaxS];
+  d[0] = hi >> 16;
+  d[1] = ((hi >> 8) & 255) - 128;
+  d[2] = (hi & 255) - 128;
+  d[3] = (int)(lo >> 24) - 128;
+  d[4] = (int)((lo >> 16) & 255) - 128;
+  d[5] = (int)((lo >> 8) & 255) - 128;
+  d[6] = (int)(lo & 255) - 128;
 #pragma unroll
-  for (int s = kMaxS - 1; s >= 1; --s) {
-    d[s] = (int)((F + 128) & 255) - 128;
-    F = (F - d[s]) >> 8;
+  for (int s = 0; s < kMaxS; ++s) {
+    const float f = __int_as_float(0x4B400000 + d[s]) - 12582912.0f;
+    dg[s] = (s < S) ? (__float_as_uint(f) >> 16) : 0u;
   }
-  d[0] = (int)F;
-#pragma unroll
-  for (int s = 0; s < kMaxS; ++s) dg[s] = (s < S) ? (float)d[s] : 0.0f;
+}
+
+// Eight BF16 patterns (low halves of v[0..7]) into one 16-byte store.
+__device__ __forceinline__ uint4 pack8(const uint32_t* v) {
+  uint4 o;
+  o.x = v[0] | (v[1] << 16);
+  o.y = v[2] | (v[3] << 16);
+  o.z = v[4] | (v[5] << 16);
+  o.w = v[6] | (v[7] << 16);
+  return o;
 }
 
 __device__ __forceinline__ int find_seg(const GemmSeg* segs, int nseg, int64_t w, int which) {
@@ -90,18 +111,6 @@ __device__ __forceinline__ int find_seg(const GemmSeg* segs, int nseg, int64_t w
   return lo;
 }
 
-__device__ __forceinline__ uint4 pack8(const float* v) {
-  uint4 o;
-  __nv_bfloat162 p0 = __floats2bfloat162_rn(v[0], v[1]);
-  __nv_bfloat162 p1 = __floats2bfloat162_rn(v[2], v[3]);
-  __nv_bfloat162 p2 = __floats2bfloat162_rn(v[4], v[5]);
-  __nv_bfloat162 p3 = __floats2bfloat162_rn(v[6], v[7]);
-  o.x = *reinterpret_cast<uint32_t*>(&p0);
-  o.y = *reinterpret_cast<uint32_t*>(&p1);
-  o.z = *reinterpret_cast<uint32_t*>(&p2);
-  o.w = *reinterpret_cast<uint32_t*>(&p3);
-  return o;
-}
 }  // namespace
 
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S) {
@@ -313,7 +322,7 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
     for (int u = tid; u < BM * (BK / 8); u += blockDim.x) {
       const int r = u % BM, kg = u / BM;  // BK/8 groups of 8 consecutive k
       const int row = rt * BM + r;
-      float dig[8][kMaxS];
+      uint32_t dig[8][kMaxS];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int q = kb * BK + kg * 8 + i;
@@ -323,13 +332,13 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
           const int col = sg.acol ? sg.acol[p] : p;
           x = sg.A[(int64_t)row * sg.ars + (int64_t)col * sg.lda];
         }
-        digits_of(x, S, dig[i]);
+        digits_bf16(x, S, dig[i]);
       }
       const int off = core_off(r, kg * 8);
 #pragma unroll
       for (int s = 0; s < kMaxS; ++s) {
         if (s >= S) break;
-        float v[8];
+        uint32_t v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) v[i] = dig[i][s];
         *reinterpret_cast<uint4*>(tile + (int64_t)s * kATileElems + off) = pack8(v);
@@ -365,7 +374,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
         sj = sg.scol[jj];
       }
     }
-    float dig[8][kMaxS];
+    uint32_t dig[8][kMaxS];
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int q = kb * BK + kg * 8 + i;
@@ -374,13 +383,13 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
         const int p = sg.plist ? sg.plist[q] : q;
         u = sg.Bd ? sg.Bd[p + (int64_t)jj * sg.ldb] * sj : (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
       }
-      digits_of(u, S, dig[i]);
+      digits_bf16(u, S, dig[i]);
     }
     const int off = core_off(j, kg * 8);
 #pragma unroll
     for (int s = 0; s < kMaxS; ++s) {
       if (s >= S) break;
-      float v[8];
+      uint32_t v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) v[i] = dig[i][s];
       *reinterpret_cast<uint4*>(tile + (int64_t)s * kBTileElems + off) = pack8(v);
