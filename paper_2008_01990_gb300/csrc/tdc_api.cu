@@ -213,19 +213,24 @@ struct Layout {
   size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
 };
 
-static constexpr int kVecD = 19;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz)
+static constexpr int kVecD = 23;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz, 4 boundary rows)
 static constexpr int kVecI = 16;  // int32 per slot (incl. 4 for rij, 2 for stag)
 static constexpr int kVecB = 3;   // bytes per slot
+
+// int64 words of one set of merge prefixes: tiles, roots, root blocks, image offsets, split passes
+static int64_t tiles_per_set(const HostPlan& H) { return 4 * H.Mmax + 5 + 2 * H.max_passes + 2; }
 
 static Layout layout_of(const HostPlan& H) {
   Layout L;
   size_t o = 0;
   L.prob = o; o = align_up(o + sizeof(Problem) * std::max<size_t>(1, H.prob.size()));
-  L.vec_d = o; o = align_up(o + sizeof(double) * kVecD * (size_t)std::max<int64_t>(1, H.N));
-  L.vec_i = o; o = align_up(o + sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
-  L.vec_b = o; o = align_up(o + kVecB * (size_t)std::max<int64_t>(1, H.N));
-  L.minfo = o; o = align_up(o + sizeof(int32_t) * 6 * (size_t)H.Mmax);
-  L.tiles = o; o = align_up(o + sizeof(int64_t) * (4 * (size_t)H.Mmax + 5 + 2 * (size_t)H.max_passes + 2));
+  // two sets of the per-level vectors and merge data, by level parity: a level reads
+  // its children's results from the other set
+  L.vec_d = o; o = align_up(o + 2 * sizeof(double) * kVecD * (size_t)std::max<int64_t>(1, H.N));
+  L.vec_i = o; o = align_up(o + 2 * sizeof(int32_t) * kVecI * (size_t)std::max<int64_t>(1, H.N));
+  L.vec_b = o; o = align_up(o + 2 * kVecB * (size_t)std::max<int64_t>(1, H.N));
+  L.minfo = o; o = align_up(o + 2 * sizeof(int32_t) * 6 * (size_t)std::max<int64_t>(1, H.Mmax));
+  L.tiles = o; o = align_up(o + 2 * sizeof(int64_t) * tiles_per_set(H));
   L.stats = o; o = align_up(o + sizeof(Stats));
   L.segs = o; o = align_up(o + ((H.split_S || H.struct_m) ? sizeof(GemmSeg) * (size_t)(2 * H.Mmax + 1) : 0));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * (size_t)H.img_elems);
@@ -241,10 +246,10 @@ static Layout layout_of(const HostPlan& H) {
   return L;
 }
 
-static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
+// Set k (0 or 1) of the per-level vectors and merge data.
+static void carve_set(Vecs& v, MergeInfo& m, const HostPlan& H, const Layout& L, char* base, int k) {
   const size_t N = (size_t)std::max<int64_t>(1, H.N);
-  double* vd = (double*)(base + L.vec_d);
-  Vecs& v = P.v;
+  double* vd = (double*)(base + L.vec_d) + (size_t)k * kVecD * N;
   v.dmod = vd + 0 * N; v.lam = vd + 1 * N; v.Dc = vd + 2 * N; v.zc = vd + 3 * N;
   v.Ds = vd + 4 * N; v.zs = vd + 5 * N; v.Dk = vd + 6 * N; v.zk = vd + 7 * N;
   v.tau = vd + 8 * N; v.zhat = vd + 9 * N; v.scol = vd + 10 * N; v.xz = (float2*)(vd + 11 * N);
@@ -252,23 +257,35 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
   v.skey = vd + 15 * N;                        // 2 per slot (15N..17N)
   v.xlo = (float*)(vd + 17 * N);
   v.zz = vd + 18 * N;
-  int32_t* vi = (int32_t*)(base + L.vec_i);
+  v.bf = vd + 19 * N; v.bl = vd + 20 * N; v.rbf = vd + 21 * N; v.rbl = vd + 22 * N;
+  int32_t* vi = (int32_t*)(base + L.vec_i) + (size_t)k * kVecI * N;
   v.perm = vi + 0 * N; v.kept = vi + 1 * N; v.org = vi + 2 * N; v.dcol = vi + 3 * N;
   v.tlist = vi + 4 * N; v.blist = vi + 5 * N; v.posr = vi + 6 * N; v.posd = vi + 7 * N;
   v.rch = vi + 8 * N; v.stag = vi + 9 * N;  // 2N
   v.rij = vi + 11 * N;                       // 4N (ends at 15N)
-  uint8_t* vb = (uint8_t*)(base + L.vec_b);
+  uint8_t* vb = (uint8_t*)(base + L.vec_b) + (size_t)k * kVecB * N;
   v.kseg = vb; v.dseg = vb + N; v.cseg = vb + 2 * N;
-  int32_t* mi = (int32_t*)(base + L.minfo);
-  const size_t M = (size_t)H.Mmax;
-  P.m.K = mi; P.m.nd = mi + M; P.m.nrot = mi + 2 * M; P.m.ntop = mi + 3 * M; P.m.nbot = mi + 4 * M;
-  P.m.nchain = mi + 5 * M;
-  P.m.tiles = (int64_t*)(base + L.tiles);
-  P.m.roff = P.m.tiles + (H.Mmax + 1);
-  P.m.boff = P.m.roff + (H.Mmax + 2);
-  P.m.ioff = P.m.boff + (H.Mmax + 1);
-  P.m.spass = P.m.ioff + (H.Mmax + 1);
-  P.m.sseg = P.m.spass + (2 * H.max_passes + 1);
+  const size_t M = (size_t)std::max<int64_t>(1, H.Mmax);
+  int32_t* mi = (int32_t*)(base + L.minfo) + (size_t)k * 6 * M;
+  m.K = mi; m.nd = mi + M; m.nrot = mi + 2 * M; m.ntop = mi + 3 * M; m.nbot = mi + 4 * M;
+  m.nchain = mi + 5 * M;
+  m.tiles = (int64_t*)(base + L.tiles) + (size_t)k * tiles_per_set(H);
+  m.roff = m.tiles + (H.Mmax + 1);
+  m.boff = m.roff + (H.Mmax + 2);
+  m.ioff = m.boff + (H.Mmax + 1);
+  m.spass = m.ioff + (H.Mmax + 1);
+  m.sseg = m.spass + (2 * H.max_passes + 1);
+}
+
+static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
+  Vecs v1;
+  MergeInfo m1;
+  carve_set(P.v, P.m, H, L, base, 0);
+  carve_set(v1, m1, H, L, base, 1);
+  P.lam2[0] = P.v.lam; P.lam2[1] = v1.lam;
+  P.bf2[0] = P.v.bf; P.bf2[1] = v1.bf;
+  P.bl2[0] = P.v.bl; P.bl2[1] = v1.bl;
+  P.clam = v1.lam; P.cbf = v1.bf; P.cbl = v1.bl;
   P.Q1 = (double*)(base + L.q1);
   P.prob = (const Problem*)(base + L.prob);
   P.segs = (H.split_S || H.struct_m) ? (GemmSeg*)(base + L.segs) : nullptr;
@@ -348,6 +365,13 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   if (!P.status) return TDC_ECUDA;
   P.stats = o.collect_stats ? (Stats*)(base + L.stats) : nullptr;
   if (H.N == 0) return TDC_OK;
+  // PP[k]: the plan of the levels of parity k (their vectors in set k, the children's
+  // in the other); PP[0] also serves the leaves and the output
+  Plan PP[2] = {P, P};
+  carve_set(PP[1].v, PP[1].m, H, L, base, 1);
+  PP[1].clam = P.v.lam;
+  PP[1].cbf = P.v.bf;
+  PP[1].cbl = P.v.bl;
   cudaError_t err = upload_problems(H, (Problem*)P.prob, s);
   if (err == cudaSuccess && P.stats) err = cudaMemsetAsync(P.stats, 0, sizeof(Stats), s);
   // Phase timing (statistics only): events recorded on the call's stream.
@@ -369,6 +393,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   // on levels that also run the thread-per-root variants), output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
+    if (l > 0) launches += 3 + (H.levels[l].nslots >= kSmallMinSlots ? 1 : 0);  // boundary rows
     if (H.levels[l].nslots >= kSmallMinSlots) launches += 5;
     if (H.levels[l].merges > 0 && H.levels[l].min_n <= kTinyN) launches += 1;
     if (H.split_S && H.levels[l].max_n >= o.split_min_K)
@@ -382,14 +407,17 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   span(0, t0, mark());
   for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
     const LevelLaunch& LL = H.levels[l];
+    const Plan& P = PP[l & 1];
     const size_t a0 = mark();
     err = launch_prepare(P, LL, s);
+    if (err == cudaSuccess) err = launch_boundary_rot(P, LL, s);
     if (err == cudaSuccess) err = launch_rotate(P, LL, s);
     const size_t a1 = mark();
     if (err == cudaSuccess) err = launch_secular(P, LL, s);
     const size_t a2 = mark();
     if (err == cudaSuccess) err = launch_lowner(P, LL, s);
     if (err == cudaSuccess) err = launch_finalize(P, LL, s);
+    if (err == cudaSuccess) err = launch_boundary_rows(P, LL, s);
     const size_t a3 = mark();
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
     if (err == cudaSuccess) err = launch_gemm_tiny(P, LL, s);

@@ -44,6 +44,10 @@ struct Vecs {  // per-slot vectors of length N (sum of n); a merge owns [voff+lo
   float2* xz;      // FP32 pole coordinate d_i - d_centre (high part) and z_i^2 (secular pre-iteration)
   float* xlo;      // low part of that coordinate (xz.x + xlo = d_i - d_centre to about 2^-48)
   double* zz;      // z_i^2 of the non-deflated poles
+  double* bf;      // first row of each node's eigenvector matrix (by output column)
+  double* bl;      // last row of it
+  double* rbf;     // first row of the children's block matrix after the deflating rotations
+  double* rbl;     // last row of it
   double* dval;    // deflated eigenvalues (scan order)
   double* rcs;     // rotations: (c, s) pairs, 2 per slot
   double* skey;    // sort scratch keys, 2 slots per vector slot
@@ -140,8 +144,14 @@ struct Plan {
   const double* d;      // caller's d
   const double* e;      // caller's e
   double* lam_out;      // caller's lam
-  Vecs v;
+  Vecs v;               // vectors of the level being processed (one of two sets by level parity)
   MergeInfo m;
+  const double* clam;   // the children's level: eigenvalues and boundary rows, i.e. the other set
+  const double* cbf;
+  const double* cbl;
+  double* lam2[2];      // leaves: both sets (a leaf writes the set of its problem's depth parity)
+  double* bf2[2];
+  double* bl2[2];
   Stats* stats;         // NULL when statistics are off
   int* status;          // device status word
   int32_t max_iter;
@@ -295,6 +305,8 @@ cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStre
 constexpr int64_t kSmallMinSlots = 65536;
 cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_boundary_rows(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, cudaStream_t s);

@@ -238,7 +238,12 @@ __global__ void __launch_bounds__(64) k_leaf(Plan P, int64_t nleaves) {
     int c = perm[k];
     for (int r = tid; r < L; r += blockDim.x) dst[r + k * ld] = Qs[r + c * L];
   }
-  for (int k = tid; k < L; k += blockDim.x) P.v.lam[p.voff + lo + k] = dd[perm[k]];
+  const int par = t & 1;
+  for (int k = tid; k < L; k += blockDim.x) {
+    P.lam2[par][p.voff + lo + k] = dd[perm[k]];
+    P.bf2[par][p.voff + lo + k] = Qs[perm[k] * L];
+    P.bl2[par][p.voff + lo + k] = Qs[(L - 1) + perm[k] * L];
+  }
 }
 
 // Many small leaves per block.  The sequential bulge chase costs one warp
@@ -416,7 +421,11 @@ __global__ void __launch_bounds__(1024) k_leaf_multi(Plan P, int64_t nleaves, in
     const int l = x / Lm, k = x % Lm, L = sL[l];
     if (k >= L) continue;
     const Problem& pr = P.prob[sprob[l]];
-    P.v.lam[pr.voff + slo[l] + k] = sm[(size_t)l * slot + Lm * Lm + perm[l * Lm + k]];
+    const int par = pr.depth & 1, c = perm[l * Lm + k];
+    const int64_t o = pr.voff + slo[l] + k;
+    P.lam2[par][o] = sm[(size_t)l * slot + Lm * Lm + c];
+    P.bf2[par][o] = sm[(size_t)l * slot + c * Lm];
+    P.bl2[par][o] = sm[(size_t)l * slot + (L - 1) + c * Lm];
   }
 }
 
@@ -529,11 +538,13 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   const double rho = 2.0 * fabs(nd.b);
   const double sg = nd.b < 0.0 ? -1.0 : 1.0;
   const double rs2 = 0.70710678118654752440;
-  // 1. z gather (last row of Q1, first row of Q2) and column supports
+  // 1. z: the last row of Q1 and the first row of Q2, the boundary rows the children
+  //    left (the rows of their eigenvector matrices, kept apart so that this level
+  //    does not have to wait for the children's full products)
   double mx = 0.0;
   for (int c = threadIdx.x; c < n; c += blockDim.x) {
-    double D = V.lam[v0 + c];
-    double z = (c < n1) ? nd.src[(n1 - 1) + (int64_t)c * nd.lds] : sg * nd.src[n1 + (int64_t)c * nd.lds];
+    double D = P.clam[v0 + c];
+    double z = (c < n1) ? P.cbl[v0 + c] : sg * P.cbf[v0 + c];
     z *= rs2;
     V.Dc[v0 + c] = D;
     V.zc[v0 + c] = z;
@@ -541,13 +552,13 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   }
   const double tol = 8.0 * kEps * block_reduce_max(mx, redd);
   // 2. ascending order of the two sorted spectra (stable: first half first on ties)
-  const double* D1 = V.lam + v0;
-  const double* D2 = V.lam + v0 + n1;
+  const double* D1 = P.clam + v0;
+  const double* D2 = P.clam + v0 + n1;
   const int n2 = n - n1;
   __shared__ int s_bad;
   if (threadIdx.x == 0) s_bad = 0;
   auto rank_of = [&](int c) -> int {
-    const double D = V.lam[v0 + c];
+    const double D = P.clam[v0 + c];
     if (c < n1) {  // count of D2 < D
       int a = 0, b = n2;
       while (a < b) { int m = (a + b) >> 1; if (D2[m] < D) a = m + 1; else b = m; }
@@ -1889,6 +1900,134 @@ cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   k_colnorm<<<wgrid, 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
   if (small_k) k_colnorm_small<<<tblocks, 256, 0, s>>>(P, L.level, L.merges);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Boundary rows.  Each node's first and last eigenvector rows are kept apart
+// (P.v.bf, P.v.bl, by output column): the parent's z is made of them, so the
+// parent's roots do not need this node's full product.  At a merge, rbf = (first
+// row of Q1, 0) and rbl = (0, last row of Q2) take the deflating rotations as
+// k_rotate applies them to the columns of diag(Q1, Q2) (row 0 lies in the top
+// half, row n-1 in the bottom one); once the roots, zhat, the normalisers and the
+// output order are known, the node's rows are these vectors times Qhat for the
+// non-deflated columns (the same pole lists and entries as the products) and
+// copies for the deflated ones.  The top level has no parent and skips all this.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_boundary_rot(Plan P, int level) {
+  const int64_t g = blockIdx.x;
+  const Node nd = make_node(P, level, g);
+  const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
+  const int64_t v0 = nd.v0;
+  double* rf = P.v.rbf + v0;
+  double* rl = P.v.rbl + v0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    rf[c] = c < n1 ? P.cbf[v0 + c] : 0.0;
+    rl[c] = c < n1 ? 0.0 : P.cbl[v0 + c];
+  }
+  const int nr = P.m.nrot[g];
+  if (nr == 0) return;
+  __syncthreads();
+  const int nch = P.m.nchain[g];
+  for (int h = threadIdx.x; h < nch; h += blockDim.x) {
+    const int k0 = P.v.rch[v0 + h];
+    const int k1 = (h + 1 < nch) ? P.v.rch[v0 + h + 1] : nr;
+    for (int k = k0; k < k1; ++k) {
+      const int pj = P.v.rij[4 * (v0 + k) + 0];
+      const int ci = P.v.rij[4 * (v0 + k) + 1];
+      const int sup = P.v.rij[4 * (v0 + k) + 2];
+      const int sp = sup & 0xff, si = sup >> 8;
+      const double c = P.v.rcs[2 * (v0 + k)], s = P.v.rcs[2 * (v0 + k) + 1];
+      if ((sp | si) & 1) {
+        const double x = (sp & 1) ? rf[pj] : 0.0, y = (si & 1) ? rf[ci] : 0.0;
+        rf[pj] = c * x + s * y;
+        rf[ci] = c * y - s * x;
+      }
+      if ((sp | si) & 2) {
+        const double x = (sp & 2) ? rl[pj] : 0.0, y = (si & 2) ? rl[ci] : 0.0;
+        rl[pj] = c * x + s * y;
+        rl[ci] = c * y - s * x;
+      }
+    }
+  }
+}
+
+// Output column of root j: the rotated first row times Qhat over the top list, the
+// rotated last row over the bottom list (W lanes share the sums).
+template <int W>
+__device__ __forceinline__ void boundary_col(const Plan& P, const Node& nd, int64_t g, int j) {
+  const int64_t v0 = nd.v0;
+  const double* Dk = P.v.Dk + v0;
+  const double dorg = Dk[P.v.org[v0 + j]], tj = P.v.tau[v0 + j], sj = P.v.scol[v0 + j];
+  const int* tl = P.v.tlist + v0;
+  const int* bl = P.v.blist + v0;
+  const int* kept = P.v.kept + v0;
+  const double* zh = P.v.zhat + v0;
+  const double* rf = P.v.rbf + v0;
+  const double* rl = P.v.rbl + v0;
+  const int ntop = P.m.ntop[g], nbot = P.m.nbot[g];
+  double f = 0.0, l = 0.0;
+  const int k0 = W == 32 ? (threadIdx.x & 31) : 0;
+  for (int k = k0; k < ntop; k += W) {
+    const int q = tl[k];
+    f = fma(rf[kept[q]], (zh[q] * sj) * rcp_nr((Dk[q] - dorg) - tj), f);
+  }
+  for (int k = k0; k < nbot; k += W) {
+    const int q = bl[k];
+    l = fma(rl[kept[q]], (zh[q] * sj) * rcp_nr((Dk[q] - dorg) - tj), l);
+  }
+  if (W == 32) {
+    f = warp_sum(f);
+    l = warp_sum(l);
+  }
+  if (W == 1 || (threadIdx.x & 31) == 0) {
+    const int pos = P.v.posr[v0 + j];
+    P.v.bf[v0 + pos] = f;
+    P.v.bl[v0 + pos] = l;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_boundary_rows(Plan P, int level, int64_t M, int small_k, bool listed) {
+  for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int j) {
+    boundary_col<32>(P, make_node(P, level, g), g, j);
+  });
+}
+
+__global__ void __launch_bounds__(256) k_boundary_rows_small(Plan P, int level, int64_t M) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t g;
+  int j;
+  if (!small_root(P, M, t, g, j)) return;
+  boundary_col<1>(P, make_node(P, level, g), g, j);
+}
+
+// Deflated entry q of merge g: a copy of its (rotated) column's boundary entries.
+__global__ void __launch_bounds__(256) k_boundary_defl(Plan P, int level) {
+  const int64_t g = blockIdx.x;
+  const int q = blockIdx.y * blockDim.x + threadIdx.x;
+  if (q >= P.m.nd[g]) return;
+  const int64_t v0 = make_node(P, level, g).v0;
+  const int c = P.v.dcol[v0 + q], sp = P.v.dseg[v0 + q], o = P.v.posd[v0 + q];
+  P.v.bf[v0 + o] = (sp & 1) ? P.v.rbf[v0 + c] : 0.0;
+  P.v.bl[v0 + o] = (sp & 2) ? P.v.rbl[v0 + c] : 0.0;
+}
+
+cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  if (L.level == 0 || L.merges == 0) return cudaSuccess;
+  int threads = 1024;
+  while (threads > 32 && threads / 2 >= L.max_n) threads /= 2;
+  k_boundary_rot<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_rows(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+  if (L.level == 0 || L.nslots == 0) return cudaSuccess;
+  const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
+  const bool listed = small_k > 0;  // block list left by launch_secular's k_root_scan
+  k_boundary_rows<<<warp_root_grid(L, listed), 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
+  if (small_k)
+    k_boundary_rows_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.merges);
+  k_boundary_defl<<<dim3((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256)), 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
 }
 
