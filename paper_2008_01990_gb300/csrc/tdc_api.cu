@@ -329,6 +329,20 @@ static int validate_opts(const tdc_opts* o) {
   return 0;
 }
 
+// The second stream of the solver, one per host thread and device, created on first
+// use with the highest priority (the products are the critical path).
+static cudaStream_t gemm_stream() {
+  static thread_local cudaStream_t st[16] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 16) return nullptr;
+  if (st[dev] == nullptr) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&st[dev], cudaStreamNonBlocking, hi) != cudaSuccess) st[dev] = nullptr;
+  }
+  return st[dev];
+}
+
 static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const double* e, double* lam, double* Q,
                     void* ws, size_t ws_bytes, cudaStream_t s) {
   Layout L = layout_of(H);
@@ -378,14 +392,15 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   const bool timing = o.collect_stats != 0;
   std::vector<cudaEvent_t> evs;
   std::vector<std::pair<int, std::pair<size_t, size_t>>> spans;  // (phase, (from, to))
-  auto mark = [&]() -> size_t {
+  auto mark_on = [&](cudaStream_t st) -> size_t {
     if (!timing) return 0;
     cudaEvent_t ev;
     cudaEventCreate(&ev);
-    cudaEventRecord(ev, s);
+    cudaEventRecord(ev, st);
     evs.push_back(ev);
     return evs.size() - 1;
   };
+  auto mark = [&]() -> size_t { return mark_on(s); };
   auto span = [&](int phase, size_t a0, size_t a1) {
     if (timing) spans.push_back({phase, {a0, a1}});
   };
@@ -405,13 +420,29 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   if (err == cudaSuccess) err = launch_dmod(P, s);
   if (err == cudaSuccess) err = launch_leaves(P, H.nleaves, H.max_leaf, s);
   span(0, t0, mark());
+  // Two streams.  The caller's stream s runs each level's roots and vectors
+  // (deflation, secular equation, zhat, normalisers, ordering, boundary rows); a
+  // second stream sg runs its products and copies (rotations of the children's
+  // columns, FP64 / split / structured products, deflated copies).  The roots of
+  // level l-1 need only level l's boundary rows, so they run on s while level l's
+  // products run on sg.  Level l's products wait for its roots (evE); level l-2's
+  // roots reuse level l's vector set and wait for its products (evG); the output
+  // waits for the top level's products.
+  cudaStream_t sg = gemm_stream();
+  if (sg == nullptr) err = cudaErrorUnknown;
+  std::vector<cudaEvent_t> evE(H.T, nullptr), evG(H.T, nullptr);
+  for (int l = 0; l < H.T && err == cudaSuccess; ++l) {
+    if (cudaEventCreateWithFlags(&evE[l], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&evG[l], cudaEventDisableTiming) != cudaSuccess)
+      err = cudaErrorUnknown;
+  }
   for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
     const LevelLaunch& LL = H.levels[l];
     const Plan& P = PP[l & 1];
+    if (l + 2 < H.T) err = cudaStreamWaitEvent(s, evG[l + 2], 0);
     const size_t a0 = mark();
-    err = launch_prepare(P, LL, s);
+    if (err == cudaSuccess) err = launch_prepare(P, LL, s);
     if (err == cudaSuccess) err = launch_boundary_rot(P, LL, s);
-    if (err == cudaSuccess) err = launch_rotate(P, LL, s);
     const size_t a1 = mark();
     if (err == cudaSuccess) err = launch_secular(P, LL, s);
     const size_t a2 = mark();
@@ -419,8 +450,17 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     if (err == cudaSuccess) err = launch_finalize(P, LL, s);
     if (err == cudaSuccess) err = launch_boundary_rows(P, LL, s);
     const size_t a3 = mark();
-    if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], s);
-    if (err == cudaSuccess) err = launch_gemm_tiny(P, LL, s);
+    span(1, a0, a1);
+    span(2, a1, a2);
+    span(3, a2, a3);
+    if (err == cudaSuccess) err = cudaEventRecord(evE[l], s);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sg, evE[l], 0);
+    const size_t g0 = mark_on(sg);
+    if (err == cudaSuccess) err = launch_rotate(P, LL, sg);
+    const size_t g1 = mark_on(sg);
+    span(1, g0, g1);
+    if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], sg);
+    if (err == cudaSuccess) err = launch_gemm_tiny(P, LL, sg);
     if (err == cudaSuccess && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
       int64_t Tmax, ldw;
       level_struct_dims(LL, H.struct_m, Tmax, ldw);
@@ -428,19 +468,16 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       SA.ldw = ldw;
       SA.status = P.status;
       SA.flops = P.stats ? &P.stats->struct_flops : nullptr;
-      err = launch_struct_segs(P, LL, s);
-      if (err == cudaSuccess) err = launch_struct(P.segs, (int)(2 * LL.merges), SA, s);
+      err = launch_struct_segs(P, LL, sg);
+      if (err == cudaSuccess) err = launch_struct(P.segs, (int)(2 * LL.merges), SA, sg);
     }
-    const size_t a4 = mark();
-    span(1, a0, a1);
-    span(2, a1, a2);
-    span(3, a2, a3);
-    span(4, a3, a4);
+    const size_t a4 = mark_on(sg);
+    span(4, g1, a4);
     size_t a6 = a4;
     if (err == cudaSuccess && P.split_min_K > 0 && LL.max_n >= P.split_min_K) {
       // several passes on the host's bound: packed again on the device from the actual sizes
       const int npass = (int)H.split_chunks[l].size();
-      if (npass > 1) err = launch_split_pack(P, LL, npass, s);
+      if (npass > 1) err = launch_split_pack(P, LL, npass, sg);
       int pass = 0;
       for (auto& ch : H.split_chunks[l]) {
         cudaEvent_t mid = nullptr;
@@ -450,15 +487,21 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
         }
         const size_t b5 = timing ? evs.size() - 1 : 0;
         const size_t b4 = a6;
-        if (err == cudaSuccess) err = launch_gemm_split(P, LL, ch.first, ch.second, npass > 1 ? pass : -1, s, mid);
+        if (err == cudaSuccess) err = launch_gemm_split(P, LL, ch.first, ch.second, npass > 1 ? pass : -1, sg, mid);
         ++pass;
-        a6 = mark();
+        a6 = mark_on(sg);
         span(5, b4, b5);
         span(6, b5, a6);
       }
     }
-    if (err == cudaSuccess) err = launch_copy_deflated(P, LL, o.sign_normalise, s);
-    span(7, a6, mark());
+    if (err == cudaSuccess) err = launch_copy_deflated(P, LL, o.sign_normalise, sg);
+    span(7, a6, mark_on(sg));
+    if (err == cudaSuccess) err = cudaEventRecord(evG[l], sg);
+  }
+  if (err == cudaSuccess && H.T > 0) err = cudaStreamWaitEvent(s, evG[0], 0);
+  for (int l = 0; l < H.T; ++l) {
+    if (evE[l]) cudaEventDestroy(evE[l]);
+    if (evG[l]) cudaEventDestroy(evG[l]);
   }
   const size_t t8 = mark();
   if (err == cudaSuccess) err = launch_sign_and_output(P, o.sign_normalise, s);

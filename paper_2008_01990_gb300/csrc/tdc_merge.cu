@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
 }
 
 cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
-  int threads = 1024;
+  int threads = 256;
   while (threads > 64 && threads / 2 >= L.max_n) threads /= 2;
   k_prepare<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
   return cudaGetLastError();
@@ -1584,14 +1584,18 @@ __global__ void __launch_bounds__(1024) k_root_scan(Plan P, int64_t M, int small
 // the roots 8y .. 8y+7 of merge g, and blocks past K or of small merges leave at
 // once.  Listed: a fixed grid walks the compacted block list of k_root_scan (on
 // levels with many merges, most of the merge-major blocks would be empty).
+// A block of fewer than 8 warps takes the 8 roots of its unit in turns.
 template <typename F>
 __device__ __forceinline__ void for_warp_roots(const Plan& P, int64_t M, int small_k, bool listed, F&& f) {
-  const int wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (!listed) {
     const int64_t g = blockIdx.x;
     const int K = P.m.K[g];
-    const int j = blockIdx.y * 8 + wid;
-    if (K > small_k && j < K) f(g, K, j);
+    if (K <= small_k) return;
+    for (int u = wid; u < 8; u += nw) {
+      const int j = blockIdx.y * 8 + u;
+      if (j < K) f(g, K, j);
+    }
     return;
   }
   const int64_t total = P.m.boff[M];
@@ -1602,10 +1606,17 @@ __device__ __forceinline__ void for_warp_roots(const Plan& P, int64_t M, int sma
       if (P.m.boff[m] <= w) lo = m; else hi = m - 1;
     }
     const int K = P.m.K[lo];
-    const int j = (int)(w - P.m.boff[lo]) * 8 + wid;
-    if (j < K) f(lo, K, j);
+    for (int u = wid; u < 8; u += nw) {
+      const int j = (int)(w - P.m.boff[lo]) * 8 + u;
+      if (j < K) f(lo, K, j);
+    }
   }
 }
+
+// Block sizes of the root-side kernels are chosen so that a block fits on an SM
+// beside a resident split-GEMM CTA (about 17.9K registers and 59 KB of shared
+// memory left): the roots of the next level run while this level's products do.
+constexpr int kSecThreads = 128;
 
 static dim3 warp_root_grid(const LevelLaunch& L, bool listed) {
   return listed ? dim3(152 * 8) : dim3((unsigned)L.merges, (unsigned)((L.max_n + 7) / 8));
@@ -1630,7 +1641,7 @@ __device__ __forceinline__ bool small_root(const Plan& P, int64_t M, int64_t t, 
 // finished by a warp each in k_secular_fixup.  With an iteration limit below two
 // passes the thread runs the whole iteration itself.
 
-__global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_t M) {
+__global__ void __launch_bounds__(kSecThreads) k_secular_small(Plan P, int level, int64_t M) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t g;
   int j;
@@ -1661,7 +1672,7 @@ __global__ void __launch_bounds__(256) k_secular_small(Plan P, int level, int64_
 }
 
 // The listed roots, a warp each (the warp-per-root solver with its full budget).
-__global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int nprob_act, int64_t M) {
+__global__ void __launch_bounds__(kSecThreads) k_secular_fixup(Plan P, int level, int nprob_act, int64_t M) {
   const int64_t cnt = P.m.roff[M + 1];
   if (P.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&P.stats->handoffs, (unsigned long long)cnt);
   for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < cnt;
@@ -1688,7 +1699,7 @@ __global__ void __launch_bounds__(256) k_secular_fixup(Plan P, int level, int np
 }
 
 // Warp per root over the merges with K > small_k (for_warp_roots).
-__global__ void __launch_bounds__(256) k_secular(Plan P, int level, int64_t M, int small_k, bool listed) {
+__global__ void __launch_bounds__(kSecThreads) k_secular(Plan P, int level, int64_t M, int small_k, bool listed) {
   for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int jw) {
     const Node nd = make_node(P, level, g);
     const int64_t v0 = nd.v0;
@@ -1718,12 +1729,13 @@ cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s) 
   if (L.nslots == 0) return cudaSuccess;
   const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
   const bool listed = small_k > 0;
-  if (listed) k_root_scan<<<1, 1024, 0, s>>>(P, L.merges, small_k);
-  k_secular<<<warp_root_grid(L, listed), 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
+  if (listed) k_root_scan<<<1, 512, 0, s>>>(P, L.merges, small_k);
+  k_secular<<<warp_root_grid(L, listed), kSecThreads, 0, s>>>(P, L.level, L.merges, small_k, listed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || small_k == 0) return e;
-  k_secular_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.merges);
-  k_secular_fixup<<<152 * 8, 256, 0, s>>>(P, L.level, L.nprob_act, L.merges);
+  k_secular_small<<<(unsigned)((L.nslots + kSecThreads - 1) / kSecThreads), kSecThreads, 0, s>>>(P, L.level,
+                                                                                                  L.merges);
+  k_secular_fixup<<<152 * 16, kSecThreads, 0, s>>>(P, L.level, L.nprob_act, L.merges);
   return cudaGetLastError();
 }
 
@@ -2014,7 +2026,7 @@ __global__ void __launch_bounds__(256) k_boundary_defl(Plan P, int level) {
 
 cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.level == 0 || L.merges == 0) return cudaSuccess;
-  int threads = 1024;
+  int threads = 256;
   while (threads > 32 && threads / 2 >= L.max_n) threads /= 2;
   k_boundary_rot<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
   return cudaGetLastError();
@@ -2163,12 +2175,12 @@ __global__ void k_tile_scan(Plan P, int64_t M) {
 }
 
 cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
-  int threads = 1024;
+  int threads = 512;
   while (threads > 64 && threads / 2 >= L.max_n) threads /= 2;
   k_finalize<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_tile_scan<<<1, 1024, 0, s>>>(P, L.merges);
+  k_tile_scan<<<1, 512, 0, s>>>(P, L.merges);
   return cudaGetLastError();
 }
 
