@@ -1965,9 +1965,12 @@ __global__ void __launch_bounds__(1024) k_boundary_rot(Plan P, int level) {
 }
 
 // Output column of root j: the rotated first row times Qhat over the top list, the
-// rotated last row over the bottom list (W lanes share the sums).
+// rotated last row over the bottom list (W lanes share the sums).  Only merges read
+// these rows -- a node's last row if it is a top child, its first row if a bottom
+// child, and through them the rows its ancestors need -- so the leftmost node of a
+// level (index 0) never needs its first row and the rightmost its last row.
 template <int W>
-__device__ __forceinline__ void boundary_col(const Plan& P, const Node& nd, int64_t g, int j) {
+__device__ __forceinline__ void boundary_col(const Plan& P, const Node& nd, int level, int64_t g, int j) {
   const int64_t v0 = nd.v0;
   const double* Dk = P.v.Dk + v0;
   const double dorg = Dk[P.v.org[v0 + j]], tj = P.v.tau[v0 + j], sj = P.v.scol[v0 + j];
@@ -1977,7 +1980,9 @@ __device__ __forceinline__ void boundary_col(const Plan& P, const Node& nd, int6
   const double* zh = P.v.zhat + v0;
   const double* rf = P.v.rbf + v0;
   const double* rl = P.v.rbl + v0;
-  const int ntop = P.m.ntop[g], nbot = P.m.nbot[g];
+  const int64_t idx = g & ((((int64_t)1) << level) - 1);
+  const int ntop = idx != 0 ? P.m.ntop[g] : 0;
+  const int nbot = idx != (((int64_t)1) << level) - 1 ? P.m.nbot[g] : 0;
   double f = 0.0, l = 0.0;
   const int k0 = W == 32 ? (threadIdx.x & 31) : 0;
   for (int k = k0; k < ntop; k += W) {
@@ -2001,7 +2006,7 @@ __device__ __forceinline__ void boundary_col(const Plan& P, const Node& nd, int6
 
 __global__ void __launch_bounds__(256) k_boundary_rows(Plan P, int level, int64_t M, int small_k, bool listed) {
   for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int j) {
-    boundary_col<32>(P, make_node(P, level, g), g, j);
+    boundary_col<32>(P, make_node(P, level, g), level, g, j);
   });
 }
 
@@ -2010,7 +2015,7 @@ __global__ void __launch_bounds__(256) k_boundary_rows_small(Plan P, int level, 
   int64_t g;
   int j;
   if (!small_root(P, M, t, g, j)) return;
-  boundary_col<1>(P, make_node(P, level, g), g, j);
+  boundary_col<1>(P, make_node(P, level, g), level, g, j);
 }
 
 // Deflated entry q of merge g: a copy of its (rotated) column's boundary entries.
