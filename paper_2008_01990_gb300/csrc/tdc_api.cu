@@ -213,7 +213,7 @@ struct Layout {
   size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
 };
 
-static constexpr int kVecD = 23;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz, 4 boundary rows)
+static constexpr int kVecD = 27;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz, 8 boundary rows)
 static constexpr int kVecI = 16;  // int32 per slot (incl. 4 for rij, 2 for stag)
 static constexpr int kVecB = 3;   // bytes per slot
 
@@ -258,6 +258,7 @@ static void carve_set(Vecs& v, MergeInfo& m, const HostPlan& H, const Layout& L,
   v.xlo = (float*)(vd + 17 * N);
   v.zz = vd + 18 * N;
   v.bf = vd + 19 * N; v.bl = vd + 20 * N; v.rbf = vd + 21 * N; v.rbl = vd + 22 * N;
+  v.pf = vd + 23 * N; v.pl = vd + 24 * N; v.rf = vd + 25 * N; v.rl = vd + 26 * N;
   int32_t* vi = (int32_t*)(base + L.vec_i) + (size_t)k * kVecI * N;
   v.perm = vi + 0 * N; v.kept = vi + 1 * N; v.org = vi + 2 * N; v.dcol = vi + 3 * N;
   v.tlist = vi + 4 * N; v.blist = vi + 5 * N; v.posr = vi + 6 * N; v.posd = vi + 7 * N;
@@ -408,7 +409,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   // on levels that also run the thread-per-root variants), output
   int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
-    if (l > 0) launches += 3 + (H.levels[l].nslots >= kSmallMinSlots ? 1 : 0);  // boundary rows
+    if (l > 0) launches += 2;  // boundary rows: rotation and gather, output order
     if (H.levels[l].nslots >= kSmallMinSlots) launches += 5;
     if (H.levels[l].merges > 0 && H.levels[l].min_n <= kTinyN) launches += 1;
     if (H.split_S && H.levels[l].max_n >= o.split_min_K)

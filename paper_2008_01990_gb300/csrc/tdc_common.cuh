@@ -48,6 +48,10 @@ struct Vecs {  // per-slot vectors of length N (sum of n); a merge owns [voff+lo
   double* bl;      // last row of it
   double* rbf;     // first row of the children's block matrix after the deflating rotations
   double* rbl;     // last row of it
+  double* pf;      // rbf at the column of non-deflated pole i where it has top support, else 0
+  double* pl;      // rbl at that column where it has bottom support, else 0
+  double* rf;      // the node's first row at root j's column (by root index, before ordering)
+  double* rl;      // its last row there
   double* dval;    // deflated eigenvalues (scan order)
   double* rcs;     // rotations: (c, s) pairs, 2 per slot
   double* skey;    // sort scratch keys, 2 slots per vector slot

@@ -1839,21 +1839,78 @@ __device__ double column_norm(const double* D, const double* zh, int K, double d
   return 1.0 / sqrt(acc);
 }
 
+// The same pass for a merge below the top level, which also forms its boundary
+// rows at root j's column: with u_i = zhat_i / delta_ij, Qhat_ij = s_j u_i, so the
+// first row there is s_j sum_i pf_i u_i and the last s_j sum_i pl_i u_i (pf, pl:
+// the rotated children rows at the poles' columns, zero outside their support) --
+// two more multiply-adds per term.  The leftmost node of a level skips the first
+// row and the rightmost the last (no merge reads them).
+template <int W = 32>
+__device__ double column_norm_rows(const Plan& P, int64_t v0, int K, int j, bool need_f, bool need_l) {
+  const double* D = P.v.Dk + v0;
+  const double* zh = P.v.zhat + v0;
+  const double* pf = P.v.pf + v0;
+  const double* pl = P.v.pl + v0;
+  const double dorg = D[P.v.org[v0 + j]], tj = P.v.tau[v0 + j];
+  double acc = 0.0, f = 0.0, l = 0.0;
+  const int i0 = W == 32 ? (threadIdx.x & 31) : 0;
+  if (need_f && need_l) {
+    for (int i = i0; i < K; i += W) {
+      const double u = zh[i] * rcp_nr((D[i] - dorg) - tj);
+      acc = fma(u, u, acc);
+      f = fma(pf[i], u, f);
+      l = fma(pl[i], u, l);
+    }
+  } else {
+    const double* pq = need_f ? pf : pl;
+    double x = 0.0;
+    for (int i = i0; i < K; i += W) {
+      const double u = zh[i] * rcp_nr((D[i] - dorg) - tj);
+      acc = fma(u, u, acc);
+      x = fma(pq[i], u, x);
+    }
+    if (need_f) f = x; else l = x;
+  }
+  if (W == 32) {
+    acc = warp_sum(acc);
+    f = warp_sum(f);
+    l = warp_sum(l);
+  }
+  const double sj = 1.0 / sqrt(acc);
+  if (W == 1 || (threadIdx.x & 31) == 0) {
+    P.v.rf[v0 + j] = sj * f;
+    P.v.rl[v0 + j] = sj * l;
+  }
+  return sj;
+}
+
 __global__ void __launch_bounds__(256) k_colnorm_small(Plan P, int level, int64_t M) {
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int64_t g;
   int j;
   if (!small_root(P, M, t, g, j)) return;
   const int64_t v0 = make_node(P, level, g).v0;
+  const int K = P.m.K[g];
+  if (level > 0) {
+    const int64_t idx = g & ((((int64_t)1) << level) - 1);
+    P.v.scol[v0 + j] = column_norm_rows<1>(P, v0, K, j, idx != 0, idx != (((int64_t)1) << level) - 1);
+    return;
+  }
   const double* D = P.v.Dk + v0;
-  P.v.scol[v0 + j] = column_norm<1>(D, P.v.zhat + v0, P.m.K[g], D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
+  P.v.scol[v0 + j] = column_norm<1>(D, P.v.zhat + v0, K, D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
 }
 
 __global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int64_t M, int small_k, bool listed) {
   for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int j) {
     const int64_t v0 = make_node(P, level, g).v0;
-    const double* D = P.v.Dk + v0;
-    const double sj = column_norm(D, P.v.zhat + v0, K, D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
+    double sj;
+    if (level > 0) {
+      const int64_t idx = g & ((((int64_t)1) << level) - 1);
+      sj = column_norm_rows(P, v0, K, j, idx != 0, idx != (((int64_t)1) << level) - 1);
+    } else {
+      const double* D = P.v.Dk + v0;
+      sj = column_norm(D, P.v.zhat + v0, K, D[P.v.org[v0 + j]], P.v.tau[v0 + j]);
+    }
     if ((threadIdx.x & 31) == 0) P.v.scol[v0 + j] = sj;
   });
 }
@@ -1938,9 +1995,8 @@ __global__ void __launch_bounds__(1024) k_boundary_rot(Plan P, int level) {
     rl[c] = c < n1 ? 0.0 : P.cbl[v0 + c];
   }
   const int nr = P.m.nrot[g];
-  if (nr == 0) return;
   __syncthreads();
-  const int nch = P.m.nchain[g];
+  const int nch = nr > 0 ? P.m.nchain[g] : 0;
   for (int h = threadIdx.x; h < nch; h += blockDim.x) {
     const int k0 = P.v.rch[v0 + h];
     const int k1 = (h + 1 < nch) ? P.v.rch[v0 + h + 1] : nr;
@@ -1962,68 +2018,33 @@ __global__ void __launch_bounds__(1024) k_boundary_rot(Plan P, int level) {
       }
     }
   }
-}
-
-// Output column of root j: the rotated first row times Qhat over the top list, the
-// rotated last row over the bottom list (W lanes share the sums).  Only merges read
-// these rows -- a node's last row if it is a top child, its first row if a bottom
-// child, and through them the rows its ancestors need -- so the leftmost node of a
-// level (index 0) never needs its first row and the rightmost its last row.
-template <int W>
-__device__ __forceinline__ void boundary_col(const Plan& P, const Node& nd, int level, int64_t g, int j) {
-  const int64_t v0 = nd.v0;
-  const double* Dk = P.v.Dk + v0;
-  const double dorg = Dk[P.v.org[v0 + j]], tj = P.v.tau[v0 + j], sj = P.v.scol[v0 + j];
-  const int* tl = P.v.tlist + v0;
-  const int* bl = P.v.blist + v0;
-  const int* kept = P.v.kept + v0;
-  const double* zh = P.v.zhat + v0;
-  const double* rf = P.v.rbf + v0;
-  const double* rl = P.v.rbl + v0;
-  const int64_t idx = g & ((((int64_t)1) << level) - 1);
-  const int ntop = idx != 0 ? P.m.ntop[g] : 0;
-  const int nbot = idx != (((int64_t)1) << level) - 1 ? P.m.nbot[g] : 0;
-  double f = 0.0, l = 0.0;
-  const int k0 = W == 32 ? (threadIdx.x & 31) : 0;
-  for (int k = k0; k < ntop; k += W) {
-    const int q = tl[k];
-    f = fma(rf[kept[q]], (zh[q] * sj) * rcp_nr((Dk[q] - dorg) - tj), f);
-  }
-  for (int k = k0; k < nbot; k += W) {
-    const int q = bl[k];
-    l = fma(rl[kept[q]], (zh[q] * sj) * rcp_nr((Dk[q] - dorg) - tj), l);
-  }
-  if (W == 32) {
-    f = warp_sum(f);
-    l = warp_sum(l);
-  }
-  if (W == 1 || (threadIdx.x & 31) == 0) {
-    const int pos = P.v.posr[v0 + j];
-    P.v.bf[v0 + pos] = f;
-    P.v.bl[v0 + pos] = l;
+  __syncthreads();
+  // by pole: the rotated rows at the pole's column, where the pole has support
+  const int K = P.m.K[g];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    const int col = P.v.kept[v0 + i];
+    const int sup = P.v.kseg[v0 + i];
+    P.v.pf[v0 + i] = (sup & 1) ? rf[col] : 0.0;
+    P.v.pl[v0 + i] = (sup & 2) ? rl[col] : 0.0;
   }
 }
 
-__global__ void __launch_bounds__(256) k_boundary_rows(Plan P, int level, int64_t M, int small_k, bool listed) {
-  for_warp_roots(P, M, small_k, listed, [&](int64_t g, int K, int j) {
-    boundary_col<32>(P, make_node(P, level, g), level, g, j);
-  });
-}
-
-__global__ void __launch_bounds__(256) k_boundary_rows_small(Plan P, int level, int64_t M) {
-  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  int64_t g;
-  int j;
-  if (!small_root(P, M, t, g, j)) return;
-  boundary_col<1>(P, make_node(P, level, g), level, g, j);
-}
-
-// Deflated entry q of merge g: a copy of its (rotated) column's boundary entries.
-__global__ void __launch_bounds__(256) k_boundary_defl(Plan P, int level) {
+// The node's boundary rows in output order: root j's entries (formed with the
+// column norms) go to column posr[j]; deflated entry q copies its (rotated)
+// column's entries to column posd[q].
+__global__ void __launch_bounds__(256) k_boundary_out(Plan P, int level) {
   const int64_t g = blockIdx.x;
-  const int q = blockIdx.y * blockDim.x + threadIdx.x;
-  if (q >= P.m.nd[g]) return;
+  const int t = blockIdx.y * blockDim.x + threadIdx.x;
+  const int K = P.m.K[g];
   const int64_t v0 = make_node(P, level, g).v0;
+  if (t < K) {
+    const int o = P.v.posr[v0 + t];
+    P.v.bf[v0 + o] = P.v.rf[v0 + t];
+    P.v.bl[v0 + o] = P.v.rl[v0 + t];
+    return;
+  }
+  const int q = t - K;
+  if (q >= P.m.nd[g]) return;
   const int c = P.v.dcol[v0 + q], sp = P.v.dseg[v0 + q], o = P.v.posd[v0 + q];
   P.v.bf[v0 + o] = (sp & 1) ? P.v.rbf[v0 + c] : 0.0;
   P.v.bl[v0 + o] = (sp & 2) ? P.v.rbl[v0 + c] : 0.0;
@@ -2039,12 +2060,7 @@ cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_
 
 cudaError_t launch_boundary_rows(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.level == 0 || L.nslots == 0) return cudaSuccess;
-  const int small_k = L.nslots >= kSmallMinSlots ? kSmallK : 0;
-  const bool listed = small_k > 0;  // block list left by launch_secular's k_root_scan
-  k_boundary_rows<<<warp_root_grid(L, listed), 256, 0, s>>>(P, L.level, L.merges, small_k, listed);
-  if (small_k)
-    k_boundary_rows_small<<<(unsigned)((L.nslots + 255) / 256), 256, 0, s>>>(P, L.level, L.merges);
-  k_boundary_defl<<<dim3((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256)), 256, 0, s>>>(P, L.level);
+  k_boundary_out<<<dim3((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256)), 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
 }
 
