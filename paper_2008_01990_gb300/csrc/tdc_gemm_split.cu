@@ -175,7 +175,9 @@ __device__ __forceinline__ void block_excl_scan4(int64_t (&v)[4], int64_t (&sc)[
 }
 
 // Merges [g0, g1), or (pass >= 0) the merge range of that pass from k_split_pack
-// (none past the pass count); the segment count goes to P.m.sseg in that case.
+// (none past the pass count).  Only merge parts on the split path get a segment
+// (the list is compacted: on many-merge levels most merges are below the
+// threshold); the count goes to P.m.sseg, which the digit and product kernels read.
 __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t g0, int64_t g1, int pass) {
   __shared__ int64_t sc[4][32];
   const int S = P.split_slices;
@@ -183,23 +185,29 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
     const bool live = pass < P.m.spass[0];
     g0 = live ? P.m.spass[1 + 2 * pass] : 0;
     g1 = live ? P.m.spass[2 + 2 * pass] : 0;
-    if (threadIdx.x == 0) *P.m.sseg = 2 * (g1 - g0);
   }
   const int64_t M = g1 - g0, items = 2 * M;
   const int64_t per = (items + blockDim.x - 1) / blockDim.x;
   const int64_t w0 = min(items, (int64_t)threadIdx.x * per), w1 = min(items, w0 + per);
-  int64_t cta = 0, ctb = 0, ctt = 0, cel = 0;
+  int64_t cta = 0, ctb = 0, ctt = 0, cel = 0, cns = 0;
   for (int64_t w = w0; w < w1; ++w) {
     int64_t ta, tb, tt, el;
     split_seg_counts(P, level, g0 + w / 2, S, (int)(w & 1), ta, tb, tt, el);
     cta += ta; ctb += tb; ctt += tt; cel += el;
+    cns += el > 0 ? 1 : 0;
   }
   int64_t v[4] = {cta, ctb, ctt, cel};
   block_excl_scan4(v, sc);
-  int64_t ia = v[0], ib = v[1], it = v[2], e = v[3];
+  __syncthreads();
+  int64_t vn[4] = {cns, 0, 0, 0};
+  block_excl_scan4(vn, sc);
+  int64_t ia = v[0], ib = v[1], it = v[2], e = v[3], ns = vn[0];
   for (int64_t w = w0; w < w1; ++w) {
     const int64_t g = g0 + w / 2;
     const int p = (int)(w & 1);
+    int64_t ta, tb, tt, el;
+    split_seg_counts(P, level, g, S, p, ta, tb, tt, el);
+    if (el == 0) continue;
     const Node nd = make_node(P, level, g);
     const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
     const int K = P.m.K[g];
@@ -225,8 +233,6 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
     sg.it_a = ia;
     sg.it_b = ib;
     sg.it_t = it;
-    int64_t ta, tb, tt, el;
-    split_seg_counts(P, level, g, S, p, ta, tb, tt, el);
     sg.a_img = e;
     sg.b_img = e + ta * S * kATileElems;
     if (el > 0 && P.stats) {
@@ -236,9 +242,10 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
       atomicAdd(&P.stats->split_bytes, 2ull * S * (r * kq + kq * kc) + 8ull * r * kc);
     }
     ia += ta; ib += tb; it += tt; e += el;
-    P.segs[w] = sg;
+    P.segs[ns++] = sg;
   }
   if (threadIdx.x == blockDim.x - 1) {
+    *P.m.sseg = ns;
     GemmSeg last;
     memset(&last, 0, sizeof(last));
     last.it_a = ia;
@@ -249,7 +256,7 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
       last.it_a = last.it_b = last.it_t = 0;
       set_status(P.status, TDC_EUNSUPPORTED);
     }
-    P.segs[items] = last;
+    P.segs[ns] = last;
   }
 }
 
@@ -716,8 +723,8 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, i
   k_split_segs<<<1, 1024, 0, s>>>(P, L.level, g0, g1, pass);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int nseg = (int)(2 * (g1 - g0));
-  const int64_t* dn = pass >= 0 ? P.m.sseg : nullptr;
+  const int nseg = (int)(2 * (g1 - g0));  // bound; the kernels read the compacted count
+  const int64_t* dn = P.m.sseg;
   e = launch_split_digits(P.segs, nseg, dn, P.split_slices, P.img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
