@@ -212,3 +212,42 @@ def test_c2_toeplitz_16384_sampled(tdc):
     V = np.sqrt(2.0 / (n + 1)) * torch.sin(j * m[None, :] * np.pi / (n + 1))
     dots = torch.abs(torch.sum(V * Qs, dim=0))
     assert torch.max(torch.abs(dots - 1.0)).item() <= 1e-6
+
+
+def test_calls_from_two_host_threads_on_two_streams(tdc):
+    """Each host thread gets its own internal products stream; two eigensolves issued
+    at the same time from two threads on two caller streams give the results of the
+    same calls made one after the other."""
+    import threading
+    cases = [inputs.uniform_tridiag(1500, 11), inputs.c4_tridiag(1800, 12)]
+    o = tdc.default_opts(leaf=32)
+    ref = []
+    for d, e in cases:
+        lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o, check=True)
+        ref.append((lam.cpu().numpy(), Q.cpu().numpy()))
+    out = [None, None]
+    errors = []
+
+    def work(k):
+        try:
+            s = torch.cuda.Stream()
+            d, e = cases[k]
+            with torch.cuda.stream(s):
+                dt, et = torch.tensor(d, device=DEV), torch.tensor(e, device=DEV)
+                for _ in range(3):
+                    lam, Q = tdc.eig(dt, et, o, stream=s)
+                s.synchronize()
+            out[k] = (lam.cpu().numpy(), Q.cpu().numpy())
+        except Exception as exc:  # reported below, on the test's thread
+            errors.append(exc)
+
+    threads = [threading.Thread(target=work, args=(k,)) for k in range(2)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    assert tdc.sync_status() == 0
+    for k in range(2):
+        assert np.array_equal(out[k][0], ref[k][0])
+        assert np.array_equal(out[k][1], ref[k][1])
