@@ -306,7 +306,7 @@ struct LevelLaunch {
 cudaError_t launch_dmod(const Plan& P, cudaStream_t s);
 cudaError_t launch_leaves(const Plan& P, int64_t nleaves, int max_leaf, cudaStream_t s);
 // levels with at least this many slots also run the thread-per-root kernels
-constexpr int64_t kSmallMinSlots = 65536;
+constexpr int64_t kSmallMinSlots = 32768;
 cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_t s);
