@@ -20,7 +20,11 @@
  *     allocates no device memory on these paths;
  *   - matrices are column-major FP64 with a leading dimension argument;
  *   - work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
- *     stream) and the call returns without synchronising;
+ *     stream) and the call returns without synchronising.  The eigensolvers
+ *     also use a second, high-priority stream of the calling host thread
+ *     (created on first use and kept) for each level's products, forked from
+ *     and joined back into `stream` with events: the call stays ordered on
+ *     `stream` and can be captured in a CUDA graph like single-stream work;
  *   - the return value is a status: TDC_OK (0); -i when argument i (1-based)
  *     is invalid, checked on the host before anything is enqueued; or one of
  *     the TDC_E* codes below.  Device-side failures (secular non-convergence,
