@@ -408,16 +408,19 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 // The tensor-core GEMM over the digit images: one CTA per SM, persistent over
 // the tile list, three roles in separate warps so that no role waits on another
 // one's bookkeeping:
-//   warp 5 (one thread)  producer: bulk copies of one k-step (S A-slices + S
+//   warp 9 (one thread)  producer: bulk copies of one k-step (S A-slices + S
 //                        B-slices, contiguous) into a kStages ring, completion
 //                        on full[st]; a stage is reused once empty[st] fires;
-//   warp 4 (one thread)  MMA issuer: waits full[st], issues the S wide MMAs of the
+//   warp 8 (one thread)  MMA issuer: waits full[st], issues the S wide MMAs of the
 //                        step, commits them to empty[st]; after a tile's last
 //                        step commits to tfull, and starts the next tile only
 //                        after the epilogue has released the accumulators
 //                        (tempty);
-//   warps 0-3            epilogue: TMEM lane quarter w of the tile, the S level
-//                        accumulators combined in FP64, released, then stored.
+//   warps 0-7            epilogue: warp w takes TMEM lane quarter w mod 4 (the
+//                        lanes a warp may read) and column half w / 4 of the
+//                        tile, combines the S level accumulators, releases
+//                        them, then stores (two warps per quarter halve the
+//                        epilogue, which sets the time of shallow tiles).
 // The producer runs ahead into the next tile while the epilogue drains, and S is
 // a compile-time constant so that the issue loop is straight-line code (every
 // descriptor a constant offset of the stage base).  Every wait is bounded; a
@@ -425,7 +428,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 // reports TDC_ETIMEOUT after its copies and MMAs in flight have landed.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kMmaWarp = 4, kLoadWarp = 5, kSplitThreads = 192;
+constexpr int kEpiWarps = 8, kMmaWarp = 8, kLoadWarp = 9, kSplitThreads = 320;
 
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, long long budget,
                                              volatile int* fail) {
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       umma::mbar_init(&empty[i], 1);
     }
     umma::mbar_init(tfull, 1);
-    umma::mbar_init(tempty, 4);
+    umma::mbar_init(tempty, kEpiWarps);
     umma::mbar_init(done, 1);
     umma::fence_mbar_init();
     s_fail = 0;
@@ -596,7 +599,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
     // field (I != 0 gives |I| >= 1, so the result stays normal); otherwise, e.g.
     // for the adjoint's column-scaled products, in FP64 as written.
     int it = 0;
-    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    const int quarter = warp & 3, c0 = (warp >> 2) * 32;
+    const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++it) {
       const TileRef t = tile_ref(segs, nseg, w);
       const bool okw = __all_sync(0xffffffffu, wait_or_fail(tfull, (uint32_t)(it & 1), budget, vfail));
@@ -605,9 +609,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
         break;
       }
       umma::tc_fence_after();
-      double val[BN];
-#pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 32) {
+      double val[32];
+      {
         long long hi[32];
         float lo[32];
 #pragma unroll
@@ -646,22 +649,22 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           for (int i = 0; i < 32; ++i) {
             const long long I = hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]);
             const long long b = __double_as_longlong(__ll2double_rn(I)) - (58ll << 52);
-            val[c0 + i] = I == 0 ? 0.0 : __longlong_as_double(b);
+            val[i] = I == 0 ? 0.0 : __longlong_as_double(b);
           }
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) val[c0 + i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+          for (int i = 0; i < 32; ++i) val[i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
         }
       }
       umma::tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty);
       const GemmSeg& sg = *t.sg;
-      const int row = t.rt * BM + warp * 32 + lane;
+      const int row = t.rt * BM + quarter * 32 + lane;
       if (row < sg.rows) {
 #pragma unroll
-        for (int i = 0; i < BN; ++i) {
-          const int j = t.ct * BN + i;
+        for (int i = 0; i < 32; ++i) {
+          const int j = t.ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
             sg.C[row + (int64_t)pos * sg.ldc] = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
