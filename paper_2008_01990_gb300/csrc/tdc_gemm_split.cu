@@ -408,18 +408,18 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 // The tensor-core GEMM over the digit images: one CTA per SM, persistent over
 // the tile list, three roles in separate warps so that no role waits on another
 // one's bookkeeping:
-//   warp 9 (one thread)  producer: bulk copies of one k-step (S A-slices + S
+//   warp 17 (one thread) producer: bulk copies of one k-step (S A-slices + S
 //                        B-slices, contiguous) into a kStages ring, completion
 //                        on full[st]; a stage is reused once empty[st] fires;
-//   warp 8 (one thread)  MMA issuer: waits full[st], issues the S wide MMAs of the
+//   warp 16 (one thread) MMA issuer: waits full[st], issues the S wide MMAs of the
 //                        step, commits them to empty[st]; after a tile's last
 //                        step commits to tfull, and starts the next tile only
 //                        after the epilogue has released the accumulators
 //                        (tempty);
-//   warps 0-7            epilogue: warp w takes TMEM lane quarter w mod 4 (the
-//                        lanes a warp may read) and column half w / 4 of the
+//   warps 0-15           epilogue: warp w takes TMEM lane quarter w mod 4 (the
+//                        lanes a warp may read) and column quarter w / 4 of the
 //                        tile, combines the S level accumulators, releases
-//                        them, then stores (two warps per quarter halve the
+//                        them, then stores (four warps per lane quarter cut the
 //                        epilogue, which sets the time of shallow tiles).
 // The producer runs ahead into the next tile while the epilogue drains, and S is
 // a compile-time constant so that the issue loop is straight-line code (every
@@ -428,7 +428,11 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 // reports TDC_ETIMEOUT after its copies and MMAs in flight have landed.
 // ---------------------------------------------------------------------------
 namespace {
-constexpr int kEpiWarps = 8, kMmaWarp = 8, kLoadWarp = 9, kSplitThreads = 320;
+constexpr int kEpiWarps = 16, kMmaWarp = 16, kLoadWarp = 17, kSplitThreads = 576;
+constexpr int kEpiCols = BN / (kEpiWarps / 4);  // columns per epilogue warp
+static_assert(kEpiCols == 16 || kEpiCols == 32, "epilogue column split");
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[16]) { umma::tmem_ld16(taddr, v); }
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[32]) { umma::tmem_ld32(taddr, v); }
 
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, long long budget,
                                              volatile int* fail) {
@@ -599,7 +603,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
     // field (I != 0 gives |I| >= 1, so the result stays normal); otherwise, e.g.
     // for the adjoint's column-scaled products, in FP64 as written.
     int it = 0;
-    const int quarter = warp & 3, c0 = (warp >> 2) * 32;
+    const int quarter = warp & 3, c0 = (warp >> 2) * kEpiCols;
     const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++it) {
       const TileRef t = tile_ref(segs, nseg, w);
@@ -609,12 +613,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
         break;
       }
       umma::tc_fence_after();
-      double val[32];
+      double val[kEpiCols];
       {
-        long long hi[32];
-        float lo[32];
+        long long hi[kEpiCols];
+        float lo[kEpiCols];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < kEpiCols; ++i) {
           hi[i] = 0;
           lo[i] = 0.0f;
         }
@@ -622,38 +626,38 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
 #pragma unroll
           for (int m = 0; m < 5; ++m) {
             if (m < S) {
-              float v[32];
-              umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
+              float v[kEpiCols];
+              tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
 #pragma unroll
-              for (int i = 0; i < 32; ++i) hi[i] = hi[i] * 256 + (long long)__float2int_rn(v[i]);
+              for (int i = 0; i < kEpiCols; ++i) hi[i] = hi[i] * 256 + (long long)__float2int_rn(v[i]);
             } else {
 #pragma unroll
-              for (int i = 0; i < 32; ++i) hi[i] *= 256;
+              for (int i = 0; i < kEpiCols; ++i) hi[i] *= 256;
             }
           }
 #pragma unroll
           for (int m = 6; m >= 5; --m) {
             if (m < S) {
-              float v[32];
-              umma::tmem_ld32(tl + (uint32_t)(m * BN + c0), v);
+              float v[kEpiCols];
+              tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
 #pragma unroll
-              for (int i = 0; i < 32; ++i) lo[i] = fmaf(lo[i], 0.00390625f, v[i]);
+              for (int i = 0; i < kEpiCols; ++i) lo[i] = fmaf(lo[i], 0.00390625f, v[i]);
             }
           }
         }
         bool fits = true;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
+        for (int i = 0; i < kEpiCols; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
         if (__all_sync(0xffffffffu, fits)) {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < kEpiCols; ++i) {
             const long long I = hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]);
             const long long b = __double_as_longlong(__ll2double_rn(I)) - (58ll << 52);
             val[i] = I == 0 ? 0.0 : __longlong_as_double(b);
           }
         } else {
 #pragma unroll
-          for (int i = 0; i < 32; ++i) val[i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+          for (int i = 0; i < kEpiCols; ++i) val[i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
         }
       }
       umma::tc_fence_before();
@@ -663,7 +667,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       const int row = t.rt * BM + quarter * 32 + lane;
       if (row < sg.rows) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < kEpiCols; ++i) {
           const int j = t.ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
