@@ -1,15 +1,21 @@
 // tdc_merge.cu -- the merge step of Cuppen's divide and conquer on the GPU,
 // level by level over every node of every problem in the plan:
 //   k_dmod      corner modification of the split points (Eq. (T2))
-//   k_leaf      leaf eigensolves, one warp per leaf (Algorithm 1, "QR")
-//   k_prepare   z gather (Eq. (T3)), merge of the two sorted spectra,
-//               deflation scan (Section 3.2, Eq. (T3-def)), compaction
+//   k_leaf      leaf eigensolves (Algorithm 1, "QR"): two warps per leaf, or
+//   k_leaf_multi  a lane per leaf for leaves of at most 32 rows
+//   k_prepare   z (Eq. (T3)) from the children's boundary rows, merge of the
+//               two sorted spectra, deflation scan (Section 3.2, Eq. (T3-def)),
+//               compaction
+//   k_boundary_rot  the children's boundary rows through the deflating rotations
 //   k_rotate    plane rotations of deflation applied to Q's columns
-//   k_secular   secular equation (Eq. (secular)), one warp per root, FP64,
-//               roots stored as (origin pole, offset) (Eq. (d-lambda))
-//   k_lowner    zhat recomputed from (d, lambda), one warp per pole
-//   k_colnorm   normalisers s_j of the Cauchy-like Qhat (Eq. (Q_Cauchy))
+//   k_secular   secular equation (Eq. (secular)), one warp per root (a thread
+//               per root for small merges on many-merge levels), FP64, roots
+//               stored as (origin pole, offset) (Eq. (d-lambda))
+//   k_lowner    zhat recomputed from (d, lambda), one warp (or thread) per pole
+//   k_colnorm   normalisers s_j of the Cauchy-like Qhat (Eq. (Q_Cauchy)) and,
+//               below the top level, the node's boundary rows
 //   k_finalize  ascending order of all eigenvalues of the node, column targets
+//   k_boundary_out  boundary rows in output order
 //   k_copy_defl deflated eigenvectors copied to their columns
 //   k_sign_out  sign convention and eigenvalue output
 #include <float.h>
