@@ -4,7 +4,10 @@
 // The tree of a problem of order n has depth t (the smallest t with
 // ceil(n/2^t) <= leaf) and node boundaries floor(i n / 2^l) on level l
 // (Algorithm 1's recursive split, written level by level).  Every kernel of a
-// merge level processes all nodes of that level of all problems at once.
+// merge level processes all nodes of that level of all problems at once; each
+// level's roots side runs on the caller's stream and its products side on a
+// second stream, so that the roots of one level overlap the products of the
+// level below (run_plan).
 #include <algorithm>
 #include <array>
 #include <cstdio>

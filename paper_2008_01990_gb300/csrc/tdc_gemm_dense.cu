@@ -8,10 +8,12 @@
 // column j goes to the node's eigenvector column posr[j].
 //
 // One CTA computes a 128 x 64 tile with 256 threads (8 x 4 outputs each) on
-// the FP64 pipe; per 16-deep k-step it stages the Qtilde tile in shared memory
-// and generates the 16 x 64 Qhat tile there (8 FP64 operations per entry,
-// amortised over 128 rows).  Tiles of all merges of the level form one work
-// list (prefix in MergeInfo::tiles) that a fixed grid walks.
+// the FP64 pipe -- 32 x 32 (2 x 2 each) for merges of order <= 128, whose halves
+// have at most 64 rows; per 16-deep k-step it stages the Qtilde tile in shared
+// memory and generates the 16 x 64 (16 x 32) Qhat tile there (8 FP64 operations
+// per entry, amortised over the tile's rows).  Tiles of all merges of the level
+// form one work list (prefix in MergeInfo::tiles) that a fixed grid walks.
+// Merges of order <= 32 take a warp each instead (k_gemm_tiny).
 #include <float.h>
 
 #include "tdc_common.cuh"

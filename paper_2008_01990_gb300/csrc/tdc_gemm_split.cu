@@ -28,6 +28,8 @@
 // costs about the same issue time for any N up to 128, so the S(S+1)/2 digit
 // products of a step are issued as S wide MMAs (A_s against the stacked B slices,
 // N = 64 (S - s), split at 256): 10 MMAs per step for S = 7 instead of 28.
+// Sixteen epilogue warps read the accumulators (four per TMEM lane quarter):
+// on shallow tiles the epilogue, not the MMAs, sets the time.
 #include <float.h>
 
 #include "tdc_common.cuh"
