@@ -128,6 +128,14 @@ int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, in
 // One block: each thread counts the digit tiles, output tiles and image elements
 // of a contiguous range of merges, a block scan gives every range its offsets,
 // then the threads write their segments.
+// When every non-deflated pole has support in both halves (cross rotations pair
+// each pole of one child with one of the other, as for equal spectra), the two
+// pole lists are the same and the bottom part reuses the top part's Qhat image.
+__device__ __forceinline__ bool shared_b(const Plan& P, int64_t g) {
+  const int K = P.m.K[g];
+  return P.m.ntop[g] == K && P.m.nbot[g] == K;
+}
+
 __device__ __forceinline__ void split_seg_counts(const Plan& P, int level, int64_t g, int S, int p, int64_t& ta,
                                                  int64_t& tb, int64_t& tt, int64_t& el) {
   ta = tb = tt = el = 0;
@@ -138,7 +146,7 @@ __device__ __forceinline__ void split_seg_counts(const Plan& P, int level, int64
   const int64_t rows = p ? n - n1 : n1, kk = p ? P.m.nbot[g] : P.m.ntop[g];
   const int64_t RT = cdiv(rows, BM), KB = cdiv(kk, BK), CT = cdiv(K, BN);
   ta = RT * KB;
-  tb = CT * KB;
+  tb = (p == 1 && shared_b(P, g)) ? 0 : CT * KB;
   tt = RT * CT;
   el = ta * S * kATileElems + tb * S * kBTileElems;
 }
@@ -237,6 +245,11 @@ __global__ void __launch_bounds__(1024) k_split_segs(Plan P, int level, int64_t 
     sg.it_t = it;
     sg.a_img = e;
     sg.b_img = e + ta * S * kATileElems;
+    if (p == 1 && tb == 0) {  // the top part's image: it ends where this part's starts
+      int64_t ta0, tb0, tt0, el0;
+      split_seg_counts(P, level, g, S, 0, ta0, tb0, tt0, el0);
+      sg.b_img = e - el0 + ta0 * S * kATileElems;
+    }
     if (el > 0 && P.stats) {
       const unsigned long long r = (unsigned long long)sg.rows, kq = (unsigned long long)sg.kk,
                                kc = (unsigned long long)K;
