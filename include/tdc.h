@@ -149,7 +149,7 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
  * tdc_eig minus the workspace and uses instead a fixed 24 MiB array in the
  * library's own device memory (a file-scope __device__ array that every GPU which
  * loads the library holds until the process exits).  That covers orders up to
- * about n = 1750 with the FP64 merge (whatever tdc_workspace_size(n, o) fits in
+ * about n = 1730 with the FP64 merge (whatever tdc_workspace_size(n, o) fits in
  * 24 MiB); with merge_mode AUTO the FP64 merge is used whenever the split path's
  * digit images would not fit, and larger n returns TDC_ETOOLARGE before
  * anything is enqueued.  The first call on each
