@@ -452,7 +452,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     const size_t a2 = mark();
     if (err == cudaSuccess) err = launch_lowner(P, LL, s);
     if (err == cudaSuccess) err = launch_finalize(P, LL, s);
-    if (err == cudaSuccess) err = launch_boundary_rows(P, LL, s);
+    if (err == cudaSuccess) err = launch_boundary_out(P, LL, s);
     const size_t a3 = mark();
     span(1, a0, a1);
     span(2, a1, a2);

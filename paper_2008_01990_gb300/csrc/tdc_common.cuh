@@ -310,7 +310,7 @@ constexpr int64_t kSmallMinSlots = 32768;
 cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_rotate(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_t s);
-cudaError_t launch_boundary_rows(const Plan& P, const LevelLaunch& L, cudaStream_t s);
+cudaError_t launch_boundary_out(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_secular(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, cudaStream_t s);

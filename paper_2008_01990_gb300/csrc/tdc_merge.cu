@@ -2064,7 +2064,7 @@ cudaError_t launch_boundary_rot(const Plan& P, const LevelLaunch& L, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t launch_boundary_rows(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
+cudaError_t launch_boundary_out(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   if (L.level == 0 || L.nslots == 0) return cudaSuccess;
   k_boundary_out<<<dim3((unsigned)L.merges, (unsigned)((L.max_n + 255) / 256)), 256, 0, s>>>(P, L.level);
   return cudaGetLastError();
