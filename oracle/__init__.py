@@ -74,7 +74,13 @@ def _load():
     if _lib is not None:
         return _lib
     build()
-    lib = ctypes.CDLL(_LIB)
+    _lib = _bind(ctypes.CDLL(_LIB))
+    return _lib
+
+
+def _bind(lib):
+    """Declare the C signatures on a loaded copy of the oracle library (the tests
+    also bind copies built from the source with a planted mistake)."""
     P = ctypes.c_void_p
     i64 = ctypes.c_int64
     ci = ctypes.c_int
@@ -100,7 +106,6 @@ def _load():
     lib.orc_eig.restype = ci
     lib.orc_sign_normalise.argtypes = [ci, P, i64]
     lib.orc_gemm.argtypes = [ci, ci, ci, P, i64, P, i64, P, i64]
-    _lib = lib
     return lib
 
 

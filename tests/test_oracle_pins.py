@@ -250,6 +250,27 @@ def test_deflation_type2_duplicate_poles(orc):
     assert np.allclose(Q.T @ Q, np.eye(n), atol=1e-15)
 
 
+def test_deflation_type2_near_poles_small_weight(orc):
+    # Section 3.2: poles 1e-7 apart whose weight ratio is 3e-9 deflate by one rotation
+    # (|t c s| ~ 3e-16 is below the tolerance) although neither weight is negligible on its
+    # own.  The rotated column must then be an eigenvector of Q^T M Q for the pole left
+    # in its place, up to the deflation tolerance, and the kept pole must carry the weight.
+    D = np.array([-0.8, -0.2, 0.1, 0.3, 0.3 + 1e-7, 0.6, 0.9])
+    z = np.array([0.4, 0.35, 0.3, 1e-9, 0.5, 0.45, 0.42])
+    z /= np.linalg.norm(z)
+    rho = 1.0
+    K, kept, defl, D2, z2, Q, t1, t2 = orc.deflate(D, z, rho)
+    assert (t1, t2, K) == (0, 1, 6)
+    assert defl.tolist() == [3]
+    M = np.diag(D) + rho * np.outer(z, z)
+    Mr = Q.T @ M @ Q
+    row = Mr[3].copy()
+    row[3] -= D2[3]
+    assert np.abs(row).max() <= 16 * EPS
+    assert abs(D2[3] - 0.3) <= 1e-15 and abs(D2[4] - (0.3 + 1e-7)) <= 1e-15
+    assert z2[3] == 0 and abs(z2[4] - np.hypot(z[3], z[4])) <= EPS
+
+
 def test_deflation_everything_when_rho_zero(orc):
     n = 6
     K, kept, defl, *_ = orc.deflate(np.arange(n, dtype=float), np.ones(n) / np.sqrt(n), 0.0)
