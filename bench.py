@@ -136,7 +136,21 @@ def workload(name: str):
     if name == "c4_32768":
         d, e = inputs.c4_tridiag(32768, 4)
         return d, e, 64, "d uniform(0,1), e=1, n=32768 leaf 64 seed 4"
+    # the closed-form and spherical-harmonic families of Examples 2 and 3 at n = 30000
+    if name == "clement30000":
+        d, e = inputs.clement_tridiag(30000)
+        return d, e, 64, "Clement/Kac, e_i = sqrt(i(n-i)), n=30000 leaf 64"
+    if name == "hermite30000":
+        d, e = inputs.hermite_tridiag(30000)
+        return d, e, 64, "Hermite, e_i = sqrt(i), n=30000 leaf 64"
+    if name == "sht30000":
+        d, e = inputs.sht_tridiag(30000)
+        return d, e, 64, "spherical-harmonic transform (Example 3, m = n), n=30000 leaf 64"
     raise ValueError(name)
+
+
+FAMILY = {"toeplitz16384": "toeplitz", "toeplitz4096": "toeplitz", "uniform1024": "uniform", "c4_32768": "c4",
+          "clement30000": "clement", "hermite30000": "hermite", "sht30000": "sht"}
 
 
 def cpu_baseline(wl: str, budget_s: float = 20.0):
@@ -151,7 +165,7 @@ def cpu_baseline(wl: str, budget_s: float = 20.0):
     d_full, e_full, leaf, desc = workload(wl)
     n_full = d_full.size
     n = min(n_full, 2048)
-    fam = {"toeplitz16384": "toeplitz", "toeplitz4096": "toeplitz", "uniform1024": "uniform", "c4_32768": "c4"}[wl]
+    fam = FAMILY[wl]
     while True:
         d, e = inputs.family(fam, n, 4 if fam == "c4" else 1)
         t0 = time.perf_counter()
@@ -504,6 +518,10 @@ def run_ours(args):
         k = torch.arange(1, n + 1, dtype=torch.float64, device=dev)
         ref = torch.sort(2.0 + 2.0 * torch.cos(k * np.pi / (n + 1))).values
         lam_err = torch.max(torch.abs(lam - ref)).item() / 4.0
+    elif args.workload.startswith("clement"):
+        # eigenvalues -(n-1), -(n-3), ..., n-1; ||T||_2 = n - 1
+        ref = torch.arange(-(n - 1), n, 2, dtype=torch.float64, device=dev)
+        lam_err = torch.max(torch.abs(lam - ref)).item() / (n - 1)
     if rank != 0:
         if ws_n > 1:
             dist.destroy_process_group()
@@ -551,7 +569,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
-                                                          "batched4096", "backward256"])
+                                                          "batched4096", "backward256", "clement30000",
+                                                          "hermite30000", "sht30000"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (default: the workload's)")

@@ -55,15 +55,25 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
 #define TDC_ETOOLARGE (-107)   /* problem needs more than the fixed scratch of tdc_eig_noalloc */
 
 /* merge modes: how the eigenvector update Q * U is computed */
-#define TDC_MERGE_AUTO 0        /* library choice (structured above structured_min_K) */
+#define TDC_MERGE_AUTO 0        /* library choice: the split path for merges with K >= split_min_K, FP64 below */
 #define TDC_MERGE_DENSE 1       /* FP64 GEMM, U generated from its generators in the producer */
 #define TDC_MERGE_STRUCTURED 2  /* near-diagonal tiles dense, off-diagonal tiles SRRSC-compressed */
 #define TDC_MERGE_SPLIT 3       /* BF16 slice products on tcgen05 tensor cores, FP32/FP64 accumulation */
+/* Accuracy of the split path (SPLIT and AUTO): the digit products of one level are
+ * summed in FP32 accumulators, exact only while each level's sum stays below 2^24.
+ * On random and weakly structured spectra (tridiag(1,2,1), uniform, d ~ U(0,1) with
+ * e = 1) the residual and orthogonality ratios ||TQ - Q Lam||_1 / (n ||T|| eps) and
+ * ||Q^T Q - I||_1 / (n eps) stay below 2.  On matrices whose eigenvectors are smooth
+ * and deflate little (Clement/Kac, Hermite, spherical-harmonic) level sums exceed
+ * 2^24 from order 16384 on, and the orthogonality ratio grows to 9.2e3
+ * (spherical-harmonic, n = 16384) and 1.9e4 to 1.1e5 (the three, n = 30000); with
+ * TDC_MERGE_DENSE it is 0.2 (spherical-harmonic, n = 30000).  Use TDC_MERGE_DENSE
+ * for such inputs. */
 
 typedef struct {
   int32_t leaf;             /* leaf size L in 2..64: the tree depth is the smallest t with ceil(n/2^t) <= L */
   int32_t merge_mode;       /* TDC_MERGE_* */
-  int32_t structured_min_K; /* AUTO: merges with K >= this use the structured path */
+  int32_t structured_min_K; /* STRUCTURED: merges with K >= this use the structured path, smaller ones FP64 */
   int32_t lr_tile;          /* tile size m of the structured path (multiple of 64) */
   double lr_tol;            /* SRRSC stopping tolerance, relative to the tile's largest entry */
   int32_t split_slices;     /* base-256 BF16 digits per operand on the split path (3..7) */

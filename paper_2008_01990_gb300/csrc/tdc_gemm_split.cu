@@ -9,14 +9,19 @@
 //     C = sum_{s+t <= S-1} 2^(-8(s+t+2)) (a_s . u_t),
 // and every product of digits is an integer of magnitude at most 2^16.  All
 // products of one level m = s+t accumulate in their own FP32 TMEM accumulator
-// over the whole reduction: by Cauchy-Schwarz on the unit-norm rows of A and
-// columns of Qhat the partial sums of levels 0 and 1 stay below 2^24 (exact in
-// FP32); the digits below the top one are zero-mean, so the partial sums of the
-// higher levels are random walks of about 2^12.4 sqrt((m+1) kk), far below 2^24
-// (signed-magnitude digits would not do: their mean follows sign(A U), which is
-// coherent for smooth eigenvectors).  The S level accumulators (S x 64 TMEM
-// columns) are combined in FP64 once per tile.  Dropped levels (m >= S) and the
-// rounded digits cost about 2^-8S absolute per entry.
+// over the whole reduction, which is exact while the level's partial sums stay
+// below 2^24.  By Cauchy-Schwarz on the unit-norm rows of A and columns of Qhat
+// the sums of levels 0 and 1 do; the digits below the top one are zero-mean, so on
+// random and weakly structured spectra the higher levels are random walks of about
+// 2^12.4 sqrt((m+1) kk), far below 2^24 (signed-magnitude digits would not do:
+// their mean follows sign(A U), which is coherent for smooth eigenvectors).  That
+// argument fails where small entries vary smoothly along k: a small entry's
+// leading digit is one of the lower ones and keeps its sign, and on the Clement,
+// Hermite and spherical-harmonic matrices of order 16384 the level-3 sums of the
+// level-1 merges exceed 2^24, so those products lose exactness (orthogonality
+// ratio about 1e4; the FP64 merge is the path for such inputs).  The S level
+// accumulators (S x 64 TMEM columns) are combined in FP64 once per tile.  Dropped
+// levels (m >= S) and the rounded digits cost about 2^-8S absolute per entry.
 //
 // Data flow per merge part: k_split_a writes the digits of the gathered A
 // columns, k_split_b generates Qhat from its generators in FP64 (once per entry)

@@ -1,0 +1,72 @@
+"""Accuracy on matrices whose eigenvectors are smooth and deflate little: the
+spherical-harmonic matrix of Example 3 at n = 16384 (leaf 64).
+
+The FP64 merge must meet the residual and orthogonality bounds there.  The split
+path (the AUTO default) does not yet: its FP32 level accumulators are exact only
+while each level's sum stays below 2^24, and on this matrix the level-3 sums of
+the merges one level below the top exceed it, so the product loses about four
+decimal digits (orthogonality ratio about 9e3).  That test is marked xfail so
+that it reports the state of the split path without stopping the suite; it turns
+into an unexpected pass once the accumulation is made exact for such inputs.
+Ratios are taken on 256 sampled columns, as in the benchmark."""
+import numpy as np
+import pytest
+import torch
+
+from helpers import EPS
+from paper_2008_01990_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+N = 16384
+
+
+@pytest.fixture(scope="module")
+def tdc():
+    from paper_2008_01990_gb300 import build, tdc as t
+    build.build()
+    t.lib()
+    return t
+
+
+def sampled_ratios(dt, et, lam, Q, ns=256):
+    """(||T q - lam q||_1 / (n ||T|| eps), ||Q^T q - e||_1 / (n eps)), max over sampled columns q."""
+    n = dt.numel()
+    g = np.random.default_rng(0)
+    cols = torch.tensor(np.sort(g.choice(n, ns, replace=False)), device=DEV)
+    Qs = Q[:, cols]
+    Tq = dt[:, None] * Qs
+    Tq[1:] += et[:, None] * Qs[:-1]
+    Tq[:-1] += et[:, None] * Qs[1:]
+    nT = max(abs(lam[0].item()), abs(lam[-1].item()))
+    res = torch.abs(Tq - Qs * lam[cols]).sum(dim=0).max().item() / (n * nT * EPS)
+    G = Qs.t() @ Q
+    G[torch.arange(ns, device=DEV), cols] -= 1.0
+    orth = torch.abs(G).sum(dim=1).max().item() / (n * EPS)
+    return res, orth
+
+
+def solve(tdc, mode):
+    d, e = inputs.sht_tridiag(N)
+    dt = torch.tensor(d, device=DEV)
+    et = torch.tensor(e, device=DEV)
+    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=64, merge_mode=mode), check=True)
+    return dt, et, lam, Q
+
+
+def test_sht_16384_fp64_merge(tdc):
+    dt, et, lam, Q = solve(tdc, tdc.MERGE_DENSE)
+    assert torch.all(lam[1:] >= lam[:-1])
+    # trace invariant: sum of the eigenvalues equals the trace
+    nT = max(abs(lam[0].item()), abs(lam[-1].item()))
+    assert abs(lam.sum().item() - dt.sum().item()) <= 1e-12 * N * nT
+    res, orth = sampled_ratios(dt, et, lam, Q)
+    assert res <= 50 and orth <= 50, (res, orth)
+
+
+@pytest.mark.xfail(strict=False, reason="split-path level sums exceed 2^24 on smooth eigenvectors (orthogonality ~9e3)")
+def test_sht_16384_split_path(tdc):
+    dt, et, lam, Q = solve(tdc, tdc.MERGE_AUTO)
+    res, orth = sampled_ratios(dt, et, lam, Q)
+    assert res <= 50 and orth <= 50, (res, orth)
