@@ -548,7 +548,7 @@ def run_ours(args):
         "K_per_level": stats["sum_K"],
         "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"]},
         "test_ratios": {"lam_err_over_normT": lam_err, "residual": res, "orthogonality": orth,
-                        "sampled_columns": 256},
+                        "sampled_columns": 256, "within_bounds": bool(res <= 50 and orth <= 50)},
         "gpu_launches": int(stats["launches"]) * args.steps,
         "clocks": clocks,
         "e2e": {"value": job_seconds_per_solve(e2e_ms, ws_n), "unit": "s", "h2d_bytes_per_step": 2 * 8 * n - 8,

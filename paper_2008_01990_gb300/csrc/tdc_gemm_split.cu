@@ -15,11 +15,12 @@
 // random and weakly structured spectra the higher levels are random walks of about
 // 2^12.4 sqrt((m+1) kk), far below 2^24 (signed-magnitude digits would not do:
 // their mean follows sign(A U), which is coherent for smooth eigenvectors).  That
-// argument fails where small entries vary smoothly along k: a small entry's
-// leading digit is one of the lower ones and keeps its sign, and on the Clement,
-// Hermite and spherical-harmonic matrices of order 16384 the level-3 sums of the
-// level-1 merges exceed 2^24, so those products lose exactness (orthogonality
-// ratio about 1e4; the FP64 merge is the path for such inputs).  The S level
+// argument fails in the rows next to a merge's split when the eigenvectors are
+// smooth: there the rows of A are nearly parallel to z, so A U sums the secular
+// terms z_k zhat_k / delta_kj, which share their sign over long runs of k.  On the
+// Clement, Hermite and spherical-harmonic matrices of order 16384 those level-3
+// sums exceed 2^24 and round (orthogonality ratio about 1e4; the FP64 merge is the
+// path for such inputs).  The S level
 // accumulators (S x 64 TMEM columns) are combined in FP64 once per tile.  Dropped
 // levels (m >= S) and the rounded digits cost about 2^-8S absolute per entry.
 //
