@@ -5,9 +5,10 @@ The FP64 merge must meet the residual and orthogonality bounds there.  The split
 path (the AUTO default) does not yet: its FP32 level accumulators are exact only
 while each level's sum stays below 2^24, and on this matrix the level-3 sums in
 the rows next to each split (where the eigenvector rows are nearly parallel to z)
-exceed it, so those rows carry errors near 1e-11 (orthogonality ratio about 9e3).  That test is marked xfail so
-that it reports the state of the split path without stopping the suite; it turns
-into an unexpected pass once the accumulation is made exact for such inputs.
+exceed it, so those rows carry errors near 1e-11 (orthogonality ratio about
+9e3).  That test is marked xfail so that it reports the state of the split path
+without stopping the suite; it turns into an unexpected pass once the
+accumulation is made exact for such inputs.
 Ratios are taken on 256 sampled columns, as in the benchmark."""
 import numpy as np
 import pytest
