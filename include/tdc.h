@@ -82,6 +82,10 @@ typedef struct {
   int32_t sign_normalise;   /* 1: make the largest-magnitude entry of every column positive */
   int32_t collect_stats;    /* 1: record per-level statistics for tdc_get_stats (adds a sync) */
   int64_t spin_budget;      /* bounded-wait iteration cap for persistent kernels */
+  int32_t split_chunk_k;    /* SPLIT/AUTO: 0 (default) sums each level over a tile's whole reduction; a
+                               positive multiple of 16 drains the FP32 level sums into the 64-bit
+                               running sums every split_chunk_k terms, which bounds them for any order
+                               (requires split_slices = 7) */
 } tdc_opts;
 
 #define TDC_MAX_LEVELS 32

@@ -149,7 +149,7 @@ cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q,
     k_adj_segs<<<sgrid, 128, 0, s>>>(batch, n, kAdjSlices, Q, ldq, 1, sQ, Q_bar, ldq, sQb, cexp, W, nn, segs);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_seg_split(segs, batch, kAdjSlices, status, spin_budget, img, s);
+    e = launch_seg_split(segs, batch, kAdjSlices, status, spin_budget, img, 0, s);
     if (e != cudaSuccess) return e;
   } else {
     e = cudaMemsetAsync(W, 0, sizeof(double) * batch * nn, s);
@@ -162,7 +162,7 @@ cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q,
   k_adj_segs<<<sgrid, 128, 0, s>>>(batch, n, kAdjSlices, Q, 1, ldq, sQ, W, n, nn, cexp, R, nn, segs);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = launch_seg_split(segs, batch, kAdjSlices, status, spin_budget, img, s);
+  e = launch_seg_split(segs, batch, kAdjSlices, status, spin_budget, img, 0, s);
   if (e != cudaSuccess) return e;
   k_adj_dots<<<dim3((unsigned)((n * 32 + 255) / 256), batch), 256, 0, s>>>(n, R, nn, Q, ldq, sQ, d_bar, n, e_bar,
                                                                           n > 1 ? n - 1 : 1);

@@ -328,6 +328,8 @@ static int validate_opts(const tdc_opts* o) {
   if (o->lr_tile < 64 || (o->lr_tile % 64) != 0) return 1;
   if (o->split_slices < 3 || o->split_slices > 7) return 1;
   if (o->split_min_K < 1) return 1;
+  if (o->split_chunk_k < 0 || (o->split_chunk_k % 16) != 0) return 1;
+  if (o->split_chunk_k > 0 && o->split_slices != 7) return 1;
   if (o->spin_budget < 1) return 1;
   if (!(o->lr_tol > 0.0)) return 1;
   return 0;
@@ -365,6 +367,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   P.max_iter = o.max_iter;
   P.split_min_K = H.split_S ? o.split_min_K : 0;
   P.split_slices = H.split_S ? H.split_S : 7;
+  P.split_chunk_steps = o.split_chunk_k / 16;
   P.spin_budget = o.spin_budget;
   P.struct_min_K = H.struct_m ? o.structured_min_K : 0;
   P.struct_m = H.struct_m;
@@ -573,6 +576,7 @@ void tdc_default_opts(tdc_opts* o) {
   o->sign_normalise = 1;
   o->collect_stats = 0;
   o->spin_budget = 1 << 24;
+  o->split_chunk_k = 0;
 }
 
 int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
@@ -798,7 +802,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
     last.a_img = tot;
     k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
     err = cudaGetLastError();
-    if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, cs);
+    if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, op.split_chunk_k / 16, cs);
   }
   return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }

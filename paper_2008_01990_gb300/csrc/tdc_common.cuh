@@ -161,6 +161,7 @@ struct Plan {
   int32_t max_iter;
   int32_t split_min_K;  // merges with K >= this use the split path (0: never)
   int32_t split_slices; // BF16 digit slices per operand
+  int32_t split_chunk_steps;  // > 0: drain the split accumulators every this many k-steps
   GemmSeg* segs;        // 2 M + 1 segments of the current level (split and structured paths)
   __nv_bfloat16* img;   // digit images (split path)
   int64_t img_cap;      // capacity of img in elements
@@ -324,7 +325,7 @@ cudaError_t launch_split_pack(const Plan& P, const LevelLaunch& L, int max_pass,
 cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, int64_t g1, int pass, cudaStream_t s,
                               cudaEvent_t mid);
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
-                             __nv_bfloat16* img, cudaStream_t s);
+                             __nv_bfloat16* img, int chunk_steps, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);

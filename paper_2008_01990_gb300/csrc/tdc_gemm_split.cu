@@ -434,9 +434,9 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 //                        on full[st]; a stage is reused once empty[st] fires;
 //   warp 16 (one thread) MMA issuer: waits full[st], issues the S wide MMAs of the
 //                        step, commits them to empty[st]; after a tile's last
-//                        step commits to tfull, and starts the next tile only
-//                        after the epilogue has released the accumulators
-//                        (tempty);
+//                        step (with chunked drains: after every ck steps)
+//                        commits to tfull, and reuses the accumulators only
+//                        after the epilogue has released them (tempty);
 //   warps 0-15           epilogue: warp w takes TMEM lane quarter w mod 4 (the
 //                        lanes a warp may read) and column quarter w / 4 of the
 //                        tile, combines the S level accumulators, releases
@@ -492,10 +492,13 @@ __device__ __forceinline__ TileRef tile_ref(const GemmSeg* segs, int nseg, int64
 }
 }  // namespace
 
-template <int S>
+// kChunk: the accumulators are drained into the epilogue's running sums every ck
+// k-steps of a tile (the MMA warp waits for each drain), so that every level sum
+// covers at most 16 ck terms; without it they cover the tile's whole reduction.
+template <int S, bool kChunk>
 __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* segs, int nseg, const int64_t* dnseg,
                                                                  const __nv_bfloat16* img, int* status,
-                                                                 long long budget) {
+                                                                 long long budget, int ck) {
   if (dnseg) nseg = (int)*dnseg;
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t a_bytes = S * kATileElems * 2, b_bytes = S * kBTileElems * 2;
@@ -569,41 +572,49 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       const uint64_t desc0 = umma::sdesc(sbase, 128, BK * 16);
       for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x, ++it) {
         const TileRef t = tile_ref(segs, nseg, w);
-        if (it > 0 && !wait_or_fail(tempty, (uint32_t)((it - 1) & 1), budget, vfail)) {
-          ok = false;
-          break;
-        }
-        umma::tc_fence_after();
-        for (int kb = 0; kb < t.KB; ++kb, ++g) {
-          const int st = (int)(g % kStages);
-          if (!wait_or_fail(&full[st], (uint32_t)((g / kStages) & 1), budget, vfail)) {
+        // one accumulator hand-off per chunk of ck k-steps (kChunk), else per tile
+        const int nch = kChunk && t.KB > 0 ? (t.KB + ck - 1) / ck : 1;
+        int kb0 = 0;
+        for (int c = 0; c < nch; ++c) {
+          if (kChunk && c > 0) ++it;
+          if (it > 0 && !wait_or_fail(tempty, (uint32_t)((it - 1) & 1), budget, vfail)) {
             ok = false;
             break;
           }
           umma::tc_fence_after();
-          // The S B-slices are stacked along N in shared memory and level m's
-          // accumulator starts at TMEM column m*BN, so A_s against the stacked slices
-          // B_0..B_{S-1-s} (N = BN (S - s)) drops every product A_s B_t into level
-          // s+t: one wide MMA per A-slice (split at N = 256) instead of one per pair.
-          // Every operand descriptor is the stage-0 descriptor plus a constant, so
-          // the issue loop is a handful of integer adds per MMA.
-          const uint64_t dst = desc0 + (uint64_t)((st * stage_bytes) >> 4);
-#pragma unroll
-          for (int s = 0; s < S; ++s) {
-            const uint64_t ad = dst + (uint64_t)((s * kATileElems * 2) >> 4);
-#pragma unroll
-            for (int off = 0; off < BN * (S - s); off += 256) {
-              const int nn = BN * (S - s) - off < 256 ? BN * (S - s) - off : 256;
-              const uint64_t bd = dst + (uint64_t)((a_bytes + (off / BN) * kBTileElems * 2) >> 4);
-              umma::mma_bf16(tmem + s * BN + off, ad, bd, umma::idesc_bf16(BM, nn), (kb > 0 || s > 0) ? 1u : 0u);
+          const int kb1 = kChunk ? min(t.KB, kb0 + ck) : t.KB;
+          for (int kb = kb0; kb < kb1; ++kb, ++g) {
+            const int st = (int)(g % kStages);
+            if (!wait_or_fail(&full[st], (uint32_t)((g / kStages) & 1), budget, vfail)) {
+              ok = false;
+              break;
             }
+            umma::tc_fence_after();
+            // The S B-slices are stacked along N in shared memory and level m's
+            // accumulator starts at TMEM column m*BN, so A_s against the stacked slices
+            // B_0..B_{S-1-s} (N = BN (S - s)) drops every product A_s B_t into level
+            // s+t: one wide MMA per A-slice (split at N = 256) instead of one per pair.
+            // Every operand descriptor is the stage-0 descriptor plus a constant, so
+            // the issue loop is a handful of integer adds per MMA.
+            const uint64_t dst = desc0 + (uint64_t)((st * stage_bytes) >> 4);
+#pragma unroll
+            for (int s = 0; s < S; ++s) {
+              const uint64_t ad = dst + (uint64_t)((s * kATileElems * 2) >> 4);
+#pragma unroll
+              for (int off = 0; off < BN * (S - s); off += 256) {
+                const int nn = BN * (S - s) - off < 256 ? BN * (S - s) - off : 256;
+                const uint64_t bd = dst + (uint64_t)((a_bytes + (off / BN) * kBTileElems * 2) >> 4);
+                umma::mma_bf16(tmem + s * BN + off, ad, bd, umma::idesc_bf16(BM, nn), (kb > kb0 || s > 0) ? 1u : 0u);
+              }
+            }
+            umma::mma_commit(&empty[st]);
+            issued = true;
           }
-          umma::mma_commit(&empty[st]);
-          issued = true;
+          if (!ok) break;
+          if (kb1 > kb0) umma::mma_commit(tfull);
+          else mbar_arrive(tfull);
+          kb0 = kb1;
         }
-        if (!ok) break;
-        if (t.KB > 0) umma::mma_commit(tfull);
-        else mbar_arrive(tfull);
       }
       if (!ok) *vfail = 1;
       // every MMA issued has completed before the accumulators are released
@@ -628,6 +639,80 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
     const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++it) {
       const TileRef t = tile_ref(segs, nseg, w);
+      if constexpr (kChunk) {
+        // the same combination, accumulated over the tile's chunks: level m of a
+        // chunk adds P_m 2^(8(4-m)) to hi (m < 5, exact) or its share to lo
+        const int nch = t.KB > 0 ? (t.KB + ck - 1) / ck : 1;
+        long long hi[kEpiCols];
+        float lo[kEpiCols];
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i) {
+          hi[i] = 0;
+          lo[i] = 0.0f;
+        }
+        bool okc = true;
+        for (int c = 0; c < nch; ++c) {
+          if (c > 0) ++it;
+          okc = __all_sync(0xffffffffu, wait_or_fail(tfull, (uint32_t)(it & 1), budget, vfail));
+          if (!okc) break;
+          umma::tc_fence_after();
+          if (t.KB > 0) {
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+              if (m < S) {
+                float v[kEpiCols];
+                tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
+#pragma unroll
+                for (int i = 0; i < kEpiCols; ++i) hi[i] += (long long)__float2int_rn(v[i]) * (1ll << (8 * (4 - m)));
+              }
+            }
+#pragma unroll
+            for (int m = 6; m >= 5; --m) {
+              if (m < S) {
+                float v[kEpiCols];
+                tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
+#pragma unroll
+                for (int i = 0; i < kEpiCols; ++i) lo[i] += m == 6 ? v[i] * 0.00390625f : v[i];
+              }
+            }
+          }
+          umma::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(tempty);
+        }
+        if (!okc) {
+          if (lane == 0) *vfail = 1;
+          break;
+        }
+        double val[kEpiCols];
+        bool fits = true;
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
+        if (__all_sync(0xffffffffu, fits)) {
+#pragma unroll
+          for (int i = 0; i < kEpiCols; ++i) {
+            const long long I = hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]);
+            const long long b = __double_as_longlong(__ll2double_rn(I)) - (58ll << 52);
+            val[i] = I == 0 ? 0.0 : __longlong_as_double(b);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < kEpiCols; ++i) val[i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+        }
+        const GemmSeg& sg = *t.sg;
+        const int row = t.rt * BM + quarter * 32 + lane;
+        if (row < sg.rows) {
+#pragma unroll
+          for (int i = 0; i < kEpiCols; ++i) {
+            const int j = t.ct * BN + c0 + i;
+            if (j < sg.K) {
+              const int pos = sg.cpos ? sg.cpos[j] : j;
+              sg.C[row + (int64_t)pos * sg.ldc] = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+            }
+          }
+        }
+        continue;
+      }
       const bool okw = __all_sync(0xffffffffu, wait_or_fail(tfull, (uint32_t)(it & 1), budget, vfail));
       if (!okw) {
         if (lane == 0) *vfail = 1;
@@ -713,27 +798,32 @@ static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, const int6
   return cudaGetLastError();
 }
 
-template <int S>
+template <int S, bool kChunk>
 static cudaError_t launch_split_mma_s(const GemmSeg* segs, int nseg, const int64_t* dnseg, int* status,
-                                      long long budget, const __nv_bfloat16* img, int sms, cudaStream_t s) {
+                                      long long budget, const __nv_bfloat16* img, int sms, int ck, cudaStream_t s) {
   const int smem = kStages * S * (kATileElems + kBTileElems) * 2 + 128;
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S, kChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_gemm_split<S><<<sms, kSplitThreads, smem, s>>>(segs, nseg, dnseg, img, status, budget);
+  k_gemm_split<S, kChunk><<<sms, kSplitThreads, smem, s>>>(segs, nseg, dnseg, img, status, budget, ck);
   return cudaGetLastError();
 }
 
+// ck > 0: drain the accumulators every ck k-steps (seven digits only)
 static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S, int* status,
-                                    long long budget, const __nv_bfloat16* img, cudaStream_t s) {
+                                    long long budget, const __nv_bfloat16* img, int ck, cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ck > 0) {
+    if (S != 7) return cudaErrorInvalidValue;
+    return launch_split_mma_s<7, true>(segs, nseg, dnseg, status, budget, img, sms, ck, s);
+  }
   switch (S) {
-    case 3: return launch_split_mma_s<3>(segs, nseg, dnseg, status, budget, img, sms, s);
-    case 4: return launch_split_mma_s<4>(segs, nseg, dnseg, status, budget, img, sms, s);
-    case 5: return launch_split_mma_s<5>(segs, nseg, dnseg, status, budget, img, sms, s);
-    case 6: return launch_split_mma_s<6>(segs, nseg, dnseg, status, budget, img, sms, s);
-    case 7: return launch_split_mma_s<7>(segs, nseg, dnseg, status, budget, img, sms, s);
+    case 3: return launch_split_mma_s<3, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
+    case 4: return launch_split_mma_s<4, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
+    case 5: return launch_split_mma_s<5, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
+    case 6: return launch_split_mma_s<6, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
+    case 7: return launch_split_mma_s<7, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -756,14 +846,14 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, i
   e = launch_split_digits(P.segs, nseg, dn, P.split_slices, P.img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
-  return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, s);
+  return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, P.split_chunk_steps, s);
 }
 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
-                             __nv_bfloat16* img, cudaStream_t s) {
+                             __nv_bfloat16* img, int chunk_steps, cudaStream_t s) {
   cudaError_t e = launch_split_digits(segs_dev, nseg, nullptr, S, img, s);
   if (e != cudaSuccess) return e;
-  return launch_split_mma(segs_dev, nseg, nullptr, S, status, spin_budget, img, s);
+  return launch_split_mma(segs_dev, nseg, nullptr, S, status, spin_budget, img, chunk_steps, s);
 }
 
 }  // namespace tdc

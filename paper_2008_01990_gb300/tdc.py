@@ -45,6 +45,7 @@ class Opts(ctypes.Structure):
         ("sign_normalise", ctypes.c_int32),
         ("collect_stats", ctypes.c_int32),
         ("spin_budget", ctypes.c_int64),
+        ("split_chunk_k", ctypes.c_int32),
     ]
 
 

@@ -33,10 +33,13 @@ def test_default_opts_and_workspace(lib):
     from paper_2008_01990_gb300 import tdc
     o = tdc.default_opts()
     assert o.leaf == 32 and o.max_iter >= 1 and o.sign_normalise == 1
+    assert o.split_chunk_k == 0 and ctypes.sizeof(o) == 64
     w1 = tdc.workspace_size(1024, o)
     w2 = tdc.workspace_size(2048, o)
     assert 2048 * 2048 * 8 < w2 and w1 < w2
     assert tdc.workspace_size(0, o) > 0
+    # chunked drains of the split accumulators change no workspace
+    assert tdc.workspace_size(2048, tdc.default_opts(split_chunk_k=512)) == w2
 
 
 def test_host_argument_checks(lib):
@@ -65,7 +68,9 @@ def test_host_argument_checks(lib):
 
 @pytest.mark.parametrize("bad", [dict(leaf=1), dict(leaf=65), dict(merge_mode=4), dict(max_iter=0),
                                  dict(lr_tile=100), dict(split_slices=2), dict(split_slices=8),
-                                 dict(split_min_K=0), dict(spin_budget=0), dict(lr_tol=0.0)])
+                                 dict(split_min_K=0), dict(spin_budget=0), dict(lr_tol=0.0),
+                                 dict(split_chunk_k=8), dict(split_chunk_k=-16),
+                                 dict(split_chunk_k=512, split_slices=6)])
 def test_invalid_options_rejected_on_host(lib, bad):
     """Every option outside its documented range is refused before anything is
     enqueued (the workspace query validates the same way)."""
