@@ -1,0 +1,107 @@
+"""A model, in numpy, of the arithmetic of the split product (balanced base-256
+digits, one integer sum per level m = s + t, the epilogue's 64-bit / FP32
+combination, optionally drained every C terms), checked against facts fixed
+outside it: exact reconstruction of the digits, the FP64 product to the
+digits' rounding level, and the size of the level sums that the FP32
+accumulators must hold exactly (below 2^24).
+
+The smooth case is a rank-one problem with evenly spaced poles and a smooth
+positive z, and the row multiplied is the one parallel to z: the rows next to a
+merge's split behave like it on matrices with smooth eigenvectors.  Over the
+whole reduction its level-3 sums exceed 2^24 at K = 16384, which is the
+exactness defect of the product path's default schedule; drained every 256
+terms they stay below 2^23.  Verification only; the product path is CUDA."""
+import numpy as np
+import pytest
+
+S = 7
+
+
+def digits(x):
+    """Balanced base-256 digits of round(x 2^56): d_0 carries the rest, d_1..d_6 in [-128, 127]."""
+    F = np.rint(np.ldexp(np.asarray(x, dtype=np.float64), 56)).astype(np.int64)
+    G = F + np.int64(sum(128 << (8 * i) for i in range(6)))
+    out = [G >> 48]
+    for sh in range(40, -1, -8):
+        out.append(((G >> sh) & 255) - 128)
+    return out
+
+
+def level_sums(Ad, Ud, sl):
+    """Exact integer level sums P_m over the terms in slice sl (float64 holds them exactly)."""
+    return [sum(Ad[a][..., sl].astype(np.float64) @ Ud[m - a][sl].astype(np.float64) for a in range(m + 1))
+            for m in range(S)]
+
+
+def combine(A, U, chunk):
+    """C = 2^-48 hi + 2^-56 lo with hi = sum_m<5 P_m 2^(8(4-m)) (64-bit, exact) and
+    lo = P_5 + 2^-8 P_6, the sums drained every `chunk` terms; also the largest |P_m|."""
+    Ad, Ud = digits(A), digits(U)
+    K = A.shape[-1]
+    hi = 0
+    lo = 0.0
+    big = np.zeros(S)
+    for c0 in range(0, K, chunk):
+        P = level_sums(Ad, Ud, slice(c0, c0 + chunk))
+        big = np.maximum(big, [np.abs(p).max() for p in P])
+        hi = hi + sum(P[m].astype(np.int64) * (1 << (8 * (4 - m))) for m in range(5))
+        lo = lo + P[5] + P[6] / 256.0
+    return np.ldexp(hi.astype(np.float64), -48) + np.ldexp(lo, -56), big
+
+
+def test_digits_reconstruct_exactly():
+    g = np.random.default_rng(1)
+    x = np.concatenate([g.uniform(-1, 1, 4000), [1.0, -1.0, 0.0, 2.0 ** -57, -(2.0 ** -30), 1 - 2.0 ** -53]])
+    d = digits(x)
+    F = np.rint(np.ldexp(x, 56)).astype(np.int64)
+    rebuilt = sum(d[s].astype(np.int64) << (8 * (6 - s)) for s in range(S))
+    assert np.array_equal(rebuilt, F)
+    assert np.all(np.abs(d[0]) <= 256)
+    for s in range(1, S):
+        assert d[s].min() >= -128 and d[s].max() <= 127
+    # every digit is an integer that BF16 holds exactly (at most 8 significant bits)
+    for s in range(S):
+        v = np.abs(d[s])
+        v = v[v > 0]
+        assert np.all((v >> np.maximum(np.floor(np.log2(v)).astype(np.int64) - 7, 0)) << np.maximum(
+            np.floor(np.log2(v)).astype(np.int64) - 7, 0) == v)
+
+
+@pytest.mark.parametrize("chunk", [4096, 256])
+def test_combination_matches_fp64_product(chunk):
+    g = np.random.default_rng(2)
+    K = 4096
+    A = g.standard_normal((8, K))
+    A /= np.linalg.norm(A, axis=1, keepdims=True)
+    U = g.standard_normal((K, 16))
+    U /= np.linalg.norm(U, axis=0, keepdims=True)
+    C, big = combine(A, U, chunk)
+    # dropped levels s + t >= 7 and the digit rounding: about 2^-56 per term pair
+    assert np.abs(C - A @ U).max() <= 2.0 ** -50
+    assert big.max() < 2.0 ** 24
+
+
+def smooth_rank_one(orc, K):
+    k = np.arange(K)
+    D = np.linspace(-1.0, 1.0, K)
+    z = np.sin(np.pi * (k + 1) / (K + 1)) + 0.1
+    z /= np.linalg.norm(z)
+    org, tau, _, _ = orc.secular(D, z, 1.0, max_iter=2000)
+    zh = orc.lowner(D, z, 1.0, org, tau)
+    s = orc.colnorm(D, org, tau, zh)
+    cols = np.arange(0, K, 32)
+    U = zh[:, None] * s[None, cols] / ((D[:, None] - D[org[cols]][None, :]) - tau[None, cols])
+    return zh[None, :], U
+
+
+def test_smooth_row_level_sums_need_chunked_drains(orc):
+    A, U = smooth_rank_one(orc, 16384)
+    C_whole, big_whole = combine(A, U, 16384)
+    C_256, big_256 = combine(A, U, 256)
+    # the model's combination is exact either way (integer sums)
+    assert np.abs(C_whole - C_256).max() <= 2.0 ** -52
+    assert np.abs(C_256 - A @ U).max() <= 2.0 ** -48
+    # over the whole reduction the level-3 sums leave FP32's exact-integer range ...
+    assert big_whole[3] > 2.0 ** 24
+    # ... drained every 256 terms every level stays below 2^23
+    assert big_256.max() < 2.0 ** 23
