@@ -395,6 +395,8 @@ def run_ours(args):
         t = autotune.tune_single(d, e, mode, cache_path=None)
         leaf, kw = t.leaf, {"split_min_K": t.split_min_K}
         desc = desc.split(" leaf ")[0] + " leaf %d (autotuned, split_min_K %d) seed 4" % (leaf, t.split_min_K)
+    if args.split_chunk_k:
+        kw["split_chunk_k"] = args.split_chunk_k
     opts = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1, **kw)
     lam = torch.empty(n, dtype=torch.float64, device=dev)
     Q = torch.empty(n, n, dtype=torch.float64, device=dev).t()
@@ -539,7 +541,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if args.merge == "dense" else "f64 (Q*U as bf16 digit products, fp32 accumulate)",
         "data": "synthetic",
-        "config": {"workload": desc, "merge": args.merge, "l2": "no flush: Q and workspace (%.1f GiB) exceed the 129 MB L2" % ((8 * n * n + wsb.numel()) / 2**30),
+        "config": {"workload": desc, "merge": args.merge, "split_chunk_k": opts.split_chunk_k, "l2": "no flush: Q and workspace (%.1f GiB) exceed the 129 MB L2" % ((8 * n * n + wsb.numel()) / 2**30),
                    "parallelism": "replicas" if ws_n > 1 else "single"},
         "roofline": roof,
         "qu_tflops_fp64_equivalent": qu_tflops,
@@ -576,6 +578,8 @@ def main():
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (default: the workload's)")
     ap.add_argument("--batch", type=int, default=4096, help="problems of the batched workload (first ones of its sequence)")
     ap.add_argument("--split-min-k", type=int, default=0, help="smallest merge on the split path (default: library's)")
+    ap.add_argument("--split-chunk-k", type=int, default=0,
+                    help="drain the split product's level sums every this many terms (multiple of 16; 0: per tile)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
