@@ -19,10 +19,13 @@
 // smooth: there the rows of A are nearly parallel to z, so A U sums the secular
 // terms z_k zhat_k / delta_kj, which share their sign over long runs of k.  On the
 // Clement, Hermite and spherical-harmonic matrices of order 16384 those level-3
-// sums exceed 2^24 and round (orthogonality ratio about 1e4; the FP64 merge is the
-// path for such inputs).  The S level
-// accumulators (S x 64 TMEM columns) are combined in FP64 once per tile.  Dropped
-// levels (m >= S) and the rounded digits cost about 2^-8S absolute per entry.
+// sums exceed 2^24 and round (orthogonality ratio about 1e4).  Draining the
+// accumulators every ck k-steps (the kChunk instance) bounds every level sum by
+// the chunk's length instead of the whole reduction; until that schedule is the
+// default, the FP64 merge is the path for such inputs.  The S level accumulators
+// (S x 64 TMEM columns) are combined in FP64 once per tile (once per chunk with
+// drains).  Dropped levels (m >= S) and the rounded digits cost about 2^-8S
+// absolute per entry.
 //
 // Data flow per merge part: k_split_a writes the digits of the gathered A
 // columns, k_split_b generates Qhat from its generators in FP64 (once per entry)
