@@ -34,19 +34,23 @@ def level_sums(Ad, Ud, sl):
 
 
 def combine(A, U, chunk):
-    """C = 2^-48 hi + 2^-56 lo with hi = sum_m<5 P_m 2^(8(4-m)) (64-bit, exact) and
-    lo = P_5 + 2^-8 P_6, the sums drained every `chunk` terms; also the largest |P_m|."""
+    """The epilogue: hi = sum_m<5 P_m 2^(8(4-m)) in 64-bit integers (exact) and
+    lo = sum of 2^-8 P_6 + P_5 in FP32, both accumulated over chunks of `chunk`
+    terms; C = (2^10 hi + round(4 lo)) 2^-58 (one conversion to double).  Also the
+    largest |P_m| of any chunk."""
     Ad, Ud = digits(A), digits(U)
     K = A.shape[-1]
     hi = 0
-    lo = 0.0
+    lo = np.float32(0.0)
     big = np.zeros(S)
     for c0 in range(0, K, chunk):
         P = level_sums(Ad, Ud, slice(c0, c0 + chunk))
         big = np.maximum(big, [np.abs(p).max() for p in P])
         hi = hi + sum(P[m].astype(np.int64) * (1 << (8 * (4 - m))) for m in range(5))
-        lo = lo + P[5] + P[6] / 256.0
-    return np.ldexp(hi.astype(np.float64), -48) + np.ldexp(lo, -56), big
+        lo = (lo + (P[6] * (1.0 / 256.0)).astype(np.float32)).astype(np.float32)
+        lo = (lo + P[5].astype(np.float32)).astype(np.float32)
+    I = hi * 1024 + np.rint(np.float32(4.0) * lo).astype(np.int64)
+    return np.ldexp(I.astype(np.float64), -58), big
 
 
 def test_digits_reconstruct_exactly():
