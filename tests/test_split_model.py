@@ -109,3 +109,38 @@ def test_smooth_row_level_sums_need_chunked_drains(orc):
     assert big_whole[3] > 2.0 ** 24
     # ... drained every 256 terms every level stays below 2^23
     assert big_256.max() < 2.0 ** 23
+
+
+def test_hermite_8192_top_merge_rows_next_to_the_split(orc):
+    """The same on a real merge: the top merge of the Hermite matrix (Example 2 family)
+    of order 8192, children solved exactly, its top part's last eight rows (the rows
+    next to the split) against every column of Qhat."""
+    sla = pytest.importorskip("scipy.linalg")
+    from paper_2008_01990_gb300 import inputs
+    n = 8192
+    d, e = inputs.hermite_tridiag(n)
+    k = n // 2
+    b = e[k - 1]
+    d1 = d[:k].copy()
+    d1[-1] -= abs(b)
+    d2 = d[k:].copy()
+    d2[0] -= abs(b)
+    l1, Q1 = sla.eigh_tridiagonal(d1, e[:k - 1])
+    l2, Q2 = sla.eigh_tridiagonal(d2, e[k:])
+    z = np.concatenate([Q1[-1], np.sign(b) * Q2[0]]) / np.sqrt(2.0)
+    K, kept, defl, D2, z2, Qr, t1, t2 = orc.deflate(np.concatenate([l1, l2]), z, 2.0 * abs(b))
+    assert t2 == 0  # no rotations: the top part's columns are Q1's kept columns
+    Dk, zk = D2[kept], z2[kept]
+    rho = 2.0 * abs(b)
+    org, tau, _, _ = orc.secular(Dk, zk, rho, max_iter=2000)
+    zh = orc.lowner(Dk, zk, rho, org, tau)
+    s = orc.colnorm(Dk, org, tau, zh)
+    top = kept < k
+    A = Q1[-8:, kept[top]]
+    U = zh[top][:, None] * s[None, :] / ((Dk[top][:, None] - Dk[org][None, :]) - tau[None, :])
+    kk = A.shape[1]
+    C_whole, big_whole = combine(A, U, kk)
+    C_256, big_256 = combine(A, U, 256)
+    assert np.abs(C_256 - A @ U).max() <= 2.0 ** -48
+    assert big_whole[3] > 2.0 ** 24
+    assert big_256.max() < 2.0 ** 23
