@@ -65,10 +65,10 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
  * e = 1) the residual and orthogonality ratios ||TQ - Q Lam||_1 / (n ||T|| eps) and
  * ||Q^T Q - I||_1 / (n eps) stay below 2.  On matrices whose eigenvectors are smooth
  * and deflate little (Clement/Kac, Hermite, spherical-harmonic) level sums exceed
- * 2^24 from order 8192 on (Hermite, top merge), and the orthogonality ratio grows to 9.2e3
- * (spherical-harmonic, n = 16384) and 1.9e4 to 1.1e5 (the three, n = 30000); with
- * TDC_MERGE_DENSE it is 0.2 (spherical-harmonic, n = 30000).  Use TDC_MERGE_DENSE
- * for such inputs. */
+ * 2^24 from order 8192 on (Hermite, top merge), and the orthogonality ratio grows
+ * to 9.2e3 (spherical-harmonic, n = 16384) and 1.9e4 to 1.1e5 (the three,
+ * n = 30000); with TDC_MERGE_DENSE it is 0.2 (spherical-harmonic, n = 30000).
+ * Use TDC_MERGE_DENSE for such inputs. */
 
 typedef struct {
   int32_t leaf;             /* leaf size L in 2..64: the tree depth is the smallest t with ceil(n/2^t) <= L */
