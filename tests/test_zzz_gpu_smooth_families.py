@@ -9,7 +9,9 @@ exceed it, so those rows carry errors near 1e-11 (orthogonality ratio about
 9e3).  That test is marked xfail so that it reports the state of the split path
 without stopping the suite; it turns into an unexpected pass once the
 accumulation is made exact for such inputs.
-Ratios are taken on 256 sampled columns, as in the benchmark."""
+Ratios are taken on 256 sampled columns, as in the benchmark.  The two tests of
+the chunked-drain schedule (split_chunk_k), which bounds the level sums, stay
+skipped until that kernel instance has had a first run of its own on a GPU."""
 import numpy as np
 import pytest
 import torch
@@ -69,5 +71,34 @@ def test_sht_16384_fp64_merge(tdc):
 @pytest.mark.xfail(strict=False, reason="split-path level sums exceed 2^24 on smooth eigenvectors (orthogonality ~9e3)")
 def test_sht_16384_split_path(tdc):
     dt, et, lam, Q = solve(tdc, tdc.MERGE_AUTO)
+    res, orth = sampled_ratios(dt, et, lam, Q)
+    assert res <= 50 and orth <= 50, (res, orth)
+
+
+CHUNKED_NOT_RUN = "the chunked drains (split_chunk_k) have not run on a GPU yet: run this test alone first"
+
+
+@pytest.mark.skip(reason=CHUNKED_NOT_RUN)
+def test_chunked_drains_match_per_tile_schedule_on_random_data(tdc):
+    """On random data both schedules are exact, so the products agree to rounding."""
+    K = 4096
+    g = torch.Generator(device=DEV)
+    g.manual_seed(7)
+    D = torch.sort(torch.rand(K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1).values
+    z = torch.rand(K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1
+    z /= torch.linalg.norm(z)
+    org, tau, zh, s = tdc.rank_one(D, z, 0.9, check=True)
+    A = ((torch.rand(K, K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1) / np.sqrt(K)).t()
+    C0 = tdc.cauchy_gemm(A, D, org, tau, zh, s, tdc.MERGE_SPLIT, tdc.default_opts(), check=True)
+    C1 = tdc.cauchy_gemm(A, D, org, tau, zh, s, tdc.MERGE_SPLIT, tdc.default_opts(split_chunk_k=256), check=True)
+    assert torch.max(torch.abs(C0 - C1)).item() <= 1e-15
+
+
+@pytest.mark.skip(reason=CHUNKED_NOT_RUN)
+def test_sht_16384_split_path_chunked_drains(tdc):
+    d, e = inputs.sht_tridiag(N)
+    dt = torch.tensor(d, device=DEV)
+    et = torch.tensor(e, device=DEV)
+    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_AUTO, split_chunk_k=256), check=True)
     res, orth = sampled_ratios(dt, et, lam, Q)
     assert res <= 50 and orth <= 50, (res, orth)
