@@ -342,6 +342,19 @@ def test_dc_vs_dense_library(orc):
     assert np.max(np.abs(lam - ref)) <= 1e-12 * norm1(d, e)
 
 
+@pytest.mark.parametrize("fam,n,leaf", [("sht", 400, 32), ("hermite", 333, 16), ("clement", 257, 8),
+                                        ("toeplitz", 300, 64)])
+def test_dc_families_vs_dense_library(orc, fam, n, leaf):
+    # every family the GPU parity tests use: eigenvalues against the dense library
+    # solver, residual and orthogonality ratios
+    d, e = inputs.family(fam, n, 4)
+    lam, Q = orc.eig(d, e, leaf=leaf)
+    nT = norm1(d, e)
+    assert np.max(np.abs(lam - np.linalg.eigvalsh(dense(d, e)))) <= 1e-12 * nT
+    res, orth = ratios(d, e, lam, Q)
+    assert res <= 50 and orth <= 50
+
+
 def test_dc_zero_coupling_deflates_everything(orc):
     # e at the top split is 0: the merge is a pure sort of the two halves
     n = 64
