@@ -181,7 +181,11 @@ int orc_leaf_qr(int n, double* d, double* e, double* Q, int64_t ldq) {
 /*   g(tau) = 1/rho + sum_i z_i^2 / (delta_i - tau)                    */
 /* has the sign of f and increases with tau.  Newton steps safeguarded */
 /* by bisection on the bracket until the bracket or the step reaches    */
-/* rounding level.  D ascending, rho > 0, z_i != 0.                    */
+/* rounding level: a Newton step is taken only if it stays inside the   */
+/* bracket and is at most half the step before last, otherwise the      */
+/* bracket is halved, so the bracket at least halves every second step  */
+/* (once g is rounding noise, Newton steps alone can shrink it by tiny  */
+/* amounts for thousands of steps).  D ascending, rho > 0, z_i != 0.    */
 /* Returns the iteration count (negative when the cap was hit).        */
 /* ------------------------------------------------------------------ */
 static void secular_eval(int K, const double* D, const double* z, double rho, int org, double tau,
@@ -215,6 +219,7 @@ int orc_secular_root(int K, const double* D, const double* z, double rho, int j,
     org = K - 1; lo = 0.0; hi = rho * zz;
   }
   double tau = 0.5 * (lo + hi);
+  double prev = hi - lo, last = hi - lo; /* the two previous step lengths */
   int it;
   for (it = 1; it <= max_iter; ++it) {
     double g, dg, ga;
@@ -223,7 +228,9 @@ int orc_secular_root(int K, const double* D, const double* z, double rho, int j,
     if (g < 0.0) lo = tau; else hi = tau;
     double step = g / dg;
     double tn = tau - step;
-    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);
+    if (!(tn > lo && tn < hi) || fabs(step) > 0.5 * prev) tn = 0.5 * (lo + hi);
+    prev = last;
+    last = fabs(tn - tau);
     double w = hi - lo;
     if (w <= 2.0 * ORC_EPS * fmax(fabs(lo), fabs(hi))) { tau = tn; break; }
     if (fabs(tn - tau) <= ORC_EPS * fabs(tau)) { tau = tn; break; }

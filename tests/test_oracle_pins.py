@@ -380,3 +380,28 @@ def test_gemm_matches_numpy(orc):
     A = g.uniform(35 * 17, -1, 1).reshape(35, 17)
     B = g.uniform(17 * 9, -1, 1).reshape(17, 9)
     assert np.allclose(orc.gemm(A, B), A @ B, atol=1e-14)
+
+
+def test_secular_iteration_stays_within_its_cap(orc):
+    """The safeguarded Newton iteration halves its bracket at least every second step, so
+    every root converges within the default cap of 200: on a problem of the batched
+    workload that once needed 783 steps (n = 1633, entries uniform(-1,1)), and on a
+    rank-one problem with a weight of 1e-14 (just above the deflation tolerance of
+    about 8 eps), whose root sits about 1e-28 from its pole: the hardest root the merge
+    passes to the secular solver."""
+    from paper_2008_01990_gb300 import inputs
+    sizes = inputs.batched_sizes(4096, 64, 2048, 3)
+    d, e, offs = inputs.batched_uniform(sizes, 3)
+    b = 2023
+    nb = int(sizes[b])
+    assert nb == 1633
+    _, _, st = orc.eig(d[offs[b]:offs[b] + nb], e[offs[b]:offs[b] + nb - 1], leaf=32, with_stats=True)
+    assert st["secular_noconv"] == 0 and st["secular_iter_max"] <= 200
+    K = 64
+    D = np.linspace(-1.0, 1.0, K)
+    z = np.full(K, 1.0 / np.sqrt(K - 1))
+    z[20] = 1e-14
+    org, tau, lam, it = orc.secular(D, z, 0.7)
+    assert 0 < it <= 200
+    # the root next to the tiny weight: d_20 < lam_20 < d_20 + 1e-26
+    assert org[20] == 20 and 0.0 < tau[20] < 1e-26
