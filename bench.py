@@ -395,7 +395,7 @@ def run_ours(args):
         t = autotune.tune_single(d, e, mode, cache_path=None)
         leaf, kw = t.leaf, {"split_min_K": t.split_min_K}
         desc = desc.split(" leaf ")[0] + " leaf %d (autotuned, split_min_K %d) seed 4" % (leaf, t.split_min_K)
-    if args.split_chunk_k:
+    if args.split_chunk_k >= 0:
         kw["split_chunk_k"] = args.split_chunk_k
     opts = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1, **kw)
     lam = torch.empty(n, dtype=torch.float64, device=dev)
@@ -409,7 +409,7 @@ def run_ours(args):
     for _ in range(args.warmup):
         step()
     st = tdc.sync_status(stream)
-    if st != 0:
+    if st not in (0, tdc.TDC_WPRECISION):
         raise RuntimeError("device status %d (%s)" % (st, tdc.strerror(st)))
     sampler = ClockSampler(local)
     if ws_n > 1:
@@ -549,6 +549,8 @@ def run_ours(args):
         "phase_ms": stats["phase_ms"],
         "K_per_level": stats["sum_K"],
         "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"]},
+        "split_level_max": stats.get("split_level_max"),
+        "device_status": tdc.strerror(st),
         "test_ratios": {"lam_err_over_normT": lam_err, "residual": res, "orthogonality": orth,
                         "sampled_columns": 256, "within_bounds": bool(res <= 50 and orth <= 50)},
         "gpu_launches": int(stats["launches"]) * args.steps,
@@ -578,8 +580,9 @@ def main():
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (default: the workload's)")
     ap.add_argument("--batch", type=int, default=4096, help="problems of the batched workload (first ones of its sequence)")
     ap.add_argument("--split-min-k", type=int, default=0, help="smallest merge on the split path (default: library's)")
-    ap.add_argument("--split-chunk-k", type=int, default=0,
-                    help="drain the split product's level sums every this many terms (multiple of 16; 0: per tile)")
+    ap.add_argument("--split-chunk-k", type=int, default=-1,
+                    help="drain the split product's level sums every this many terms (multiple of 16; 0: once "
+                         "per tile; default: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()

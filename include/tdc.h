@@ -28,7 +28,8 @@
  *   - the return value is a status: TDC_OK (0); -i when argument i (1-based)
  *     is invalid, checked on the host before anything is enqueued; or one of
  *     the TDC_E* codes below.  Device-side failures (secular non-convergence,
- *     a bounded wait that expired) are recorded in a device status word that
+ *     a bounded wait that expired) and warnings are recorded in the call's
+ *     status slot (the first 256 bytes of its workspace), which
  *     tdc_sync_status() returns;
  *   - inputs d and e are never modified.
  */
@@ -53,6 +54,11 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
 #define TDC_ECUDA (-105)       /* a CUDA runtime call failed */
 #define TDC_EUNSUPPORTED (-106) /* option combination not supported */
 #define TDC_ETOOLARGE (-107)   /* problem needs more than the fixed scratch of tdc_eig_noalloc */
+/* warning (device status, positive): the results were written, but a level sum of the split
+ * product reached 2^23, half of the range its FP32 accumulators hold exactly, so the
+ * eigenvectors may miss the FP64 accuracy bound (use a smaller split_chunk_k or
+ * TDC_MERGE_DENSE).  Errors take precedence over it. */
+#define TDC_WPRECISION 1
 
 /* merge modes: how the eigenvector update Q * U is computed */
 #define TDC_MERGE_AUTO 0        /* library choice: the split path for merges with K >= split_min_K, FP64 below */
@@ -61,14 +67,16 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
 #define TDC_MERGE_SPLIT 3       /* BF16 slice products on tcgen05 tensor cores, FP32/FP64 accumulation */
 /* Accuracy of the split path (SPLIT and AUTO): the digit products of one level are
  * summed in FP32 accumulators, exact only while each level's sum stays below 2^24.
- * On random and weakly structured spectra (tridiag(1,2,1), uniform, d ~ U(0,1) with
- * e = 1) the residual and orthogonality ratios ||TQ - Q Lam||_1 / (n ||T|| eps) and
- * ||Q^T Q - I||_1 / (n eps) stay below 2.  On matrices whose eigenvectors are smooth
- * and deflate little (Clement/Kac, Hermite, spherical-harmonic) level sums exceed
- * 2^24 from order 8192 on (Hermite, top merge), and the orthogonality ratio grows
- * to 9.2e3 (spherical-harmonic, n = 16384) and 1.9e4 to 1.1e5 (the three,
- * n = 30000); with TDC_MERGE_DENSE it is 0.2 (spherical-harmonic, n = 30000).
- * Use TDC_MERGE_DENSE for such inputs. */
+ * The default schedule drains them into 64-bit integer sums every split_chunk_k = 256
+ * terms, which keeps every level sum far below that limit: the residual and
+ * orthogonality ratios ||TQ - Q Lam||_1 / (n ||T|| eps) and ||Q^T Q - I||_1 / (n eps)
+ * stay below 2 on random spectra, tridiag(1,2,1), d ~ U(0,1) with e = 1, and on the
+ * smooth-eigenvector families (Clement/Kac, Hermite, spherical-harmonic) up to n = 30000.
+ * Summing over a tile's whole reduction instead (split_chunk_k = 0) is about 10 %
+ * faster at n = 16384 but not exact on smooth-eigenvector matrices from n = 8192 on
+ * (orthogonality ratios of 1e3 to 1e5).  Every drain checks its level sums; one that
+ * reached 2^23 raises the warning TDC_WPRECISION and is counted in
+ * tdc_stats.split_level_max. */
 
 typedef struct {
   int32_t leaf;             /* leaf size L in 2..64: the tree depth is the smallest t with ceil(n/2^t) <= L */
@@ -82,10 +90,10 @@ typedef struct {
   int32_t sign_normalise;   /* 1: make the largest-magnitude entry of every column positive */
   int32_t collect_stats;    /* 1: record per-level statistics for tdc_get_stats (adds a sync) */
   int64_t spin_budget;      /* bounded-wait iteration cap for persistent kernels */
-  int32_t split_chunk_k;    /* SPLIT/AUTO: 0 (default) sums each level over a tile's whole reduction; a
-                               positive multiple of 16 drains the FP32 level sums into the 64-bit
-                               running sums every split_chunk_k terms, which bounds them for any order
-                               (requires split_slices = 7) */
+  int32_t split_chunk_k;    /* SPLIT/AUTO: a positive multiple of 16 (default 256) drains the FP32 level
+                               sums into 64-bit running sums every split_chunk_k terms, which bounds
+                               them for any order; 0 sums each level over a tile's whole reduction
+                               (faster, not exact on smooth eigenvectors) */
 } tdc_opts;
 
 #define TDC_MAX_LEVELS 32
@@ -114,11 +122,14 @@ typedef struct {
   int64_t launches;                      /* kernel launches of the call */
   int64_t secular_handoffs;              /* roots of small merges whose thread-per-root solve was not
                                             certified in one pass and went to a warp-per-root solve */
+  float split_level_max;                 /* largest |level sum| / 2^24 that a hand-off of the split
+                                            product's FP32 accumulators held (levels 0-4); the
+                                            product is exact while it stays below 1 */
 } tdc_stats;
 
 /* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,
  * lr_tol 1e-15, split_slices 7, split_min_K 128, max_iter 64, sign_normalise 1,
- * collect_stats 0, spin_budget 2^24). */
+ * collect_stats 0, spin_budget 2^24, split_chunk_k 256). */
 void tdc_default_opts(tdc_opts* o);
 
 /* Workspace bytes tdc_eig needs for order n (o may be NULL = defaults).
@@ -221,8 +232,15 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
                     const double* tau, const double* zhat, const double* s, double* C, int64_t ldc, int32_t mode,
                     const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream);
 
-/* Synchronise `stream` and return the device status word of the last call on
- * it (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE), then clear it. */
+/* Synchronise `stream` and return the device status of the last call enqueued on it
+ * (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE, TDC_EUNSUPPORTED, or the warning
+ * TDC_WPRECISION), then clear it.  Every call that takes a workspace keeps its status
+ * in the first 256 bytes of that workspace (cleared when the call is enqueued), so
+ * calls on different streams with different workspaces never see each other's status;
+ * read it before the workspace is reused.  A stream that no call was enqueued on
+ * (for example one a captured graph is replayed on) reports the last call made on
+ * the device.  tdc_rank_one called without a workspace uses a per-device word that
+ * every such call shares. */
 int tdc_sync_status(tdc_stream_t stream);
 
 /* Copy the statistics of the last call made with collect_stats = 1. */

@@ -102,6 +102,7 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   unsigned long long iter_roots;
   int iter_max;
   unsigned long long handoffs;
+  unsigned int split_level_max;  // FP32 bits of the largest |level sum| of a split hand-off (levels 0-4)
 };
 
 // One GEMM segment C(rows x K) = A(rows x kk) * Qhat(list, :) of the merge
@@ -288,8 +289,14 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
+// A call's status slot is two words: status[0] the first error (first writer wins),
+// status[1] warning bits (results written, accuracy possibly reduced).
 __device__ __forceinline__ void set_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
+}
+constexpr int kWarnSplitLevel = 1;  // a split-path level sum reached 2^23 (half its exact FP32 range)
+__device__ __forceinline__ void set_warning(int* status, int bit) {
+  if (status) atomicOr(status + 1, bit);
 }
 
 }  // namespace tdc

@@ -454,9 +454,67 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
 namespace {
 constexpr int kEpiWarps = 16, kMmaWarp = 16, kLoadWarp = 17, kSplitThreads = 576;
 constexpr int kEpiCols = BN / (kEpiWarps / 4);  // columns per epilogue warp
-static_assert(kEpiCols == 16 || kEpiCols == 32, "epilogue column split");
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[16]) { umma::tmem_ld16(taddr, v); }
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, float (&v)[32]) { umma::tmem_ld32(taddr, v); }
+static_assert(kEpiCols == 16, "epilogue column split: one 16-column TMEM load per level");
+
+// Level m < 5 of one hand-off (16 columns, exact integers held in FP32) into the
+// 64-bit running sums: hi += P_m 2^sh with sh = 8 (4 - m).  An FP32 integer v with
+// |v| < 2^22 becomes an integer without the conversion unit (16 per clock per SM):
+// v + 1.5 2^23 lies in [2^23, 2^24), where the float's ulp is 1, so its bit pattern
+// is 0x4B400000 + v exactly; bias collects the 0x4B400000 2^sh this adds, removed
+// once per tile.  A thread holding a larger value (a level sum near the 2^24 limit)
+// forms the same 0x4B400000 + v with cvt instead.  The sums are kept modulo 2^64
+// (unsigned) and are exact once the bias is removed.
+__device__ __forceinline__ void add_level_int(const uint32_t (&r)[16], int sh, unsigned long long (&hi)[16],
+                                              unsigned long long& bias, float& gmax) {
+  float mx = 0.0f;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) mx = fmaxf(mx, fabsf(__uint_as_float(r[i])));
+  gmax = fmaxf(gmax, mx);
+  if (mx < 4194304.0f) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      hi[i] += (unsigned long long)__float_as_uint(__uint_as_float(r[i]) + 12582912.0f) << sh;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      hi[i] += (unsigned long long)((long long)__float2int_rn(__uint_as_float(r[i])) + 0x4B400000ll) << sh;
+  }
+  bias += 0x4B400000ull << sh;
+}
+
+// One hand-off of the S level accumulators (this warp's 32 TMEM lanes, 16 columns at
+// ta): hi += sum_{m<5} P_m 2^(8(4-m)), lo += P_6 2^-8 then += P_5.  One level at a
+// time (16 registers; sixteen epilogue warps hide the load latency).  Summing these
+// per hand-off gives the same integers as the per-tile Horner combination, and lo
+// the same FP32 roundings.
+template <int S>
+__device__ __forceinline__ void drain_levels(uint32_t ta, unsigned long long (&hi)[16], float (&lo)[16],
+                                             unsigned long long& bias, float& gmax) {
+  uint32_t a[16];
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    if (m < S) {
+      umma::tmem_ld16_nowait(ta + (uint32_t)(m * BN), a);
+      umma::tmem_wait_ld(a);
+      add_level_int(a, 8 * (4 - m), hi, bias, gmax);
+    }
+  }
+#pragma unroll
+  for (int m = 6; m >= 5; --m) {
+    if (m < S) {
+      umma::tmem_ld16_nowait(ta + (uint32_t)(m * BN), a);
+      umma::tmem_wait_ld(a);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) lo[i] += m == 6 ? __uint_as_float(a[i]) * 0.00390625f : __uint_as_float(a[i]);
+    }
+  }
+}
+
+// Bound of the waits on the give-up path (copies and MMAs already issued, which
+// complete in microseconds): independent of the caller's spin budget, so that a
+// small budget can only make the roles give up, never leave a copy or an MMA in
+// flight when the CTA releases its TMEM and exits.
+constexpr long long kDrainBudget = 1ll << 24;
 
 __device__ __forceinline__ bool wait_or_fail(uint64_t* bar, uint32_t parity, long long budget,
                                              volatile int* fail) {
@@ -501,7 +559,7 @@ __device__ __forceinline__ TileRef tile_ref(const GemmSeg* segs, int nseg, int64
 template <int S, bool kChunk>
 __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* segs, int nseg, const int64_t* dnseg,
                                                                  const __nv_bfloat16* img, int* status,
-                                                                 long long budget, int ck) {
+                                                                 long long budget, int ck, unsigned int* lvl_max) {
   if (dnseg) nseg = (int)*dnseg;
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr uint32_t a_bytes = S * kATileElems * 2, b_bytes = S * kBTileElems * 2;
@@ -561,7 +619,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       if (!ok) *vfail = 1;
       // copies issued but not consumed (only after a failure) land before the CTA exits
       for (long long q = g > kStages ? g - kStages : 0; q < g; ++q)
-        umma::mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1), budget);
+        umma::mbar_wait(&full[q % kStages], (uint32_t)((q / kStages) & 1), kDrainBudget);
     }
   } else if (warp == kMmaWarp) {
     if (lane == 0) {
@@ -623,7 +681,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       // every MMA issued has completed before the accumulators are released
       if (issued) {
         umma::mma_commit(done);
-        umma::mbar_wait(done, 0, budget);
+        umma::mbar_wait(done, 0, kDrainBudget);
       }
     }
   } else {
@@ -638,6 +696,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
     // field (I != 0 gives |I| >= 1, so the result stays normal); otherwise, e.g.
     // for the adjoint's column-scaled products, in FP64 as written.
     int it = 0;
+    float gmax = 0.0f;  // largest |level sum| (levels 0-4) this thread drained
     const int quarter = warp & 3, c0 = (warp >> 2) * kEpiCols;
     const uint32_t tl = tmem + ((uint32_t)(quarter * 32) << 16);
     for (int64_t w = blockIdx.x; w < total; w += gridDim.x, ++it) {
@@ -646,11 +705,11 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
         // the same combination, accumulated over the tile's chunks: level m of a
         // chunk adds P_m 2^(8(4-m)) to hi (m < 5, exact) or its share to lo
         const int nch = t.KB > 0 ? (t.KB + ck - 1) / ck : 1;
-        long long hi[kEpiCols];
+        unsigned long long hu[kEpiCols], bias = 0;
         float lo[kEpiCols];
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) {
-          hi[i] = 0;
+          hu[i] = 0;
           lo[i] = 0.0f;
         }
         bool okc = true;
@@ -659,26 +718,7 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           okc = __all_sync(0xffffffffu, wait_or_fail(tfull, (uint32_t)(it & 1), budget, vfail));
           if (!okc) break;
           umma::tc_fence_after();
-          if (t.KB > 0) {
-#pragma unroll
-            for (int m = 0; m < 5; ++m) {
-              if (m < S) {
-                float v[kEpiCols];
-                tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
-#pragma unroll
-                for (int i = 0; i < kEpiCols; ++i) hi[i] += (long long)__float2int_rn(v[i]) * (1ll << (8 * (4 - m)));
-              }
-            }
-#pragma unroll
-            for (int m = 6; m >= 5; --m) {
-              if (m < S) {
-                float v[kEpiCols];
-                tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
-#pragma unroll
-                for (int i = 0; i < kEpiCols; ++i) lo[i] += m == 6 ? v[i] * 0.00390625f : v[i];
-              }
-            }
-          }
+          if (t.KB > 0) drain_levels<S>(tl + (uint32_t)c0, hu, lo, bias, gmax);
           umma::tc_fence_before();
           __syncwarp();
           if (lane == 0) mbar_arrive(tempty);
@@ -687,6 +727,9 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           if (lane == 0) *vfail = 1;
           break;
         }
+        long long hi[kEpiCols];
+#pragma unroll
+        for (int i = 0; i < kEpiCols; ++i) hi[i] = (long long)(hu[i] - bias);
         double val[kEpiCols];
         bool fits = true;
 #pragma unroll
@@ -724,36 +767,17 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       umma::tc_fence_after();
       double val[kEpiCols];
       {
-        long long hi[kEpiCols];
+        unsigned long long hu[kEpiCols], bias = 0;
         float lo[kEpiCols];
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) {
-          hi[i] = 0;
+          hu[i] = 0;
           lo[i] = 0.0f;
         }
-        if (t.KB > 0) {
+        if (t.KB > 0) drain_levels<S>(tl + (uint32_t)c0, hu, lo, bias, gmax);
+        long long hi[kEpiCols];
 #pragma unroll
-          for (int m = 0; m < 5; ++m) {
-            if (m < S) {
-              float v[kEpiCols];
-              tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
-#pragma unroll
-              for (int i = 0; i < kEpiCols; ++i) hi[i] = hi[i] * 256 + (long long)__float2int_rn(v[i]);
-            } else {
-#pragma unroll
-              for (int i = 0; i < kEpiCols; ++i) hi[i] *= 256;
-            }
-          }
-#pragma unroll
-          for (int m = 6; m >= 5; --m) {
-            if (m < S) {
-              float v[kEpiCols];
-              tmem_ld_cols(tl + (uint32_t)(m * BN + c0), v);
-#pragma unroll
-              for (int i = 0; i < kEpiCols; ++i) lo[i] = fmaf(lo[i], 0.00390625f, v[i]);
-            }
-          }
-        }
+        for (int i = 0; i < kEpiCols; ++i) hi[i] = (long long)(hu[i] - bias);
         bool fits = true;
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
@@ -785,6 +809,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
         }
       }
     }
+    // the level sums' margin: statistics, and a warning once a hand-off reached 2^23
+    const float wmax = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(gmax)));
+    if (lane == 0) {
+      if (lvl_max) atomicMax(lvl_max, __float_as_uint(wmax));
+      if (wmax >= 8388608.0f) set_warning(status, kWarnSplitLevel);
+    }
   }
   umma::tc_fence_before();
   __syncthreads();
@@ -803,30 +833,38 @@ static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, const int6
 
 template <int S, bool kChunk>
 static cudaError_t launch_split_mma_s(const GemmSeg* segs, int nseg, const int64_t* dnseg, int* status,
-                                      long long budget, const __nv_bfloat16* img, int sms, int ck, cudaStream_t s) {
+                                      long long budget, const __nv_bfloat16* img, int sms, int ck,
+                                      unsigned int* lvl_max, cudaStream_t s) {
   const int smem = kStages * S * (kATileElems + kBTileElems) * 2 + 128;
   cudaError_t e = cudaFuncSetAttribute(k_gemm_split<S, kChunk>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  k_gemm_split<S, kChunk><<<sms, kSplitThreads, smem, s>>>(segs, nseg, dnseg, img, status, budget, ck);
+  k_gemm_split<S, kChunk><<<sms, kSplitThreads, smem, s>>>(segs, nseg, dnseg, img, status, budget, ck, lvl_max);
   return cudaGetLastError();
 }
 
-// ck > 0: drain the accumulators every ck k-steps (seven digits only)
+// ck > 0: drain the accumulators every ck k-steps
 static cudaError_t launch_split_mma(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S, int* status,
-                                    long long budget, const __nv_bfloat16* img, int ck, cudaStream_t s) {
+                                    long long budget, const __nv_bfloat16* img, int ck, unsigned int* lvl_max,
+                                    cudaStream_t s) {
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (ck > 0) {
-    if (S != 7) return cudaErrorInvalidValue;
-    return launch_split_mma_s<7, true>(segs, nseg, dnseg, status, budget, img, sms, ck, s);
+    switch (S) {
+      case 3: return launch_split_mma_s<3, true>(segs, nseg, dnseg, status, budget, img, sms, ck, lvl_max, s);
+      case 4: return launch_split_mma_s<4, true>(segs, nseg, dnseg, status, budget, img, sms, ck, lvl_max, s);
+      case 5: return launch_split_mma_s<5, true>(segs, nseg, dnseg, status, budget, img, sms, ck, lvl_max, s);
+      case 6: return launch_split_mma_s<6, true>(segs, nseg, dnseg, status, budget, img, sms, ck, lvl_max, s);
+      case 7: return launch_split_mma_s<7, true>(segs, nseg, dnseg, status, budget, img, sms, ck, lvl_max, s);
+      default: return cudaErrorInvalidValue;
+    }
   }
   switch (S) {
-    case 3: return launch_split_mma_s<3, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
-    case 4: return launch_split_mma_s<4, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
-    case 5: return launch_split_mma_s<5, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
-    case 6: return launch_split_mma_s<6, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
-    case 7: return launch_split_mma_s<7, false>(segs, nseg, dnseg, status, budget, img, sms, 0, s);
+    case 3: return launch_split_mma_s<3, false>(segs, nseg, dnseg, status, budget, img, sms, 0, lvl_max, s);
+    case 4: return launch_split_mma_s<4, false>(segs, nseg, dnseg, status, budget, img, sms, 0, lvl_max, s);
+    case 5: return launch_split_mma_s<5, false>(segs, nseg, dnseg, status, budget, img, sms, 0, lvl_max, s);
+    case 6: return launch_split_mma_s<6, false>(segs, nseg, dnseg, status, budget, img, sms, 0, lvl_max, s);
+    case 7: return launch_split_mma_s<7, false>(segs, nseg, dnseg, status, budget, img, sms, 0, lvl_max, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -849,14 +887,15 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, i
   e = launch_split_digits(P.segs, nseg, dn, P.split_slices, P.img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
-  return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, P.split_chunk_steps, s);
+  return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, P.split_chunk_steps,
+                          P.stats ? &P.stats->split_level_max : nullptr, s);
 }
 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, int chunk_steps, cudaStream_t s) {
   cudaError_t e = launch_split_digits(segs_dev, nseg, nullptr, S, img, s);
   if (e != cudaSuccess) return e;
-  return launch_split_mma(segs_dev, nseg, nullptr, S, status, spin_budget, img, chunk_steps, s);
+  return launch_split_mma(segs_dev, nseg, nullptr, S, status, spin_budget, img, chunk_steps, nullptr, s);
 }
 
 }  // namespace tdc

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import warnings
 
 import torch
 
@@ -23,6 +24,7 @@ TDC_ETIMEOUT = -104
 TDC_ECUDA = -105
 TDC_EUNSUPPORTED = -106
 TDC_ETOOLARGE = -107
+TDC_WPRECISION = 1
 
 MERGE_AUTO = 0
 MERGE_DENSE = 1
@@ -67,6 +69,7 @@ class Stats(ctypes.Structure):
         ("struct_flops", ctypes.c_double),
         ("launches", ctypes.c_int64),
         ("secular_handoffs", ctypes.c_int64),
+        ("split_level_max", ctypes.c_float),
     ]
 
     def as_dict(self):
@@ -90,7 +93,13 @@ class Stats(ctypes.Structure):
             "struct_flops": self.struct_flops,
             "launches": self.launches,
             "secular_handoffs": self.secular_handoffs,
+            "split_level_max": self.split_level_max,
         }
+
+
+class TdcPrecisionWarning(RuntimeWarning):
+    """The device status of a call was TDC_WPRECISION: a split-path level sum reached half of
+    its exact FP32 range, so the eigenvectors may miss the FP64 accuracy bound."""
 
 
 class TdcError(RuntimeError):
@@ -139,7 +148,9 @@ def lib():
 
 
 def _check(fn, st):
-    if st != 0:
+    if st == TDC_WPRECISION:
+        warnings.warn("%s: %s" % (fn, lib().tdc_strerror(st).decode()), TdcPrecisionWarning, stacklevel=3)
+    elif st != 0:
         raise TdcError(fn, st)
 
 
@@ -239,16 +250,23 @@ def rank_one(D: torch.Tensor, z: torch.Tensor, rho: float, max_iter: int = 64, s
     return org, tau, zhat, s
 
 
-def cauchy_gemm(A: torch.Tensor, D: torch.Tensor, org: torch.Tensor, tau: torch.Tensor, zhat: torch.Tensor,
-                s: torch.Tensor, mode: int = MERGE_DENSE, opts: Opts | None = None, stream=None, check=False):
-    """C = A * Qhat with Qhat_ij = zhat_i s_j / ((D_i - D_org_j) - tau_j); A is a column-major m x K view."""
-    m, K = A.shape
-    lda = A.stride(1) if K > 0 else max(m, 1)
-    C = torch.empty(K, m, dtype=torch.float64, device=A.device).t()
+def cauchy_gemm_workspace_size(m: int, K: int, mode: int = MERGE_DENSE, opts: Opts | None = None) -> int:
     b = ctypes.c_size_t(0)
     _check("tdc_cauchy_gemm_workspace_size",
            lib().tdc_cauchy_gemm_workspace_size(m, K, mode, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
-    ws = workspace(b.value, A.device)
+    return b.value
+
+
+def cauchy_gemm(A: torch.Tensor, D: torch.Tensor, org: torch.Tensor, tau: torch.Tensor, zhat: torch.Tensor,
+                s: torch.Tensor, mode: int = MERGE_DENSE, opts: Opts | None = None, stream=None, check=False,
+                ws: torch.Tensor | None = None):
+    """C = A * Qhat with Qhat_ij = zhat_i s_j / ((D_i - D_org_j) - tau_j); A is a column-major m x K view.
+    The call's device status lives in its workspace: pass `ws` (and keep it) to read the status later."""
+    m, K = A.shape
+    lda = A.stride(1) if K > 0 else max(m, 1)
+    C = torch.empty(K, m, dtype=torch.float64, device=A.device).t()
+    if ws is None:
+        ws = workspace(cauchy_gemm_workspace_size(m, K, mode, opts), A.device)
     _check("tdc_cauchy_gemm", lib().tdc_cauchy_gemm(m, K, _ptr(A), max(lda, 1), _ptr(D), _ptr(org), _ptr(tau),
                                                     _ptr(zhat), _ptr(s), _ptr(C), max(m, 1), mode,
                                                     ctypes.byref(opts) if opts else None, _ptr(ws), ws.numel(),

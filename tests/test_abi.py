@@ -33,13 +33,14 @@ def test_default_opts_and_workspace(lib):
     from paper_2008_01990_gb300 import tdc
     o = tdc.default_opts()
     assert o.leaf == 32 and o.max_iter >= 1 and o.sign_normalise == 1
-    assert o.split_chunk_k == 0 and ctypes.sizeof(o) == 64
+    assert o.split_chunk_k == 256 and ctypes.sizeof(o) == 64
     w1 = tdc.workspace_size(1024, o)
     w2 = tdc.workspace_size(2048, o)
     assert 2048 * 2048 * 8 < w2 and w1 < w2
     assert tdc.workspace_size(0, o) > 0
-    # chunked drains of the split accumulators change no workspace
+    # the chunk length of the split accumulators' drains changes no workspace
     assert tdc.workspace_size(2048, tdc.default_opts(split_chunk_k=512)) == w2
+    assert tdc.workspace_size(2048, tdc.default_opts(split_chunk_k=0)) == w2
 
 
 def test_host_argument_checks(lib):
@@ -64,13 +65,13 @@ def test_host_argument_checks(lib):
                                bogus, bogus, bogus, 1 << 30, None, None) == -1001
     assert lib.tdc_rank_one(4, bogus, bogus, -1.0, bogus, bogus, bogus, bogus, 8, bogus, 256, None) == -4
     assert tdc.strerror(tdc.TDC_ENOWS).startswith("workspace")
+    assert tdc.strerror(tdc.TDC_WPRECISION).startswith("warning")
 
 
 @pytest.mark.parametrize("bad", [dict(leaf=1), dict(leaf=65), dict(merge_mode=4), dict(max_iter=0),
                                  dict(lr_tile=100), dict(split_slices=2), dict(split_slices=8),
                                  dict(split_min_K=0), dict(spin_budget=0), dict(lr_tol=0.0),
-                                 dict(split_chunk_k=8), dict(split_chunk_k=-16),
-                                 dict(split_chunk_k=512, split_slices=6)])
+                                 dict(split_chunk_k=8), dict(split_chunk_k=-16)])
 def test_invalid_options_rejected_on_host(lib, bad):
     """Every option outside its documented range is refused before anything is
     enqueued (the workspace query validates the same way)."""

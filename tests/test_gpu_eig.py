@@ -47,6 +47,17 @@ def check_vs_oracle(orc, d, e, lam, Q, leaf, vec_tol=1e-9):
     return lam_o, Q_o
 
 
+def assert_same_deflation(st, sto):
+    """Deflation decisions agree level by level: the GPU's parallel tests and chain
+    resolution must reproduce the oracle's sequential scan of Section 3.2 exactly
+    (both decide in FP64 with the same tolerance): equal non-deflated sizes, equal
+    type-1 (small z) and type-2 (rotation) counts."""
+    assert st["levels"] == sto["levels"]
+    assert st["sum_K"] == sto["sum_K"]
+    assert st["type1"] == sto["type1"]
+    assert st["type2"] == sto["type2"]
+
+
 def test_c1_uniform_1024(tdc, orc):
     n = 1024
     d, e = inputs.uniform_tridiag(n, 1)
@@ -55,9 +66,17 @@ def test_c1_uniform_1024(tdc, orc):
     st = tdc.get_stats()
     _, _, sto = orc.eig(d, e, leaf=32, with_stats=True)
     assert st["levels"] == sto["levels"] == 5
-    # deflation decisions agree level by level (both sides decide in FP64)
-    for a, b in zip(st["sum_K"], sto["sum_K"]):
-        assert abs(a - b) <= max(2, 0.01 * b)
+    assert_same_deflation(st, sto)
+
+
+@pytest.mark.parametrize("fam,n,leaf", [("c4", 1500, 64), ("toeplitz", 2048, 64), ("uniform", 3000, 16),
+                                        ("clement", 2049, 32)])
+def test_deflation_counts_equal_the_oracle_scan(tdc, orc, fam, n, leaf):
+    d, e = inputs.family(fam, n, 4)
+    run_gpu(tdc, d, e, leaf=leaf, collect_stats=1)
+    st = tdc.get_stats()
+    _, _, sto = orc.eig(d, e, leaf=leaf, with_stats=True)
+    assert_same_deflation(st, sto)
 
 
 @pytest.mark.parametrize("n,leaf", [(1, 32), (2, 2), (3, 2), (5, 2), (9, 2), (31, 32), (33, 32), (64, 64), (65, 64),

@@ -139,3 +139,74 @@ def test_c4_split_32768_sampled(tdc):
     Gm[torch.arange(256, device=DEV), cols] -= 1.0
     orth = torch.abs(Gm).sum(dim=1).max().item() / (n * EPS)
     assert res <= 50 and orth <= 50, (res, orth)
+
+
+def test_bounded_waits_expire_report_a_timeout_and_leave_the_device_usable(tdc, orc):
+    """Failure detection without a GPU fault: with a spin budget of one try, the split
+    product's epilogue cannot wait out a tile of 512 k-steps (about 0.3 ms), so its
+    bounded wait expires.  The CTA then lets its issued copies and MMAs land (their
+    own, fixed bound), releases its TMEM and returns; the call reports TDC_ETIMEOUT
+    through its status slot.  The next calls, with the default budget, are correct."""
+    K = m = 8192
+    g = torch.Generator(device=DEV)
+    g.manual_seed(11)
+    D = torch.sort(torch.rand(K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1).values
+    z = torch.rand(K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1
+    z /= torch.linalg.norm(z)
+    org, tau, zh, s = tdc.rank_one(D, z, 0.9, check=True)
+    A = ((torch.rand(K, m, dtype=torch.float64, device=DEV, generator=g) * 2 - 1) / np.sqrt(K)).t()
+    o1 = tdc.default_opts(spin_budget=1)
+    ws = tdc.workspace(tdc.cauchy_gemm_workspace_size(m, K, tdc.MERGE_SPLIT, o1), DEV)  # holds the status slot
+    tdc.cauchy_gemm(A, D, org, tau, zh, s, tdc.MERGE_SPLIT, o1, ws=ws)
+    assert tdc.sync_status() == tdc.TDC_ETIMEOUT
+    # the eigensolver's split merges report it the same way
+    d, e = inputs.toeplitz_tridiag(8192)
+    dt, et = torch.tensor(d, device=DEV), torch.tensor(e, device=DEV)
+    oe = tdc.default_opts(leaf=64, spin_budget=1)
+    wse = tdc.workspace(tdc.workspace_size(8192, oe), DEV)
+    tdc.eig(dt, et, oe, ws=wse)
+    assert tdc.sync_status() == tdc.TDC_ETIMEOUT
+    # then: clean calls, checked against the oracle
+    Kc, mc = 1024, 300
+    Dn, on, tn, zn, sn = generators(orc, Kc, 91)
+    An = orthogonal_rows(orc, mc, Kc, 92)
+    Co = orc.gemm(An, orc.qhat(Dn, on, tn, zn, sn))
+    C = run_cauchy(tdc, An, Dn, on, tn, zn, sn, tdc.MERGE_SPLIT)
+    assert np.max(np.abs(C - Co)) <= 1e-14 * np.sqrt(Kc)
+    d1, e1 = inputs.uniform_tridiag(1024, 93)
+    lam, Q = tdc.eig(torch.tensor(d1, device=DEV), torch.tensor(e1, device=DEV), tdc.default_opts(leaf=32), check=True)
+    lo, Qo = orc.eig(d1, e1, leaf=32)
+    lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
+    nT = max(abs(lo[0]), abs(lo[-1]))
+    assert np.max(np.abs(lam - lo)) <= 1e-12 * nT
+    res, orth = ratios(d1, e1, lam, Q)
+    assert res <= 50 and orth <= 50
+    compare_vectors(Q, Qo, lo, 1e-8 * nT, 1e-9)
+
+
+def test_status_slots_of_calls_on_two_streams_stay_apart(tdc):
+    """Each call keeps its status in its own workspace: a timeout on one stream is not
+    reported for, or cleared by, a clean call on another stream."""
+    K = 8192
+    g = torch.Generator(device=DEV)
+    g.manual_seed(12)
+    D = torch.sort(torch.rand(K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1).values
+    z = torch.rand(K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1
+    z /= torch.linalg.norm(z)
+    org, tau, zh, s = tdc.rank_one(D, z, 0.9, check=True)
+    A = ((torch.rand(K, K, dtype=torch.float64, device=DEV, generator=g) * 2 - 1) / np.sqrt(K)).t()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    o1 = tdc.default_opts(spin_budget=1)
+    ws1 = tdc.workspace(tdc.cauchy_gemm_workspace_size(K, K, tdc.MERGE_SPLIT, o1), DEV)
+    d, e = inputs.uniform_tridiag(500, 94)
+    dt, et = torch.tensor(d, device=DEV), torch.tensor(e, device=DEV)
+    o2 = tdc.default_opts(leaf=32)
+    ws2 = tdc.workspace(tdc.workspace_size(500, o2), DEV)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s1):
+        tdc.cauchy_gemm(A, D, org, tau, zh, s, tdc.MERGE_SPLIT, o1, stream=s1, ws=ws1)
+    with torch.cuda.stream(s2):
+        tdc.eig(dt, et, o2, ws=ws2, stream=s2)
+    assert tdc.sync_status(s2) == 0
+    assert tdc.sync_status(s1) == tdc.TDC_ETIMEOUT
+    assert tdc.sync_status(s1) == 0  # read and cleared

@@ -144,3 +144,38 @@ def test_hermite_8192_top_merge_rows_next_to_the_split(orc):
     assert np.abs(C_256 - A @ U).max() <= 2.0 ** -48
     assert big_whole[3] > 2.0 ** 24
     assert big_256.max() < 2.0 ** 23
+
+
+def magic_bits(v):
+    """The epilogue's conversion of an exact FP32 integer |v| < 2^22: the bit pattern of
+    v + 1.5 2^23 (computed in FP32), read as an unsigned integer."""
+    return (np.asarray(v, dtype=np.float32) + np.float32(12582912.0)).view(np.uint32).astype(np.uint64)
+
+
+def test_fp32_integer_conversion_by_offset():
+    # every representable integer |v| < 2^22 maps to 0x4B400000 + v (no rounding in [2^23, 2^24))
+    v = np.arange(-(1 << 22) + 1, 1 << 22, dtype=np.int64)
+    b = magic_bits(v.astype(np.float32)).astype(np.int64)
+    assert np.array_equal(b - 0x4B400000, v)
+    # negative zero behaves like zero
+    assert int(magic_bits(np.float32(-0.0))) == 0x4B400000
+
+
+def test_offset_sums_modulo_2_64_recover_the_level_combination():
+    """hi = sum over hand-offs and levels of bits(P_m) 2^(8(4-m)) kept modulo 2^64, minus the
+    summed offsets, equals sum P_m 2^(8(4-m)) in exact integers (Python ints)."""
+    g = np.random.default_rng(5)
+    for trial in range(50):
+        chunks = int(g.integers(1, 40))
+        P = g.integers(-(1 << 22) + 1, 1 << 22, size=(chunks, 5))
+        hu, bias, exact = 0, 0, 0
+        for c in range(chunks):
+            for m in range(5):
+                sh = 8 * (4 - m)
+                hu = (hu + (int(magic_bits(np.float32(P[c, m]))) << sh)) % (1 << 64)
+                bias = (bias + (0x4B400000 << sh)) % (1 << 64)
+                exact += int(P[c, m]) << sh
+        got = (hu - bias) % (1 << 64)
+        if got >= 1 << 63:
+            got -= 1 << 64
+        assert got == exact

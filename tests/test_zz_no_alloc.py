@@ -5,9 +5,11 @@ allocator, plugins that must not touch the allocator, latency-critical paths
 where an allocation may block or fail) pass only inputs and outputs; the solver
 then works in a fixed array inside the library.  This test calls the entry point
 through the C ABI twice in a row and checks each result against tdc_eig with a
-caller-provided workspace, using the tolerances of the other GPU tests
-(|lam - lam_ref| <= 1e-12 ||T||, eigenvectors equal up to sign).  It is collected
-last so that a failure here cannot hide the other tests.
+caller-provided workspace.  Both calls run the same kernels on the same inputs in
+the same order, so the results must be identical bit for bit: once where the
+library's default merge (the split path) fits the fixed array and runs inside it,
+and once where it does not and the entry point takes the FP64 merge.  It is
+collected last so that a failure here cannot hide the other tests.
 """
 import ctypes
 
@@ -15,7 +17,6 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import compare_vectors
 from paper_2008_01990_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -43,20 +44,39 @@ def _noalloc(tdc, d, e, opts):
     return lam, Q
 
 
+SCRATCH = 24 << 20  # the entry point's fixed array
+
+
+def _same_as_workspace_path(tdc, n, seed, ref_mode):
+    d_np, e_np = inputs.uniform_tridiag(n, seed)
+    d = torch.tensor(d_np, device=DEV)
+    e = torch.tensor(e_np, device=DEV)
+    lam, Q = _noalloc(tdc, d, e, tdc.default_opts(leaf=32))
+    lam_ref, Q_ref = tdc.eig(d, e, tdc.default_opts(leaf=32, merge_mode=ref_mode), check=True)
+    assert torch.equal(lam, lam_ref)
+    assert torch.equal(Q, Q_ref)
+    # and the result is an eigen-decomposition (tolerances of the other GPU tests)
+    lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
+    nT = max(abs(lam[0]), abs(lam[-1]))
+    T = np.diag(d_np) + np.diag(e_np, 1) + np.diag(e_np, -1)
+    eps = np.finfo(float).eps
+    assert np.abs(T @ Q - Q * lam).sum(axis=0).max() / (n * nT * eps) <= 50
+    assert np.abs(Q.T @ Q - np.eye(n)).sum(axis=0).max() / (n * eps) <= 50
+
+
+def test_noalloc_split_path_inside_the_scratch_twice(tdc):
+    # orders whose default (split-path) workspace fits the fixed array: the split kernels
+    # run out of it
+    for n, seed in ((300, 23), (400, 24)):
+        assert tdc.workspace_size(n, tdc.default_opts(leaf=32)) <= SCRATCH
+        _same_as_workspace_path(tdc, n, seed, tdc.MERGE_AUTO)
+
+
 def test_noalloc_matches_workspace_path_twice(tdc):
-    # the library's default merge choice falls back to the FP64 merge inside the fixed scratch
-    opts = tdc.default_opts(leaf=32, merge_mode=tdc.MERGE_DENSE)
+    # orders whose split-path workspace does not fit: the FP64 merge inside the fixed array
     for n, seed in ((1000, 21), (700, 22)):
-        d_np, e_np = inputs.uniform_tridiag(n, seed)
-        d = torch.tensor(d_np, device=DEV)
-        e = torch.tensor(e_np, device=DEV)
-        lam, Q = _noalloc(tdc, d, e, tdc.default_opts(leaf=32))
-        lam_ref, Q_ref = tdc.eig(d, e, opts, check=True)
-        lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
-        lam_ref, Q_ref = lam_ref.cpu().numpy(), Q_ref.cpu().numpy()
-        nT = max(abs(lam_ref[0]), abs(lam_ref[-1]))
-        assert np.max(np.abs(lam - lam_ref)) <= 1e-12 * nT
-        compare_vectors(Q, Q_ref, lam_ref, 1e-8 * nT, 1e-9)
+        assert tdc.workspace_size(n, tdc.default_opts(leaf=32)) > SCRATCH
+        _same_as_workspace_path(tdc, n, seed, tdc.MERGE_DENSE)
 
 
 def test_noalloc_rejects_orders_beyond_its_scratch(tdc):
