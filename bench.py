@@ -6,17 +6,25 @@ quoted on.  One step = one full eigensolve T = Q diag(lam) Q^T through the C ABI
 (tdc_eig) with d, e resident in HBM.  The Q and internal buffers (2 x 2 GiB) are
 larger than L2, so no explicit flush is needed between steps.
 
+The default line also carries the merge comparison on the same matrix (dense FP64
+and structured merges, each with its own accuracy check and roofline), the other
+workloads (uniform n = 1024, the batch of 4096 tridiagonals under a CUDA graph,
+d ~ U(0,1) with e = 1 at n = 32768, and the adjoint of 256 problems of order 512),
+each timed with a few steps, and the FP64 CPU oracle timed on the host's cores on
+the headline matrix itself.
+
 Output: one JSON line (rank 0).  Under torchrun every rank solves its own copy
 (replicas, weak scaling); the timed region is bracketed by a barrier and
 synchronisations and the maximum over ranks is reported.
 
 ``--impl reference`` times the plain FP64 CPU oracle (the reference arm of this
 project: there is no other implementation of the method to run) on the host's
-cores on a bounded sample of the same workload.
+cores on the same matrix.
 """
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import subprocess
@@ -153,10 +161,20 @@ FAMILY = {"toeplitz16384": "toeplitz", "toeplitz4096": "toeplitz", "uniform1024"
           "clement30000": "clement", "hermite30000": "hermite", "sht30000": "sht"}
 
 
-def cpu_baseline(wl: str, budget_s: float = 20.0):
-    """Time the FP64 oracle on the host cores on a bounded sample of the workload:
-    the same matrix family at a smaller order, scaled by the cube of the order
-    ratio (the dense merges make the method O(n^3) on this family)."""
+def _oracle_time(d, e, leaf):
+    import oracle
+    t0 = time.perf_counter()
+    # the iteration cap only guards against a runaway root: the oracle bisects every root
+    # to the rounding level of its offset, which can take a few hundred halvings
+    oracle.eig(d, e, leaf=leaf, max_iter=2000)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl: str, budget_s: float = 180.0):
+    """Time the FP64 oracle on the host's cores on the workload's own matrix: one full
+    eigensolve at the workload's order.  Only when a quick estimate (the same family at
+    n = 2048, scaled by the cube of the order ratio) exceeds budget_s does it fall back
+    to that bounded sample, scaled, and the line says so."""
     import oracle
     from paper_2008_01990_gb300 import inputs
     oracle.build()
@@ -164,44 +182,59 @@ def cpu_baseline(wl: str, budget_s: float = 20.0):
     oracle.set_threads(cores)
     d_full, e_full, leaf, desc = workload(wl)
     n_full = d_full.size
-    n = min(n_full, 2048)
     fam = FAMILY[wl]
-    while True:
-        d, e = inputs.family(fam, n, 4 if fam == "c4" else 1)
-        t0 = time.perf_counter()
-        # the iteration cap only guards against a runaway root: bisection alone may need
-        # a few hundred halvings on these spectra before the bracket reaches rounding level
-        oracle.eig(d, e, leaf=leaf, max_iter=2000)
-        dt = time.perf_counter() - t0
-        if n >= n_full or dt * 8 > budget_s:
-            break
-        n *= 2
-    scale = (n_full / n) ** 3
-    return {"value": dt * scale, "unit": "s", "cores": oracle.get_threads(), "kind": "oracle",
-            "sample": "oracle eigensolve of the same family at n=%d (%.2f s measured), scaled by (%d/%d)^3"
-                      % (n, dt, n_full, n)}
+    n_s = min(n_full, 2048)
+    d_s, e_s = inputs.family(fam, n_s, 4 if fam == "c4" else 1)
+    t_s = _oracle_time(d_s, e_s, leaf)
+    est = t_s * (n_full / n_s) ** 3
+    if n_s == n_full:
+        dt, sample = t_s, "one oracle eigensolve of the workload's matrix (n=%d)" % n_full
+    elif est <= budget_s:
+        dt = _oracle_time(d_full, e_full, leaf)
+        sample = "one oracle eigensolve of the workload's matrix (n=%d), %.1f s wall" % (n_full, dt)
+    else:
+        dt = est
+        sample = ("oracle eigensolve of the same family at n=%d (%.2f s measured), scaled by (%d/%d)^3: the "
+                  "full order would exceed %.0f s" % (n_s, t_s, n_full, n_s, budget_s))
+    return {"value": dt, "unit": "s", "cores": oracle.get_threads(), "kind": "oracle", "sample": sample,
+            "scaled": n_s != n_full and est > budget_s}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle on the host's cores, on the same matrix as
+    the GPU arm.  Warm-up: W solves of the same family at n = 1024 (page-in, thread
+    start).  Timed: full-order eigensolves, as many as fit in about three minutes (at
+    least one, at most --steps); the line reports the number actually timed."""
+    import oracle
+    from paper_2008_01990_gb300 import inputs
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
+    oracle.build()
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
     wl = args.workload
-    times = []
-    info = None
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(wl, budget_s=max(2.0, 60.0 / max(1, args.warmup + args.steps)))
-        if i >= args.warmup:
-            times.append(cb["value"])
-        info = cb
-    v = float(np.mean(times))
     d, e, leaf, desc = workload(wl)
+    fam = FAMILY[wl]
+    dw, ew = inputs.family(fam, min(1024, d.size), 4 if fam == "c4" else 1)
+    for _ in range(args.warmup):
+        _oracle_time(dw, ew, leaf)
+    times = []
+    t_start = time.perf_counter()
+    while len(times) < max(1, args.steps):
+        times.append(_oracle_time(d, e, leaf))
+        if time.perf_counter() - t_start + times[-1] > 180.0:
+            break
+    v = float(np.mean(times))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "steps": len(times), "steps_requested": args.steps, "warmup": args.warmup,
+            "warmup_kind": "oracle solves of the same family at n=%d" % dw.size,
+            "ms_per_step": v * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc},
-            "cpu_baseline": {"value": v, "unit": "s", "cores": info["cores"], "kind": "oracle",
-                             "sample": info["sample"]},
+            "cpu_baseline": {"value": v, "unit": "s", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": "%d full oracle eigensolve(s) of the workload's matrix (n=%d)"
+                                       % (len(times), d.size)},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -260,7 +293,87 @@ def run_qhat(args):
     return 0
 
 
-def run_batched(args):
+def _event_ms(fn, steps, stream=None):
+    """Average device time of fn over `steps` calls, CUDA events on `stream`."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def full_ratios(d, e, lam, Q):
+    """Residual and orthogonality ratios on every column (small orders), device FP64."""
+    import torch
+    n = d.numel()
+    Tq = d[:, None] * Q
+    Tq[1:] += e[:, None] * Q[:-1]
+    Tq[:-1] += e[:, None] * Q[1:]
+    nT = max(abs(lam[0].item()), abs(lam[-1].item()))
+    res = torch.abs(Tq - Q * lam[None, :]).sum(dim=0).max().item() / (n * nT * EPS)
+    G = Q.t() @ Q - torch.eye(n, dtype=Q.dtype, device=Q.device)
+    orth = torch.abs(G).sum(dim=0).max().item() / (n * EPS)
+    return res, orth, nT
+
+
+def invariants(d, e, lam):
+    """|sum lam - trace| / (n ||T||) and |sum lam^2 - ||T||_F^2| / (n ||T||^2): the trace and
+    Frobenius invariants of the eigenvalues, in units of eps."""
+    n = d.numel()
+    nT = max(abs(lam[0].item()), abs(lam[-1].item()), 1e-300)
+    tr = abs(lam.sum().item() - d.sum().item()) / (n * nT * EPS)
+    fro = abs((lam * lam).sum().item() - ((d * d).sum().item() + 2 * (e * e).sum().item())) / (n * nT * nT * EPS)
+    return tr, fro
+
+
+def split_roofline(stats, split_ms, S, pk, pk_kind, note=""):
+    products = S * (S + 1) // 2
+    flops = float(stats["split_flops"])
+    if not (flops > 0 and split_ms > 0):
+        return None
+    achieved = flops * products / (split_ms * 1e-3) / 1e12
+    return {"bound": "tensor", "kernel": "k_gemm_split (BF16 digit products, tcgen05, TMEM FP32 levels)",
+            "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["bf16_tflops"],
+            "peak_kind": "bf16_tflops (burst) of %s%s" % (pk_kind, note),
+            "fp64_equivalent_tflops": flops / (split_ms * 1e-3) / 1e12, "bf16_products_per_fp64_product": products}
+
+
+def config_c1(args):
+    """uniform(-1,1) n = 1024 (seed 1), leaf 32, the library's default merge."""
+    import torch
+    from paper_2008_01990_gb300 import tdc
+    dev = torch.device("cuda", 0)
+    d_np, e_np, leaf, desc = workload("uniform1024")
+    d, e = torch.tensor(d_np, device=dev), torch.tensor(e_np, device=dev)
+    o = tdc.default_opts(leaf=leaf)
+    n = d.numel()
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    Q = torch.empty(n, n, dtype=torch.float64, device=dev).t()
+    ws = tdc.workspace(tdc.workspace_size(n, o), dev)
+    step = lambda: tdc.eig(d, e, o, ws=ws, lam=lam, Q=Q)
+    for _ in range(3):
+        step()
+    st = tdc.sync_status()
+    ms = _event_ms(step, 20)
+    res, orth, nT = full_ratios(d, e, lam, Q)
+    tr, fro = invariants(d, e, lam)
+    oi = tdc.default_opts(leaf=leaf, collect_stats=1)
+    tdc.eig(d, e, oi, ws=ws, lam=lam, Q=Q)
+    stats = tdc.get_stats()
+    return {"workload": desc, "ms": ms, "steps": 20, "status": tdc.strerror(st),
+            "checks": {"residual": res, "orthogonality": orth, "columns": "all", "trace_eps": tr,
+                       "frobenius_eps": fro, "within_bounds": bool(res <= 50 and orth <= 50)},
+            "bound": "latency: %d kernel launches per solve on a 1024-order tree" % stats["launches"],
+            "phase_ms": stats["phase_ms"], "launches_per_solve": int(stats["launches"])}
+
+
+def config_c3(args, steps=3, warmup=3):
     """The batched workload: 4096 tridiagonals, n_b uniform in [64, 2048] (seed 3), entries
     uniform(-1,1) (seed 3 + b), solved by one tdc_eig_batched call replayed from a CUDA
     graph, options chosen by the autotuner (outside the timed region)."""
@@ -271,10 +384,12 @@ def run_batched(args):
     d, e, offs = inputs.batched_uniform(sizes, 3)
     qoffs = np.concatenate([[0], np.cumsum(sizes.astype(np.int64) ** 2)])
     dt, et = torch.tensor(d, device=dev), torch.tensor(e, device=dev)
+    t0 = time.perf_counter()
     if args.leaf or args.split_min_k:
         opts = tdc.default_opts(leaf=args.leaf or 32, split_min_K=args.split_min_k or 128)
     else:
         opts = autotune.tune_batched(sizes, dt, et, offs[:-1], cache_path=None)
+    tune_s = time.perf_counter() - t0
     lam = torch.empty(int(offs[-1]), dtype=torch.float64, device=dev)
     Q = torch.empty(int(qoffs[-1]), dtype=torch.float64, device=dev)
     ws = tdc.workspace(tdc.batched_workspace_size(sizes, opts), dev)
@@ -285,34 +400,88 @@ def run_batched(args):
     g = torch.cuda.CUDAGraph()
     with torch.cuda.graph(g, stream=s):
         tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, opts, ws=ws, stream=s)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.replay()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        g.replay()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = _event_ms(g.replay, steps)
     st = tdc.sync_status()
+    # checks outside the timed region: every problem's eigenvalues sorted and finite;
+    # residual and orthogonality ratios on 16 problems spread over the size range
+    lam_h = lam.cpu().numpy()
+    sorted_ok = bool(np.all(np.isfinite(lam_h)) and all(
+        np.all(np.diff(lam_h[offs[b]:offs[b] + sizes[b]]) >= 0) for b in range(len(sizes))))
+    order = np.argsort(sizes, kind="stable")
+    pick = sorted(set(int(order[i]) for i in np.linspace(0, len(sizes) - 1, 16).round().astype(int)))
+    worst_res = worst_orth = 0.0
+    for b in pick:
+        nb = int(sizes[b])
+        Qb = Q[int(qoffs[b]):int(qoffs[b]) + nb * nb].view(nb, nb).t()
+        r, o_, _ = full_ratios(dt[offs[b]:offs[b] + nb], et[offs[b]:offs[b] + nb - 1], lam[offs[b]:offs[b] + nb], Qb)
+        worst_res, worst_orth = max(worst_res, r), max(worst_orth, o_)
     # one more solve with statistics (outside the timed region): launches and phases
     ost = tdc.default_opts(leaf=opts.leaf, split_min_K=opts.split_min_K, collect_stats=1)
     tdc.eig_batched(sizes, dt, et, offs[:-1], qoffs[:-1], lam, Q, ost, ws=ws)
     stats = tdc.get_stats()
-    print(json.dumps({"workload": "batched4096" if args.batch == 4096 else "batched%d" % args.batch,
-                      "ms_per_batch": ms, "problems_per_s": args.batch / (ms * 1e-3),
-                      "leaf": opts.leaf, "split_min_K": opts.split_min_K, "status": st,
-                      "sum_n": int(sizes.sum()), "q_bytes": int(qoffs[-1]) * 8,
-                      "launches_per_solve": int(stats["launches"]), "phase_ms": stats["phase_ms"],
-                      "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"],
-                                             "handoffs": stats.get("secular_handoffs")},
-                      "K_per_level": stats["sum_K"], "n_per_level": stats["sum_n"]}), flush=True)
-    return 0
+    pk, pk_kind = peaks()
+    out = {"workload": "4096 tridiagonals, n_b uniform in [64,2048] (seed 3), d, e uniform(-1,1)"
+                       if args.batch == 4096 else "batched%d" % args.batch,
+           "ms_per_batch": ms, "problems_per_s": args.batch / (ms * 1e-3), "steps": steps,
+           "leaf": opts.leaf, "split_min_K": opts.split_min_K, "autotune_s": tune_s, "status": tdc.strerror(st),
+           "graph": "one tdc_eig_batched call captured and replayed", "sum_n": int(sizes.sum()),
+           "q_bytes": int(qoffs[-1]) * 8,
+           "checks": {"eigenvalues_sorted_finite": sorted_ok, "problems_checked": len(pick),
+                      "residual_max": worst_res, "orthogonality_max": worst_orth,
+                      "within_bounds": bool(worst_res <= 50 and worst_orth <= 50)},
+           "launches_per_solve": int(stats["launches"]), "phase_ms": stats["phase_ms"],
+           "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"],
+                                  "handoffs": stats.get("secular_handoffs")},
+           "K_per_level": stats["sum_K"], "n_per_level": stats["sum_n"],
+           "split_roofline": split_roofline(stats, stats["phase_ms"]["split_mma"], opts.split_slices, pk, pk_kind,
+                                            "; phase time with statistics on, two streams")}
+    del g, ws, Q, lam
+    torch.cuda.empty_cache()
+    return out
 
 
-def run_backward(args):
+def config_c4(args, steps=3, warmup=3):
+    """d ~ U(0,1), e = 1, n = 32768 (seed 4), leaf and split threshold autotuned on the matrix."""
+    import torch
+    from paper_2008_01990_gb300 import autotune, tdc
+    dev = torch.device("cuda", 0)
+    d_np, e_np, _, desc = workload("c4_32768")
+    d, e = torch.tensor(d_np, device=dev), torch.tensor(e_np, device=dev)
+    n = d.numel()
+    t0 = time.perf_counter()
+    t = autotune.tune_single(d, e, tdc.MERGE_AUTO, cache_path=None)
+    tune_s = time.perf_counter() - t0
+    o = tdc.default_opts(leaf=t.leaf, split_min_K=t.split_min_K)
+    lam = torch.empty(n, dtype=torch.float64, device=dev)
+    Q = torch.empty(n, n, dtype=torch.float64, device=dev).t()
+    ws = tdc.workspace(tdc.workspace_size(n, o), dev)
+    step = lambda: tdc.eig(d, e, o, ws=ws, lam=lam, Q=Q)
+    for _ in range(warmup):
+        step()
+    st = tdc.sync_status()
+    ms = _event_ms(step, steps)
+    oi = tdc.default_opts(leaf=t.leaf, split_min_K=t.split_min_K, collect_stats=1)
+    tdc.eig(d, e, oi, ws=ws, lam=lam, Q=Q)
+    stats = tdc.get_stats()
+    res, orth, nT = sampled_ratios(lam, Q, d, e)
+    tr, fro = invariants(d, e, lam)
+    pk, pk_kind = peaks()
+    out = {"workload": desc.split(" leaf ")[0] + " leaf %d, split_min_K %d (autotuned)" % (t.leaf, t.split_min_K),
+           "ms": ms, "steps": steps, "autotune_s": tune_s, "status": tdc.strerror(st),
+           "checks": {"residual": res, "orthogonality": orth, "sampled_columns": 256, "trace_eps": tr,
+                      "frobenius_eps": fro, "within_bounds": bool(res <= 50 and orth <= 50)},
+           "split_level_max": stats["split_level_max"], "phase_ms": stats["phase_ms"],
+           "K_per_level": stats["sum_K"],
+           "roofline": split_roofline(stats, stats["phase_ms"]["split_mma"], o.split_slices, pk, pk_kind,
+                                      "; phase time of one solve with statistics on")}
+    del ws, Q, lam
+    torch.cuda.empty_cache()
+    return out
+
+
+def config_c5(args, steps=5, warmup=3):
     """The backward workload: 256 tridiagonals of order 512 (d, e uniform(-1,1), seed 5,
     redrawn until the smallest eigen-gap is >= 1e-5 ||T||), loss sum w_j lam_j + sum G_ij Q_ij
     with w, G ~ N(0,1); one step = batched forward solve + batched adjoint."""
@@ -335,36 +504,35 @@ def run_backward(args):
         loss.backward()
         return dd.grad, ee.grad
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    ms = _event_ms(step, steps)
     # adjoint alone (the two n^3 products per problem)
     lam, Q = tdc.eigh_tridiagonal(d, e, opts)
     Qs = Q.transpose(1, 2).contiguous()
     Gs_t = G.transpose(1, 2).contiguous()
     tdc.eig_backward_batched(lam, Qs, w, Gs_t)
-    torch.cuda.synchronize()
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record()
-    for _ in range(args.steps):
-        tdc.eig_backward_batched(lam, Qs, w, Gs_t)
-    a1.record()
-    torch.cuda.synchronize()
-    ams = a0.elapsed_time(a1) / args.steps
+    ams = _event_ms(lambda: tdc.eig_backward_batched(lam, Qs, w, Gs_t), steps)
+    # check (closed form, Hellmann-Feynman): with Q_bar = 0 the cotangents are
+    # d_bar_i = sum_k w_k Q_ik^2 and e_bar_i = 2 sum_k w_k Q_ik Q_i+1,k
+    db, eb = tdc.eig_backward_batched(lam, Qs, w, None)
+    Qm = Q  # (B, n, n) with Q[b] the eigenvector matrix
+    db_ref = torch.einsum("bik,bk->bi", Qm * Qm, w)
+    eb_ref = 2.0 * torch.einsum("bik,bk->bi", Qm[:, :-1, :] * Qm[:, 1:, :], w)
+    scale = torch.abs(w).max().item()
+    hf = max(torch.max(torch.abs(db - db_ref)).item(), torch.max(torch.abs(eb - eb_ref)).item()) / scale
     flops = B * 4.0 * n ** 3
-    print(json.dumps({"workload": "backward256x512", "ms_forward_backward": ms, "ms_adjoint": ams,
-                      "adjoint_tflops_fp64_equivalent": flops / (ams * 1e-3) / 1e12, "min_gap_rel": float(gaps.min()),
-                      "draws": int(draws)}), flush=True)
-    return 0
+    return {"workload": "backward: 256 x n=512, d, e uniform(-1,1) (seed 5), min gap >= 1e-5 ||T||",
+            "ms_forward_backward": ms, "ms_adjoint": ams, "steps": steps,
+            "adjoint_tflops_fp64_equivalent": flops / (ams * 1e-3) / 1e12,
+            "checks": {"hellmann_feynman_max_err_over_max_w": hf, "within_bounds": bool(hf <= 1e-12)},
+            "min_gap_rel": float(gaps.min()), "draws": int(draws)}
+
+
+# DRAM bytes of k_gemm_split over one eigensolve, summed over its launches, from
+# single-pass ncu captures of the kernel as it stands; keyed by the exact
+# configuration (workload, leaf, split_min_K, split_chunk_k), null for any other
+TRAFFIC = {}
 
 
 def run_ours(args):
@@ -381,8 +549,6 @@ def run_ours(args):
     n = d_np.size
     mode = {"dense": tdc.MERGE_DENSE, "auto": tdc.MERGE_AUTO, "structured": tdc.MERGE_STRUCTURED,
             "split": tdc.MERGE_SPLIT}[args.merge]
-    # statistics on: the library records CUDA events around its phases on the call's
-    # stream, so the per-kernel times below come from the timed steps themselves
     if args.leaf:
         leaf = args.leaf
         desc = desc.split(" leaf ")[0] + " leaf %d" % leaf + (" seed" + desc.split(" seed")[1] if " seed" in desc else "")
@@ -397,7 +563,8 @@ def run_ours(args):
         desc = desc.split(" leaf ")[0] + " leaf %d (autotuned, split_min_K %d) seed 4" % (leaf, t.split_min_K)
     if args.split_chunk_k >= 0:
         kw["split_chunk_k"] = args.split_chunk_k
-    opts = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1, **kw)
+    opts = tdc.default_opts(leaf=leaf, merge_mode=mode, **kw)
+    opts_i = tdc.default_opts(leaf=leaf, merge_mode=mode, collect_stats=1, **kw)
     lam = torch.empty(n, dtype=torch.float64, device=dev)
     Q = torch.empty(n, n, dtype=torch.float64, device=dev).t()
     wsb = tdc.workspace(tdc.workspace_size(n, opts), dev)
@@ -406,11 +573,14 @@ def run_ours(args):
     def step():
         tdc.eig(d, e, opts, ws=wsb, lam=lam, Q=Q, stream=stream)
 
+    progress("inputs and workspace ready")
     for _ in range(args.warmup):
         step()
     st = tdc.sync_status(stream)
+    progress("warm-up done")
     if st not in (0, tdc.TDC_WPRECISION):
         raise RuntimeError("device status %d (%s)" % (st, tdc.strerror(st)))
+    # the timed region: K eigensolves, statistics off, clocks sampled meanwhile
     sampler = ClockSampler(local)
     if ws_n > 1:
         dist.barrier()
@@ -418,11 +588,9 @@ def run_ours(args):
     sampler.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    phases = []
     e0.record(stream)
     for _ in range(args.steps):
         step()
-        phases.append(tdc.get_stats())
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -430,45 +598,47 @@ def run_ours(args):
     if ws_n > 1:
         ms = max_over_ranks(ms, dist, dev)
         dist.barrier()
-    # per-phase CUDA-event times of the timed steps (same stream) and algorithmic flops
+    # an instrumented region (statistics on: the library records CUDA events around its
+    # phases on the stream each phase runs on; one host synchronisation per solve):
+    # per-kernel times, flops and launch counts of the same solves
+    isteps = max(1, min(args.steps, 5))
+    phases = []
+    i0 = torch.cuda.Event(enable_timing=True)
+    i1 = torch.cuda.Event(enable_timing=True)
+    i0.record(stream)
+    for _ in range(isteps):
+        tdc.eig(d, e, opts_i, ws=wsb, lam=lam, Q=Q, stream=stream)
+        phases.append(tdc.get_stats())
+    i1.record(stream)
+    torch.cuda.synchronize()
+    ims = i0.elapsed_time(i1) / isteps
+    progress("timed and instrumented regions done")
     stats = phases[-1]
     S = opts.split_slices
-    products = S * (S + 1) // 2
     split_ms = float(np.median([p["phase_ms"]["split_mma"] for p in phases]))
     digits_ms = float(np.median([p["phase_ms"]["split_digits"] for p in phases]))
     dense_ms = float(np.median([p["phase_ms"]["gemm_fp64"] for p in phases]))
     split_flops = float(stats["split_flops"])
     dense_flops = float(sum(stats["gemm_flops"])) - split_flops
     pk, pk_kind = peaks()
-    # DRAM bytes of k_gemm_split over one eigensolve, summed over its launches, from
-    # single-pass ncu captures of this kernel; keyed by the exact configuration,
-    # absent (null) for any other
-    traffic_table = {("toeplitz16384", 64, 128): 50.42e9, ("c4_32768", 16, 64): 16.31e9}
-    traffic = traffic_table.get((args.workload, opts.leaf, opts.split_min_K))
     if split_flops > 0 and split_ms > 0:
-        achieved = split_flops * products / (split_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": "k_gemm_split (BF16 digit products, tcgen05, TMEM FP32 levels)",
-                "achieved": achieved, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
-                "frac": achieved / pk["bf16_tflops"], "traffic": traffic,
-                "traffic_scope": "DRAM bytes of all k_gemm_split launches of one eigensolve (ncu)",
-                "algorithmic_bytes": stats.get("split_bytes"),
-                "peak_kind": "bf16_tflops (burst) of %s: the kernel runs in bursts of tens of ms and the SM "
-                             "clock stays at its maximum (see clocks)" % pk_kind,
-                "frac_of_sustained": achieved / pk["bf16_tflops_sustained"],
-                "fp64_equivalent_tflops": split_flops / (split_ms * 1e-3) / 1e12,
-                "bf16_products_per_fp64_product": products}
+        roof = split_roofline(stats, split_ms, S, pk, pk_kind,
+                              ": the kernel runs in bursts of tens of ms and the SM clock stays at its maximum "
+                              "(see clocks)")
+        roof["traffic"] = TRAFFIC.get((args.workload, opts.leaf, opts.split_min_K, opts.split_chunk_k))
+        roof["traffic_scope"] = "DRAM bytes of all k_gemm_split launches of one eigensolve (ncu)"
+        roof["algorithmic_bytes"] = stats.get("split_bytes")
+        roof["frac_of_sustained"] = roof["achieved"] / pk["bf16_tflops_sustained"]
+        roof["timing"] = "median phase time over %d instrumented solves" % isteps
         qu_tflops = (split_flops + dense_flops) / ((split_ms + digits_ms + dense_ms) * 1e-3) / 1e12
     elif stats["struct_flops"] > 0:
-        # structured path: the executed flops (dense near-diagonal tiles and the two thin
-        # products of the low-rank tiles), not the dense flops it avoids
         sflops = float(stats["struct_flops"])
         achieved = sflops / (dense_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": "k_gemm_dense (near-diagonal) + k_struct_w + k_struct_apply (FP64)",
                 "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
-                "executed_flops": sflops, "dense_equivalent_flops": dense_flops,
-                "note": "the phase also holds the FP32 SRRSC pivot searches"}
+                "executed_flops": sflops, "dense_equivalent_flops": dense_flops}
         qu_tflops = dense_flops / (dense_ms * 1e-3) / 1e12
     else:
         achieved = dense_flops / (dense_ms * 1e-3) / 1e12
@@ -477,42 +647,6 @@ def run_ours(args):
                 "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
                 "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}
         qu_tflops = achieved
-    # the plain dense FP64 merge on the same input, for the structured/split comparison
-    compare = {args.merge: ms / 1e3}
-    if args.merge != "dense" and not args.no_compare:
-        od = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_DENSE)
-        tdc.eig(d, e, od, ws=wsb, lam=lam, Q=Q, stream=stream)
-        c0 = torch.cuda.Event(enable_timing=True)
-        c1 = torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        tdc.eig(d, e, od, ws=wsb, lam=lam, Q=Q, stream=stream)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        compare["dense"] = c0.elapsed_time(c1) / 1e3
-        tdc.eig(d, e, opts, ws=wsb, lam=lam, Q=Q, stream=stream)  # leave the timed configuration's result
-    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
-    d_h = torch.tensor(d_np).pin_memory()
-    e_h = torch.tensor(e_np).pin_memory()
-    lam_h = torch.empty(n, dtype=torch.float64).pin_memory()
-    Q_h = torch.empty(n, n, dtype=torch.float64).pin_memory()
-    d_d = torch.empty_like(d)
-    e_d = torch.empty_like(e)
-    torch.cuda.synchronize()
-    ee0 = torch.cuda.Event(enable_timing=True)
-    ee1 = torch.cuda.Event(enable_timing=True)
-    e2e_steps = max(1, min(args.steps, 3))
-    ee0.record(stream)
-    for _ in range(e2e_steps):
-        d_d.copy_(d_h, non_blocking=True)
-        e_d.copy_(e_h, non_blocking=True)
-        tdc.eig(d_d, e_d, opts, ws=wsb, lam=lam, Q=Q, stream=stream)
-        lam_h.copy_(lam, non_blocking=True)
-        Q_h.copy_(Q.t(), non_blocking=True)  # the storage of the column-major Q
-    ee1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
-    if ws_n > 1:
-        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
     # accuracy of the timed configuration (outside the timed region)
     res, orth, nT = sampled_ratios(lam, Q, d, e)
     lam_err = None
@@ -524,6 +658,87 @@ def run_ours(args):
         # eigenvalues -(n-1), -(n-3), ..., n-1; ||T||_2 = n - 1
         ref = torch.arange(-(n - 1), n, 2, dtype=torch.float64, device=dev)
         lam_err = torch.max(torch.abs(lam - ref)).item() / (n - 1)
+
+    def accuracy():
+        r, o_, _ = sampled_ratios(lam, Q, d, e)
+        le = None
+        if args.workload.startswith("toeplitz"):
+            le = torch.max(torch.abs(lam - ref)).item() / 4.0
+        return {"lam_err_over_normT": le, "residual": r, "orthogonality": o_, "sampled_columns": 256,
+                "within_bounds": bool(r <= 50 and o_ <= 50)}
+
+    # the merge comparison on the same input: the plain dense FP64 merge and the
+    # structured (SRRSC) merge, one warm-up and one timed solve each
+    compare = {args.merge: ms / 1e3}
+    compare_detail = {}
+    if args.merge != "dense" and not args.no_compare:
+        od = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_DENSE, collect_stats=1)
+        tdc.eig(d, e, od, ws=wsb, lam=lam, Q=Q, stream=stream)
+        tdc.eig(d, e, od, ws=wsb, lam=lam, Q=Q, stream=stream)
+        sd = tdc.get_stats()
+        compare["dense"] = sd["phase_ms"]["total"] / 1e3
+        progress("dense merge done")
+        dfl = float(sum(sd["gemm_flops"]))
+        compare_detail["dense"] = {
+            "s": compare["dense"], "test_ratios": accuracy(),
+            "roofline": {"bound": "alu", "kernel": "k_gemm_dense (FP64 Q*U with generated U)",
+                         "achieved": dfl / (sd["phase_ms"]["gemm_fp64"] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": dfl / (sd["phase_ms"]["gemm_fp64"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz"}}
+    if args.merge not in ("dense", "structured") and not args.no_compare and n >= 4096:
+        osd = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_STRUCTURED, collect_stats=1)
+        wss = tdc.workspace(tdc.workspace_size(n, osd), dev)
+        tdc.eig(d, e, osd, ws=wss, lam=lam, Q=Q, stream=stream)
+        tdc.eig(d, e, osd, ws=wss, lam=lam, Q=Q, stream=stream)
+        ss = tdc.get_stats()
+        del wss
+        compare["structured"] = ss["phase_ms"]["total"] / 1e3
+        progress("structured merge done")
+        sfl = float(ss["struct_flops"])
+        kept = max(1, ss["lr_tiles"] - ss["lr_dense_fallbacks"])
+        compare_detail["structured"] = {
+            "s": compare["structured"], "test_ratios": accuracy(),
+            "options": {"lr_tile": osd.lr_tile, "structured_min_K": osd.structured_min_K, "lr_tol": osd.lr_tol,
+                        "rank_cap": 64},
+            "srrsc": {"far_tiles": ss["lr_tiles"], "mean_rank": ss["lr_rank_sum"] / kept,
+                      "max_rank": ss["lr_rank_max"], "dense_fallbacks": ss["lr_dense_fallbacks"]},
+            "gemm_fp64_ms": ss["phase_ms"]["gemm_fp64"],
+            "roofline": {"bound": "alu",
+                         "kernel": "k_gemm_dense (near-diagonal tiles) + k_struct_w + k_struct_apply (FP64)",
+                         "executed_flops": sfl,
+                         "achieved": sfl / (ss["phase_ms"]["gemm_fp64"] * 1e-3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s",
+                         "frac": sfl / (ss["phase_ms"]["gemm_fp64"] * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
+                         "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
+                         "note": "executed flops only (the dense flops it avoids are not counted); the phase "
+                                 "also holds the FP32 SRRSC pivot searches"}}
+    if compare_detail:
+        tdc.eig(d, e, opts, ws=wsb, lam=lam, Q=Q, stream=stream)  # leave the timed configuration's result
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    d_h = torch.tensor(d_np).pin_memory()
+    e_h = torch.tensor(e_np).pin_memory()
+    lam_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    Q_h = torch.empty(n, n, dtype=torch.float64).pin_memory()
+    d_d = torch.empty_like(d)
+    e_d = torch.empty_like(e)
+    torch.cuda.synchronize()
+    ee0 = torch.cuda.Event(enable_timing=True)
+    ee1 = torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(1, min(args.steps, 10))
+    ee0.record(stream)
+    for _ in range(e2e_steps):
+        d_d.copy_(d_h, non_blocking=True)
+        e_d.copy_(e_h, non_blocking=True)
+        tdc.eig(d_d, e_d, opts, ws=wsb, lam=lam, Q=Q, stream=stream)
+        lam_h.copy_(lam, non_blocking=True)
+        Q_h.copy_(Q.t(), non_blocking=True)  # the storage of the column-major Q
+    ee1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
+    progress("end-to-end done")
+    if ws_n > 1:
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    del d_h, e_h, lam_h, Q_h
     if rank != 0:
         if ws_n > 1:
             dist.destroy_process_group()
@@ -541,11 +756,14 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64" if args.merge == "dense" else "f64 (Q*U as bf16 digit products, fp32 accumulate)",
         "data": "synthetic",
-        "config": {"workload": desc, "merge": args.merge, "split_chunk_k": opts.split_chunk_k, "l2": "no flush: Q and workspace (%.1f GiB) exceed the 129 MB L2" % ((8 * n * n + wsb.numel()) / 2**30),
+        "config": {"workload": desc, "merge": args.merge, "split_chunk_k": opts.split_chunk_k,
+                   "l2": "no flush: Q and workspace (%.1f GiB) exceed the 129 MB L2" % ((8 * n * n + wsb.numel()) / 2**30),
                    "parallelism": "replicas" if ws_n > 1 else "single"},
         "roofline": roof,
         "qu_tflops_fp64_equivalent": qu_tflops,
         "merge_compare_s": compare,
+        "merge_compare": compare_detail,
+        "instrumented_ms_per_step": ims,
         "phase_ms": stats["phase_ms"],
         "K_per_level": stats["sum_K"],
         "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"]},
@@ -556,17 +774,36 @@ def run_ours(args):
         "gpu_launches": int(stats["launches"]) * args.steps,
         "clocks": clocks,
         "e2e": {"value": job_seconds_per_solve(e2e_ms, ws_n), "unit": "s", "h2d_bytes_per_step": 2 * 8 * n - 8,
-                "d2h_bytes_per_step": 8 * n + 8 * n * n},
+                "d2h_bytes_per_step": 8 * n + 8 * n * n, "steps": e2e_steps},
     }
+    if ws_n == 1 and args.workload == "toeplitz16384" and not args.no_configs:
+        del wsb, Q, lam
+        torch.cuda.empty_cache()
+        cfg = {}
+        for key, fn in (("c1_uniform1024", config_c1), ("c3_batched4096", config_c3), ("c4_split32768", config_c4),
+                        ("c5_backward256x512", config_c5)):
+            cfg[key] = fn(args)
+            progress(key + " done")
+        line["configs"] = cfg
     if not args.no_cpu_baseline and ws_n == 1:
         line["cpu_baseline"] = cpu_baseline(args.workload, budget_s=args.cpu_budget)
+        progress("cpu baseline done")
     print(json.dumps(line), flush=True)
     if ws_n > 1:
         dist.destroy_process_group()
     return 0
 
 
+def progress(msg):
+    """One line on stderr per stage (the JSON line alone goes to stdout)."""
+    print("bench: %s (%.1f s)" % (msg, time.perf_counter() - T_START), file=sys.stderr, flush=True)
+
+
+T_START = time.perf_counter()
+
+
 def main():
+    faulthandler.enable()
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -584,16 +821,20 @@ def main():
                     help="drain the split product's level sums every this many terms (multiple of 16; 0: once "
                          "per tile; default: the library's)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-configs", action="store_true", help="default workload only: skip the other workloads")
+    ap.add_argument("--cpu-budget", type=float, default=180.0,
+                    help="seconds the CPU oracle may take on the full matrix before a scaled sample is used")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "qhat8192":
         return run_qhat(args)
     if args.workload == "batched4096":
-        return run_batched(args)
+        print(json.dumps(config_c3(args, steps=args.steps, warmup=args.warmup)), flush=True)
+        return 0
     if args.workload == "backward256":
-        return run_backward(args)
+        print(json.dumps(config_c5(args, steps=args.steps, warmup=args.warmup)), flush=True)
+        return 0
     return run_ours(args)
 
 

@@ -28,9 +28,8 @@
  *   - the return value is a status: TDC_OK (0); -i when argument i (1-based)
  *     is invalid, checked on the host before anything is enqueued; or one of
  *     the TDC_E* codes below.  Device-side failures (secular non-convergence,
- *     a bounded wait that expired) and warnings are recorded in the call's
- *     status slot (the first 256 bytes of its workspace), which
- *     tdc_sync_status() returns;
+ *     a bounded wait that expired) and warnings are recorded in the status
+ *     slot of the call's stream, which tdc_sync_status() returns;
  *   - inputs d and e are never modified.
  */
 #ifndef TDC_H
@@ -125,6 +124,11 @@ typedef struct {
   float split_level_max;                 /* largest |level sum| / 2^24 that a hand-off of the split
                                             product's FP32 accumulators held (levels 0-4); the
                                             product is exact while it stays below 1 */
+  int64_t lr_tiles;                      /* structured path: off-diagonal tiles compressed by SRRSC */
+  int64_t lr_rank_sum;                   /* sum of their ranks (mean rank = lr_rank_sum / (lr_tiles -
+                                            lr_dense_fallbacks)) */
+  int64_t lr_dense_fallbacks;            /* tiles whose rank exceeded the cap and stayed dense */
+  int64_t lr_rank_max;                   /* largest rank kept in low-rank form */
 } tdc_stats;
 
 /* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,
@@ -234,13 +238,13 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
 
 /* Synchronise `stream` and return the device status of the last call enqueued on it
  * (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE, TDC_EUNSUPPORTED, or the warning
- * TDC_WPRECISION), then clear it.  Every call that takes a workspace keeps its status
- * in the first 256 bytes of that workspace (cleared when the call is enqueued), so
- * calls on different streams with different workspaces never see each other's status;
- * read it before the workspace is reused.  A stream that no call was enqueued on
- * (for example one a captured graph is replayed on) reports the last call made on
- * the device.  tdc_rank_one called without a workspace uses a per-device word that
- * every such call shares. */
+ * TDC_WPRECISION), then clear it.  Each stream that calls the library gets its own
+ * status slot (two words in a fixed device array of the library, assigned on the
+ * stream's first call; beyond 1024 streams per device the later ones share the last
+ * slot).  A call clears its stream's slot when it is enqueued, so calls on different
+ * streams never see or clear each other's status, and the status outlives the call's
+ * workspace.  A stream that no call was enqueued on (for example one a captured
+ * graph is replayed on) reports the slot of the last call made on the device. */
 int tdc_sync_status(tdc_stream_t stream);
 
 /* Copy the statistics of the last call made with collect_stats = 1. */

@@ -20,47 +20,52 @@
 
 namespace tdc {
 
-// Device-side status.  Every call that has a workspace keeps its status in a slot
-// of two words at the start of that workspace (cleared when the call is enqueued):
-// the first error and the warning bits.  The host remembers, per device and stream,
-// the slot of the last call enqueued there, so that tdc_sync_status(stream) reads the
-// status of that call and of no other.  Calls without a workspace (tdc_rank_one
-// given none) use the per-device word g_status.
-__device__ int g_status[2];
+// Device-side status.  Every stream that calls the library gets a slot of two words
+// in a fixed device array (assigned on its first call; loaded with the library, so no
+// allocation): the first error and the warning bits.  A call clears its stream's slot
+// when it is enqueued and its kernels write there, so tdc_sync_status(stream) reads
+// the status of the last call on that stream and of no other, whatever became of the
+// call's workspace.  With more streams than slots, later streams share the last slot.
+constexpr int kStatusSlots = 1024;
+__device__ int g_status_slots[kStatusSlots][2];
 
 static std::mutex g_mu;
-static int* g_status_ptr[64];
-static int* g_last_slot[64];                               // slot of the last call per device
-static std::map<std::pair<int, cudaStream_t>, int*> g_stream_slot;  // slot of the last call per stream
+static int* g_slots_base[64];                            // device address of the slot array per device
+static int g_slots_used[64];
+static int* g_last_slot[64];                             // slot of the last call per device
+static std::map<std::pair<int, cudaStream_t>, int*> g_stream_slot;  // slot of each stream
 static tdc_stats g_last_stats;
 
-static int* status_ptr() {
+// The slot of (current device, stream), assigned on first use; NULL on failure.
+static int* stream_slot(cudaStream_t s, bool assign) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_status_ptr[dev]) {
+  if (!g_slots_base[dev]) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_status) != cudaSuccess) return nullptr;
-    g_status_ptr[dev] = (int*)p;
+    if (cudaGetSymbolAddress(&p, g_status_slots) != cudaSuccess || !p) return nullptr;
+    g_slots_base[dev] = (int*)p;
   }
-  return g_status_ptr[dev];
+  auto it = g_stream_slot.find({dev, s});
+  if (it != g_stream_slot.end()) return it->second;
+  if (!assign) return g_last_slot[dev];
+  const int idx = std::min(g_slots_used[dev], kStatusSlots - 1);
+  if (g_slots_used[dev] < kStatusSlots) ++g_slots_used[dev];
+  int* slot = g_slots_base[dev] + 2 * idx;
+  g_stream_slot[{dev, s}] = slot;
+  return slot;
 }
 
-static constexpr size_t kStatusSlotBytes = 256;  // keeps what follows 256-byte aligned
-
-// Clear a call's status slot on its stream and remember it as the stream's last call.
-static cudaError_t begin_status(int* slot, cudaStream_t s) {
+// Clear the stream's status slot (stream-ordered) and note it as the device's last.
+static int* begin_status(cudaStream_t s) {
+  int* slot = stream_slot(s, true);
+  if (!slot) return nullptr;
+  if (cudaMemsetAsync(slot, 0, 2 * sizeof(int), s) != cudaSuccess) return nullptr;
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(slot, 0, 2 * sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  if (dev >= 0 && dev < 64) {
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_stream_slot[{dev, s}] = slot;
-    g_last_slot[dev] = slot;
-  }
-  return cudaSuccess;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_last_slot[dev] = slot;
+  return slot;
 }
 
 static int depth_of(int64_t n, int leaf) {
@@ -239,7 +244,7 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
 
 // workspace carving
 struct Layout {
-  size_t status, prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
+  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
 };
 
 static constexpr int kVecD = 27;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz, 8 boundary rows)
@@ -252,7 +257,6 @@ static int64_t tiles_per_set(const HostPlan& H) { return 4 * H.Mmax + 5 + 2 * H.
 static Layout layout_of(const HostPlan& H) {
   Layout L;
   size_t o = 0;
-  L.status = o; o = align_up(o + kStatusSlotBytes);
   L.prob = o; o = align_up(o + sizeof(Problem) * std::max<size_t>(1, H.prob.size()));
   // two sets of the per-level vectors and merge data, by level parity: a level reads
   // its children's results from the other set
@@ -408,10 +412,10 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   SA.svr = (double*)(base + L.svr);
   SA.scolpiv = (int*)(base + L.scolpiv);
   SA.W = (double*)(base + L.sw);
-  P.status = (int*)(base + L.status);
   P.stats = o.collect_stats ? (Stats*)(base + L.stats) : nullptr;
   if (H.N == 0) return TDC_OK;
-  if (begin_status(P.status, s) != cudaSuccess) return TDC_ECUDA;
+  P.status = begin_status(s);
+  if (!P.status) return TDC_ECUDA;
   // PP[k]: the plan of the levels of parity k (their vectors in set k, the children's
   // in the other); PP[0] also serves the leaves and the output
   Plan PP[2] = {P, P};
@@ -501,6 +505,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       SA.ldw = ldw;
       SA.status = P.status;
       SA.flops = P.stats ? &P.stats->struct_flops : nullptr;
+      SA.ranks = P.stats ? P.stats->srrsc : nullptr;
       err = launch_struct_segs(P, LL, sg);
       if (err == cudaSuccess) err = launch_struct(P.segs, (int)(2 * LL.merges), SA, sg);
     }
@@ -578,6 +583,10 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     float lmf;
     memcpy(&lmf, &lm, sizeof(lmf));
     g_last_stats.split_level_max = lmf / 16777216.0f;
+    g_last_stats.lr_tiles = (int64_t)hs.srrsc[0];
+    g_last_stats.lr_rank_sum = (int64_t)hs.srrsc[1];
+    g_last_stats.lr_dense_fallbacks = (int64_t)hs.srrsc[2];
+    g_last_stats.lr_rank_max = (int64_t)hs.srrsc[3];
     g_last_stats.secular_iter_max = hs.iter_max;
     g_last_stats.secular_iter_mean = hs.iter_roots ? (double)hs.iter_sum / (double)hs.iter_roots : 0.0;
     for (int i = 0; i < 12; ++i) g_last_stats.phase_ms[i] = phase[i];
@@ -691,7 +700,7 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
 int tdc_rank_one_workspace_size(int64_t K, size_t* bytes) {
   if (K < 0) return -1;
   if (!bytes) return -2;
-  *bytes = 2 * kStatusSlotBytes;  // the status slot (aligned inside)
+  *bytes = 256;
   return TDC_OK;
 }
 
@@ -707,13 +716,9 @@ int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_
   if (!zhat) return -7;
   if (!s) return -8;
   if (max_iter < 1) return -9;
-  int* st = nullptr;
-  if (ws && ws_bytes >= 2 * kStatusSlotBytes) {
-    st = (int*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-    if (begin_status(st, (cudaStream_t)stream) != cudaSuccess) return TDC_ECUDA;
-  } else {
-    st = status_ptr();
-  }
+  (void)ws;
+  (void)ws_bytes;
+  int* st = begin_status((cudaStream_t)stream);
   if (!st) return TDC_ECUDA;
   cudaError_t e = launch_rank_one(D, z, K, rho, max_iter, org, tau, zhat, s, st, (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
@@ -743,18 +748,18 @@ int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc
   if (validate_opts(&op)) return -4;
   if (!bytes) return -5;
   if (mode == TDC_MERGE_DENSE) {
-    *bytes = 256 + kStatusSlotBytes;
+    *bytes = 256;
     return TDC_OK;
   }
   if (mode == TDC_MERGE_STRUCTURED) {
     const int64_t mm = op.lr_tile, T = (K + mm - 1) / mm, ns = T * T;
-    *bytes = 256 + kStatusSlotBytes + align_up(2 * sizeof(GemmSeg)) + align_up(sizeof(int) * ns) +
+    *bytes = 256 + align_up(2 * sizeof(GemmSeg)) + align_up(sizeof(int) * ns) +
              align_up(sizeof(int) * ns * kStructRmax) + align_up(sizeof(double) * ns * kStructRmax) +
              align_up(sizeof(double) * ns * mm) + align_up(sizeof(int) * ns * mm) +
              align_up(sizeof(double) * T * kStructRmax * std::max<int64_t>(m, 1));
     return TDC_OK;
   }
-  *bytes = 256 + kStatusSlotBytes + align_up(2 * sizeof(GemmSeg)) +
+  *bytes = 256 + align_up(2 * sizeof(GemmSeg)) +
            sizeof(__nv_bfloat16) * (size_t)cauchy_split_elems(m, K, op.split_slices, nullptr);
   return TDC_OK;
 }
@@ -782,11 +787,10 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   size_t need = 0;
   tdc_cauchy_gemm_workspace_size(m, K, mode, &op, &need);
   if (!ws || ws_bytes < need) return TDC_ENOWS;
-  // the status slot, then the rest of the workspace (256-byte aligned)
-  int* st = (int*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  char* wbase = (char*)st + kStatusSlotBytes;
+  char* wbase = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   cudaStream_t cs = (cudaStream_t)stream;
-  if (begin_status(st, cs) != cudaSuccess) return TDC_ECUDA;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
   GemmSeg sg;
   memset(&sg, 0, sizeof(sg));
   sg.ars = 1;
@@ -847,7 +851,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
 // W and R (n^2 doubles each per problem), column exponents, segments and the
 // digit images of the split products
 static size_t adjoint_ws_bytes(int32_t batch, int64_t n) {
-  return 256 + kStatusSlotBytes + align_up(sizeof(double) * 2 * (size_t)batch * (size_t)n * (size_t)n) +
+  return 256 + align_up(sizeof(double) * 2 * (size_t)batch * (size_t)n * (size_t)n) +
          align_up(sizeof(int32_t) * (size_t)batch * (size_t)n) + align_up(sizeof(GemmSeg) * ((size_t)batch + 1)) +
          256 + sizeof(__nv_bfloat16) * (size_t)adjoint_split_img_elems(batch, n);
 }
@@ -872,9 +876,9 @@ int tdc_eig_backward(int64_t n, const double* lam, const double* Q, int64_t ldq,
   size_t need = 0;
   tdc_backward_workspace_size(n, &need);
   if (!ws || ws_bytes < need) return TDC_ENOWS;
-  int* st = (int*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  double* w = (double*)((char*)st + kStatusSlotBytes);
-  if (begin_status(st, (cudaStream_t)stream) != cudaSuccess) return TDC_ECUDA;
+  double* w = (double*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  int* st = begin_status((cudaStream_t)stream);
+  if (!st) return TDC_ECUDA;
   cudaError_t e = launch_adjoint(1, (int)n, lam, Q, ldq, 0, lam_bar, Q_bar, 0, d_bar, e_bar, w, st, 1ll << 24,
                                  (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
@@ -901,9 +905,9 @@ int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const 
   size_t need = 0;
   tdc_backward_batched_workspace_size(batch, n, &need);
   if (!ws || ws_bytes < need) return TDC_ENOWS;
-  int* st = (int*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  double* w = (double*)((char*)st + kStatusSlotBytes);
-  if (begin_status(st, (cudaStream_t)stream) != cudaSuccess) return TDC_ECUDA;
+  double* w = (double*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  int* st = begin_status((cudaStream_t)stream);
+  if (!st) return TDC_ECUDA;
   const int64_t nn = n * n;
   cudaError_t e = launch_adjoint(batch, (int)n, lam, Q, n, nn, lam_bar, Q_bar, nn, d_bar, e_bar, w, st, 1ll << 24,
                                  (cudaStream_t)stream);
@@ -913,27 +917,14 @@ int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const 
 int tdc_sync_status(tdc_stream_t stream) {
   cudaStream_t cs = (cudaStream_t)stream;
   if (cudaStreamSynchronize(cs) != cudaSuccess) return TDC_ECUDA;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TDC_ECUDA;
-  int* dw = status_ptr();
-  if (!dw) return TDC_ECUDA;
-  int* slot = nullptr;
-  {
-    std::lock_guard<std::mutex> lk(g_mu);
-    auto it = g_stream_slot.find({dev, cs});
-    slot = it != g_stream_slot.end() ? it->second : g_last_slot[dev];
-  }
-  // the call's slot and the device word (calls without a workspace); both are read and cleared
-  int v[2] = {0, 0}, w[2] = {0, 0}, z[2] = {0, 0};
-  if (slot) {
-    if (cudaMemcpy(v, slot, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return TDC_ECUDA;
-    if (cudaMemcpy(slot, z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return TDC_ECUDA;
-  }
-  if (cudaMemcpy(w, dw, sizeof(w), cudaMemcpyDeviceToHost) != cudaSuccess) return TDC_ECUDA;
-  if (cudaMemcpy(dw, z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return TDC_ECUDA;
+  // the stream's slot (a stream no call was made on: the device's last call's)
+  int* slot = stream_slot(cs, false);
+  if (!slot) return TDC_OK;
+  int v[2] = {0, 0}, z[2] = {0, 0};
+  if (cudaMemcpy(v, slot, sizeof(v), cudaMemcpyDeviceToHost) != cudaSuccess) return TDC_ECUDA;
+  if (cudaMemcpy(slot, z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return TDC_ECUDA;
   if (v[0] != 0) return v[0];
-  if (w[0] != 0) return w[0];
-  if ((v[1] | w[1]) & kWarnSplitLevel) return TDC_WPRECISION;
+  if (v[1] & kWarnSplitLevel) return TDC_WPRECISION;
   return TDC_OK;
 }
 

@@ -103,6 +103,7 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   int iter_max;
   unsigned long long handoffs;
   unsigned int split_level_max;  // FP32 bits of the largest |level sum| of a split hand-off (levels 0-4)
+  unsigned long long srrsc[4];   // far tiles, sum of ranks, dense fallbacks, largest rank
 };
 
 // One GEMM segment C(rows x K) = A(rows x kk) * Qhat(list, :) of the merge
@@ -186,6 +187,8 @@ struct StructArgs {
   int64_t ldw;
   int* status;
   unsigned long long* flops;  // executed multiply-add flops (statistics; NULL when off)
+  unsigned long long* ranks;  // statistics (NULL when off): far tiles, sum of their ranks,
+                              // dense fallbacks, largest rank kept
 };
 
 // A merge (node) of level l: node i of problem p splits at mid.

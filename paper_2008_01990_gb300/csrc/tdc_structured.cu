@@ -170,6 +170,14 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
     __syncthreads();
   }
   const int r = s_r;
+  if (S.ranks && tid == 0) {
+    atomicAdd(&S.ranks[0], 1ull);
+    if (fallback) atomicAdd(&S.ranks[2], 1ull);
+    else {
+      atomicAdd(&S.ranks[1], (unsigned long long)r);
+      atomicMax(&S.ranks[3], (unsigned long long)r);
+    }
+  }
   if (fallback) {
     if (tid == 0) S.srank[slot] = -1;
     return;

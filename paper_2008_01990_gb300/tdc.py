@@ -70,6 +70,10 @@ class Stats(ctypes.Structure):
         ("launches", ctypes.c_int64),
         ("secular_handoffs", ctypes.c_int64),
         ("split_level_max", ctypes.c_float),
+        ("lr_tiles", ctypes.c_int64),
+        ("lr_rank_sum", ctypes.c_int64),
+        ("lr_dense_fallbacks", ctypes.c_int64),
+        ("lr_rank_max", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -94,6 +98,10 @@ class Stats(ctypes.Structure):
             "launches": self.launches,
             "secular_handoffs": self.secular_handoffs,
             "split_level_max": self.split_level_max,
+            "lr_tiles": self.lr_tiles,
+            "lr_rank_sum": self.lr_rank_sum,
+            "lr_dense_fallbacks": self.lr_dense_fallbacks,
+            "lr_rank_max": self.lr_rank_max,
         }
 
 
@@ -261,7 +269,7 @@ def cauchy_gemm(A: torch.Tensor, D: torch.Tensor, org: torch.Tensor, tau: torch.
                 s: torch.Tensor, mode: int = MERGE_DENSE, opts: Opts | None = None, stream=None, check=False,
                 ws: torch.Tensor | None = None):
     """C = A * Qhat with Qhat_ij = zhat_i s_j / ((D_i - D_org_j) - tau_j); A is a column-major m x K view.
-    The call's device status lives in its workspace: pass `ws` (and keep it) to read the status later."""
+    ws: an optional caller-owned workspace of cauchy_gemm_workspace_size bytes."""
     m, K = A.shape
     lda = A.stride(1) if K > 0 else max(m, 1)
     C = torch.empty(K, m, dtype=torch.float64, device=A.device).t()

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import EPS, compare_vectors, dense, ratios
+from helpers import EPS, check_toeplitz_sampled, compare_vectors, dense, ratios
 from paper_2008_01990_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -211,26 +211,7 @@ def test_c2_toeplitz_16384_sampled(tdc):
     dt = torch.tensor(d, device=DEV)
     et = torch.tensor(e, device=DEV)
     lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=64), check=True)
-    k = torch.arange(1, n + 1, dtype=torch.float64, device=DEV)
-    ref = torch.sort(2.0 + 2.0 * torch.cos(k * np.pi / (n + 1))).values
-    assert torch.max(torch.abs(lam - ref)).item() <= 1e-12 * 4
-    g = np.random.default_rng(0)
-    cols = torch.tensor(np.sort(g.choice(n, 256, replace=False)), device=DEV)
-    Qs = Q[:, cols]
-    Tq = 2.0 * Qs
-    Tq[1:] += Qs[:-1]
-    Tq[:-1] += Qs[1:]
-    res = torch.abs(Tq - Qs * lam[cols]).sum(dim=0).max().item() / (n * 4.0 * EPS)
-    G = Qs.t() @ Q
-    G[torch.arange(256, device=DEV), cols] -= 1.0
-    orth = torch.abs(G).sum(dim=1).max().item() / (n * EPS)
-    assert res <= 50 and orth <= 50, (res, orth)
-    # eigenvalue lam_k (ascending) belongs to index m = n+1-k of 2+2cos(m pi/(n+1))
-    m = (n - cols).to(torch.float64)
-    j = torch.arange(1, n + 1, dtype=torch.float64, device=DEV)[:, None]
-    V = np.sqrt(2.0 / (n + 1)) * torch.sin(j * m[None, :] * np.pi / (n + 1))
-    dots = torch.abs(torch.sum(V * Qs, dim=0))
-    assert torch.max(torch.abs(dots - 1.0)).item() <= 1e-6
+    check_toeplitz_sampled(lam, Q, n)
 
 
 def test_calls_from_two_host_threads_on_two_streams(tdc):

@@ -156,7 +156,7 @@ def test_bounded_waits_expire_report_a_timeout_and_leave_the_device_usable(tdc, 
     org, tau, zh, s = tdc.rank_one(D, z, 0.9, check=True)
     A = ((torch.rand(K, m, dtype=torch.float64, device=DEV, generator=g) * 2 - 1) / np.sqrt(K)).t()
     o1 = tdc.default_opts(spin_budget=1)
-    ws = tdc.workspace(tdc.cauchy_gemm_workspace_size(m, K, tdc.MERGE_SPLIT, o1), DEV)  # holds the status slot
+    ws = tdc.workspace(tdc.cauchy_gemm_workspace_size(m, K, tdc.MERGE_SPLIT, o1), DEV)
     tdc.cauchy_gemm(A, D, org, tau, zh, s, tdc.MERGE_SPLIT, o1, ws=ws)
     assert tdc.sync_status() == tdc.TDC_ETIMEOUT
     # the eigensolver's split merges report it the same way
@@ -185,8 +185,8 @@ def test_bounded_waits_expire_report_a_timeout_and_leave_the_device_usable(tdc, 
 
 
 def test_status_slots_of_calls_on_two_streams_stay_apart(tdc):
-    """Each call keeps its status in its own workspace: a timeout on one stream is not
-    reported for, or cleared by, a clean call on another stream."""
+    """Each stream has its own status slot: a timeout on one stream is not reported for,
+    or cleared by, a clean call on another stream, and it outlives the call's workspace."""
     K = 8192
     g = torch.Generator(device=DEV)
     g.manual_seed(12)
@@ -207,6 +207,9 @@ def test_status_slots_of_calls_on_two_streams_stay_apart(tdc):
         tdc.cauchy_gemm(A, D, org, tau, zh, s, tdc.MERGE_SPLIT, o1, stream=s1, ws=ws1)
     with torch.cuda.stream(s2):
         tdc.eig(dt, et, o2, ws=ws2, stream=s2)
+    torch.cuda.synchronize()
+    del ws1, ws2
+    torch.cuda.empty_cache()  # the workspaces are gone; the statuses are not
     assert tdc.sync_status(s2) == 0
     assert tdc.sync_status(s1) == tdc.TDC_ETIMEOUT
     assert tdc.sync_status(s1) == 0  # read and cleared

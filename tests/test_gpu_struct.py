@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 import torch
 
-from helpers import compare_vectors, ratios
+from helpers import check_toeplitz_sampled, compare_vectors, ratios
 from paper_2008_01990_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -85,3 +85,24 @@ def test_eig_structured_merge_vs_oracle(tdc, orc, n, leaf, fam):
     res, orth = ratios(d, e, lam, Q)
     assert res <= 50 and orth <= 50, (res, orth)
     compare_vectors(Q, Q_o, lam_o, 1e-8 * nT, 1e-7)
+
+
+def test_c2_toeplitz_16384_structured_default_tiles(tdc):
+    """The structured merge at full size with the library's defaults (lr_tile 512,
+    structured_min_K 4096, rank cap 64, lr_tol 1e-15): the top merge of tridiag(1,2,1)
+    at n = 16384 (K = 8192 non-deflated poles) runs on the structured path.  Closed-form
+    eigenvalues, sampled residual, orthogonality and sine vectors; every far tile is
+    compressed (ranks from the statistics)."""
+    n = 16384
+    d, e = inputs.toeplitz_tridiag(n)
+    o = tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_STRUCTURED, collect_stats=1)
+    assert (o.lr_tile, o.structured_min_K) == (512, 4096)
+    lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o, check=True)
+    st = tdc.get_stats()
+    assert st["sum_K"][0] == n // 2
+    # top merge: 16 x 16 tiles of 512 poles and roots, all but the 46 on or next to the
+    # diagonal compressed, in both halves' products (the level below adds its own)
+    assert st["lr_tiles"] >= 2 * (16 * 16 - 46)
+    assert st["lr_dense_fallbacks"] == 0 and 0 < st["lr_rank_max"] <= 64
+    assert st["struct_flops"] > 0
+    check_toeplitz_sampled(lam, Q, n)
