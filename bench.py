@@ -548,7 +548,7 @@ def run_ours(args):
     d_np, e_np, leaf, desc = workload(args.workload)
     n = d_np.size
     mode = {"dense": tdc.MERGE_DENSE, "auto": tdc.MERGE_AUTO, "structured": tdc.MERGE_STRUCTURED,
-            "split": tdc.MERGE_SPLIT}[args.merge]
+            "split": tdc.MERGE_SPLIT, "structured_split": tdc.MERGE_STRUCTURED_SPLIT}[args.merge]
     if args.leaf:
         leaf = args.leaf
         desc = desc.split(" leaf ")[0] + " leaf %d" % leaf + (" seed" + desc.split(" seed")[1] if " seed" in desc else "")
@@ -712,6 +712,31 @@ def run_ours(args):
                          "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
                          "note": "executed flops only (the dense flops it avoids are not counted); the phase "
                                  "also holds the FP32 SRRSC pivot searches"}}
+    if args.merge not in ("dense", "structured_split") and not args.no_compare and n >= 4096:
+        o4 = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_STRUCTURED_SPLIT, collect_stats=1)
+        o4p = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_STRUCTURED_SPLIT)
+        ws4 = tdc.workspace(tdc.workspace_size(n, o4), dev)
+        for _ in range(2):
+            tdc.eig(d, e, o4p, ws=ws4, lam=lam, Q=Q, stream=stream)
+        st4 = tdc.sync_status(stream)
+        steps4 = max(1, min(args.steps, 10))
+        ms4 = _event_ms(lambda: tdc.eig(d, e, o4p, ws=ws4, lam=lam, Q=Q, stream=stream), steps4, stream)
+        tdc.eig(d, e, o4, ws=ws4, lam=lam, Q=Q, stream=stream)
+        s4 = tdc.get_stats()
+        del ws4
+        compare["structured_split"] = ms4 / 1e3
+        kept = max(1, s4["lr_tiles"] - s4["lr_dense_fallbacks"])
+        compare_detail["structured_split"] = {
+            "s": ms4 / 1e3, "steps": steps4, "status": tdc.strerror(st4), "test_ratios": accuracy(),
+            "options": {"lr_tile": o4.lr_tile, "structured_min_K": o4.structured_min_K, "lr_tol": o4.lr_tol,
+                        "rank_cap": 64, "split_chunk_k": o4.split_chunk_k},
+            "srrsc": {"far_tiles": s4["lr_tiles"], "mean_rank": s4["lr_rank_sum"] / kept,
+                      "max_rank": s4["lr_rank_max"], "dense_fallbacks": s4["lr_dense_fallbacks"]},
+            "split_level_max": s4["split_level_max"], "phase_ms": s4["phase_ms"],
+            "roofline": split_roofline(s4, s4["phase_ms"]["split_mma"], o4.split_slices, *peaks(),
+                                       "; executed flops of the near, W and apply products and the merges "
+                                       "below the structured threshold; phase time of one instrumented solve")}
+        progress("structured merge on the split path done")
     if compare_detail:
         tdc.eig(d, e, opts, ws=wsb, lam=lam, Q=Q, stream=stream)  # leave the timed configuration's result
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -812,7 +837,7 @@ def main():
     ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
                                                           "batched4096", "backward256", "clement30000",
                                                           "hermite30000", "sht30000"])
-    ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split"])
+    ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split", "structured_split"])
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--leaf", type=int, default=0, help="leaf size (default: the workload's)")
     ap.add_argument("--batch", type=int, default=4096, help="problems of the batched workload (first ones of its sequence)")

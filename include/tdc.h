@@ -64,6 +64,9 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
 #define TDC_MERGE_DENSE 1       /* FP64 GEMM, U generated from its generators in the producer */
 #define TDC_MERGE_STRUCTURED 2  /* near-diagonal tiles dense, off-diagonal tiles SRRSC-compressed */
 #define TDC_MERGE_SPLIT 3       /* BF16 slice products on tcgen05 tensor cores, FP32/FP64 accumulation */
+#define TDC_MERGE_STRUCTURED_SPLIT 4 /* the structured update (near-diagonal tiles dense, off-diagonal tiles
+                                        SRRSC-compressed) with all of its products on the split tensor-core
+                                        path; merges with K < structured_min_K as TDC_MERGE_AUTO */
 /* Accuracy of the split path (SPLIT and AUTO): the digit products of one level are
  * summed in FP32 accumulators, exact only while each level's sum stays below 2^24.
  * The default schedule drains them into 64-bit integer sums every split_chunk_k = 256
@@ -131,7 +134,7 @@ typedef struct {
   int64_t lr_rank_max;                   /* largest rank kept in low-rank form */
 } tdc_stats;
 
-/* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 512,
+/* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 256,
  * lr_tol 1e-15, split_slices 7, split_min_K 128, max_iter 64, sign_normalise 1,
  * collect_stats 0, spin_budget 2^24, split_chunk_k 256). */
 void tdc_default_opts(tdc_opts* o);

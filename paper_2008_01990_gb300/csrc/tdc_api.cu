@@ -97,9 +97,31 @@ struct HostPlan {
   int64_t struct_slots = 0;         // SRRSC slots (segments x Tmax^2)
   int64_t struct_w = 0;             // W doubles
   int64_t struct_segs = 0;          // segments
+  // structured path on the split GEMM (TDC_MERGE_STRUCTURED_SPLIT): largest level
+  bool ss = false;
+  int64_t ss_items = 0;             // segments x Tmax
+  int64_t ss_bcap = 0;              // W columns (and W-product columns)
+  int64_t ss_w = 0;                 // W doubles
+  int64_t ss_r = 0;                 // R doubles
+  int64_t ss_img = 0;               // digit-image elements of the largest of the three products
+  std::vector<char> ss_level;       // per level: its structured merges take that path
+  std::vector<int64_t> ss_wcap;     // per level: W columns it may use
 };
 
-static bool struct_enabled(const tdc_opts& o) { return o.merge_mode == TDC_MERGE_STRUCTURED; }
+// the structured path on the split GEMM: W columns per tile of a level, on average
+// (tiles beyond the budget stay dense), and the digit-image elements a level may use
+static constexpr int64_t kSsRankBudget = 16;
+static constexpr int64_t kSsImgBudget = (int64_t)8 << 30;
+
+static bool struct_enabled(const tdc_opts& o) {
+  return o.merge_mode == TDC_MERGE_STRUCTURED || o.merge_mode == TDC_MERGE_STRUCTURED_SPLIT;
+}
+static bool struct_split_mode(const tdc_opts& o) { return o.merge_mode == TDC_MERGE_STRUCTURED_SPLIT; }
+// merges with K >= this take the structured path (on the split GEMM it never starts
+// below the split threshold)
+static int struct_threshold(const tdc_opts& o) {
+  return struct_split_mode(o) ? std::max(o.structured_min_K, o.split_min_K) : o.structured_min_K;
+}
 
 static void level_struct_dims(const LevelLaunch& L, int m, int64_t& Tmax, int64_t& ldw) {
   Tmax = (L.max_n + m - 1) / m;
@@ -109,22 +131,54 @@ static void level_struct_dims(const LevelLaunch& L, int m, int64_t& Tmax, int64_
 static void plan_struct(HostPlan& H, const tdc_opts& o) {
   H.struct_m = struct_enabled(o) ? o.lr_tile : 0;
   H.struct_slots = H.struct_w = H.struct_segs = 0;
+  H.ss = struct_split_mode(o);
+  H.ss_items = H.ss_bcap = H.ss_w = H.ss_r = H.ss_img = 0;
+  H.ss_level.assign(H.T, 0);
+  H.ss_wcap.assign(H.T, 0);
   if (!H.struct_m) return;
+  const int64_t m = H.struct_m, S = o.split_slices, rmax = kStructRmax;
+  const int64_t at = (int64_t)kSplitBM * kSplitBK, bt = (int64_t)kSplitBN * kSplitBK;
   for (int l = 0; l < H.T; ++l) {
     const LevelLaunch& L = H.levels[l];
-    if (L.max_n < o.structured_min_K) continue;
+    if (L.max_n < struct_threshold(o)) continue;
     int64_t Tmax, ldw;
     level_struct_dims(L, H.struct_m, Tmax, ldw);
     const int64_t nseg = 2 * L.merges;
     H.struct_slots = std::max(H.struct_slots, nseg * Tmax * Tmax);
-    H.struct_w = std::max(H.struct_w, nseg * Tmax * kStructRmax * ldw);
+    if (!H.ss) H.struct_w = std::max(H.struct_w, nseg * Tmax * kStructRmax * ldw);
     H.struct_segs = std::max(H.struct_segs, nseg + 1);
+    if (!H.ss) continue;
+    // W budget: on average kSsRankBudget columns per tile of the level, at most 4 GiB
+    // (tiles beyond it stay dense, in FP64); the R blocks, column lists and digit
+    // images follow from it.  A row tile holds at most m poles, the near range of a
+    // column tile at most 3m.
+    (void)rmax;
+    const int64_t items = nseg * Tmax;
+    const int64_t wcap = std::max<int64_t>(
+        kSplitBN, std::min<int64_t>(items * Tmax * kSsRankBudget, ((int64_t)1 << 29) / std::max<int64_t>(ldw, 1)));
+    const int64_t RT = (ldw + kSplitBM - 1) / kSplitBM, CTm = (m + kSplitBN - 1) / kSplitBN;
+    const int64_t KBn = (std::min(3 * m, L.max_n) + kSplitBK - 1) / kSplitBK + 1;
+    const int64_t KBm = (m + kSplitBK - 1) / kSplitBK + 1;
+    const int64_t near = items * KBn * (RT * at + CTm * bt) * S;
+    const int64_t wimg = (items * RT * KBm * at + (wcap / kSplitBN + items) * KBm * bt) * S;
+    const int64_t aimg = (wcap / kSplitBK + items) * (RT * at + CTm * bt) * S;
+    const int64_t img = std::max(near, std::max(wimg, aimg));
+    H.ss_level[l] = img <= kSsImgBudget;
+    if (!H.ss_level[l]) continue;  // this level's merges take the split path
+    H.ss_wcap[l] = wcap;
+    H.ss_items = std::max(H.ss_items, items);
+    H.ss_bcap = std::max(H.ss_bcap, wcap);
+    H.ss_w = std::max(H.ss_w, wcap * ldw);
+    H.ss_r = std::max(H.ss_r, wcap * m);
+    H.ss_img = std::max(H.ss_img, img);
   }
+  H.img_elems = std::max(H.img_elems, H.ss_img);
 }
 
 // the split path is used for merge_mode SPLIT and AUTO
 static bool split_enabled(const tdc_opts& o) {
-  return o.merge_mode == TDC_MERGE_SPLIT || o.merge_mode == TDC_MERGE_AUTO;
+  return o.merge_mode == TDC_MERGE_SPLIT || o.merge_mode == TDC_MERGE_AUTO ||
+         o.merge_mode == TDC_MERGE_STRUCTURED_SPLIT;
 }
 
 // Digit images of a merge of order nm on the split path (upper bound: kk, K <= nm).
@@ -244,7 +298,8 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
 
 // workspace carving
 struct Layout {
-  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw, q1, total;
+  size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw;
+  size_t ss_segs, ss_counts, ss_wcol0, ss_bcol, ss_wpos, ss_w, ss_r, ss_cexp, ss_item, q1, total;
 };
 
 static constexpr int kVecD = 27;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz, 8 boundary rows)
@@ -275,6 +330,16 @@ static Layout layout_of(const HostPlan& H) {
   L.svr = o; o = align_up(o + sizeof(double) * ns * mm);
   L.scolpiv = o; o = align_up(o + sizeof(int) * ns * mm);
   L.sw = o; o = align_up(o + sizeof(double) * (size_t)H.struct_w);
+  const size_t it = (size_t)H.ss_items;
+  L.ss_segs = o; o = align_up(o + (H.ss ? 3 * sizeof(GemmSeg) * (it + 1) : 0));
+  L.ss_counts = o; o = align_up(o + (H.ss ? 3 * sizeof(int64_t) : 0));
+  L.ss_wcol0 = o; o = align_up(o + sizeof(int32_t) * ns);
+  L.ss_bcol = o; o = align_up(o + sizeof(int32_t) * (size_t)H.ss_bcap);
+  L.ss_wpos = o; o = align_up(o + sizeof(int32_t) * (size_t)H.ss_bcap);
+  L.ss_w = o; o = align_up(o + sizeof(double) * (size_t)H.ss_w);
+  L.ss_r = o; o = align_up(o + sizeof(double) * (size_t)H.ss_r);
+  L.ss_cexp = o; o = align_up(o + sizeof(int32_t) * it * mm);
+  L.ss_item = o; o = align_up(o + sizeof(int64_t) * 6 * it);
   L.q1 = o; o = align_up(o + sizeof(double) * (size_t)H.Q1);
   L.total = o + 256;  // slack for aligning an unaligned base
   return L;
@@ -354,7 +419,7 @@ static cudaError_t upload_problems(const HostPlan& H, Problem* dst, cudaStream_t
 
 static int validate_opts(const tdc_opts* o) {
   if (o->leaf < 2 || o->leaf > 64) return 1;  // leaf >= 2 keeps every tree node non-empty
-  if (o->merge_mode < 0 || o->merge_mode > 3) return 1;
+  if (o->merge_mode < 0 || o->merge_mode > 4) return 1;
   if (o->max_iter < 1) return 1;
   if (o->lr_tile < 64 || (o->lr_tile % 64) != 0) return 1;
   if (o->split_slices < 3 || o->split_slices > 7) return 1;
@@ -399,8 +464,9 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   P.split_slices = H.split_S ? H.split_S : 7;
   P.split_chunk_steps = o.split_chunk_k / 16;
   P.spin_budget = o.spin_budget;
-  P.struct_min_K = H.struct_m ? o.structured_min_K : 0;
+  P.struct_min_K = H.struct_m ? struct_threshold(o) : 0;
   P.struct_m = H.struct_m;
+  P.struct_split = 0;  // set per level below
   StructArgs SA;
   memset(&SA, 0, sizeof(SA));
   SA.m = H.struct_m;
@@ -475,7 +541,9 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   }
   for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
     const LevelLaunch& LL = H.levels[l];
-    const Plan& P = PP[l & 1];
+    Plan P = PP[l & 1];
+    const bool ss = H.ss && H.ss_level[l] && LL.max_n >= P.struct_min_K;
+    P.struct_split = ss ? 1 : 0;
     if (l + 2 < H.T) err = cudaStreamWaitEvent(s, evG[l + 2], 0);
     const size_t a0 = mark();
     if (err == cudaSuccess) err = launch_prepare(P, LL, s);
@@ -494,11 +562,70 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     if (err == cudaSuccess) err = cudaStreamWaitEvent(sg, evE[l], 0);
     const size_t g0 = mark_on(sg);
     if (err == cudaSuccess) err = launch_rotate(P, LL, sg);
-    const size_t g1 = mark_on(sg);
+    size_t g1 = mark_on(sg);
     span(1, g0, g1);
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], sg);
     if (err == cudaSuccess) err = launch_gemm_tiny(P, LL, sg);
-    if (err == cudaSuccess && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
+    if (err == cudaSuccess && ss) {
+      // the structured path on the split GEMM: SRRSC, the three segment lists and R,
+      // then the near, W and apply products, then the tiles that stayed dense (FP64)
+      int64_t Tmax, ldw;
+      level_struct_dims(LL, H.struct_m, Tmax, ldw);
+      SA.Tmax = (int)Tmax;
+      SA.ldw = ldw;
+      SA.status = P.status;
+      SA.flops = P.stats ? &P.stats->struct_flops : nullptr;
+      SA.ranks = P.stats ? P.stats->srrsc : nullptr;
+      SA.fallback_only = 1;
+      const int nseg = (int)(2 * LL.merges);
+      const int64_t items = (int64_t)nseg * Tmax;
+      SSArgs A;
+      memset(&A, 0, sizeof(A));
+      A.ssegs = P.segs;
+      A.nseg = nseg;
+      A.S = SA;
+      A.digits = P.split_slices;
+      A.near_segs = (GemmSeg*)(base + L.ss_segs);
+      A.w_segs = A.near_segs + (H.ss_items + 1);
+      A.ap_segs = A.w_segs + (H.ss_items + 1);
+      A.counts = (int64_t*)(base + L.ss_counts);
+      A.wcol0 = (int32_t*)(base + L.ss_wcol0);
+      A.bcol = (int32_t*)(base + L.ss_bcol);
+      A.wpos = (int32_t*)(base + L.ss_wpos);
+      A.bcap = H.ss_wcap[l];
+      A.W = (double*)(base + L.ss_w);
+      A.ldw = ldw;
+      A.wcap = H.ss_wcap[l];
+      A.R = (double*)(base + L.ss_r);
+      A.rcap = H.ss_wcap[l] * H.struct_m;
+      A.cexp = (int32_t*)(base + L.ss_cexp);
+      A.item = (int64_t*)(base + L.ss_item);
+      A.img_cap = P.img_cap;
+      A.status = P.status;
+      A.flops = P.stats ? &P.stats->split_flops : nullptr;
+      err = launch_struct_segs(P, LL, sg);
+      if (err == cudaSuccess) err = launch_srrsc(P.segs, nseg, SA, sg);
+      if (err == cudaSuccess) err = launch_ss_build(A, sg);
+      GemmSeg* lists[3] = {A.near_segs, A.w_segs, A.ap_segs};
+      size_t b4 = mark_on(sg);
+      span(4, g1, b4);
+      for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+        cudaEvent_t mid = nullptr;
+        if (timing) {
+          cudaEventCreate(&mid);
+          evs.push_back(mid);
+        }
+        const size_t b5 = timing ? evs.size() - 1 : 0;
+        err = launch_split_list(lists[k], (int)items, A.counts + k, P.split_slices, P.status, P.spin_budget, P.img,
+                                P.split_chunk_steps, P.stats ? &P.stats->split_level_max : nullptr, sg, mid);
+        const size_t b6 = mark_on(sg);
+        span(5, b4, b5);
+        span(6, b5, b6);
+        b4 = b6;
+      }
+      g1 = b4;
+      if (err == cudaSuccess) err = launch_struct_fallback(P.segs, nseg, SA, sg);
+    } else if (err == cudaSuccess && !H.ss && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
       int64_t Tmax, ldw;
       level_struct_dims(LL, H.struct_m, Tmax, ldw);
       SA.Tmax = (int)Tmax;
@@ -607,7 +734,7 @@ void tdc_default_opts(tdc_opts* o) {
   o->leaf = 32;
   o->merge_mode = TDC_MERGE_AUTO;
   o->structured_min_K = 4096;
-  o->lr_tile = 512;
+  o->lr_tile = 256;
   o->lr_tol = 1e-15;
   o->split_slices = 7;
   o->split_min_K = 128;
@@ -738,15 +865,67 @@ __global__ void k_write_segs(GemmSeg s0, GemmSeg s1, GemmSeg* dst) {
   if (threadIdx.x == 0) { dst[0] = s0; dst[1] = s1; }
 }
 
+__global__ void k_iota(int32_t* a, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = (int32_t)i;
+}
+
+// Workspace of the stand-alone structured product on the split GEMM (one segment of
+// m rows and K poles / roots): SRRSC scratch, the identity pole list, the three
+// segment lists, W, R, scales and digit images (bounds as for an eigensolver level).
+struct CauchySS {
+  size_t segs, srank, spiv, sy, svr, scolpiv, iota, lists, counts, wcol0, bcol, wpos, w, r, cexp, item, img, total;
+  int64_t T, wcap, img_elems;
+};
+static CauchySS cauchy_ss_layout(int64_t m, int64_t K, const tdc_opts& op) {
+  CauchySS L;
+  const int64_t mm = op.lr_tile, T = std::max<int64_t>(1, (K + mm - 1) / mm), ns = T * T, S = op.split_slices;
+  const int64_t at = (int64_t)kSplitBM * kSplitBK, bt = (int64_t)kSplitBN * kSplitBK;
+  L.T = T;
+  L.wcap = std::max<int64_t>(kSplitBN, std::min<int64_t>(T * T * kSsRankBudget, ((int64_t)1 << 29) / std::max<int64_t>(m, 1)));
+  const int64_t RT = (m + kSplitBM - 1) / kSplitBM, CTm = (mm + kSplitBN - 1) / kSplitBN;
+  const int64_t KBn = (std::min(3 * mm, K) + kSplitBK - 1) / kSplitBK + 1, KBm = (mm + kSplitBK - 1) / kSplitBK + 1;
+  const int64_t near = T * KBn * (RT * at + CTm * bt) * S;
+  const int64_t wimg = (T * RT * KBm * at + (L.wcap / kSplitBN + T) * KBm * bt) * S;
+  const int64_t aimg = (L.wcap / kSplitBK + T) * (RT * at + CTm * bt) * S;
+  L.img_elems = std::max(near, std::max(wimg, aimg));
+  size_t o = 0;
+  L.segs = o; o = align_up(o + 2 * sizeof(GemmSeg));
+  L.srank = o; o = align_up(o + sizeof(int) * ns);
+  L.spiv = o; o = align_up(o + sizeof(int) * ns * kStructRmax);
+  L.sy = o; o = align_up(o + sizeof(double) * ns * kStructRmax);
+  L.svr = o; o = align_up(o + sizeof(double) * ns * mm);
+  L.scolpiv = o; o = align_up(o + sizeof(int) * ns * mm);
+  L.iota = o; o = align_up(o + sizeof(int32_t) * K);
+  L.lists = o; o = align_up(o + 3 * sizeof(GemmSeg) * (T + 1));
+  L.counts = o; o = align_up(o + 3 * sizeof(int64_t));
+  L.wcol0 = o; o = align_up(o + sizeof(int32_t) * ns);
+  L.bcol = o; o = align_up(o + sizeof(int32_t) * L.wcap);
+  L.wpos = o; o = align_up(o + sizeof(int32_t) * L.wcap);
+  L.w = o; o = align_up(o + sizeof(double) * L.wcap * std::max<int64_t>(m, 1));
+  L.r = o; o = align_up(o + sizeof(double) * L.wcap * mm);
+  L.cexp = o; o = align_up(o + sizeof(int32_t) * T * mm);
+  L.item = o; o = align_up(o + sizeof(int64_t) * 6 * T);
+  L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * L.img_elems);
+  L.total = 256 + o;
+  return L;
+}
+
 int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc_opts* o, size_t* bytes) {
   tdc_opts op;
   tdc_default_opts(&op);
   if (o) op = *o;
   if (m < 0) return -1;
   if (K < 0) return -2;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED) return -3;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED &&
+      mode != TDC_MERGE_STRUCTURED_SPLIT)
+    return -3;
   if (validate_opts(&op)) return -4;
   if (!bytes) return -5;
+  if (mode == TDC_MERGE_STRUCTURED_SPLIT) {
+    *bytes = cauchy_ss_layout(m, K, op).total;
+    return TDC_OK;
+  }
   if (mode == TDC_MERGE_DENSE) {
     *bytes = 256;
     return TDC_OK;
@@ -782,7 +961,9 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   if (!s) return -9;
   if (!C) return -10;
   if (ldc < m) return -11;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED) return -12;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED &&
+      mode != TDC_MERGE_STRUCTURED_SPLIT)
+    return -12;
   if (validate_opts(&op)) return -13;
   size_t need = 0;
   tdc_cauchy_gemm_workspace_size(m, K, mode, &op, &need);
@@ -800,6 +981,66 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
   cudaError_t err;
   if (mode == TDC_MERGE_DENSE) {
     err = launch_seg_dense(sg, cs);
+  } else if (mode == TDC_MERGE_STRUCTURED_SPLIT) {
+    const CauchySS L = cauchy_ss_layout(m, K, op);
+    char* p = wbase;
+    GemmSeg* segs = (GemmSeg*)(p + L.segs);
+    int32_t* iota = (int32_t*)(p + L.iota);
+    StructArgs SA;
+    memset(&SA, 0, sizeof(SA));
+    SA.m = op.lr_tile;
+    SA.rmax = kStructRmax;
+    SA.Tmax = (int)L.T;
+    SA.tol = op.lr_tol;
+    SA.srank = (int*)(p + L.srank);
+    SA.spiv = (int*)(p + L.spiv);
+    SA.sy = (double*)(p + L.sy);
+    SA.svr = (double*)(p + L.svr);
+    SA.scolpiv = (int*)(p + L.scolpiv);
+    SA.ldw = m;
+    SA.status = st;
+    SA.fallback_only = 1;
+    SSArgs A;
+    memset(&A, 0, sizeof(A));
+    A.ssegs = segs;
+    A.nseg = 1;
+    A.S = SA;
+    A.digits = op.split_slices;
+    A.near_segs = (GemmSeg*)(p + L.lists);
+    A.w_segs = A.near_segs + (L.T + 1);
+    A.ap_segs = A.w_segs + (L.T + 1);
+    A.counts = (int64_t*)(p + L.counts);
+    A.wcol0 = (int32_t*)(p + L.wcol0);
+    A.bcol = (int32_t*)(p + L.bcol);
+    A.wpos = (int32_t*)(p + L.wpos);
+    A.bcap = L.wcap;
+    A.W = (double*)(p + L.w);
+    A.ldw = m;
+    A.wcap = L.wcap;
+    A.R = (double*)(p + L.r);
+    A.rcap = L.wcap * op.lr_tile;
+    A.cexp = (int32_t*)(p + L.cexp);
+    A.item = (int64_t*)(p + L.item);
+    A.img_cap = L.img_elems;
+    A.status = st;
+    __nv_bfloat16* img = (__nv_bfloat16*)(p + L.img);
+    sg.near_m = op.lr_tile;
+    sg.plist = iota;
+    GemmSeg last;
+    memset(&last, 0, sizeof(last));
+    k_iota<<<(unsigned)std::min<int64_t>(1024, (K + 255) / 256), 256, 0, cs>>>(iota, K);
+    err = cudaGetLastError();
+    if (err == cudaSuccess) {
+      k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
+      err = cudaGetLastError();
+    }
+    if (err == cudaSuccess) err = launch_srrsc(segs, 1, SA, cs);
+    if (err == cudaSuccess) err = launch_ss_build(A, cs);
+    GemmSeg* lists[3] = {A.near_segs, A.w_segs, A.ap_segs};
+    for (int k = 0; k < 3 && err == cudaSuccess; ++k)
+      err = launch_split_list(lists[k], (int)L.T, A.counts + k, op.split_slices, st, op.spin_budget, img,
+                              op.split_chunk_k / 16, nullptr, cs, nullptr);
+    if (err == cudaSuccess) err = launch_struct_fallback(segs, 1, SA, cs);
   } else if (mode == TDC_MERGE_STRUCTURED) {
     const int64_t mm = op.lr_tile, T = (K + mm - 1) / mm, ns = T * T;
     char* p = wbase;

@@ -138,6 +138,11 @@ struct GemmSeg {
   const double* Bd;
   int64_t ldb;
   const int32_t* cexp;
+  // generated B with its columns drawn from a root list: column jj is root bcol[jj]
+  // (the structured path's W products, Qhat(I, pivot roots)); NULL = identity
+  const int32_t* bcol;
+  int32_t acc;  // 1: the product is added to C (the structured path's low-rank part)
+  int32_t pad_;
 };
 
 struct Plan {
@@ -170,6 +175,8 @@ struct Plan {
   long long spin_budget;
   int32_t struct_min_K; // merges with K >= this use the structured path (0: never)
   int32_t struct_m;     // tile size of the structured path
+  int32_t struct_split; // 1: the structured path's products run on the split tensor-core GEMM
+  int32_t pad_;
 };
 
 // Scratch of the structured path: one slot per (segment, row tile I, column tile J).
@@ -189,7 +196,70 @@ struct StructArgs {
   unsigned long long* flops;  // executed multiply-add flops (statistics; NULL when off)
   unsigned long long* ranks;  // statistics (NULL when off): far tiles, sum of their ranks,
                               // dense fallbacks, largest rank kept
+  int fallback_only;          // k_struct_apply: only the tiles that stayed dense (the split variant)
 };
+
+// Scratch and outputs of the structured path on the split GEMM (one level, or one
+// stand-alone product): from the SRRSC results of the structured segments it builds
+// three lists of split segments -- the near-diagonal products (written), the W
+// products Qtilde(:, I) Qhat(I, pivot roots) (into W), and the applications
+// C(:, J) += W_J R_J (added) -- and the R_J blocks with their column scales.
+struct SSArgs {
+  const GemmSeg* ssegs;  // structured segments (near_m > 0 marks a part on the structured path)
+  int nseg;
+  StructArgs S;          // the SRRSC results and tile geometry
+  int digits;            // split slices per operand
+  GemmSeg* near_segs;    // each list: nseg * Tmax segments + the terminator
+  GemmSeg* w_segs;
+  GemmSeg* ap_segs;
+  int64_t* counts;       // [3]: segments in the three lists (device)
+  int32_t* wcol0;        // per slot: first W column of its pivots
+  int32_t* bcol;         // root of each W column, in W-product order
+  int32_t* wpos;         // W column of each W-product column
+  int64_t bcap;          // capacity of bcol / wpos
+  double* W;             // ldw x wcap
+  int64_t ldw, wcap;
+  double* R;             // R_J blocks, column-major with ld = the block's rows
+  int64_t rcap;
+  int32_t* cexp;         // per (segment, J) x m: column scale exponents of R_J
+  int64_t* item;         // per (segment, tile) scratch: 6 x nseg x Tmax
+  int64_t img_cap;       // digit-image capacity (elements) of each of the three products
+  int* status;
+  unsigned long long* flops;  // statistics: executed flops of the three products (NULL when off)
+};
+
+// Exclusive scan of four int64 values over the block (warp shuffles, then the
+// warp totals scanned by warp 0); blockDim.x a multiple of 32, at most 1024.
+__device__ __forceinline__ void block_excl_scan4(int64_t (&v)[4], int64_t (&sc)[4][32]) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int64_t inc[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    inc[q] = v[q];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, inc[q], o);
+      if (lane >= o) inc[q] += t;
+    }
+    if (lane == 31) sc[q][w] = inc[q];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int64_t x = lane < nw ? sc[q][lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+      }
+      if (lane < nw) sc[q][lane] = x;  // inclusive over warps
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = inc[q] - v[q] + (w > 0 ? sc[q][w - 1] : 0);
+}
 
 // A merge (node) of level l: node i of problem p splits at mid.
 struct Node {
@@ -336,6 +406,12 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, i
                               cudaEvent_t mid);
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, int chunk_steps, cudaStream_t s);
+cudaError_t launch_split_list(const GemmSeg* segs, int nseg_bound, const int64_t* dcount, int S, int* status,
+                              long long spin_budget, __nv_bfloat16* img, int chunk_steps, unsigned int* lvl_max,
+                              cudaStream_t s, cudaEvent_t mid);
+cudaError_t launch_srrsc(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
+cudaError_t launch_struct_fallback(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
+cudaError_t launch_ss_build(const SSArgs& A, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);

@@ -150,6 +150,7 @@ __device__ __forceinline__ void split_seg_counts(const Plan& P, int level, int64
   ta = tb = tt = el = 0;
   const int K = P.m.K[g];
   if (!(P.split_min_K > 0 && K >= P.split_min_K)) return;
+  if (P.struct_split && P.struct_min_K > 0 && K >= P.struct_min_K) return;  // the structured path's
   const Node nd = make_node(P, level, g);
   const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
   const int64_t rows = p ? n - n1 : n1, kk = p ? P.m.nbot[g] : P.m.ntop[g];
@@ -158,39 +159,6 @@ __device__ __forceinline__ void split_seg_counts(const Plan& P, int level, int64
   tb = (p == 1 && shared_b(P, g)) ? 0 : CT * KB;
   tt = RT * CT;
   el = ta * S * kATileElems + tb * S * kBTileElems;
-}
-
-// Exclusive scan of four int64 values over the block (warp shuffles, then the
-// warp totals scanned by warp 0); blockDim.x a multiple of 32, at most 1024.
-__device__ __forceinline__ void block_excl_scan4(int64_t (&v)[4], int64_t (&sc)[4][32]) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int64_t inc[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    inc[q] = v[q];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t t = __shfl_up_sync(0xffffffffu, inc[q], o);
-      if (lane >= o) inc[q] += t;
-    }
-    if (lane == 31) sc[q][w] = inc[q];
-  }
-  __syncthreads();
-  if (w == 0) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int64_t x = lane < nw ? sc[q][lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int64_t t = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += t;
-      }
-      if (lane < nw) sc[q][lane] = x;  // inclusive over warps
-    }
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < 4; ++q) v[q] = inc[q] - v[q] + (w > 0 ? sc[q][w - 1] : 0);
 }
 
 // Merges [g0, g1), or (pass >= 0) the merge range of that pass from k_split_pack
@@ -400,9 +368,10 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
       if (sg.Bd) {
         sj = sg.cexp ? pow2(-sg.cexp[jj]) : 1.0;
       } else {
-        dorg = sg.D[sg.org[jj]];
-        tj = sg.tau[jj];
-        sj = sg.scol[jj];
+        const int jr = sg.bcol ? sg.bcol[jj] : jj;
+        dorg = sg.D[sg.org[jr]];
+        tj = sg.tau[jr];
+        sj = sg.scol[jr];
       }
     }
     uint32_t dig[8][kMaxS];
@@ -753,7 +722,9 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
             const int j = t.ct * BN + c0 + i;
             if (j < sg.K) {
               const int pos = sg.cpos ? sg.cpos[j] : j;
-              sg.C[row + (int64_t)pos * sg.ldc] = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+              const double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+              double* cp = sg.C + row + (int64_t)pos * sg.ldc;
+              if (sg.acc) *cp += v; else *cp = v;
             }
           }
         }
@@ -804,7 +775,9 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           const int j = t.ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            sg.C[row + (int64_t)pos * sg.ldc] = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+            const double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+            double* cp = sg.C + row + (int64_t)pos * sg.ldc;
+            if (sg.acc) *cp += v; else *cp = v;
           }
         }
       }
@@ -889,6 +862,18 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, i
   if (mid) cudaEventRecord(mid, s);
   return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, P.split_chunk_steps,
                           P.stats ? &P.stats->split_level_max : nullptr, s);
+}
+
+// A segment list whose count lives on the device (*dcount; nseg_bound bounds it):
+// digit images, then the products; `mid` (optional) is recorded between the two.
+cudaError_t launch_split_list(const GemmSeg* segs, int nseg_bound, const int64_t* dcount, int S, int* status,
+                              long long spin_budget, __nv_bfloat16* img, int chunk_steps, unsigned int* lvl_max,
+                              cudaStream_t s, cudaEvent_t mid) {
+  if (nseg_bound <= 0) return cudaSuccess;
+  cudaError_t e = launch_split_digits(segs, nseg_bound, dcount, S, img, s);
+  if (e != cudaSuccess) return e;
+  if (mid) cudaEventRecord(mid, s);
+  return launch_split_mma(segs, nseg_bound, dcount, S, status, spin_budget, img, chunk_steps, lvl_max, s);
 }
 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,

@@ -322,6 +322,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_struct_apply(const GemmSeg* seg
   const int r0 = blockIdx.x * kBM;
   if (r0 >= sg.rows) return;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (S.fallback_only) {  // nothing to add unless a tile of this column tile stayed dense
+    bool any = false;
+    for (int I = 0; I < T && !any; ++I)
+      any = iabs(I - J) > 1 && S.srank[((int64_t)s * S.Tmax + I) * S.Tmax + J] < 0;
+    if (!any) return;
+  }
   double acc[8][4];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_struct_apply(const GemmSeg* seg
     if (iabs(I - J) <= 1) continue;
     const int64_t slot = ((int64_t)s * S.Tmax + I) * S.Tmax + J;
     const int r = S.srank[slot];
-    if (r == 0) continue;
+    if (r == 0 || (S.fallback_only && r > 0)) continue;
     __syncthreads();
     if (tid < kBN) {  // this tile's column generators for the 64 output columns
       const int c = blockIdx.y * kBN + tid;
@@ -468,15 +474,31 @@ cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t
   return cudaGetLastError();
 }
 
+// SRRSC of every far tile of nseg segments.
+cudaError_t launch_srrsc(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s) {
+  if (nseg <= 0 || A.Tmax <= 0) return cudaSuccess;
+  const size_t smem = (size_t)A.m * (5 * sizeof(double) + 4 * sizeof(float) + 2);
+  cudaError_t e = cudaFuncSetAttribute(k_srrsc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_srrsc<<<dim3((unsigned)(A.Tmax * A.Tmax), (unsigned)nseg), 256, smem, s>>>(segs, A);
+  return cudaGetLastError();
+}
+
+// The tiles whose rank exceeded the cap (they stayed dense): C(:, J) += Qtilde(:, I)
+// Qhat(I, J) in FP64, after the split path's products (A.fallback_only set).
+cudaError_t launch_struct_fallback(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s) {
+  if (nseg <= 0 || A.Tmax <= 0) return cudaSuccess;
+  const unsigned rt = (unsigned)((A.ldw + kBM - 1) / kBM);
+  for (int J = 0; J < A.Tmax; ++J)
+    k_struct_apply<<<dim3(rt, (unsigned)((A.m + kBN - 1) / kBN), (unsigned)nseg), kThreads, 0, s>>>(segs, A, J);
+  return cudaGetLastError();
+}
+
 // The low-rank part for nseg segments whose dense near-diagonal part is done.
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s) {
   if (nseg <= 0 || A.Tmax <= 0) return cudaSuccess;
   const int m = A.m;
-  const size_t smem = (size_t)m * (5 * sizeof(double) + 4 * sizeof(float) + 2);
-  cudaError_t e = cudaFuncSetAttribute(k_srrsc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_srrsc<<<dim3((unsigned)(A.Tmax * A.Tmax), (unsigned)nseg), 256, smem, s>>>(segs, A);
-  e = cudaGetLastError();
+  cudaError_t e = launch_srrsc(segs, nseg, A, s);
   if (e != cudaSuccess) return e;
   const unsigned rt = (unsigned)((A.ldw + kBM - 1) / kBM);
   for (int J = 0; J < A.Tmax; ++J) {

@@ -30,6 +30,7 @@ MERGE_AUTO = 0
 MERGE_DENSE = 1
 MERGE_STRUCTURED = 2
 MERGE_SPLIT = 3
+MERGE_STRUCTURED_SPLIT = 4
 
 MAX_LEVELS = 32
 

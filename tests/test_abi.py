@@ -38,6 +38,11 @@ def test_default_opts_and_workspace(lib):
     w2 = tdc.workspace_size(2048, o)
     assert 2048 * 2048 * 8 < w2 and w1 < w2
     assert tdc.workspace_size(0, o) > 0
+    # the structured merge on the split path needs its own scratch on top of the split path's
+    w4 = tdc.workspace_size(16384, tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_STRUCTURED_SPLIT))
+    assert w4 > tdc.workspace_size(16384, tdc.default_opts(leaf=64))
+    assert tdc.cauchy_gemm_workspace_size(300, 1000, tdc.MERGE_STRUCTURED_SPLIT,
+                                          tdc.default_opts(lr_tile=128)) > 300 * 1000 * 2
     # the chunk length of the split accumulators' drains changes no workspace
     assert tdc.workspace_size(2048, tdc.default_opts(split_chunk_k=512)) == w2
     assert tdc.workspace_size(2048, tdc.default_opts(split_chunk_k=0)) == w2
@@ -68,7 +73,7 @@ def test_host_argument_checks(lib):
     assert tdc.strerror(tdc.TDC_WPRECISION).startswith("warning")
 
 
-@pytest.mark.parametrize("bad", [dict(leaf=1), dict(leaf=65), dict(merge_mode=4), dict(max_iter=0),
+@pytest.mark.parametrize("bad", [dict(leaf=1), dict(leaf=65), dict(merge_mode=5), dict(max_iter=0),
                                  dict(lr_tile=100), dict(split_slices=2), dict(split_slices=8),
                                  dict(split_min_K=0), dict(spin_budget=0), dict(lr_tol=0.0),
                                  dict(split_chunk_k=8), dict(split_chunk_k=-16)])
