@@ -6,8 +6,11 @@ quoted on.  One step = one full eigensolve T = Q diag(lam) Q^T through the C ABI
 (tdc_eig) with d, e resident in HBM.  The Q and internal buffers (2 x 2 GiB) are
 larger than L2, so no explicit flush is needed between steps.
 
-The default line also carries the merge comparison on the same matrix (dense FP64
-and structured merges, each with its own accuracy check and roofline), the other
+The timed solve uses the library's default merge: the structured update (SRRSC
+low-rank far tiles, Section 2.1 / Algorithm 2) with its products on the split
+tensor-core GEMM for the large merges.  The default line also carries the merge
+comparison on the same matrix (the plain split product, and the dense FP64 and
+structured FP64 merges, each with its own accuracy check and roofline), the other
 workloads (uniform n = 1024, the batch of 4096 tridiagonals under a CUDA graph,
 d ~ U(0,1) with e = 1 at n = 32768, and the adjoint of 256 problems of order 512),
 each timed with a few steps, and the FP64 CPU oracle timed on the host's cores on
@@ -712,31 +715,26 @@ def run_ours(args):
                          "peak_kind": "derived: 152 SMs x 2 DFMA/clk x 2.07 GHz",
                          "note": "executed flops only (the dense flops it avoids are not counted); the phase "
                                  "also holds the FP32 SRRSC pivot searches"}}
-    if args.merge not in ("dense", "structured_split") and not args.no_compare and n >= 4096:
-        o4 = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_STRUCTURED_SPLIT, collect_stats=1)
-        o4p = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_STRUCTURED_SPLIT)
-        ws4 = tdc.workspace(tdc.workspace_size(n, o4), dev)
+    if args.merge not in ("dense", "split") and not args.no_compare and n >= 4096:
+        # the plain split product (every merge unstructured) on the tensor cores
+        o3p = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_SPLIT, **kw)
+        o3 = tdc.default_opts(leaf=leaf, merge_mode=tdc.MERGE_SPLIT, collect_stats=1, **kw)
+        ws3 = tdc.workspace(tdc.workspace_size(n, o3p), dev)
         for _ in range(2):
-            tdc.eig(d, e, o4p, ws=ws4, lam=lam, Q=Q, stream=stream)
-        st4 = tdc.sync_status(stream)
-        steps4 = max(1, min(args.steps, 10))
-        ms4 = _event_ms(lambda: tdc.eig(d, e, o4p, ws=ws4, lam=lam, Q=Q, stream=stream), steps4, stream)
-        tdc.eig(d, e, o4, ws=ws4, lam=lam, Q=Q, stream=stream)
-        s4 = tdc.get_stats()
-        del ws4
-        compare["structured_split"] = ms4 / 1e3
-        kept = max(1, s4["lr_tiles"] - s4["lr_dense_fallbacks"])
-        compare_detail["structured_split"] = {
-            "s": ms4 / 1e3, "steps": steps4, "status": tdc.strerror(st4), "test_ratios": accuracy(),
-            "options": {"lr_tile": o4.lr_tile, "structured_min_K": o4.structured_min_K, "lr_tol": o4.lr_tol,
-                        "rank_cap": 64, "split_chunk_k": o4.split_chunk_k},
-            "srrsc": {"far_tiles": s4["lr_tiles"], "mean_rank": s4["lr_rank_sum"] / kept,
-                      "max_rank": s4["lr_rank_max"], "dense_fallbacks": s4["lr_dense_fallbacks"]},
-            "split_level_max": s4["split_level_max"], "phase_ms": s4["phase_ms"],
-            "roofline": split_roofline(s4, s4["phase_ms"]["split_mma"], o4.split_slices, *peaks(),
-                                       "; executed flops of the near, W and apply products and the merges "
-                                       "below the structured threshold; phase time of one instrumented solve")}
-        progress("structured merge on the split path done")
+            tdc.eig(d, e, o3p, ws=ws3, lam=lam, Q=Q, stream=stream)
+        st3 = tdc.sync_status(stream)
+        steps3 = max(1, min(args.steps, 10))
+        ms3 = _event_ms(lambda: tdc.eig(d, e, o3p, ws=ws3, lam=lam, Q=Q, stream=stream), steps3, stream)
+        tdc.eig(d, e, o3, ws=ws3, lam=lam, Q=Q, stream=stream)
+        s3 = tdc.get_stats()
+        del ws3
+        compare["split"] = ms3 / 1e3
+        compare_detail["split"] = {
+            "s": ms3 / 1e3, "steps": steps3, "status": tdc.strerror(st3), "test_ratios": accuracy(),
+            "split_level_max": s3["split_level_max"], "phase_ms": s3["phase_ms"],
+            "roofline": split_roofline(s3, s3["phase_ms"]["split_mma"], o3p.split_slices, *peaks(),
+                                       "; phase time of one instrumented solve")}
+        progress("plain split merge done")
     if compare_detail:
         tdc.eig(d, e, opts, ws=wsb, lam=lam, Q=Q, stream=stream)  # leave the timed configuration's result
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -793,6 +791,12 @@ def run_ours(args):
         "K_per_level": stats["sum_K"],
         "secular_iterations": {"mean": stats["secular_iter_mean"], "max": stats["secular_iter_max"]},
         "split_level_max": stats.get("split_level_max"),
+        "structured": {"merge_parts_structured": stats.get("lr_parts_structured"),
+                       "merge_parts_left_to_split": stats.get("lr_parts_split"),
+                       "far_tiles": stats.get("lr_tiles"),
+                       "mean_rank": stats["lr_rank_sum"] / max(1, stats["lr_tiles"] - stats["lr_dense_fallbacks"]),
+                       "max_rank": stats.get("lr_rank_max"), "lr_tile": opts.lr_tile,
+                       "structured_min_K": opts.structured_min_K, "lr_tol": opts.lr_tol},
         "device_status": tdc.strerror(st),
         "test_ratios": {"lam_err_over_normT": lam_err, "residual": res, "orthogonality": orth,
                         "sampled_columns": 256, "within_bounds": bool(res <= 50 and orth <= 50)},

@@ -60,13 +60,19 @@ typedef struct CUstream_st* tdc_stream_t; /* identical to cudaStream_t */
 #define TDC_WPRECISION 1
 
 /* merge modes: how the eigenvector update Q * U is computed */
-#define TDC_MERGE_AUTO 0        /* library choice: the split path for merges with K >= split_min_K, FP64 below */
+#define TDC_MERGE_AUTO 0        /* library choice: merges with K >= structured_min_K take the structured path on
+                                   the split GEMM (TDC_MERGE_STRUCTURED_SPLIT), merges with K >= split_min_K
+                                   the split path, smaller ones FP64 */
 #define TDC_MERGE_DENSE 1       /* FP64 GEMM, U generated from its generators in the producer */
 #define TDC_MERGE_STRUCTURED 2  /* near-diagonal tiles dense, off-diagonal tiles SRRSC-compressed */
-#define TDC_MERGE_SPLIT 3       /* BF16 slice products on tcgen05 tensor cores, FP32/FP64 accumulation */
+#define TDC_MERGE_SPLIT 3       /* BF16 slice products on tcgen05 tensor cores, FP32/FP64 accumulation, for
+                                   merges with K >= split_min_K (FP64 below), every merge unstructured */
 #define TDC_MERGE_STRUCTURED_SPLIT 4 /* the structured update (near-diagonal tiles dense, off-diagonal tiles
                                         SRRSC-compressed) with all of its products on the split tensor-core
-                                        path; merges with K < structured_min_K as TDC_MERGE_AUTO */
+                                        path, for merges with K >= max(structured_min_K, split_min_K); a merge
+                                        half whose far tiles pass the rank cap (64) or need more low-rank
+                                        columns than the path's buffer takes the split path whole; smaller
+                                        merges as TDC_MERGE_SPLIT.  This is AUTO's choice. */
 /* Accuracy of the split path (SPLIT and AUTO): the digit products of one level are
  * summed in FP32 accumulators, exact only while each level's sum stays below 2^24.
  * The default schedule drains them into 64-bit integer sums every split_chunk_k = 256
@@ -132,6 +138,10 @@ typedef struct {
                                             lr_dense_fallbacks)) */
   int64_t lr_dense_fallbacks;            /* tiles whose rank exceeded the cap and stayed dense */
   int64_t lr_rank_max;                   /* largest rank kept in low-rank form */
+  int64_t lr_parts_structured;           /* TDC_MERGE_STRUCTURED_SPLIT: merge parts (one per half of a
+                                            merge) the structured products took */
+  int64_t lr_parts_split;                /* ... parts left to the plain split product: a far tile past
+                                            the rank cap, or more low-rank columns than its buffer */
 } tdc_stats;
 
 /* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 256,

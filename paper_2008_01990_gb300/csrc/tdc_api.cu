@@ -110,13 +110,33 @@ struct HostPlan {
 
 // the structured path on the split GEMM: W columns per tile of a level, on average
 // (tiles beyond the budget stay dense), and the digit-image elements a level may use
-static constexpr int64_t kSsRankBudget = 16;
+static constexpr int64_t kSsRankBudget = 8;
 static constexpr int64_t kSsImgBudget = (int64_t)8 << 30;
 
-static bool struct_enabled(const tdc_opts& o) {
-  return o.merge_mode == TDC_MERGE_STRUCTURED || o.merge_mode == TDC_MERGE_STRUCTURED_SPLIT;
+// Digit-image elements of the structured path on the split GEMM for nseg parts of at
+// most `rows` rows and kmax poles, `items` column tiles in all, tiles of m: one A
+// image per part (read by its near and W products), with the larger of the near and
+// W products' B images after it; then the apply products' own images, which reuse
+// the buffer.  A near range holds at most 3m poles, a row tile at most m, and the W
+// and apply products at most wcap columns / rows in all.
+static int64_t ss_img_bound(int64_t nseg, int64_t items, int64_t rows, int64_t kmax, int64_t m, int64_t wcap,
+                            int64_t S) {
+  const int64_t at = (int64_t)kSplitBM * kSplitBK, bt = (int64_t)kSplitBN * kSplitBK;
+  const int64_t RT = (rows + kSplitBM - 1) / kSplitBM, CTm = (m + kSplitBN - 1) / kSplitBN;
+  const int64_t imgA = nseg * RT * ((kmax + kSplitBK - 1) / kSplitBK) * S * at;
+  const int64_t nearB = items * CTm * ((3 * m + kSplitBK - 1) / kSplitBK + 2) * S * bt;
+  const int64_t wB = (wcap / kSplitBN + items) * ((m + kSplitBK - 1) / kSplitBK + 2) * S * bt;
+  const int64_t ap = (wcap / kSplitBK + items) * (RT * at + CTm * bt) * S;
+  return std::max(imgA + std::max(nearB, wB), ap);
 }
-static bool struct_split_mode(const tdc_opts& o) { return o.merge_mode == TDC_MERGE_STRUCTURED_SPLIT; }
+
+// AUTO takes the structured path on the split GEMM for merges with K >= structured_min_K
+static bool struct_split_mode(const tdc_opts& o) {
+  return o.merge_mode == TDC_MERGE_STRUCTURED_SPLIT || o.merge_mode == TDC_MERGE_AUTO;
+}
+static bool struct_enabled(const tdc_opts& o) {
+  return o.merge_mode == TDC_MERGE_STRUCTURED || struct_split_mode(o);
+}
 // merges with K >= this take the structured path (on the split GEMM it never starts
 // below the split threshold)
 static int struct_threshold(const tdc_opts& o) {
@@ -136,8 +156,7 @@ static void plan_struct(HostPlan& H, const tdc_opts& o) {
   H.ss_level.assign(H.T, 0);
   H.ss_wcap.assign(H.T, 0);
   if (!H.struct_m) return;
-  const int64_t m = H.struct_m, S = o.split_slices, rmax = kStructRmax;
-  const int64_t at = (int64_t)kSplitBM * kSplitBK, bt = (int64_t)kSplitBN * kSplitBK;
+  const int64_t m = H.struct_m, S = o.split_slices;
   for (int l = 0; l < H.T; ++l) {
     const LevelLaunch& L = H.levels[l];
     if (L.max_n < struct_threshold(o)) continue;
@@ -152,17 +171,10 @@ static void plan_struct(HostPlan& H, const tdc_opts& o) {
     // (tiles beyond it stay dense, in FP64); the R blocks, column lists and digit
     // images follow from it.  A row tile holds at most m poles, the near range of a
     // column tile at most 3m.
-    (void)rmax;
     const int64_t items = nseg * Tmax;
     const int64_t wcap = std::max<int64_t>(
         kSplitBN, std::min<int64_t>(items * Tmax * kSsRankBudget, ((int64_t)1 << 29) / std::max<int64_t>(ldw, 1)));
-    const int64_t RT = (ldw + kSplitBM - 1) / kSplitBM, CTm = (m + kSplitBN - 1) / kSplitBN;
-    const int64_t KBn = (std::min(3 * m, L.max_n) + kSplitBK - 1) / kSplitBK + 1;
-    const int64_t KBm = (m + kSplitBK - 1) / kSplitBK + 1;
-    const int64_t near = items * KBn * (RT * at + CTm * bt) * S;
-    const int64_t wimg = (items * RT * KBm * at + (wcap / kSplitBN + items) * KBm * bt) * S;
-    const int64_t aimg = (wcap / kSplitBK + items) * (RT * at + CTm * bt) * S;
-    const int64_t img = std::max(near, std::max(wimg, aimg));
+    const int64_t img = ss_img_bound(nseg, items, ldw, L.max_n, m, wcap, S);
     H.ss_level[l] = img <= kSsImgBudget;
     if (!H.ss_level[l]) continue;  // this level's merges take the split path
     H.ss_wcap[l] = wcap;
@@ -299,7 +311,7 @@ static void build_plan(HostPlan& H, int32_t batch, const int64_t* n_host, const 
 // workspace carving
 struct Layout {
   size_t prob, vec_d, vec_i, vec_b, minfo, tiles, stats, segs, img, srank, spiv, sy, svr, scolpiv, sw;
-  size_t ss_segs, ss_counts, ss_wcol0, ss_bcol, ss_wpos, ss_w, ss_r, ss_cexp, ss_item, q1, total;
+  size_t ss_segs, ss_counts, ss_wcol0, ss_bcol, ss_wpos, ss_w, ss_r, ss_cexp, ss_item, ss_accept, q1, total;
 };
 
 static constexpr int kVecD = 27;  // doubles per slot (13 vectors, 2 for rcs, 2 for skey, xlo, zz, 8 boundary rows)
@@ -331,8 +343,8 @@ static Layout layout_of(const HostPlan& H) {
   L.scolpiv = o; o = align_up(o + sizeof(int) * ns * mm);
   L.sw = o; o = align_up(o + sizeof(double) * (size_t)H.struct_w);
   const size_t it = (size_t)H.ss_items;
-  L.ss_segs = o; o = align_up(o + (H.ss ? 3 * sizeof(GemmSeg) * (it + 1) : 0));
-  L.ss_counts = o; o = align_up(o + (H.ss ? 3 * sizeof(int64_t) : 0));
+  L.ss_segs = o; o = align_up(o + (H.ss ? 4 * sizeof(GemmSeg) * (it + 1) : 0));
+  L.ss_counts = o; o = align_up(o + (H.ss ? 4 * sizeof(int64_t) : 0));
   L.ss_wcol0 = o; o = align_up(o + sizeof(int32_t) * ns);
   L.ss_bcol = o; o = align_up(o + sizeof(int32_t) * (size_t)H.ss_bcap);
   L.ss_wpos = o; o = align_up(o + sizeof(int32_t) * (size_t)H.ss_bcap);
@@ -340,6 +352,7 @@ static Layout layout_of(const HostPlan& H) {
   L.ss_r = o; o = align_up(o + sizeof(double) * (size_t)H.ss_r);
   L.ss_cexp = o; o = align_up(o + sizeof(int32_t) * it * mm);
   L.ss_item = o; o = align_up(o + sizeof(int64_t) * 6 * it);
+  L.ss_accept = o; o = align_up(o + (H.ss ? sizeof(int32_t) * 2 * (size_t)H.Mmax : 0));
   L.q1 = o; o = align_up(o + sizeof(double) * (size_t)H.Q1);
   L.total = o + 256;  // slack for aligning an unaligned base
   return L;
@@ -588,6 +601,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       A.near_segs = (GemmSeg*)(base + L.ss_segs);
       A.w_segs = A.near_segs + (H.ss_items + 1);
       A.ap_segs = A.w_segs + (H.ss_items + 1);
+      A.img_segs = A.ap_segs + (H.ss_items + 1);
       A.counts = (int64_t*)(base + L.ss_counts);
       A.wcol0 = (int32_t*)(base + L.ss_wcol0);
       A.bcol = (int32_t*)(base + L.ss_bcol);
@@ -600,23 +614,28 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       A.rcap = H.ss_wcap[l] * H.struct_m;
       A.cexp = (int32_t*)(base + L.ss_cexp);
       A.item = (int64_t*)(base + L.ss_item);
+      A.accept = (int32_t*)(base + L.ss_accept);
       A.img_cap = P.img_cap;
       A.status = P.status;
       A.flops = P.stats ? &P.stats->split_flops : nullptr;
+      A.parts = P.stats ? P.stats->ss_parts : nullptr;
+      P.ss_accept = A.accept;  // the plain split path below takes the parts this one leaves
       err = launch_struct_segs(P, LL, sg);
       if (err == cudaSuccess) err = launch_srrsc(P.segs, nseg, SA, sg);
       if (err == cudaSuccess) err = launch_ss_build(A, sg);
-      GemmSeg* lists[3] = {A.near_segs, A.w_segs, A.ap_segs};
+      // the parts' A images (digits only), then the near, W and apply products
+      GemmSeg* lists[4] = {A.img_segs, A.near_segs, A.w_segs, A.ap_segs};
+      const int64_t* cnts[4] = {A.counts + 3, A.counts + 0, A.counts + 1, A.counts + 2};
       size_t b4 = mark_on(sg);
       span(4, g1, b4);
-      for (int k = 0; k < 3 && err == cudaSuccess; ++k) {
+      for (int k = 0; k < 4 && err == cudaSuccess; ++k) {
         cudaEvent_t mid = nullptr;
         if (timing) {
           cudaEventCreate(&mid);
           evs.push_back(mid);
         }
         const size_t b5 = timing ? evs.size() - 1 : 0;
-        err = launch_split_list(lists[k], (int)items, A.counts + k, P.split_slices, P.status, P.spin_budget, P.img,
+        err = launch_split_list(lists[k], (int)items, cnts[k], P.split_slices, P.status, P.spin_budget, P.img,
                                 P.split_chunk_steps, P.stats ? &P.stats->split_level_max : nullptr, sg, mid);
         const size_t b6 = mark_on(sg);
         span(5, b4, b5);
@@ -624,7 +643,6 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
         b4 = b6;
       }
       g1 = b4;
-      if (err == cudaSuccess) err = launch_struct_fallback(P.segs, nseg, SA, sg);
     } else if (err == cudaSuccess && !H.ss && P.struct_min_K > 0 && LL.max_n >= P.struct_min_K) {
       int64_t Tmax, ldw;
       level_struct_dims(LL, H.struct_m, Tmax, ldw);
@@ -714,6 +732,8 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     g_last_stats.lr_rank_sum = (int64_t)hs.srrsc[1];
     g_last_stats.lr_dense_fallbacks = (int64_t)hs.srrsc[2];
     g_last_stats.lr_rank_max = (int64_t)hs.srrsc[3];
+    g_last_stats.lr_parts_structured = (int64_t)hs.ss_parts[0];
+    g_last_stats.lr_parts_split = (int64_t)hs.ss_parts[1];
     g_last_stats.secular_iter_max = hs.iter_max;
     g_last_stats.secular_iter_mean = hs.iter_roots ? (double)hs.iter_sum / (double)hs.iter_roots : 0.0;
     for (int i = 0; i < 12; ++i) g_last_stats.phase_ms[i] = phase[i];
@@ -874,21 +894,16 @@ __global__ void k_iota(int32_t* a, int64_t n) {
 // m rows and K poles / roots): SRRSC scratch, the identity pole list, the three
 // segment lists, W, R, scales and digit images (bounds as for an eigensolver level).
 struct CauchySS {
-  size_t segs, srank, spiv, sy, svr, scolpiv, iota, lists, counts, wcol0, bcol, wpos, w, r, cexp, item, img, total;
+  size_t segs, srank, spiv, sy, svr, scolpiv, iota, lists, counts, wcol0, bcol, wpos, w, r, cexp, item, accept, plain, img,
+      total;
   int64_t T, wcap, img_elems;
 };
 static CauchySS cauchy_ss_layout(int64_t m, int64_t K, const tdc_opts& op) {
   CauchySS L;
   const int64_t mm = op.lr_tile, T = std::max<int64_t>(1, (K + mm - 1) / mm), ns = T * T, S = op.split_slices;
-  const int64_t at = (int64_t)kSplitBM * kSplitBK, bt = (int64_t)kSplitBN * kSplitBK;
   L.T = T;
   L.wcap = std::max<int64_t>(kSplitBN, std::min<int64_t>(T * T * kSsRankBudget, ((int64_t)1 << 29) / std::max<int64_t>(m, 1)));
-  const int64_t RT = (m + kSplitBM - 1) / kSplitBM, CTm = (mm + kSplitBN - 1) / kSplitBN;
-  const int64_t KBn = (std::min(3 * mm, K) + kSplitBK - 1) / kSplitBK + 1, KBm = (mm + kSplitBK - 1) / kSplitBK + 1;
-  const int64_t near = T * KBn * (RT * at + CTm * bt) * S;
-  const int64_t wimg = (T * RT * KBm * at + (L.wcap / kSplitBN + T) * KBm * bt) * S;
-  const int64_t aimg = (L.wcap / kSplitBK + T) * (RT * at + CTm * bt) * S;
-  L.img_elems = std::max(near, std::max(wimg, aimg));
+  L.img_elems = ss_img_bound(1, T, m, K, mm, L.wcap, S);
   size_t o = 0;
   L.segs = o; o = align_up(o + 2 * sizeof(GemmSeg));
   L.srank = o; o = align_up(o + sizeof(int) * ns);
@@ -897,8 +912,8 @@ static CauchySS cauchy_ss_layout(int64_t m, int64_t K, const tdc_opts& op) {
   L.svr = o; o = align_up(o + sizeof(double) * ns * mm);
   L.scolpiv = o; o = align_up(o + sizeof(int) * ns * mm);
   L.iota = o; o = align_up(o + sizeof(int32_t) * K);
-  L.lists = o; o = align_up(o + 3 * sizeof(GemmSeg) * (T + 1));
-  L.counts = o; o = align_up(o + 3 * sizeof(int64_t));
+  L.lists = o; o = align_up(o + 4 * sizeof(GemmSeg) * (T + 1));
+  L.counts = o; o = align_up(o + 4 * sizeof(int64_t));
   L.wcol0 = o; o = align_up(o + sizeof(int32_t) * ns);
   L.bcol = o; o = align_up(o + sizeof(int32_t) * L.wcap);
   L.wpos = o; o = align_up(o + sizeof(int32_t) * L.wcap);
@@ -906,6 +921,11 @@ static CauchySS cauchy_ss_layout(int64_t m, int64_t K, const tdc_opts& op) {
   L.r = o; o = align_up(o + sizeof(double) * L.wcap * mm);
   L.cexp = o; o = align_up(o + sizeof(int32_t) * T * mm);
   L.item = o; o = align_up(o + sizeof(int64_t) * 6 * T);
+  L.accept = o; o = align_up(o + sizeof(int32_t));
+  L.plain = o; o = align_up(o + 2 * sizeof(GemmSeg));
+  // the images: those of the structured products, or those of the plain split product
+  // when the part is left to it
+  L.img_elems = std::max(L.img_elems, cauchy_split_elems(m, K, S, nullptr));
   L.img = o; o = align_up(o + sizeof(__nv_bfloat16) * L.img_elems);
   L.total = 256 + o;
   return L;
@@ -1009,6 +1029,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
     A.near_segs = (GemmSeg*)(p + L.lists);
     A.w_segs = A.near_segs + (L.T + 1);
     A.ap_segs = A.w_segs + (L.T + 1);
+    A.img_segs = A.ap_segs + (L.T + 1);
     A.counts = (int64_t*)(p + L.counts);
     A.wcol0 = (int32_t*)(p + L.wcol0);
     A.bcol = (int32_t*)(p + L.bcol);
@@ -1021,6 +1042,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
     A.rcap = L.wcap * op.lr_tile;
     A.cexp = (int32_t*)(p + L.cexp);
     A.item = (int64_t*)(p + L.item);
+    A.accept = (int32_t*)(p + L.accept);
     A.img_cap = L.img_elems;
     A.status = st;
     __nv_bfloat16* img = (__nv_bfloat16*)(p + L.img);
@@ -1036,11 +1058,34 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
     }
     if (err == cudaSuccess) err = launch_srrsc(segs, 1, SA, cs);
     if (err == cudaSuccess) err = launch_ss_build(A, cs);
-    GemmSeg* lists[3] = {A.near_segs, A.w_segs, A.ap_segs};
-    for (int k = 0; k < 3 && err == cudaSuccess; ++k)
-      err = launch_split_list(lists[k], (int)L.T, A.counts + k, op.split_slices, st, op.spin_budget, img,
+    GemmSeg* lists[4] = {A.img_segs, A.near_segs, A.w_segs, A.ap_segs};
+    const int64_t* cnts[4] = {A.counts + 3, A.counts + 0, A.counts + 1, A.counts + 2};
+    for (int k = 0; k < 4 && err == cudaSuccess; ++k)
+      err = launch_split_list(lists[k], (int)L.T, cnts[k], op.split_slices, st, op.spin_budget, img,
                               op.split_chunk_k / 16, nullptr, cs, nullptr);
-    if (err == cudaSuccess) err = launch_struct_fallback(segs, 1, SA, cs);
+    // the plain split product, emptied by the gate when the structured path took the part
+    if (err == cudaSuccess) {
+      GemmSeg* plain = (GemmSeg*)(p + L.plain);
+      GemmSeg ps = sg;
+      ps.near_m = 0;
+      ps.plist = nullptr;
+      const int64_t RT = cdiv64(m, kSplitBM), KB = cdiv64(K, kSplitBK), CT = cdiv64(K, kSplitBN);
+      int64_t a_el = 0;
+      const int64_t tot = cauchy_split_elems(m, K, op.split_slices, &a_el);
+      ps.a_img = 0;
+      ps.b_img = a_el;
+      GemmSeg pl;
+      memset(&pl, 0, sizeof(pl));
+      pl.it_a = RT * KB;
+      pl.it_b = CT * KB;
+      pl.it_t = RT * CT;
+      pl.a_img = tot;
+      k_write_segs<<<1, 32, 0, cs>>>(ps, pl, plain);
+      err = cudaGetLastError();
+      if (err == cudaSuccess) err = launch_ss_gate(A.accept, plain, cs);
+      if (err == cudaSuccess)
+        err = launch_seg_split(plain, 1, op.split_slices, st, op.spin_budget, img, op.split_chunk_k / 16, cs);
+    }
   } else if (mode == TDC_MERGE_STRUCTURED) {
     const int64_t mm = op.lr_tile, T = (K + mm - 1) / mm, ns = T * T;
     char* p = wbase;

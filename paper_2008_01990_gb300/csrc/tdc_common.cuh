@@ -104,6 +104,7 @@ struct Stats {  // device-side per-call statistics (index 0 = top level)
   unsigned long long handoffs;
   unsigned int split_level_max;  // FP32 bits of the largest |level sum| of a split hand-off (levels 0-4)
   unsigned long long srrsc[4];   // far tiles, sum of ranks, dense fallbacks, largest rank
+  unsigned long long ss_parts[2];  // structured split path: merge parts taken, parts left to the split path
 };
 
 // One GEMM segment C(rows x K) = A(rows x kk) * Qhat(list, :) of the merge
@@ -142,7 +143,12 @@ struct GemmSeg {
   // (the structured path's W products, Qhat(I, pivot roots)); NULL = identity
   const int32_t* bcol;
   int32_t acc;  // 1: the product is added to C (the structured path's low-rank part)
-  int32_t pad_;
+  // shared A image: a_kt > 0 makes the segment read the A digits written for another
+  // segment (a_img points at its first k-tile, a_kt is that image's k-tiles per row
+  // tile), and the first bq0 rows of B are zero (the segment's poles start there)
+  int32_t bq0;
+  int32_t a_kt;
+  int32_t part;  // the structured path's segment builder: the part a segment belongs to
 };
 
 struct Plan {
@@ -177,6 +183,7 @@ struct Plan {
   int32_t struct_m;     // tile size of the structured path
   int32_t struct_split; // 1: the structured path's products run on the split tensor-core GEMM
   int32_t pad_;
+  const int32_t* ss_accept;  // per merge part (2g + p): 1 if the structured split path took it
 };
 
 // Scratch of the structured path: one slot per (segment, row tile I, column tile J).
@@ -209,10 +216,11 @@ struct SSArgs {
   int nseg;
   StructArgs S;          // the SRRSC results and tile geometry
   int digits;            // split slices per operand
+  GemmSeg* img_segs;     // nseg + 1: one per part, owning its A digit image (no products)
   GemmSeg* near_segs;    // each list: nseg * Tmax segments + the terminator
   GemmSeg* w_segs;
   GemmSeg* ap_segs;
-  int64_t* counts;       // [3]: segments in the three lists (device)
+  int64_t* counts;       // [4]: segments of the near, W, apply and image lists (device)
   int32_t* wcol0;        // per slot: first W column of its pivots
   int32_t* bcol;         // root of each W column, in W-product order
   int32_t* wpos;         // W column of each W-product column
@@ -223,9 +231,11 @@ struct SSArgs {
   int64_t rcap;
   int32_t* cexp;         // per (segment, J) x m: column scale exponents of R_J
   int64_t* item;         // per (segment, tile) scratch: 6 x nseg x Tmax
+  int32_t* accept;       // per segment: 1 if this path takes the part (else the plain split path)
   int64_t img_cap;       // digit-image capacity (elements) of each of the three products
   int* status;
   unsigned long long* flops;  // statistics: executed flops of the three products (NULL when off)
+  unsigned long long* parts;  // statistics: parts taken, parts left (NULL when off)
 };
 
 // Exclusive scan of four int64 values over the block (warp shuffles, then the
@@ -412,6 +422,7 @@ cudaError_t launch_split_list(const GemmSeg* segs, int nseg_bound, const int64_t
 cudaError_t launch_srrsc(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_fallback(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_ss_build(const SSArgs& A, cudaStream_t s);
+cudaError_t launch_ss_gate(const int32_t* accept, GemmSeg* plain_list, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);

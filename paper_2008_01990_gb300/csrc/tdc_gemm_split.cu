@@ -150,7 +150,8 @@ __device__ __forceinline__ void split_seg_counts(const Plan& P, int level, int64
   ta = tb = tt = el = 0;
   const int K = P.m.K[g];
   if (!(P.split_min_K > 0 && K >= P.split_min_K)) return;
-  if (P.struct_split && P.struct_min_K > 0 && K >= P.struct_min_K) return;  // the structured path's
+  // parts the structured split path took (it leaves the others to this path)
+  if (P.struct_split && P.struct_min_K > 0 && K >= P.struct_min_K && P.ss_accept && P.ss_accept[2 * g + p]) return;
   const Node nd = make_node(P, level, g);
   const int n = (int)(nd.hi - nd.lo), n1 = (int)(nd.mid - nd.lo);
   const int64_t rows = p ? n - n1 : n1, kk = p ? P.m.nbot[g] : P.m.ntop[g];
@@ -379,7 +380,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
     for (int i = 0; i < 8; ++i) {
       const int q = kb * BK + kg * 8 + i;
       double u = 0.0;
-      if (q < sg.kk && jj < sg.K) {
+      if (q < sg.kk && q >= sg.bq0 && jj < sg.K) {
         const int p = sg.plist ? sg.plist[q] : q;
         u = sg.Bd ? sg.Bd[p + (int64_t)jj * sg.ldb] * sj : (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
       }
@@ -571,7 +572,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
       bool ok = true;
       for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
         const TileRef t = tile_ref(segs, nseg, w);
-        const uint8_t* ai = reinterpret_cast<const uint8_t*>(img + t.sg->a_img + (int64_t)t.rt * t.KB * S * kATileElems);
+        const int akt = t.sg->a_kt > 0 ? t.sg->a_kt : t.KB;  // k-tiles per row tile of the A image
+        const uint8_t* ai = reinterpret_cast<const uint8_t*>(img + t.sg->a_img + (int64_t)t.rt * akt * S * kATileElems);
         const uint8_t* bi = reinterpret_cast<const uint8_t*>(img + t.sg->b_img + (int64_t)t.ct * t.KB * S * kBTileElems);
         for (int kb = 0; kb < t.KB; ++kb, ++g) {
           const int st = (int)(g % kStages);

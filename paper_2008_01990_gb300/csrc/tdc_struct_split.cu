@@ -17,9 +17,11 @@
 //          J's far tiles, materialised in FP64 with a power-of-two scale per column
 //          so that every entry is at most 1 (the split product's fixed-point range;
 //          the epilogue scales the column back).
-// Tiles whose rank exceeded the cap stay dense and are added in FP64 afterwards
-// (k_struct_apply, fallback tiles only).  Both the near product and the W
-// products read Qtilde directly; |W| <= 1 by Cauchy-Schwarz on the unit rows of
+// A part is taken only when every far tile's rank stayed within the cap and its W
+// columns fit the W buffer; any other part is left whole to the plain split path
+// (accept[] tells its segment builder), so no tile needs a dense fallback.  Each
+// taken part's A digits (Qtilde's rows over its pole list) are written once and
+// read by its near and W products; |W| <= 1 by Cauchy-Schwarz on the unit rows of
 // Qtilde and the unit columns of Qhat.
 #include "tdc_common.cuh"
 
@@ -49,16 +51,19 @@ enum { kItKr = 0, kItWbase = 1, kItRofs = 2, kItKw = 3, kItBofs = 4, kItNext = 5
 __device__ __forceinline__ void seg_work(const GemmSeg& g, int S, int64_t& ta, int64_t& tb, int64_t& tt,
                                          int64_t& el) {
   const int64_t RT = cdiv(g.rows, kBM), KB = cdiv(g.kk, kBK), CT = cdiv(g.K, kBN);
-  ta = RT * KB;
+  ta = g.a_kt > 0 ? 0 : RT * KB;  // a segment reading a shared A image writes none
   tb = CT * KB;
   tt = (g.rows > 0 && g.K > 0) ? RT * CT : 0;
   el = ta * S * kATile + tb * S * kBTile;
 }
 
 // Work-list offsets and digit-image offsets of the first cnt segments of a list
-// (one block), the terminator at [cnt]; images beyond cap are refused.
-__device__ void finish_list(GemmSeg* L, int64_t cnt, int S, int64_t cap, int* status,
-                            unsigned long long* flops, int64_t (&sc)[4][32]) {
+// (one block), the terminator at [cnt]; the list's own images start at element
+// `base` (a segment reading a shared A image keeps the a_img it was given); images
+// beyond cap are refused.  Returns the end of the list's images (every thread).
+__device__ int64_t finish_list(GemmSeg* L, int64_t cnt, int S, int64_t base, int64_t cap, int* status,
+                               unsigned long long* flops, int64_t (&sc)[4][32]) {
+  __shared__ int64_t s_end;
   const int64_t per = (cnt + blockDim.x - 1) / blockDim.x;
   const int64_t a = min(cnt, (int64_t)threadIdx.x * per), b = min(cnt, a + per);
   int64_t v[4] = {0, 0, 0, 0};
@@ -77,8 +82,8 @@ __device__ void finish_list(GemmSeg* L, int64_t cnt, int S, int64_t cap, int* st
     L[i].it_a = v[0];
     L[i].it_b = v[1];
     L[i].it_t = v[2];
-    L[i].a_img = v[3];
-    L[i].b_img = v[3] + ta * S * kATile;
+    if (L[i].a_kt == 0) L[i].a_img = base + v[3];
+    L[i].b_img = base + v[3] + ta * S * kATile;
     v[0] += ta; v[1] += tb; v[2] += tt; v[3] += el;
   }
   if (threadIdx.x == blockDim.x - 1) {
@@ -87,14 +92,16 @@ __device__ void finish_list(GemmSeg* L, int64_t cnt, int S, int64_t cap, int* st
     t.it_a = v[0];
     t.it_b = v[1];
     t.it_t = v[2];
-    t.a_img = v[3];
-    if (v[3] > cap) {  // cannot happen with the host's bound; never write past the images
+    t.a_img = base + v[3];
+    if (base + v[3] > cap) {  // cannot happen with the host's bound; never write past the images
       t.it_a = t.it_b = t.it_t = 0;
       set_status(status, TDC_EUNSUPPORTED);
     }
     L[cnt] = t;
+    s_end = base + v[3];
   }
   __syncthreads();
+  return s_end;
 }
 }  // namespace
 
@@ -113,55 +120,55 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
   const int64_t per = (nit + blockDim.x - 1) / blockDim.x;
   const int64_t a0 = min(nit, (int64_t)threadIdx.x * per), a1 = min(nit, a0 + per);
   int64_t* item = A.item;
-  // pass 0: the W columns of each column tile's far tiles (kr); the columns that do
-  // not fit the W buffer (in item order) become dense fallback tiles, added in FP64
-  // afterwards, so the buffer bounds the work whatever the ranks
-  {
-    int64_t c0[4] = {0, 0, 0, 0};
-    for (int64_t it = a0; it < a1; ++it) {
-      const int s = (int)(it / Tm), t = (int)(it % Tm);
-      const GemmSeg& sg = A.ssegs[s];
-      const int T = (sg.near_m > 0 && sg.K > 0 && sg.rows > 0) ? (int)cdiv(sg.K, m) : 0;
-      int64_t kr = 0;
-      for (int I = 0; t < T && I < T; ++I) {
-        if (iabs(I - t) < 2) continue;
-        const int r = S.srank[((int64_t)s * Tm + I) * Tm + t];
-        if (r > 0) kr += r;
-      }
-      item[kItKr * nit + it] = kr;
-      c0[0] += kr;
+  // pass 0: which parts this path takes.  A part is taken when none of its far tiles
+  // passed the rank cap and its W columns (the sum of its far tiles' ranks) fit the W
+  // buffer, parts in order; every other part is left to the plain split path, so no
+  // tile needs a dense fallback here.
+  for (int64_t it = a0; it < a1; ++it) {
+    const int s = (int)(it / Tm), t = (int)(it % Tm);
+    const GemmSeg& sg = A.ssegs[s];
+    const int T = (sg.near_m > 0 && sg.K > 0 && sg.rows > 0) ? (int)cdiv(sg.K, m) : 0;
+    int64_t kr = 0;
+    bool dense = false;
+    for (int I = 0; t < T && I < T; ++I) {
+      if (iabs(I - t) < 2) continue;
+      const int r = S.srank[((int64_t)s * Tm + I) * Tm + t];
+      if (r > 0) kr += r;
+      if (r < 0) dense = true;
     }
-    int64_t cs[4] = {c0[0], 0, 0, 0};
-    block_excl_scan4(cs, sc);
-    int64_t run = cs[0];
-    unsigned long long moved = 0;
-    for (int64_t it = a0; it < a1; ++it) {
-      const int64_t kr = item[kItKr * nit + it];
-      if (kr > 0 && run + kr > A.wcap) {
-        const int s = (int)(it / Tm), t = (int)(it % Tm);
-        const int T = (int)cdiv(A.ssegs[s].K, m);
-        for (int I = 0; I < T; ++I) {
-          if (iabs(I - t) < 2) continue;
-          const int64_t slot = ((int64_t)s * Tm + I) * Tm + t;
-          if (S.srank[slot] > 0) {
-            S.srank[slot] = -1;
-            ++moved;
-          }
-        }
-      } else {
-        run += kr;
-      }
-    }
-    if (moved && S.ranks) atomicAdd(&S.ranks[2], moved);
-    __syncthreads();
+    item[kItKr * nit + it] = dense ? -1 : kr;
   }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t run = 0;
+    unsigned long long taken = 0, left = 0;
+    for (int s = 0; s < A.nseg; ++s) {
+      const GemmSeg& sg = A.ssegs[s];
+      const bool on = sg.near_m > 0 && sg.K > 0 && sg.rows > 0;
+      int64_t tot = 0;
+      bool ok = on;
+      for (int t = 0; on && t < Tm; ++t) {
+        const int64_t kr = item[kItKr * nit + (int64_t)s * Tm + t];
+        if (kr < 0) ok = false; else tot += kr;
+      }
+      ok = ok && run + tot <= A.wcap;
+      if (ok) run += tot;
+      A.accept[s] = ok ? 1 : 0;
+      if (on) { if (ok) ++taken; else ++left; }
+    }
+    if (A.parts) {
+      atomicAdd(&A.parts[0], taken);
+      atomicAdd(&A.parts[1], left);
+    }
+  }
+  __syncthreads();
   // pass 1: per item, the W columns of J's far tiles (kr), R_J's size, and the
   // W-product columns of row tile I (kw); relative W column of each far slot
   int64_t v[4] = {0, 0, 0, 0}, w[4] = {0, 0, 0, 0};
   for (int64_t it = a0; it < a1; ++it) {
     const int s = (int)(it / Tm), t = (int)(it % Tm);
     const GemmSeg& sg = A.ssegs[s];
-    const bool on = sg.near_m > 0 && sg.K > 0 && sg.rows > 0;
+    const bool on = sg.near_m > 0 && sg.K > 0 && sg.rows > 0 && A.accept[s];
     const int T = on ? (int)cdiv(sg.K, m) : 0;
     int64_t kr = 0, kw = 0, mc = 0;
     if (t < T) {
@@ -214,7 +221,7 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
   for (int64_t it = a0; it < a1; ++it) {
     const int s = (int)(it / Tm), t = (int)(it % Tm);
     const GemmSeg& sg = A.ssegs[s];
-    const bool on = sg.near_m > 0 && sg.K > 0 && sg.rows > 0;
+    const bool on = sg.near_m > 0 && sg.K > 0 && sg.rows > 0 && A.accept[s];
     const int T = on ? (int)cdiv(sg.K, m) : 0;
     const int64_t kr = item[kItKr * nit + it], kw = item[kItKw * nit + it];
     item[kItWbase * nit + it] = wb;
@@ -227,13 +234,19 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
         const int64_t slot = ((int64_t)s * Tm + I) * Tm + t;
         if (S.srank[slot] > 0) A.wcol0[slot] += (int32_t)wb;
       }
-      // near product: poles of tiles t-1..t+1 (a contiguous range of the list)
+      // near product: poles of tiles t-1..t+1 (a contiguous range of the list), read
+      // from the part's A image from the k-tile holding the first of them
       const int plo = t >= 1 ? (t - 1) * m : 0, phi = min(sg.K, (t + 2) * m);
       const int qa = lower_bound_i(sg.plist, sg.kk, plo), qb = lower_bound_i(sg.plist, sg.kk, phi);
+      const int q0 = qa & ~(kBK - 1);
       GemmSeg g = sg;
       g.near_m = 0;
-      g.plist = sg.plist + qa;
-      g.kk = qb - qa;
+      g.plist = sg.plist + q0;
+      g.kk = qb - q0;
+      g.bq0 = qa - q0;
+      g.a_kt = (int32_t)cdiv(sg.kk, kBK);
+      g.a_img = (int64_t)(q0 / kBK) * A.digits * kATile;  // + the part image's offset (pass 4)
+      g.part = s;
       g.K = mc;
       g.org = sg.org + j0;
       g.tau = sg.tau + j0;
@@ -289,10 +302,15 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
       }
     }
     const int qa = lower_bound_i(sg.plist, sg.kk, t * m), qb = lower_bound_i(sg.plist, sg.kk, (t + 1) * m);
+    const int q0 = qa & ~(kBK - 1);
     GemmSeg g = sg;
     g.near_m = 0;
-    g.plist = sg.plist + qa;
-    g.kk = qb - qa;
+    g.plist = sg.plist + q0;
+    g.kk = qb - q0;
+    g.bq0 = qa - q0;
+    g.a_kt = (int32_t)cdiv(sg.kk, kBK);
+    g.a_img = (int64_t)(q0 / kBK) * A.digits * kATile;  // + the part image's offset (pass 4)
+    g.part = s;
     g.K = (int32_t)kw;
     g.bcol = A.bcol + b0;
     g.C = A.W;
@@ -303,15 +321,43 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
     g.acc = 0;
     A.w_segs[wi++] = g;
   }
+  // pass 4: one A image per part (written once, read by its near and W segments),
+  // then the lists' own images after the shared ones; the apply products come last
+  // and reuse the whole buffer
+  for (int s = threadIdx.x; s < A.nseg; s += blockDim.x) {
+    const GemmSeg& sg = A.ssegs[s];
+    GemmSeg g;
+    memset(&g, 0, sizeof(g));
+    if (sg.near_m > 0 && sg.K > 0 && sg.rows > 0 && A.accept[s]) {
+      g = sg;
+      g.near_m = 0;
+      g.K = 0;  // digits only
+      g.Bd = nullptr;
+      g.cexp = nullptr;
+      g.bcol = nullptr;
+      g.acc = 0;
+      g.bq0 = 0;
+      g.a_kt = 0;
+    }
+    A.img_segs[s] = g;
+  }
+  __syncthreads();
+  const int64_t shared_end = finish_list(A.img_segs, A.nseg, A.digits, 0, A.img_cap, A.status, nullptr, sc);
+  for (int which = 0; which < 2; ++which) {  // add each part's image offset
+    GemmSeg* L = which == 0 ? A.near_segs : A.w_segs;
+    const int64_t cnt = which == 0 ? tot[3] : tot[5];
+    for (int64_t i = threadIdx.x; i < cnt; i += blockDim.x) L[i].a_img += A.img_segs[L[i].part].a_img;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     A.counts[0] = tot[3];
     A.counts[1] = tot[5];
     A.counts[2] = tot[4];
+    A.counts[3] = A.nseg;
   }
-  finish_list(A.near_segs, tot[3], A.digits, A.img_cap, A.status, A.flops, sc);
-  finish_list(A.w_segs, tot[5], A.digits, A.img_cap, A.status, A.flops, sc);
-  finish_list(A.ap_segs, tot[4], A.digits, A.img_cap, A.status, A.flops, sc);
+  finish_list(A.near_segs, tot[3], A.digits, shared_end, A.img_cap, A.status, A.flops, sc);
+  finish_list(A.w_segs, tot[5], A.digits, shared_end, A.img_cap, A.status, A.flops, sc);
+  finish_list(A.ap_segs, tot[4], A.digits, 0, A.img_cap, A.status, A.flops, sc);
 }
 
 // ---------------------------------------------------------------------------
@@ -360,6 +406,17 @@ __global__ void __launch_bounds__(128) k_ss_rmat(SSArgs A) {
     }
   }
   A.cexp[it * m + c] = mx > 1.0 ? ilogb(mx) + 1 : 0;
+}
+
+// The stand-alone product's plain split segment runs only if the structured path
+// left its part: otherwise its work lists are emptied.
+__global__ void k_ss_gate(const int32_t* accept, GemmSeg* plain_list) {
+  if (threadIdx.x == 0 && accept[0]) plain_list[1].it_a = plain_list[1].it_b = plain_list[1].it_t = 0;
+}
+
+cudaError_t launch_ss_gate(const int32_t* accept, GemmSeg* plain_list, cudaStream_t s) {
+  k_ss_gate<<<1, 32, 0, s>>>(accept, plain_list);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_ss_build(const SSArgs& A, cudaStream_t s) {

@@ -75,6 +75,8 @@ class Stats(ctypes.Structure):
         ("lr_rank_sum", ctypes.c_int64),
         ("lr_dense_fallbacks", ctypes.c_int64),
         ("lr_rank_max", ctypes.c_int64),
+        ("lr_parts_structured", ctypes.c_int64),
+        ("lr_parts_split", ctypes.c_int64),
     ]
 
     def as_dict(self):
@@ -103,6 +105,8 @@ class Stats(ctypes.Structure):
             "lr_rank_sum": self.lr_rank_sum,
             "lr_dense_fallbacks": self.lr_dense_fallbacks,
             "lr_rank_max": self.lr_rank_max,
+            "lr_parts_structured": self.lr_parts_structured,
+            "lr_parts_split": self.lr_parts_split,
         }
 
 

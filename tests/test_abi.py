@@ -40,7 +40,8 @@ def test_default_opts_and_workspace(lib):
     assert tdc.workspace_size(0, o) > 0
     # the structured merge on the split path needs its own scratch on top of the split path's
     w4 = tdc.workspace_size(16384, tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_STRUCTURED_SPLIT))
-    assert w4 > tdc.workspace_size(16384, tdc.default_opts(leaf=64))
+    assert w4 > tdc.workspace_size(16384, tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_SPLIT))
+    assert w4 == tdc.workspace_size(16384, tdc.default_opts(leaf=64))  # the library's default merge
     assert tdc.cauchy_gemm_workspace_size(300, 1000, tdc.MERGE_STRUCTURED_SPLIT,
                                           tdc.default_opts(lr_tile=128)) > 300 * 1000 * 2
     # the chunk length of the split accumulators' drains changes no workspace

@@ -1,6 +1,7 @@
 """Accuracy on matrices whose eigenvectors are smooth and deflate little: the
 spherical-harmonic matrix of Example 3 at n = 16384 and the Hermite matrix of
-Example 2 at n = 8192 (leaf 64).
+Example 2 at n = 8192 (leaf 64), with the library's default merge (the structured
+products on the split path for the large merges) and with the plain split product.
 
 On such matrices the rows next to each split are nearly parallel to z, so the
 split product's level-3 sums are secular-equation sums whose terms share their
@@ -69,9 +70,12 @@ def test_sht_16384_fp64_merge(tdc):
     assert res <= 50 and orth <= 50, (res, orth)
 
 
-def test_sht_16384_split_path_default_schedule(tdc):
+@pytest.mark.parametrize("mode", ["auto", "split"])
+def test_sht_16384_split_path_default_schedule(tdc, mode):
+    """The library's default merge (the structured products on the split path for the
+    large merges) and the plain split product, both with the default drains."""
     d, e = inputs.sht_tridiag(N)
-    dt, et, lam, Q, st, stats = solve(tdc, tdc.MERGE_AUTO, d, e)
+    dt, et, lam, Q, st, stats = solve(tdc, tdc.MERGE_AUTO if mode == "auto" else tdc.MERGE_SPLIT, d, e)
     assert st == 0, tdc.strerror(st)
     # every drained level sum stayed below half of the exact FP32 range
     assert 0 < stats["split_level_max"] < 0.5, stats["split_level_max"]
@@ -80,10 +84,11 @@ def test_sht_16384_split_path_default_schedule(tdc):
 
 
 def test_sht_16384_per_tile_schedule_raises_the_precision_warning(tdc):
-    """Summed over whole tiles the level sums pass 2^24 on this matrix: the guard must
-    report it (the warning is the only sign of the inexact product)."""
+    """Summed over whole tiles of the plain split product the level sums pass 2^24 on this
+    matrix: the guard must report it (the warning is the only sign of the inexact
+    product)."""
     d, e = inputs.sht_tridiag(N)
-    _, _, _, _, st, stats = solve(tdc, tdc.MERGE_AUTO, d, e, split_chunk_k=0)
+    _, _, _, _, st, stats = solve(tdc, tdc.MERGE_SPLIT, d, e, split_chunk_k=0)
     assert st == tdc.TDC_WPRECISION, st
     assert stats["split_level_max"] >= 0.5
 

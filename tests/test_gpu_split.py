@@ -162,7 +162,7 @@ def test_bounded_waits_expire_report_a_timeout_and_leave_the_device_usable(tdc, 
     # the eigensolver's split merges report it the same way
     d, e = inputs.toeplitz_tridiag(8192)
     dt, et = torch.tensor(d, device=DEV), torch.tensor(e, device=DEV)
-    oe = tdc.default_opts(leaf=64, spin_budget=1)
+    oe = tdc.default_opts(leaf=64, merge_mode=tdc.MERGE_SPLIT, spin_budget=1)
     wse = tdc.workspace(tdc.workspace_size(8192, oe), DEV)
     tdc.eig(dt, et, oe, ws=wse)
     assert tdc.sync_status() == tdc.TDC_ETIMEOUT

@@ -126,9 +126,9 @@ def test_cauchy_structured_split_vs_oracle(tdc, orc, m, K, tile):
 @pytest.mark.parametrize("tile", [64, 128])
 def test_cauchy_structured_split_dense_fallbacks(tdc, orc, tile):
     """lr_tol = 1e-300 keeps every far tile at full rank: with 128-wide tiles SRRSC passes
-    the rank cap (64) and the tiles stay dense (added in FP64); with 64-wide tiles every
-    tile keeps rank 64, beyond the W buffer's budget, and the tiles that do not fit stay
-    dense.  Either way the product equals the oracle's."""
+    the rank cap (64); with 64-wide tiles every tile keeps rank 64, more low-rank columns
+    than the W buffer's budget.  Either way the structured path leaves the part to the
+    plain split product, and the product equals the oracle's."""
     m, K = 200, 1500
     D, org, tau, zh, s = generators(orc, K, 61)
     g = inputs.SplitMix64(62)
@@ -154,7 +154,7 @@ def test_eig_structured_split_merge_vs_oracle(tdc, orc, n, leaf, fam):
     assert res <= 50 and orth <= 50, (res, orth)
     compare_vectors(Q, Q_o, lam_o, 1e-8 * nT, 1e-7)
     if st["sum_K"][0] >= 256 + 2 * 128:  # a top merge with far tiles took the structured path
-        assert st["lr_tiles"] > 0 and st["split_flops"] > 0
+        assert st["lr_tiles"] > 0 and st["split_flops"] > 0 and st["lr_parts_structured"] > 0
 
 
 def test_c2_toeplitz_16384_structured_split_default_tiles(tdc):
@@ -166,5 +166,6 @@ def test_c2_toeplitz_16384_structured_split_default_tiles(tdc):
     lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), o, check=True)
     st = tdc.get_stats()
     assert st["lr_tiles"] >= 2 * (32 * 32 - 94) and st["lr_dense_fallbacks"] == 0
+    assert st["lr_parts_split"] == 0 and st["lr_parts_structured"] >= 2
     assert 0 < st["split_level_max"] < 0.5
     check_toeplitz_sampled(lam, Q, n)
