@@ -534,8 +534,9 @@ def config_c5(args, steps=5, warmup=3):
 
 # DRAM bytes of k_gemm_split over one eigensolve, summed over its launches, from
 # single-pass ncu captures of the kernel as it stands; keyed by the exact
-# configuration (workload, leaf, split_min_K, split_chunk_k), null for any other
-TRAFFIC = {}
+# configuration (workload, merge, leaf, split_min_K, split_chunk_k, lr_tile), null for
+# any other
+TRAFFIC = {("toeplitz16384", "auto", 64, 128, 256, 256): 23.01e9}
 
 
 def run_ours(args):
@@ -628,7 +629,8 @@ def run_ours(args):
         roof = split_roofline(stats, split_ms, S, pk, pk_kind,
                               ": the kernel runs in bursts of tens of ms and the SM clock stays at its maximum "
                               "(see clocks)")
-        roof["traffic"] = TRAFFIC.get((args.workload, opts.leaf, opts.split_min_K, opts.split_chunk_k))
+        roof["traffic"] = TRAFFIC.get((args.workload, args.merge, opts.leaf, opts.split_min_K, opts.split_chunk_k,
+                                       opts.lr_tile))
         roof["traffic_scope"] = "DRAM bytes of all k_gemm_split launches of one eigensolve (ncu)"
         roof["algorithmic_bytes"] = stats.get("split_bytes")
         roof["frac_of_sustained"] = roof["achieved"] / pk["bf16_tflops_sustained"]

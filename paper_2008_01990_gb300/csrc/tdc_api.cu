@@ -618,6 +618,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
       A.img_cap = P.img_cap;
       A.status = P.status;
       A.flops = P.stats ? &P.stats->split_flops : nullptr;
+      A.bytes = P.stats ? &P.stats->split_bytes : nullptr;
       A.parts = P.stats ? P.stats->ss_parts : nullptr;
       P.ss_accept = A.accept;  // the plain split path below takes the parts this one leaves
       err = launch_struct_segs(P, LL, sg);

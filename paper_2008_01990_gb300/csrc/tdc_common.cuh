@@ -235,6 +235,7 @@ struct SSArgs {
   int64_t img_cap;       // digit-image capacity (elements) of each of the three products
   int* status;
   unsigned long long* flops;  // statistics: executed flops of the three products (NULL when off)
+  unsigned long long* bytes;  // statistics: their algorithmic HBM bytes (NULL when off)
   unsigned long long* parts;  // statistics: parts taken, parts left (NULL when off)
 };
 

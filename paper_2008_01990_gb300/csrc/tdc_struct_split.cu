@@ -62,19 +62,25 @@ __device__ __forceinline__ void seg_work(const GemmSeg& g, int S, int64_t& ta, i
 // `base` (a segment reading a shared A image keeps the a_img it was given); images
 // beyond cap are refused.  Returns the end of the list's images (every thread).
 __device__ int64_t finish_list(GemmSeg* L, int64_t cnt, int S, int64_t base, int64_t cap, int* status,
-                               unsigned long long* flops, int64_t (&sc)[4][32]) {
+                               unsigned long long* flops, unsigned long long* bytes, int64_t (&sc)[4][32]) {
   __shared__ int64_t s_end;
   const int64_t per = (cnt + blockDim.x - 1) / blockDim.x;
   const int64_t a = min(cnt, (int64_t)threadIdx.x * per), b = min(cnt, a + per);
   int64_t v[4] = {0, 0, 0, 0};
-  unsigned long long fl = 0;
+  unsigned long long fl = 0, by = 0;
   for (int64_t i = a; i < b; ++i) {
     int64_t ta, tb, tt, el;
     seg_work(L[i], S, ta, tb, tt, el);
     v[0] += ta; v[1] += tb; v[2] += tt; v[3] += el;
-    fl += 2ull * (unsigned long long)L[i].rows * (unsigned long long)L[i].kk * (unsigned long long)L[i].K;
+    const unsigned long long r = (unsigned long long)L[i].rows, kq = (unsigned long long)L[i].kk,
+                             kc = (unsigned long long)L[i].K;
+    fl += 2ull * r * kq * kc;
+    // algorithmic bytes: the A digits once (shared images count for their owner), the
+    // B digits once, the FP64 result written (read as well when added)
+    by += 2ull * S * ((L[i].a_kt > 0 ? 0ull : r * kq) + kq * kc) + (L[i].acc ? 16ull : 8ull) * r * kc;
   }
   if (flops && fl) atomicAdd(flops, fl);
+  if (bytes && by) atomicAdd(bytes, by);
   block_excl_scan4(v, sc);
   for (int64_t i = a; i < b; ++i) {
     int64_t ta, tb, tt, el;
@@ -342,7 +348,8 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
     A.img_segs[s] = g;
   }
   __syncthreads();
-  const int64_t shared_end = finish_list(A.img_segs, A.nseg, A.digits, 0, A.img_cap, A.status, nullptr, sc);
+  const int64_t shared_end =
+      finish_list(A.img_segs, A.nseg, A.digits, 0, A.img_cap, A.status, nullptr, A.bytes, sc);
   for (int which = 0; which < 2; ++which) {  // add each part's image offset
     GemmSeg* L = which == 0 ? A.near_segs : A.w_segs;
     const int64_t cnt = which == 0 ? tot[3] : tot[5];
@@ -355,9 +362,9 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
     A.counts[2] = tot[4];
     A.counts[3] = A.nseg;
   }
-  finish_list(A.near_segs, tot[3], A.digits, shared_end, A.img_cap, A.status, A.flops, sc);
-  finish_list(A.w_segs, tot[5], A.digits, shared_end, A.img_cap, A.status, A.flops, sc);
-  finish_list(A.ap_segs, tot[4], A.digits, 0, A.img_cap, A.status, A.flops, sc);
+  finish_list(A.near_segs, tot[3], A.digits, shared_end, A.img_cap, A.status, A.flops, A.bytes, sc);
+  finish_list(A.w_segs, tot[5], A.digits, shared_end, A.img_cap, A.status, A.flops, A.bytes, sc);
+  finish_list(A.ap_segs, tot[4], A.digits, 0, A.img_cap, A.status, A.flops, A.bytes, sc);
 }
 
 // ---------------------------------------------------------------------------
