@@ -296,6 +296,42 @@ def run_qhat(args):
     return 0
 
 
+def run_example1(args, n):
+    """Example 1 of the paper: C = A B with A random (uniform(-1,1)) and the Cauchy-like
+    B_ij = u_i v_j / (d_i - w_j), d_i = 8 i / n, w_j = d_j + 4 / n, u, v uniform(0,1):
+    every product mode timed (CUDA events, after a warm-up), with its error against the
+    FP64 dense product on sampled columns."""
+    import torch
+    from paper_2008_01990_gb300 import inputs, tdc
+    dev = torch.device("cuda", 0)
+    d_np, w_np, u_np, v_np = inputs.example1_cauchy(n)
+    d, w, u, v = (torch.tensor(x, device=dev) for x in (d_np, w_np, u_np, v_np))
+    g = torch.Generator(device=dev)
+    g.manual_seed(n)
+    A = (torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1).t()
+    cols = torch.tensor(np.sort(np.random.default_rng(0).choice(n, 64, replace=False)), device=dev)
+    Bs = (u[:, None] * v[cols][None, :]) / (d[:, None] - w[cols][None, :])
+    Cref = A @ Bs  # FP64 reference on the sampled columns (a library matmul, verification only)
+    scale = torch.linalg.norm(A, dim=1)[:, None] * torch.linalg.norm(Bs, dim=0)[None, :]
+    out = {"workload": "example1 n=%d: C = A B, B_ij = u_i v_j / (d_i - w_j)" % n, "modes": {}}
+    opts = tdc.default_opts()
+    for name, md in (("dense", tdc.MERGE_DENSE), ("structured", tdc.MERGE_STRUCTURED), ("split", tdc.MERGE_SPLIT),
+                     ("structured_split", tdc.MERGE_STRUCTURED_SPLIT)):
+        if name in ("dense", "structured") and n > 16384:
+            continue  # the FP64 products at n = 32768 take tens of seconds each
+        C = tdc.cauchy_like_gemm(A, d, w, u, v, md, opts, check=True)
+        steps = 1 if name in ("dense", "structured") else max(1, min(args.steps, 5))
+        ms = _event_ms(lambda: tdc.cauchy_like_gemm(A, d, w, u, v, md, opts), steps)
+        err = float(torch.max(torch.abs(C[:, cols] - Cref) / scale).item())
+        out["modes"][name] = {"ms": ms, "steps": steps, "max_err_over_rownorm_colnorm": err,
+                              "fp64_equivalent_tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+        del C
+        progress("example1 %d %s done" % (n, name))
+    R = tdc.cauchy_like_ranks(d, w, u, v, tdc.default_opts(lr_tile=4096, lr_tol=1e-15)).cpu().numpy()
+    out["ranks_4096_tiles_first_block_column"] = [int(x) for x in R[1:, 0]]
+    return out
+
+
 def _event_ms(fn, steps, stream=None):
     """Average device time of fn over `steps` calls, CUDA events on `stream`."""
     import torch
@@ -841,6 +877,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
+                                                          "example1_8192", "example1_16384", "example1_32768",
                                                           "batched4096", "backward256", "clement30000",
                                                           "hermite30000", "sht30000"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split", "structured_split"])
@@ -860,6 +897,9 @@ def main():
         return run_reference(args)
     if args.workload == "qhat8192":
         return run_qhat(args)
+    if args.workload.startswith("example1_"):
+        print(json.dumps(run_example1(args, int(args.workload.split("_")[1]))), flush=True)
+        return 0
     if args.workload == "batched4096":
         print(json.dumps(config_c3(args, steps=args.steps, warmup=args.warmup)), flush=True)
         return 0

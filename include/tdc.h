@@ -249,6 +249,36 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
                     const double* tau, const double* zhat, const double* s, double* C, int64_t ldc, int32_t mode,
                     const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream);
 
+/* General Cauchy-like product (Section 4, Example 1): C = A * B for the n x n matrix
+ *   B_ij = u_i v_j / (d_i - w_j)
+ * given by its generators (device FP64): row nodes d[n] and column nodes w[n], both
+ * ascending, with d_i != w_j, and vectors u[n], v[n].  A is m x n (lda), C is m x n
+ * (ldc).  B is brought to the form of a merge's Qhat (each column node as the nearest
+ * row node plus an offset), so every mode of tdc_cauchy_gemm applies: TDC_MERGE_DENSE
+ * (FP64), TDC_MERGE_STRUCTURED (SRRSC low-rank far tiles, FP64), TDC_MERGE_SPLIT (BF16
+ * digit products on the tensor cores) and TDC_MERGE_STRUCTURED_SPLIT (the structured
+ * products on the split path).  The structured modes assume the row and column nodes
+ * interlace (tiles far apart in index are far apart in value), as in Example 1.  For
+ * the split modes A and the columns of B are scaled by powers of two (exactly) so that
+ * every operand entry is at most 1, and the product is scaled back.
+ * ws of tdc_cauchy_like_gemm_workspace_size(m, n, mode, o) bytes.
+ * Errors: -1 m, -2 n, -3 A, -4 lda, -5..-8 d, w, u, v, -9 C, -10 ldc, -11 mode,
+ * -12 options, TDC_ENOWS, TDC_ECUDA. */
+int tdc_cauchy_like_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes);
+int tdc_cauchy_like_gemm(int64_t m, int64_t n, const double* A, int64_t lda, const double* d, const double* w,
+                         const double* u, const double* v, double* C, int64_t ldc, int32_t mode, const tdc_opts* o,
+                         void* ws, size_t ws_bytes, tdc_stream_t stream);
+
+/* Rank profile of a Cauchy-like operand (the ranks of Table 2): B of
+ * tdc_cauchy_like_gemm cut into o->lr_tile square tiles (T = ceil(n / lr_tile) per
+ * dimension); ranks[I * T + J] (device int32, T x T) receives the SRRSC rank at
+ * tolerance o->lr_tol of every tile off the diagonal (I != J), -1 when it exceeds the
+ * rank cap (64), and 0 on the diagonal.  ws of tdc_cauchy_like_ranks_workspace_size
+ * bytes. */
+int tdc_cauchy_like_ranks_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
+int tdc_cauchy_like_ranks(int64_t n, const double* d, const double* w, const double* u, const double* v,
+                          const tdc_opts* o, int32_t* ranks, void* ws, size_t ws_bytes, tdc_stream_t stream);
+
 /* Synchronise `stream` and return the device status of the last call enqueued on it
  * (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE, TDC_EUNSUPPORTED, or the warning
  * TDC_WPRECISION), then clear it.  Each stream that calls the library gets its own

@@ -434,7 +434,7 @@ static int validate_opts(const tdc_opts* o) {
   if (o->leaf < 2 || o->leaf > 64) return 1;  // leaf >= 2 keeps every tree node non-empty
   if (o->merge_mode < 0 || o->merge_mode > 4) return 1;
   if (o->max_iter < 1) return 1;
-  if (o->lr_tile < 64 || (o->lr_tile % 64) != 0) return 1;
+  if (o->lr_tile < 64 || o->lr_tile > 4096 || (o->lr_tile % 64) != 0) return 1;
   if (o->split_slices < 3 || o->split_slices > 7) return 1;
   if (o->split_min_K < 1) return 1;
   if (o->split_chunk_k < 0 || (o->split_chunk_k % 16) != 0) return 1;
@@ -964,41 +964,24 @@ int tdc_cauchy_gemm_workspace_size(int64_t m, int64_t K, int32_t mode, const tdc
   return TDC_OK;
 }
 
-int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const double* D, const int32_t* org,
-                    const double* tau, const double* zhat, const double* s, double* C, int64_t ldc, int32_t mode,
-                    const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream) {
-  tdc_opts op;
-  tdc_default_opts(&op);
-  if (o) op = *o;
-  if (m < 0 || m > 0x7fffffff) return -1;
-  if (K < 0 || K > 0x7fffffff) return -2;
-  if (m == 0 || K == 0) return TDC_OK;
-  if (!A) return -3;
-  if (lda < m) return -4;
-  if (!D) return -5;
-  if (!org) return -6;
-  if (!tau) return -7;
-  if (!zhat) return -8;
-  if (!s) return -9;
-  if (!C) return -10;
-  if (ldc < m) return -11;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED &&
-      mode != TDC_MERGE_STRUCTURED_SPLIT)
-    return -12;
-  if (validate_opts(&op)) return -13;
-  size_t need = 0;
-  tdc_cauchy_gemm_workspace_size(m, K, mode, &op, &need);
-  if (!ws || ws_bytes < need) return TDC_ENOWS;
-  char* wbase = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  cudaStream_t cs = (cudaStream_t)stream;
-  int* st = begin_status(cs);
-  if (!st) return TDC_ECUDA;
+}  // extern "C"
+
+// C = A * B for B the K x K Cauchy-like operand given by (D, org, tau, zhat, s) in one
+// of the product modes (the body of tdc_cauchy_gemm and tdc_cauchy_like_gemm).  With
+// cexp / eA (device, split modes of general operands) A enters as A 2^-eA and column j
+// of the product is scaled back by 2^cexp[j].
+static int cauchy_product(int64_t m, int64_t K, const double* A, int64_t lda, const double* D, const int32_t* org,
+                          const double* tau, const double* zhat, const double* s, double* C, int64_t ldc,
+                          int32_t mode, const tdc_opts& op, char* wbase, int* st, const int32_t* cexp,
+                          const int32_t* eA, cudaStream_t cs) {
   GemmSeg sg;
   memset(&sg, 0, sizeof(sg));
   sg.ars = 1;
   sg.A = A; sg.lda = lda; sg.rows = (int32_t)m; sg.kk = (int32_t)K; sg.K = (int32_t)K;
   sg.D = D; sg.org = org; sg.tau = tau; sg.zhat = zhat; sg.scol = s;
   sg.C = C; sg.ldc = ldc;
+  const bool scaled = eA != nullptr && (mode == TDC_MERGE_SPLIT || mode == TDC_MERGE_STRUCTURED_SPLIT);
+  if (scaled) sg.cexp = cexp;
   cudaError_t err;
   if (mode == TDC_MERGE_DENSE) {
     err = launch_seg_dense(sg, cs);
@@ -1057,6 +1040,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
       k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
       err = cudaGetLastError();
     }
+    if (err == cudaSuccess && scaled) err = launch_cauchy_like_patch(segs, eA, cs);
     if (err == cudaSuccess) err = launch_srrsc(segs, 1, SA, cs);
     if (err == cudaSuccess) err = launch_ss_build(A, cs);
     GemmSeg* lists[4] = {A.img_segs, A.near_segs, A.w_segs, A.ap_segs};
@@ -1083,6 +1067,7 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
       pl.a_img = tot;
       k_write_segs<<<1, 32, 0, cs>>>(ps, pl, plain);
       err = cudaGetLastError();
+      if (err == cudaSuccess && scaled) err = launch_cauchy_like_patch(plain, eA, cs);
       if (err == cudaSuccess) err = launch_ss_gate(A.accept, plain, cs);
       if (err == cudaSuccess)
         err = launch_seg_split(plain, 1, op.split_slices, st, op.spin_budget, img, op.split_chunk_k / 16, cs);
@@ -1130,9 +1115,186 @@ int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const do
     last.a_img = tot;
     k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
     err = cudaGetLastError();
+    if (err == cudaSuccess && scaled) err = launch_cauchy_like_patch(segs, eA, cs);
     if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, op.split_chunk_k / 16, cs);
   }
   return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+extern "C" {
+
+int tdc_cauchy_gemm(int64_t m, int64_t K, const double* A, int64_t lda, const double* D, const int32_t* org,
+                    const double* tau, const double* zhat, const double* s, double* C, int64_t ldc, int32_t mode,
+                    const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0 || m > 0x7fffffff) return -1;
+  if (K < 0 || K > 0x7fffffff) return -2;
+  if (m == 0 || K == 0) return TDC_OK;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (!D) return -5;
+  if (!org) return -6;
+  if (!tau) return -7;
+  if (!zhat) return -8;
+  if (!s) return -9;
+  if (!C) return -10;
+  if (ldc < m) return -11;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED &&
+      mode != TDC_MERGE_STRUCTURED_SPLIT)
+    return -12;
+  if (validate_opts(&op)) return -13;
+  size_t need = 0;
+  tdc_cauchy_gemm_workspace_size(m, K, mode, &op, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  char* wbase = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  return cauchy_product(m, K, A, lda, D, org, tau, zhat, s, C, ldc, mode, op, wbase, st, nullptr, nullptr, cs);
+}
+
+// the general Cauchy-like product: the generator arrays and scales after the product's
+// own workspace
+static size_t cauchy_like_extra(int64_t n) {
+  return align_up(sizeof(int32_t) * n) + align_up(sizeof(double) * n) + align_up(sizeof(double) * n) +
+         2 * align_up(sizeof(int32_t) * n) + 256;
+}
+
+int tdc_cauchy_like_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes) {
+  if (!bytes) return -5;
+  size_t b = 0;
+  const int st = tdc_cauchy_gemm_workspace_size(m, n, mode, o, &b);
+  if (st != TDC_OK) return st;
+  *bytes = b + cauchy_like_extra(std::max<int64_t>(n, 0));
+  return TDC_OK;
+}
+
+int tdc_cauchy_like_ranks_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (validate_opts(&op)) return -2;
+  if (!bytes) return -3;
+  const int64_t mm = op.lr_tile, T = std::max<int64_t>(1, (n + mm - 1) / mm), ns = T * T;
+  *bytes = 256 + align_up(2 * sizeof(GemmSeg)) + align_up(sizeof(int) * ns) + align_up(sizeof(int) * ns * kStructRmax) +
+           align_up(sizeof(double) * ns * kStructRmax) + align_up(sizeof(double) * ns * mm) +
+           align_up(sizeof(int) * ns * mm) + align_up(sizeof(int32_t) * n) + cauchy_like_extra(std::max<int64_t>(n, 0));
+  return TDC_OK;
+}
+
+int tdc_cauchy_like_ranks(int64_t n, const double* d, const double* w, const double* u, const double* v,
+                          const tdc_opts* o, int32_t* ranks, void* ws, size_t ws_bytes, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0 || n > 0x7fffffff) return -1;
+  if (n == 0) return TDC_OK;
+  if (!d) return -2;
+  if (!w) return -3;
+  if (!u) return -4;
+  if (!v) return -5;
+  if (validate_opts(&op)) return -6;
+  if (!ranks) return -7;
+  size_t need = 0;
+  tdc_cauchy_like_ranks_workspace_size(n, &op, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  const int64_t mm = op.lr_tile, T = std::max<int64_t>(1, (n + mm - 1) / mm), ns = T * T;
+  char* p = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  GemmSeg* segs = (GemmSeg*)p; p += align_up(2 * sizeof(GemmSeg));
+  StructArgs SA;
+  memset(&SA, 0, sizeof(SA));
+  SA.m = (int)mm;
+  SA.rmax = kStructRmax;
+  SA.Tmax = (int)T;
+  SA.tol = op.lr_tol;
+  SA.all_offdiag = 1;
+  SA.srank = (int*)p; p += align_up(sizeof(int) * ns);
+  SA.spiv = (int*)p; p += align_up(sizeof(int) * ns * kStructRmax);
+  SA.sy = (double*)p; p += align_up(sizeof(double) * ns * kStructRmax);
+  SA.svr = (double*)p; p += align_up(sizeof(double) * ns * mm);
+  SA.scolpiv = (int*)p; p += align_up(sizeof(int) * ns * mm);
+  int32_t* iota = (int32_t*)p; p += align_up(sizeof(int32_t) * n);
+  int32_t* org = (int32_t*)p; p += align_up(sizeof(int32_t) * n);
+  double* tau = (double*)p; p += align_up(sizeof(double) * n);
+  double* scol = (double*)p; p += align_up(sizeof(double) * n);
+  int32_t* eb = (int32_t*)p;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  SA.status = st;
+  if (launch_cauchy_like_prep(0, n, nullptr, 0, d, w, u, v, org, tau, scol, eb, nullptr, nullptr, nullptr, false, cs) !=
+      cudaSuccess)
+    return TDC_ECUDA;
+  GemmSeg sg, last;
+  memset(&sg, 0, sizeof(sg));
+  memset(&last, 0, sizeof(last));
+  sg.rows = 1;
+  sg.kk = (int32_t)n;
+  sg.K = (int32_t)n;
+  sg.near_m = (int32_t)mm;
+  sg.plist = iota;
+  sg.D = d;
+  sg.org = org;
+  sg.tau = tau;
+  sg.zhat = u;
+  sg.scol = scol;
+  k_iota<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, cs>>>(iota, n);
+  cudaError_t err = cudaGetLastError();
+  if (err == cudaSuccess) {
+    k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
+    err = cudaGetLastError();
+  }
+  if (err == cudaSuccess) err = cudaMemsetAsync(SA.srank, 0, sizeof(int) * ns, cs);
+  if (err == cudaSuccess) err = launch_srrsc(segs, 1, SA, cs);
+  if (err == cudaSuccess) err = cudaMemcpyAsync(ranks, SA.srank, sizeof(int32_t) * ns, cudaMemcpyDeviceToDevice, cs);
+  return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+int tdc_cauchy_like_gemm(int64_t m, int64_t n, const double* A, int64_t lda, const double* d, const double* w,
+                         const double* u, const double* v, double* C, int64_t ldc, int32_t mode, const tdc_opts* o,
+                         void* ws, size_t ws_bytes, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0 || m > 0x7fffffff) return -1;
+  if (n < 0 || n > 0x7fffffff) return -2;
+  if (m == 0 || n == 0) return TDC_OK;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (!d) return -5;
+  if (!w) return -6;
+  if (!u) return -7;
+  if (!v) return -8;
+  if (!C) return -9;
+  if (ldc < m) return -10;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT && mode != TDC_MERGE_STRUCTURED &&
+      mode != TDC_MERGE_STRUCTURED_SPLIT)
+    return -11;
+  if (validate_opts(&op)) return -12;
+  size_t need = 0, prod = 0;
+  tdc_cauchy_like_gemm_workspace_size(m, n, mode, &op, &need);
+  tdc_cauchy_gemm_workspace_size(m, n, mode, &op, &prod);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  char* wbase = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  char* x = wbase + align_up(prod);
+  int32_t* org = (int32_t*)x; x += align_up(sizeof(int32_t) * n);
+  double* tau = (double*)x; x += align_up(sizeof(double) * n);
+  double* scol = (double*)x; x += align_up(sizeof(double) * n);
+  int32_t* eb = (int32_t*)x; x += align_up(sizeof(int32_t) * n);
+  int32_t* cexp = (int32_t*)x; x += align_up(sizeof(int32_t) * n);
+  unsigned long long* maxsq = (unsigned long long*)x;
+  int32_t* eA = (int32_t*)(x + 64);
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  const bool scale = mode == TDC_MERGE_SPLIT || mode == TDC_MERGE_STRUCTURED_SPLIT;
+  if (launch_cauchy_like_prep(m, n, A, lda, d, w, u, v, org, tau, scol, eb, cexp, eA, maxsq, scale, cs) != cudaSuccess)
+    return TDC_ECUDA;
+  return cauchy_product(m, n, A, lda, d, org, tau, u, scol, C, ldc, mode, op, wbase, st, scale ? cexp : nullptr,
+                        scale ? eA : nullptr, cs);
 }
 
 // W and R (n^2 doubles each per problem), column exponents, segments and the

@@ -149,6 +149,10 @@ struct GemmSeg {
   int32_t bq0;
   int32_t a_kt;
   int32_t part;  // the structured path's segment builder: the part a segment belongs to
+  // general Cauchy-like products: A enters the split product as A 2^-aexp, and column j
+  // of the product is scaled back by a further 2^oexp[j] (NULL: none)
+  int32_t aexp;
+  const int32_t* oexp;
 };
 
 struct Plan {
@@ -204,6 +208,7 @@ struct StructArgs {
   unsigned long long* ranks;  // statistics (NULL when off): far tiles, sum of their ranks,
                               // dense fallbacks, largest rank kept
   int fallback_only;          // k_struct_apply: only the tiles that stayed dense (the split variant)
+  int all_offdiag;            // k_srrsc: every tile off the diagonal (rank profile), not only |I - J| >= 2
 };
 
 // Scratch and outputs of the structured path on the split GEMM (one level, or one
@@ -424,6 +429,11 @@ cudaError_t launch_srrsc(const GemmSeg* segs, int nseg, const StructArgs& A, cud
 cudaError_t launch_struct_fallback(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_ss_build(const SSArgs& A, cudaStream_t s);
 cudaError_t launch_ss_gate(const int32_t* accept, GemmSeg* plain_list, cudaStream_t s);
+cudaError_t launch_cauchy_like_prep(int64_t m, int64_t n, const double* A, int64_t lda, const double* d,
+                                    const double* w, const double* u, const double* v, int32_t* org, double* tau,
+                                    double* scol, int32_t* eb, int32_t* cexp, int32_t* eA,
+                                    unsigned long long* maxsq, bool scale, cudaStream_t s);
+cudaError_t launch_cauchy_like_patch(GemmSeg* seg, const int32_t* eA, cudaStream_t s);
 cudaError_t launch_seg_dense(const GemmSeg& seg, cudaStream_t s);
 cudaError_t launch_struct(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s);
 cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t s);

@@ -331,6 +331,7 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
           const int p = sg.plist ? sg.plist[q] : q;
           const int col = sg.acol ? sg.acol[p] : p;
           x = sg.A[(int64_t)row * sg.ars + (int64_t)col * sg.lda];
+          if (sg.aexp) x *= pow2(-sg.aexp);
         }
         digits_bf16(x, S, dig[i]);
       }
@@ -724,7 +725,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
             const int j = t.ct * BN + c0 + i;
             if (j < sg.K) {
               const int pos = sg.cpos ? sg.cpos[j] : j;
-              const double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+              double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+              if (sg.oexp) v *= pow2(sg.oexp[j]);
               double* cp = sg.C + row + (int64_t)pos * sg.ldc;
               if (sg.acc) *cp += v; else *cp = v;
             }
@@ -777,7 +779,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           const int j = t.ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            const double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+            double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
+            if (sg.oexp) v *= pow2(sg.oexp[j]);
             double* cp = sg.C + row + (int64_t)pos * sg.ldc;
             if (sg.acc) *cp += v; else *cp = v;
           }

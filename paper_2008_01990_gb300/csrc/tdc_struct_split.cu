@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
       g.C = sg.cpos ? sg.C : sg.C + (int64_t)j0 * sg.ldc;
       g.cpos = sg.cpos ? sg.cpos + j0 : nullptr;
       g.Bd = nullptr;
-      g.cexp = nullptr;
+      g.cexp = sg.cexp ? sg.cexp + j0 : nullptr;  // a general product's column scales
       g.bcol = nullptr;
       g.acc = 0;
       A.near_segs[ni++] = g;
@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(1024) k_ss_build(SSArgs A) {
         h.Bd = A.R + rb;
         h.ldb = kr;
         h.cexp = A.cexp + ((int64_t)s * Tm + t) * m;
+        h.oexp = sg.cexp ? sg.cexp + j0 : nullptr;  // R's scale in cexp, the product's here
         h.C = g.C;
         h.ldc = sg.ldc;
         h.cpos = g.cpos;

@@ -48,6 +48,9 @@ __device__ __forceinline__ int iabs(int x) { return x < 0 ? -x : x; }
 // ---------------------------------------------------------------------------
 constexpr int kMaxTile = 2048;
 
+// kF32: pivot search in FP32 on copies of the generators (tiles up to 2048); larger
+// tiles search in FP64, which fits their generators in shared memory.
+template <bool kF32>
 __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S) {
   extern __shared__ double sm[];
   const int s = blockIdx.y;
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
   const int m = S.m;
   if (sg.near_m == 0 || sg.K == 0) return;
   const int T = (sg.K + m - 1) / m;
-  if (I >= T || J >= T || iabs(I - J) <= 1) return;
+  if (I >= T || J >= T || iabs(I - J) <= (S.all_offdiag ? 0 : 1)) return;
   const int64_t slot = ((int64_t)s * S.Tmax + I) * S.Tmax + J;
   int qa, qb;
   row_range(sg, I, m, qa, qb);
@@ -76,10 +79,10 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
   double* wo = dr + m;
   double* wt = wo + m;
   float* uf = reinterpret_cast<float*>(wt + m);
-  float* vf = uf + m;
-  float* df = vf + m;
-  float* wf = df + m;
-  uint8_t* ract = reinterpret_cast<uint8_t*>(wf + m);
+  float* vf = uf + (kF32 ? m : 0);
+  float* df = vf + (kF32 ? m : 0);
+  float* wf = df + (kF32 ? m : 0);
+  uint8_t* ract = reinterpret_cast<uint8_t*>(wf + (kF32 ? m : 0));
   uint8_t* cact = ract + m;
   __shared__ int prow[kStructRmax], pcol[kStructRmax];
   __shared__ float redv[8];
@@ -101,8 +104,10 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
   }
   __syncthreads();
   const double ref = dr[0];
-  for (int i = tid; i < mr; i += blockDim.x) { df[i] = (float)(dr[i] - ref); uf[i] = (float)u[i]; }
-  for (int c = tid; c < mc; c += blockDim.x) { wf[c] = (float)((wo[c] - ref) + wt[c]); vf[c] = (float)v[c]; }
+  if (kF32) {
+    for (int i = tid; i < mr; i += blockDim.x) { df[i] = (float)(dr[i] - ref); uf[i] = (float)u[i]; }
+    for (int c = tid; c < mc; c += blockDim.x) { wf[c] = (float)((wo[c] - ref) + wt[c]); vf[c] = (float)v[c]; }
+  }
   if (tid == 0) { s_r = 0; s_stop = 0; s_amax0 = 0.0; }
   __syncthreads();
   const int total = mr * mc;
@@ -114,7 +119,9 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
     for (int idx = tid; idx < total; idx += blockDim.x) {
       const int i = idx / mc, c = idx - i * mc;
       if (!ract[i] || !cact[c]) continue;
-      const float val = fabsf(uf[i] * vf[c]) / fabsf(df[i] - wf[c]);
+      float val;
+      if (kF32) val = fabsf(uf[i] * vf[c]) / fabsf(df[i] - wf[c]);
+      else val = (float)(fabs(u[i] * v[c]) / fabs((dr[i] - wo[c]) - wt[c]));
       if (val > best) { best = val; bidx = idx; }
     }
     for (int o = 16; o > 0; o >>= 1) {
@@ -160,12 +167,12 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
     for (int i = tid; i < mr; i += blockDim.x)
       if (ract[i]) {
         u[i] *= (dr[i] - dk) / ((dr[i] - wko) - wkt);
-        uf[i] = (float)u[i];
+        if (kF32) uf[i] = (float)u[i];
       }
     for (int c = tid; c < mc; c += blockDim.x)
       if (cact[c]) {
         v[c] *= ((wo[c] - wko) + (wt[c] - wkt)) / ((wo[c] - dk) + wt[c]);
-        vf[c] = (float)v[c];
+        if (kF32) vf[c] = (float)v[c];
       }
     __syncthreads();
   }
@@ -477,10 +484,14 @@ cudaError_t launch_struct_segs(const Plan& P, const LevelLaunch& L, cudaStream_t
 // SRRSC of every far tile of nseg segments.
 cudaError_t launch_srrsc(const GemmSeg* segs, int nseg, const StructArgs& A, cudaStream_t s) {
   if (nseg <= 0 || A.Tmax <= 0) return cudaSuccess;
-  const size_t smem = (size_t)A.m * (5 * sizeof(double) + 4 * sizeof(float) + 2);
-  cudaError_t e = cudaFuncSetAttribute(k_srrsc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const bool f32 = A.m <= kMaxTile;
+  const size_t smem = (size_t)A.m * (5 * sizeof(double) + (f32 ? 4 * sizeof(float) : 0) + 2);
+  cudaError_t e = cudaFuncSetAttribute(f32 ? k_srrsc<true> : k_srrsc<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_srrsc<<<dim3((unsigned)(A.Tmax * A.Tmax), (unsigned)nseg), 256, smem, s>>>(segs, A);
+  const dim3 grid((unsigned)(A.Tmax * A.Tmax), (unsigned)nseg);
+  if (f32) k_srrsc<true><<<grid, 256, smem, s>>>(segs, A);
+  else k_srrsc<false><<<grid, 256, smem, s>>>(segs, A);
   return cudaGetLastError();
 }
 

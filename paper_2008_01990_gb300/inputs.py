@@ -166,3 +166,16 @@ def backward_problems(count: int, n: int, seed: int, min_gap_rel: float = 1e-5, 
         ws.append(g.normal(n))
         Gs.append(g.normal(n * n).reshape(n, n, order="F"))
     return np.array(ds), np.array(es), np.array(ws), np.array(Gs), np.array(gaps), draws
+
+
+def example1_cauchy(n: int, seed: int = 2020, a: float = 1.0, b: float = 9.0):
+    """Generators of Example 1's Cauchy-like matrix B_ij = u_i v_j / (d_i - w_j):
+    d_i = i (b - a) / n, w_j = d_j + (b - a) / (2 n) (i, j = 1..n), u and v uniform(0,1)
+    from SplitMix64(seed)."""
+    i = np.arange(1, n + 1, dtype=np.float64)
+    d = i * (b - a) / n
+    w = d + (b - a) / (2 * n)
+    g = SplitMix64(seed)
+    u = g.uniform01(n)
+    v = g.uniform01(n)
+    return d, w, u, v

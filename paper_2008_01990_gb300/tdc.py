@@ -152,6 +152,11 @@ def lib():
     if hasattr(L, "tdc_rank_one"):
         L.tdc_rank_one_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
         L.tdc_rank_one.argtypes = [i64, P, P, ctypes.c_double, P, P, P, P, i32, P, sz, P]
+    if hasattr(L, "tdc_cauchy_like_gemm"):
+        L.tdc_cauchy_like_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_cauchy_like_gemm.argtypes = [i64, i64, P, i64, P, P, P, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
+        L.tdc_cauchy_like_ranks_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_cauchy_like_ranks.argtypes = [i64, P, P, P, P, ctypes.POINTER(Opts), P, P, sz, P]
     if hasattr(L, "tdc_cauchy_gemm"):
         L.tdc_cauchy_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_cauchy_gemm.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, i64, i32, ctypes.POINTER(Opts), P,
@@ -287,6 +292,44 @@ def cauchy_gemm(A: torch.Tensor, D: torch.Tensor, org: torch.Tensor, tau: torch.
     if check:
         _check("tdc_cauchy_gemm (device status)", sync_status(stream))
     return C
+
+
+def cauchy_like_gemm(A: torch.Tensor, d: torch.Tensor, w: torch.Tensor, u: torch.Tensor, v: torch.Tensor,
+                     mode: int = MERGE_DENSE, opts: Opts | None = None, stream=None, check=False):
+    """C = A * B with B_ij = u_i v_j / (d_i - w_j) (Example 1's operand); A a column-major
+    m x n view, d and w ascending (device FP64)."""
+    m, n = A.shape
+    lda = A.stride(1) if n > 0 else max(m, 1)
+    C = torch.empty(n, m, dtype=torch.float64, device=A.device).t()
+    b = ctypes.c_size_t(0)
+    _check("tdc_cauchy_like_gemm_workspace_size",
+           lib().tdc_cauchy_like_gemm_workspace_size(m, n, mode, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    ws = workspace(b.value, A.device)
+    _check("tdc_cauchy_like_gemm", lib().tdc_cauchy_like_gemm(m, n, _ptr(A), max(lda, 1), _ptr(d), _ptr(w), _ptr(u),
+                                                              _ptr(v), _ptr(C), max(m, 1), mode,
+                                                              ctypes.byref(opts) if opts else None, _ptr(ws),
+                                                              ws.numel(), _stream(stream)))
+    if check:
+        _check("tdc_cauchy_like_gemm (device status)", sync_status(stream))
+    return C
+
+
+def cauchy_like_ranks(d: torch.Tensor, w: torch.Tensor, u: torch.Tensor, v: torch.Tensor,
+                      opts: Opts | None = None, stream=None) -> torch.Tensor:
+    """SRRSC ranks of the off-diagonal tiles of B_ij = u_i v_j / (d_i - w_j): a T x T int32
+    tensor (rank of tile (I, J), -1 above the rank cap, 0 on the diagonal)."""
+    n = d.numel()
+    o = opts if opts else default_opts()
+    T = max(1, (n + o.lr_tile - 1) // o.lr_tile)
+    ranks = torch.zeros(T, T, dtype=torch.int32, device=d.device)
+    b = ctypes.c_size_t(0)
+    _check("tdc_cauchy_like_ranks_workspace_size", lib().tdc_cauchy_like_ranks_workspace_size(n, ctypes.byref(o),
+                                                                                              ctypes.byref(b)))
+    ws = workspace(b.value, d.device)
+    _check("tdc_cauchy_like_ranks", lib().tdc_cauchy_like_ranks(n, _ptr(d), _ptr(w), _ptr(u), _ptr(v), ctypes.byref(o),
+                                                                _ptr(ranks), _ptr(ws), ws.numel(), _stream(stream)))
+    _check("tdc_cauchy_like_ranks (device status)", sync_status(stream))
+    return ranks
 
 
 def eig_backward(lam: torch.Tensor, Q: torch.Tensor, lam_bar=None, Q_bar=None, stream=None):
