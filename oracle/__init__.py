@@ -7,7 +7,9 @@ package.  The CUDA product path never imports it and shares no code with it.
 The arithmetic lives in ``tdc_oracle.c`` (plain C, optional OpenMP), compiled
 by :func:`build` into ``liboracle.so`` next to this file and called through
 ctypes with numpy arrays.  ``adjoint.py`` and ``srrsc.py`` hold the numpy
-oracles of the adjoint and of the SRRSC low-rank approximation.
+oracles of the adjoint and of the SRRSC low-rank approximation; ``householder.py``
+the Householder reduction of a dense symmetric matrix to tridiagonal form and its
+back-transform.
 """
 from __future__ import annotations
 
