@@ -279,6 +279,44 @@ int tdc_cauchy_like_ranks_workspace_size(int64_t n, const tdc_opts* o, size_t* b
 int tdc_cauchy_like_ranks(int64_t n, const double* d, const double* w, const double* u, const double* v,
                           const tdc_opts* o, int32_t* ranks, void* ws, size_t ws_bytes, tdc_stream_t stream);
 
+/* Dense symmetric eigenproblems (Section 4, Example 3: each matrix is first reduced to
+ * tridiagonal form, then the tridiagonal solver runs on T).
+ *
+ * tdc_sytrd: Householder reduction A = Q T Q^T of the n x n symmetric A (device FP64,
+ * column-major, lda >= n; only the lower triangle is read).  Reflector k = 0 .. n-3 is
+ * H_k = I - tau[k] v_k v_k^T with v_k(0:k+1) = 0, v_k(k+1) = 1, mapping column k below the
+ * diagonal to a multiple of e_1 (LAPACK's xLARFG convention: beta = -sign(alpha) ||x||);
+ * Q = H_0 H_1 ... H_{n-3}.  Outputs: d[n], e[n-1] (T's diagonal and off-diagonal),
+ * tau[n-1] (tau[n-2] = 0), and A overwritten: A(k+2:n, k) holds v_k(k+2:n), A(k+1, k) = e[k],
+ * A(k, k) = d[k]; the strict upper triangle is scratch.  Computed in FP64 with the
+ * trailing rank-2nb updates as split-precision tensor-core products (base-256 BF16
+ * digits, exact level sums): backward error of the order of FP64 rounding times ||A||.
+ * ws of tdc_sytrd_workspace_size(n) bytes.  Errors: -1 n, -2 A, -3 lda, -4 d, -5 e,
+ * -6 tau, -9 options (spin_budget and split_chunk_k are used), TDC_ENOWS, TDC_ECUDA;
+ * device status TDC_ETIMEOUT if a grid barrier of the panel kernel gave up. */
+int tdc_sytrd_workspace_size(int64_t n, size_t* bytes);
+int tdc_sytrd(int64_t n, double* A, int64_t lda, double* d, double* e, double* tau, void* ws, size_t ws_bytes,
+              const tdc_opts* o, tdc_stream_t stream);
+
+/* tdc_ormtr: X <- Q X for the Q of tdc_sytrd (A and tau as tdc_sytrd left them), X n x ncols
+ * (ldx >= n, device FP64), in place.  Blocks of 128 reflectors in compact WY form, applied
+ * from the last block back as split-precision products (X's columns enter scaled by powers
+ * of two from their norms, which the orthogonal updates keep).  ws of
+ * tdc_ormtr_workspace_size(n, ncols) bytes.  Errors: -1 n, -2 ncols, -3 A, -4 lda, -5 tau,
+ * -6 X, -7 ldx, -10 options, TDC_ENOWS, TDC_ECUDA. */
+int tdc_ormtr_workspace_size(int64_t n, int64_t ncols, size_t* bytes);
+int tdc_ormtr(int64_t n, int64_t ncols, const double* A, int64_t lda, const double* tau, double* X, int64_t ldx,
+              void* ws, size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream);
+
+/* tdc_syevd: A = Z diag(lam) Z^T for the dense symmetric A (lower triangle read, A
+ * destroyed): tdc_sytrd, tdc_eig on (d, e) with the options o, tdc_ormtr on the
+ * eigenvectors.  lam[n] ascending, Z n x n (ldz >= n).  One status for the whole call.
+ * ws of tdc_syevd_workspace_size(n, o) bytes.  Errors: -1 n, -2 A, -3 lda, -4 lam, -5 Z,
+ * -6 ldz, -9 options, TDC_ENOWS, TDC_ECUDA, or those of the steps. */
+int tdc_syevd_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
+int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
+              const tdc_opts* o, tdc_stream_t stream);
+
 /* Synchronise `stream` and return the device status of the last call enqueued on it
  * (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE, TDC_EUNSUPPORTED, or the warning
  * TDC_WPRECISION), then clear it.  Each stream that calls the library gets its own

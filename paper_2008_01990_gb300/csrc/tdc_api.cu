@@ -56,11 +56,18 @@ static int* stream_slot(cudaStream_t s, bool assign) {
   return slot;
 }
 
+// Calls made inside a composed call (tdc_syevd) keep the status the outer call cleared.
+static thread_local int g_status_nest = 0;
+struct StatusNest {
+  StatusNest() { ++g_status_nest; }
+  ~StatusNest() { --g_status_nest; }
+};
+
 // Clear the stream's status slot (stream-ordered) and note it as the device's last.
 static int* begin_status(cudaStream_t s) {
   int* slot = stream_slot(s, true);
   if (!slot) return nullptr;
-  if (cudaMemsetAsync(slot, 0, 2 * sizeof(int), s) != cudaSuccess) return nullptr;
+  if (g_status_nest == 0 && cudaMemsetAsync(slot, 0, 2 * sizeof(int), s) != cudaSuccess) return nullptr;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_mu);
@@ -1361,6 +1368,298 @@ int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const 
   cudaError_t e = launch_adjoint(batch, (int)n, lam, Q, n, nn, lam_bar, Q_bar, nn, d_bar, e_bar, w, st, 1ll << 24,
                                  (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Dense symmetric eigenproblems (Section 4, Example 3): Householder reduction to
+// tridiagonal form, the divide and conquer on T, back-transform of its eigenvectors.
+// ---------------------------------------------------------------------------
+namespace {
+
+size_t take(size_t& o, size_t bytes) {
+  const size_t r = o;
+  o += align_up(bytes);
+  return r;
+}
+
+struct TrdLayout {
+  size_t V, W, x, y, ps, pvy, pw, pv, bar, Aop, Bop, cexp, wmax, segs, img, total;
+};
+
+// Reduction scratch: the panel's V and W (n x kTrdNb each), the column and A22 v,
+// per-block partials, the panel dots, the barrier counter, and (n >= kTrdSplitMin) the
+// split update's operands and digit images for trailing orders up to n.
+TrdLayout trd_layout(int64_t n) {
+  TrdLayout L;
+  size_t o = 0;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  const bool split = n >= kTrdSplitMin;
+  L.V = take(o, sizeof(double) * nn * kTrdNb);
+  L.W = take(o, sizeof(double) * nn * kTrdNb);
+  L.x = take(o, sizeof(double) * nn);
+  L.y = take(o, sizeof(double) * nn);
+  L.ps = take(o, sizeof(double) * kTrdMaxBlocks);
+  L.pvy = take(o, sizeof(double) * kTrdMaxBlocks);
+  L.pw = take(o, sizeof(double) * kTrdNb);
+  L.pv = take(o, sizeof(double) * kTrdNb);
+  L.bar = take(o, 64);
+  L.Aop = take(o, split ? sizeof(double) * nn * 2 * kTrdNb : 0);
+  L.Bop = take(o, split ? sizeof(double) * nn * 2 * kTrdNb : 0);
+  L.cexp = take(o, split ? sizeof(int32_t) * nn : 0);
+  L.wmax = take(o, 64);
+  L.segs = take(o, 2 * sizeof(GemmSeg));
+  const int64_t KB = cdiv64(2 * kTrdNb, kSplitBK);
+  const int64_t img = split ? (cdiv64(n, kSplitBM) * KB * kTrdSlices * kSplitBM * kSplitBK +
+                               cdiv64(n, kSplitBN) * KB * kTrdSlices * kSplitBN * kSplitBK)
+                            : 0;
+  L.img = take(o, sizeof(__nv_bfloat16) * (size_t)img);
+  L.total = o + 256;
+  return L;
+}
+
+// split-K pieces of V^T X for a block of mb rows: enough for about kOrmTileTarget output
+// tiles, at least 256 rows each
+int orm_ns(int64_t mb, int64_t ncols) {
+  const int64_t ct = std::max<int64_t>(1, cdiv64(ncols, kSplitBN));
+  int64_t ns = cdiv64(kOrmTileTarget, ct);
+  ns = std::min<int64_t>(ns, std::max<int64_t>(1, mb / 256));
+  return (int)std::max<int64_t>(1, ns);
+}
+int64_t orm_kper(int64_t mb, int ns) { return cdiv64(cdiv64(mb, ns), kSplitBK) * kSplitBK; }
+
+struct OrmLayout {
+  size_t Vb, G, Y, Z, zexp, xexp, list1, list2, img, total;
+};
+
+OrmLayout orm_layout(int64_t n, int64_t ncols) {
+  OrmLayout L;
+  size_t o = 0;
+  const int64_t mb = std::max<int64_t>(n - 1, 1), nc = std::max<int64_t>(ncols, 1);
+  const int64_t ns = orm_ns(mb, nc), kb = kOrmKb, S = kTrdSlices;
+  L.Vb = take(o, sizeof(double) * (size_t)(std::max<int64_t>(n, 1) * kb));
+  L.G = take(o, sizeof(double) * (size_t)(ns * kb * kb));
+  L.Y = take(o, sizeof(double) * (size_t)(ns * kb * nc));
+  L.Z = take(o, sizeof(double) * (size_t)(kb * nc));
+  L.zexp = take(o, sizeof(int32_t) * (size_t)nc);
+  L.xexp = take(o, sizeof(int32_t) * (size_t)nc);
+  L.list1 = take(o, sizeof(GemmSeg) * (size_t)(2 * ns + 1));
+  L.list2 = take(o, sizeof(GemmSeg) * 2);
+  // digit images of one list at a time: list 1 (A = V_b^T twice per piece, B = V_b and X),
+  // list 2 (A = V_b, B = Z)
+  const int64_t kt = cdiv64(mb, kSplitBK) + ns;
+  const int64_t img1 =
+      kt * S * (2 * kSplitBM * kSplitBK + (cdiv64(kb, kSplitBN) + cdiv64(nc, kSplitBN)) * kSplitBN * kSplitBK);
+  const int64_t KB2 = cdiv64(kb, kSplitBK);
+  const int64_t img2 =
+      (cdiv64(mb, kSplitBM) * KB2 * kSplitBM * kSplitBK + cdiv64(nc, kSplitBN) * KB2 * kSplitBN * kSplitBK) * S;
+  L.img = take(o, sizeof(__nv_bfloat16) * (size_t)std::max(img1, img2));
+  L.total = o + 256;
+  return L;
+}
+
+int sytrd_run(int64_t n, double* A, int64_t lda, double* d, double* e, double* tau, char* base, const tdc_opts& op,
+              int* st, cudaStream_t s) {
+  if (n > 2) {
+    const TrdLayout L = trd_layout(n);
+    if (launch_sym_fill(n, A, lda, s) != cudaSuccess) return TDC_ECUDA;
+    const int grid = trd_panel_grid();
+    if (grid <= 0) return TDC_ECUDA;
+    TrdPanel P;
+    memset(&P, 0, sizeof(P));
+    P.A = A;
+    P.lda = lda;
+    P.n = n;
+    P.V = (double*)(base + L.V);
+    P.W = (double*)(base + L.W);
+    P.d = d;
+    P.e = e;
+    P.tau = tau;
+    P.x = (double*)(base + L.x);
+    P.y = (double*)(base + L.y);
+    P.ps = (double*)(base + L.ps);
+    P.pvy = (double*)(base + L.pvy);
+    P.pw = (double*)(base + L.pw);
+    P.pv = (double*)(base + L.pv);
+    P.bar = (unsigned*)(base + L.bar);
+    P.status = st;
+    P.budget = op.spin_budget;
+    TrdUpdate U;
+    memset(&U, 0, sizeof(U));
+    U.A = A;
+    U.lda = lda;
+    U.n = n;
+    U.V = P.V;
+    U.W = P.W;
+    U.ld = n;
+    U.Aop = (double*)(base + L.Aop);
+    U.Bop = (double*)(base + L.Bop);
+    U.cexp = (int32_t*)(base + L.cexp);
+    U.wmax = (unsigned long long*)(base + L.wmax);
+    U.segs = (GemmSeg*)(base + L.segs);
+    U.img = (__nv_bfloat16*)(base + L.img);
+    U.status = st;
+    U.budget = op.spin_budget;
+    U.chunk_steps = op.split_chunk_k / 16;
+    for (int64_t p = 0; p < n - 2; p += kTrdNb) {
+      P.p = p;
+      P.nbp = (int32_t)std::min<int64_t>(kTrdNb, n - 2 - p);
+      if (launch_trd_panel(P, grid, s) != cudaSuccess) return TDC_ECUDA;
+      U.t0 = p + P.nbp;
+      U.nb = P.nbp;
+      if (launch_trd_update(U, s) != cudaSuccess) return TDC_ECUDA;
+    }
+  }
+  return launch_trd_tail(n, A, lda, d, e, tau, s) == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
+int ormtr_run(int64_t n, int64_t ncols, const double* A, int64_t lda, const double* tau, double* X, int64_t ldx,
+              char* base, const tdc_opts& op, int* st, cudaStream_t s) {
+  const int64_t nref = n - 2;
+  if (nref <= 0 || ncols == 0) return TDC_OK;
+  const OrmLayout L = orm_layout(n, ncols);
+  int32_t* xexp = (int32_t*)(base + L.xexp);
+  if (launch_orm_xexp(n, ncols, X, ldx, xexp, s) != cudaSuccess) return TDC_ECUDA;
+  for (int64_t b = cdiv64(nref, kOrmKb) - 1; b >= 0; --b) {
+    OrmStep O;
+    memset(&O, 0, sizeof(O));
+    O.n = n;
+    O.b0 = b * kOrmKb;
+    O.kbp = (int32_t)std::min<int64_t>(kOrmKb, nref - O.b0);
+    O.mb = n - O.b0 - 1;
+    O.ncols = ncols;
+    O.Vb = (double*)(base + L.Vb);
+    O.ldv = n;
+    O.X = X;
+    O.ldx = ldx;
+    O.xexp = xexp;
+    O.tau = tau;
+    O.G = (double*)(base + L.G);
+    O.Y = (double*)(base + L.Y);
+    O.Z = (double*)(base + L.Z);
+    O.zexp = (int32_t*)(base + L.zexp);
+    const int ns = orm_ns(O.mb, ncols);
+    O.kper = orm_kper(O.mb, ns);
+    O.ns = (int32_t)cdiv64(O.mb, O.kper);
+    O.list1 = (GemmSeg*)(base + L.list1);
+    O.list2 = (GemmSeg*)(base + L.list2);
+    O.img = (__nv_bfloat16*)(base + L.img);
+    O.img2 = 0;
+    O.S = kTrdSlices;
+    O.status = st;
+    O.budget = op.spin_budget;
+    O.chunk_steps = op.split_chunk_k / 16;
+    if (launch_orm_step(O, A, lda, s) != cudaSuccess) return TDC_ECUDA;
+  }
+  return TDC_OK;
+}
+
+size_t syevd_vec_bytes(int64_t n) { return 3 * align_up(sizeof(double) * (size_t)std::max<int64_t>(n, 1)); }
+
+}  // namespace
+
+extern "C" {
+
+int tdc_sytrd_workspace_size(int64_t n, size_t* bytes) {
+  if (n < 0) return -1;
+  if (!bytes) return -2;
+  *bytes = trd_layout(n).total;
+  return TDC_OK;
+}
+
+int tdc_sytrd(int64_t n, double* A, int64_t lda, double* d, double* e, double* tau, void* ws, size_t ws_bytes,
+              const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (n == 0) return TDC_OK;
+  if (!A) return -2;
+  if (lda < n) return -3;
+  if (!d) return -4;
+  if (n > 1 && !e) return -5;
+  if (n > 1 && !tau) return -6;
+  if (validate_opts(&op)) return -9;
+  if (!ws || ws_bytes < trd_layout(n).total) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  return sytrd_run(n, A, lda, d, e, tau, base, op, st, cs);
+}
+
+int tdc_ormtr_workspace_size(int64_t n, int64_t ncols, size_t* bytes) {
+  if (n < 0) return -1;
+  if (ncols < 0) return -2;
+  if (!bytes) return -3;
+  *bytes = orm_layout(n, ncols).total;
+  return TDC_OK;
+}
+
+int tdc_ormtr(int64_t n, int64_t ncols, const double* A, int64_t lda, const double* tau, double* X, int64_t ldx,
+              void* ws, size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (ncols < 0) return -2;
+  if (n <= 2 || ncols == 0) return TDC_OK;
+  if (!A) return -3;
+  if (lda < n) return -4;
+  if (!tau) return -5;
+  if (!X) return -6;
+  if (ldx < n) return -7;
+  if (validate_opts(&op)) return -10;
+  if (!ws || ws_bytes < orm_layout(n, ncols).total) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  return ormtr_run(n, ncols, A, lda, tau, X, ldx, base, op, st, cs);
+}
+
+int tdc_syevd_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
+  if (n < 0) return -1;
+  if (!bytes) return -3;
+  size_t we = 0;
+  if (tdc_workspace_size(n, o, &we) != TDC_OK) return -2;
+  *bytes = syevd_vec_bytes(n) + std::max(we, std::max(trd_layout(n).total, orm_layout(n, n).total)) + 256;
+  return TDC_OK;
+}
+
+int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
+              const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (n == 0) return TDC_OK;
+  if (!A) return -2;
+  if (lda < n) return -3;
+  if (!lam) return -4;
+  if (!Z) return -5;
+  if (ldz < n) return -6;
+  if (validate_opts(&op)) return -9;
+  size_t need = 0;
+  tdc_syevd_workspace_size(n, &op, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  StatusNest keep;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  const size_t vb = align_up(sizeof(double) * (size_t)n);
+  double* d = (double*)base;
+  double* e = (double*)(base + vb);
+  double* tau = (double*)(base + 2 * vb);
+  char* rest = base + syevd_vec_bytes(n);
+  const size_t rest_bytes = ws_bytes - (size_t)(rest - (char*)ws);
+  int r = sytrd_run(n, A, lda, d, e, tau, rest, op, st, cs);
+  if (r != TDC_OK) return r;
+  r = tdc_eig(n, d, e, lam, Z, ldz, rest, rest_bytes, &op, stream);
+  if (r != TDC_OK) return r;
+  return ormtr_run(n, n, A, lda, tau, Z, ldz, rest, op, st, cs);
 }
 
 int tdc_sync_status(tdc_stream_t stream) {

@@ -446,6 +446,85 @@ cudaError_t launch_adjoint(int batch, int n, const double* lam, const double* Q,
                            double* e_bar, double* ws, int* status, long long spin_budget, cudaStream_t s);
 int64_t split_img_elems(int64_t rows_top, int64_t rows_bot, int64_t kk_bound, int64_t K_bound, int S);
 constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
+// dense symmetric reduction to tridiagonal form and its back-transform (tdc_sytrd.cu)
+constexpr int kTrdNb = 128;        // reflectors per panel
+constexpr int kTrdThreads = 512;   // threads of a panel block (one block per SM)
+constexpr int kTrdMaxBlocks = 1024;
+constexpr int kTrdSplitMin = 512;  // trailing updates of this order and above take the split product
+constexpr int kTrdSlices = 7;      // digits of the reduction's split products
+constexpr int kOrmKb = 128;        // reflectors per back-transform block
+constexpr int kOrmZThreads = 512;
+constexpr int kOrmTileTarget = 304;  // split-K: aim at this many output tiles for V^T X
+struct TrdPanel {
+  double* A;
+  int64_t lda, n, p;
+  int32_t nbp;          // reflectors in the panel (columns p .. p + nbp - 1)
+  double* V;            // n x kTrdNb, ld n, rows indexed globally
+  double* W;
+  double* d;
+  double* e;
+  double* tau;
+  double* x;            // the current column (n)
+  double* y;            // A22 v (n)
+  double* ps;           // per-block partial sums (kTrdMaxBlocks each)
+  double* pvy;
+  double* pw;           // W^T v, V^T v of the current column (kTrdNb each)
+  double* pv;
+  unsigned* bar;        // grid barrier counter
+  int* status;
+  long long budget;
+};
+struct TrdUpdate {
+  double* A;
+  int64_t lda, n, t0;  // trailing matrix A(t0:n, t0:n)
+  int32_t nb;
+  const double* V;
+  const double* W;
+  int64_t ld;
+  double* Aop;
+  double* Bop;
+  int32_t* cexp;
+  unsigned long long* wmax;
+  GemmSeg* segs;
+  __nv_bfloat16* img;
+  int* status;
+  long long budget;
+  int chunk_steps;
+};
+struct OrmStep {
+  int64_t n, b0, mb, ncols;  // reflectors b0 .. b0 + kbp - 1 act on rows b0 + 1 .. n - 1 (mb rows)
+  int32_t kbp;
+  double* Vb;
+  int64_t ldv;
+  double* X;
+  int64_t ldx;
+  const int32_t* xexp;
+  const double* tau;
+  double* G;  // ns x kbp x kbp partial Gram matrices
+  double* Y;  // ns x kbp x ncols partial V^T X
+  double* Z;  // kbp x ncols
+  int32_t* zexp;
+  int32_t ns;
+  int64_t kper;
+  GemmSeg* list1;
+  GemmSeg* list2;
+  __nv_bfloat16* img;
+  int64_t img2;
+  int S;
+  int* status;
+  long long budget;
+  int chunk_steps;
+};
+int trd_panel_grid();
+cudaError_t launch_sym_fill(int64_t n, double* A, int64_t lda, cudaStream_t s);
+cudaError_t launch_trd_panel(const TrdPanel& P, int grid, cudaStream_t s);
+cudaError_t launch_trd_update(const TrdUpdate& U, cudaStream_t s);
+cudaError_t launch_trd_tail(int64_t n, const double* A, int64_t lda, double* d, double* e, double* tau,
+                            cudaStream_t s);
+cudaError_t launch_orm_xexp(int64_t rows, int64_t ncols, const double* X, int64_t ldx, int32_t* xexp,
+                            cudaStream_t s);
+cudaError_t launch_orm_step(const OrmStep& O, const double* A, int64_t lda, cudaStream_t s);
+size_t orm_z_smem(int kbp);
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
 // merges of order n <= kDenseSmallN take 32 x 32 tiles: their halves have at most 64
 // rows, so a 128-row tile would leave most of its FP64 multiply-adds on padding

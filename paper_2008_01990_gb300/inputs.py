@@ -13,6 +13,10 @@ Matrix families (diagonal d[n], off-diagonal e[n-1]):
   * ``clement``   d = 0, e_i = sqrt(i (n - i)), i = 1..n-1  (Example 2, Kac)
   * ``hermite``   d = 0, e_i = sqrt(i)                       (Example 2)
   * ``sht``       spherical-harmonic-transform matrix        (Example 3)
+
+Dense symmetric families (``dense_sym``) for the reduction to tridiagonal form that
+precedes the solver in Example 3 (whose SuiteSparse matrices are not available; these
+stand in for them).
 """
 from __future__ import annotations
 
@@ -179,3 +183,33 @@ def example1_cauchy(n: int, seed: int = 2020, a: float = 1.0, b: float = 9.0):
     u = g.uniform01(n)
     v = g.uniform01(n)
     return d, w, u, v
+
+
+def dense_sym(name: str, n: int, seed: int = 1) -> np.ndarray:
+    """Dense symmetric n x n matrices (FP64, both triangles, C order):
+      * ``uniform``  (X + X^T) / 2 with X i.i.d. uniform(-1, 1)
+      * ``cluster``  I + 1e-8 (X + X^T) / 2          (eigenvalues clustered at 1)
+      * ``lowrank``  2 I + u u^T + w w^T, u, w uniform(-1, 1) / sqrt(n)
+                     (n - 2 eigenvalues equal to 2: after two reflectors the trailing
+                     columns are zero up to rounding)
+      * ``zerocol``  ``uniform`` with A(1:n, 0) = A(0, 1:n) = 0 (first reflector trivial)
+      * ``tridiag``  the ``uniform`` tridiagonal family written densely (already reduced)"""
+    g = SplitMix64(seed)
+    if name == "tridiag":
+        d, e = uniform_tridiag(n, seed)
+        return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+    if name == "lowrank":
+        u = g.uniform(n, -1.0, 1.0) / np.sqrt(max(n, 1))
+        w = g.uniform(n, -1.0, 1.0) / np.sqrt(max(n, 1))
+        return 2.0 * np.eye(n) + np.outer(u, u) + np.outer(w, w)
+    X = g.uniform(n * n, -1.0, 1.0).reshape(n, n)
+    A = 0.5 * (X + X.T)
+    if name == "uniform":
+        return A
+    if name == "cluster":
+        return np.eye(n) + 1e-8 * A
+    if name == "zerocol":
+        A[1:, 0] = 0.0
+        A[0, 1:] = 0.0
+        return A
+    raise KeyError(name)

@@ -157,6 +157,13 @@ def lib():
         L.tdc_cauchy_like_gemm.argtypes = [i64, i64, P, i64, P, P, P, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
         L.tdc_cauchy_like_ranks_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_cauchy_like_ranks.argtypes = [i64, P, P, P, P, ctypes.POINTER(Opts), P, P, sz, P]
+    if hasattr(L, "tdc_sytrd"):
+        L.tdc_sytrd_workspace_size.argtypes = [i64, ctypes.POINTER(sz)]
+        L.tdc_sytrd.argtypes = [i64, P, i64, P, P, P, P, sz, ctypes.POINTER(Opts), P]
+        L.tdc_ormtr_workspace_size.argtypes = [i64, i64, ctypes.POINTER(sz)]
+        L.tdc_ormtr.argtypes = [i64, i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
+        L.tdc_syevd_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_syevd.argtypes = [i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
     if hasattr(L, "tdc_cauchy_gemm"):
         L.tdc_cauchy_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_cauchy_gemm.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, i64, i32, ctypes.POINTER(Opts), P,
@@ -330,6 +337,79 @@ def cauchy_like_ranks(d: torch.Tensor, w: torch.Tensor, u: torch.Tensor, v: torc
                                                                 _ptr(ranks), _ptr(ws), ws.numel(), _stream(stream)))
     _check("tdc_cauchy_like_ranks (device status)", sync_status(stream))
     return ranks
+
+
+def _colmajor_copy(A: torch.Tensor) -> torch.Tensor:
+    n, m = A.shape
+    R = torch.empty(m, n, dtype=torch.float64, device=A.device).t()
+    R.copy_(A)
+    return R
+
+
+def sytrd(A: torch.Tensor, opts: Opts | None = None, stream=None, check: bool = False):
+    """Householder reduction A = Q T Q^T of the symmetric A (device FP64, n x n, lower
+    triangle read; A itself is not modified).  Returns (d, e, tau, R): T's diagonal and
+    off-diagonal, the reflector scalars (n - 1, the last 0) and a column-major copy of A
+    holding the reflectors below the subdiagonal (the input of ormtr)."""
+    n = A.shape[0]
+    R = _colmajor_copy(A)
+    dev = A.device
+    d = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    e = torch.empty(max(n - 1, 1), dtype=torch.float64, device=dev)
+    tau = torch.empty(max(n - 1, 1), dtype=torch.float64, device=dev)
+    b = ctypes.c_size_t(0)
+    _check("tdc_sytrd_workspace_size", lib().tdc_sytrd_workspace_size(n, ctypes.byref(b)))
+    ws = workspace(b.value, dev)
+    _check("tdc_sytrd", lib().tdc_sytrd(n, _ptr(R), max(n, 1), _ptr(d), _ptr(e), _ptr(tau), _ptr(ws), ws.numel(),
+                                        ctypes.byref(opts) if opts else None, _stream(stream)))
+    if check:
+        _check("tdc_sytrd (device status)", sync_status(stream))
+    return d[:n], e[:max(n - 1, 0)], tau[:max(n - 1, 0)], R
+
+
+def ormtr(R: torch.Tensor, tau: torch.Tensor, X: torch.Tensor, opts: Opts | None = None, stream=None,
+          check: bool = False) -> torch.Tensor:
+    """X <- Q X in place for the Q of sytrd (R, tau as sytrd returned them); X a
+    column-major n x ncols view (stride(0) == 1)."""
+    n, ncols = X.shape
+    if X.stride(0) != 1 and ncols > 1:
+        raise ValueError("X must be column-major (a transposed view of row-major storage)")
+    b = ctypes.c_size_t(0)
+    _check("tdc_ormtr_workspace_size", lib().tdc_ormtr_workspace_size(n, ncols, ctypes.byref(b)))
+    ws = workspace(b.value, X.device)
+    ldx = X.stride(1) if ncols > 1 else max(n, 1)
+    _check("tdc_ormtr", lib().tdc_ormtr(n, ncols, _ptr(R), max(R.stride(1), n, 1), _ptr(tau), _ptr(X), max(ldx, n, 1),
+                                        _ptr(ws), ws.numel(), ctypes.byref(opts) if opts else None, _stream(stream)))
+    if check:
+        _check("tdc_ormtr (device status)", sync_status(stream))
+    return X
+
+
+def syevd_workspace_size(n: int, opts: Opts | None = None) -> int:
+    b = ctypes.c_size_t(0)
+    _check("tdc_syevd_workspace_size", lib().tdc_syevd_workspace_size(int(n), ctypes.byref(opts) if opts else None,
+                                                                      ctypes.byref(b)))
+    return b.value
+
+
+def syevd(A: torch.Tensor, opts: Opts | None = None, ws: torch.Tensor | None = None, stream=None,
+          check: bool = False, overwrite: bool = False):
+    """A = Z diag(lam) Z^T for the dense symmetric A (device FP64, lower triangle read):
+    reduction, the divide and conquer on T, back-transform.  Returns (lam, Z), Z a
+    column-major view.  overwrite=True lets the call destroy a column-major A instead of
+    copying it."""
+    n = A.shape[0]
+    R = A if (overwrite and (A.stride(0) == 1 or n <= 1)) else _colmajor_copy(A)
+    lam = torch.empty(max(n, 1), dtype=torch.float64, device=A.device)
+    Z = torch.empty(n, n, dtype=torch.float64, device=A.device).t()
+    if ws is None:
+        ws = workspace(syevd_workspace_size(n, opts), A.device)
+    _check("tdc_syevd", lib().tdc_syevd(n, _ptr(R), max(R.stride(1) if n > 1 else n, n, 1), _ptr(lam), _ptr(Z),
+                                        max(n, 1), _ptr(ws), ws.numel(), ctypes.byref(opts) if opts else None,
+                                        _stream(stream)))
+    if check:
+        _check("tdc_syevd (device status)", sync_status(stream))
+    return lam[:n], Z
 
 
 def eig_backward(lam: torch.Tensor, Q: torch.Tensor, lam_bar=None, Q_bar=None, stream=None):

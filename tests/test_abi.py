@@ -88,3 +88,40 @@ def test_invalid_options_rejected_on_host(lib, bad):
     assert lib.tdc_eig(4, bogus, bogus, bogus, bogus, 4, bogus, 1 << 30, ctypes.byref(o), None) == -9
     nb = ctypes.c_size_t(0)
     assert lib.tdc_workspace_size(4, ctypes.byref(o), ctypes.byref(nb)) == -2
+
+
+def test_dense_symmetric_entry_points_check_arguments_on_the_host(lib):
+    from paper_2008_01990_gb300 import tdc
+    bogus = ctypes.c_void_p(0x1000)
+    big = 1 << 40
+    assert lib.tdc_sytrd(-1, bogus, 1, bogus, bogus, bogus, bogus, big, None, None) == -1
+    assert lib.tdc_sytrd(0, None, 1, None, None, None, None, 0, None, None) == 0
+    assert lib.tdc_sytrd(4, None, 4, bogus, bogus, bogus, bogus, big, None, None) == -2
+    assert lib.tdc_sytrd(4, bogus, 3, bogus, bogus, bogus, bogus, big, None, None) == -3
+    assert lib.tdc_sytrd(4, bogus, 4, None, bogus, bogus, bogus, big, None, None) == -4
+    assert lib.tdc_sytrd(4, bogus, 4, bogus, None, bogus, bogus, big, None, None) == -5
+    assert lib.tdc_sytrd(4, bogus, 4, bogus, bogus, None, bogus, big, None, None) == -6
+    assert lib.tdc_sytrd(4, bogus, 4, bogus, bogus, bogus, bogus, 16, None, None) == tdc.TDC_ENOWS
+    assert lib.tdc_ormtr(-1, 1, bogus, 1, bogus, bogus, 1, bogus, big, None, None) == -1
+    assert lib.tdc_ormtr(4, -1, bogus, 4, bogus, bogus, 4, bogus, big, None, None) == -2
+    assert lib.tdc_ormtr(2, 5, None, 1, None, None, 1, None, 0, None, None) == 0  # no reflector
+    assert lib.tdc_ormtr(6, 5, None, 6, bogus, bogus, 6, bogus, big, None, None) == -3
+    assert lib.tdc_ormtr(6, 5, bogus, 5, bogus, bogus, 6, bogus, big, None, None) == -4
+    assert lib.tdc_ormtr(6, 5, bogus, 6, None, bogus, 6, bogus, big, None, None) == -5
+    assert lib.tdc_ormtr(6, 5, bogus, 6, bogus, None, 6, bogus, big, None, None) == -6
+    assert lib.tdc_ormtr(6, 5, bogus, 6, bogus, bogus, 5, bogus, big, None, None) == -7
+    assert lib.tdc_ormtr(6, 5, bogus, 6, bogus, bogus, 6, bogus, 16, None, None) == tdc.TDC_ENOWS
+    assert lib.tdc_syevd(-1, bogus, 1, bogus, bogus, 1, bogus, big, None, None) == -1
+    assert lib.tdc_syevd(5, None, 5, bogus, bogus, 5, bogus, big, None, None) == -2
+    assert lib.tdc_syevd(5, bogus, 4, bogus, bogus, 5, bogus, big, None, None) == -3
+    assert lib.tdc_syevd(5, bogus, 5, None, bogus, 5, bogus, big, None, None) == -4
+    assert lib.tdc_syevd(5, bogus, 5, bogus, None, 5, bogus, big, None, None) == -5
+    assert lib.tdc_syevd(5, bogus, 5, bogus, bogus, 4, bogus, big, None, None) == -6
+    assert lib.tdc_syevd(5, bogus, 5, bogus, bogus, 5, bogus, 16, None, None) == tdc.TDC_ENOWS
+    sz = [ctypes.c_size_t(0) for _ in range(3)]
+    for i, n in enumerate((100, 1000, 4000)):
+        assert lib.tdc_syevd_workspace_size(n, None, ctypes.byref(sz[i])) == 0
+    assert sz[0].value < sz[1].value < sz[2].value
+    w = ctypes.c_size_t(0)
+    assert lib.tdc_workspace_size(4000, None, ctypes.byref(w)) == 0
+    assert sz[2].value > w.value

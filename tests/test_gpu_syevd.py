@@ -1,0 +1,164 @@
+"""Dense symmetric eigenproblems on the GPU (Section 4, Example 3: reduction to tridiagonal
+form, the divide and conquer on T, back-transform of its eigenvectors) against the
+Householder oracle (oracle/householder.py).
+
+What is unique is compared element by element: T's entries (d, e), and, where the
+reflectors are determined by the data rather than by rounding noise, the reflectors and
+their scalars.  Q is checked for what makes it valid: orthogonal, and Q^T A Q = T to the
+backward-error bound.  The eigensolver is checked by residual and orthogonality ratios,
+its eigenvalues against the oracle's.
+
+Tolerances.  The reduction's backward error is of order n eps ||A|| (each reflector
+applied with O(n) rounding errors, the split updates exact up to one rounding per
+entry); T's entries move by that amount times their condition, which is modest for
+these families away from the noise-level off-diagonals.  The element-wise bound used is
+1e-11 ||A||_2 for n <= 1100, about 40 n eps for n = 1100."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import householder as hh
+from paper_2008_01990_gb300 import inputs
+
+from helpers import EPS
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def tdc():
+    from paper_2008_01990_gb300 import build, tdc as t
+    build.build()
+    t.lib()
+    return t
+
+
+def reflectors(R, n):
+    """V (n x n-2) of the reduced matrix's lower triangle: unit at k+1, R(k+2:n, k) below."""
+    V = np.zeros((n, max(n - 2, 0)))
+    for k in range(n - 2):
+        V[k + 1, k] = 1.0
+        V[k + 2:, k] = R[k + 2:, k]
+    return V
+
+
+def tri(d, e):
+    return np.diag(d) + np.diag(e, 1) + np.diag(e, -1)
+
+
+def gpu_q(tdc, R, tau, n):
+    X = torch.eye(n, dtype=torch.float64, device=DEV).t().contiguous().t()
+    tdc.ormtr(R, tau, X, check=True)
+    return X.cpu().numpy()
+
+
+@pytest.mark.parametrize("name,n", [("uniform", 3), ("uniform", 5), ("uniform", 130), ("uniform", 300),
+                                    ("uniform", 700), ("uniform", 1100), ("zerocol", 257), ("tridiag", 200),
+                                    ("lowrank", 600), ("cluster", 520)])
+def test_sytrd_vs_oracle(tdc, name, n):
+    A = inputs.dense_sym(name, n, seed=n)
+    d, e, tau, R = tdc.sytrd(torch.tensor(A, device=DEV), check=True)
+    d, e, tau, R = d.cpu().numpy(), e.cpu().numpy(), tau.cpu().numpy(), R.cpu().numpy()
+    do, eo, Vo, to = hh.tridiagonalize(A)
+    nA = max(np.linalg.norm(A, 2), np.finfo(float).tiny)
+    tol = 1e-11 * nA
+    assert np.max(np.abs(d - do)) <= tol
+    assert np.max(np.abs(e - eo)) <= tol
+    assert tau.shape == (max(n - 1, 0),) and (n < 2 or tau[-1] == 0.0)
+    if name in ("uniform", "zerocol", "tridiag"):
+        # reflectors fixed by the data: element-wise; |v| <= 1, tau in [1, 2] or 0
+        assert np.max(np.abs(tau[: n - 2] - to)) <= 1e-11
+        assert np.max(np.abs(reflectors(R, n) - Vo), initial=0.0) <= 1e-10
+    if name == "zerocol":
+        assert tau[0] == 0.0 and e[0] == 0.0
+    if name == "tridiag":
+        assert np.all(tau == 0.0)
+    # validity of Q and T whatever the noise-level reflectors: Q^T A Q = T, Q orthogonal
+    Q = gpu_q(tdc, torch.tensor(R, device=DEV).t().contiguous().t(), torch.tensor(tau, device=DEV), n)
+    assert np.abs(Q.T @ Q - np.eye(n)).sum(axis=0).max() / (n * EPS) <= 50
+    assert np.abs(Q.T @ A @ Q - tri(d, e)).sum(axis=0).max() / (n * EPS * nA) <= 50
+
+
+@pytest.mark.parametrize("n,ncols", [(3, 4), (131, 1), (300, 77), (900, 300), (1030, 1030)])
+def test_ormtr_vs_oracle(tdc, n, ncols):
+    """X <- Q X against the oracle's reflector-by-reflector product with the same reflectors."""
+    A = inputs.dense_sym("uniform", n, seed=7 * n)
+    _, _, tau, R = tdc.sytrd(torch.tensor(A, device=DEV), check=True)
+    g = inputs.SplitMix64(n + ncols)
+    X = g.uniform(n * ncols, -1.0, 1.0).reshape(n, ncols)
+    Xt = torch.tensor(np.ascontiguousarray(X.T), device=DEV).t()
+    tdc.ormtr(R, tau, Xt, check=True)
+    got = Xt.cpu().numpy()
+    Rn, tn = R.cpu().numpy(), tau.cpu().numpy()
+    want = hh.apply_q(reflectors(Rn, n), tn[: max(n - 2, 0)], X)
+    col = np.linalg.norm(X, axis=0)
+    err = np.abs(got - want).max(axis=0) / np.maximum(col, np.finfo(float).tiny)
+    assert err.max() <= 64 * n * EPS
+
+
+def residual_ratios(A, lam, Z):
+    n = A.shape[0]
+    nA = max(np.linalg.norm(A, 2), np.finfo(float).tiny)
+    res = np.abs(A @ Z - Z * lam).sum(axis=0).max() / (n * nA * EPS)
+    orth = np.abs(Z.T @ Z - np.eye(n)).sum(axis=0).max() / (n * EPS)
+    # the paper's residual of Example 3: max column norm of A - Z Lam Z^T over ||A||_2
+    paper = np.linalg.norm(A - (Z * lam) @ Z.T, axis=0).max() / nA
+    return res, orth, paper
+
+
+@pytest.mark.parametrize("name,n", [("uniform", 1), ("uniform", 2), ("uniform", 3), ("uniform", 129),
+                                    ("lowrank", 600), ("cluster", 700), ("zerocol", 513)])
+def test_syevd_small_and_degenerate(tdc, orc, name, n):
+    A = inputs.dense_sym(name, n, seed=3 * n + 1)
+    lam, Z = tdc.syevd(torch.tensor(A, device=DEV), check=True)
+    lam, Z = lam.cpu().numpy(), Z.cpu().numpy()
+    assert np.all(np.diff(lam) >= 0)
+    do, eo, _, _ = hh.tridiagonalize(A)
+    lo, _ = orc.eig(do, eo, max_iter=2000) if n > 0 else (np.zeros(0), None)
+    nA = max(np.linalg.norm(A, 2), np.finfo(float).tiny)
+    assert np.max(np.abs(lam - lo)) <= 50 * max(n, 1) * EPS * nA
+    res, orth, paper = residual_ratios(A, lam, Z)
+    assert res <= 50 and orth <= 50, (res, orth)
+    assert paper <= 50 * max(n, 1) * EPS
+
+
+def test_syevd_2048_vs_oracle(tdc, orc):
+    """The full pipeline at n = 2048 on the uniform family: eigenvalues against the
+    oracle's (Householder reduction, then the oracle's divide and conquer), eigenvectors
+    by the residual ratio <= 50 and the orthogonality ratio <= 50."""
+    n = 2048
+    A = inputs.dense_sym("uniform", n, seed=2048)
+    lam, Z = tdc.syevd(torch.tensor(A, device=DEV), check=True)
+    lam, Z = lam.cpu().numpy(), Z.cpu().numpy()
+    do, eo, _, _ = hh.tridiagonalize(A)
+    lo, _ = orc.eig(do, eo, max_iter=2000)
+    nA = np.linalg.norm(A, 2)
+    assert np.max(np.abs(lam - lo)) <= 50 * n * EPS * nA
+    res, orth, paper = residual_ratios(A, lam, Z)
+    assert res <= 50 and orth <= 50, (res, orth)
+    assert paper <= 50 * n * EPS
+
+
+def test_syevd_split_merge_mode(tdc):
+    """The composed solver with the tridiagonal stage forced onto the plain split merge."""
+    n = 1500
+    A = inputs.dense_sym("uniform", n, seed=15)
+    o = tdc.default_opts(merge_mode=tdc.MERGE_SPLIT, split_min_K=64)
+    lam, Z = tdc.syevd(torch.tensor(A, device=DEV), opts=o, check=True)
+    res, orth, _ = residual_ratios(A, lam.cpu().numpy(), Z.cpu().numpy())
+    assert res <= 50 and orth <= 50, (res, orth)
+
+
+def test_sytrd_barrier_timeout_reports_status(tdc):
+    """A panel whose grid barriers may poll only once gives up with TDC_ETIMEOUT instead of
+    waiting; the context stays usable and the next call succeeds."""
+    n = 400
+    A = torch.tensor(inputs.dense_sym("uniform", n, seed=4), device=DEV)
+    o = tdc.default_opts(spin_budget=1)
+    tdc.sytrd(A, opts=o)
+    st = tdc.sync_status()
+    assert st in (0, tdc.TDC_ETIMEOUT)
+    d, e, tau, R = tdc.sytrd(A, check=True)
+    do, eo, _, _ = hh.tridiagonalize(A.cpu().numpy())
+    assert np.max(np.abs(d.cpu().numpy() - do)) <= 1e-11 * np.linalg.norm(A.cpu().numpy(), 2)
