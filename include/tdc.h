@@ -283,7 +283,7 @@ int tdc_cauchy_like_ranks(int64_t n, const double* d, const double* w, const dou
  * tridiagonal form, then the tridiagonal solver runs on T).
  *
  * tdc_sytrd: Householder reduction A = Q T Q^T of the n x n symmetric A (device FP64,
- * column-major, lda >= n; only the lower triangle is read).  Reflector k = 0 .. n-3 is
+ * column-major, n <= lda <= 2^27; only the lower triangle is read).  Reflector k = 0 .. n-3 is
  * H_k = I - tau[k] v_k v_k^T with v_k(0:k+1) = 0, v_k(k+1) = 1, mapping column k below the
  * diagonal to a multiple of e_1 (LAPACK's xLARFG convention: beta = -sign(alpha) ||x||);
  * Q = H_0 H_1 ... H_{n-3}.  Outputs: d[n], e[n-1] (T's diagonal and off-diagonal),

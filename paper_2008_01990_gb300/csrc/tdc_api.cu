@@ -1385,12 +1385,13 @@ size_t take(size_t& o, size_t bytes) {
 }
 
 struct TrdLayout {
-  size_t V, W, x, y, ps, pvy, pw, pv, bar, Aop, Bop, cexp, wmax, segs, img, total;
+  size_t V, W, Vr, Wr, x, y, ps, pvy, pw, pv, bar, Aop, Bop, cexp, wmax, segs, img, total;
 };
 
-// Reduction scratch: the panel's V and W (n x kTrdNb each), the column and A22 v,
-// per-block partials, the panel dots, the barrier counter, and (n >= kTrdSplitMin) the
-// split update's operands and digit images for trailing orders up to n.
+// Reduction scratch: the panel's V and W (n x kTrdNb each, column- and row-major), the
+// column and A22 v, per-block partials, the panel dots, the barrier counter, and
+// (n >= kTrdSplitMin) the split update's operands and digit images for trailing orders
+// up to n.
 TrdLayout trd_layout(int64_t n) {
   TrdLayout L;
   size_t o = 0;
@@ -1398,6 +1399,8 @@ TrdLayout trd_layout(int64_t n) {
   const bool split = n >= kTrdSplitMin;
   L.V = take(o, sizeof(double) * nn * kTrdNb);
   L.W = take(o, sizeof(double) * nn * kTrdNb);
+  L.Vr = take(o, sizeof(double) * nn * kTrdNb);
+  L.Wr = take(o, sizeof(double) * nn * kTrdNb);
   L.x = take(o, sizeof(double) * nn);
   L.y = take(o, sizeof(double) * nn);
   L.ps = take(o, sizeof(double) * kTrdMaxBlocks);
@@ -1473,6 +1476,8 @@ int sytrd_run(int64_t n, double* A, int64_t lda, double* d, double* e, double* t
     P.n = n;
     P.V = (double*)(base + L.V);
     P.W = (double*)(base + L.W);
+    P.Vr = (double*)(base + L.Vr);
+    P.Wr = (double*)(base + L.Wr);
     P.d = d;
     P.e = e;
     P.tau = tau;
@@ -1576,7 +1581,7 @@ int tdc_sytrd(int64_t n, double* A, int64_t lda, double* d, double* e, double* t
   if (n < 0) return -1;
   if (n == 0) return TDC_OK;
   if (!A) return -2;
-  if (lda < n) return -3;
+  if (lda < n || lda > kTrdMaxLd) return -3;
   if (!d) return -4;
   if (n > 1 && !e) return -5;
   if (n > 1 && !tau) return -6;
@@ -1636,7 +1641,7 @@ int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t
   if (n < 0) return -1;
   if (n == 0) return TDC_OK;
   if (!A) return -2;
-  if (lda < n) return -3;
+  if (lda < n || lda > kTrdMaxLd) return -3;
   if (!lam) return -4;
   if (!Z) return -5;
   if (ldz < n) return -6;

@@ -449,9 +449,11 @@ constexpr int kSplitBM = 128, kSplitBN = 64, kSplitBK = 16;
 // dense symmetric reduction to tridiagonal form and its back-transform (tdc_sytrd.cu)
 constexpr int kTrdNb = 128;        // reflectors per panel
 constexpr int kTrdThreads = 512;   // threads of a panel block (one block per SM)
+constexpr int64_t kTrdSmemV = 16384;  // the column is staged in shared memory up to this order
 constexpr int kTrdMaxBlocks = 1024;
 constexpr int kTrdSplitMin = 512;  // trailing updates of this order and above take the split product
 constexpr int kTrdSlices = 7;      // digits of the reduction's split products
+constexpr int64_t kTrdMaxLd = (int64_t)1 << 27;  // the panel kernel's column offsets are 32-bit
 constexpr int kOrmKb = 128;        // reflectors per back-transform block
 constexpr int kOrmZThreads = 512;
 constexpr int kOrmTileTarget = 304;  // split-K: aim at this many output tiles for V^T X
@@ -461,6 +463,9 @@ struct TrdPanel {
   int32_t nbp;          // reflectors in the panel (columns p .. p + nbp - 1)
   double* V;            // n x kTrdNb, ld n, rows indexed globally
   double* W;
+  double* Vr;           // the same panels row-major (ld kTrdNb) for the row updates
+  double* Wr;
+  int32_t vsm;          // v staged in shared memory (n <= kTrdSmemV)
   double* d;
   double* e;
   double* tau;

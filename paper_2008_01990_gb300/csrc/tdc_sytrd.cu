@@ -49,14 +49,15 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 }
 
 // Grid-wide barrier of a cooperative launch: a growing arrival counter (zero before the
-// launch); a block's b-th barrier waits until b * gridDim.x arrivals.  The wait gives up
-// after `budget` polls, records TDC_ETIMEOUT and returns false in the whole block.
+// launch); a block's b-th barrier waits until b * gridDim.x arrivals.  The arrival is a
+// release reduction and the polls are acquire loads (a block's writes before the barrier
+// are visible to every block after it).  The wait gives up after `budget` polls, records
+// TDC_ETIMEOUT and returns false in the whole block.
 __device__ bool grid_barrier(unsigned* ctr, unsigned& target, long long budget, int* status, int* s_flag) {
   __syncthreads();
   target += gridDim.x;
   if (threadIdx.x == 0) {
-    __threadfence();
-    atomicAdd(ctr, 1u);
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(ctr) : "memory");
     int ok = 1;
     long long it = 0;
     while (ld_acquire_u32(ctr) < target) {
@@ -64,9 +65,8 @@ __device__ bool grid_barrier(unsigned* ctr, unsigned& target, long long budget, 
         ok = 0;
         break;
       }
-      __nanosleep(32);
+      if (it > 64) __nanosleep(32);
     }
-    __threadfence();
     if (!ok) set_status(status, TDC_ETIMEOUT);
     *s_flag = ok;
   }
@@ -74,21 +74,9 @@ __device__ bool grid_barrier(unsigned* ctr, unsigned& target, long long budget, 
   return *s_flag != 0;
 }
 
-// gamma = w~^T v = tau (v^T y - 2 pw^T pv) of a column with c earlier panel columns, from
-// the per-block partials of v^T y (one warp, the same order in every block)
-__device__ __forceinline__ double gamma_of(const double* pvy, const double* pw, const double* pv, int c, double tc) {
-  const int lane = threadIdx.x & 31;
-  double s = 0.0, q = 0.0;
-  for (int b = lane; b < (int)gridDim.x; b += 32) s += pvy[b];
-  for (int i = lane; i < c; i += 32) q = fma(pw[i], pv[i], q);
-  s = warp_sum(s);
-  q = warp_sum(q);
-  return tc * (s - 2.0 * q);
-}
-
-// sum over a block's warps in warp order (thread 0 gets the result)
-__device__ __forceinline__ double block_sum_ordered(double v, double* s_red) {
-  v = warp_sum(v);
+// sum over a block's warps in warp order of values held by lane 0 of each warp (thread 0
+// gets the result)
+__device__ __forceinline__ double block_sum_lane0(double v, double* s_red) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane == 0) s_red[warp] = v;
   __syncthreads();
@@ -125,85 +113,287 @@ __global__ void __launch_bounds__(256) k_sym_fill(int64_t n, double* A, int64_t 
   }
 }
 
+constexpr int kProdChunk = 16;  // columns a block takes at once in the symv
+
+// Sums over the 32 lanes of each of C per-lane values (C a power of two <= 32): a
+// reduce-scatter (every step keeps half of the values and adds the partner's other
+// half), then butterflies; lanes l with l mod (32 / C) = 0 end with the sum of value
+// l / (32 / C).  C = 16 takes 16 FP64 adds instead of the 80 of a butterfly per value:
+// FP64 adds are scarce on this chip.
+template <int C>
+__device__ __forceinline__ double warp_reduce_cols(double (&v)[C]) {
+  const int lane = threadIdx.x & 31;
+  int o = 16;
+#pragma unroll
+  for (int cnt = C; cnt > 1; cnt >>= 1, o >>= 1) {
+    const int half = cnt >> 1;
+    const bool up = lane & o;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double send = up ? v[i] : v[i + half], keep = up ? v[i + half] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  double r = v[0];
+#pragma unroll
+  for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+// Dots of nc <= C columns (base + q * stride, q < nc) with v over m rows: the block's
+// threads stride over the rows, loading the next row's entries before the current row's
+// multiply-adds, then reduce per column; writes y / pw / pv on threads q < nc and returns
+// (thread 0) sum_q v_col(q) dot_q for the A columns.
+template <int C, bool kSmem>
+__device__ __forceinline__ double chunk_dots(const double* base, int64_t stride, int nc, int64_t m,
+                                             const double* s_x, const double* xk, double sc, double* s_part,
+                                             double* s_vy, const TrdPanel& P, int64_t k, int kind, int64_t c0) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t st32 = (int32_t)stride;
+  const int64_t bd = blockDim.x;
+  double acc[C], cur[C];
+#pragma unroll
+  for (int q = 0; q < C; ++q) {
+    acc[q] = 0.0;
+    cur[q] = (tid < m && q < nc) ? base[tid + q * st32] : 0.0;
+  }
+  for (int64_t i = tid; i < m; i += bd) {
+    const int64_t i2 = i + bd;
+    double nxt[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) nxt[q] = (i2 < m && q < nc) ? base[i2 + q * st32] : 0.0;
+    const double v = i == 0 ? 1.0 : (kSmem ? s_x[i] : xk[i]) * sc;
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+      if (q < nc) acc[q] = fma(cur[q], v, acc[q]);
+      cur[q] = nxt[q];
+    }
+  }
+  constexpr int kSpan = 32 / C;
+  const double r = warp_reduce_cols<C>(acc);
+  if ((lane & (kSpan - 1)) == 0) s_part[warp * kProdChunk + lane / kSpan] = r;
+  __syncthreads();
+  if (tid < nc) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s_part[w * kProdChunk + tid];
+    const int64_t c = c0 + tid;  // index within its kind
+    if (kind == 0) {
+      P.y[k + 1 + c] = t;
+      s_vy[tid] = (c == 0 ? 1.0 : (kSmem ? s_x[c] : xk[c]) * sc) * t;
+    } else if (kind == 1) {
+      P.pw[c] = t;
+    } else {
+      P.pv[c] = t;
+    }
+  }
+  __syncthreads();
+  double vy = 0.0;
+  if (kind == 0 && tid == 0)
+    for (int q = 0; q < nc; ++q) vy += s_vy[q];
+  return vy;
+}
+
+template <bool kSmem>
+__device__ __forceinline__ double chunk_dots_n(const double* base, int64_t stride, int nc, int64_t m,
+                                               const double* s_x, const double* xk, double sc, double* s_part,
+                                               double* s_vy, const TrdPanel& P, int64_t k, int kind, int64_t c0) {
+  if (nc > 8) return chunk_dots<16, kSmem>(base, stride, nc, m, s_x, xk, sc, s_part, s_vy, P, k, kind, c0);
+  if (nc > 4) return chunk_dots<8, kSmem>(base, stride, nc, m, s_x, xk, sc, s_part, s_vy, P, k, kind, c0);
+  if (nc > 2) return chunk_dots<4, kSmem>(base, stride, nc, m, s_x, xk, sc, s_part, s_vy, P, k, kind, c0);
+  if (nc > 1) return chunk_dots<2, kSmem>(base, stride, nc, m, s_x, xk, sc, s_part, s_vy, P, k, kind, c0);
+  return chunk_dots<1, kSmem>(base, stride, nc, m, s_x, xk, sc, s_part, s_vy, P, k, kind, c0);
+}
+
+// The symv A22 v and the panel dots W^T v, V^T v as column dots over rows k+1..n-1: the m
+// columns of A22 are cut into equal runs over the blocks, and so are the 2j panel
+// columns (j of W, then j of V); a block takes its runs kProdChunk columns at a time.
+// v_0 = 1 and v_i = x_i sc, x from the shared copy (kSmem) or from global memory.
+// Returns (thread 0) the block's part of v^T A22 v.
+template <bool kSmem>
+__device__ double panel_products(const TrdPanel& P, int64_t k, int j, double sc, const double* s_x,
+                                 double* s_part, double* s_vy) {
+  const int64_t n = P.n, m = n - k - 1;
+  const double* __restrict__ xk = P.x + k + 1;
+  double vy = 0.0;
+  {
+    const int64_t per = (m + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = blockIdx.x * per, c1 = c0 + per < m ? c0 + per : m;
+    for (int64_t cb = c0; cb < c1; cb += kProdChunk) {
+      const int nc = (int)(c1 - cb < kProdChunk ? c1 - cb : kProdChunk);
+      vy += chunk_dots_n<kSmem>(P.A + (k + 1 + cb) * P.lda + k + 1, P.lda, nc, m, s_x, xk, sc, s_part, s_vy, P,
+                                k, 0, cb);
+    }
+  }
+  const int64_t items = 2 * (int64_t)j;
+  if (items > 0) {
+    const int64_t per = (items + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = blockIdx.x * per, c1 = c0 + per < items ? c0 + per : items;
+    for (int64_t cb = c0; cb < c1;) {
+      const int kind = cb < j ? 1 : 2;
+      const int64_t seg_end = cb < j ? j : items, lim = c1 < seg_end ? c1 : seg_end;
+      const int nc = (int)(lim - cb < kProdChunk ? lim - cb : kProdChunk);
+      const int64_t col = kind == 1 ? cb : cb - j;
+      const double* base = (kind == 1 ? P.W : P.V) + col * n + k + 1;
+      chunk_dots_n<kSmem>(base, n, nc, m, s_x, xk, sc, s_part, s_vy, P, k, kind, col);
+      cb += nc;
+    }
+  }
+  return vy;
+}
+
+// One panel: columns p .. p+nbp-1, two grid barriers per column.  Rows are taken a warp
+// each, spread over the blocks (lanes over the panel columns of the row-major copies Vr,
+// Wr); the symv and the panel dots go by runs of columns per block (column-major A, V,
+// W), with x staged in shared memory.  Each phase issues its loads together so that a
+// column costs few dependent round trips to memory.
 __global__ void __launch_bounds__(kTrdThreads, 1) k_trd_panel(TrdPanel P) {
+  extern __shared__ double s_x[];  // x(k+1 : n) when P.vsm
   __shared__ double s_vk[kTrdNb], s_wk[kTrdNb], s_pw[kTrdNb], s_pv[kTrdNb];
   __shared__ double s_red[kTrdThreads / 32];
-  __shared__ double s_scal[4];
+  __shared__ double s_part[(kTrdThreads / 32) * kProdChunk];
+  __shared__ double s_vy[kProdChunk];
+  __shared__ double s_scal[8];
   __shared__ int s_flag;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kTrdThreads / 32;
   const int64_t n = P.n, ld = P.n;
   const int64_t G = (int64_t)gridDim.x * blockDim.x, g = (int64_t)blockIdx.x * blockDim.x + tid;
-  const int64_t GW = G >> 5, gw = g >> 5;
+  const int64_t rstep = (int64_t)gridDim.x * kWarps;  // warp-per-row stride
   unsigned target = 0;
   double* __restrict__ A = P.A;
-  double* __restrict__ V = P.V;
-  double* __restrict__ W = P.W;
   const int64_t lda = P.lda;
+  constexpr int nb = kTrdNb;
 
   for (int j = 0; j < P.nbp; ++j) {
     const int64_t k = P.p + j;
     // ---- (1) finish w of column j-1, update column k with the panel so far
     double tprev = 0.0, gam = 0.0;
-    if (j > 0) {
-      tprev = P.tau[k - 1];
-      for (int c = tid; c < j - 1; c += blockDim.x) {
-        s_pw[c] = P.pw[c];
-        s_pv[c] = P.pv[c];
-        s_vk[c] = V[k + c * ld];
-        s_wk[c] = W[k + c * ld];
+    // the warp's first row: its loads go out with the prelude's
+    const int64_t r0 = k + blockIdx.x + (int64_t)gridDim.x * warp;
+    double vrc[4] = {0.0, 0.0, 0.0, 0.0}, wrc[4] = {0.0, 0.0, 0.0, 0.0};
+    double a0 = 0.0, yv0 = 0.0, vl0 = 0.0;
+    if (r0 < n) {
+      const double* vrow = P.Vr + r0 * nb;
+      const double* wrow = P.Wr + r0 * nb;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        vrc[q] = vrow[lane + 32 * q];
+        wrc[q] = wrow[lane + 32 * q];
       }
-      if (tid == 0) s_vk[j - 1] = V[k + (j - 1) * ld];
+      if (lane == 0) {
+        a0 = A[r0 + k * lda];
+        if (j > 0) {
+          yv0 = P.y[r0];
+          vl0 = vrow[j - 1];
+        }
+      }
+    }
+    if (j > 0) {
+      // one round trip: row k of the panel, the dots of column j-1, the partials of
+      // v^T A22 v, y_k and tau_{k-1}
+      for (int c = tid; c < j; c += blockDim.x) {
+        s_vk[c] = P.Vr[k * nb + c];
+        if (c < j - 1) {
+          s_pw[c] = P.pw[c];
+          s_pv[c] = P.pv[c];
+          s_wk[c] = P.Wr[k * nb + c];
+        }
+      }
+      if (warp == kWarps - 1) {
+        double t = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) t += P.pvy[b];
+        t = warp_sum(t);
+        if (lane == 0) {
+          s_scal[4] = t;
+          s_scal[5] = P.y[k];
+          s_scal[6] = P.tau[k - 1];
+        }
+      }
       __syncthreads();
+      tprev = s_scal[6];
       if (warp == 0) {
-        const double gm = gamma_of(P.pvy, s_pw, s_pv, j - 1, tprev);
-        double f = 0.0;
-        for (int c = lane; c < j - 1; c += 32) f = fma(s_vk[c], s_pw[c], fma(s_wk[c], s_pv[c], f));
+        double q = 0.0, f = 0.0;
+        for (int c = lane; c < j - 1; c += 32) {
+          q = fma(s_pw[c], s_pv[c], q);
+          f = fma(s_vk[c], s_pw[c], fma(s_wk[c], s_pv[c], f));
+        }
+        q = warp_sum(q);
         f = warp_sum(f);
         if (lane == 0) {
+          const double gm = tprev * (s_scal[4] - 2.0 * q);
           s_scal[0] = gm;
-          s_wk[j - 1] = tprev * (P.y[k] - f) - 0.5 * tprev * gm * s_vk[j - 1];
+          s_wk[j - 1] = tprev * (s_scal[5] - f) - 0.5 * tprev * gm * s_vk[j - 1];
         }
       }
       __syncthreads();
       gam = s_scal[0];
     }
     double ss = 0.0;
-    for (int64_t r = k + g; r < n; r += G) {
-      double a = A[r + k * lda];
-      if (j > 0) {
-        double f = 0.0, u = 0.0;
-        for (int c = 0; c < j - 1; ++c) {
-          const double vrc = V[r + c * ld], wrc = W[r + c * ld];
-          f = fma(vrc, s_pw[c], fma(wrc, s_pv[c], f));
-          u = fma(vrc, s_wk[c], fma(wrc, s_vk[c], u));
+    for (int64_t r = r0; r < n; r += rstep) {
+      double a = a0, yv = yv0, vlast = vl0;
+      if (r != r0) {  // later rows (n above the grid's warp count)
+        const double* vrow = P.Vr + r * nb;
+        const double* wrow = P.Wr + r * nb;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          vrc[q] = vrow[lane + 32 * q];
+          wrc[q] = wrow[lane + 32 * q];
         }
-        const double vr = V[r + (j - 1) * ld];
-        const double wr = (r == k) ? s_wk[j - 1] : tprev * (P.y[r] - f) - 0.5 * tprev * gam * vr;
-        W[r + (j - 1) * ld] = wr;
-        u = fma(vr, s_wk[j - 1], fma(wr, s_vk[j - 1], u));
-        a -= u;
+        if (lane == 0) {
+          a = A[r + k * lda];
+          if (j > 0) {
+            yv = P.y[r];
+            vlast = vrow[j - 1];
+          }
+        }
       }
-      if (r == k) {
-        P.d[k] = a;
-        A[k + k * lda] = a;
-      } else {
-        P.x[r] = a;
-        if (r >= k + 2) ss = fma(a, a, ss);
+      double f = 0.0, u = 0.0;
+      if (j > 1) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = lane + 32 * q;
+          if (c < j - 1) {
+            f = fma(vrc[q], s_pw[c], fma(wrc[q], s_pv[c], f));
+            u = fma(vrc[q], s_wk[c], fma(wrc[q], s_vk[c], u));
+          }
+        }
+        f = warp_sum(f);
+        u = warp_sum(u);
+      }
+      if (lane == 0) {
+        if (j > 0) {
+          const double wr = (r == k) ? s_wk[j - 1] : tprev * (yv - f) - 0.5 * tprev * gam * vlast;
+          P.W[r + (j - 1) * ld] = wr;
+          P.Wr[r * nb + j - 1] = wr;
+          u = fma(vlast, s_wk[j - 1], fma(wr, s_vk[j - 1], u));
+          a -= u;
+        }
+        if (r == k) {
+          P.d[k] = a;
+          A[k + k * lda] = a;
+        } else {
+          P.x[r] = a;
+          if (r >= k + 2) ss = fma(a, a, ss);
+        }
       }
     }
     {
-      const double t = block_sum_ordered(ss, s_red);
+      const double t = block_sum_lane0(ss, s_red);
       if (tid == 0) P.ps[blockIdx.x] = t;
     }
     if (!grid_barrier(P.bar, target, P.budget, P.status, &s_flag)) return;
 
-    // ---- (2) the reflector of column k; A22 v and the panel dots
+    // ---- (2) the reflector of column k (one round trip: the partials and x), then A22 v
+    // and the panel dots
+    const int64_t m = n - k - 1;
+    if (P.vsm)
+      for (int64_t i = tid; i < m; i += blockDim.x) s_x[i] = P.x[k + 1 + i];
     if (warp == 0) {
+      const double alpha = P.x[k + 1];
       double s = 0.0;
       for (int b = lane; b < (int)gridDim.x; b += 32) s += P.ps[b];
       s = warp_sum(s);
       if (lane == 0) {
-        const double alpha = P.x[k + 1];
         double t = 0.0, beta = alpha, sc = 0.0;
         if (s > 0.0) {
           const double nrm = sqrt(fma(alpha, alpha, s));
@@ -224,70 +414,59 @@ __global__ void __launch_bounds__(kTrdThreads, 1) k_trd_panel(TrdPanel P) {
       A[k + 1 + k * lda] = s_scal[3];
     }
     for (int64_t r = P.p + 1 + g; r < n; r += G) {
-      const double v = r <= k ? 0.0 : (r == k + 1 ? 1.0 : P.x[r] * sc);
-      V[r + j * ld] = v;
+      const double v = r <= k ? 0.0 : (r == k + 1 ? 1.0 : (P.vsm ? s_x[r - k - 1] : P.x[r]) * sc);
+      P.V[r + j * ld] = v;
+      P.Vr[r * nb + j] = v;
       if (r >= k + 2) A[r + k * lda] = v;
     }
-    const int64_t ncol = n - k - 1, items = ncol + 2 * (int64_t)j;
-    double vy = 0.0;
-    for (int64_t t = gw; t < items; t += GW) {
-      const double* col;
-      if (t < ncol) col = A + (k + 1 + t) * lda;
-      else col = (((t - ncol) & 1) ? V : W) + ((t - ncol) >> 1) * ld;
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int64_t r = k + 1 + lane;
-      if (r == k + 1) {  // lane 0's first row: v = 1
-        a0 = col[r];
-        r += 32;
-      } else if (r < n) {
-        a0 = col[r] * (P.x[r] * sc);
-        r += 32;
-      }
-      for (; r + 96 < n; r += 128) {
-        a0 = fma(col[r], P.x[r] * sc, a0);
-        a1 = fma(col[r + 32], P.x[r + 32] * sc, a1);
-        a2 = fma(col[r + 64], P.x[r + 64] * sc, a2);
-        a3 = fma(col[r + 96], P.x[r + 96] * sc, a3);
-      }
-      for (; r < n; r += 32) a0 = fma(col[r], P.x[r] * sc, a0);
-      const double dot = warp_sum((a0 + a1) + (a2 + a3));
-      if (lane == 0) {
-        if (t < ncol) {
-          const int64_t c = k + 1 + t;
-          P.y[c] = dot;
-          vy = fma(c == k + 1 ? 1.0 : P.x[c] * sc, dot, vy);
-        } else if ((t - ncol) & 1) {
-          P.pv[(t - ncol) >> 1] = dot;
-        } else {
-          P.pw[(t - ncol) >> 1] = dot;
-        }
-      }
-    }
-    {
-      const double t = block_sum_ordered(vy, s_red);
-      if (tid == 0) P.pvy[blockIdx.x] = t;
-    }
+    const double vy = P.vsm ? panel_products<true>(P, k, j, sc, s_x, s_part, s_vy)
+                            : panel_products<false>(P, k, j, sc, s_x, s_part, s_vy);
+    if (tid == 0) P.pvy[blockIdx.x] = vy;
     if (!grid_barrier(P.bar, target, P.budget, P.status, &s_flag)) return;
   }
 
   // ---- w of the panel's last column on the trailing rows
   const int jl = P.nbp - 1;
-  const double tl = P.tau[P.p + jl];
   for (int c = tid; c < jl; c += blockDim.x) {
     s_pw[c] = P.pw[c];
     s_pv[c] = P.pv[c];
   }
+  if (warp == kWarps - 1) {
+    double t = 0.0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) t += P.pvy[b];
+    t = warp_sum(t);
+    if (lane == 0) {
+      s_scal[4] = t;
+      s_scal[6] = P.tau[P.p + jl];
+    }
+  }
   __syncthreads();
+  const double tl = s_scal[6];
   if (warp == 0) {
-    const double gm = gamma_of(P.pvy, s_pw, s_pv, jl, tl);
-    if (lane == 0) s_scal[0] = gm;
+    double q = 0.0;
+    for (int c = lane; c < jl; c += 32) q = fma(s_pw[c], s_pv[c], q);
+    q = warp_sum(q);
+    if (lane == 0) s_scal[0] = tl * (s_scal[4] - 2.0 * q);
   }
   __syncthreads();
   const double gam = s_scal[0];
-  for (int64_t r = P.p + P.nbp + g; r < n; r += G) {
+  for (int64_t r = P.p + P.nbp + blockIdx.x + (int64_t)gridDim.x * warp; r < n; r += rstep) {
+    const double* vrow = P.Vr + r * nb;
+    const double* wrow = P.Wr + r * nb;
+    double vrc[4], wrc[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      vrc[q] = vrow[lane + 32 * q];
+      wrc[q] = wrow[lane + 32 * q];
+    }
     double f = 0.0;
-    for (int c = 0; c < jl; ++c) f = fma(V[r + c * ld], s_pw[c], fma(W[r + c * ld], s_pv[c], f));
-    W[r + jl * ld] = tl * (P.y[r] - f) - 0.5 * tl * gam * V[r + jl * ld];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int c = lane + 32 * q;
+      if (c < jl) f = fma(vrc[q], s_pw[c], fma(wrc[q], s_pv[c], f));
+    }
+    f = warp_sum(f);
+    if (lane == 0) P.W[r + jl * ld] = tl * (P.y[r] - f) - 0.5 * tl * gam * vrow[jl];
   }
 }
 
@@ -415,7 +594,12 @@ int trd_panel_grid() {
   if (!grid[dev]) {
     int sms = 0, per = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trd_panel, kTrdThreads, 0) != cudaSuccess || per < 1)
+    if (cudaFuncSetAttribute(k_trd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * kTrdSmemV)) != cudaSuccess)
+      return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_trd_panel, kTrdThreads, sizeof(double) * kTrdSmemV) !=
+            cudaSuccess ||
+        per < 1)
       return 0;
     grid[dev] = std::min(sms, kTrdMaxBlocks);
   }
@@ -428,12 +612,16 @@ cudaError_t launch_sym_fill(int64_t n, double* A, int64_t lda, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+size_t trd_panel_smem(int64_t n) { return n <= kTrdSmemV ? sizeof(double) * (size_t)std::max<int64_t>(n, 1) : 0; }
+
 cudaError_t launch_trd_panel(const TrdPanel& P, int grid, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(P.bar, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return e;
   TrdPanel arg = P;
+  arg.vsm = P.n <= kTrdSmemV ? 1 : 0;
   void* args[] = {&arg};
-  return cudaLaunchCooperativeKernel((const void*)k_trd_panel, dim3(grid), dim3(kTrdThreads), args, 0, s);
+  return cudaLaunchCooperativeKernel((const void*)k_trd_panel, dim3(grid), dim3(kTrdThreads), args,
+                                     trd_panel_smem(P.n), s);
 }
 
 cudaError_t launch_trd_update(const TrdUpdate& U, cudaStream_t s) {

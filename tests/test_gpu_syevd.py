@@ -11,8 +11,10 @@ its eigenvalues against the oracle's.
 Tolerances.  The reduction's backward error is of order n eps ||A|| (each reflector
 applied with O(n) rounding errors, the split updates exact up to one rounding per
 entry); T's entries move by that amount times their condition, which is modest for
-these families away from the noise-level off-diagonals.  The element-wise bound used is
-1e-11 ||A||_2 for n <= 1100, about 40 n eps for n = 1100."""
+these families away from the noise-level off-diagonals.  The element-wise bound used for
+d and e is 1e-11 ||A||_2 for n <= 1100, about 40 n eps for n = 1100.  Reflector k
+depends on x / ||x|| with ||x|| = |e_k|, so its scalar and vector get the bound
+50 n eps ||A||_2 / |e_k|."""
 import numpy as np
 import pytest
 import torch
@@ -66,10 +68,14 @@ def test_sytrd_vs_oracle(tdc, name, n):
     assert np.max(np.abs(d - do)) <= tol
     assert np.max(np.abs(e - eo)) <= tol
     assert tau.shape == (max(n - 1, 0),) and (n < 2 or tau[-1] == 0.0)
-    if name in ("uniform", "zerocol", "tridiag"):
-        # reflectors fixed by the data: element-wise; |v| <= 1, tau in [1, 2] or 0
-        assert np.max(np.abs(tau[: n - 2] - to)) <= 1e-11
-        assert np.max(np.abs(reflectors(R, n) - Vo), initial=0.0) <= 1e-10
+    if name in ("uniform", "zerocol", "tridiag") and n > 2:
+        # reflectors fixed by the data, element-wise.  tau_k = 1 + |alpha| / ||x|| and
+        # v_k = x / (alpha - beta) with ||x|| = |e_k|, so a backward perturbation of size
+        # n eps ||A|| moves them by about that over |e_k|
+        bound = 50 * n * EPS * nA / np.maximum(np.abs(eo[: n - 2]), np.finfo(float).tiny)
+        assert np.all(np.abs(tau[: n - 2] - to) <= np.minimum(bound, 2.0))
+        dV = np.abs(reflectors(R, n) - Vo).max(axis=0)
+        assert np.all(dV <= np.minimum(bound, 2.0))
     if name == "zerocol":
         assert tau[0] == 0.0 and e[0] == 0.0
     if name == "tridiag":
