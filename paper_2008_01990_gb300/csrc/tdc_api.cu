@@ -414,12 +414,14 @@ static void carve(Plan& P, const HostPlan& H, const Layout& L, char* base) {
 }
 
 // Problem table upload through kernel parameters (capture-safe: the values
-// are copied into the launch).
-static constexpr int kProbChunk = 40;
+// are copied into the launch).  440 entries of 64 bytes fill most of the 32 KB of
+// parameters a launch may carry, so a 4096-problem batch takes 10 launches.
+static constexpr int kProbChunk = 440;
+static_assert(sizeof(Problem) == 64, "problem table entry");
 struct ProbChunk {
   Problem p[kProbChunk];
 };
-__global__ void k_write_problems(ProbChunk c, int cnt, Problem* dst) {
+__global__ void __launch_bounds__(512) k_write_problems(ProbChunk c, int cnt, Problem* dst) {
   if (threadIdx.x < cnt) dst[threadIdx.x] = c.p[threadIdx.x];
 }
 
@@ -430,7 +432,7 @@ static cudaError_t upload_problems(const HostPlan& H, Problem* dst, cudaStream_t
     const int cnt = std::min(kProbChunk, n - b);
     memset(&c, 0, sizeof(c));
     for (int i = 0; i < cnt; ++i) c.p[i] = H.prob[b + i];
-    k_write_problems<<<1, 64, 0, s>>>(c, cnt, dst + b);
+    k_write_problems<<<1, 512, 0, s>>>(c, cnt, dst + b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -448,6 +450,27 @@ static int validate_opts(const tdc_opts* o) {
   if (o->spin_budget < 1) return 1;
   if (!(o->lr_tol > 0.0)) return 1;
   return 0;
+}
+
+// Events ordering the two streams level by level: a pool per host thread and device,
+// created on first use and reused by every later call (a re-recorded event stands for
+// its latest record, and a call's waits are enqueued after its own records).
+static cudaError_t level_events(int T, cudaEvent_t** evE, cudaEvent_t** evG) {
+  static thread_local std::vector<cudaEvent_t> pool[16];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
+  std::vector<cudaEvent_t>& v = pool[dev];
+  while ((int)v.size() < 2 * T) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    v.push_back(ev);
+  }
+  *evE = v.data();
+  *evG = v.data() + T;
+  return cudaSuccess;
 }
 
 // The second stream of the solver, one per host thread and device, created on first
@@ -553,12 +576,9 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   // waits for the top level's products.
   cudaStream_t sg = gemm_stream();
   if (sg == nullptr) err = cudaErrorUnknown;
-  std::vector<cudaEvent_t> evE(H.T, nullptr), evG(H.T, nullptr);
-  for (int l = 0; l < H.T && err == cudaSuccess; ++l) {
-    if (cudaEventCreateWithFlags(&evE[l], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&evG[l], cudaEventDisableTiming) != cudaSuccess)
-      err = cudaErrorUnknown;
-  }
+  cudaEvent_t* evE = nullptr;
+  cudaEvent_t* evG = nullptr;
+  if (err == cudaSuccess) err = level_events(H.T, &evE, &evG);
   for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
     const LevelLaunch& LL = H.levels[l];
     Plan P = PP[l & 1];
@@ -690,10 +710,6 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     if (err == cudaSuccess) err = cudaEventRecord(evG[l], sg);
   }
   if (err == cudaSuccess && H.T > 0) err = cudaStreamWaitEvent(s, evG[0], 0);
-  for (int l = 0; l < H.T; ++l) {
-    if (evE[l]) cudaEventDestroy(evE[l]);
-    if (evG[l]) cudaEventDestroy(evG[l]);
-  }
   const size_t t8 = mark();
   if (err == cudaSuccess) err = launch_sign_and_output(P, o.sign_normalise, s);
   const size_t t9 = mark();
