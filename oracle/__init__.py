@@ -9,7 +9,7 @@ by :func:`build` into ``liboracle.so`` next to this file and called through
 ctypes with numpy arrays.  ``adjoint.py`` and ``srrsc.py`` hold the numpy
 oracles of the adjoint and of the SRRSC low-rank approximation; ``householder.py``
 the Householder reduction of a dense symmetric matrix to tridiagonal form and its
-back-transform.
+back-transform; ``bidiag.py`` the bidiagonal SVD read off the Golub-Kahan tridiagonal.
 """
 from __future__ import annotations
 
