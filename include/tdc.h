@@ -317,6 +317,24 @@ int tdc_syevd_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
 int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
               const tdc_opts* o, tdc_stream_t stream);
 
+/* tdc_bdsdc: SVD B = U diag(sigma) VT of the n x n upper bidiagonal B (diagonal d[n],
+ * superdiagonal e[n-1], device FP64, not modified) through the divide and conquer (the
+ * paper's introduction points to it for the bidiagonal SVD): tdc_eig on the Golub-Kahan
+ * tridiagonal of order 2n (zero diagonal, off-diagonal d_1, e_1, d_2, ..., e_{n-1}, d_n),
+ * whose eigenvalues are +-sigma_i and whose eigenvector of +sigma_i is
+ * (v_1, u_1, ..., v_n, u_n) / sqrt(2).  sigma[n] descending; U (ldu >= n) holds the left
+ * singular vectors as columns, VT (ldvt >= n) the right ones as rows.  Singular values and
+ * the residuals B V - U Sigma, B^T U - V Sigma are accurate to FP64 rounding times ||B||;
+ * the singular vectors of sigma_i hold to about eps ||B|| / sigma_i (the pair +-sigma_i of
+ * the Golub-Kahan matrix is 2 sigma_i apart), so orthogonality degrades by ||B|| / sigma_min
+ * for ill-conditioned B, and an exactly singular B is not supported.  ws of
+ * tdc_bdsdc_workspace_size(n, o) bytes (the order-2n eigensolve and its 4 n^2 matrix).
+ * Errors: -1 n, -2 d, -3 e, -4 sigma, -5 U, -6 ldu, -7 VT, -8 ldvt, -11 options, TDC_ENOWS,
+ * TDC_ECUDA, or those of tdc_eig. */
+int tdc_bdsdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
+int tdc_bdsdc(int64_t n, const double* d, const double* e, double* sigma, double* U, int64_t ldu, double* VT,
+              int64_t ldvt, void* ws, size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream);
+
 /* Synchronise `stream` and return the device status of the last call enqueued on it
  * (TDC_OK, TDC_ENOCONV, TDC_ETIMEOUT, TDC_ENONFINITE, TDC_EUNSUPPORTED, or the warning
  * TDC_WPRECISION), then clear it.  Each stream that calls the library gets its own

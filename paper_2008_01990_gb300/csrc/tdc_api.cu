@@ -1683,6 +1683,58 @@ int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t
   return ormtr_run(n, n, A, lda, tau, Z, ldz, rest, op, st, cs);
 }
 
+// Bidiagonal SVD: the Golub-Kahan tridiagonal (order 2n), its eigenvalues and vectors,
+// and the singular triplets read off the positive half.
+static size_t bdsdc_head(int64_t n) {
+  const size_t m = (size_t)std::max<int64_t>(2 * n, 1);
+  return 3 * align_up(sizeof(double) * m) + align_up(sizeof(double) * m * m);
+}
+
+int tdc_bdsdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes) {
+  if (n < 0) return -1;
+  if (!bytes) return -3;
+  size_t we = 0;
+  if (tdc_workspace_size(2 * n, o, &we) != TDC_OK) return -2;
+  *bytes = bdsdc_head(n) + we + 256;
+  return TDC_OK;
+}
+
+int tdc_bdsdc(int64_t n, const double* d, const double* e, double* sigma, double* U, int64_t ldu, double* VT,
+              int64_t ldvt, void* ws, size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (n == 0) return TDC_OK;
+  if (!d) return -2;
+  if (n > 1 && !e) return -3;
+  if (!sigma) return -4;
+  if (!U) return -5;
+  if (ldu < n) return -6;
+  if (!VT) return -7;
+  if (ldvt < n) return -8;
+  if (validate_opts(&op)) return -11;
+  size_t need = 0;
+  tdc_bdsdc_workspace_size(n, &op, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  StatusNest keep;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  const size_t vb = align_up(sizeof(double) * (size_t)(2 * n));
+  double* td = (double*)base;
+  double* te = (double*)(base + vb);
+  double* lam = (double*)(base + 2 * vb);
+  double* Q = (double*)(base + 3 * vb);
+  char* rest = base + bdsdc_head(n);
+  const size_t rest_bytes = ws_bytes - (size_t)(rest - (char*)ws);
+  if (launch_gk_build(n, d, e, td, te, cs) != cudaSuccess) return TDC_ECUDA;
+  const int r = tdc_eig(2 * n, td, te, lam, Q, 2 * n, rest, rest_bytes, &op, stream);
+  if (r != TDC_OK) return r;
+  return launch_gk_extract(n, lam, Q, 2 * n, sigma, U, ldu, VT, ldvt, cs) == cudaSuccess ? TDC_OK : TDC_ECUDA;
+}
+
 int tdc_sync_status(tdc_stream_t stream) {
   cudaStream_t cs = (cudaStream_t)stream;
   if (cudaStreamSynchronize(cs) != cudaSuccess) return TDC_ECUDA;

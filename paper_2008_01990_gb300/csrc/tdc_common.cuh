@@ -530,6 +530,10 @@ cudaError_t launch_orm_xexp(int64_t rows, int64_t ncols, const double* X, int64_
                             cudaStream_t s);
 cudaError_t launch_orm_step(const OrmStep& O, const double* A, int64_t lda, cudaStream_t s);
 size_t orm_z_smem(int kbp);
+// bidiagonal SVD through the Golub-Kahan tridiagonal (tdc_bdsdc.cu)
+cudaError_t launch_gk_build(int64_t n, const double* d, const double* e, double* td, double* te, cudaStream_t s);
+cudaError_t launch_gk_extract(int64_t n, const double* lam, const double* Q, int64_t ldq, double* sigma, double* U,
+                              int64_t ldu, double* VT, int64_t ldvt, cudaStream_t s);
 constexpr int kDenseBM = 128, kDenseBN = 64, kDenseBK = 16;
 // merges of order n <= kDenseSmallN take 32 x 32 tiles: their halves have at most 64
 // rows, so a 128-row tile would leave most of its FP64 multiply-adds on padding

@@ -213,3 +213,22 @@ def dense_sym(name: str, n: int, seed: int = 1) -> np.ndarray:
         A[0, 1:] = 0.0
         return A
     raise KeyError(name)
+
+
+def bidiag_family(name: str, n: int, seed: int = 1):
+    """Upper bidiagonal matrices (d[n], e[n-1]) for the SVD:
+      * ``uniform``  |d| uniform(0.5, 1.5) with random signs, e uniform(-1, 1)
+      * ``ones``     d = e = 1 (sigma_k = 2 cos(k pi / (2n + 1)), k = 1..n)
+      * ``graded``   d_i = 2^(-20 i / n) times uniform(0.5, 1.5), e uniform(-1, 1) 2^(-20 i / n)"""
+    if name == "ones":
+        return np.ones(n), np.ones(max(n - 1, 0))
+    g = SplitMix64(seed)
+    mag = g.uniform(n, 0.5, 1.5)
+    sgn = np.where(g.uniform01(n) < 0.5, -1.0, 1.0)
+    e = g.uniform(max(n - 1, 0), -1.0, 1.0)
+    if name == "uniform":
+        return mag * sgn, e
+    if name == "graded":
+        s = 2.0 ** (-20.0 * np.arange(n) / max(n, 1))
+        return mag * sgn * s, e * s[: max(n - 1, 0)]
+    raise KeyError(name)

@@ -164,6 +164,9 @@ def lib():
         L.tdc_ormtr.argtypes = [i64, i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
         L.tdc_syevd_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_syevd.argtypes = [i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
+    if hasattr(L, "tdc_bdsdc"):
+        L.tdc_bdsdc_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_bdsdc.argtypes = [i64, P, P, P, P, i64, P, i64, P, sz, ctypes.POINTER(Opts), P]
     if hasattr(L, "tdc_cauchy_gemm"):
         L.tdc_cauchy_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_cauchy_gemm.argtypes = [i64, i64, P, i64, P, P, P, P, P, P, i64, i32, ctypes.POINTER(Opts), P,
@@ -410,6 +413,27 @@ def syevd(A: torch.Tensor, opts: Opts | None = None, ws: torch.Tensor | None = N
     if check:
         _check("tdc_syevd (device status)", sync_status(stream))
     return lam[:n], Z
+
+
+def bdsdc(d: torch.Tensor, e: torch.Tensor, opts: Opts | None = None, stream=None, check: bool = False):
+    """SVD B = U diag(sigma) VT of the upper bidiagonal B (diagonal d, superdiagonal e,
+    device FP64) through the divide and conquer on the Golub-Kahan tridiagonal.  Returns
+    (sigma, U, VT): sigma descending, U and VT column-major n x n views."""
+    n = d.numel()
+    dev = d.device
+    sigma = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+    U = torch.empty(n, n, dtype=torch.float64, device=dev).t()
+    VT = torch.empty(n, n, dtype=torch.float64, device=dev).t()
+    b = ctypes.c_size_t(0)
+    _check("tdc_bdsdc_workspace_size", lib().tdc_bdsdc_workspace_size(n, ctypes.byref(opts) if opts else None,
+                                                                      ctypes.byref(b)))
+    ws = workspace(b.value, dev)
+    _check("tdc_bdsdc", lib().tdc_bdsdc(n, _ptr(d), _ptr(e), _ptr(sigma), _ptr(U), max(n, 1), _ptr(VT), max(n, 1),
+                                        _ptr(ws), ws.numel(), ctypes.byref(opts) if opts else None,
+                                        _stream(stream)))
+    if check:
+        _check("tdc_bdsdc (device status)", sync_status(stream))
+    return sigma[:n], U, VT
 
 
 def eig_backward(lam: torch.Tensor, Q: torch.Tensor, lam_bar=None, Q_bar=None, stream=None):

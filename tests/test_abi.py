@@ -125,3 +125,23 @@ def test_dense_symmetric_entry_points_check_arguments_on_the_host(lib):
     w = ctypes.c_size_t(0)
     assert lib.tdc_workspace_size(4000, None, ctypes.byref(w)) == 0
     assert sz[2].value > w.value
+
+
+def test_bdsdc_checks_arguments_on_the_host(lib):
+    from paper_2008_01990_gb300 import tdc
+    bogus = ctypes.c_void_p(0x1000)
+    big = 1 << 40
+    assert lib.tdc_bdsdc(-1, bogus, bogus, bogus, bogus, 1, bogus, 1, bogus, big, None, None) == -1
+    assert lib.tdc_bdsdc(0, None, None, None, None, 1, None, 1, None, 0, None, None) == 0
+    assert lib.tdc_bdsdc(4, None, bogus, bogus, bogus, 4, bogus, 4, bogus, big, None, None) == -2
+    assert lib.tdc_bdsdc(4, bogus, None, bogus, bogus, 4, bogus, 4, bogus, big, None, None) == -3
+    assert lib.tdc_bdsdc(4, bogus, bogus, None, bogus, 4, bogus, 4, bogus, big, None, None) == -4
+    assert lib.tdc_bdsdc(4, bogus, bogus, bogus, None, 4, bogus, 4, bogus, big, None, None) == -5
+    assert lib.tdc_bdsdc(4, bogus, bogus, bogus, bogus, 3, bogus, 4, bogus, big, None, None) == -6
+    assert lib.tdc_bdsdc(4, bogus, bogus, bogus, bogus, 4, None, 4, bogus, big, None, None) == -7
+    assert lib.tdc_bdsdc(4, bogus, bogus, bogus, bogus, 4, bogus, 3, bogus, big, None, None) == -8
+    assert lib.tdc_bdsdc(4, bogus, bogus, bogus, bogus, 4, bogus, 4, bogus, 16, None, None) == tdc.TDC_ENOWS
+    a, b = ctypes.c_size_t(0), ctypes.c_size_t(0)
+    assert lib.tdc_bdsdc_workspace_size(1000, None, ctypes.byref(a)) == 0
+    assert lib.tdc_workspace_size(2000, None, ctypes.byref(b)) == 0
+    assert a.value > b.value + 8 * 2000 * 2000
