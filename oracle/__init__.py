@@ -9,7 +9,9 @@ by :func:`build` into ``liboracle.so`` next to this file and called through
 ctypes with numpy arrays.  ``adjoint.py`` and ``srrsc.py`` hold the numpy
 oracles of the adjoint and of the SRRSC low-rank approximation; ``householder.py``
 the Householder reduction of a dense symmetric matrix to tridiagonal form and its
-back-transform; ``bidiag.py`` the bidiagonal SVD read off the Golub-Kahan tridiagonal.
+back-transform; ``bidiag.py`` the bidiagonal SVD read off the Golub-Kahan tridiagonal;
+``structured.py`` products with Toeplitz and Hankel operands written out from their
+generators.
 """
 from __future__ import annotations
 
