@@ -153,6 +153,11 @@ struct GemmSeg {
   // of the product is scaled back by a further 2^oexp[j] (NULL: none)
   int32_t aexp;
   const int32_t* oexp;
+  // Toeplitz / Hankel B from its 2n - 1 generators: B(k, j) = tgen[k - j + toff]
+  // (tkind 1) or tgen[k + j] (tkind 2); NULL: the Cauchy-like or dense B above
+  const double* tgen;
+  int64_t toff;
+  int32_t tkind;
 };
 
 struct Plan {
@@ -530,6 +535,11 @@ cudaError_t launch_orm_xexp(int64_t rows, int64_t ncols, const double* X, int64_
                             cudaStream_t s);
 cudaError_t launch_orm_step(const OrmStep& O, const double* A, int64_t lda, cudaStream_t s);
 size_t orm_z_smem(int kbp);
+// Toeplitz / Hankel products (tdc_toeplitz.cu): per-column exponents of the generated B
+// (the largest |t| of each column's window) and A's row-norm exponent
+cudaError_t launch_toeplitz_prep(int64_t m, int64_t n, const double* A, int64_t lda, const double* t, int kind,
+                                 double* winmax, int32_t* cexp, int32_t* oexp, int32_t* eA,
+                                 unsigned long long* maxsq, cudaStream_t s);
 // bidiagonal SVD through the Golub-Kahan tridiagonal (tdc_bdsdc.cu)
 cudaError_t launch_gk_build(int64_t n, const double* d, const double* e, double* td, double* te, cudaStream_t s);
 cudaError_t launch_gk_extract(int64_t n, const double* lam, const double* Q, int64_t ldq, double* sigma, double* U,

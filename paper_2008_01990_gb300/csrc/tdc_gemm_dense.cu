@@ -249,19 +249,21 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_gemm_tiny(Plan P, int level
   }
 }
 
-// The same FP64 product for one stand-alone segment (tdc_cauchy_gemm).
+// The same FP64 product for one stand-alone segment (tdc_cauchy_gemm; with tgen set, the
+// Toeplitz / Hankel products of tdc_toeplitz_gemm).
 __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
   __shared__ double As[BK][BM];
   __shared__ double Us[BK][BN];
   __shared__ double sDo[BN], sTau[BN], sS[BN];
-  __shared__ int sCol[BK];
+  __shared__ int sCol[BK], sP[BK];
   __shared__ double sDq[BK], sZq[BK];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int rtiles = (sg.rows + BM - 1) / BM, ctiles = (sg.K + BN - 1) / BN;
+  const bool gen_t = sg.tgen != nullptr;  // Toeplitz / Hankel B instead of the Cauchy-like one
   for (int64_t w = blockIdx.x; w < (int64_t)rtiles * ctiles; w += gridDim.x) {
     const int r0 = (int)(w / ctiles) * BM, j0 = (int)(w % ctiles) * BN;
     __syncthreads();
-    if (tid < BN) {
+    if (tid < BN && !gen_t) {
       const int j = j0 + tid;
       if (j < sg.K) { sDo[tid] = sg.D[sg.org[j]]; sTau[tid] = sg.tau[j]; sS[tid] = sg.scol[j]; }
       else { sDo[tid] = 0.0; sTau[tid] = 1.0; sS[tid] = 0.0; }
@@ -280,10 +282,11 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
         if (k < qhi) {
           const int p = sg.plist ? sg.plist[k] : k;
           sCol[tid] = sg.acol ? sg.acol[p] : p;
-          sDq[tid] = sg.D[p];
-          sZq[tid] = sg.zhat[p];
+          sP[tid] = p;
+          sDq[tid] = gen_t ? 0.0 : sg.D[p];
+          sZq[tid] = gen_t ? 0.0 : sg.zhat[p];
         } else {
-          sCol[tid] = -1; sDq[tid] = 0.0; sZq[tid] = 0.0;
+          sCol[tid] = -1; sP[tid] = -1; sDq[tid] = 0.0; sZq[tid] = 0.0;
         }
       }
       __syncthreads();
@@ -298,7 +301,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
       for (int e = 0; e < (BK * BN) / kThreads; ++e) {
         const int idx = tid + e * kThreads;
         const int k = idx / BN, c = idx % BN;
-        Us[k][c] = (sZq[k] * sS[c]) * rcp_nr((sDq[k] - sDo[c]) - sTau[c]);
+        if (gen_t) {
+          const int p = sP[k], j = j0 + c;
+          Us[k][c] = (p >= 0 && j < sg.K) ? sg.tgen[sg.tkind == 1 ? (int64_t)p - j + sg.toff : (int64_t)p + j]
+                                          : 0.0;
+        } else {
+          Us[k][c] = (sZq[k] * sS[c]) * rcp_nr((sDq[k] - sDo[c]) - sTau[c]);
+        }
       }
       __syncthreads();
 #pragma unroll

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
     const int jj = ct * BN + j;
     double dorg = 0.0, tj = 1.0, sj = 0.0;
     if (jj < sg.K) {
-      if (sg.Bd) {
+      if (sg.Bd || sg.tgen) {
         sj = sg.cexp ? pow2(-sg.cexp[jj]) : 1.0;
       } else {
         const int jr = sg.bcol ? sg.bcol[jj] : jj;
@@ -383,7 +383,9 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
       double u = 0.0;
       if (q < sg.kk && q >= sg.bq0 && jj < sg.K) {
         const int p = sg.plist ? sg.plist[q] : q;
-        u = sg.Bd ? sg.Bd[p + (int64_t)jj * sg.ldb] * sj : (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
+        if (sg.Bd) u = sg.Bd[p + (int64_t)jj * sg.ldb] * sj;
+        else if (sg.tgen) u = sg.tgen[sg.tkind == 1 ? (int64_t)p - jj + sg.toff : (int64_t)p + jj] * sj;
+        else u = (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
       }
       digits_bf16(u, S, dig[i]);
     }

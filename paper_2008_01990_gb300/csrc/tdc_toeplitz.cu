@@ -1,0 +1,78 @@
+// tdc_toeplitz.cu -- products C = A B with a Toeplitz or Hankel B given by its 2n - 1
+// generators (the further structured operands of Sections 1, 3.1 and 5: matrices of O(n)
+// parameters).  B(k, j) = t[k - j + n - 1] (Toeplitz) or t[k + j] (Hankel) is generated
+// inside the product kernels -- the FP64 tiles of k_gemm_dense_seg and the digit images of
+// k_split_b -- so only the generators travel to the GPU (the point made in Section 5).
+// For the split product, column j of B enters scaled by 2^-eb_j with 2^eb_j above its
+// largest |entry|: the maximum of |t| over the column's window of n consecutive
+// generators, from a table of maxima over 2^L-wide windows (2^L <= n < 2^(L+1)) built in
+// L doubling passes; A enters scaled by 2^-eA from its largest row norm, and the
+// product's column is scaled back by 2^eb_j (cexp) and 2^eA (oexp).
+#include "tdc_common.cuh"
+
+namespace tdc {
+
+namespace {
+__device__ __forceinline__ int exp_above_t(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
+}  // namespace
+
+// One block: w0 = |t|, then L passes w_{l}[i] = max(w_{l-1}[i], w_{l-1}[i + 2^(l-1)]) between
+// the two halves of `win` (2 x (2n - 1) doubles); eb[j] from the window of column j.
+__global__ void __launch_bounds__(1024) k_tp_windows(int64_t n, const double* t, int kind, double* win,
+                                                     int32_t* eb) {
+  const int64_t len = 2 * n - 1;
+  double* a = win;
+  double* b = win + len;
+  for (int64_t i = threadIdx.x; i < len; i += blockDim.x) a[i] = fabs(t[i]);
+  __syncthreads();
+  int64_t w = 1;
+  while (2 * w <= n) {
+    for (int64_t i = threadIdx.x; i + w < len; i += blockDim.x) b[i] = fmax(a[i], a[i + w]);
+    __syncthreads();
+    double* c = a;
+    a = b;
+    b = c;
+    w *= 2;
+  }
+  // a holds maxima over windows of width w (w <= n < 2w)
+  for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+    const int64_t s = kind == 1 ? n - 1 - j : j;
+    eb[j] = exp_above_t(fmax(a[s], a[s + n - w]));
+  }
+}
+
+// Largest squared row norm of A (m x n, lda) as the bits of a non-negative double.
+__global__ void __launch_bounds__(256) k_tp_rows(int64_t m, int64_t n, const double* A, int64_t lda,
+                                                unsigned long long* maxsq) {
+  double best = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int64_t k = 0; k < n; ++k) s = fma(A[i + k * lda], A[i + k * lda], s);
+    best = fmax(best, s);
+  }
+  for (int off = 16; off > 0; off >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, off));
+  if ((threadIdx.x & 31) == 0) atomicMax(maxsq, (unsigned long long)__double_as_longlong(best));
+}
+
+// eA with (largest row norm of A) 2^-eA < 1, and oexp[j] = eA: the product's columns are
+// scaled back by 2^cexp[j] (B's column scale) and then by 2^oexp[j] (A's scale).
+__global__ void __launch_bounds__(256) k_tp_exps(int64_t n, const unsigned long long* maxsq, int32_t* oexp,
+                                                int32_t* eA) {
+  const int e = exp_above_t(sqrt(__longlong_as_double((long long)*maxsq)));
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    oexp[j] = e;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *eA = e;
+}
+
+cudaError_t launch_toeplitz_prep(int64_t m, int64_t n, const double* A, int64_t lda, const double* t, int kind,
+                                 double* winmax, int32_t* cexp, int32_t* oexp, int32_t* eA,
+                                 unsigned long long* maxsq, cudaStream_t s) {
+  k_tp_windows<<<1, 1024, 0, s>>>(n, t, kind, winmax, cexp);
+  cudaError_t e = cudaMemsetAsync(maxsq, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  k_tp_rows<<<(unsigned)std::min<int64_t>(1024, (m + 255) / 256), 256, 0, s>>>(m, n, A, lda, maxsq);
+  k_tp_exps<<<(unsigned)std::min<int64_t>(1024, (n + 255) / 256), 256, 0, s>>>(n, maxsq, oexp, eA);
+  return cudaGetLastError();
+}
+
+}  // namespace tdc

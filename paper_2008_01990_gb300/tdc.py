@@ -164,6 +164,9 @@ def lib():
         L.tdc_ormtr.argtypes = [i64, i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
         L.tdc_syevd_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_syevd.argtypes = [i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
+    if hasattr(L, "tdc_toeplitz_gemm"):
+        L.tdc_toeplitz_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_toeplitz_gemm.argtypes = [i64, i64, P, i64, i32, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
     if hasattr(L, "tdc_bdsdc"):
         L.tdc_bdsdc_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_bdsdc.argtypes = [i64, P, P, P, P, i64, P, i64, P, sz, ctypes.POINTER(Opts), P]
@@ -413,6 +416,29 @@ def syevd(A: torch.Tensor, opts: Opts | None = None, ws: torch.Tensor | None = N
     if check:
         _check("tdc_syevd (device status)", sync_status(stream))
     return lam[:n], Z
+
+
+TOEPLITZ, HANKEL = 1, 2
+
+
+def toeplitz_gemm(A: torch.Tensor, t: torch.Tensor, kind: int = TOEPLITZ, mode: int = MERGE_DENSE,
+                  opts: Opts | None = None, stream=None, check: bool = False) -> torch.Tensor:
+    """C = A * B with B the n x n Toeplitz (B_kj = t[k - j + n - 1]) or Hankel (B_kj =
+    t[k + j]) matrix of the 2n - 1 generators t; A a column-major m x n view (device FP64);
+    mode MERGE_DENSE (FP64) or MERGE_SPLIT (BF16 digit products on the tensor cores)."""
+    m, n = A.shape
+    lda = A.stride(1) if n > 1 else max(m, 1)
+    C = torch.empty(n, m, dtype=torch.float64, device=A.device).t()
+    b = ctypes.c_size_t(0)
+    _check("tdc_toeplitz_gemm_workspace_size",
+           lib().tdc_toeplitz_gemm_workspace_size(m, n, mode, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    ws = workspace(b.value, A.device)
+    _check("tdc_toeplitz_gemm", lib().tdc_toeplitz_gemm(m, n, _ptr(A), max(lda, m, 1), kind, _ptr(t), _ptr(C),
+                                                        max(m, 1), mode, ctypes.byref(opts) if opts else None,
+                                                        _ptr(ws), ws.numel(), _stream(stream)))
+    if check:
+        _check("tdc_toeplitz_gemm (device status)", sync_status(stream))
+    return C
 
 
 def bdsdc(d: torch.Tensor, e: torch.Tensor, opts: Opts | None = None, stream=None, check: bool = False):

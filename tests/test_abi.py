@@ -145,3 +145,21 @@ def test_bdsdc_checks_arguments_on_the_host(lib):
     assert lib.tdc_bdsdc_workspace_size(1000, None, ctypes.byref(a)) == 0
     assert lib.tdc_workspace_size(2000, None, ctypes.byref(b)) == 0
     assert a.value > b.value + 8 * 2000 * 2000
+
+
+def test_toeplitz_gemm_checks_arguments_on_the_host(lib):
+    from paper_2008_01990_gb300 import tdc
+    bogus = ctypes.c_void_p(0x1000)
+    big = 1 << 40
+    f = lib.tdc_toeplitz_gemm
+    assert f(-1, 4, bogus, 1, 1, bogus, bogus, 1, 0, None, bogus, big, None) == -1
+    assert f(4, -1, bogus, 4, 1, bogus, bogus, 4, 0, None, bogus, big, None) == -2
+    assert f(0, 4, None, 1, 1, None, None, 1, 0, None, None, 0, None) == 0
+    assert f(4, 4, None, 4, 1, bogus, bogus, 4, 0, None, bogus, big, None) == -3
+    assert f(4, 4, bogus, 3, 1, bogus, bogus, 4, 0, None, bogus, big, None) == -4
+    assert f(4, 4, bogus, 4, 3, bogus, bogus, 4, 0, None, bogus, big, None) == -5
+    assert f(4, 4, bogus, 4, 1, None, bogus, 4, 0, None, bogus, big, None) == -6
+    assert f(4, 4, bogus, 4, 1, bogus, None, 4, 0, None, bogus, big, None) == -7
+    assert f(4, 4, bogus, 4, 1, bogus, bogus, 3, 0, None, bogus, big, None) == -8
+    assert f(4, 4, bogus, 4, 1, bogus, bogus, 4, tdc.MERGE_STRUCTURED, None, bogus, big, None) == -9
+    assert f(4, 4, bogus, 4, 1, bogus, bogus, 4, tdc.MERGE_DENSE, None, bogus, 8, None) == tdc.TDC_ENOWS
