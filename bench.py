@@ -332,6 +332,50 @@ def run_example1(args, n):
     return out
 
 
+def run_structured_products(args, n):
+    """The further structured operands: C = A B with B Toeplitz (t[k - j + n - 1]) or
+    Hankel (t[k + j]) from 2n - 1 generators uniform(-1, 1), A uniform(-1, 1) n x n; FP64
+    and split modes timed with CUDA events after a warm-up, error against the FP64 dense
+    product on sampled columns; and the bidiagonal SVD of order n (uniform family)."""
+    import torch
+    from paper_2008_01990_gb300 import inputs, tdc
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev)
+    g.manual_seed(n)
+    A = (torch.rand(n, n, dtype=torch.float64, device=dev, generator=g) * 2 - 1).t()
+    t = torch.tensor(inputs.SplitMix64(n).uniform(2 * n - 1, -1.0, 1.0), device=dev)
+    cols = torch.tensor(np.sort(np.random.default_rng(0).choice(n, 64, replace=False)), device=dev)
+    k = torch.arange(n, device=dev)
+    out = {"workload": "Toeplitz / Hankel products n=%d and the bidiagonal SVD" % n, "products": {}}
+    for kind, kname in ((tdc.TOEPLITZ, "toeplitz"), (tdc.HANKEL, "hankel")):
+        idx = (k[:, None] - cols[None, :] + n - 1) if kind == tdc.TOEPLITZ else (k[:, None] + cols[None, :])
+        Bs = t[idx]
+        Cref = A @ Bs  # FP64 reference on the sampled columns (a library matmul, verification only)
+        scale = torch.linalg.norm(A, dim=1)[:, None] * torch.linalg.norm(Bs, dim=0)[None, :]
+        for mname, md in (("dense", tdc.MERGE_DENSE), ("split", tdc.MERGE_SPLIT)):
+            C = tdc.toeplitz_gemm(A, t, kind, md, check=True)
+            steps = 1 if mname == "dense" else max(1, min(args.steps, 5))
+            ms = _event_ms(lambda: tdc.toeplitz_gemm(A, t, kind, md), steps)
+            err = float(torch.max(torch.abs(C[:, cols] - Cref) / scale).item())
+            out["products"]["%s_%s" % (kname, mname)] = {
+                "ms": ms, "steps": steps, "max_err_over_rownorm_colnorm": err,
+                "fp64_equivalent_tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
+            del C
+    d_np, e_np = inputs.bidiag_family("uniform", n, seed=n)
+    d, e = torch.tensor(d_np, device=dev), torch.tensor(e_np, device=dev)
+    s, U, VT = tdc.bdsdc(d, e, check=True)
+    ms = _event_ms(lambda: tdc.bdsdc(d, e), max(1, min(args.steps, 3)))
+    cs = cols[:64]
+    V = VT.t()
+    Bv = d[:, None] * V[:, cs]
+    Bv[:-1] += e[:, None] * V[1:, cs]
+    res = torch.abs(Bv - U[:, cs] * s[cs][None, :]).sum(dim=0).max().item() / (n * s[0].item() * EPS)
+    orth = torch.abs(U.t() @ U - torch.eye(n, dtype=U.dtype, device=dev)).sum(dim=0).max().item() / (n * EPS)
+    out["bdsdc"] = {"ms": ms, "residual_sampled": res, "orthogonality_U": orth,
+                    "note": "tdc_eig on the order-2n Golub-Kahan tridiagonal"}
+    return out
+
+
 def _event_ms(fn, steps, stream=None):
     """Average device time of fn over `steps` calls, CUDA events on `stream`."""
     import torch
@@ -927,7 +971,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
                                                           "example1_8192", "example1_16384", "example1_32768",
-                                                          "batched4096", "backward256", "dense4096", "dense8192", "clement30000",
+                                                          "batched4096", "backward256", "dense4096", "dense8192", "structured16384",
+                                                          "clement30000",
                                                           "hermite30000", "sht30000"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split", "structured_split"])
     ap.add_argument("--no-compare", action="store_true")
@@ -954,6 +999,9 @@ def main():
         return 0
     if args.workload == "backward256":
         print(json.dumps(config_c5(args, steps=args.steps, warmup=args.warmup)), flush=True)
+        return 0
+    if args.workload == "structured16384":
+        print(json.dumps(run_structured_products(args, 16384)), flush=True)
         return 0
     if args.workload.startswith("dense"):
         print(json.dumps(config_dense(args, n=int(args.workload[5:]), steps=args.steps)), flush=True)
