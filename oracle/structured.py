@@ -1,4 +1,5 @@
-"""Oracle for products with Toeplitz and Hankel operands given by their generators.
+"""Oracle for products with Toeplitz, Hankel, Vandermonde and DFT operands given by their
+generators.
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -7,24 +8,47 @@ operands of its product (the matrices of O(n) parameters, Section 1; the remarks
 Section 3.1 and Section 5).  An n x n Toeplitz matrix is constant along its diagonals,
 B(k, j) = t[k - j + n - 1] with t of length 2n - 1 (t[n - 1 + i] on the i-th
 subdiagonal); a Hankel matrix is constant along its anti-diagonals, B(k, j) = t[k + j].
-The oracle writes the matrix out from that definition and multiplies with the C
-oracle's plain triple loop.
+A Vandermonde matrix of nodes x has B(k, j) = x_k^j; the DFT matrix of order n has
+F(k, j) = exp(-2 pi i k j / n), whose real and imaginary parts are cos(2 pi k j / n) and
+-sin(2 pi k j / n).  The oracle writes the matrix out from that definition and multiplies
+with the C oracle's plain triple loop (the DFT product as its two real parts).
 """
 from __future__ import annotations
 
 import numpy as np
 
-TOEPLITZ, HANKEL = 1, 2
+TOEPLITZ, HANKEL, VANDERMONDE = 1, 2, 3
 
 
 def dense(t, n, kind):
-    """The n x n matrix of generators t (length 2n - 1), entry by entry."""
+    """The n x n matrix of generators t (length 2n - 1; the n nodes for Vandermonde), entry
+    by entry."""
     t = np.asarray(t, dtype=np.float64)
     B = np.empty((n, n))
     for k in range(n):
         for j in range(n):
-            B[k, j] = t[k - j + n - 1] if kind == TOEPLITZ else t[k + j]
+            if kind == TOEPLITZ:
+                B[k, j] = t[k - j + n - 1]
+            elif kind == HANKEL:
+                B[k, j] = t[k + j]
+            else:
+                B[k, j] = t[k] ** j
     return B
+
+
+def dft_parts(n):
+    """Real and imaginary parts of the DFT matrix F(k, j) = exp(-2 pi i k j / n)."""
+    k = np.arange(n)
+    ang = 2.0 * np.pi * np.outer(k, k) / n
+    return np.cos(ang), -np.sin(ang)
+
+
+def dft_product(A):
+    """(Re, Im) of C = A F, F the DFT matrix of order n = A's column count."""
+    from . import gemm
+    A = np.asarray(A, dtype=np.float64)
+    Fr, Fi = dft_parts(A.shape[1])
+    return gemm(A, Fr), gemm(A, Fi)
 
 
 def product(A, t, kind):
