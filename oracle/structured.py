@@ -39,7 +39,9 @@ def dense(t, n, kind):
 def dft_parts(n):
     """Real and imaginary parts of the DFT matrix F(k, j) = exp(-2 pi i k j / n)."""
     k = np.arange(n)
-    ang = 2.0 * np.pi * np.outer(k, k) / n
+    # omega^(kj) with omega = exp(-2 pi i / n) depends on kj mod n only; reducing it in
+    # integer arithmetic keeps the angle below 2 pi (no rounding of large arguments)
+    ang = 2.0 * np.pi * (np.outer(k, k) % n) / n
     return np.cos(ang), -np.sin(ang)
 
 

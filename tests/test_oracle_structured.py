@@ -28,11 +28,14 @@ def test_vandermonde_matches_library():
     assert np.allclose(so.dense(x, 9, so.VANDERMONDE), np.vander(x, 9, increasing=True), rtol=1e-15, atol=0)
 
 
-def test_dft_matches_library_fft(orc):
-    A = np.random.default_rng(4).uniform(-1, 1, (7, 48))
+@pytest.mark.parametrize("n", [48, 1000])
+def test_dft_matches_library_fft(orc, n):
+    A = np.random.default_rng(4).uniform(-1, 1, (7, n))
     re, im = so.dft_product(A)
     F = np.fft.fft(A, axis=1)  # sum_k A(i, k) exp(-2 pi i k j / n)
-    assert np.max(np.abs(re - F.real)) <= 1e-13 and np.max(np.abs(im - F.imag)) <= 1e-13
+    scale = np.linalg.norm(A, axis=1)[:, None] * np.sqrt(n)
+    assert np.max(np.abs(re - F.real) / scale) <= 4e-16 * np.log2(n)
+    assert np.max(np.abs(im - F.imag) / scale) <= 4e-16 * np.log2(n)
 
 
 def test_product(orc):
