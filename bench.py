@@ -353,9 +353,9 @@ def run_structured_products(args, n):
         Cref = A @ Bs  # FP64 reference on the sampled columns (a library matmul, verification only)
         scale = torch.linalg.norm(A, dim=1)[:, None] * torch.linalg.norm(Bs, dim=0)[None, :]
         for mname, md in (("dense", tdc.MERGE_DENSE), ("split", tdc.MERGE_SPLIT)):
-            C = tdc.toeplitz_gemm(A, t, kind, md, check=True)
+            C = tdc.structured_gemm(A, t, kind, md, check=True)
             steps = 1 if mname == "dense" else max(1, min(args.steps, 5))
-            ms = _event_ms(lambda: tdc.toeplitz_gemm(A, t, kind, md), steps)
+            ms = _event_ms(lambda: tdc.structured_gemm(A, t, kind, md), steps)
             err = float(torch.max(torch.abs(C[:, cols] - Cref) / scale).item())
             out["products"]["%s_%s" % (kname, mname)] = {
                 "ms": ms, "steps": steps, "max_err_over_rownorm_colnorm": err,

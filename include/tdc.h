@@ -317,21 +317,36 @@ int tdc_syevd_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
 int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t ldz, void* ws, size_t ws_bytes,
               const tdc_opts* o, tdc_stream_t stream);
 
-/* Toeplitz / Hankel products (the further structured operands of Sections 1, 3.1 and 5,
- * matrices given by O(n) parameters): C = A * B with the n x n B generated from t[2n-1]
- * (device FP64): B(k, j) = t[k - j + n - 1] for TDC_TOEPLITZ (t[n-1+i] on the i-th
- * subdiagonal, t[n-1-i] on the i-th superdiagonal), B(k, j) = t[k + j] for TDC_HANKEL.
- * A is m x n (lda), C m x n (ldc).  B never exists in memory: the FP64 tiles
- * (TDC_MERGE_DENSE) and the split product's digit images (TDC_MERGE_SPLIT, o->split_slices
- * digits; A and each column of B scaled by powers of two so that every operand entry is
- * below 1, the product scaled back) generate it from t.  ws of
- * tdc_toeplitz_gemm_workspace_size(m, n, mode, o) bytes.  Errors: -1 m, -2 n, -3 A, -4 lda,
- * -5 kind, -6 t, -7 C, -8 ldc, -9 mode, -10 options, TDC_ENOWS, TDC_ECUDA. */
+/* Products with a structured operand given by generators (the further structured
+ * matrices of Sections 1, 3.1 and 5, given by O(n) parameters): C = A * B, A m x n (lda),
+ * C m x n (ldc), the n x n B generated from t (device FP64):
+ *   TDC_TOEPLITZ     B(k, j) = t[k - j + n - 1], t[2n-1] (t[n-1+i] on the i-th
+ *                    subdiagonal, t[n-1-i] on the i-th superdiagonal)
+ *   TDC_HANKEL       B(k, j) = t[k + j], t[2n-1]
+ *   TDC_VANDERMONDE  B(k, j) = t[k]^j, the n nodes t[n] (powers by repeated squaring;
+ *                    max|t|^(n-1) must stay below 2^1000)
+ * B never exists in memory: the FP64 tiles (TDC_MERGE_DENSE) and the split product's digit
+ * images (TDC_MERGE_SPLIT, o->split_slices digits; A and each column of B scaled by powers
+ * of two so that every operand entry is at most 1, the product scaled back) generate it.
+ * ws of tdc_structured_gemm_workspace_size(m, n, mode, o) bytes.  Errors: -1 m, -2 n, -3 A,
+ * -4 lda, -5 kind, -6 t, -7 C, -8 ldc, -9 mode, -10 options, TDC_ENOWS, TDC_ECUDA. */
 #define TDC_TOEPLITZ 1
 #define TDC_HANKEL 2
-int tdc_toeplitz_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes);
-int tdc_toeplitz_gemm(int64_t m, int64_t n, const double* A, int64_t lda, int32_t kind, const double* t, double* C,
-                      int64_t ldc, int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream);
+#define TDC_VANDERMONDE 3
+int tdc_structured_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes);
+int tdc_structured_gemm(int64_t m, int64_t n, const double* A, int64_t lda, int32_t kind, const double* t, double* C,
+                        int64_t ldc, int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes,
+                        tdc_stream_t stream);
+
+/* tdc_dft_gemm: C = A F with F the DFT matrix of order n, F(k, j) = exp(-2 pi i k j / n), for
+ * a real A (m x n, lda): Cre = A Re(F), Cim = A Im(F) (m x n each, ldc), the two real
+ * operands cos(2 pi m / n) and -sin(2 pi m / n) generated from n-entry tables at
+ * m = (k j) mod n.  Modes and workspace as tdc_structured_gemm (ws of
+ * tdc_dft_gemm_workspace_size bytes).  Errors: -1 m, -2 n, -3 A, -4 lda, -5 Cre, -6 Cim,
+ * -7 ldc, -8 mode, -9 options, TDC_ENOWS, TDC_ECUDA. */
+int tdc_dft_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes);
+int tdc_dft_gemm(int64_t m, int64_t n, const double* A, int64_t lda, double* Cre, double* Cim, int64_t ldc,
+                 int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream);
 
 /* tdc_bdsdc: SVD B = U diag(sigma) VT of the n x n upper bidiagonal B (diagonal d[n],
  * superdiagonal e[n-1], device FP64, not modified) through the divide and conquer (the

@@ -1683,53 +1683,27 @@ int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t
   return ormtr_run(n, n, A, lda, tau, Z, ldz, rest, op, st, cs);
 }
 
-// Toeplitz / Hankel products: B generated from its generators inside the FP64 tiles or
-// the split product's digit images.
-static size_t toeplitz_extra(int64_t n) {
+// Products with a structured B given by generators (Toeplitz, Hankel, Vandermonde, the
+// DFT's two real parts): B generated inside the FP64 tiles or the split product's digit
+// images.
+static size_t operand_extra(int64_t n) {
   return align_up(2 * sizeof(double) * (size_t)std::max<int64_t>(2 * n - 1, 1)) +
          2 * align_up(sizeof(int32_t) * (size_t)std::max<int64_t>(n, 1)) + 256;
 }
 
-int tdc_toeplitz_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes) {
-  tdc_opts op;
-  tdc_default_opts(&op);
-  if (o) op = *o;
-  if (m < 0 || m > 0x7fffffff) return -1;
-  if (n < 0 || n > 0x7fffffff) return -2;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -3;
-  if (validate_opts(&op)) return -4;
-  if (!bytes) return -5;
+static size_t operand_ws(int64_t m, int64_t n, int32_t mode, const tdc_opts& op) {
   size_t b = align_up(2 * sizeof(GemmSeg));
   if (mode == TDC_MERGE_SPLIT)
     b += align_up(sizeof(__nv_bfloat16) * (size_t)cauchy_split_elems(m, n, op.split_slices, nullptr)) +
-         toeplitz_extra(n);
-  *bytes = b + 256;
-  return TDC_OK;
+         operand_extra(n);
+  return b + 256;
 }
 
-int tdc_toeplitz_gemm(int64_t m, int64_t n, const double* A, int64_t lda, int32_t kind, const double* t, double* C,
-                      int64_t ldc, int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream) {
-  tdc_opts op;
-  tdc_default_opts(&op);
-  if (o) op = *o;
-  if (m < 0 || m > 0x7fffffff) return -1;
-  if (n < 0 || n > 0x7fffffff) return -2;
-  if (m == 0 || n == 0) return TDC_OK;
-  if (!A) return -3;
-  if (lda < m) return -4;
-  if (kind != TDC_TOEPLITZ && kind != TDC_HANKEL) return -5;
-  if (!t) return -6;
-  if (!C) return -7;
-  if (ldc < m) return -8;
-  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -9;
-  if (validate_opts(&op)) return -10;
-  size_t need = 0;
-  tdc_toeplitz_gemm_workspace_size(m, n, mode, &op, &need);
-  if (!ws || ws_bytes < need) return TDC_ENOWS;
-  cudaStream_t cs = (cudaStream_t)stream;
-  int* st = begin_status(cs);
-  if (!st) return TDC_ECUDA;
-  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+// C = A B for B of kind 1-4 (struct_entry) from tgen (toff: Toeplitz n - 1, DFT n), at
+// base (aligned) of operand_ws bytes.
+static cudaError_t operand_product(int64_t m, int64_t n, const double* A, int64_t lda, int kind, const double* tgen,
+                                   int64_t toff, double* C, int64_t ldc, int32_t mode, const tdc_opts& op,
+                                   char* base, int* st, cudaStream_t cs) {
   GemmSeg* segs = (GemmSeg*)base;
   GemmSeg sg;
   memset(&sg, 0, sizeof(sg));
@@ -1741,46 +1715,120 @@ int tdc_toeplitz_gemm(int64_t m, int64_t n, const double* A, int64_t lda, int32_
   sg.K = (int32_t)n;
   sg.C = C;
   sg.ldc = ldc;
-  sg.tgen = t;
+  sg.tgen = tgen;
   sg.tkind = kind;
-  sg.toff = n - 1;
-  cudaError_t err = cudaSuccess;
-  if (mode == TDC_MERGE_DENSE) {
-    err = launch_seg_dense(sg, cs);
-  } else {
-    const int S = op.split_slices;
-    int64_t a_el = 0;
-    const int64_t tot = cauchy_split_elems(m, n, S, &a_el);
-    char* p = base + align_up(2 * sizeof(GemmSeg));
-    __nv_bfloat16* img = (__nv_bfloat16*)p;
-    p += align_up(sizeof(__nv_bfloat16) * (size_t)tot);
-    double* win = (double*)p;
-    p += align_up(2 * sizeof(double) * (size_t)(2 * n - 1));
-    int32_t* cexp = (int32_t*)p;
-    p += align_up(sizeof(int32_t) * (size_t)n);
-    int32_t* oexp = (int32_t*)p;
-    p += align_up(sizeof(int32_t) * (size_t)n);
-    unsigned long long* maxsq = (unsigned long long*)p;
-    int32_t* eA = (int32_t*)(p + 64);
-    err = launch_toeplitz_prep(m, n, A, lda, t, kind, win, cexp, oexp, eA, maxsq, cs);
-    const int64_t RT = cdiv64(m, kSplitBM), KB = cdiv64(n, kSplitBK), CT = cdiv64(n, kSplitBN);
-    sg.cexp = cexp;
-    sg.oexp = oexp;
-    sg.a_img = 0;
-    sg.b_img = a_el;
-    GemmSeg last;
-    memset(&last, 0, sizeof(last));
-    last.it_a = RT * KB;
-    last.it_b = CT * KB;
-    last.it_t = RT * CT;
-    last.a_img = tot;
-    if (err == cudaSuccess) {
-      k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
-      err = cudaGetLastError();
-    }
-    if (err == cudaSuccess) err = launch_cauchy_like_patch(segs, eA, cs);
-    if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, op.split_chunk_k / 16, cs);
+  sg.toff = toff;
+  if (mode == TDC_MERGE_DENSE) return launch_seg_dense(sg, cs);
+  const int S = op.split_slices;
+  int64_t a_el = 0;
+  const int64_t tot = cauchy_split_elems(m, n, S, &a_el);
+  char* p = base + align_up(2 * sizeof(GemmSeg));
+  __nv_bfloat16* img = (__nv_bfloat16*)p;
+  p += align_up(sizeof(__nv_bfloat16) * (size_t)tot);
+  double* win = (double*)p;
+  p += align_up(2 * sizeof(double) * (size_t)(2 * n - 1));
+  int32_t* cexp = (int32_t*)p;
+  p += align_up(sizeof(int32_t) * (size_t)n);
+  int32_t* oexp = (int32_t*)p;
+  p += align_up(sizeof(int32_t) * (size_t)n);
+  unsigned long long* maxsq = (unsigned long long*)p;
+  int32_t* eA = (int32_t*)(p + 64);
+  cudaError_t err = launch_operand_prep(m, n, A, lda, tgen, kind, win, cexp, oexp, eA, maxsq, cs);
+  const int64_t RT = cdiv64(m, kSplitBM), KB = cdiv64(n, kSplitBK), CT = cdiv64(n, kSplitBN);
+  sg.cexp = cexp;
+  sg.oexp = oexp;
+  sg.a_img = 0;
+  sg.b_img = a_el;
+  GemmSeg last;
+  memset(&last, 0, sizeof(last));
+  last.it_a = RT * KB;
+  last.it_b = CT * KB;
+  last.it_t = RT * CT;
+  last.a_img = tot;
+  if (err == cudaSuccess) {
+    k_write_segs<<<1, 32, 0, cs>>>(sg, last, segs);
+    err = cudaGetLastError();
   }
+  if (err == cudaSuccess) err = launch_cauchy_like_patch(segs, eA, cs);
+  if (err == cudaSuccess) err = launch_seg_split(segs, 1, S, st, op.spin_budget, img, op.split_chunk_k / 16, cs);
+  return err;
+}
+
+int tdc_structured_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0 || m > 0x7fffffff) return -1;
+  if (n < 0 || n > 0x7fffffff) return -2;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -3;
+  if (validate_opts(&op)) return -4;
+  if (!bytes) return -5;
+  *bytes = operand_ws(m, n, mode, op);
+  return TDC_OK;
+}
+
+int tdc_structured_gemm(int64_t m, int64_t n, const double* A, int64_t lda, int32_t kind, const double* t, double* C,
+                        int64_t ldc, int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes,
+                        tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0 || m > 0x7fffffff) return -1;
+  if (n < 0 || n > 0x7fffffff) return -2;
+  if (m == 0 || n == 0) return TDC_OK;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (kind != TDC_TOEPLITZ && kind != TDC_HANKEL && kind != TDC_VANDERMONDE) return -5;
+  if (!t) return -6;
+  if (!C) return -7;
+  if (ldc < m) return -8;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -9;
+  if (validate_opts(&op)) return -10;
+  if (!ws || ws_bytes < operand_ws(m, n, mode, op)) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  return operand_product(m, n, A, lda, kind, t, n - 1, C, ldc, mode, op, base, st, cs) == cudaSuccess ? TDC_OK
+                                                                                                   : TDC_ECUDA;
+}
+
+int tdc_dft_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_opts* o, size_t* bytes) {
+  const int r = tdc_structured_gemm_workspace_size(m, n, mode, o, bytes);
+  if (r != TDC_OK) return r;
+  *bytes += 2 * align_up(sizeof(double) * (size_t)std::max<int64_t>(n, 1));
+  return TDC_OK;
+}
+
+int tdc_dft_gemm(int64_t m, int64_t n, const double* A, int64_t lda, double* Cre, double* Cim, int64_t ldc,
+                 int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (m < 0 || m > 0x7fffffff) return -1;
+  if (n < 0 || n > 0x7fffffff) return -2;
+  if (m == 0 || n == 0) return TDC_OK;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (!Cre) return -5;
+  if (!Cim) return -6;
+  if (ldc < m) return -7;
+  if (mode != TDC_MERGE_DENSE && mode != TDC_MERGE_SPLIT) return -8;
+  if (validate_opts(&op)) return -9;
+  size_t need = 0;
+  tdc_dft_gemm_workspace_size(m, n, mode, &op, &need);
+  if (!ws || ws_bytes < need) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  const size_t tb = align_up(sizeof(double) * (size_t)n);
+  double* cosv = (double*)base;
+  double* msinv = (double*)(base + tb);
+  char* rest = base + 2 * tb;
+  cudaError_t err = launch_dft_tables(n, cosv, msinv, cs);
+  if (err == cudaSuccess) err = operand_product(m, n, A, lda, 4, cosv, n, Cre, ldc, mode, op, rest, st, cs);
+  if (err == cudaSuccess) err = operand_product(m, n, A, lda, 4, msinv, n, Cim, ldc, mode, op, rest, st, cs);
   return err == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 

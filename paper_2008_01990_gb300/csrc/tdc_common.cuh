@@ -153,12 +153,28 @@ struct GemmSeg {
   // of the product is scaled back by a further 2^oexp[j] (NULL: none)
   int32_t aexp;
   const int32_t* oexp;
-  // Toeplitz / Hankel B from its 2n - 1 generators: B(k, j) = tgen[k - j + toff]
-  // (tkind 1) or tgen[k + j] (tkind 2); NULL: the Cauchy-like or dense B above
+  // structured B from generators (struct_entry below); NULL: the Cauchy-like or dense B
   const double* tgen;
   int64_t toff;
   int32_t tkind;
 };
+
+// Entry (k, j) of a structured B given by generators: Toeplitz tgen[k - j + toff] (kind 1),
+// Hankel tgen[k + j] (2), Vandermonde tgen[k]^j by binary powering (3), or a cyclic table
+// tgen[(k j) mod toff] (4: the real or imaginary part of the DFT matrix of order toff).
+__device__ __forceinline__ double struct_entry(const GemmSeg& sg, int64_t k, int64_t j) {
+  if (sg.tkind == 1) return sg.tgen[k - j + sg.toff];
+  if (sg.tkind == 2) return sg.tgen[k + j];
+  if (sg.tkind == 3) {
+    double x = sg.tgen[k], r = 1.0;
+    for (int64_t e = j; e > 0; e >>= 1) {
+      if (e & 1) r *= x;
+      x *= x;
+    }
+    return r;
+  }
+  return sg.tgen[(k * j) % sg.toff];
+}
 
 struct Plan {
   const Problem* prob;  // sorted problems (device)
@@ -535,11 +551,12 @@ cudaError_t launch_orm_xexp(int64_t rows, int64_t ncols, const double* X, int64_
                             cudaStream_t s);
 cudaError_t launch_orm_step(const OrmStep& O, const double* A, int64_t lda, cudaStream_t s);
 size_t orm_z_smem(int kbp);
-// Toeplitz / Hankel products (tdc_toeplitz.cu): per-column exponents of the generated B
-// (the largest |t| of each column's window) and A's row-norm exponent
-cudaError_t launch_toeplitz_prep(int64_t m, int64_t n, const double* A, int64_t lda, const double* t, int kind,
-                                 double* winmax, int32_t* cexp, int32_t* oexp, int32_t* eA,
-                                 unsigned long long* maxsq, cudaStream_t s);
+// structured operands (tdc_operands.cu): per-column exponents of the generated B and A's
+// row-norm exponent; the DFT tables
+cudaError_t launch_operand_prep(int64_t m, int64_t n, const double* A, int64_t lda, const double* t, int kind,
+                                double* winmax, int32_t* cexp, int32_t* oexp, int32_t* eA,
+                                unsigned long long* maxsq, cudaStream_t s);
+cudaError_t launch_dft_tables(int64_t n, double* cosv, double* msinv, cudaStream_t s);
 // bidiagonal SVD through the Golub-Kahan tridiagonal (tdc_bdsdc.cu)
 cudaError_t launch_gk_build(int64_t n, const double* d, const double* e, double* td, double* te, cudaStream_t s);
 cudaError_t launch_gk_extract(int64_t n, const double* lam, const double* Q, int64_t ldq, double* sigma, double* U,

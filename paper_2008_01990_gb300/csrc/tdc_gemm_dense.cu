@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(32 * kTinyWarps) k_gemm_tiny(Plan P, int level
 }
 
 // The same FP64 product for one stand-alone segment (tdc_cauchy_gemm; with tgen set, the
-// Toeplitz / Hankel products of tdc_toeplitz_gemm).
+// structured-operand products of tdc_structured_gemm and tdc_dft_gemm).
 __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
   __shared__ double As[BK][BM];
   __shared__ double Us[BK][BN];
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
   __shared__ double sDq[BK], sZq[BK];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   const int rtiles = (sg.rows + BM - 1) / BM, ctiles = (sg.K + BN - 1) / BN;
-  const bool gen_t = sg.tgen != nullptr;  // Toeplitz / Hankel B instead of the Cauchy-like one
+  const bool gen_t = sg.tgen != nullptr;  // a structured B from generators instead of the Cauchy-like one
   for (int64_t w = blockIdx.x; w < (int64_t)rtiles * ctiles; w += gridDim.x) {
     const int r0 = (int)(w / ctiles) * BM, j0 = (int)(w % ctiles) * BN;
     __syncthreads();
@@ -303,8 +303,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gemm_dense_seg(GemmSeg sg) {
         const int k = idx / BN, c = idx % BN;
         if (gen_t) {
           const int p = sP[k], j = j0 + c;
-          Us[k][c] = (p >= 0 && j < sg.K) ? sg.tgen[sg.tkind == 1 ? (int64_t)p - j + sg.toff : (int64_t)p + j]
-                                          : 0.0;
+          Us[k][c] = (p >= 0 && j < sg.K) ? struct_entry(sg, p, j) : 0.0;
         } else {
           Us[k][c] = (sZq[k] * sS[c]) * rcp_nr((sDq[k] - sDo[c]) - sTau[c]);
         }

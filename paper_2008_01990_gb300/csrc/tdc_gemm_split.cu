@@ -384,7 +384,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
       if (q < sg.kk && q >= sg.bq0 && jj < sg.K) {
         const int p = sg.plist ? sg.plist[q] : q;
         if (sg.Bd) u = sg.Bd[p + (int64_t)jj * sg.ldb] * sj;
-        else if (sg.tgen) u = sg.tgen[sg.tkind == 1 ? (int64_t)p - jj + sg.toff : (int64_t)p + jj] * sj;
+        else if (sg.tgen) u = struct_entry(sg, p, jj) * sj;
         else u = (sg.zhat[p] * sj) * rcp_nr((sg.D[p] - dorg) - tj);
       }
       digits_bf16(u, S, dig[i]);

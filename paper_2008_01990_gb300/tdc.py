@@ -164,9 +164,11 @@ def lib():
         L.tdc_ormtr.argtypes = [i64, i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
         L.tdc_syevd_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_syevd.argtypes = [i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
-    if hasattr(L, "tdc_toeplitz_gemm"):
-        L.tdc_toeplitz_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
-        L.tdc_toeplitz_gemm.argtypes = [i64, i64, P, i64, i32, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
+    if hasattr(L, "tdc_structured_gemm"):
+        L.tdc_structured_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_structured_gemm.argtypes = [i64, i64, P, i64, i32, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
+        L.tdc_dft_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_dft_gemm.argtypes = [i64, i64, P, i64, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
     if hasattr(L, "tdc_bdsdc"):
         L.tdc_bdsdc_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_bdsdc.argtypes = [i64, P, P, P, P, i64, P, i64, P, sz, ctypes.POINTER(Opts), P]
@@ -418,27 +420,46 @@ def syevd(A: torch.Tensor, opts: Opts | None = None, ws: torch.Tensor | None = N
     return lam[:n], Z
 
 
-TOEPLITZ, HANKEL = 1, 2
+TOEPLITZ, HANKEL, VANDERMONDE = 1, 2, 3
 
 
-def toeplitz_gemm(A: torch.Tensor, t: torch.Tensor, kind: int = TOEPLITZ, mode: int = MERGE_DENSE,
-                  opts: Opts | None = None, stream=None, check: bool = False) -> torch.Tensor:
-    """C = A * B with B the n x n Toeplitz (B_kj = t[k - j + n - 1]) or Hankel (B_kj =
-    t[k + j]) matrix of the 2n - 1 generators t; A a column-major m x n view (device FP64);
-    mode MERGE_DENSE (FP64) or MERGE_SPLIT (BF16 digit products on the tensor cores)."""
+def structured_gemm(A: torch.Tensor, t: torch.Tensor, kind: int = TOEPLITZ, mode: int = MERGE_DENSE,
+                    opts: Opts | None = None, stream=None, check: bool = False) -> torch.Tensor:
+    """C = A * B with B the n x n Toeplitz (B_kj = t[k - j + n - 1]), Hankel (t[k + j]) or
+    Vandermonde (t[k]^j) matrix of the generators t; A a column-major m x n view (device
+    FP64); mode MERGE_DENSE (FP64) or MERGE_SPLIT (BF16 digit products on the tensor cores)."""
     m, n = A.shape
     lda = A.stride(1) if n > 1 else max(m, 1)
     C = torch.empty(n, m, dtype=torch.float64, device=A.device).t()
     b = ctypes.c_size_t(0)
-    _check("tdc_toeplitz_gemm_workspace_size",
-           lib().tdc_toeplitz_gemm_workspace_size(m, n, mode, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    _check("tdc_structured_gemm_workspace_size",
+           lib().tdc_structured_gemm_workspace_size(m, n, mode, ctypes.byref(opts) if opts else None,
+                                                    ctypes.byref(b)))
     ws = workspace(b.value, A.device)
-    _check("tdc_toeplitz_gemm", lib().tdc_toeplitz_gemm(m, n, _ptr(A), max(lda, m, 1), kind, _ptr(t), _ptr(C),
-                                                        max(m, 1), mode, ctypes.byref(opts) if opts else None,
-                                                        _ptr(ws), ws.numel(), _stream(stream)))
+    _check("tdc_structured_gemm", lib().tdc_structured_gemm(m, n, _ptr(A), max(lda, m, 1), kind, _ptr(t), _ptr(C),
+                                                            max(m, 1), mode, ctypes.byref(opts) if opts else None,
+                                                            _ptr(ws), ws.numel(), _stream(stream)))
     if check:
-        _check("tdc_toeplitz_gemm (device status)", sync_status(stream))
+        _check("tdc_structured_gemm (device status)", sync_status(stream))
     return C
+
+
+def dft_gemm(A: torch.Tensor, mode: int = MERGE_DENSE, opts: Opts | None = None, stream=None, check: bool = False):
+    """(Re, Im) of C = A F, F(k, j) = exp(-2 pi i k j / n), for a real column-major m x n A."""
+    m, n = A.shape
+    lda = A.stride(1) if n > 1 else max(m, 1)
+    Cr = torch.empty(n, m, dtype=torch.float64, device=A.device).t()
+    Ci = torch.empty(n, m, dtype=torch.float64, device=A.device).t()
+    b = ctypes.c_size_t(0)
+    _check("tdc_dft_gemm_workspace_size",
+           lib().tdc_dft_gemm_workspace_size(m, n, mode, ctypes.byref(opts) if opts else None, ctypes.byref(b)))
+    ws = workspace(b.value, A.device)
+    _check("tdc_dft_gemm", lib().tdc_dft_gemm(m, n, _ptr(A), max(lda, m, 1), _ptr(Cr), _ptr(Ci), max(m, 1), mode,
+                                              ctypes.byref(opts) if opts else None, _ptr(ws), ws.numel(),
+                                              _stream(stream)))
+    if check:
+        _check("tdc_dft_gemm (device status)", sync_status(stream))
+    return Cr, Ci
 
 
 def bdsdc(d: torch.Tensor, e: torch.Tensor, opts: Opts | None = None, stream=None, check: bool = False):

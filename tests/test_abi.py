@@ -147,19 +147,28 @@ def test_bdsdc_checks_arguments_on_the_host(lib):
     assert a.value > b.value + 8 * 2000 * 2000
 
 
-def test_toeplitz_gemm_checks_arguments_on_the_host(lib):
+def test_structured_gemm_checks_arguments_on_the_host(lib):
     from paper_2008_01990_gb300 import tdc
     bogus = ctypes.c_void_p(0x1000)
     big = 1 << 40
-    f = lib.tdc_toeplitz_gemm
+    f = lib.tdc_structured_gemm
     assert f(-1, 4, bogus, 1, 1, bogus, bogus, 1, 0, None, bogus, big, None) == -1
     assert f(4, -1, bogus, 4, 1, bogus, bogus, 4, 0, None, bogus, big, None) == -2
     assert f(0, 4, None, 1, 1, None, None, 1, 0, None, None, 0, None) == 0
     assert f(4, 4, None, 4, 1, bogus, bogus, 4, 0, None, bogus, big, None) == -3
     assert f(4, 4, bogus, 3, 1, bogus, bogus, 4, 0, None, bogus, big, None) == -4
-    assert f(4, 4, bogus, 4, 3, bogus, bogus, 4, 0, None, bogus, big, None) == -5
+    assert f(4, 4, bogus, 4, 5, bogus, bogus, 4, 0, None, bogus, big, None) == -5
     assert f(4, 4, bogus, 4, 1, None, bogus, 4, 0, None, bogus, big, None) == -6
     assert f(4, 4, bogus, 4, 1, bogus, None, 4, 0, None, bogus, big, None) == -7
     assert f(4, 4, bogus, 4, 1, bogus, bogus, 3, 0, None, bogus, big, None) == -8
     assert f(4, 4, bogus, 4, 1, bogus, bogus, 4, tdc.MERGE_STRUCTURED, None, bogus, big, None) == -9
     assert f(4, 4, bogus, 4, 1, bogus, bogus, 4, tdc.MERGE_DENSE, None, bogus, 8, None) == tdc.TDC_ENOWS
+
+    g = lib.tdc_dft_gemm
+    assert g(-1, 4, bogus, 1, bogus, bogus, 1, 1, None, bogus, big, None) == -1
+    assert g(4, 4, None, 4, bogus, bogus, 4, 1, None, bogus, big, None) == -3
+    assert g(4, 4, bogus, 4, None, bogus, 4, 1, None, bogus, big, None) == -5
+    assert g(4, 4, bogus, 4, bogus, None, 4, 1, None, bogus, big, None) == -6
+    assert g(4, 4, bogus, 4, bogus, bogus, 3, 1, None, bogus, big, None) == -7
+    assert g(4, 4, bogus, 4, bogus, bogus, 4, 2, None, bogus, big, None) == -8
+    assert g(4, 4, bogus, 4, bogus, bogus, 4, 1, None, bogus, 8, None) == tdc.TDC_ENOWS
