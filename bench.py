@@ -336,7 +336,8 @@ def run_structured_products(args, n):
     """The further structured operands: C = A B with B Toeplitz (t[k - j + n - 1]) or
     Hankel (t[k + j]) from 2n - 1 generators uniform(-1, 1), A uniform(-1, 1) n x n; FP64
     and split modes timed with CUDA events after a warm-up, error against the FP64 dense
-    product on sampled columns; and the bidiagonal SVD of order n (uniform family)."""
+    product on sampled columns; the DFT product (split); and the bidiagonal SVD of order n
+    (uniform family)."""
     import torch
     from paper_2008_01990_gb300 import inputs, tdc
     dev = torch.device("cuda", 0)
@@ -346,7 +347,7 @@ def run_structured_products(args, n):
     t = torch.tensor(inputs.SplitMix64(n).uniform(2 * n - 1, -1.0, 1.0), device=dev)
     cols = torch.tensor(np.sort(np.random.default_rng(0).choice(n, 64, replace=False)), device=dev)
     k = torch.arange(n, device=dev)
-    out = {"workload": "Toeplitz / Hankel products n=%d and the bidiagonal SVD" % n, "products": {}}
+    out = {"workload": "Toeplitz / Hankel / DFT products n=%d and the bidiagonal SVD" % n, "products": {}}
     for kind, kname in ((tdc.TOEPLITZ, "toeplitz"), (tdc.HANKEL, "hankel")):
         idx = (k[:, None] - cols[None, :] + n - 1) if kind == tdc.TOEPLITZ else (k[:, None] + cols[None, :])
         Bs = t[idx]
@@ -361,6 +362,14 @@ def run_structured_products(args, n):
                 "ms": ms, "steps": steps, "max_err_over_rownorm_colnorm": err,
                 "fp64_equivalent_tflops": 2.0 * n ** 3 / (ms * 1e-3) / 1e12}
             del C
+    Fr_ref = A @ torch.cos(2 * np.pi * ((k[:, None] * cols[None, :]) % n).double() / n)
+    Cr, Ci = tdc.dft_gemm(A, tdc.MERGE_SPLIT, check=True)
+    ms = _event_ms(lambda: tdc.dft_gemm(A, tdc.MERGE_SPLIT), max(1, min(args.steps, 5)))
+    scale = torch.linalg.norm(A, dim=1)[:, None] * np.sqrt(n)
+    out["products"]["dft_split"] = {"ms": ms, "max_err_over_rownorm_colnorm":
+                                    float(torch.max(torch.abs(Cr[:, cols] - Fr_ref) / scale).item()),
+                                    "note": "two real products (cos and -sin parts)"}
+    del Cr, Ci, Fr_ref
     d_np, e_np = inputs.bidiag_family("uniform", n, seed=n)
     d, e = torch.tensor(d_np, device=dev), torch.tensor(e_np, device=dev)
     s, U, VT = tdc.bdsdc(d, e, check=True)
