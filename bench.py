@@ -137,26 +137,26 @@ def workload(name: str):
     from paper_2008_01990_gb300 import inputs
     if name == "toeplitz16384":
         d, e = inputs.toeplitz_tridiag(16384)
-        return d, e, 64, "tridiag(1,2,1) n=16384 leaf 64"
+        return d, e, 16, "tridiag(1,2,1) n=16384 leaf 16"
     if name == "toeplitz4096":
         d, e = inputs.toeplitz_tridiag(4096)
-        return d, e, 64, "tridiag(1,2,1) n=4096 leaf 64"
+        return d, e, 16, "tridiag(1,2,1) n=4096 leaf 16"
     if name == "uniform1024":
         d, e = inputs.uniform_tridiag(1024, 1)
-        return d, e, 32, "uniform(-1,1) n=1024 leaf 32 seed 1"
+        return d, e, 16, "uniform(-1,1) n=1024 leaf 16 seed 1"
     if name == "c4_32768":
         d, e = inputs.c4_tridiag(32768, 4)
-        return d, e, 64, "d uniform(0,1), e=1, n=32768 leaf 64 seed 4"
+        return d, e, 16, "d uniform(0,1), e=1, n=32768 leaf 16 seed 4"
     # the closed-form and spherical-harmonic families of Examples 2 and 3 at n = 30000
     if name == "clement30000":
         d, e = inputs.clement_tridiag(30000)
-        return d, e, 64, "Clement/Kac, e_i = sqrt(i(n-i)), n=30000 leaf 64"
+        return d, e, 16, "Clement/Kac, e_i = sqrt(i(n-i)), n=30000 leaf 16"
     if name == "hermite30000":
         d, e = inputs.hermite_tridiag(30000)
-        return d, e, 64, "Hermite, e_i = sqrt(i), n=30000 leaf 64"
+        return d, e, 16, "Hermite, e_i = sqrt(i), n=30000 leaf 16"
     if name == "sht30000":
         d, e = inputs.sht_tridiag(30000)
-        return d, e, 64, "spherical-harmonic transform (Example 3, m = n), n=30000 leaf 64"
+        return d, e, 16, "spherical-harmonic transform (Example 3, m = n), n=30000 leaf 16"
     raise ValueError(name)
 
 
@@ -625,7 +625,7 @@ def config_c5(args, steps=5, warmup=3):
 # single-pass ncu captures of the kernel as it stands; keyed by the exact
 # configuration (workload, merge, leaf, split_min_K, split_chunk_k, lr_tile), null for
 # any other
-TRAFFIC = {("toeplitz16384", "auto", 64, 128, 256, 256): 23.01e9}
+TRAFFIC = {("toeplitz16384", "auto", 16, 128, 256, 256): 22.72e9}
 
 
 def config_dense(args, n=4096, steps=3):

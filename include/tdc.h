@@ -144,7 +144,7 @@ typedef struct {
                                             the rank cap, or more low-rank columns than its buffer */
 } tdc_stats;
 
-/* Fill *o with the defaults (leaf 32, AUTO, structured_min_K 4096, lr_tile 256,
+/* Fill *o with the defaults (leaf 16, AUTO, structured_min_K 4096, lr_tile 256,
  * lr_tol 1e-15, split_slices 7, split_min_K 128, max_iter 64, sign_normalise 1,
  * collect_stats 0, spin_budget 2^24, split_chunk_k 256). */
 void tdc_default_opts(tdc_opts* o);

@@ -775,7 +775,7 @@ extern "C" {
 void tdc_default_opts(tdc_opts* o) {
   if (!o) return;
   memset(o, 0, sizeof(*o));
-  o->leaf = 32;
+  o->leaf = 16;
   o->merge_mode = TDC_MERGE_AUTO;
   o->structured_min_K = 4096;
   o->lr_tile = 256;

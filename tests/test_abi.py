@@ -32,7 +32,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_default_opts_and_workspace(lib):
     from paper_2008_01990_gb300 import tdc
     o = tdc.default_opts()
-    assert o.leaf == 32 and o.max_iter >= 1 and o.sign_normalise == 1
+    assert o.leaf == 16 and o.max_iter >= 1 and o.sign_normalise == 1
     assert o.split_chunk_k == 256 and ctypes.sizeof(o) == 64
     w1 = tdc.workspace_size(1024, o)
     w2 = tdc.workspace_size(2048, o)

@@ -204,13 +204,14 @@ def test_status_nonfinite_input(tdc):
 
 
 def test_c2_toeplitz_16384_sampled(tdc):
-    """Full-size tridiag(1,2,1) at n=16384 (leaf 64): every eigenvalue against the
-    closed form; residual, orthogonality and sine vectors on sampled columns."""
+    """Full-size tridiag(1,2,1) at n=16384 in the benchmark's configuration (leaf 16,
+    default merge): every eigenvalue against the closed form; residual, orthogonality and
+    sine vectors on sampled columns."""
     n = 16384
     d, e = inputs.toeplitz_tridiag(n)
     dt = torch.tensor(d, device=DEV)
     et = torch.tensor(e, device=DEV)
-    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=64), check=True)
+    lam, Q = tdc.eig(dt, et, tdc.default_opts(leaf=16), check=True)
     check_toeplitz_sampled(lam, Q, n)
 
 
