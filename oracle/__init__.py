@@ -11,7 +11,8 @@ oracles of the adjoint and of the SRRSC low-rank approximation; ``householder.py
 the Householder reduction of a dense symmetric matrix to tridiagonal form and its
 back-transform; ``bidiag.py`` the bidiagonal SVD read off the Golub-Kahan tridiagonal;
 ``structured.py`` products with Toeplitz and Hankel operands written out from their
-generators.
+generators; ``banded.py`` the symmetric band eigenproblem from LAPACK's lower band
+storage.
 """
 from __future__ import annotations
 
