@@ -348,6 +348,25 @@ int tdc_dft_gemm_workspace_size(int64_t m, int64_t n, int32_t mode, const tdc_op
 int tdc_dft_gemm(int64_t m, int64_t n, const double* A, int64_t lda, double* Cre, double* Cim, int64_t ldc,
                  int32_t mode, const tdc_opts* o, void* ws, size_t ws_bytes, tdc_stream_t stream);
 
+/* tdc_sbevd: A = Q diag(lam) Q^T for the n x n symmetric band matrix of bandwidth b
+ * (0 <= b < n, b <= 64) in LAPACK's lower band storage: AB(i - j, j) = A(i, j) for
+ * j <= i <= min(n - 1, j + b), AB column-major with ldab >= b + 1 (device FP64, not
+ * modified).  Divide and conquer for band matrices (Section 5's band case): a node splits
+ * at its middle; the b x b coupling block, row k being B_k, is written as
+ * sum_k (x_k; y_k)(x_k; y_k)^T with x_k = s_k e, y_k = B_k / s_k, s_k = sqrt(||B_k||), and
+ * subtracted from the two halves' corners; leaves of at most max(128, 8b) rows are solved
+ * densely (tdc_syevd's kernels); a merge takes the b terms in turn as rank-one
+ * modifications D + z z^T with z = Q^T (x_k; y_k): sort, deflation (Section 3.2's two
+ * tests), the secular equation, the Cauchy-like update of the non-deflated columns (split
+ * tensor-core product from K = 128 on).  lam[n] ascending, Q n x n (ldq >= n).  The call
+ * reads each rank-one step's deflation count back to the host, so it returns when the
+ * solve is done.  ws of tdc_sbevd_workspace_size(n, b, o) bytes.  Errors: -1 n, -2 b,
+ * -3 AB, -4 ldab, -5 lam, -6 Q, -7 ldq, -10 options, TDC_ENOWS, TDC_ECUDA, or those of
+ * the steps. */
+int tdc_sbevd_workspace_size(int64_t n, int64_t b, const tdc_opts* o, size_t* bytes);
+int tdc_sbevd(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam, double* Q, int64_t ldq, void* ws,
+              size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream);
+
 /* tdc_bdsdc: SVD B = U diag(sigma) VT of the n x n upper bidiagonal B (diagonal d[n],
  * superdiagonal e[n-1], device FP64, not modified) through the divide and conquer (the
  * paper's introduction points to it for the bidiagonal SVD): tdc_eig on the Golub-Kahan

@@ -1578,9 +1578,208 @@ int ormtr_run(int64_t n, int64_t ncols, const double* A, int64_t lda, const doub
 
 size_t syevd_vec_bytes(int64_t n) { return 3 * align_up(sizeof(double) * (size_t)std::max<int64_t>(n, 1)); }
 
+// ---- symmetric band eigenproblem: divide and conquer with b rank-one merges per node
+struct BandNode {
+  int64_t lo, hi;
+};
+
+int64_t band_leafmax(int64_t b) { return std::max<int64_t>(128, 8 * b); }
+
+// nodes in post order (children before their parent); leaves have at most leafmax rows
+void band_nodes(int64_t lo, int64_t hi, int64_t leafmax, std::vector<BandNode>& out) {
+  if (hi - lo > leafmax) {
+    const int64_t m = lo + (hi - lo) / 2;
+    band_nodes(lo, m, leafmax, out);
+    band_nodes(m, hi, leafmax, out);
+  }
+  out.push_back({lo, hi});
+}
+
+struct BandLayout {
+  size_t ABw, wv, Ad, Dcur, z, Ds, zs, perm, kept, defl, rotp, rotcs, cnt, DK, zK, Dd, org, tau, zhat, scol, iota, Qw,
+      prod, leaf, total;
+  size_t leaf_bytes;
+};
+
+BandLayout band_layout(int64_t n, int64_t b, const tdc_opts& op) {
+  BandLayout L;
+  size_t o = 0;
+  const size_t nn = (size_t)std::max<int64_t>(n, 1);
+  const int64_t lm = std::min<int64_t>(std::max<int64_t>(n, 1), band_leafmax(b));
+  std::vector<BandNode> nodes;
+  band_nodes(0, std::max<int64_t>(n, 1), band_leafmax(b), nodes);
+  L.ABw = take(o, sizeof(double) * (size_t)(b + 1) * nn);
+  L.wv = take(o, sizeof(double) * nodes.size() * (size_t)std::max<int64_t>(b, 1) * (size_t)(b + 1));
+  L.Ad = take(o, sizeof(double) * (size_t)(lm * lm));
+  L.Dcur = take(o, sizeof(double) * nn);
+  L.z = take(o, sizeof(double) * nn);
+  L.Ds = take(o, sizeof(double) * nn);
+  L.zs = take(o, sizeof(double) * nn);
+  L.perm = take(o, sizeof(int32_t) * nn);
+  L.kept = take(o, sizeof(int32_t) * nn);
+  L.defl = take(o, sizeof(int32_t) * nn);
+  L.rotp = take(o, 2 * sizeof(int32_t) * nn);
+  L.rotcs = take(o, 2 * sizeof(double) * nn);
+  L.cnt = take(o, 64);
+  L.DK = take(o, sizeof(double) * nn);
+  L.zK = take(o, sizeof(double) * nn);
+  L.Dd = take(o, sizeof(double) * nn);
+  L.org = take(o, sizeof(int32_t) * nn);
+  L.tau = take(o, sizeof(double) * nn);
+  L.zhat = take(o, sizeof(double) * nn);
+  L.scol = take(o, sizeof(double) * nn);
+  L.iota = take(o, sizeof(int32_t) * nn);
+  L.Qw = take(o, sizeof(double) * nn * nn);
+  size_t pb = 0;
+  tdc_cauchy_gemm_workspace_size((int64_t)nn, (int64_t)nn, TDC_MERGE_SPLIT, &op, &pb);
+  L.prod = take(o, pb);
+  size_t we = 0;
+  tdc_workspace_size(lm, &op, &we);
+  L.leaf_bytes = syevd_vec_bytes(lm) + std::max(we, std::max(trd_layout(lm).total, orm_layout(lm, lm).total)) + 256;
+  L.leaf = take(o, L.leaf_bytes);
+  L.total = o + 256;
+  return L;
+}
+
+int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam, double* Q, int64_t ldq, char* base,
+              const tdc_opts& op, int* st, cudaStream_t cs) {
+  const BandLayout L = band_layout(n, b, op);
+  const int64_t ldw = b + 1;
+  double* ABw = (double*)(base + L.ABw);
+  double* wv = (double*)(base + L.wv);
+  double* Ad = (double*)(base + L.Ad);
+  double* Dcur = (double*)(base + L.Dcur);
+  double* z = (double*)(base + L.z);
+  double* Ds = (double*)(base + L.Ds);
+  double* zs = (double*)(base + L.zs);
+  int32_t* perm = (int32_t*)(base + L.perm);
+  int32_t* kept = (int32_t*)(base + L.kept);
+  int32_t* defl = (int32_t*)(base + L.defl);
+  int32_t* rotp = (int32_t*)(base + L.rotp);
+  double* rotcs = (double*)(base + L.rotcs);
+  int32_t* cnt = (int32_t*)(base + L.cnt);
+  double* rhod = (double*)(base + L.cnt + 32);
+  double* DK = (double*)(base + L.DK);
+  double* zK = (double*)(base + L.zK);
+  double* Dd = (double*)(base + L.Dd);
+  int32_t* org = (int32_t*)(base + L.org);
+  double* tau = (double*)(base + L.tau);
+  double* zhat = (double*)(base + L.zhat);
+  double* scol = (double*)(base + L.scol);
+  int32_t* iota = (int32_t*)(base + L.iota);
+  double* Qw = (double*)(base + L.Qw);
+  char* prod = base + L.prod;
+  char* leaf = base + L.leaf;
+  std::vector<BandNode> nodes;
+  band_nodes(0, n, band_leafmax(b), nodes);
+  if (launch_bd_copy_band(n, (int)b, AB, ldab, ABw, cs) != cudaSuccess) return TDC_ECUDA;
+  if (launch_bd_zero(n, n, Q, ldq, cs) != cudaSuccess) return TDC_ECUDA;
+  k_iota<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, cs>>>(iota, n);
+  // tearings (they touch disjoint entries: nodes have at least 4b rows)
+  for (size_t i = 0; i < nodes.size(); ++i) {
+    const BandNode& nd = nodes[i];
+    if (nd.hi - nd.lo <= band_leafmax(b)) continue;
+    const int64_t m = nd.lo + (nd.hi - nd.lo) / 2;
+    if (launch_bd_tear(ABw, ldw, (int)b, m, wv + i * b * (b + 1), cs) != cudaSuccess) return TDC_ECUDA;
+  }
+  const size_t lvb = align_up(sizeof(double) * (size_t)std::min<int64_t>(n, band_leafmax(b)));
+  for (size_t i = 0; i < nodes.size(); ++i) {
+    const BandNode& nd = nodes[i];
+    const int64_t nn = nd.hi - nd.lo;
+    double* Qn = Q + nd.lo + nd.lo * ldq;
+    if (nn <= band_leafmax(b)) {  // leaf: dense eigensolve of the torn block
+      if (launch_bd_leaf_dense(ABw, ldw, (int)b, nd.lo, nn, Ad, cs) != cudaSuccess) return TDC_ECUDA;
+      double* d = (double*)leaf;
+      double* e = (double*)(leaf + lvb);
+      double* tv = (double*)(leaf + 2 * lvb);
+      char* rest = leaf + 3 * lvb;
+      const size_t rest_bytes = L.leaf_bytes - 3 * lvb;
+      int r = sytrd_run(nn, Ad, nn, d, e, tv, rest, op, st, cs);
+      if (r != TDC_OK) return r;
+      r = tdc_eig(nn, d, e, lam + nd.lo, Qn, ldq, rest, rest_bytes, &op, cs);
+      if (r != TDC_OK) return r;
+      r = ormtr_run(nn, nn, Ad, nn, tv, Qn, ldq, rest, op, st, cs);
+      if (r != TDC_OK) return r;
+      continue;
+    }
+    const int64_t m = nd.lo + (nd.hi - nd.lo) / 2;
+    if (cudaMemcpyAsync(Dcur, lam + nd.lo, sizeof(double) * nn, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+      return TDC_ECUDA;
+    for (int64_t k = 0; k < b; ++k) {
+      const double* w = wv + i * b * (b + 1) + k * (b + 1);
+      if (launch_bd_z(nn, Qn, ldq, (m - b + k) - nd.lo, m - nd.lo, (int)b, w, z, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_sort(nn, Dcur, z, Ds, zs, perm, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_deflate(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rhod, cs) != cudaSuccess) return TDC_ECUDA;
+      int32_t hc[3] = {0, 0, 0};
+      double hrho = 0.0;
+      if (cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+          cudaMemcpyAsync(&hrho, rhod, sizeof(double), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+          cudaStreamSynchronize(cs) != cudaSuccess)
+        return TDC_ECUDA;
+      const int K = hc[0], ndf = hc[1], nr = hc[2];
+      if (launch_bd_rotate(nn, Qn, ldq, perm, rotp, rotcs, nr, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_gather(nn, Qn, ldq, perm, kept, K, defl, ndf, Ds, zs, Qw, DK, zK, Dd, cs) != cudaSuccess)
+        return TDC_ECUDA;
+      if (K > 0) {
+        if (launch_rank_one(DK, zK, K, hrho, op.max_iter, org, tau, zhat, scol, st, cs) != cudaSuccess)
+          return TDC_ECUDA;
+        const int32_t mode = K >= 128 ? TDC_MERGE_SPLIT : TDC_MERGE_DENSE;
+        char* pw = (char*)(((uintptr_t)prod + 255) & ~(uintptr_t)255);
+        const int r = cauchy_product(nn, K, Qw, nn, DK, org, tau, zhat, scol, Qn, ldq, mode, op, pw, st, nullptr,
+                                     nullptr, cs);
+        if (r != TDC_OK) return r;
+      }
+      if (launch_bd_finish(nn, Qw, Qn, ldq, K, ndf, DK, org, tau, Dd, Dcur, cs) != cudaSuccess) return TDC_ECUDA;
+    }
+    // ascending eigenvalues and the columns in that order
+    if (launch_bd_sort(nn, Dcur, nullptr, Ds, nullptr, perm, cs) != cudaSuccess) return TDC_ECUDA;
+    if (launch_bd_gather(nn, Qn, ldq, perm, iota, (int)nn, defl, 0, Ds, Ds, Qw, DK, zK, Dd, cs) != cudaSuccess)
+      return TDC_ECUDA;
+    if (launch_bd_copy_back(nn, nn, Qw, Qn, ldq, cs) != cudaSuccess) return TDC_ECUDA;
+    if (cudaMemcpyAsync(lam + nd.lo, Ds, sizeof(double) * nn, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
+      return TDC_ECUDA;
+  }
+  return TDC_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int tdc_sbevd_workspace_size(int64_t n, int64_t b, const tdc_opts* o, size_t* bytes) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (b < 0 || b > 64 || (n > 0 && b >= n)) return -2;
+  if (validate_opts(&op)) return -3;
+  if (!bytes) return -4;
+  *bytes = band_layout(n, b, op).total;
+  return TDC_OK;
+}
+
+int tdc_sbevd(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam, double* Q, int64_t ldq, void* ws,
+              size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream) {
+  tdc_opts op;
+  tdc_default_opts(&op);
+  if (o) op = *o;
+  if (n < 0) return -1;
+  if (n == 0) return TDC_OK;
+  if (b < 0 || b > 64 || b >= n) return -2;
+  if (!AB) return -3;
+  if (ldab < b + 1) return -4;
+  if (!lam) return -5;
+  if (!Q) return -6;
+  if (ldq < n) return -7;
+  if (validate_opts(&op)) return -10;
+  if (!ws || ws_bytes < band_layout(n, b, op).total) return TDC_ENOWS;
+  cudaStream_t cs = (cudaStream_t)stream;
+  int* st = begin_status(cs);
+  if (!st) return TDC_ECUDA;
+  StatusNest keep;
+  char* base = (char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  return sbevd_run(n, b, AB, ldab, lam, Q, ldq, base, op, st, cs);
+}
 
 int tdc_sytrd_workspace_size(int64_t n, size_t* bytes) {
   if (n < 0) return -1;

@@ -557,6 +557,27 @@ cudaError_t launch_operand_prep(int64_t m, int64_t n, const double* A, int64_t l
                                 double* winmax, int32_t* cexp, int32_t* oexp, int32_t* eA,
                                 unsigned long long* maxsq, cudaStream_t s);
 cudaError_t launch_dft_tables(int64_t n, double* cosv, double* msinv, cudaStream_t s);
+// symmetric band divide and conquer (tdc_banded.cu)
+cudaError_t launch_bd_copy_band(int64_t n, int b, const double* AB, int64_t ldab, double* ABw, cudaStream_t s);
+cudaError_t launch_bd_tear(double* ABw, int64_t ldab, int b, int64_t m, double* wv, cudaStream_t s);
+cudaError_t launch_bd_leaf_dense(const double* ABw, int64_t ldab, int b, int64_t lo, int64_t L, double* Ad,
+                                 cudaStream_t s);
+cudaError_t launch_bd_z(int64_t nn, const double* Q, int64_t ldq, int64_t ra, int64_t rb, int b, const double* w,
+                        double* z, cudaStream_t s);
+cudaError_t launch_bd_sort(int64_t nn, const double* D, const double* z, double* Ds, double* zs, int32_t* perm,
+                           cudaStream_t s);
+cudaError_t launch_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, int32_t* defl, int32_t* rotp,
+                              double* rotcs, int32_t* cnt, double* rho, cudaStream_t s);
+cudaError_t launch_bd_rotate(int64_t nrows, double* Q, int64_t ldq, const int32_t* perm, const int32_t* rotp,
+                             const double* rotcs, int nr, cudaStream_t s);
+cudaError_t launch_bd_gather(int64_t nrows, const double* Q, int64_t ldq, const int32_t* perm, const int32_t* kept,
+                             int K, const int32_t* defl, int nd, const double* Ds, const double* zs, double* Qw,
+                             double* DK, double* zK, double* Dd, cudaStream_t s);
+cudaError_t launch_bd_finish(int64_t nrows, const double* Qw, double* Q, int64_t ldq, int K, int nd, const double* DK,
+                             const int32_t* org, const double* tau, const double* Dd, double* D, cudaStream_t s);
+cudaError_t launch_bd_copy_back(int64_t nrows, int64_t ncols, const double* Qw, double* Q, int64_t ldq,
+                                cudaStream_t s);
+cudaError_t launch_bd_zero(int64_t rows, int64_t cols, double* Q, int64_t ldq, cudaStream_t s);
 // bidiagonal SVD through the Golub-Kahan tridiagonal (tdc_bdsdc.cu)
 cudaError_t launch_gk_build(int64_t n, const double* d, const double* e, double* td, double* te, cudaStream_t s);
 cudaError_t launch_gk_extract(int64_t n, const double* lam, const double* Q, int64_t ldq, double* sigma, double* U,

@@ -232,3 +232,28 @@ def bidiag_family(name: str, n: int, seed: int = 1):
         s = 2.0 ** (-20.0 * np.arange(n) / max(n, 1))
         return mag * sgn * s, e * s[: max(n - 1, 0)]
     raise KeyError(name)
+
+
+def band_sym(name: str, n: int, b: int, seed: int = 1) -> np.ndarray:
+    """Symmetric band matrices of bandwidth b in lower band storage ((b + 1) x n,
+    AB[r, j] = A(j + r, j), zero past the matrix):
+      * ``uniform``  entries uniform(-1, 1)
+      * ``laplace``  the 1-D operator with coupling to b neighbours: 2 b on the diagonal,
+                     -1 on each of the b sub-diagonals (many close eigenvalues)
+      * ``graded``   ``uniform`` with column j scaled by 2^(-10 j / n) on both sides"""
+    AB = np.zeros((b + 1, n))
+    if name == "laplace":
+        AB[0, :] = 2.0 * b
+        AB[1:, :] = -1.0
+    else:
+        g = SplitMix64(seed)
+        AB[:, :] = g.uniform((b + 1) * n, -1.0, 1.0).reshape(b + 1, n)
+        if name == "graded":
+            sc = 2.0 ** (-10.0 * np.arange(n) / max(n, 1))
+            for r in range(b + 1):
+                AB[r, : n - r] *= sc[: n - r] * sc[r:]
+        elif name != "uniform":
+            raise KeyError(name)
+    for r in range(1, b + 1):
+        AB[r, max(n - r, 0):] = 0.0
+    return AB

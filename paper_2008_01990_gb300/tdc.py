@@ -169,6 +169,9 @@ def lib():
         L.tdc_structured_gemm.argtypes = [i64, i64, P, i64, i32, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
         L.tdc_dft_gemm_workspace_size.argtypes = [i64, i64, i32, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_dft_gemm.argtypes = [i64, i64, P, i64, P, P, i64, i32, ctypes.POINTER(Opts), P, sz, P]
+    if hasattr(L, "tdc_sbevd"):
+        L.tdc_sbevd_workspace_size.argtypes = [i64, i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
+        L.tdc_sbevd.argtypes = [i64, i64, P, i64, P, P, i64, P, sz, ctypes.POINTER(Opts), P]
     if hasattr(L, "tdc_bdsdc"):
         L.tdc_bdsdc_workspace_size.argtypes = [i64, ctypes.POINTER(Opts), ctypes.POINTER(sz)]
         L.tdc_bdsdc.argtypes = [i64, P, P, P, P, i64, P, i64, P, sz, ctypes.POINTER(Opts), P]
@@ -460,6 +463,26 @@ def dft_gemm(A: torch.Tensor, mode: int = MERGE_DENSE, opts: Opts | None = None,
     if check:
         _check("tdc_dft_gemm (device status)", sync_status(stream))
     return Cr, Ci
+
+
+def sbevd(AB: torch.Tensor, opts: Opts | None = None, stream=None, check: bool = False):
+    """A = Q diag(lam) Q^T for the symmetric band matrix in lower band storage AB
+    ((b + 1) x n, AB[i - j, j] = A[i, j]; device FP64, any layout: copied column-major).
+    Returns (lam, Q), Q a column-major n x n view."""
+    b1, n = AB.shape
+    b = b1 - 1
+    ABc = _colmajor_copy(AB)
+    lam = torch.empty(max(n, 1), dtype=torch.float64, device=AB.device)
+    Q = torch.empty(n, n, dtype=torch.float64, device=AB.device).t()
+    nb = ctypes.c_size_t(0)
+    _check("tdc_sbevd_workspace_size", lib().tdc_sbevd_workspace_size(n, b, ctypes.byref(opts) if opts else None,
+                                                                      ctypes.byref(nb)))
+    ws = workspace(nb.value, AB.device)
+    _check("tdc_sbevd", lib().tdc_sbevd(n, b, _ptr(ABc), max(b1, 1), _ptr(lam), _ptr(Q), max(n, 1), _ptr(ws),
+                                        ws.numel(), ctypes.byref(opts) if opts else None, _stream(stream)))
+    if check:
+        _check("tdc_sbevd (device status)", sync_status(stream))
+    return lam[:n], Q
 
 
 def bdsdc(d: torch.Tensor, e: torch.Tensor, opts: Opts | None = None, stream=None, check: bool = False):

@@ -172,3 +172,22 @@ def test_structured_gemm_checks_arguments_on_the_host(lib):
     assert g(4, 4, bogus, 4, bogus, bogus, 3, 1, None, bogus, big, None) == -7
     assert g(4, 4, bogus, 4, bogus, bogus, 4, 2, None, bogus, big, None) == -8
     assert g(4, 4, bogus, 4, bogus, bogus, 4, 1, None, bogus, 8, None) == tdc.TDC_ENOWS
+
+
+def test_sbevd_checks_arguments_on_the_host(lib):
+    from paper_2008_01990_gb300 import tdc
+    bogus = ctypes.c_void_p(0x1000)
+    big = 1 << 40
+    f = lib.tdc_sbevd
+    assert f(-1, 0, bogus, 1, bogus, bogus, 1, bogus, big, None, None) == -1
+    assert f(0, 0, None, 1, None, None, 1, None, 0, None, None) == 0
+    assert f(10, 10, bogus, 11, bogus, bogus, 10, bogus, big, None, None) == -2
+    assert f(10, 65, bogus, 66, bogus, bogus, 10, bogus, big, None, None) == -2
+    assert f(10, 2, None, 3, bogus, bogus, 10, bogus, big, None, None) == -3
+    assert f(10, 2, bogus, 2, bogus, bogus, 10, bogus, big, None, None) == -4
+    assert f(10, 2, bogus, 3, None, bogus, 10, bogus, big, None, None) == -5
+    assert f(10, 2, bogus, 3, bogus, None, 10, bogus, big, None, None) == -6
+    assert f(10, 2, bogus, 3, bogus, bogus, 9, bogus, big, None, None) == -7
+    assert f(10, 2, bogus, 3, bogus, bogus, 10, bogus, 16, None, None) == tdc.TDC_ENOWS
+    a = ctypes.c_size_t(0)
+    assert lib.tdc_sbevd_workspace_size(1000, 8, None, ctypes.byref(a)) == 0 and a.value > 8 * 1000 * 1000
