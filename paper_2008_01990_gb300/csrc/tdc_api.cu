@@ -1709,7 +1709,7 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
       const double* w = wv + i * b * (b + 1) + k * (b + 1);
       if (launch_bd_z(nn, Qn, ldq, (m - b + k) - nd.lo, m - nd.lo, (int)b, w, z, cs) != cudaSuccess) return TDC_ECUDA;
       if (launch_bd_sort(nn, Dcur, z, Ds, zs, perm, cs) != cudaSuccess) return TDC_ECUDA;
-      if (launch_bd_deflate(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rhod, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_deflate(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rhod, st, cs) != cudaSuccess) return TDC_ECUDA;
       int32_t hc[3] = {0, 0, 0};
       double hrho = 0.0;
       if (cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
@@ -1717,8 +1717,8 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
           cudaStreamSynchronize(cs) != cudaSuccess)
         return TDC_ECUDA;
       const int K = hc[0], ndf = hc[1], nr = hc[2];
-      if (launch_bd_rotate(nn, Qn, ldq, perm, rotp, rotcs, nr, cs) != cudaSuccess) return TDC_ECUDA;
-      if (launch_bd_gather(nn, Qn, ldq, perm, kept, K, defl, ndf, Ds, zs, Qw, DK, zK, Dd, cs) != cudaSuccess)
+      if (launch_bd_rotate(nn, Qn, ldq, perm, rotp, rotcs, nr, st, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_gather(nn, Qn, ldq, perm, kept, K, defl, ndf, Ds, zs, Qw, DK, zK, Dd, st, cs) != cudaSuccess)
         return TDC_ECUDA;
       if (K > 0) {
         if (launch_rank_one(DK, zK, K, hrho, op.max_iter, org, tau, zhat, scol, st, cs) != cudaSuccess)
@@ -1733,7 +1733,7 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
     }
     // ascending eigenvalues and the columns in that order
     if (launch_bd_sort(nn, Dcur, nullptr, Ds, nullptr, perm, cs) != cudaSuccess) return TDC_ECUDA;
-    if (launch_bd_gather(nn, Qn, ldq, perm, iota, (int)nn, defl, 0, Ds, Ds, Qw, DK, zK, Dd, cs) != cudaSuccess)
+    if (launch_bd_gather(nn, Qn, ldq, perm, iota, (int)nn, defl, 0, Ds, Ds, Qw, DK, zK, Dd, st, cs) != cudaSuccess)
       return TDC_ECUDA;
     if (launch_bd_copy_back(nn, nn, Qw, Qn, ldq, cs) != cudaSuccess) return TDC_ECUDA;
     if (cudaMemcpyAsync(lam + nd.lo, Ds, sizeof(double) * nn, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)

@@ -75,16 +75,21 @@ __global__ void __launch_bounds__(256) k_bd_z(int64_t nn, const double* Q, int64
   }
 }
 
+// (a, ia) before (b, ib) in a strict total order: ascending values, NaNs last, ties by
+// index -- so that the ranks below always form a permutation.
+__device__ __forceinline__ bool bd_before(double a, int64_t ia, double b, int64_t ib) {
+  const bool na = a != a, nb = b != b;
+  if (na || nb) return (!na && nb) || (na && nb && ia < ib);
+  return a < b || (a == b && ia < ib);
+}
+
 // Stable rank sort: Ds[rank(i)] = D[i], zs likewise (z may be NULL), perm[rank(i)] = i.
 __global__ void __launch_bounds__(256) k_bd_rank_sort(int64_t nn, const double* D, const double* z, double* Ds,
                                                      double* zs, int32_t* perm) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
     const double v = D[i];
     int64_t rk = 0;
-    for (int64_t j = 0; j < nn; ++j) {
-      const double u = D[j];
-      rk += (u < v || (u == v && j < i)) ? 1 : 0;
-    }
+    for (int64_t j = 0; j < nn; ++j) rk += bd_before(D[j], j, v, i) ? 1 : 0;
     Ds[rk] = v;
     if (z) zs[rk] = z[i];
     perm[rk] = (int32_t)i;
@@ -93,11 +98,26 @@ __global__ void __launch_bounds__(256) k_bd_rank_sort(int64_t nn, const double* 
 
 // Deflation scan over the sorted poles (one thread): zs normalised in place, kept / defl
 // positions, rotations (pj, nj, c, s) on sorted positions, cnt = {K, nd, nrot}, *rho_out.
+// A non-finite pole or weight records TDC_ENONFINITE and deflates every pole (no secular
+// solve and no product run on it).
 __global__ void k_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, int32_t* defl, int32_t* rotp,
-                             double* rotcs, int32_t* cnt, double* rho_out) {
+                             double* rotcs, int32_t* cnt, double* rho_out, int* status) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double s2 = 0.0;
-  for (int64_t i = 0; i < nn; ++i) s2 = fma(zs[i], zs[i], s2);
+  bool finite = true;
+  for (int64_t i = 0; i < nn; ++i) {
+    s2 = fma(zs[i], zs[i], s2);
+    finite = finite && isfinite(zs[i]) && isfinite(Ds[i]);
+  }
+  if (!finite || !isfinite(s2)) {
+    set_status(status, TDC_ENONFINITE);
+    for (int64_t i = 0; i < nn; ++i) defl[i] = (int32_t)i;
+    cnt[0] = 0;
+    cnt[1] = (int32_t)nn;
+    cnt[2] = 0;
+    *rho_out = 0.0;
+    return;
+  }
   const double zn = sqrt(s2), rho = s2;
   double dmax = 0.0, zmax = 0.0;
   for (int64_t i = 0; i < nn; ++i) {
@@ -149,11 +169,17 @@ __global__ void k_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, 
 // The deflation rotations on the columns of Q (sorted position p is column perm[p]), in
 // order, each row independently.
 __global__ void __launch_bounds__(256) k_bd_rotate(int64_t nrows, double* Q, int64_t ldq, const int32_t* perm,
-                                                  const int32_t* rotp, const double* rotcs, int nr) {
+                                                  const int32_t* rotp, const double* rotcs, int nr, int* status) {
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
     for (int t = 0; t < nr; ++t) {
-      double* a = Q + r + (int64_t)perm[rotp[2 * t]] * ldq;
-      double* bq = Q + r + (int64_t)perm[rotp[2 * t + 1]] * ldq;
+      const int32_t pa = rotp[2 * t], pb = rotp[2 * t + 1];
+      if (pa < 0 || pa >= nrows || pb < 0 || pb >= nrows || perm[pa] < 0 || perm[pa] >= nrows || perm[pb] < 0 ||
+          perm[pb] >= nrows) {  // cannot happen for a permutation; never touch memory outside Q
+        set_status(status, TDC_EUNSUPPORTED);
+        continue;
+      }
+      double* a = Q + r + (int64_t)perm[pa] * ldq;
+      double* bq = Q + r + (int64_t)perm[pb] * ldq;
       const double c = rotcs[2 * t], s = rotcs[2 * t + 1];
       const double x = *a, y = *bq;
       *a = c * x + s * y;
@@ -167,9 +193,13 @@ __global__ void __launch_bounds__(256) k_bd_rotate(int64_t nrows, double* Q, int
 __global__ void __launch_bounds__(256) k_bd_gather(int64_t nrows, const double* Q, int64_t ldq, const int32_t* perm,
                                                   const int32_t* kept, int K, const int32_t* defl, int nd,
                                                   const double* Ds, const double* zs, double* Qw, double* DK,
-                                                  double* zK, double* Dd) {
+                                                  double* zK, double* Dd, int* status) {
   for (int64_t t = blockIdx.x; t < K + nd; t += gridDim.x) {
     const int32_t sp = t < K ? kept[t] : defl[t - K];
+    if (t >= nrows || sp < 0 || sp >= nrows || perm[sp] < 0 || perm[sp] >= nrows) {  // cannot happen; never
+      if (threadIdx.x == 0) set_status(status, TDC_EUNSUPPORTED);                   // read or write outside
+      continue;
+    }
     const double* src = Q + (int64_t)perm[sp] * ldq;
     double* dst = Qw + t * nrows;
     for (int64_t r = threadIdx.x; r < nrows; r += blockDim.x) dst[r] = src[r];
@@ -188,13 +218,13 @@ __global__ void __launch_bounds__(256) k_bd_gather(int64_t nrows, const double* 
 __global__ void __launch_bounds__(256) k_bd_finish(int64_t nrows, const double* Qw, double* Q, int64_t ldq, int K,
                                                   int nd, const double* DK, const int32_t* org, const double* tau,
                                                   const double* Dd, double* D) {
-  for (int64_t t = blockIdx.x; t < K + nd; t += gridDim.x) {
+  for (int64_t t = blockIdx.x; t < K + nd && t < nrows; t += gridDim.x) {
     if (t >= K) {
       const double* src = Qw + t * nrows;
       double* dst = Q + t * ldq;
       for (int64_t r = threadIdx.x; r < nrows; r += blockDim.x) dst[r] = src[r];
     }
-    if (threadIdx.x == 0) D[t] = t < K ? DK[org[t]] + tau[t] : Dd[t - K];
+    if (threadIdx.x == 0) D[t] = t < K ? ((org[t] >= 0 && org[t] < K) ? DK[org[t]] + tau[t] : __longlong_as_double(0x7ff8000000000000ll)) : Dd[t - K];
   }
 }
 
@@ -254,21 +284,21 @@ cudaError_t launch_bd_sort(int64_t nn, const double* D, const double* z, double*
   return cudaGetLastError();
 }
 cudaError_t launch_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, int32_t* defl, int32_t* rotp,
-                              double* rotcs, int32_t* cnt, double* rho, cudaStream_t s) {
-  k_bd_deflate<<<1, 32, 0, s>>>(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rho);
+                              double* rotcs, int32_t* cnt, double* rho, int* status, cudaStream_t s) {
+  k_bd_deflate<<<1, 32, 0, s>>>(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rho, status);
   return cudaGetLastError();
 }
 cudaError_t launch_bd_rotate(int64_t nrows, double* Q, int64_t ldq, const int32_t* perm, const int32_t* rotp,
-                             const double* rotcs, int nr, cudaStream_t s) {
+                             const double* rotcs, int nr, int* status, cudaStream_t s) {
   if (nr <= 0) return cudaSuccess;
-  k_bd_rotate<<<grid_for(nrows), 256, 0, s>>>(nrows, Q, ldq, perm, rotp, rotcs, nr);
+  k_bd_rotate<<<grid_for(nrows), 256, 0, s>>>(nrows, Q, ldq, perm, rotp, rotcs, nr, status);
   return cudaGetLastError();
 }
 cudaError_t launch_bd_gather(int64_t nrows, const double* Q, int64_t ldq, const int32_t* perm, const int32_t* kept,
                              int K, const int32_t* defl, int nd, const double* Ds, const double* zs, double* Qw,
-                             double* DK, double* zK, double* Dd, cudaStream_t s) {
+                             double* DK, double* zK, double* Dd, int* status, cudaStream_t s) {
   k_bd_gather<<<(unsigned)std::max(1, std::min(K + nd, 8192)), 256, 0, s>>>(nrows, Q, ldq, perm, kept, K, defl, nd, Ds,
-                                                                            zs, Qw, DK, zK, Dd);
+                                                                            zs, Qw, DK, zK, Dd, status);
   return cudaGetLastError();
 }
 cudaError_t launch_bd_finish(int64_t nrows, const double* Qw, double* Q, int64_t ldq, int K, int nd, const double* DK,

@@ -567,12 +567,12 @@ cudaError_t launch_bd_z(int64_t nn, const double* Q, int64_t ldq, int64_t ra, in
 cudaError_t launch_bd_sort(int64_t nn, const double* D, const double* z, double* Ds, double* zs, int32_t* perm,
                            cudaStream_t s);
 cudaError_t launch_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, int32_t* defl, int32_t* rotp,
-                              double* rotcs, int32_t* cnt, double* rho, cudaStream_t s);
+                              double* rotcs, int32_t* cnt, double* rho, int* status, cudaStream_t s);
 cudaError_t launch_bd_rotate(int64_t nrows, double* Q, int64_t ldq, const int32_t* perm, const int32_t* rotp,
-                             const double* rotcs, int nr, cudaStream_t s);
+                             const double* rotcs, int nr, int* status, cudaStream_t s);
 cudaError_t launch_bd_gather(int64_t nrows, const double* Q, int64_t ldq, const int32_t* perm, const int32_t* kept,
                              int K, const int32_t* defl, int nd, const double* Ds, const double* zs, double* Qw,
-                             double* DK, double* zK, double* Dd, cudaStream_t s);
+                             double* DK, double* zK, double* Dd, int* status, cudaStream_t s);
 cudaError_t launch_bd_finish(int64_t nrows, const double* Qw, double* Q, int64_t ldq, int K, int nd, const double* DK,
                              const int32_t* org, const double* tau, const double* Dd, double* D, cudaStream_t s);
 cudaError_t launch_bd_copy_back(int64_t nrows, int64_t ncols, const double* Qw, double* Q, int64_t ldq,

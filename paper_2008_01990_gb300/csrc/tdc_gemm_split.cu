@@ -308,7 +308,7 @@ __global__ void __launch_bounds__(1024) k_split_pack(Plan P, int level, int64_t 
 // Digit images
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
-                                                 __nv_bfloat16* img) {
+                                                 __nv_bfloat16* img, int* status) {
   if (dnseg) nseg = (int)*dnseg;
   const int64_t total = segs[nseg].it_a;
   const int tid = threadIdx.x;
@@ -318,7 +318,12 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
     const int64_t local = w - sg.it_a;
     const int KB = (int)cdiv(sg.kk, BK);
     const int rt = (int)(local / KB), kb = (int)(local % KB);
-    __nv_bfloat16* tile = img + sg.a_img + ((int64_t)rt * KB + kb) * S * kATileElems;
+    const int64_t toff = sg.a_img + ((int64_t)rt * KB + kb) * S * kATileElems;
+    if (toff < 0 || toff + (int64_t)S * kATileElems > segs[nseg].a_img) {  // never write outside the images
+      if (threadIdx.x == 0) set_status(status, TDC_EUNSUPPORTED);
+      continue;
+    }
+    __nv_bfloat16* tile = img + toff;
     for (int u = tid; u < BM * (BK / 8); u += blockDim.x) {
       const int r = u % BM, kg = u / BM;  // BK/8 groups of 8 consecutive k
       const int row = rt * BM + r;
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
 // (64 columns x BK/8 groups of 8 poles).
 static_assert(BN * (BK / 8) == 128, "k_split_b maps 128 threads onto one B tile");
 __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
-                                                 __nv_bfloat16* img) {
+                                                 __nv_bfloat16* img, int* status) {
   if (dnseg) nseg = (int)*dnseg;
   const int64_t total = segs[nseg].it_b;
   const int tid = threadIdx.x & 127;
@@ -362,7 +367,12 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
     const int64_t local = w - sg.it_b;
     const int KB = (int)cdiv(sg.kk, BK);
     const int ct = (int)(local / KB), kb = (int)(local % KB);
-    __nv_bfloat16* tile = img + sg.b_img + ((int64_t)ct * KB + kb) * S * kBTileElems;
+    const int64_t toff = sg.b_img + ((int64_t)ct * KB + kb) * S * kBTileElems;
+    if (toff < 0 || toff + (int64_t)S * kBTileElems > segs[nseg].a_img) {  // never write outside the images
+      if ((threadIdx.x & 127) == 0) set_status(status, TDC_EUNSUPPORTED);
+      continue;
+    }
+    __nv_bfloat16* tile = img + toff;
     const int j = tid % BN, kg = tid / BN;  // 64 columns x BK/8 groups of 8 poles
     const int jj = ct * BN + j;
     double dorg = 0.0, tj = 1.0, sj = 0.0;
@@ -573,11 +583,20 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
     if (lane == 0) {
       long long g = 0;  // k-steps loaded by this CTA (stage g % kStages, use g / kStages)
       bool ok = true;
+      const int64_t img_end = segs[nseg].a_img;  // the list's images end here (the terminator)
       for (int64_t w = blockIdx.x; w < total && ok; w += gridDim.x) {
         const TileRef t = tile_ref(segs, nseg, w);
         const int akt = t.sg->a_kt > 0 ? t.sg->a_kt : t.KB;  // k-tiles per row tile of the A image
-        const uint8_t* ai = reinterpret_cast<const uint8_t*>(img + t.sg->a_img + (int64_t)t.rt * akt * S * kATileElems);
-        const uint8_t* bi = reinterpret_cast<const uint8_t*>(img + t.sg->b_img + (int64_t)t.ct * t.KB * S * kBTileElems);
+        const int64_t a0 = t.sg->a_img + (int64_t)t.rt * akt * S * kATileElems;
+        const int64_t b0 = t.sg->b_img + (int64_t)t.ct * t.KB * S * kBTileElems;
+        if (a0 < 0 || b0 < 0 || a0 + (int64_t)t.KB * S * kATileElems > img_end ||
+            b0 + (int64_t)t.KB * S * kBTileElems > img_end) {  // cannot happen for a built list; never read
+          set_status(status, TDC_EUNSUPPORTED);                 // outside the images
+          ok = false;
+          break;
+        }
+        const uint8_t* ai = reinterpret_cast<const uint8_t*>(img + a0);
+        const uint8_t* bi = reinterpret_cast<const uint8_t*>(img + b0);
         for (int kb = 0; kb < t.KB; ++kb, ++g) {
           const int st = (int)(g % kStages);
           if (g >= kStages && !wait_or_fail(&empty[st], (uint32_t)(((g - kStages) / kStages) & 1), budget, vfail)) {
@@ -802,12 +821,12 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
   if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
-static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
+static cudaError_t launch_split_digits(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S, int* status,
                                        __nv_bfloat16* img, cudaStream_t s) {
-  k_split_a<<<152 * 8, 256, 0, s>>>(segs, nseg, dnseg, S, img);
+  k_split_a<<<152 * 8, 256, 0, s>>>(segs, nseg, dnseg, S, img, status);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_split_b<<<152 * 8, 256, 0, s>>>(segs, nseg, dnseg, S, img);
+  k_split_b<<<152 * 8, 256, 0, s>>>(segs, nseg, dnseg, S, img, status);
   return cudaGetLastError();
 }
 
@@ -864,7 +883,7 @@ cudaError_t launch_gemm_split(const Plan& P, const LevelLaunch& L, int64_t g0, i
   if (e != cudaSuccess) return e;
   const int nseg = (int)(2 * (g1 - g0));  // bound; the kernels read the compacted count
   const int64_t* dn = P.m.sseg;
-  e = launch_split_digits(P.segs, nseg, dn, P.split_slices, P.img, s);
+  e = launch_split_digits(P.segs, nseg, dn, P.split_slices, P.status, P.img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   return launch_split_mma(P.segs, nseg, dn, P.split_slices, P.status, P.spin_budget, P.img, P.split_chunk_steps,
@@ -877,7 +896,7 @@ cudaError_t launch_split_list(const GemmSeg* segs, int nseg_bound, const int64_t
                               long long spin_budget, __nv_bfloat16* img, int chunk_steps, unsigned int* lvl_max,
                               cudaStream_t s, cudaEvent_t mid) {
   if (nseg_bound <= 0) return cudaSuccess;
-  cudaError_t e = launch_split_digits(segs, nseg_bound, dcount, S, img, s);
+  cudaError_t e = launch_split_digits(segs, nseg_bound, dcount, S, status, img, s);
   if (e != cudaSuccess) return e;
   if (mid) cudaEventRecord(mid, s);
   return launch_split_mma(segs, nseg_bound, dcount, S, status, spin_budget, img, chunk_steps, lvl_max, s);
@@ -885,7 +904,7 @@ cudaError_t launch_split_list(const GemmSeg* segs, int nseg_bound, const int64_t
 
 cudaError_t launch_seg_split(const GemmSeg* segs_dev, int nseg, int S, int* status, long long spin_budget,
                              __nv_bfloat16* img, int chunk_steps, cudaStream_t s) {
-  cudaError_t e = launch_split_digits(segs_dev, nseg, nullptr, S, img, s);
+  cudaError_t e = launch_split_digits(segs_dev, nseg, nullptr, S, status, img, s);
   if (e != cudaSuccess) return e;
   return launch_split_mma(segs_dev, nseg, nullptr, S, status, spin_budget, img, chunk_steps, nullptr, s);
 }

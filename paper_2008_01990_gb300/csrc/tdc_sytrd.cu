@@ -533,6 +533,7 @@ __global__ void k_trd_seg(GemmSeg* segs, int64_t m, int kk, const double* Aop, c
   end.it_a = RT * KB;
   end.it_b = CT * KB;
   end.it_t = RT * CT;
+  end.a_img = sg.b_img + CT * KB * S * kSplitBN * kSplitBK;  // the images' end
   segs[1] = end;
 }
 
@@ -741,6 +742,7 @@ __global__ void k_orm_segs(OrmStep O, GemmSeg* list1, GemmSeg* list2) {
   end.it_a = ia;
   end.it_b = ib;
   end.it_t = it;
+  end.a_img = img;  // the images' end
   list1[2 * O.ns] = end;
 
   const int64_t RT = (mb + kSplitBM - 1) / kSplitBM, KB = (O.kbp + kSplitBK - 1) / kSplitBK,
@@ -767,6 +769,7 @@ __global__ void k_orm_segs(OrmStep O, GemmSeg* list1, GemmSeg* list2) {
   e2.it_a = RT * KB;
   e2.it_b = CT * KB;
   e2.it_t = RT * CT;
+  e2.a_img = u.b_img + CT * KB * S * kSplitBN * kSplitBK;  // the images' end
   list2[1] = e2;
 }
 
