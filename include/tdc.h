@@ -162,7 +162,11 @@ int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
  *   ws      device workspace of at least tdc_workspace_size(n) bytes, 256-byte aligned
  *   o       options (NULL = defaults)
  * Errors: -1 n < 0; -2/-3 NULL d/e when n > 0 (e may be NULL when n = 1);
- * -4/-5 NULL lam/Q; -6 ldq < max(1,n); TDC_ENOWS; -9 invalid options; TDC_ECUDA. */
+ * -4/-5 NULL lam/Q; -6 ldq < max(1,n); TDC_ENOWS; -9 invalid options; TDC_ECUDA.
+ * A non-finite entry of d or e is read as zero (in every problem of a batch alike) and
+ * the stream's status records TDC_ENONFINITE: lam and Q are then the finite
+ * eigendecomposition of the input with those entries zeroed.  No scaling is applied:
+ * entries are expected well inside the FP64 range (|d|, |e| below about 2^400). */
 int tdc_eig(int64_t n, const double* d, const double* e, double* lam, double* Q, int64_t ldq, void* ws,
             size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream);
 

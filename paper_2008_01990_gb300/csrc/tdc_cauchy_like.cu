@@ -15,10 +15,6 @@
 
 namespace tdc {
 
-namespace {
-__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((1023 + e) << 20, 0); }
-}  // namespace
-
 // org_j: the row node nearest to w_j (d ascending); tau_j = w_j - d[org_j].
 __global__ void k_cl_nodes(int64_t n, const double* d, const double* w, int32_t* org, double* tau) {
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
@@ -53,9 +49,9 @@ __global__ void k_cl_cols(int64_t n, const double* d, const double* u, const dou
     for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
     if (lane == 0) {
       const double nrm = fabs(v[j]) * sqrt(s);
-      const int e = (scale && nrm > 0.0) ? ilogb(nrm) + 1 : 0;
+      const int e = scale ? exp_above(nrm) : 0;
       eb[j] = e;
-      scol[j] = scale ? v[j] * pow2i(-e) : v[j];
+      scol[j] = scale ? v[j] * pow2c(-e) : v[j];
     }
   }
 }
@@ -80,7 +76,7 @@ __global__ void k_cl_rows(int64_t m, int64_t K, const double* A, int64_t lda, un
 __global__ void k_cl_exps(int64_t n, const unsigned long long* maxsq, const int32_t* eb, int32_t* cexp,
                           int32_t* eA) {
   const double mx = sqrt(__longlong_as_double((long long)*maxsq));
-  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  const int e = exp_above(mx);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
     cexp[j] = eb[j] + e;
   if (blockIdx.x == 0 && threadIdx.x == 0) *eA = e;

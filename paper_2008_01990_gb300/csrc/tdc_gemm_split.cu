@@ -60,8 +60,6 @@ __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 
 // matrix, core matrices along K 64 elements apart, 8-row groups BK*8 elements apart)
 __device__ __forceinline__ int core_off(int r, int k) { return (r >> 3) * (BK * 8) + (k >> 3) * 64 + (r & 7) * 8 + (k & 7); }
 
-// 2^e for e in [-1022, 1023], built from its bits
-__device__ __forceinline__ double pow2(int e) { return __hiloint2double((1023 + e) << 20, 0); }
 
 // The S leading balanced base-256 digits of x (|x| <= 1 + O(eps)), as BF16 bit
 // patterns: F = round(x 2^56) as a two's-complement integer, written as
@@ -336,7 +334,7 @@ __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, 
           const int p = sg.plist ? sg.plist[q] : q;
           const int col = sg.acol ? sg.acol[p] : p;
           x = sg.A[(int64_t)row * sg.ars + (int64_t)col * sg.lda];
-          if (sg.aexp) x *= pow2(-sg.aexp);
+          if (sg.aexp) x *= pow2c(-sg.aexp);
         }
         digits_bf16(x, S, dig[i]);
       }
@@ -378,7 +376,7 @@ __global__ void __launch_bounds__(256) k_split_b(const GemmSeg* segs, int nseg, 
     double dorg = 0.0, tj = 1.0, sj = 0.0;
     if (jj < sg.K) {
       if (sg.Bd || sg.tgen) {
-        sj = sg.cexp ? pow2(-sg.cexp[jj]) : 1.0;
+        sj = sg.cexp ? pow2c(-sg.cexp[jj]) : 1.0;
       } else {
         const int jr = sg.bcol ? sg.bcol[jj] : jj;
         dorg = sg.D[sg.org[jr]];
@@ -746,8 +744,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
             const int j = t.ct * BN + c0 + i;
             if (j < sg.K) {
               const int pos = sg.cpos ? sg.cpos[j] : j;
-              double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
-              if (sg.oexp) v *= pow2(sg.oexp[j]);
+              double v = sg.cexp ? scale2(val[i], sg.cexp[j]) : val[i];
+              if (sg.oexp) v = scale2(v, sg.oexp[j]);
               double* cp = sg.C + row + (int64_t)pos * sg.ldc;
               if (sg.acc) *cp += v; else *cp = v;
             }
@@ -800,8 +798,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           const int j = t.ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            double v = sg.cexp ? val[i] * pow2(sg.cexp[j]) : val[i];
-            if (sg.oexp) v *= pow2(sg.oexp[j]);
+            double v = sg.cexp ? scale2(val[i], sg.cexp[j]) : val[i];
+            if (sg.oexp) v = scale2(v, sg.oexp[j]);
             double* cp = sg.C + row + (int64_t)pos * sg.ldc;
             if (sg.acc) *cp += v; else *cp = v;
           }

@@ -43,11 +43,12 @@ __global__ void k_dmod(Plan P) {
     int pi = find_problem_by_slot(P.prob, P.nprob, s);
     const Problem& p = P.prob[pi];
     int64_t r = s - p.voff;
-    double d = P.d[p.off_de + r];
-    bool ok = isfinite(d);
+    const double d0 = P.d[p.off_de + r];
+    bool ok = isfinite(d0);
     if (r + 1 < p.n) ok = ok && isfinite(P.e[p.off_de + r]);
-    if (is_boundary(r, p.n, p.depth)) d -= fabs(P.e[p.off_de + r - 1]);
-    if (is_boundary(r + 1, p.n, p.depth)) d -= fabs(P.e[p.off_de + r]);
+    double d = finite_or_zero(d0);
+    if (is_boundary(r, p.n, p.depth)) d -= fabs(finite_or_zero(P.e[p.off_de + r - 1]));
+    if (is_boundary(r + 1, p.n, p.depth)) d -= fabs(finite_or_zero(P.e[p.off_de + r]));
     if (!ok) set_status(P.status, TDC_ENONFINITE);
     P.v.dmod[s] = d;
   }
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(64) k_leaf(Plan P, int64_t nleaves) {
   for (int k = tid; k < L * L; k += blockDim.x) Qs[k] = ((k % L) == (k / L)) ? 1.0 : 0.0;
   for (int k = tid; k < L; k += blockDim.x) {
     dd[k] = P.v.dmod[p.voff + lo + k];
-    ee[k] = (k < L - 1) ? P.e[p.off_de + lo + k] : 0.0;
+    ee[k] = (k < L - 1) ? finite_or_zero(P.e[p.off_de + lo + k]) : 0.0;
   }
   if (tid == 0) ctrl[4] = (L <= 1) ? 1 : 0;
   __syncthreads();
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(1024) k_leaf_multi(Plan P, int64_t nleaves, in
     if (k < L) {
       const Problem& pr = P.prob[sprob[l]];
       dd[k] = P.v.dmod[pr.voff + slo[l] + k];
-      ee[k] = (k < L - 1) ? P.e[pr.off_de + slo[l] + k] : 0.0;
+      ee[k] = (k < L - 1) ? finite_or_zero(P.e[pr.off_de + slo[l] + k]) : 0.0;
     }
   }
   __syncthreads();
@@ -901,7 +902,7 @@ __device__ __forceinline__ Slot slot_of(const Plan& P, int level, int nprob_act,
   o.j = (int)(r - lo);
   o.K = P.m.K[o.g];
   o.v0 = p.voff + lo;
-  o.rho = 2.0 * fabs(P.e[p.off_de + mid - 1]);
+  o.rho = 2.0 * fabs(finite_or_zero(P.e[p.off_de + mid - 1]));
   o.valid = o.j < o.K;
   return o;
 }

@@ -15,14 +15,6 @@
 
 namespace tdc {
 
-namespace {
-// e with mx < 2^e (0 for mx = 0), within the range of pow2 scale factors
-__device__ __forceinline__ int exp_above_t(double mx) {
-  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
-  return e < -1000 ? -1000 : (e > 1000 ? 1000 : e);
-}
-}  // namespace
-
 // One block: w0 = |t|, then L passes w_{l}[i] = max(w_{l-1}[i], w_{l-1}[i + 2^(l-1)]) between
 // the two halves of `win` (2 x (2n - 1) doubles); eb[j] from the window of column j.
 __global__ void __launch_bounds__(1024) k_tp_windows(int64_t n, const double* t, int kind, double* win,
@@ -44,7 +36,7 @@ __global__ void __launch_bounds__(1024) k_tp_windows(int64_t n, const double* t,
   // a holds maxima over windows of width w (w <= n < 2w)
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
     const int64_t s = kind == 1 ? n - 1 - j : j;
-    eb[j] = exp_above_t(fmax(a[s], a[s + n - w]));
+    eb[j] = exp_above(fmax(a[s], a[s + n - w]));
   }
 }
 
@@ -61,7 +53,7 @@ __global__ void __launch_bounds__(256) k_vd_max(int64_t n, const double* x, unsi
 __global__ void __launch_bounds__(256) k_vd_exps(int64_t n, const unsigned long long* mx, int32_t* eb) {
   const double m = __longlong_as_double((long long)*mx);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-    eb[j] = exp_above_t(pow(m, (double)j) * (1.0 + 0x1p-40));
+    eb[j] = exp_above(pow(m, (double)j) * (1.0 + 0x1p-40));
 }
 
 __global__ void __launch_bounds__(256) k_zero_i32(int64_t n, int32_t* a) {
@@ -97,7 +89,7 @@ __global__ void __launch_bounds__(256) k_tp_rows(int64_t m, int64_t n, const dou
 // scaled back by 2^cexp[j] (B's column scale) and then by 2^oexp[j] (A's scale).
 __global__ void __launch_bounds__(256) k_tp_exps(int64_t n, const unsigned long long* maxsq, int32_t* oexp,
                                                 int32_t* eA) {
-  const int e = exp_above_t(sqrt(__longlong_as_double((long long)*maxsq)));
+  const int e = exp_above(sqrt(__longlong_as_double((long long)*maxsq)));
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
     oexp[j] = e;
   if (blockIdx.x == 0 && threadIdx.x == 0) *eA = e;

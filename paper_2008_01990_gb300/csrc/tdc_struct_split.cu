@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(128) k_ss_rmat(SSArgs A) {
       mx = fmax(mx, fabs(x));
     }
   }
-  A.cexp[it * m + c] = mx > 1.0 ? ilogb(mx) + 1 : 0;
+  A.cexp[it * m + c] = mx > 1.0 ? exp_above(mx) : 0;
 }
 
 // The stand-alone product's plain split segment runs only if the structured path

@@ -37,11 +37,6 @@ namespace tdc {
 
 namespace {
 
-__device__ __forceinline__ double pow2i(int e) { return __hiloint2double((1023 + e) << 20, 0); }
-
-// exponent e with |x| < 2^e for the largest magnitude x (0 for x = 0)
-__device__ __forceinline__ int exp_above(double mx) { return mx > 0.0 ? ilogb(mx) + 1 : 0; }
-
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
@@ -490,7 +485,7 @@ __global__ void __launch_bounds__(256) k_trd_ops(int64_t t0, int64_t n, int nb, 
                                                 double* Bop, int32_t* cexp) {
   const int64_t m = n - t0;
   const int ew = exp_above(__longlong_as_double((long long)*wmax));
-  const double dn = pow2i(-ew), up = pow2i(ew);
+  const double dn = pow2c(-ew), up = pow2c(ew);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
     double mx = 0.0;
     for (int c = 0; c < nb; ++c) {
@@ -671,7 +666,7 @@ __global__ void __launch_bounds__(256) k_orm_xexp(int64_t rows, int64_t ncols, c
     if (lane == 0) {
       const double nrm = sqrt(s) * (1.0 + 0x1p-20);
       int e = exp_above(nrm);
-      if (pow2i(e) < nrm) ++e;
+      if (pow2c(e) < nrm && e < 1022) ++e;
       xexp[j] = e;
     }
   }

@@ -57,6 +57,32 @@ def test_graph_replay_matches_direct_call(tdc):
     assert tdc.sync_status() == 0
 
 
+def test_nonfinite_problem_leaves_the_others_intact(tdc):
+    """One problem of a batch with a NaN off-diagonal: the call reports TDC_ENONFINITE,
+    that problem is solved with the entry read as zero, and the others are untouched."""
+    from scipy.linalg import eigvalsh_tridiagonal
+    sizes = [300, 500, 700]
+    d, e, offs, qoffs = batch(sizes, 5)
+    e[offs[1] + 123] = np.nan
+    o = tdc.default_opts(leaf=16)
+    lam = torch.zeros(int(offs[-1]), dtype=torch.float64, device=DEV)
+    Q = torch.zeros(int(qoffs[-1]), dtype=torch.float64, device=DEV)
+    tdc.eig_batched(sizes, torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), offs[:-1], qoffs[:-1], lam, Q,
+                    o)
+    assert tdc.sync_status() == tdc.TDC_ENONFINITE
+    e[offs[1] + 123] = 0.0
+    lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
+    for i, n in enumerate(sizes):
+        di, ei = d[offs[i]:offs[i] + n], e[offs[i]:offs[i] + n - 1]
+        li = lam[offs[i]:offs[i] + n]
+        Qi = Q[qoffs[i]:qoffs[i] + n * n].reshape(n, n).T
+        ref = eigvalsh_tridiagonal(di, ei)
+        assert np.max(np.abs(li - ref)) <= 50 * n * np.finfo(float).eps * np.max(np.abs(ref))
+        res, orth = ratios(di, ei, li, Qi)
+        assert res <= 50 and orth <= 50, (i, res, orth)
+    assert tdc.sync_status() == 0
+
+
 def test_autotuner_picks_and_caches(tdc, tmp_path):
     from paper_2008_01990_gb300 import autotune
     sizes = inputs.batched_sizes(48, 64, 600, 41)

@@ -194,12 +194,25 @@ def test_status_nonconvergence_then_recovery(tdc, orc):
     check_vs_oracle(orc, d, e, lam, Q, 32)
 
 
-def test_status_nonfinite_input(tdc):
-    n = 100
+@pytest.mark.parametrize("n,where,val", [(100, "d", np.nan), (3000, "e", np.nan), (9000, "d", np.inf),
+                                         (9000, "e", -np.inf)])
+def test_status_nonfinite_input(tdc, n, where, val):
+    """A non-finite d or e entry is read as zero: the call reports TDC_ENONFINITE and
+    returns the eigendecomposition of the input with that entry zeroed (finite, so no
+    NaN reaches the orderings and ranks the kernels index with, on every merge path the
+    default options take up to n = 9000); the next call is clean."""
+    from scipy.linalg import eigvalsh_tridiagonal
     d, e = inputs.uniform_tridiag(n, 9)
-    d[37] = np.nan
-    tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), tdc.default_opts(leaf=16))
+    (d if where == "d" else e)[n // 3] = val
+    lam, Q = tdc.eig(torch.tensor(d, device=DEV), torch.tensor(e, device=DEV), tdc.default_opts(leaf=16))
     assert tdc.sync_status() == tdc.TDC_ENONFINITE
+    assert bool(torch.isfinite(lam).all()) and bool(torch.isfinite(Q).all())
+    (d if where == "d" else e)[n // 3] = 0.0
+    lam, ref = lam.cpu().numpy(), eigvalsh_tridiagonal(d, e)
+    assert np.max(np.abs(lam - ref)) <= 50 * n * EPS * np.max(np.abs(ref))
+    if n <= 3000:
+        res, orth = ratios(d, e, lam, Q.cpu().numpy())
+        assert res <= 50 and orth <= 50, (res, orth)
     assert tdc.sync_status() == 0
 
 

@@ -156,6 +156,54 @@ def test_syevd_split_merge_mode(tdc):
     assert res <= 50 and orth <= 50, (res, orth)
 
 
+def test_sytrd_subnormal_rows_stay_finite(tdc):
+    """Rows and columns scaled down through the subnormal range in quarter binades: the
+    split update's per-column scales come from row maxima down to 2^-1074, and each must
+    stay a normal power of two (2^+-1024 built from exponent bits is infinite, and one
+    infinite scale turns a zero entry into NaN).  T stays finite and Q^T A Q = T."""
+    n = 1024
+    A = inputs.dense_sym("uniform", n, seed=1024)
+    s = np.ones(n)
+    s[600:900] = 2.0 ** (-1000.0 - 0.25 * np.arange(300))
+    B = np.tril((A * s[:, None]) * s[None, :])
+    B = B + np.tril(B, -1).T
+    d, e, tau, R = tdc.sytrd(torch.tensor(B, device=DEV), check=True)
+    assert bool(torch.isfinite(d).all() and torch.isfinite(e).all() and torch.isfinite(tau).all())
+    d, e = d.cpu().numpy(), e.cpu().numpy()
+    Q = gpu_q(tdc, R.t().contiguous().t(), tau, n)
+    nB = np.linalg.norm(B, 2)
+    assert np.abs(Q.T @ Q - np.eye(n)).sum(axis=0).max() / (n * EPS) <= 50
+    assert np.abs(Q.T @ B @ Q - tri(d, e)).sum(axis=0).max() / (n * EPS * nB) <= 50
+
+
+def test_band_matrix_reduction_and_solve(tdc):
+    """A band matrix of order 8192, half-bandwidth 8: its reflectors fill in behind a
+    front whose entries decay through the whole exponent range, down to subnormals, so
+    the split updates see every scale exponent.  T is finite with the eigenvalues of A
+    (LAPACK's banded solver as reference); the composed solver's eigenpairs pass the
+    residual and orthogonality ratios on sampled columns.  Only T's spectrum is compared,
+    not its entries: the reduction of this matrix is backward stable but T itself is
+    sensitive (two stable reductions, LAPACK's and the oracle's, part at column 132)."""
+    from scipy.linalg import eig_banded, eigvalsh_tridiagonal
+    from oracle import banded as bo
+    n, b = 8192, 8
+    AB = inputs.band_sym("uniform", n, b, seed=1)
+    ref = eig_banded(AB, lower=True, eigvals_only=True)
+    A = torch.tensor(bo.dense_from_band(AB), device=DEV)
+    nA = float(np.max(np.abs(ref)))
+    d, e, tau, R = tdc.sytrd(A, check=True)
+    assert bool(torch.isfinite(d).all() and torch.isfinite(e).all() and torch.isfinite(tau).all())
+    lt = eigvalsh_tridiagonal(d.cpu().numpy(), e.cpu().numpy())
+    assert np.max(np.abs(lt - ref)) <= 50 * n * EPS * nA
+    lam, Z = tdc.syevd(A, check=True)
+    assert np.max(np.abs(lam.cpu().numpy() - ref)) <= 50 * n * EPS * nA
+    idx = torch.tensor(np.unique((inputs.SplitMix64(8).uniform01(256) * n).astype(np.int64)), device=DEV)
+    Zs = Z[:, idx]
+    res = torch.abs(A @ Zs - Zs * lam[idx]).sum(dim=0).max().item() / (n * nA * EPS)
+    orth = torch.abs(Z.t() @ Zs - torch.eye(n, dtype=torch.float64, device=DEV)[:, idx]).sum(dim=0).max().item()
+    assert res <= 50 and orth / (n * EPS) <= 50, (res, orth / (n * EPS))
+
+
 def test_sytrd_barrier_timeout_reports_status(tdc):
     """A panel whose grid barriers may poll only once gives up with TDC_ETIMEOUT instead of
     waiting; the context stays usable and the next call succeeds."""
