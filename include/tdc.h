@@ -24,7 +24,10 @@
  *     also use a second, high-priority stream of the calling host thread
  *     (created on first use and kept) for each level's products, forked from
  *     and joined back into `stream` with events: the call stays ordered on
- *     `stream` and can be captured in a CUDA graph like single-stream work;
+ *     `stream` and can be captured in a CUDA graph like single-stream work.
+ *     That stream and the thread's event pool are created by the first call
+ *     from each host thread on each device, so make that call before capturing
+ *     from the thread;
  *   - the return value is a status: TDC_OK (0); -i when argument i (1-based)
  *     is invalid, checked on the host before anything is enqueued; or one of
  *     the TDC_E* codes below.  Device-side failures (secular non-convergence,
@@ -200,7 +203,9 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
  * digit images would not fit, and larger n returns TDC_ETOOLARGE before
  * anything is enqueued.  The first call on each
  * device looks the array's device address up (cudaGetSymbolAddress, with that
- * device current), so make that first call before any stream capture.  All
+ * device current), and the first call from each host thread on each device creates
+ * that thread's second stream and event pool, so make those first calls before
+ * any stream capture.  All
  * calls share the one array and it keeps the last call's contents (nothing in it
  * has to start at zero): calls that overlap on the GPU race on it and must be
  * ordered by the caller.  Allocates nothing; collect_stats is ignored.

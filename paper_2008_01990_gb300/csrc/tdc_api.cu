@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -1596,10 +1597,20 @@ void band_nodes(int64_t lo, int64_t hi, int64_t leafmax, std::vector<BandNode>& 
 }
 
 struct BandLayout {
-  size_t ABw, wv, Ad, Dcur, z, Ds, zs, perm, kept, defl, rotp, rotcs, cnt, DK, zK, Dd, org, tau, zhat, scol, iota, Qw,
-      prod, leaf, total;
-  size_t leaf_bytes;
+  size_t ABw, wv, Ab, Zb, dl, el, taul, Dcur, z, Ds, zs, perm, kept, defl, rotp, rotcs, cnt, DK, zK, Dd, org, tau, zhat,
+      scol, iota, Qw, prod, leafws, total;
+  size_t leafws_bytes;
 };
+
+// sizes of the leaves (post order) and their first rows
+void band_leaves(const std::vector<BandNode>& nodes, int64_t leafmax, std::vector<int64_t>& lo,
+                 std::vector<int64_t>& sz) {
+  for (const BandNode& nd : nodes)
+    if (nd.hi - nd.lo <= leafmax) {
+      lo.push_back(nd.lo);
+      sz.push_back(nd.hi - nd.lo);
+    }
+}
 
 BandLayout band_layout(int64_t n, int64_t b, const tdc_opts& op) {
   BandLayout L;
@@ -1610,7 +1621,11 @@ BandLayout band_layout(int64_t n, int64_t b, const tdc_opts& op) {
   band_nodes(0, std::max<int64_t>(n, 1), band_leafmax(b), nodes);
   L.ABw = take(o, sizeof(double) * (size_t)(b + 1) * nn);
   L.wv = take(o, sizeof(double) * nodes.size() * (size_t)std::max<int64_t>(b, 1) * (size_t)(b + 1));
-  L.Ad = take(o, sizeof(double) * (size_t)(lm * lm));
+  L.Ab = take(o, sizeof(double) * nn * (size_t)lm);
+  L.Zb = take(o, sizeof(double) * nn * (size_t)lm);
+  L.dl = take(o, sizeof(double) * nn);
+  L.el = take(o, sizeof(double) * nn);
+  L.taul = take(o, sizeof(double) * nn);
   L.Dcur = take(o, sizeof(double) * nn);
   L.z = take(o, sizeof(double) * nn);
   L.Ds = take(o, sizeof(double) * nn);
@@ -1633,10 +1648,12 @@ BandLayout band_layout(int64_t n, int64_t b, const tdc_opts& op) {
   size_t pb = 0;
   tdc_cauchy_gemm_workspace_size((int64_t)nn, (int64_t)nn, TDC_MERGE_SPLIT, &op, &pb);
   L.prod = take(o, pb);
+  std::vector<int64_t> llo, lsz;
+  band_leaves(nodes, band_leafmax(b), llo, lsz);
   size_t we = 0;
-  tdc_workspace_size(lm, &op, &we);
-  L.leaf_bytes = syevd_vec_bytes(lm) + std::max(we, std::max(trd_layout(lm).total, orm_layout(lm, lm).total)) + 256;
-  L.leaf = take(o, L.leaf_bytes);
+  tdc_eig_batched_workspace_size((int32_t)lsz.size(), lsz.data(), &op, &we);
+  L.leafws_bytes = we + 256;
+  L.leafws = take(o, L.leafws_bytes);
   L.total = o + 256;
   return L;
 }
@@ -1647,7 +1664,6 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
   const int64_t ldw = b + 1;
   double* ABw = (double*)(base + L.ABw);
   double* wv = (double*)(base + L.wv);
-  double* Ad = (double*)(base + L.Ad);
   double* Dcur = (double*)(base + L.Dcur);
   double* z = (double*)(base + L.z);
   double* Ds = (double*)(base + L.Ds);
@@ -1669,9 +1685,20 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
   int32_t* iota = (int32_t*)(base + L.iota);
   double* Qw = (double*)(base + L.Qw);
   char* prod = base + L.prod;
-  char* leaf = base + L.leaf;
   std::vector<BandNode> nodes;
   band_nodes(0, n, band_leafmax(b), nodes);
+  // scratch of the sort and the deflation: arrays that the gather, the secular solve and
+  // the product write only after them
+  BdScratch S;
+  S.sk = DK;
+  S.si = org;
+  S.surv = org;
+  S.slot = (int32_t*)zK;
+  S.c = tau;
+  S.s = zhat;
+  S.w = DK;
+  S.dp = scol;
+  S.dn = Dd;
   if (launch_bd_copy_band(n, (int)b, AB, ldab, ABw, cs) != cudaSuccess) return TDC_ECUDA;
   if (launch_bd_zero(n, n, Q, ldq, cs) != cudaSuccess) return TDC_ECUDA;
   k_iota<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, cs>>>(iota, n);
@@ -1682,34 +1709,59 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
     const int64_t m = nd.lo + (nd.hi - nd.lo) / 2;
     if (launch_bd_tear(ABw, ldw, (int)b, m, wv + i * b * (b + 1), cs) != cudaSuccess) return TDC_ECUDA;
   }
-  const size_t lvb = align_up(sizeof(double) * (size_t)std::min<int64_t>(n, band_leafmax(b)));
+  // leaves, all at once: dense blocks of the torn band reduced to tridiagonal form (a block
+  // each), their tridiagonals solved as one batch, the eigenvectors back-transformed into Q
+  {
+    const int64_t lm = std::min<int64_t>(n, band_leafmax(b));
+    std::vector<int64_t> llo, lsz;
+    band_leaves(nodes, band_leafmax(b), llo, lsz);
+    BdLeafArgs A;
+    memset(&A, 0, sizeof(A));
+    A.ABw = ABw;
+    A.ldab = ldw;
+    A.b = (int32_t)b;
+    A.lmax = lm;
+    A.Ab = (double*)(base + L.Ab);
+    A.d = (double*)(base + L.dl);
+    A.e = (double*)(base + L.el);
+    A.tau = (double*)(base + L.taul);
+    A.Zb = (double*)(base + L.Zb);
+    A.Q = Q;
+    A.ldq = ldq;
+    std::unique_ptr<BdLeafTable> T(new BdLeafTable);  // the kernel-parameter table (copied at launch)
+    for (int pass = 0; pass < 2; ++pass) {
+      for (size_t c0 = 0; c0 < llo.size(); c0 += kBdLeafChunk) {
+        A.nleaf = (int32_t)std::min<size_t>(kBdLeafChunk, llo.size() - c0);
+        for (int32_t t = 0; t < A.nleaf; ++t) {
+          T->lo[t] = llo[c0 + t];
+          T->L[t] = (int32_t)lsz[c0 + t];
+        }
+        const cudaError_t e = pass == 0 ? launch_bd_leaf_trd(A, *T, cs) : launch_bd_leaf_back(A, *T, cs);
+        if (e != cudaSuccess) return TDC_ECUDA;
+      }
+      if (pass == 0) {
+        std::vector<int64_t> oq(llo.size());
+        for (size_t t = 0; t < llo.size(); ++t) oq[t] = llo[t] * lm;
+        const int r = tdc_eig_batched((int32_t)llo.size(), lsz.data(), llo.data(), oq.data(), A.d, A.e, lam,
+                                      (double*)(base + L.Zb), base + L.leafws, L.leafws_bytes, &op, cs);
+        if (r != TDC_OK) return r;
+      }
+    }
+  }
   for (size_t i = 0; i < nodes.size(); ++i) {
     const BandNode& nd = nodes[i];
     const int64_t nn = nd.hi - nd.lo;
     double* Qn = Q + nd.lo + nd.lo * ldq;
-    if (nn <= band_leafmax(b)) {  // leaf: dense eigensolve of the torn block
-      if (launch_bd_leaf_dense(ABw, ldw, (int)b, nd.lo, nn, Ad, cs) != cudaSuccess) return TDC_ECUDA;
-      double* d = (double*)leaf;
-      double* e = (double*)(leaf + lvb);
-      double* tv = (double*)(leaf + 2 * lvb);
-      char* rest = leaf + 3 * lvb;
-      const size_t rest_bytes = L.leaf_bytes - 3 * lvb;
-      int r = sytrd_run(nn, Ad, nn, d, e, tv, rest, op, st, cs);
-      if (r != TDC_OK) return r;
-      r = tdc_eig(nn, d, e, lam + nd.lo, Qn, ldq, rest, rest_bytes, &op, cs);
-      if (r != TDC_OK) return r;
-      r = ormtr_run(nn, nn, Ad, nn, tv, Qn, ldq, rest, op, st, cs);
-      if (r != TDC_OK) return r;
-      continue;
-    }
+    if (nn <= band_leafmax(b)) continue;  // a leaf, solved above
     const int64_t m = nd.lo + (nd.hi - nd.lo) / 2;
     if (cudaMemcpyAsync(Dcur, lam + nd.lo, sizeof(double) * nn, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
       return TDC_ECUDA;
     for (int64_t k = 0; k < b; ++k) {
       const double* w = wv + i * b * (b + 1) + k * (b + 1);
       if (launch_bd_z(nn, Qn, ldq, (m - b + k) - nd.lo, m - nd.lo, (int)b, w, z, cs) != cudaSuccess) return TDC_ECUDA;
-      if (launch_bd_sort(nn, Dcur, z, Ds, zs, perm, cs) != cudaSuccess) return TDC_ECUDA;
-      if (launch_bd_deflate(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rhod, st, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_sort(nn, Dcur, z, Ds, zs, perm, S, cs) != cudaSuccess) return TDC_ECUDA;
+      if (launch_bd_deflate(nn, Ds, zs, kept, defl, rotp, rotcs, cnt, rhod, S, st, cs) != cudaSuccess)
+        return TDC_ECUDA;
       int32_t hc[3] = {0, 0, 0};
       double hrho = 0.0;
       if (cudaMemcpyAsync(hc, cnt, sizeof(hc), cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
@@ -1732,7 +1784,7 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
       if (launch_bd_finish(nn, Qw, Qn, ldq, K, ndf, DK, org, tau, Dd, Dcur, cs) != cudaSuccess) return TDC_ECUDA;
     }
     // ascending eigenvalues and the columns in that order
-    if (launch_bd_sort(nn, Dcur, nullptr, Ds, nullptr, perm, cs) != cudaSuccess) return TDC_ECUDA;
+    if (launch_bd_sort(nn, Dcur, nullptr, Ds, nullptr, perm, S, cs) != cudaSuccess) return TDC_ECUDA;
     if (launch_bd_gather(nn, Qn, ldq, perm, iota, (int)nn, defl, 0, Ds, Ds, Qw, DK, zK, Dd, st, cs) != cudaSuccess)
       return TDC_ECUDA;
     if (launch_bd_copy_back(nn, nn, Qw, Qn, ldq, cs) != cudaSuccess) return TDC_ECUDA;

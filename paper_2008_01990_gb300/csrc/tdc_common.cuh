@@ -587,14 +587,51 @@ cudaError_t launch_dft_tables(int64_t n, double* cosv, double* msinv, cudaStream
 // symmetric band divide and conquer (tdc_banded.cu)
 cudaError_t launch_bd_copy_band(int64_t n, int b, const double* AB, int64_t ldab, double* ABw, cudaStream_t s);
 cudaError_t launch_bd_tear(double* ABw, int64_t ldab, int b, int64_t m, double* wv, cudaStream_t s);
-cudaError_t launch_bd_leaf_dense(const double* ABw, int64_t ldab, int b, int64_t lo, int64_t L, double* Ad,
-                                 cudaStream_t s);
+// The leaves of the band tree, all at once: dense block of leaf t (rows [lo, lo + L) of the
+// torn band) at Ab + lo lmax (ld L), its tridiagonal in d, e and reflector scalars in tau at
+// offset lo; the tridiagonal eigenvectors Zb + lo lmax (ld L) back-transformed into the
+// diagonal block of Q.
+constexpr int kBdLeafChunk = 1024;
+constexpr int kBdLeafThreads = 512;
+struct BdLeafTable {
+  int64_t lo[kBdLeafChunk];
+  int32_t L[kBdLeafChunk];
+};
+struct BdLeafArgs {
+  const double* ABw;
+  int64_t ldab;
+  int32_t b;
+  int32_t nleaf;  // leaves in this launch's table
+  int64_t lmax;
+  double* Ab;
+  double* d;
+  double* e;
+  double* tau;
+  const double* Zb;
+  double* Q;
+  int64_t ldq;
+};
+cudaError_t launch_bd_leaf_trd(const BdLeafArgs& A, const BdLeafTable& T, cudaStream_t s);
+cudaError_t launch_bd_leaf_back(const BdLeafArgs& A, const BdLeafTable& T, cudaStream_t s);
 cudaError_t launch_bd_z(int64_t nn, const double* Q, int64_t ldq, int64_t ra, int64_t rb, int b, const double* w,
                         double* z, cudaStream_t s);
+// Scratch of the band sort and deflation (arrays of nn entries, free while they run).
+struct BdScratch {
+  double* sk;      // sort: the chunks' sorted keys
+  int32_t* si;     // sort: their indices
+  int32_t* surv;   // deflation: sorted positions of the poles surviving type 1
+  int32_t* slot;   // deflation: deflated entry keyed by the position at which the scan deflates it
+  double* c;       // deflation: speculative rotation of each consecutive survivor pair: c, s,
+  double* s;       //   the combined weight and the two new poles
+  double* w;
+  double* dp;
+  double* dn;
+};
 cudaError_t launch_bd_sort(int64_t nn, const double* D, const double* z, double* Ds, double* zs, int32_t* perm,
-                           cudaStream_t s);
+                           const BdScratch& S, cudaStream_t s);
 cudaError_t launch_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, int32_t* defl, int32_t* rotp,
-                              double* rotcs, int32_t* cnt, double* rho, int* status, cudaStream_t s);
+                              double* rotcs, int32_t* cnt, double* rho, const BdScratch& S, int* status,
+                              cudaStream_t s);
 cudaError_t launch_bd_rotate(int64_t nrows, double* Q, int64_t ldq, const int32_t* perm, const int32_t* rotp,
                              const double* rotcs, int nr, int* status, cudaStream_t s);
 cudaError_t launch_bd_gather(int64_t nrows, const double* Q, int64_t ldq, const int32_t* perm, const int32_t* kept,

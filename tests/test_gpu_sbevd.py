@@ -24,7 +24,8 @@ def tdc():
 
 @pytest.mark.parametrize("name,n,b", [("uniform", 5, 1), ("uniform", 100, 3), ("uniform", 300, 1),
                                       ("uniform", 600, 4), ("uniform", 1100, 8), ("laplace", 700, 5),
-                                      ("graded", 513, 2), ("uniform", 2000, 16), ("uniform", 40, 0)])
+                                      ("graded", 513, 2), ("uniform", 2000, 16), ("uniform", 40, 0),
+                                      ("uniform", 1, 0), ("uniform", 257, 8), ("uniform", 1500, 64)])
 def test_sbevd_vs_oracle(tdc, orc, name, n, b):
     AB = inputs.band_sym(name, n, b, seed=n + b)
     lam, Q = tdc.sbevd(torch.tensor(AB, device=DEV), check=True)
@@ -41,6 +42,24 @@ def test_sbevd_vs_oracle(tdc, orc, name, n, b):
     for i in np.where(gap > 1e-3 * nA)[0][:32]:
         sg = np.sign(Q[:, i] @ Qo[:, i])
         assert np.max(np.abs(sg * Q[:, i] - Qo[:, i])) <= 1e-9
+
+
+def test_sbevd_clustered_laplace_2500(tdc):
+    """The 1-D operator coupled to 8 neighbours at n = 2500 (many close eigenvalues, so many
+    type-2 deflations in chains): eigenvalues against LAPACK's banded solver, residual and
+    orthogonality ratios <= 50."""
+    from scipy.linalg import eig_banded
+    n, b = 2500, 8
+    AB = inputs.band_sym("laplace", n, b)
+    lam, Q = tdc.sbevd(torch.tensor(AB, device=DEV), check=True)
+    lam, Q = lam.cpu().numpy(), Q.cpu().numpy()
+    ref = eig_banded(AB, lower=True, eigvals_only=True)
+    A = bo.dense_from_band(AB)
+    nA = np.abs(ref).max()
+    assert np.max(np.abs(lam - ref)) <= 50 * n * EPS * nA
+    res = np.abs(A @ Q - Q * lam).sum(axis=0).max() / (n * nA * EPS)
+    orth = np.abs(Q.T @ Q - np.eye(n)).sum(axis=0).max() / (n * EPS)
+    assert res <= 50 and orth <= 50, (res, orth)
 
 
 def test_sbevd_tridiagonal_case_matches_eig(tdc):
