@@ -236,7 +236,8 @@ int tdc_eig_backward_batched(int32_t batch, int64_t n, const double* lam, const 
  * D[K] strictly ascending, z[K] nonzero, rho > 0.  Writes org[K] (int32: index of
  * the pole the root is measured from, j or j+1), tau[K] (lambda_j = D[org_j] + tau_j),
  * zhat[K] (Loewner recomputation) and s[K] (column normalisers of Eq. (Q_Cauchy)).
- * ws of tdc_rank_one_workspace_size(K) bytes. */
+ * ws: device scratch of tdc_rank_one_workspace_size(K) bytes (the FP32 copies of the
+ * poles for the roots' pre-iteration, about 20 K bytes); smaller or NULL: TDC_ENOWS. */
 int tdc_rank_one_workspace_size(int64_t K, size_t* bytes);
 int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_t* org, double* tau,
                  double* zhat, double* s, int32_t max_iter, void* ws, size_t ws_bytes, tdc_stream_t stream);

@@ -872,8 +872,16 @@ int tdc_eig_batched(int32_t batch, const int64_t* n_host, const int64_t* off_de_
 int tdc_rank_one_workspace_size(int64_t K, size_t* bytes) {
   if (K < 0) return -1;
   if (!bytes) return -2;
-  *bytes = 256;
+  *bytes = rank_one_scratch_bytes(K) + 256;
   return TDC_OK;
+}
+
+// the FP32 pre-iteration scratch of a rank-one solve carved from 256-byte aligned memory
+static void rank_one_carve(char* base, int64_t K, double*& zz, float2*& xz, float*& xlo) {
+  const size_t k = (size_t)std::max<int64_t>(K, 1);
+  zz = (double*)base;
+  xz = (float2*)(base + align_up(sizeof(double) * k));
+  xlo = (float*)(base + align_up(sizeof(double) * k) + align_up(sizeof(float2) * k));
 }
 
 int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_t* org, double* tau, double* zhat,
@@ -888,11 +896,14 @@ int tdc_rank_one(int64_t K, const double* D, const double* z, double rho, int32_
   if (!zhat) return -7;
   if (!s) return -8;
   if (max_iter < 1) return -9;
-  (void)ws;
-  (void)ws_bytes;
+  if (!ws || ws_bytes < rank_one_scratch_bytes(K) + 256) return TDC_ENOWS;
   int* st = begin_status((cudaStream_t)stream);
   if (!st) return TDC_ECUDA;
-  cudaError_t e = launch_rank_one(D, z, K, rho, max_iter, org, tau, zhat, s, st, (cudaStream_t)stream);
+  double* zz;
+  float2* xz;
+  float* xlo;
+  rank_one_carve((char*)(((uintptr_t)ws + 255) & ~(uintptr_t)255), K, zz, xz, xlo);
+  cudaError_t e = launch_rank_one(D, z, K, rho, max_iter, org, tau, zhat, s, zz, xz, xlo, st, (cudaStream_t)stream);
   return e == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
@@ -1598,7 +1609,7 @@ void band_nodes(int64_t lo, int64_t hi, int64_t leafmax, std::vector<BandNode>& 
 
 struct BandLayout {
   size_t ABw, wv, Ab, Zb, dl, el, taul, Dcur, z, Ds, zs, perm, kept, defl, rotp, rotcs, cnt, DK, zK, Dd, org, tau, zhat,
-      scol, iota, Qw, prod, leafws, total;
+      scol, iota, Qw, prod, leafws, r1, total;
   size_t leafws_bytes;
 };
 
@@ -1644,6 +1655,7 @@ BandLayout band_layout(int64_t n, int64_t b, const tdc_opts& op) {
   L.zhat = take(o, sizeof(double) * nn);
   L.scol = take(o, sizeof(double) * nn);
   L.iota = take(o, sizeof(int32_t) * nn);
+  L.r1 = take(o, rank_one_scratch_bytes((int64_t)nn));
   L.Qw = take(o, sizeof(double) * nn * nn);
   size_t pb = 0;
   tdc_cauchy_gemm_workspace_size((int64_t)nn, (int64_t)nn, TDC_MERGE_SPLIT, &op, &pb);
@@ -1773,7 +1785,12 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
       if (launch_bd_gather(nn, Qn, ldq, perm, kept, K, defl, ndf, Ds, zs, Qw, DK, zK, Dd, st, cs) != cudaSuccess)
         return TDC_ECUDA;
       if (K > 0) {
-        if (launch_rank_one(DK, zK, K, hrho, op.max_iter, org, tau, zhat, scol, st, cs) != cudaSuccess)
+        double* r1zz;
+        float2* r1xz;
+        float* r1xlo;
+        rank_one_carve(base + L.r1, K, r1zz, r1xz, r1xlo);
+        if (launch_rank_one(DK, zK, K, hrho, op.max_iter, org, tau, zhat, scol, r1zz, r1xz, r1xlo, st, cs) !=
+            cudaSuccess)
           return TDC_ECUDA;
         const int32_t mode = K >= 128 ? TDC_MERGE_SPLIT : TDC_MERGE_DENSE;
         char* pw = (char*)(((uintptr_t)prod + 255) & ~(uintptr_t)255);

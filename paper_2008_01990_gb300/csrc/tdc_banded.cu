@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(256) k_bd_rank(int64_t nn, const double* D, co
 // cnt = {K, nd, nrot}, *rho_out.  A non-finite pole or weight records TDC_ENONFINITE and
 // deflates every pole (no secular solve and no product run on it).
 constexpr int kBdDefThreads = 1024;
-constexpr int64_t kBdDefMaxN = (int64_t)96 * 1024 * 8;  // survivor bits in 96 KB of shared memory
+constexpr int64_t kBdDefMaxN = (int64_t)48 * 1024 * 8;  // two bit arrays in 96 KB of shared memory
 
 __device__ __forceinline__ double block_sum_bd(double v, double* red) {
   v = warp_sum(v);
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(kBdDefThreads) k_bd_deflate(int64_t nn, double
                                                              int32_t* defl, int32_t* rotp, double* rotcs,
                                                              int32_t* cnt, double* rho_out, BdScratch S,
                                                              int* status) {
-  extern __shared__ unsigned rotbit[];  // speculative outcome of survivor pair (q - 1, q)
+  extern __shared__ unsigned rotbit[];  // speculative outcome of survivor pair (q - 1, q), then dbit
   __shared__ double red[32];
   __shared__ int wcnt[32];
   const int tid = threadIdx.x;
@@ -389,6 +389,9 @@ __global__ void __launch_bounds__(kBdDefThreads) k_bd_deflate(int64_t nn, double
     M += total;
   }
   // type 2 on the original values, every consecutive survivor pair at once
+  const int64_t nwords = (M + 31) / 32;
+  unsigned* dbit = rotbit + (nn + 31) / 32;  // survivor q deflated by a rotation
+  for (int64_t w = tid; w < nwords; w += blockDim.x) dbit[w] = 0u;
   for (int64_t q0 = 0; q0 < M; q0 += blockDim.x) {
     const int64_t q = q0 + tid;
     bool rot = false;
@@ -410,24 +413,32 @@ __global__ void __launch_bounds__(kBdDefThreads) k_bd_deflate(int64_t nn, double
     if ((tid & 31) == 0 && q < M) rotbit[q >> 5] = bits;
   }
   __syncthreads();
+  // the chain, in one thread: a pair whose candidate was left unchanged takes its
+  // speculative outcome, so the scan jumps from one speculative rotation to the next and
+  // evaluates a pair itself only right after a rotation
   if (tid == 0) {
-    int32_t K = 0, nr = 0;
+    int32_t nr = 0;
     bool mod = false;  // the candidate's values were changed by the previous rotation
     double zc = 0.0, dc = 0.0;
-    for (int64_t q = 1; q < M; ++q) {
-      const int32_t pa = S.surv[q - 1], pb = S.surv[q];
+    int64_t q = 1;
+    while (q < M) {
       bool rot;
       double c = 0.0, s = 0.0, w = 0.0, dp = 0.0, dn = 0.0;
       if (!mod) {
-        rot = (rotbit[q >> 5] >> (q & 31)) & 1u;
-        if (rot) {
-          c = S.c[q];
-          s = S.s[q];
-          w = S.w[q];
-          dp = S.dp[q];
-          dn = S.dn[q];
-        }
+        int64_t wd = q >> 5;
+        unsigned bits = rotbit[wd] & (0xffffffffu << (q & 31));
+        while (bits == 0u && ++wd < nwords) bits = rotbit[wd];
+        if (bits == 0u) break;
+        q = wd * 32 + (__ffs(bits) - 1);
+        if (q >= M) break;
+        rot = true;
+        c = S.c[q];
+        s = S.s[q];
+        w = S.w[q];
+        dp = S.dp[q];
+        dn = S.dn[q];
       } else {
+        const int32_t pb = S.surv[q];
         const double zj = zs[pb], dj = Ds[pb];
         w = hypot(zj, zc);
         const double t = dj - dc;
@@ -440,6 +451,7 @@ __global__ void __launch_bounds__(kBdDefThreads) k_bd_deflate(int64_t nn, double
         }
       }
       if (rot) {
+        const int32_t pa = S.surv[q - 1], pb = S.surv[q];
         zs[pb] = w;
         zs[pa] = 0.0;
         Ds[pa] = dp;
@@ -450,20 +462,30 @@ __global__ void __launch_bounds__(kBdDefThreads) k_bd_deflate(int64_t nn, double
         rotcs[2 * nr + 1] = s;
         ++nr;
         S.slot[pb] = pa;
+        dbit[(q - 1) >> 5] |= 1u << ((q - 1) & 31);
         mod = true;
         zc = w;
         dc = dn;
       } else {
-        kept[K++] = pa;
         mod = false;
       }
+      ++q;
     }
-    if (M > 0) kept[K++] = S.surv[M - 1];
-    cnt[0] = K;
     cnt[2] = nr;
     *rho_out = rho;
   }
   __syncthreads();
+  // kept: the survivors no rotation deflated, in order
+  int64_t K = 0;
+  for (int64_t q0 = 0; q0 < M; q0 += blockDim.x) {
+    const int64_t q = q0 + tid;
+    const bool kp = q < M && !((dbit[q >> 5] >> (q & 31)) & 1u);
+    int total = 0;
+    const int pos = block_scan_bd(kp ? 1 : 0, wcnt, total);
+    if (kp) kept[K + pos] = S.surv[q];
+    K += total;
+  }
+  if (tid == 0) cnt[0] = (int32_t)K;
   // deflated entries in scan order
   int64_t nd = 0;
   for (int64_t i0 = 0; i0 < nn; i0 += blockDim.x) {
@@ -605,7 +627,7 @@ cudaError_t launch_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept,
                               double* rotcs, int32_t* cnt, double* rho, const BdScratch& S, int* status,
                               cudaStream_t s) {
   if (nn > kBdDefMaxN) return cudaErrorInvalidValue;
-  const size_t smem = sizeof(unsigned) * (size_t)((std::max<int64_t>(nn, 1) + 31) / 32);
+  const size_t smem = 2 * sizeof(unsigned) * (size_t)((std::max<int64_t>(nn, 1) + 31) / 32);
   static bool attr[64] = {false};  // once per device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);

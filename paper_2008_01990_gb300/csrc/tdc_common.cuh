@@ -461,8 +461,14 @@ cudaError_t launch_lowner(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_finalize(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_copy_deflated(const Plan& P, const LevelLaunch& L, int sign_normalise, cudaStream_t s);
 cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream_t s);
+// Rank-one eigenproblem: secular roots, Loewner zhat, column normalisers.  zz (K doubles),
+// xz (K float2) and xlo (K floats) are scratch for the FP32 pre-iteration of the roots
+// (NULL: the roots iterate in FP64 only).
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
-                            double* tau, double* zhat, double* s, int* status, cudaStream_t st);
+                            double* tau, double* zhat, double* s, double* zz, float2* xz, float* xlo, int* status,
+                            cudaStream_t st);
+// bytes of that scratch for K poles (three 256-byte aligned arrays)
+size_t rank_one_scratch_bytes(int64_t K);
 cudaError_t launch_gemm_dense(const Plan& P, const LevelLaunch& L, int64_t max_tiles, cudaStream_t s);
 cudaError_t launch_gemm_tiny(const Plan& P, const LevelLaunch& L, cudaStream_t s);
 cudaError_t launch_split_pack(const Plan& P, const LevelLaunch& L, int max_pass, cudaStream_t s);

@@ -1922,15 +1922,32 @@ __global__ void __launch_bounds__(256) k_colnorm(Plan P, int level, int64_t M, i
   });
 }
 
-// Stand-alone rank-one eigenproblem (tdc_rank_one): the three warp-per-entry stages.
-__global__ void __launch_bounds__(256) k_r1_secular(const double* D, const double* z, int K, double rho,
+// Stand-alone rank-one eigenproblem (tdc_rank_one, and each term of the band merge): the
+// three warp-per-entry stages, after the FP32 copies of the poles for the pre-iteration
+// (coordinates relative to the middle pole as sums of two floats, squared weights), as a
+// merge level prepares them.
+__global__ void __launch_bounds__(256) k_r1_prep(const double* D, const double* z, int K, double* zz, float2* xz,
+                                                  float* xlo) {
+  const double dc = D[K >> 1];
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < K; j += (int64_t)gridDim.x * blockDim.x) {
+    const double zj = z[j];
+    const double x = D[j] - dc;
+    const float xh = (float)x;
+    xz[j] = make_float2(xh, (float)(zj * zj));
+    zz[j] = zj * zj;
+    xlo[j] = (float)(x - (double)xh);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_r1_secular(const double* D, const double* z, const double* zz,
+                                                     const float2* xz, const float* xlo, int K, double rho,
                                                      int max_iter, int* org, double* tau, int* status) {
   const int64_t j = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   if (j >= K) return;
   int o, it;
   double t;
   bool conv;
-  secular_root(D, z, nullptr, nullptr, nullptr, K, (int)j, rho, max_iter, o, t, it, conv);
+  secular_root(D, z, zz, xz, xlo, K, (int)j, rho, max_iter, o, t, it, conv);
   if ((threadIdx.x & 31) == 0) {
     org[j] = o;
     tau[j] = t;
@@ -1954,11 +1971,21 @@ __global__ void __launch_bounds__(256) k_r1_colnorm(const double* D, const int* 
   if ((threadIdx.x & 31) == 0) s[j] = sj;
 }
 
+size_t rank_one_scratch_bytes(int64_t K) {
+  auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t k = (size_t)std::max<int64_t>(K, 1);
+  return al(sizeof(double) * k) + al(sizeof(float2) * k) + al(sizeof(float) * k);
+}
+
 cudaError_t launch_rank_one(const double* D, const double* z, int64_t K, double rho, int max_iter, int* org,
-                            double* tau, double* zhat, double* s, int* status, cudaStream_t st) {
+                            double* tau, double* zhat, double* s, double* zz, float2* xz, float* xlo, int* status,
+                            cudaStream_t st) {
   if (K == 0) return cudaSuccess;
   const unsigned blocks = (unsigned)((K * 32 + 255) / 256);
-  k_r1_secular<<<blocks, 256, 0, st>>>(D, z, (int)K, rho, max_iter, org, tau, status);
+  const bool pre = zz && xz && xlo;
+  if (pre) k_r1_prep<<<(unsigned)std::min<int64_t>((K + 255) / 256, 4096), 256, 0, st>>>(D, z, (int)K, zz, xz, xlo);
+  k_r1_secular<<<blocks, 256, 0, st>>>(D, z, pre ? zz : nullptr, pre ? xz : nullptr, pre ? xlo : nullptr, (int)K,
+                                       rho, max_iter, org, tau, status);
   k_r1_lowner<<<blocks, 256, 0, st>>>(D, z, org, tau, (int)K, rho, zhat);
   k_r1_colnorm<<<blocks, 256, 0, st>>>(D, org, tau, zhat, (int)K, s);
   return cudaGetLastError();
