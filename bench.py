@@ -677,6 +677,44 @@ def config_dense(args, n=4096, steps=3):
             "context_cusolver_syevd_ms": ms_eigh, "speedup_vs_cusolver_syevd": ms_eigh / ms}
 
 
+def config_band(args, n=4096, bws=(8, 32), steps=3):
+    """Symmetric band eigenproblems (the band divide and conquer of tdc_sbevd) on the
+    uniform band family (entries uniform(-1, 1) from SplitMix64(1), half-bandwidths b):
+    whole call timed with CUDA events after a warm-up; residual and orthogonality ratios on
+    every column; the dense solver (tdc_syevd) on the same matrix as context."""
+    import torch
+    from paper_2008_01990_gb300 import inputs, tdc
+    dev = torch.device("cuda", 0)
+    out = {"workload": "symmetric band uniform n=%d: tdc_sbevd (tearing, batched dense leaves, b rank-one "
+                       "merges per node)" % n, "bands": {}}
+    ms_dense = None
+    for b in bws:
+        AB = torch.tensor(inputs.band_sym("uniform", n, b, seed=1), device=dev)
+        tdc.sbevd(AB)
+        ms = _event_ms(lambda: tdc.sbevd(AB), steps)
+        st = tdc.sync_status()
+        lam, Q = tdc.sbevd(AB, check=True)
+        A = torch.zeros(n, n, dtype=torch.float64, device=dev)
+        for r in range(b + 1):
+            idx = torch.arange(n - r, device=dev)
+            A[idx + r, idx] = AB[r, : n - r]
+            A[idx, idx + r] = AB[r, : n - r]
+        nA = max(abs(lam[0].item()), abs(lam[-1].item()))
+        res = torch.abs(A @ Q - Q * lam[None, :]).sum(dim=0).max().item() / (n * nA * EPS)
+        orth = torch.abs(Q.t() @ Q - torch.eye(n, dtype=Q.dtype, device=dev)).sum(dim=0).max().item() / (n * EPS)
+        entry = {"b": b, "ms": ms, "steps": steps, "status": tdc.strerror(st),
+                 "checks": {"residual": res, "orthogonality": orth, "columns": "all",
+                            "within_bounds": bool(res <= 50 and orth <= 50)}}
+        if ms_dense is None and not getattr(args, "no_compare", False):
+            tdc.syevd(A)
+            ms_dense = _event_ms(lambda: tdc.syevd(A), 2)
+        if ms_dense is not None:
+            entry["context_tdc_syevd_ms"] = ms_dense
+        out["bands"]["b%d" % b] = entry
+        del A, Q, lam, AB
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -950,7 +988,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         cfg = {}
         for key, fn in (("c1_uniform1024", config_c1), ("c3_batched4096", config_c3), ("c4_split32768", config_c4),
-                        ("c5_backward256x512", config_c5), ("dense_syevd4096", config_dense)):
+                        ("c5_backward256x512", config_c5), ("dense_syevd4096", config_dense),
+                        ("band_sbevd4096", config_band)):
             cfg[key] = fn(args)
             progress(key + " done")
         line["configs"] = cfg
@@ -981,7 +1020,7 @@ def main():
     ap.add_argument("--workload", default="toeplitz16384", choices=["toeplitz16384", "toeplitz4096", "uniform1024", "c4_32768", "qhat8192",
                                                           "example1_8192", "example1_16384", "example1_32768",
                                                           "batched4096", "backward256", "dense4096", "dense8192", "structured16384",
-                                                          "clement30000",
+                                                          "clement30000", "band4096",
                                                           "hermite30000", "sht30000"])
     ap.add_argument("--merge", default="auto", choices=["dense", "auto", "structured", "split", "structured_split"])
     ap.add_argument("--no-compare", action="store_true")
@@ -991,6 +1030,7 @@ def main():
     ap.add_argument("--split-chunk-k", type=int, default=-1,
                     help="drain the split product's level sums every this many terms (multiple of 16; 0: once "
                          "per tile; default: the library's)")
+    ap.add_argument("--bands", default="8,32", help="band4096 workload: half-bandwidths, comma-separated")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-configs", action="store_true", help="default workload only: skip the other workloads")
     ap.add_argument("--cpu-budget", type=float, default=180.0,
@@ -1011,6 +1051,10 @@ def main():
         return 0
     if args.workload == "structured16384":
         print(json.dumps(run_structured_products(args, 16384)), flush=True)
+        return 0
+    if args.workload == "band4096":
+        bws = tuple(int(x) for x in args.bands.split(","))
+        print(json.dumps(config_band(args, bws=bws, steps=args.steps)), flush=True)
         return 0
     if args.workload.startswith("dense"):
         print(json.dumps(config_dense(args, n=int(args.workload[5:]), steps=args.steps)), flush=True)

@@ -214,9 +214,10 @@ __device__ __forceinline__ bool bd_before(double a, int64_t ia, double b, int64_
   return a < b || (a == b && ia < ib);
 }
 
-// Stable sort by rank in two kernels.  k_bd_chunk_sort: one block per chunk of kBdChunk
-// entries sorts (D[i], i) by bd_before with a bitonic network in shared memory (entries
-// past nn pad the chunk and sort last), writing the chunk's sorted keys and indices.
+// Stable sort by rank in two kernels.  k_bd_chunk_sort: one block per chunk of ch entries
+// (ch = kBdChunk, or the power of two at or above nn when that is smaller) sorts (D[i], i)
+// by bd_before with a bitonic network in shared memory (entries past nn pad the chunk and
+// sort last), writing the chunk's sorted keys and indices.
 // k_bd_rank: entry i at sorted place p of its chunk has rank p + the count of entries before
 // it in every other chunk (a binary search each); Ds[rank] = D[i], zs likewise (z may be
 // NULL), perm[rank] = i.  The ranks are those of the total order, a permutation.
@@ -227,19 +228,19 @@ __device__ __forceinline__ bool bd_before_pad(double a, int64_t ia, double b, in
   return bd_before(a, ia, b, ib);
 }
 
-__global__ void __launch_bounds__(1024) k_bd_chunk_sort(int64_t nn, const double* D, double* sk, int32_t* si) {
+__global__ void __launch_bounds__(1024) k_bd_chunk_sort(int64_t nn, int ch, const double* D, double* sk, int32_t* si) {
   __shared__ double key[kBdChunk];
   __shared__ int32_t idx[kBdChunk];
-  const int64_t c0 = (int64_t)blockIdx.x * kBdChunk;
-  for (int t = threadIdx.x; t < kBdChunk; t += blockDim.x) {
+  const int64_t c0 = (int64_t)blockIdx.x * ch;
+  for (int t = threadIdx.x; t < ch; t += blockDim.x) {
     const int64_t i = c0 + t;
     key[t] = i < nn ? D[i] : 0.0;
     idx[t] = (int32_t)(i < nn ? i : nn + t);
   }
   __syncthreads();
-  for (int k = 2; k <= kBdChunk; k <<= 1) {
+  for (int k = 2; k <= ch; k <<= 1) {
     for (int j = k >> 1; j > 0; j >>= 1) {
-      for (int t = threadIdx.x; t < kBdChunk / 2; t += blockDim.x) {
+      for (int t = threadIdx.x; t < ch / 2; t += blockDim.x) {
         const int lo = 2 * j * (t / j) + (t % j), hi = lo + j;
         const bool up = (lo & k) == 0;
         const bool swap = up ? bd_before_pad(key[hi], idx[hi], key[lo], idx[lo], nn)
@@ -256,23 +257,24 @@ __global__ void __launch_bounds__(1024) k_bd_chunk_sort(int64_t nn, const double
       __syncthreads();
     }
   }
-  for (int t = threadIdx.x; t < kBdChunk && c0 + t < nn; t += blockDim.x) {
+  for (int t = threadIdx.x; t < ch && c0 + t < nn; t += blockDim.x) {
     sk[c0 + t] = key[t];
     si[c0 + t] = idx[t];
   }
 }
 
-__global__ void __launch_bounds__(256) k_bd_rank(int64_t nn, const double* D, const double* z, const double* sk,
-                                                const int32_t* si, double* Ds, double* zs, int32_t* perm) {
-  const int64_t nch = (nn + kBdChunk - 1) / kBdChunk;
+__global__ void __launch_bounds__(256) k_bd_rank(int64_t nn, int ch, const double* D, const double* z,
+                                                const double* sk, const int32_t* si, double* Ds, double* zs,
+                                                int32_t* perm) {
+  const int64_t nch = (nn + ch - 1) / ch;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nn; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c = q / kBdChunk;  // q: sorted place within chunk c
+    const int64_t c = q / ch;  // q: sorted place within chunk c
     const int32_t i = si[q];
     const double v = sk[q];
-    int64_t rk = q - c * kBdChunk;
+    int64_t rk = q - c * ch;
     for (int64_t c2 = 0; c2 < nch; ++c2) {
       if (c2 == c) continue;
-      const int64_t b0 = c2 * kBdChunk, len = nn - b0 < kBdChunk ? nn - b0 : kBdChunk;
+      const int64_t b0 = c2 * ch, len = nn - b0 < ch ? nn - b0 : ch;
       int64_t lo = 0, hi = len;  // entries of chunk c2 before (v, i)
       while (lo < hi) {
         const int64_t m = (lo + hi) >> 1;
@@ -619,8 +621,11 @@ cudaError_t launch_bd_z(int64_t nn, const double* Q, int64_t ldq, int64_t ra, in
 cudaError_t launch_bd_sort(int64_t nn, const double* D, const double* z, double* Ds, double* zs, int32_t* perm,
                            const BdScratch& S, cudaStream_t s) {
   if (nn <= 0) return cudaSuccess;
-  k_bd_chunk_sort<<<(unsigned)((nn + kBdChunk - 1) / kBdChunk), 1024, 0, s>>>(nn, D, S.sk, S.si);
-  k_bd_rank<<<grid_for(nn), 256, 0, s>>>(nn, D, z, S.sk, S.si, Ds, zs, perm);
+  int ch = 2;
+  while (ch < kBdChunk && ch < nn) ch <<= 1;
+  k_bd_chunk_sort<<<(unsigned)((nn + ch - 1) / ch), std::max(32, std::min(1024, ch / 2)), 0, s>>>(nn, ch, D, S.sk,
+                                                                                                 S.si);
+  k_bd_rank<<<grid_for(nn), 256, 0, s>>>(nn, ch, D, z, S.sk, S.si, Ds, zs, perm);
   return cudaGetLastError();
 }
 cudaError_t launch_bd_deflate(int64_t nn, double* Ds, double* zs, int32_t* kept, int32_t* defl, int32_t* rotp,
