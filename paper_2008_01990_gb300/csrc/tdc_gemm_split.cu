@@ -305,6 +305,20 @@ __global__ void __launch_bounds__(1024) k_split_pack(Plan P, int level, int64_t 
 // ---------------------------------------------------------------------------
 // Digit images
 // ---------------------------------------------------------------------------
+// A level sum I (an integer count of 2^-58 units) times 2^adj as a double: the scale enters
+// the exponent field of double(I) by an integer addition, no FP64 multiply, while the
+// result stays a normal number (else two power-of-two factors).
+__device__ __forceinline__ int col_adj(const GemmSeg& sg, int j) {
+  return j < sg.K ? (sg.cexp ? sg.cexp[j] : 0) + (sg.oexp ? sg.oexp[j] : 0) : 0;
+}
+__device__ __forceinline__ double level_value(long long I, int adj) {
+  if (I == 0) return 0.0;
+  const long long b = __double_as_longlong(__ll2double_rn(I));
+  const int f = (int)((b >> 52) & 0x7ff) + adj - 58;
+  if (f >= 1 && f <= 2046) return __longlong_as_double(b + ((long long)(adj - 58) << 52));
+  return scale2(__longlong_as_double(b - (58ll << 52)), adj);
+}
+
 __global__ void __launch_bounds__(256) k_split_a(const GemmSeg* segs, int nseg, const int64_t* dnseg, int S,
                                                  __nv_bfloat16* img, int* status) {
   if (dnseg) nseg = (int)*dnseg;
@@ -725,16 +739,15 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
         bool fits = true;
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
+        // the column's scale (2^cexp_j 2^oexp_j) goes into the exponent field of the value
         if (__all_sync(0xffffffffu, fits)) {
 #pragma unroll
-          for (int i = 0; i < kEpiCols; ++i) {
-            const long long I = hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]);
-            const long long b = __double_as_longlong(__ll2double_rn(I)) - (58ll << 52);
-            val[i] = I == 0 ? 0.0 : __longlong_as_double(b);
-          }
+          for (int i = 0; i < kEpiCols; ++i)
+            val[i] = level_value(hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]), col_adj(*t.sg, t.ct * BN + c0 + i));
         } else {
 #pragma unroll
-          for (int i = 0; i < kEpiCols; ++i) val[i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+          for (int i = 0; i < kEpiCols; ++i)
+            val[i] = scale2(fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48), col_adj(*t.sg, t.ct * BN + c0 + i));
         }
         const GemmSeg& sg = *t.sg;
         const int row = t.rt * BM + quarter * 32 + lane;
@@ -744,10 +757,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
             const int j = t.ct * BN + c0 + i;
             if (j < sg.K) {
               const int pos = sg.cpos ? sg.cpos[j] : j;
-              double v = sg.cexp ? scale2(val[i], sg.cexp[j]) : val[i];
-              if (sg.oexp) v = scale2(v, sg.oexp[j]);
               double* cp = sg.C + row + (int64_t)pos * sg.ldc;
-              if (sg.acc) *cp += v; else *cp = v;
+              if (sg.acc) *cp += val[i]; else *cp = val[i];
             }
           }
         }
@@ -775,16 +786,15 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
         bool fits = true;
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) fits = fits && hi[i] < (1ll << 52) && hi[i] > -(1ll << 52);
+        // the column's scale (2^cexp_j 2^oexp_j) goes into the exponent field of the value
         if (__all_sync(0xffffffffu, fits)) {
 #pragma unroll
-          for (int i = 0; i < kEpiCols; ++i) {
-            const long long I = hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]);
-            const long long b = __double_as_longlong(__ll2double_rn(I)) - (58ll << 52);
-            val[i] = I == 0 ? 0.0 : __longlong_as_double(b);
-          }
+          for (int i = 0; i < kEpiCols; ++i)
+            val[i] = level_value(hi[i] * 1024 + (long long)__float2int_rn(4.0f * lo[i]), col_adj(*t.sg, t.ct * BN + c0 + i));
         } else {
 #pragma unroll
-          for (int i = 0; i < kEpiCols; ++i) val[i] = fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48);
+          for (int i = 0; i < kEpiCols; ++i)
+            val[i] = scale2(fma((double)lo[i], 0x1p-56, __ll2double_rn(hi[i]) * 0x1p-48), col_adj(*t.sg, t.ct * BN + c0 + i));
         }
       }
       umma::tc_fence_before();
@@ -798,10 +808,8 @@ __global__ void __launch_bounds__(kSplitThreads, 1) k_gemm_split(const GemmSeg* 
           const int j = t.ct * BN + c0 + i;
           if (j < sg.K) {
             const int pos = sg.cpos ? sg.cpos[j] : j;
-            double v = sg.cexp ? scale2(val[i], sg.cexp[j]) : val[i];
-            if (sg.oexp) v = scale2(v, sg.oexp[j]);
             double* cp = sg.C + row + (int64_t)pos * sg.ldc;
-            if (sg.acc) *cp += v; else *cp = v;
+            if (sg.acc) *cp += val[i]; else *cp = val[i];
           }
         }
       }
