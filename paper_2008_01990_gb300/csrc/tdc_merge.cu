@@ -826,6 +826,10 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
 cudaError_t launch_prepare(const Plan& P, const LevelLaunch& L, cudaStream_t s) {
   int threads = 256;
   while (threads > 64 && threads / 2 >= L.max_n) threads /= 2;
+  // a level of fewer merges than SMs: a wider block per merge (down to 16 poles a thread)
+  // shortens the level's critical path; the outputs do not depend on the block size
+  if (L.merges < 152)
+    while (threads < 1024 && (int64_t)threads * 16 <= L.max_n) threads *= 2;
   k_prepare<<<(unsigned)L.merges, threads, 0, s>>>(P, L.level);
   return cudaGetLastError();
 }
