@@ -644,11 +644,11 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
     if (type2_test(V.Dc[v0 + b], V.zc[v0 + b], sdi[q - 1], stau[q - 1], tol)) flag[q] |= 2;
   }
   __syncthreads();
-  // 3c. sequential resolution, pipelined over chunks of kCh poles in three
-  //     shared-memory buffers: while thread 0 decides chunk ch (rotate or keep,
-  //     FP64 work only after a rotation that the speculation did not cover), the
-  //     other warps write the records of chunk ch-1 (whose output positions thread
-  //     0 has already assigned) and stage the inputs of chunk ch+1.
+  // 3c. resolution of the scan, pipelined over chunks of kCh poles in three
+  //     shared-memory buffers: while warp 0 decides chunk ch (rotate or keep, FP64
+  //     work only after a rotation that the speculation did not cover) and assigns
+  //     its records, the other warps write the records of chunk ch-1 and stage the
+  //     inputs of chunk ch+1.
   constexpr int kCh = 128;
   __shared__ int sc_c[3][kCh];
   __shared__ uint8_t sc_f[3][kCh], o_code[3][kCh];
@@ -707,61 +707,127 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   const int nch_chunks = (nL + kCh - 1) / kCh;
   stage(0, 0, threadIdx.x, blockDim.x);
   __syncthreads();
+  // warp 0 decides, 32 poles at a time.  Lane 0 runs the scan's state machine over the
+  // sub-chunk's speculative bits: N (the candidate is an original pole: the pair's
+  // test is bit 0), S (the candidate came from a bit-0 rotation: bit 1), X (it came from
+  // any other rotation: the test and the rotation in FP64, the only sequential FP64
+  // work); it jumps over runs of N without a bit-0 rotation.  Each lane then derives its
+  // pole's record from the decision word: indices from popcounts, the candidate (the
+  // previous pole, its values those left by a rotation at it), the candidate's support
+  // as the OR of the supports along the run of rotations that built it.
   int K = 0, nr = 0, nch = 0;
-  int pj = -1, ps = 0;
-  double pD = 0.0, pz = 0.0;
-  bool prev_rot = false, prev_simple = false;
+  int st = 0, cpj = -1, cps = 0;  // scan state and the candidate after the last decided pole
+  double cpD = 0.0, cpz = 0.0;
+  bool cprot = false;             // the last decided pole rotated
   for (int ch = 0; ch < nch_chunks; ++ch) {
     const int b = ch % 3;
     if (threadIdx.x >= 32) {
       if (ch > 0) emit((ch + 2) % 3, (ch - 1) * kCh, threadIdx.x - 32, blockDim.x - 32);
       stage((ch + 1) % 3, (ch + 1) * kCh, threadIdx.x - 32, blockDim.x - 32);
     }
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
       const int qend = min(kCh, nL - ch * kCh);
-      for (int i = 0; i < qend; ++i) {
-        const int q = ch * kCh + i;
-        const int c = sc_c[b][i];
-        const int sp = (c < n1) ? 1 : 2;
-        const double Dq = sc_D[b][i], zq = sc_z[b][i];
-        if (q == 0) {
-          pj = c; pD = Dq; pz = zq; ps = sp; prev_rot = false;
-          continue;
-        }
-        bool rot;
-        double cc = 0.0, ss = 0.0, tau = 0.0, dp = 0.0, di = 0.0;
-        const uint8_t f = sc_f[b][i];
-        if (!prev_rot) {
-          rot = (f & 1) != 0;
-          if (rot) { tau = sc_tau[b][i]; di = sc_di[b][i]; }
-          prev_simple = rot;
-        } else {  // the survivor was rotated: test against its current values
-          rot = prev_simple ? (f & 2) != 0 : type2_test(Dq, zq, pD, pz, tol);
-          if (rot) {
-            type2_rot(Dq, zq, pD, pz, cc, ss, tau, dp, di);
-            sc_cs[b][i] = cc;
-            sc_sn[b][i] = ss;
-            sc_dp[b][i] = dp;
+      for (int s0 = 0; s0 < qend; s0 += 32) {
+        const int i = s0 + lane, q = ch * kCh + i;
+        const bool valid = i < qend;
+        const uint8_t f = valid ? sc_f[b][i] : 0;
+        const int cq = valid ? sc_c[b][i] : 0;
+        const int spq = cq < n1 ? 1 : 2;
+        const unsigned vm = __ballot_sync(0xffffffffu, valid);
+        const unsigned b0 = __ballot_sync(0xffffffffu, valid && q > 0 && (f & 1));
+        const unsigned b1 = __ballot_sync(0xffffffffu, valid && q > 0 && (f & 2));
+        const unsigned topm = __ballot_sync(0xffffffffu, valid && spq == 1);
+        const unsigned botm = __ballot_sync(0xffffffffu, valid && spq == 2);
+        const int kn = min(32, qend - s0);
+        unsigned rotw = 0;
+        int sn = st;
+        if (lane == 0) {
+          int k = 0;
+          while (k < kn) {
+            if (ch * kCh + s0 + k == 0) {
+              sn = 0;
+              ++k;
+              continue;
+            }
+            if (sn == 0) {
+              const unsigned m = b0 >> k;
+              if (m == 0u) break;
+              k += __ffs(m) - 1;
+              rotw |= 1u << k;
+              sn = 1;
+              ++k;
+              continue;
+            }
+            const int ii = s0 + k;
+            const double Dq = sc_D[b][ii], zq = sc_z[b][ii];
+            const double pDv = k > 0 ? sc_di[b][ii - 1] : cpD, pzv = k > 0 ? sc_tau[b][ii - 1] : cpz;
+            const bool r = sn == 1 ? ((b1 >> k) & 1u) != 0u : type2_test(Dq, zq, pDv, pzv, tol);
+            if (r) {
+              double cc, ss, tau, dp, di;
+              type2_rot(Dq, zq, pDv, pzv, cc, ss, tau, dp, di);
+              sc_cs[b][ii] = cc;
+              sc_sn[b][ii] = ss;
+              sc_dp[b][ii] = dp;
+              sc_tau[b][ii] = tau;
+              sc_di[b][ii] = di;
+              rotw |= 1u << k;
+              sn = 2;
+            } else {
+              sn = 0;
+            }
+            ++k;
           }
-          prev_simple = false;
         }
-        o_pj[b][i] = pj;
-        if (rot) {  // type 2: rotate (pj, c) so that z_pj = 0; pj is deflated
-          o_code[b][i] = prev_rot ? 1 : 3;
-          o_idx[b][i] = nr++;
-          if (!prev_rot) o_cidx[b][i] = nch++;
-          o_sup[b][i] = ps | (sp << 8);
-          pj = c; pD = di; pz = tau; ps |= sp;
-          prev_rot = true;
-        } else {
-          o_code[b][i] = 0;
-          o_idx[b][i] = K++;
-          o_sup[b][i] = ps;
-          sc_cs[b][i] = pD;
-          sc_sn[b][i] = pz;
-          pj = c; pD = Dq; pz = zq; ps = sp;
-          prev_rot = false;
+        rotw = __shfl_sync(0xffffffffu, rotw, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
+        __syncwarp();
+        const unsigned prevw = (rotw << 1) | (cprot ? 1u : 0u);
+        const unsigned starts = rotw & ~prevw;
+        const unsigned keepw = ~rotw & vm & ((ch == 0 && s0 == 0) ? ~1u : ~0u);
+        // OR of the supports over the run of rotations ending at sub-chunk index m
+        auto run_sup = [&](int m) -> int {
+          const unsigned upto = m >= 31 ? 0xffffffffu : ((2u << m) - 1u);
+          const unsigned zeros = ~rotw & upto & vm;
+          unsigned range = upto;
+          int extra = cps;
+          if (zeros) {
+            range = upto & ~((1u << (31 - __clz(zeros))) - 1u);
+            extra = 0;
+          }
+          return extra | ((topm & range) ? 1 : 0) | ((botm & range) ? 2 : 0);
+        };
+        if (valid && q > 0) {
+          const unsigned lt = (1u << lane) - 1u;
+          const bool rot = ((rotw >> lane) & 1u) != 0u, prot = ((prevw >> lane) & 1u) != 0u;
+          const int ps = lane > 0 ? run_sup(lane - 1) : cps;
+          o_pj[b][i] = lane > 0 ? sc_c[b][i - 1] : cpj;
+          if (rot) {
+            o_code[b][i] = prot ? 1 : 3;
+            o_idx[b][i] = nr + __popc(rotw & lt);
+            if (!prot) o_cidx[b][i] = nch + __popc(starts & lt);
+            o_sup[b][i] = ps | (spq << 8);
+          } else {
+            o_code[b][i] = 0;
+            o_idx[b][i] = K + __popc(keepw & lt);
+            o_sup[b][i] = ps;
+            sc_cs[b][i] = lane == 0 ? cpD : (prot ? sc_di[b][i - 1] : sc_D[b][i - 1]);
+            sc_sn[b][i] = lane == 0 ? cpz : (prot ? sc_tau[b][i - 1] : sc_z[b][i - 1]);
+          }
         }
+        const int last = kn - 1;
+        const bool lr = ((rotw >> last) & 1u) != 0u;
+        const int nps = run_sup(last);
+        cpj = __shfl_sync(0xffffffffu, cq, last);
+        cpD = lr ? sc_di[b][s0 + last] : sc_D[b][s0 + last];
+        cpz = lr ? sc_tau[b][s0 + last] : sc_z[b][s0 + last];
+        cps = nps;
+        cprot = lr;
+        st = sn;
+        K += __popc(keepw);
+        nr += __popc(rotw);
+        nch += __popc(starts);
+        __syncwarp();
       }
     }
     __syncthreads();
@@ -769,8 +835,8 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   if (nch_chunks > 0) emit((nch_chunks - 1) % 3, (nch_chunks - 1) * kCh, threadIdx.x, blockDim.x);
   const int ndf = t1 + nr;
   if (threadIdx.x == 0) {
-    if (pj >= 0) {
-      V.kept[v0 + K] = pj; V.Dk[v0 + K] = pD; V.zk[v0 + K] = pz; V.kseg[v0 + K] = (uint8_t)ps; ++K;
+    if (cpj >= 0) {
+      V.kept[v0 + K] = cpj; V.Dk[v0 + K] = cpD; V.zk[v0 + K] = cpz; V.kseg[v0 + K] = (uint8_t)cps; ++K;
     }
     sres[0] = K; sres[1] = ndf; sres[2] = nr; sres[3] = nch;
     P.m.K[g] = K; P.m.nd[g] = ndf; P.m.nrot[g] = nr; P.m.nchain[g] = nch;
