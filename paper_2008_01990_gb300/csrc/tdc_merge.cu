@@ -707,8 +707,8 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
   const int nch_chunks = (nL + kCh - 1) / kCh;
   stage(0, 0, threadIdx.x, blockDim.x);
   __syncthreads();
-  // warp 0 decides, 32 poles at a time.  Lane 0 runs the scan's state machine over the
-  // sub-chunk's speculative bits: N (the candidate is an original pole: the pair's
+  // warp 0 decides, 32 poles at a time.  Its lanes run, in step, the scan's state
+  // machine over the sub-chunk's speculative bits: N (the candidate is an original pole: the pair's
   // test is bit 0), S (the candidate came from a bit-0 rotation: bit 1), X (it came from
   // any other rotation: the test and the rotation in FP64, the only sequential FP64
   // work); it jumps over runs of N without a bit-0 rotation.  Each lane then derives its
@@ -742,7 +742,14 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
         const int kn = min(32, qend - s0);
         unsigned rotw = 0;
         int sn = st;
-        if (lane == 0) {
+        // no bit-0 rotation right after a rotation and no S pole with bit 1: the
+        // decisions are the bit-0 word itself (isolated pairs of equal poles)
+        const unsigned kmask = kn >= 32 ? 0xffffffffu : ((1u << kn) - 1u);
+        const unsigned sS = (b0 << 1) | (st == 1 ? 1u : 0u);
+        if (st != 2 && (b0 & sS) == 0u && (b1 & sS & kmask) == 0u) {
+          rotw = b0;
+          sn = ((b0 >> (kn - 1)) & 1u) ? 1 : 0;
+        } else {  // every lane runs it on the same warp-uniform words: uniform branches
           int k = 0;
           while (k < kn) {
             if (ch * kCh + s0 + k == 0) {
@@ -759,18 +766,29 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
               ++k;
               continue;
             }
+            if (sn == 1 && ((b1 >> k) & 1u) == 0u) {  // the rotated survivor is kept: bits only
+              sn = 0;
+              ++k;
+              continue;
+            }
+            // a rotation after a rotation: bit 1 (S) says so, X tests in FP64
             const int ii = s0 + k;
             const double Dq = sc_D[b][ii], zq = sc_z[b][ii];
             const double pDv = k > 0 ? sc_di[b][ii - 1] : cpD, pzv = k > 0 ? sc_tau[b][ii - 1] : cpz;
-            const bool r = sn == 1 ? ((b1 >> k) & 1u) != 0u : type2_test(Dq, zq, pDv, pzv, tol);
+            bool r = true;
+            if (sn == 2) r = type2_test(Dq, zq, pDv, pzv, tol);
             if (r) {
               double cc, ss, tau, dp, di;
               type2_rot(Dq, zq, pDv, pzv, cc, ss, tau, dp, di);
-              sc_cs[b][ii] = cc;
-              sc_sn[b][ii] = ss;
-              sc_dp[b][ii] = dp;
-              sc_tau[b][ii] = tau;
-              sc_di[b][ii] = di;
+              __syncwarp();  // every lane has read the candidate before lane 0 writes
+              if (lane == 0) {
+                sc_cs[b][ii] = cc;
+                sc_sn[b][ii] = ss;
+                sc_dp[b][ii] = dp;
+                sc_tau[b][ii] = tau;
+                sc_di[b][ii] = di;
+              }
+              __syncwarp();
               rotw |= 1u << k;
               sn = 2;
             } else {
@@ -779,8 +797,6 @@ __global__ void __launch_bounds__(1024) k_prepare(Plan P, int level) {
             ++k;
           }
         }
-        rotw = __shfl_sync(0xffffffffu, rotw, 0);
-        sn = __shfl_sync(0xffffffffu, sn, 0);
         __syncwarp();
         const unsigned prevw = (rotw << 1) | (cprot ? 1u : 0u);
         const unsigned starts = rotw & ~prevw;
