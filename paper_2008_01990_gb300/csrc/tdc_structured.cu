@@ -110,19 +110,29 @@ __global__ void __launch_bounds__(256) k_srrsc(const GemmSeg* segs, StructArgs S
   }
   if (tid == 0) { s_r = 0; s_stop = 0; s_amax0 = 0.0; }
   __syncthreads();
-  const int total = mr * mc;
   bool fallback = false;
   for (;;) {
     // FP32 complete-pivoting search over the active Schur complement
+    // a thread per column, the rows in order (the entry with the smallest index wins ties)
     float best = -1.0f;
     int bidx = 0x7fffffff;
-    for (int idx = tid; idx < total; idx += blockDim.x) {
-      const int i = idx / mc, c = idx - i * mc;
-      if (!ract[i] || !cact[c]) continue;
-      float val;
-      if (kF32) val = fabsf(uf[i] * vf[c]) / fabsf(df[i] - wf[c]);
-      else val = (float)(fabs(u[i] * v[c]) / fabs((dr[i] - wo[c]) - wt[c]));
-      if (val > best) { best = val; bidx = idx; }
+    for (int c = tid; c < mc; c += blockDim.x) {
+      if (!cact[c]) continue;
+      if (kF32) {
+        const float vc = vf[c], wc = wf[c];
+        for (int i = 0; i < mr; ++i) {
+          if (!ract[i]) continue;
+          const float val = fabsf(uf[i] * vc) / fabsf(df[i] - wc);
+          if (val > best || (val == best && i * mc + c < bidx)) { best = val; bidx = i * mc + c; }
+        }
+      } else {
+        const double vc = v[c], woc = wo[c], wtc = wt[c];
+        for (int i = 0; i < mr; ++i) {
+          if (!ract[i]) continue;
+          const float val = (float)(fabs(u[i] * vc) / fabs((dr[i] - woc) - wtc));
+          if (val > best || (val == best && i * mc + c < bidx)) { best = val; bidx = i * mc + c; }
+        }
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
