@@ -456,14 +456,14 @@ static int validate_opts(const tdc_opts* o) {
 // Events ordering the two streams level by level: a pool per host thread and device,
 // created on first use and reused by every later call (a re-recorded event stands for
 // its latest record, and a call's waits are enqueued after its own records).
-static cudaError_t level_events(int T, cudaEvent_t** evE, cudaEvent_t** evG) {
+static cudaError_t level_events(int T, cudaEvent_t** evE, cudaEvent_t** evG, cudaEvent_t** evR) {
   static thread_local std::vector<cudaEvent_t> pool[16];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= 16) return cudaErrorInvalidDevice;
   std::vector<cudaEvent_t>& v = pool[dev];
-  while ((int)v.size() < 2 * T) {
+  while ((int)v.size() < 3 * T) {
     cudaEvent_t ev = nullptr;
     e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     if (e != cudaSuccess) return e;
@@ -471,6 +471,7 @@ static cudaError_t level_events(int T, cudaEvent_t** evE, cudaEvent_t** evG) {
   }
   *evE = v.data();
   *evG = v.data() + T;
+  *evR = v.data() + 2 * T;
   return cudaSuccess;
 }
 
@@ -574,12 +575,15 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   // level l-1 need only level l's boundary rows, so they run on s while level l's
   // products run on sg.  Level l's products wait for its roots (evE); level l-2's
   // roots reuse level l's vector set and wait for its products (evG); the output
-  // waits for the top level's products.
+  // waits for the top level's products.  The rotations of the children's columns need
+  // only the deflation's lists, so they wait for the deflation alone (evR) and run while
+  // the level's secular equation is solved.
   cudaStream_t sg = gemm_stream();
   if (sg == nullptr) err = cudaErrorUnknown;
   cudaEvent_t* evE = nullptr;
   cudaEvent_t* evG = nullptr;
-  if (err == cudaSuccess) err = level_events(H.T, &evE, &evG);
+  cudaEvent_t* evR = nullptr;
+  if (err == cudaSuccess) err = level_events(H.T, &evE, &evG, &evR);
   for (int l = H.T - 1; l >= 0 && err == cudaSuccess; --l) {
     const LevelLaunch& LL = H.levels[l];
     Plan P = PP[l & 1];
@@ -589,6 +593,7 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     const size_t a0 = mark();
     if (err == cudaSuccess) err = launch_prepare(P, LL, s);
     if (err == cudaSuccess) err = launch_boundary_rot(P, LL, s);
+    if (err == cudaSuccess) err = cudaEventRecord(evR[l], s);
     const size_t a1 = mark();
     if (err == cudaSuccess) err = launch_secular(P, LL, s);
     const size_t a2 = mark();
@@ -600,11 +605,12 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
     span(2, a1, a2);
     span(3, a2, a3);
     if (err == cudaSuccess) err = cudaEventRecord(evE[l], s);
-    if (err == cudaSuccess) err = cudaStreamWaitEvent(sg, evE[l], 0);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sg, evR[l], 0);
     const size_t g0 = mark_on(sg);
     if (err == cudaSuccess) err = launch_rotate(P, LL, sg);
     size_t g1 = mark_on(sg);
     span(1, g0, g1);
+    if (err == cudaSuccess) err = cudaStreamWaitEvent(sg, evE[l], 0);
     if (err == cudaSuccess) err = launch_gemm_dense(P, LL, H.max_tiles[l], sg);
     if (err == cudaSuccess) err = launch_gemm_tiny(P, LL, sg);
     if (err == cudaSuccess && ss) {
