@@ -168,8 +168,10 @@ int tdc_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
  * -4/-5 NULL lam/Q; -6 ldq < max(1,n); TDC_ENOWS; -9 invalid options; TDC_ECUDA.
  * A non-finite entry of d or e is read as zero (in every problem of a batch alike) and
  * the stream's status records TDC_ENONFINITE: lam and Q are then the finite
- * eigendecomposition of the input with those entries zeroed.  No scaling is applied:
- * entries are expected well inside the FP64 range (|d|, |e| below about 2^400). */
+ * eigendecomposition of the input with those entries zeroed.  A problem whose largest
+ * finite |d|, |e| lies outside [2^-400, 2^400] is solved scaled by the power of two that
+ * puts it in [1, 2) (exact), its eigenvalues scaled back (they overflow only where the
+ * exact ones exceed the FP64 range); other problems are solved as given. */
 int tdc_eig(int64_t n, const double* d, const double* e, double* lam, double* Q, int64_t ldq, void* ws,
             size_t ws_bytes, const tdc_opts* o, tdc_stream_t stream);
 

@@ -552,9 +552,9 @@ static int run_plan(HostPlan& H, const tdc_opts& o, const double* d, const doubl
   auto span = [&](int phase, size_t a0, size_t a1) {
     if (timing) spans.push_back({phase, {a0, a1}});
   };
-  // kernel launches: problem upload, corner modification, leaves, 9 per level (14
+  // kernel launches: problem upload, input scale, corner modification, leaves, 9 per level (14
   // on levels that also run the thread-per-root variants), output
-  int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 3 + 9 * (int64_t)H.T;
+  int64_t launches = (int64_t)((H.prob.size() + kProbChunk - 1) / kProbChunk) + 4 + 9 * (int64_t)H.T;
   for (int l = 0; l < H.T; ++l) {
     if (l > 0) launches += 2;  // boundary rows: rotation and gather, output order
     if (H.levels[l].nslots >= kSmallMinSlots) launches += 5;

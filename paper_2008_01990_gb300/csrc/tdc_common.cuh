@@ -26,7 +26,7 @@ struct Problem {
   int64_t qoff1;   // offset in the internal Q buffer (prefix of n^2)
   int64_t leaf0;   // first global leaf index of the problem
   int32_t depth;   // tree depth t
-  int32_t pad;
+  int32_t escale;  // input scale: d, e enter as x 2^-escale, eigenvalues leave times 2^escale (0: none)
 };
 
 struct Vecs {  // per-slot vectors of length N (sum of n); a merge owns [voff+lo, voff+hi)
@@ -313,12 +313,41 @@ __device__ __forceinline__ int64_t node_bound(int64_t i, int64_t n, int level) {
   return (i * n) >> level;
 }
 
+// Power-of-two scales of the split products.  exp_above(mx) is an e with mx < 2^e
+// (0 for mx = 0), kept in [-1000, 1022] so that 2^e and 2^-e are both normal: a
+// subnormal mx gets 2^-1000, which still bounds it; mx >= 2^1022 is out of range.
+// pow2c(e) is 2^e built from its exponent bits for e in [-1022, 1023] and clamped
+// there (bare bit building gives inf at e = +-1024 and wraps the sign bit beyond, so
+// a 0 * inf in a scaled product becomes NaN).  scale2(x, e) = x 2^e for |e| <= 2044,
+// in two such factors, for exponents that are sums of two scales.
+__device__ __forceinline__ int exp_above(double mx) {
+  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
+  return e < -1000 ? -1000 : (e > 1022 ? 1022 : e);
+}
+__device__ __forceinline__ double pow2c(int e) {
+  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
+  return __hiloint2double((1023 + e) << 20, 0);
+}
+__device__ __forceinline__ double scale2(double x, int e) {
+  const int h = e / 2;
+  return (x * pow2c(h)) * pow2c(e - h);
+}
+
 // A non-finite d or e entry is read as zero wherever the eigensolver reads the
 // caller's arrays (the corner-modified diagonal, the leaves, each merge's coupling)
 // and the call reports TDC_ENONFINITE: that problem's results are then not those of
 // its input, but no NaN or infinity reaches the orderings, counts and ranks that
 // later kernels index with.
 __device__ __forceinline__ double finite_or_zero(double x) { return isfinite(x) ? x : 0.0; }
+
+// An entry of the caller's d or e as the solver reads it: non-finite as zero, then times
+// 2^-escale (exact).  A problem whose largest finite |d|, |e| lies outside
+// [2^-400, 2^400] is solved scaled by the power of two that brings it into [1, 2), so
+// that no square, product or sum of its entries overflows or underflows; escale is 0
+// otherwise and the values enter unchanged.
+__device__ __forceinline__ double input_entry(double x, int escale) {
+  return escale ? scale2(finite_or_zero(x), -escale) : finite_or_zero(x);
+}
 
 __device__ __forceinline__ Node make_node(const Plan& P, int level, int64_t g) {
   Node nd;
@@ -340,7 +369,7 @@ __device__ __forceinline__ Node make_node(const Plan& P, int level, int64_t g) {
     nd.dst = b0 + nd.lo + nd.lo * l0; nd.ldd = l0;
     nd.src = b1 + nd.lo + nd.lo * l1; nd.lds = l1;
   }
-  nd.b = finite_or_zero(P.e[p->off_de + nd.mid - 1]);
+  nd.b = input_entry(P.e[p->off_de + nd.mid - 1], p->escale);
   return nd;
 }
 
@@ -386,26 +415,6 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   y = y * fma(-h * y, y, 1.5);
   y = y * fma(-h * y, y, 1.5);
   return y;
-}
-
-// Power-of-two scales of the split products.  exp_above(mx) is an e with mx < 2^e
-// (0 for mx = 0), kept in [-1000, 1022] so that 2^e and 2^-e are both normal: a
-// subnormal mx gets 2^-1000, which still bounds it; mx >= 2^1022 is out of range.
-// pow2c(e) is 2^e built from its exponent bits for e in [-1022, 1023] and clamped
-// there (bare bit building gives inf at e = +-1024 and wraps the sign bit beyond, so
-// a 0 * inf in a scaled product becomes NaN).  scale2(x, e) = x 2^e for |e| <= 2044,
-// in two such factors, for exponents that are sums of two scales.
-__device__ __forceinline__ int exp_above(double mx) {
-  const int e = mx > 0.0 ? ilogb(mx) + 1 : 0;
-  return e < -1000 ? -1000 : (e > 1022 ? 1022 : e);
-}
-__device__ __forceinline__ double pow2c(int e) {
-  e = e < -1022 ? -1022 : (e > 1023 ? 1023 : e);
-  return __hiloint2double((1023 + e) << 20, 0);
-}
-__device__ __forceinline__ double scale2(double x, int e) {
-  const int h = e / 2;
-  return (x * pow2c(h)) * pow2c(e - h);
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

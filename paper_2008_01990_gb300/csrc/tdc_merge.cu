@@ -46,16 +46,41 @@ __global__ void k_dmod(Plan P) {
     const double d0 = P.d[p.off_de + r];
     bool ok = isfinite(d0);
     if (r + 1 < p.n) ok = ok && isfinite(P.e[p.off_de + r]);
-    double d = finite_or_zero(d0);
-    if (is_boundary(r, p.n, p.depth)) d -= fabs(finite_or_zero(P.e[p.off_de + r - 1]));
-    if (is_boundary(r + 1, p.n, p.depth)) d -= fabs(finite_or_zero(P.e[p.off_de + r]));
+    double d = input_entry(d0, p.escale);
+    if (is_boundary(r, p.n, p.depth)) d -= fabs(input_entry(P.e[p.off_de + r - 1], p.escale));
+    if (is_boundary(r + 1, p.n, p.depth)) d -= fabs(input_entry(P.e[p.off_de + r], p.escale));
     if (!ok) set_status(P.status, TDC_ENONFINITE);
     P.v.dmod[s] = d;
   }
 }
 
+// Each problem's input scale (a block per problem): the largest finite |d|, |e|, and
+// escale = its binary exponent when that lies outside [2^-400, 2^400], else 0.
+__global__ void __launch_bounds__(256) k_input_scale(Plan P) {
+  __shared__ double red[8];
+  for (int pi = blockIdx.x; pi < P.nprob; pi += gridDim.x) {
+    const Problem& p = P.prob[pi];
+    double m = 0.0;
+    for (int64_t r = threadIdx.x; r < p.n; r += blockDim.x) {
+      m = fmax(m, fabs(finite_or_zero(P.d[p.off_de + r])));
+      if (r + 1 < p.n) m = fmax(m, fabs(finite_or_zero(P.e[p.off_de + r])));
+    }
+    m = warp_max(m);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+      m = fmax(m, red[0]);
+      const bool out = m > 0x1p400 || (m > 0.0 && m < 0x1p-400);
+      const_cast<Problem*>(P.prob)[pi].escale = out ? ilogb(m) : 0;
+    }
+  }
+}
+
 cudaError_t launch_dmod(const Plan& P, cudaStream_t s) {
   if (P.nslots == 0) return cudaSuccess;
+  k_input_scale<<<(unsigned)std::min<int64_t>(P.nprob, 152 * 8), 256, 0, s>>>(P);
   int64_t blocks = (P.nslots + 255) / 256;
   if (blocks > 152 * 16) blocks = 152 * 16;
   k_dmod<<<(unsigned)blocks, 256, 0, s>>>(P);
@@ -102,7 +127,7 @@ __global__ void __launch_bounds__(64) k_leaf(Plan P, int64_t nleaves) {
   for (int k = tid; k < L * L; k += blockDim.x) Qs[k] = ((k % L) == (k / L)) ? 1.0 : 0.0;
   for (int k = tid; k < L; k += blockDim.x) {
     dd[k] = P.v.dmod[p.voff + lo + k];
-    ee[k] = (k < L - 1) ? finite_or_zero(P.e[p.off_de + lo + k]) : 0.0;
+    ee[k] = (k < L - 1) ? input_entry(P.e[p.off_de + lo + k], p.escale) : 0.0;
   }
   if (tid == 0) ctrl[4] = (L <= 1) ? 1 : 0;
   __syncthreads();
@@ -303,7 +328,7 @@ __global__ void __launch_bounds__(1024) k_leaf_multi(Plan P, int64_t nleaves, in
     if (k < L) {
       const Problem& pr = P.prob[sprob[l]];
       dd[k] = P.v.dmod[pr.voff + slo[l] + k];
-      ee[k] = (k < L - 1) ? finite_or_zero(P.e[pr.off_de + slo[l] + k]) : 0.0;
+      ee[k] = (k < L - 1) ? input_entry(P.e[pr.off_de + slo[l] + k], pr.escale) : 0.0;
     }
   }
   __syncthreads();
@@ -988,7 +1013,7 @@ __device__ __forceinline__ Slot slot_of(const Plan& P, int level, int nprob_act,
   o.j = (int)(r - lo);
   o.K = P.m.K[o.g];
   o.v0 = p.voff + lo;
-  o.rho = 2.0 * fabs(finite_or_zero(P.e[p.off_de + mid - 1]));
+  o.rho = 2.0 * fabs(input_entry(P.e[p.off_de + mid - 1], p.escale));
   o.valid = o.j < o.K;
   return o;
 }
@@ -2491,7 +2516,7 @@ __global__ void __launch_bounds__(256) k_sign_out(Plan P, int sign_normalise) {
       }
     }
   }
-  if (lane == 0) P.lam_out[p.off_de + c] = P.v.lam[s];
+  if (lane == 0) P.lam_out[p.off_de + c] = p.escale ? scale2(P.v.lam[s], p.escale) : P.v.lam[s];
 }
 
 cudaError_t launch_sign_and_output(const Plan& P, int sign_normalise, cudaStream_t s) {

@@ -83,6 +83,35 @@ def test_nonfinite_problem_leaves_the_others_intact(tdc):
     assert tdc.sync_status() == 0
 
 
+def test_each_problem_takes_its_own_scale(tdc):
+    """A batch whose second problem is scaled by 2^700 and third by 2^-700: each problem
+    is solved as the problem with its largest entry in [1, 2), so all three give the
+    eigenvectors of those problems bit for bit and the eigenvalues scaled back exactly."""
+    sizes = [300, 500, 700]
+    d, e, offs, qoffs = batch(sizes, 9)
+    for i in range(3):
+        a, b = offs[i], offs[i] + sizes[i]
+        m = np.frexp(max(np.abs(d[a:b]).max(), np.abs(e[a:b - 1]).max()))[1] - 1
+        d[a:b], e[a:b - 1] = np.ldexp(d[a:b], -m), np.ldexp(e[a:b - 1], -m)
+    ks = [0, 700, -700]
+    ds, es = d.copy(), e.copy()
+    for i, k in enumerate(ks):
+        a, b = offs[i], offs[i] + sizes[i]
+        ds[a:b], es[a:b - 1] = np.ldexp(d[a:b], k), np.ldexp(e[a:b - 1], k)
+    o = tdc.default_opts(leaf=16)
+    outs = []
+    for dd, ee in ((d, e), (ds, es)):
+        lam = torch.zeros(int(offs[-1]), dtype=torch.float64, device=DEV)
+        Q = torch.zeros(int(qoffs[-1]), dtype=torch.float64, device=DEV)
+        outs.append(tdc.eig_batched(sizes, torch.tensor(dd, device=DEV), torch.tensor(ee, device=DEV), offs[:-1],
+                                    qoffs[:-1], lam, Q, o, check=True))
+    (lam0, Q0), (lam1, Q1) = [(l.cpu().numpy(), q.cpu().numpy()) for l, q in outs]
+    assert np.array_equal(Q0, Q1)
+    for i, k in enumerate(ks):
+        a, b = offs[i], offs[i] + sizes[i]
+        assert np.array_equal(lam1[a:b], np.ldexp(lam0[a:b], k))
+
+
 def test_autotuner_picks_and_caches(tdc, tmp_path):
     from paper_2008_01990_gb300 import autotune
     sizes = inputs.batched_sizes(48, 64, 600, 41)

@@ -216,6 +216,28 @@ def test_status_nonfinite_input(tdc, n, where, val):
     assert tdc.sync_status() == 0
 
 
+def _unit_scaled(d, e):
+    """d, e times the power of two that puts their largest magnitude in [1, 2)."""
+    m = np.frexp(max(np.abs(d).max(), np.abs(e).max()))[1] - 1
+    return np.ldexp(d, -m), np.ldexp(e, -m)
+
+
+@pytest.mark.parametrize("n,k", [(3000, 600), (3000, -600), (3000, 1000), (3000, -900), (9000, 600)])
+def test_extreme_scales_are_solved_exactly_scaled(tdc, n, k):
+    """Entries far outside [2^-400, 2^400] (where squares and products of entries would
+    overflow or underflow): the problem is solved scaled by the power of two that puts its
+    largest entry in [1, 2), so its eigenvectors equal, bit for bit, those of that problem
+    and its eigenvalues are that problem's times 2^k exactly (n = 9000 takes the
+    structured products)."""
+    d0, e0 = _unit_scaled(*inputs.uniform_tridiag(n, 7))
+    o = tdc.default_opts(leaf=16)
+    lam0, Q0 = tdc.eig(torch.tensor(d0, device=DEV), torch.tensor(e0, device=DEV), o, check=True)
+    lam1, Q1 = tdc.eig(torch.tensor(np.ldexp(d0, k), device=DEV), torch.tensor(np.ldexp(e0, k), device=DEV), o,
+                       check=True)
+    assert torch.equal(Q0, Q1)
+    assert np.array_equal(lam1.cpu().numpy(), np.ldexp(lam0.cpu().numpy(), k))
+
+
 def test_c2_toeplitz_16384_sampled(tdc):
     """Full-size tridiag(1,2,1) at n=16384 in the benchmark's configuration (leaf 16,
     default merge): every eigenvalue against the closed form; residual, orthogonality and
