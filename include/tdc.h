@@ -323,6 +323,8 @@ int tdc_ormtr(int64_t n, int64_t ncols, const double* A, int64_t lda, const doub
 /* tdc_syevd: A = Z diag(lam) Z^T for the dense symmetric A (lower triangle read, A
  * destroyed): tdc_sytrd, tdc_eig on (d, e) with the options o, tdc_ormtr on the
  * eigenvectors.  lam[n] ascending, Z n x n (ldz >= n).  One status for the whole call.
+ * A whose largest finite |entry| lies outside [2^-400, 2^400] is scaled in place by the
+ * power of two that puts it in [1, 2) before the reduction (exact), and lam scaled back.
  * ws of tdc_syevd_workspace_size(n, o) bytes.  Errors: -1 n, -2 A, -3 lda, -4 lam, -5 Z,
  * -6 ldz, -9 options, TDC_ENOWS, TDC_ECUDA, or those of the steps. */
 int tdc_syevd_workspace_size(int64_t n, const tdc_opts* o, size_t* bytes);
@@ -367,10 +369,14 @@ int tdc_dft_gemm(int64_t m, int64_t n, const double* A, int64_t lda, double* Cre
  * at its middle; the b x b coupling block, row k being B_k, is written as
  * sum_k (x_k; y_k)(x_k; y_k)^T with x_k = s_k e, y_k = B_k / s_k, s_k = sqrt(||B_k||), and
  * subtracted from the two halves' corners; leaves of at most max(128, 8b) rows are solved
- * densely (tdc_syevd's kernels); a merge takes the b terms in turn as rank-one
+ * densely, as one batch (a block per leaf reduces it to tridiagonal form and
+ * back-transforms, tdc_eig_batched solves the tridiagonals); a merge takes the b terms in turn as rank-one
  * modifications D + z z^T with z = Q^T (x_k; y_k): sort, deflation (Section 3.2's two
  * tests), the secular equation, the Cauchy-like update of the non-deflated columns (split
- * tensor-core product from K = 128 on).  lam[n] ascending, Q n x n (ldq >= n).  The call
+ * tensor-core product from K = 128 on).  A band whose largest finite |entry| lies
+ * outside [2^-400, 2^400] is solved scaled by the power of two that puts it in [1, 2)
+ * (exact; AB itself is not modified) and lam scaled back.  lam[n] ascending, Q n x n
+ * (ldq >= n).  The call
  * reads each rank-one step's deflation count back to the host, so it returns when the
  * solve is done.  ws of tdc_sbevd_workspace_size(n, b, o) bytes.  Errors: -1 n, -2 b,
  * -3 AB, -4 ldab, -5 lam, -6 Q, -7 ldq, -10 options, TDC_ENOWS, TDC_ECUDA, or those of

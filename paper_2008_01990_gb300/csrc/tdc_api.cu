@@ -1594,7 +1594,8 @@ int ormtr_run(int64_t n, int64_t ncols, const double* A, int64_t lda, const doub
   return TDC_OK;
 }
 
-size_t syevd_vec_bytes(int64_t n) { return 3 * align_up(sizeof(double) * (size_t)std::max<int64_t>(n, 1)); }
+// d, e, tau and 256 bytes for the range guard's maximum and exponent
+size_t syevd_vec_bytes(int64_t n) { return 3 * align_up(sizeof(double) * (size_t)std::max<int64_t>(n, 1)) + 256; }
 
 // ---- symmetric band eigenproblem: divide and conquer with b rank-one merges per node
 struct BandNode {
@@ -1718,6 +1719,10 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
   S.dp = scol;
   S.dn = Dd;
   if (launch_bd_copy_band(n, (int)b, AB, ldab, ABw, cs) != cudaSuccess) return TDC_ECUDA;
+  // entries outside [2^-400, 2^400]: the band copy scaled by a power of two
+  unsigned long long* rmx = (unsigned long long*)(base + L.cnt + 40);
+  int* res = (int*)(base + L.cnt + 48);
+  if (launch_range_scale(ABw, ldw, n, ldw, 0, rmx, res, cs) != cudaSuccess) return TDC_ECUDA;
   if (launch_bd_zero(n, n, Q, ldq, cs) != cudaSuccess) return TDC_ECUDA;
   k_iota<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, cs>>>(iota, n);
   // tearings (they touch disjoint entries: nodes have at least 4b rows)
@@ -1814,7 +1819,7 @@ int sbevd_run(int64_t n, int64_t b, const double* AB, int64_t ldab, double* lam,
     if (cudaMemcpyAsync(lam + nd.lo, Ds, sizeof(double) * nn, cudaMemcpyDeviceToDevice, cs) != cudaSuccess)
       return TDC_ECUDA;
   }
-  return TDC_OK;
+  return launch_range_unscale(lam, n, res, cs) == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
 }  // namespace
@@ -1948,13 +1953,19 @@ int tdc_syevd(int64_t n, double* A, int64_t lda, double* lam, double* Z, int64_t
   double* d = (double*)base;
   double* e = (double*)(base + vb);
   double* tau = (double*)(base + 2 * vb);
+  unsigned long long* rmx = (unsigned long long*)(base + 3 * vb);
+  int* res = (int*)(base + 3 * vb + 8);
   char* rest = base + syevd_vec_bytes(n);
   const size_t rest_bytes = ws_bytes - (size_t)(rest - (char*)ws);
+  // entries outside [2^-400, 2^400]: solved scaled by a power of two (A is destroyed anyway)
+  if (launch_range_scale(A, n, n, lda, 1, rmx, res, cs) != cudaSuccess) return TDC_ECUDA;
   int r = sytrd_run(n, A, lda, d, e, tau, rest, op, st, cs);
   if (r != TDC_OK) return r;
   r = tdc_eig(n, d, e, lam, Z, ldz, rest, rest_bytes, &op, stream);
   if (r != TDC_OK) return r;
-  return ormtr_run(n, n, A, lda, tau, Z, ldz, rest, op, st, cs);
+  r = ormtr_run(n, n, A, lda, tau, Z, ldz, rest, op, st, cs);
+  if (r != TDC_OK) return r;
+  return launch_range_unscale(lam, n, res, cs) == cudaSuccess ? TDC_OK : TDC_ECUDA;
 }
 
 // Products with a structured B given by generators (Toeplitz, Hankel, Vandermonde, the

@@ -630,6 +630,14 @@ cudaError_t launch_bd_leaf_trd(const BdLeafArgs& A, const BdLeafTable& T, cudaSt
 cudaError_t launch_bd_leaf_back(const BdLeafArgs& A, const BdLeafTable& T, cudaStream_t s);
 cudaError_t launch_bd_z(int64_t nn, const double* Q, int64_t ldq, int64_t ra, int64_t rb, int b, const double* w,
                         double* z, cudaStream_t s);
+// Overflow guard of the dense and band solvers: the largest finite |entry| of a column-major
+// rows x cols block (lower != 0: its lower triangle only) and, when that lies outside
+// [2^-400, 2^400], the block times the power of two 2^-escale that puts it in [1, 2)
+// (exact); *escale = 0 otherwise.  mx and escale: 8 and 4 bytes of device scratch.
+// launch_range_unscale: x[0:n) times 2^escale.
+cudaError_t launch_range_scale(double* A, int64_t rows, int64_t cols, int64_t ld, int lower, unsigned long long* mx,
+                               int* escale, cudaStream_t s);
+cudaError_t launch_range_unscale(double* x, int64_t n, const int* escale, cudaStream_t s);
 // Scratch of the band sort and deflation (arrays of nn entries, free while they run).
 struct BdScratch {
   double* sk;      // sort: the chunks' sorted keys

@@ -583,6 +583,62 @@ __global__ void k_trd_tail(int64_t n, const double* A, int64_t lda, double* d, d
   tau[n - 2] = 0.0;
 }
 
+// Range guard of the dense and band solvers (see launch_range_scale).
+__global__ void __launch_bounds__(256) k_range_max(const double* A, int64_t rows, int64_t cols, int64_t ld, int lower,
+                                                  unsigned long long* mx) {
+  double m = 0.0;
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % rows, j = t / rows;
+    if (lower && i < j) continue;
+    const double x = A[i + j * ld];
+    if (isfinite(x)) m = fmax(m, fabs(x));
+  }
+  m = warp_max(m);
+  if ((threadIdx.x & 31) == 0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
+}
+
+__device__ __forceinline__ int range_exp(const unsigned long long* mx) {
+  const double m = __longlong_as_double((long long)*mx);
+  return (m > 0x1p400 || (m > 0.0 && m < 0x1p-400)) ? ilogb(m) : 0;
+}
+
+__global__ void __launch_bounds__(256) k_range_apply(double* A, int64_t rows, int64_t cols, int64_t ld, int lower,
+                                                    const unsigned long long* mx, int* escale) {
+  const int es = range_exp(mx);
+  if (blockIdx.x == 0 && threadIdx.x == 0) *escale = es;
+  if (es == 0) return;
+  const int64_t total = rows * cols;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = t % rows, j = t / rows;
+    if (lower && i < j) continue;
+    A[i + j * ld] = scale2(A[i + j * ld], -es);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_range_unscale(double* x, int64_t n, const int* escale) {
+  const int es = *escale;
+  if (es == 0) return;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+    x[t] = scale2(x[t], es);
+}
+
+cudaError_t launch_range_scale(double* A, int64_t rows, int64_t cols, int64_t ld, int lower, unsigned long long* mx,
+                               int* escale, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, 152 * 8));
+  k_range_max<<<g, 256, 0, s>>>(A, rows, cols, ld, lower, mx);
+  k_range_apply<<<g, 256, 0, s>>>(A, rows, cols, ld, lower, mx, escale);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_range_unscale(double* x, int64_t n, const int* escale, cudaStream_t s) {
+  k_range_unscale<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)), 256, 0, s>>>(x, n,
+                                                                                                         escale);
+  return cudaGetLastError();
+}
+
 int trd_panel_grid() {
   static int grid[64] = {0};
   int dev = 0;

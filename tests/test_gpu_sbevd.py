@@ -62,6 +62,19 @@ def test_sbevd_clustered_laplace_2500(tdc):
     assert res <= 50 and orth <= 50, (res, orth)
 
 
+@pytest.mark.parametrize("k", [700, -700])
+def test_sbevd_extreme_scales_are_solved_exactly_scaled(tdc, k):
+    """A band matrix scaled far outside [2^-400, 2^400] is solved as the band matrix with
+    its largest entry in [1, 2): the same eigenvectors bit for bit, its eigenvalues times
+    2^k exactly."""
+    AB = inputs.band_sym("uniform", 1000, 8, seed=3)
+    AB0 = np.ldexp(AB, -(np.frexp(np.abs(AB).max())[1] - 1))
+    lam0, Q0 = tdc.sbevd(torch.tensor(AB0, device=DEV), check=True)
+    lam1, Q1 = tdc.sbevd(torch.tensor(np.ldexp(AB0, k), device=DEV), check=True)
+    assert torch.equal(Q0, Q1)
+    assert np.array_equal(lam1.cpu().numpy(), np.ldexp(lam0.cpu().numpy(), k))
+
+
 def test_sbevd_tridiagonal_case_matches_eig(tdc):
     """b = 1 is the tridiagonal problem: the band solver and tdc_eig agree."""
     n = 900

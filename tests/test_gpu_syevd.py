@@ -204,6 +204,20 @@ def test_band_matrix_reduction_and_solve(tdc):
     assert res <= 50 and orth / (n * EPS) <= 50, (res, orth / (n * EPS))
 
 
+@pytest.mark.parametrize("k", [600, -600, 1000, -800])
+def test_syevd_extreme_scales_are_solved_exactly_scaled(tdc, k):
+    """A dense matrix scaled far outside [2^-400, 2^400] (where the reduction's norms would
+    overflow or underflow) is solved as the matrix with its largest entry in [1, 2): the
+    same eigenvectors bit for bit, its eigenvalues times 2^k exactly."""
+    n = 700
+    A = inputs.dense_sym("uniform", n, seed=70)
+    A0 = np.ldexp(A, -(np.frexp(np.abs(A).max())[1] - 1))
+    lam0, Z0 = tdc.syevd(torch.tensor(A0, device=DEV), check=True)
+    lam1, Z1 = tdc.syevd(torch.tensor(np.ldexp(A0, k), device=DEV), check=True)
+    assert torch.equal(Z0, Z1)
+    assert np.array_equal(lam1.cpu().numpy(), np.ldexp(lam0.cpu().numpy(), k))
+
+
 def test_sytrd_barrier_timeout_reports_status(tdc):
     """A panel whose grid barriers may poll only once gives up with TDC_ETIMEOUT instead of
     waiting; the context stays usable and the next call succeeds."""
