@@ -127,7 +127,22 @@ def batched_uniform(sizes, seed: int):
     return d, e, offs
 
 
+def glued_wilkinson(n: int, m: int = 10, glue: float = 1e-10):
+    """Copies of the Wilkinson matrix W+ of order 2m + 1 (d_i = |m - i|, e_i = 1) joined by
+    off-diagonal entries `glue`, cut to order n: each eigenvalue of W+ appears once per copy
+    to within about the glue, so the merges deflate long runs of nearly equal poles (chains
+    of type-2 rotations)."""
+    k = 2 * m + 1
+    c = (n + k - 1) // k
+    d = np.tile(np.abs(np.arange(k) - m).astype(np.float64), c)[:n]
+    e = np.ones(max(c * k - 1, 0))
+    e[k - 1::k] = glue
+    return d, e[: max(n - 1, 0)]
+
+
 def family(name: str, n: int, seed: int = 1):
+    if name == "wilkinson":
+        return glued_wilkinson(n)
     if name == "uniform":
         return uniform_tridiag(n, seed)
     if name == "toeplitz":
