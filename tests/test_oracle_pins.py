@@ -343,7 +343,7 @@ def test_dc_vs_dense_library(orc):
 
 
 @pytest.mark.parametrize("fam,n,leaf", [("sht", 400, 32), ("hermite", 333, 16), ("clement", 257, 8),
-                                        ("toeplitz", 300, 64)])
+                                        ("toeplitz", 300, 64), ("wilkinson", 525, 16)])
 def test_dc_families_vs_dense_library(orc, fam, n, leaf):
     # every family the GPU parity tests use: eigenvalues against the dense library
     # solver, residual and orthogonality ratios
@@ -353,6 +353,17 @@ def test_dc_families_vs_dense_library(orc, fam, n, leaf):
     assert np.max(np.abs(lam - np.linalg.eigvalsh(dense(d, e)))) <= 1e-12 * nT
     res, orth = ratios(d, e, lam, Q)
     assert res <= 50 and orth <= 50
+
+
+def test_glued_wilkinson_is_copies_of_w21(orc):
+    # with the glue at zero the matrix is 5 decoupled copies of W+_21: every eigenvalue of
+    # W+_21 (dense library) five times; with the glue at 1e-10 each moves by at most the glue
+    from paper_2008_01990_gb300.inputs import glued_wilkinson
+    w = np.linalg.eigvalsh(dense(np.abs(np.arange(21) - 10).astype(float), np.ones(20)))
+    for glue in (0.0, 1e-10):
+        d, e = glued_wilkinson(105, glue=glue)
+        lam, _ = orc.eig(d, e, leaf=16)
+        assert np.max(np.abs(lam - np.sort(np.repeat(w, 5)))) <= (1e-13 if glue == 0.0 else 2e-10) * 11
 
 
 def test_dc_zero_coupling_deflates_everything(orc):
