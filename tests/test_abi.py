@@ -70,6 +70,13 @@ def test_host_argument_checks(lib):
     assert lib.tdc_eig_batched(3, nh.ctypes.data_as(P), nh.ctypes.data_as(P), nh.ctypes.data_as(P), bogus, bogus,
                                bogus, bogus, bogus, 1 << 30, None, None) == -1001
     assert lib.tdc_rank_one(4, bogus, bogus, -1.0, bogus, bogus, bogus, bogus, 8, bogus, 256, None) == -4
+    # the rank-one workspace holds the FP32 copies of the poles (about 20 K bytes)
+    b = ctypes.c_size_t(0)
+    assert lib.tdc_rank_one_workspace_size(1000, ctypes.byref(b)) == 0 and b.value >= 20 * 1000
+    assert lib.tdc_rank_one(1000, bogus, bogus, 1.0, bogus, bogus, bogus, bogus, 8, bogus, b.value - 1,
+                            None) == tdc.TDC_ENOWS
+    assert lib.tdc_rank_one(1000, bogus, bogus, 1.0, bogus, bogus, bogus, bogus, 8, None, b.value,
+                            None) == tdc.TDC_ENOWS
     assert tdc.strerror(tdc.TDC_ENOWS).startswith("workspace")
     assert tdc.strerror(tdc.TDC_WPRECISION).startswith("warning")
 
