@@ -587,13 +587,12 @@ __global__ void k_trd_tail(int64_t n, const double* A, int64_t lda, double* d, d
 __global__ void __launch_bounds__(256) k_range_max(const double* A, int64_t rows, int64_t cols, int64_t ld, int lower,
                                                   unsigned long long* mx) {
   double m = 0.0;
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t % rows, j = t / rows;
-    if (lower && i < j) continue;
-    const double x = A[i + j * ld];
-    if (isfinite(x)) m = fmax(m, fabs(x));
-  }
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = (lower ? j : 0) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      const double x = A[i + j * ld];
+      if (isfinite(x)) m = fmax(m, fabs(x));
+    }
   m = warp_max(m);
   if ((threadIdx.x & 31) == 0) atomicMax(mx, (unsigned long long)__double_as_longlong(m));
 }
@@ -608,12 +607,10 @@ __global__ void __launch_bounds__(256) k_range_apply(double* A, int64_t rows, in
   const int es = range_exp(mx);
   if (blockIdx.x == 0 && threadIdx.x == 0) *escale = es;
   if (es == 0) return;
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t % rows, j = t / rows;
-    if (lower && i < j) continue;
-    A[i + j * ld] = scale2(A[i + j * ld], -es);
-  }
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = (lower ? j : 0) + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+      A[i + j * ld] = scale2(A[i + j * ld], -es);
 }
 
 __global__ void __launch_bounds__(256) k_range_unscale(double* x, int64_t n, const int* escale) {
@@ -627,7 +624,9 @@ cudaError_t launch_range_scale(double* A, int64_t rows, int64_t cols, int64_t ld
                                int* escale, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(mx, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((rows * cols + 255) / 256, 152 * 8));
+  // columns over grid.y, rows of a column over grid.x (coalesced, no index division)
+  const dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>((rows + 255) / 256, 8)),
+               (unsigned)std::max<int64_t>(1, std::min<int64_t>(cols, 1216)));
   k_range_max<<<g, 256, 0, s>>>(A, rows, cols, ld, lower, mx);
   k_range_apply<<<g, 256, 0, s>>>(A, rows, cols, ld, lower, mx, escale);
   return cudaGetLastError();
