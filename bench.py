@@ -922,6 +922,12 @@ def run_ours(args):
     Q_h = torch.empty(n, n, dtype=torch.float64).pin_memory()
     d_d = torch.empty_like(d)
     e_d = torch.empty_like(e)
+    # one untimed pass: the first copies through freshly pinned buffers map them
+    d_d.copy_(d_h, non_blocking=True)
+    e_d.copy_(e_h, non_blocking=True)
+    tdc.eig(d_d, e_d, opts, ws=wsb, lam=lam, Q=Q, stream=stream)
+    lam_h.copy_(lam, non_blocking=True)
+    Q_h.copy_(Q.t(), non_blocking=True)
     torch.cuda.synchronize()
     ee0 = torch.cuda.Event(enable_timing=True)
     ee1 = torch.cuda.Event(enable_timing=True)
